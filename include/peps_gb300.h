@@ -1,0 +1,171 @@
+/*
+ * peps_gb300.h -- C ABI of the GB300 (sm_103a) hot path of the sampling-based finite-PEPS
+ * optimiser of arXiv:2503.12557.
+ *
+ * What the library computes, per configuration S of an Lx x Ly open-boundary PEPS with physical
+ * dimension d and virtual dimension D (paper Sec. "Finite PEPS and Sampling", Eq. (PsiS)):
+ *   - the boundary-MPS environments E^u[x], E^l[x] of the single-layer network projected on S,
+ *     truncated back to bond dimension chi after every MPS-MPO product (Sec. "On the boundary
+ *     MPS method"), every tensor divided by its largest modulus with the logarithms kept
+ *     (Sec. "On Numerical Stability");
+ *   - ln psi(S) (Eq. (boundary_MPS_approx));
+ *   - the local energy E_loc(S) = sum_S' <S|H|S'> psi(S')/psi(S) with environment reuse
+ *     (Eq. (local_obs), Sec. "On reusing environments"); diagonal terms cost no contraction;
+ *   - the log-derivatives O_{S,k} = d ln psi(S) / d theta_k (Sec. "Reformulation of the
+ *     imaginary-time Schroedinger equation", Eq. (tdvp));
+ *   - the MinSR update dtheta = -tau Obar^dag (Obar Obar^dag + lambda)^+ ebar (Eq. (tdvp_fast));
+ *   - Metropolis chains over S whose acceptance uses the same environment-reusing ratios.
+ *
+ * Conventions
+ *   Sites (x, y), x = 0..Lx-1 top to bottom, y = 0..Ly-1, linear index x*Ly + y.
+ *   Site tensor T[x,y][s, l, u, r, d]; legs pointing out of the lattice have dimension 1.
+ *   theta: all site tensors in C order, concatenated in site order (length N_p, see
+ *   peps_num_params).  O rows use the same order.
+ *   Configurations: uint8, Ns x (Lx*Ly), row major, values 0..d-1.
+ *   Every pointer argument named *_dev is DEVICE memory owned by the caller; the library never
+ *   frees or keeps it beyond the call.  Host pointers are named *_host.
+ *   Every call is asynchronous on the caller's CUDA stream (passed as void*, a cudaStream_t;
+ *   NULL = legacy default stream).  Argument errors are reported before any launch.
+ *   Per-sample numerical problems are status bits written to status_dev (0 = clean):
+ *     PEPS_ST_NEAR_DEGENERATE  a truncation cut where the kept and the first discarded singular
+ *                              value differ by less than 1e-8 sigma_1 (and the latter is above
+ *                              1e-12 sigma_1): the truncated state is not unique there;
+ *     PEPS_ST_ZERO_NORM        an environment tensor or partial contraction was exactly zero;
+ *     PEPS_ST_NONFINITE        a NaN or Inf appeared (ln psi, E_loc or O of that sample invalid);
+ *     PEPS_ST_NOCONV           a one-sided Jacobi SVD hit its sweep limit.
+ *   Nothing traps on the device.
+ */
+#ifndef PEPS_GB300_H
+#define PEPS_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PEPS_OK = 0,
+    PEPS_E_ARG = -1,        /* NULL pointer, negative size, bad enum value            */
+    PEPS_E_SHAPE = -2,      /* lattice / chi / Ns outside what the handle supports     */
+    PEPS_E_WORKSPACE = -3,  /* device allocation failed                                */
+    PEPS_E_CUDA = -4,       /* a CUDA runtime call failed (peps_last_error has detail) */
+    PEPS_E_UNSUPPORTED = -5 /* option combination not implemented                      */
+} peps_status;
+
+enum {
+    PEPS_ST_NEAR_DEGENERATE = 1,
+    PEPS_ST_ZERO_NORM = 2,
+    PEPS_ST_NONFINITE = 4,
+    PEPS_ST_NOCONV = 8
+};
+
+/* Arithmetic of the contraction kernels.  FP64: every step in double.  FP32: the environment,
+ * truncation and sandwich arithmetic in float, logarithms and E_loc accumulated in double. */
+typedef enum { PEPS_PREC_FP64 = 0, PEPS_PREC_FP32 = 1 } peps_prec;
+
+typedef enum { PEPS_MOVE_EXCHANGE = 0, PEPS_MOVE_FLIP = 1 } peps_move;
+
+typedef struct {
+    int Lx, Ly;   /* lattice, Lx >= 2, Ly >= 2                                              */
+    int d;        /* physical dimension, 2 <= d <= 4                                         */
+    int D;        /* virtual bond dimension, 1 <= D <= 8                                     */
+    int chi;      /* boundary-MPS bond dimension D_c (paper's notation), D <= chi <= 64      */
+    int prec;     /* peps_prec                                                               */
+    int max_samples; /* largest Ns any later call may pass (sizes the environment store)     */
+} peps_config;
+
+/* One local Hamiltonian term: h is a d^k x d^k complex matrix, row major, interleaved
+ * (re, im) doubles, h[a][b] = <S_loc = a| h |S'_loc = b>, local index a = sum_i s_{sites[i]}
+ * d^(k-1-i).  The sites must lie in one row, or in two adjacent rows, and span at most two
+ * adjacent columns (nearest-neighbour bonds, plaquette diagonals, plaquette triangles,
+ * single sites). */
+typedef struct {
+    int nsites;          /* k, 1..4 */
+    int sites[4];
+    const double* h_host;
+} peps_term;
+
+/* H = sum_terms h + sum_pairs v s_i s_j + sum_i onsite[i][s_i].  All host memory, read during
+ * the call that receives it. */
+typedef struct {
+    int nterms;
+    const peps_term* terms;
+    int npairs;
+    const int* pair_ij_host;     /* npairs x 2 site indices                  */
+    const double* pair_v_host;   /* npairs coefficients                      */
+    const double* onsite_host;   /* (Lx*Ly) x d, may be NULL                 */
+} peps_hamiltonian;
+
+typedef struct peps_handle peps_handle;
+
+/* Create a handle for one lattice / chi / precision.  Allocates the parameter copy and the
+ * environment store for cfg->max_samples configurations on the current CUDA device.
+ * Returns PEPS_E_SHAPE when the sizes are outside the limits stated in peps_config. */
+peps_status peps_create(peps_handle** out, const peps_config* cfg);
+peps_status peps_destroy(peps_handle* h);
+
+/* N_p = sum over sites of d * Dl * Du * Dr * Dd (boundary legs of dimension 1). */
+long long peps_num_params(const peps_handle* h);
+
+/* Copy theta (N_p doubles, device) into the handle's padded kernel layout (converted to the
+ * handle's precision).  Later calls use this copy until the next peps_set_params. */
+peps_status peps_set_params(peps_handle* h, const double* theta_dev, void* stream);
+
+/* ln|psi_top(S)| and its phase (0 or pi for a real PEPS), psi_top = E^u[Lx-2] . T_proj[Lx-1]
+ * (Eq. (boundary_MPS_approx) with i = Lx-1).  logabs_dev, phase_dev: Ns doubles;
+ * status_dev: Ns int32. */
+peps_status peps_amplitudes(peps_handle* h, const uint8_t* S_dev, int Ns,
+                            double* logabs_dev, double* phase_dev, int32_t* status_dev, void* stream);
+
+/* E_loc(S) (Eq. (local_obs)) for every configuration; eloc_dev: Ns x 2 doubles (re, im).
+ * A term inside row x uses psi_x = E^u[x-1] . T_proj[x] . E^l[x+1] for S and S'; a term over
+ * rows x, x+1 uses psi_{x,x+1} = E^u[x-1] . T_proj[x] . T_proj[x+1] . E^l[x+2]. */
+peps_status peps_local_energy(peps_handle* h, const peps_hamiltonian* H, const uint8_t* S_dev, int Ns,
+                              double* eloc_dev, int32_t* status_dev, void* stream);
+
+/* O_{S,k} (Ns x N_p, row major) in the handle's precision: double for FP64, float for FP32.
+ * O_{S,k} = delta_{s, s_xy} Env_xy[l,u,r,d] / psi_x(S) for k = (x, y, s, l, u, r, d). */
+peps_status peps_logderiv(peps_handle* h, const uint8_t* S_dev, int Ns, void* O_dev,
+                          int32_t* status_dev, void* stream);
+
+/* All of the above from one environment pass: any of logabs/phase/eloc/O may be NULL
+ * (H must be non-NULL when eloc_dev is). */
+peps_status peps_evaluate(peps_handle* h, const peps_hamiltonian* H, const uint8_t* S_dev, int Ns,
+                          double* logabs_dev, double* phase_dev, double* eloc_dev, void* O_dev,
+                          int32_t* status_dev, void* stream);
+
+/* MinSR step (Eq. (tdvp_fast)):
+ *   w_S = w_dev[S] / sum w (uniform 1/Ns when w_dev is NULL);
+ *   Obar = sqrt(w) (O - w^T O), ebar = sqrt(w) (Re E_loc - w^T Re E_loc);
+ *   T = Obar Obar^T = V diag(Lambda) V^T;  kept = Lambda_i > rcond * max Lambda (all when rcond == 0);
+ *   dtheta = -tau Obar^T V diag(kept / (Lambda + lambda)) V^T ebar.
+ * O_dev: Ns x N_p in the handle's precision (as written by peps_logderiv); eloc_dev: Ns x 2
+ * doubles (the real parts are used: real PEPS); dtheta_dev: N_p doubles (written);
+ * info_dev: 4 doubles (rank kept, min Lambda, max Lambda, Jacobi sweeps used).
+ * Needs lambda > 0 or rcond > 0.  The Gram matrix and the eigendecomposition are FP64. */
+peps_status minsr_step(peps_handle* h, const void* O_dev, const double* eloc_dev, const double* w_dev,
+                       int Ns, double lambda, double rcond, double tau, double* dtheta_dev,
+                       double* info_dev, void* stream);
+
+/* nsweeps Metropolis sweeps of Ns independent chains (configurations updated in place).
+ * One sweep: bottom environments of the current S; then for x = 0..Lx-1 the moves inside row
+ * x in column order (exchange: bonds (x,y)-(x,y+1); flip: sites (x,y)) with psi_x ratios,
+ * then (exchange only, x < Lx-1) the vertical bonds (x,y)-(x+1,y) with psi_{x,x+1} ratios,
+ * then E^u[x] from the updated row.  Move slot k of sweep t of chain c draws
+ * u = Philox4x32-10(counter = (k, sweep0 + t, c, 0), key = seed) as a 53-bit double and
+ * accepts iff u < |psi'/psi|^2.  accepted_dev: Ns int64, incremented by the accepted moves.
+ * status_dev: Ns int32 (OR of the sweeps' status bits). */
+peps_status peps_sample(peps_handle* h, int move, uint8_t* S_dev, int Ns, int nsweeps,
+                        uint64_t seed, uint64_t sweep0, long long* accepted_dev,
+                        int32_t* status_dev, void* stream);
+
+/* Text of the last error seen by this handle (never NULL). */
+const char* peps_last_error(const peps_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PEPS_GB300_H */

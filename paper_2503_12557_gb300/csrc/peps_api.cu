@@ -1,0 +1,547 @@
+// C ABI of the finite-PEPS hot path (declared in include/peps_gb300.h): handle, buffer planner,
+// Hamiltonian packing and the entry points.  Host code only; every step of the path runs in
+// the kernels of peps_kernels.cu and peps_minsr.cu.
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+#include <algorithm>
+
+#include "peps_kernels.cuh"
+#include "../../include/peps_gb300.h"
+
+using namespace peps;
+
+struct KPlan {
+  Plan p;
+  size_t smem = 0;
+  int grid = 0;
+};
+
+struct peps_handle {
+  peps_config cfg{};
+  Geo g{};
+  long long Np = 0;
+  int nsm = 0;
+  size_t esz = 8;  // bytes per real
+  void* Tpad = nullptr;
+  long long* site_off = nullptr;  // device, N+1
+  std::vector<long long> site_off_h;
+  void* envs = nullptr;
+  double* logs = nullptr;
+  float* wdisc = nullptr;
+  double* rowout = nullptr;
+  double* pairout = nullptr;
+  int* status_tmp = nullptr;
+  char* gscratch = nullptr;
+  size_t gscratch_bytes = 0;
+  KPlan kp[4];  // env, row, pair, sample
+  // Hamiltonian cache
+  std::vector<char> ham_key;
+  std::vector<int> h_tinfo, h_ab, h_rowoff, h_pairoff, h_pij;
+  std::vector<double> h_eh, h_pv, h_onsite;
+  int* d_tinfo = nullptr;
+  int* d_ab = nullptr;
+  double* d_eh = nullptr;
+  int* d_rowoff = nullptr;
+  int* d_pairoff = nullptr;
+  int* d_pij = nullptr;
+  double* d_pv = nullptr;
+  double* d_onsite = nullptr;
+  int n_pair_terms = 0;
+  TermTab tt{};
+  DiagTab dg{};
+  // MinSR workspace
+  int ms_cap = 0;
+  long long ms_np = 0;
+  double *Obar = nullptr, *Tm = nullptr, *Vm = nullptr, *Hm = nullptr, *mean = nullptr, *ebar = nullptr,
+         *yv = nullptr, *xv = nullptr, *cnt = nullptr;
+  std::string err;
+};
+
+static peps_status fail(peps_handle* h, peps_status st, const std::string& msg) {
+  if (h) h->err = msg;
+  return st;
+}
+static peps_status cuda_fail(peps_handle* h, cudaError_t e, const char* where) {
+  if (h) h->err = std::string(where) + ": " + cudaGetErrorString(e);
+  return PEPS_E_CUDA;
+}
+#define CK(call, where)                                      \
+  do {                                                       \
+    cudaError_t _e = (call);                                 \
+    if (_e != cudaSuccess) return cuda_fail(h, _e, where);   \
+  } while (0)
+
+static size_t al(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
+
+// Place buffers (byte sizes, in priority order) into shared memory up to `budget`, the rest
+// into the per-CTA global arena.
+static void place(Plan& p, size_t& smem, size_t budget, const std::vector<std::pair<int, size_t>>& bufs) {
+  p.gmask = 0;
+  for (int b = 0; b < B_NBUF; ++b) p.off[b] = 0;
+  size_t s = 0, gl = 0;
+  for (auto& b : bufs) {
+    const size_t sz = al(b.second, 16);
+    if (s + sz <= budget) {
+      p.off[b.first] = s;
+      s += sz;
+    } else {
+      p.gmask |= 1u << b.first;
+      p.off[b.first] = gl;
+      gl += al(sz, 256);
+    }
+  }
+  smem = s;
+  p.gstride = gl;
+}
+
+static void plan_all(peps_handle* h) {
+  const Geo& g = h->g;
+  const size_t E = h->esz;
+  const int n = g.n, chi = g.chi, D = g.D, Ly = g.Ly;
+  const int mX = n + (n & 1);
+  const int Lr = D * chi;
+  const size_t budget = (E == 8) ? 200 * 1024 : 100 * 1024;
+  int ci = std::min(n, 16);
+  const size_t zleft = (size_t)n * D * n;
+  const size_t zright = (size_t)chi * D * D * chi + (size_t)n * Lr + (size_t)mX * Lr + (size_t)chi * Lr +
+                        (size_t)n * chi + (size_t)chi * D * chi;
+  const size_t zsz = std::max(zleft, zright);
+  // one-row / two-row temporaries
+  const size_t t1row = (size_t)chi * chi * D * D;
+  int cx = chi;
+  while (cx > 1 && (size_t)D * D * D * chi * cx > 8192) cx = (cx + 1) / 2;
+  const size_t t2row = (size_t)D * D * D * chi * cx;
+  // env plan
+  {
+    KPlan& k = h->kp[0];
+    k.p.ci = ci;
+    k.p.cx = cx;
+    std::vector<std::pair<int, size_t>> b = {
+        {B_RED, 40 * 8}, {B_SIG, (mX + 4) * E}, {B_SEL, 2 * mX * 4}, {B_A, (size_t)g.sT * E}, {B_E, (size_t)g.se * E},
+        {B_C, (size_t)n * chi * E}, {B_W, (size_t)ci * D * D * chi * E}, {B_R, (size_t)n * n * E}, {B_Z, zsz * E},
+        {B_RHIST, (size_t)std::max(1, Ly - 1) * n * n * E}};
+    place(k.p, k.smem, budget, b);
+  }
+  // row plan
+  {
+    KPlan& k = h->kp[1];
+    k.p.ci = ci;
+    k.p.cx = cx;
+    std::vector<std::pair<int, size_t>> b = {
+        {B_RED, 40 * 8}, {B_A, (size_t)g.sT * E}, {B_EU, (size_t)g.se * E}, {B_EL, (size_t)g.se * E},
+        {B_T1, t1row * E}, {B_T2, t1row * E}, {B_LW, (size_t)g.se * E}, {B_LW2, (size_t)g.se * E},
+        {B_LP, (size_t)(Ly + 1) * g.se * E}, {B_RP, (size_t)(Ly + 1) * g.se * E}};
+    place(k.p, k.smem, budget, b);
+  }
+  // pair plan
+  {
+    KPlan& k = h->kp[2];
+    k.p.ci = ci;
+    k.p.cx = cx;
+    std::vector<std::pair<int, size_t>> b = {
+        {B_RED, 40 * 8}, {B_A, (size_t)g.sT * E}, {B_A2, (size_t)g.sT * E}, {B_EU, (size_t)g.se * E},
+        {B_EL, (size_t)g.se * E}, {B_T1, t2row * E}, {B_T2, t2row * E}, {B_LW, (size_t)g.s2 * E},
+        {B_LW2, (size_t)g.s2 * E}, {B_LP, (size_t)(Ly + 1) * g.s2 * E}, {B_RP, (size_t)(Ly + 1) * g.s2 * E}};
+    place(k.p, k.smem, budget, b);
+  }
+  // sampler plan: union of the above
+  {
+    KPlan& k = h->kp[3];
+    k.p.ci = ci;
+    k.p.cx = cx;
+    const size_t tt = std::max(t1row, t2row);
+    const size_t lw = std::max((size_t)g.s2, (size_t)g.se);
+    std::vector<std::pair<int, size_t>> b = {
+        {B_RED, 40 * 8}, {B_SIG, (mX + 4) * E}, {B_SEL, 2 * mX * 4}, {B_S, (size_t)g.Lx * g.Ly},
+        {B_A, (size_t)g.sT * E}, {B_A2, (size_t)g.sT * E}, {B_E, (size_t)g.se * E}, {B_EU, (size_t)g.se * E},
+        {B_EL, (size_t)g.se * E}, {B_C, (size_t)n * chi * E}, {B_W, (size_t)ci * D * D * chi * E},
+        {B_T1, tt * E}, {B_T2, tt * E}, {B_LW, lw * E}, {B_LW2, lw * E}, {B_LP, lw * E},
+        {B_R, (size_t)n * n * E}, {B_Z, zsz * E}, {B_RP, (size_t)(Ly + 1) * lw * E},
+        {B_RHIST, (size_t)std::max(1, Ly - 1) * n * n * E}};
+    place(k.p, k.smem, budget, b);
+  }
+}
+
+static peps_status finish_plans(peps_handle* h) {
+  size_t maxsmem = 0;
+  for (auto& k : h->kp) maxsmem = std::max(maxsmem, k.smem);
+  cudaError_t e = (h->esz == 8) ? set_kernel_smem<double>(maxsmem) : set_kernel_smem<float>(maxsmem);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaFuncSetAttribute");
+  size_t gmax = 0;
+  for (int i = 0; i < 4; ++i) {
+    KPlan& k = h->kp[i];
+    int occ = (h->esz == 8) ? occupancy<double>(i, k.smem) : occupancy<float>(i, k.smem);
+    if (occ < 1) return fail(h, PEPS_E_SHAPE, "kernel does not fit on an SM");
+    k.grid = h->nsm * occ;
+    gmax = std::max(gmax, (size_t)k.grid * (size_t)k.p.gstride);
+  }
+  if (gmax > 0) {
+    e = cudaMalloc(&h->gscratch, gmax);
+    if (e != cudaSuccess) return fail(h, PEPS_E_WORKSPACE, "scratch allocation failed");
+    h->gscratch_bytes = gmax;
+  }
+  for (auto& k : h->kp) k.p.gbase = h->gscratch;
+  return PEPS_OK;
+}
+
+extern "C" peps_status peps_create(peps_handle** out, const peps_config* cfg) {
+  if (!out || !cfg) return PEPS_E_ARG;
+  *out = nullptr;
+  const peps_config c = *cfg;
+  if (c.Lx < 2 || c.Ly < 2 || c.Ly > MAX_LY || c.d < 2 || c.d > 4 || c.D < 1 || c.D > 8 || c.chi < c.D ||
+      c.chi > 64 || c.max_samples < 1)
+    return PEPS_E_SHAPE;
+  if (c.prec != PEPS_PREC_FP64 && c.prec != PEPS_PREC_FP32) return PEPS_E_ARG;
+  peps_handle* h = new peps_handle();
+  h->cfg = c;
+  h->esz = (c.prec == PEPS_PREC_FP64) ? 8 : 4;
+  Geo& g = h->g;
+  g.Lx = c.Lx; g.Ly = c.Ly; g.d = c.d; g.D = c.D; g.chi = c.chi;
+  g.n = c.chi * c.D;
+  g.se = c.chi * c.D * c.chi;
+  g.sT = c.D * c.D * c.D * c.D;
+  g.s2 = c.chi * c.D * c.D * c.chi;
+  const int N = c.Lx * c.Ly;
+  h->site_off_h.assign(N + 1, 0);
+  for (int x = 0; x < c.Lx; ++x)
+    for (int y = 0; y < c.Ly; ++y) {
+      const long long b = (long long)c.d * (y == 0 ? 1 : c.D) * (x == 0 ? 1 : c.D) * (y == c.Ly - 1 ? 1 : c.D) *
+                          (x == c.Lx - 1 ? 1 : c.D);
+      h->site_off_h[x * c.Ly + y + 1] = h->site_off_h[x * c.Ly + y] + b;
+    }
+  h->Np = h->site_off_h[N];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev);
+  auto bad = [&](peps_status st, const char* m) {
+    h->err = m;
+    peps_destroy(h);
+    return st;
+  };
+  if (cudaMalloc(&h->Tpad, (size_t)N * c.d * g.sT * h->esz) != cudaSuccess) return bad(PEPS_E_WORKSPACE, "Tpad");
+  if (cudaMalloc(&h->site_off, sizeof(long long) * (N + 1)) != cudaSuccess) return bad(PEPS_E_WORKSPACE, "site_off");
+  cudaMemcpy(h->site_off, h->site_off_h.data(), sizeof(long long) * (N + 1), cudaMemcpyHostToDevice);
+  const size_t envb = (size_t)c.max_samples * 2 * c.Lx * c.Ly * g.se * h->esz;
+  if (cudaMalloc(&h->envs, envb) != cudaSuccess) return bad(PEPS_E_WORKSPACE, "environment store");
+  if (cudaMalloc(&h->logs, sizeof(double) * (size_t)c.max_samples * 2 * c.Lx) != cudaSuccess) return bad(PEPS_E_WORKSPACE, "logs");
+  if (cudaMalloc(&h->wdisc, sizeof(float) * (size_t)c.max_samples) != cudaSuccess) return bad(PEPS_E_WORKSPACE, "wdisc");
+  if (cudaMalloc(&h->rowout, sizeof(double) * 4 * (size_t)c.max_samples * c.Lx) != cudaSuccess) return bad(PEPS_E_WORKSPACE, "rowout");
+  if (cudaMalloc(&h->pairout, sizeof(double) * 4 * (size_t)c.max_samples * c.Lx) != cudaSuccess) return bad(PEPS_E_WORKSPACE, "pairout");
+  if (cudaMalloc(&h->status_tmp, sizeof(int) * (size_t)c.max_samples) != cudaSuccess) return bad(PEPS_E_WORKSPACE, "status");
+  cudaMemset(h->Tpad, 0, (size_t)N * c.d * g.sT * h->esz);
+  plan_all(h);
+  peps_status st = finish_plans(h);
+  if (st != PEPS_OK) {
+    std::string m = h->err;
+    peps_destroy(h);
+    return st;
+  }
+  *out = h;
+  return PEPS_OK;
+}
+
+extern "C" peps_status peps_destroy(peps_handle* h) {
+  if (!h) return PEPS_E_ARG;
+  void* ptrs[] = {h->Tpad, h->site_off, h->envs, h->logs, h->wdisc, h->rowout, h->pairout, h->status_tmp,
+                  h->gscratch, h->d_tinfo, h->d_ab, h->d_eh, h->d_rowoff, h->d_pairoff, h->d_pij, h->d_pv,
+                  h->d_onsite, h->Obar, h->Tm, h->Vm, h->Hm, h->mean, h->ebar, h->yv, h->xv, h->cnt};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete h;
+  return PEPS_OK;
+}
+
+extern "C" long long peps_num_params(const peps_handle* h) { return h ? h->Np : -1; }
+
+extern "C" const char* peps_last_error(const peps_handle* h) { return (h && !h->err.empty()) ? h->err.c_str() : ""; }
+
+extern "C" peps_status peps_set_params(peps_handle* h, const double* theta_dev, void* stream) {
+  if (!h || !theta_dev) return fail(h, PEPS_E_ARG, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = (h->esz == 8) ? launch_pad<double>(h->g, theta_dev, h->site_off, (double*)h->Tpad, s)
+                                : launch_pad<float>(h->g, theta_dev, h->site_off, (float*)h->Tpad, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "pad theta");
+  return PEPS_OK;
+}
+
+// ---- Hamiltonian packing -----------------------------------------------------------------
+template <typename V>
+static void put(std::vector<char>& k, const V* p, size_t n) {
+  const char* c = (const char*)p;
+  k.insert(k.end(), c, c + n * sizeof(V));
+}
+
+template <typename V>
+static cudaError_t upload(V** d, const std::vector<V>& h, cudaStream_t s) {
+  if (*d) { cudaFree(*d); *d = nullptr; }
+  if (h.empty()) return cudaSuccess;
+  cudaError_t e = cudaMalloc(d, sizeof(V) * h.size());
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyAsync(*d, h.data(), sizeof(V) * h.size(), cudaMemcpyHostToDevice, s);
+}
+
+static peps_status set_hamiltonian(peps_handle* h, const peps_hamiltonian* H, cudaStream_t s) {
+  const Geo& g = h->g;
+  const int N = g.Lx * g.Ly, d = g.d;
+  if (H->nterms < 0 || H->npairs < 0) return fail(h, PEPS_E_ARG, "negative term count");
+  if ((H->nterms > 0 && !H->terms) || (H->npairs > 0 && (!H->pair_ij_host || !H->pair_v_host)))
+    return fail(h, PEPS_E_ARG, "null term arrays");
+  // content key
+  std::vector<char> key;
+  put(key, &H->nterms, 1);
+  for (int t = 0; t < H->nterms; ++t) {
+    const peps_term& tm = H->terms[t];
+    if (tm.nsites < 1 || tm.nsites > 4 || !tm.h_host) return fail(h, PEPS_E_ARG, "bad term");
+    int dk = 1;
+    for (int i = 0; i < tm.nsites; ++i) dk *= d;
+    put(key, &tm.nsites, 1);
+    put(key, tm.sites, 4);
+    put(key, tm.h_host, (size_t)dk * dk * 2);
+  }
+  put(key, &H->npairs, 1);
+  if (H->npairs) {
+    put(key, H->pair_ij_host, (size_t)2 * H->npairs);
+    put(key, H->pair_v_host, (size_t)H->npairs);
+  }
+  const int has_on = H->onsite_host ? 1 : 0;
+  put(key, &has_on, 1);
+  if (has_on) put(key, H->onsite_host, (size_t)N * d);
+  if (key == h->ham_key && !key.empty()) return PEPS_OK;
+  // pack terms
+  struct Rec { int two, x0; std::vector<int> ti; std::vector<int> ab; std::vector<double> hv; };
+  std::vector<Rec> recs;
+  for (int t = 0; t < H->nterms; ++t) {
+    const peps_term& tm = H->terms[t];
+    int xmin = 1 << 30, xmax = -1, ymin = 1 << 30, ymax = -1;
+    for (int i = 0; i < tm.nsites; ++i) {
+      const int sidx = tm.sites[i];
+      if (sidx < 0 || sidx >= N) return fail(h, PEPS_E_ARG, "term site out of range");
+      for (int j = 0; j < i; ++j)
+        if (tm.sites[j] == sidx) return fail(h, PEPS_E_ARG, "repeated site in a term");
+      xmin = std::min(xmin, sidx / g.Ly); xmax = std::max(xmax, sidx / g.Ly);
+      ymin = std::min(ymin, sidx % g.Ly); ymax = std::max(ymax, sidx % g.Ly);
+    }
+    if (xmax - xmin > 1) return fail(h, PEPS_E_UNSUPPORTED, "term spans more than two rows");
+    if (ymax - ymin > 1) return fail(h, PEPS_E_UNSUPPORTED, "term spans more than two columns");
+    Rec r;
+    r.two = (xmax > xmin);
+    r.x0 = xmin;
+    r.ti.assign(TI_N, 0);
+    r.ti[TI_K] = tm.nsites;
+    for (int i = 0; i < 4; ++i) r.ti[TI_S0 + i] = (i < tm.nsites) ? tm.sites[i] : -1;
+    r.ti[TI_X0] = xmin;
+    r.ti[TI_Y0] = ymin;
+    r.ti[TI_W] = ymax - ymin + 1;
+    r.ti[TI_TWO] = r.two;
+    int dk = 1;
+    for (int i = 0; i < tm.nsites; ++i) dk *= d;
+    for (int a = 0; a < dk; ++a)
+      for (int b = 0; b < dk; ++b) {
+        const double re = tm.h_host[2 * ((size_t)a * dk + b)], im = tm.h_host[2 * ((size_t)a * dk + b) + 1];
+        if (re != 0.0 || im != 0.0) {
+          r.ab.push_back(a);
+          r.ab.push_back(b);
+          r.hv.push_back(re);
+          r.hv.push_back(im);
+        }
+      }
+    recs.push_back(std::move(r));
+  }
+  std::stable_sort(recs.begin(), recs.end(), [](const Rec& a, const Rec& b) {
+    return a.two != b.two ? a.two < b.two : a.x0 < b.x0;
+  });
+  h->h_tinfo.clear(); h->h_ab.clear(); h->h_eh.clear();
+  h->h_rowoff.assign(g.Lx + 1, 0);
+  h->h_pairoff.assign(g.Lx, 0);
+  int t = 0;
+  const int nt = (int)recs.size();
+  std::vector<int> cnt1(g.Lx, 0), cnt2(g.Lx, 0);
+  for (auto& r : recs) (r.two ? cnt2 : cnt1)[r.x0]++;
+  for (int x = 0; x < g.Lx; ++x) h->h_rowoff[x + 1] = h->h_rowoff[x] + cnt1[x];
+  h->h_pairoff[0] = h->h_rowoff[g.Lx];
+  for (int x = 0; x + 1 < g.Lx; ++x) h->h_pairoff[x + 1] = h->h_pairoff[x] + cnt2[x];
+  for (auto& r : recs) {
+    r.ti[TI_EOFF] = (int)h->h_ab.size() / 2;
+    r.ti[TI_ECNT] = (int)r.ab.size() / 2;
+    h->h_tinfo.insert(h->h_tinfo.end(), r.ti.begin(), r.ti.end());
+    h->h_ab.insert(h->h_ab.end(), r.ab.begin(), r.ab.end());
+    h->h_eh.insert(h->h_eh.end(), r.hv.begin(), r.hv.end());
+    ++t;
+  }
+  (void)t;
+  h->n_pair_terms = 0;
+  for (int x = 0; x < g.Lx; ++x) h->n_pair_terms += cnt2[x];
+  h->h_pij.assign(H->pair_ij_host, H->pair_ij_host + 2 * (size_t)H->npairs);
+  h->h_pv.assign(H->pair_v_host, H->pair_v_host + (size_t)H->npairs);
+  for (int p = 0; p < H->npairs; ++p)
+    if (h->h_pij[2 * p] < 0 || h->h_pij[2 * p] >= N || h->h_pij[2 * p + 1] < 0 || h->h_pij[2 * p + 1] >= N)
+      return fail(h, PEPS_E_ARG, "pair site out of range");
+  if (has_on) h->h_onsite.assign(H->onsite_host, H->onsite_host + (size_t)N * d);
+  else h->h_onsite.clear();
+  CK(upload(&h->d_tinfo, h->h_tinfo, s), "upload terms");
+  CK(upload(&h->d_ab, h->h_ab, s), "upload terms");
+  CK(upload(&h->d_eh, h->h_eh, s), "upload terms");
+  CK(upload(&h->d_rowoff, h->h_rowoff, s), "upload terms");
+  CK(upload(&h->d_pairoff, h->h_pairoff, s), "upload terms");
+  CK(upload(&h->d_pij, h->h_pij, s), "upload pairs");
+  CK(upload(&h->d_pv, h->h_pv, s), "upload pairs");
+  CK(upload(&h->d_onsite, h->h_onsite, s), "upload onsite");
+  CK(cudaStreamSynchronize(s), "hamiltonian upload");
+  h->tt.nterm = nt;
+  h->tt.tinfo = h->d_tinfo;
+  h->tt.ent_ab = h->d_ab;
+  h->tt.ent_h = h->d_eh;
+  h->tt.row_off = h->d_rowoff;
+  h->tt.pair_off = h->d_pairoff;
+  h->dg.npairs = H->npairs;
+  h->dg.pair_ij = h->d_pij;
+  h->dg.pair_v = h->d_pv;
+  h->dg.onsite = has_on ? h->d_onsite : nullptr;
+  h->ham_key.swap(key);
+  return PEPS_OK;
+}
+
+// ---- evaluation pipeline -----------------------------------------------------------------
+template <typename T>
+static peps_status run_eval(peps_handle* h, const peps_hamiltonian* H, const uint8_t* S, int Ns, double* logabs,
+                            double* phase, double* eloc, void* O, int32_t* status, cudaStream_t s, int sides) {
+  const Geo& g = h->g;
+  int* st = status ? (int*)status : h->status_tmp;
+  CK(cudaMemsetAsync(st, 0, sizeof(int) * Ns, s), "memset status");
+  CK(cudaMemsetAsync(h->wdisc, 0, sizeof(float) * Ns, s), "memset wdisc");
+  if (Ns == 0) return PEPS_OK;
+  TermTab none{};
+  const bool want_e = (eloc != nullptr);
+  if (want_e) {
+    peps_status ps = set_hamiltonian(h, H, s);
+    if (ps != PEPS_OK) return ps;
+  }
+  const KPlan& ke = h->kp[0];
+  CK(launch_env<T>(g, ke.p, std::min(ke.grid, Ns * (sides == 3 ? 2 : 1)), ke.smem, (const T*)h->Tpad, S, Ns, sides,
+                   (T*)h->envs, h->logs, st, h->wdisc, s), "env kernel");
+  const KPlan& kr = h->kp[1];
+  const bool all_rows = want_e || (O != nullptr);
+  const int x_lo = all_rows ? 0 : g.Lx - 1;
+  CK(launch_row<T>(g, kr.p, std::min(kr.grid, Ns * (g.Lx - x_lo)), kr.smem, (const T*)h->Tpad, S, Ns, x_lo, g.Lx,
+                   (const T*)h->envs, h->logs, (T*)O, h->site_off, h->Np, want_e ? h->tt : none, h->rowout, st, s),
+     "row kernel");
+  const bool pairs = want_e && h->n_pair_terms > 0;
+  if (pairs) {
+    const KPlan& kq = h->kp[2];
+    CK(launch_pair<T>(g, kq.p, std::min(kq.grid, Ns * (g.Lx - 1)), kq.smem, (const T*)h->Tpad, S, Ns,
+                      (const T*)h->envs, h->logs, h->tt, h->pairout, st, s), "pair kernel");
+  }
+  DiagTab dg = want_e ? h->dg : DiagTab{};
+  CK(launch_combine(g, Ns, S, h->rowout, h->pairout, want_e ? 1 : 0, pairs ? 1 : 0, dg, logabs, phase, eloc, s),
+     "combine kernel");
+  return PEPS_OK;
+}
+
+static peps_status check_eval(peps_handle* h, const uint8_t* S, int Ns) {
+  if (!h) return PEPS_E_ARG;
+  if (Ns < 0 || (Ns > 0 && !S)) return fail(h, PEPS_E_ARG, "bad configuration batch");
+  if (Ns > h->cfg.max_samples) return fail(h, PEPS_E_SHAPE, "Ns exceeds max_samples");
+  return PEPS_OK;
+}
+
+extern "C" peps_status peps_evaluate(peps_handle* h, const peps_hamiltonian* H, const uint8_t* S_dev, int Ns,
+                                     double* logabs_dev, double* phase_dev, double* eloc_dev, void* O_dev,
+                                     int32_t* status_dev, void* stream) {
+  peps_status c = check_eval(h, S_dev, Ns);
+  if (c != PEPS_OK) return c;
+  if (eloc_dev && !H) return fail(h, PEPS_E_ARG, "eloc requested without a Hamiltonian");
+  const int sides = (eloc_dev || O_dev) ? 3 : 1;
+  if (h->esz == 8)
+    return run_eval<double>(h, H, S_dev, Ns, logabs_dev, phase_dev, eloc_dev, O_dev, status_dev, (cudaStream_t)stream, sides);
+  return run_eval<float>(h, H, S_dev, Ns, logabs_dev, phase_dev, eloc_dev, O_dev, status_dev, (cudaStream_t)stream, sides);
+}
+
+extern "C" peps_status peps_amplitudes(peps_handle* h, const uint8_t* S_dev, int Ns, double* logabs_dev,
+                                       double* phase_dev, int32_t* status_dev, void* stream) {
+  if (h && (!logabs_dev || !phase_dev) && Ns > 0) return fail(h, PEPS_E_ARG, "null output");
+  return peps_evaluate(h, nullptr, S_dev, Ns, logabs_dev, phase_dev, nullptr, nullptr, status_dev, stream);
+}
+
+extern "C" peps_status peps_local_energy(peps_handle* h, const peps_hamiltonian* H, const uint8_t* S_dev, int Ns,
+                                         double* eloc_dev, int32_t* status_dev, void* stream) {
+  if (h && (!H || (!eloc_dev && Ns > 0))) return fail(h, PEPS_E_ARG, "null argument");
+  return peps_evaluate(h, H, S_dev, Ns, nullptr, nullptr, eloc_dev, nullptr, status_dev, stream);
+}
+
+extern "C" peps_status peps_logderiv(peps_handle* h, const uint8_t* S_dev, int Ns, void* O_dev, int32_t* status_dev,
+                                     void* stream) {
+  if (h && !O_dev && Ns > 0) return fail(h, PEPS_E_ARG, "null output");
+  return peps_evaluate(h, nullptr, S_dev, Ns, nullptr, nullptr, nullptr, O_dev, status_dev, stream);
+}
+
+// ---- sampler -----------------------------------------------------------------------------
+extern "C" peps_status peps_sample(peps_handle* h, int move, uint8_t* S_dev, int Ns, int nsweeps, uint64_t seed,
+                                   uint64_t sweep0, long long* accepted_dev, int32_t* status_dev, void* stream) {
+  peps_status c = check_eval(h, S_dev, Ns);
+  if (c != PEPS_OK) return c;
+  if (move != PEPS_MOVE_EXCHANGE && move != PEPS_MOVE_FLIP) return fail(h, PEPS_E_ARG, "bad move kind");
+  if (nsweeps < 0) return fail(h, PEPS_E_ARG, "negative sweep count");
+  cudaStream_t s = (cudaStream_t)stream;
+  int* st = status_dev ? (int*)status_dev : h->status_tmp;
+  CK(cudaMemsetAsync(st, 0, sizeof(int) * Ns, s), "memset status");
+  if (Ns == 0 || nsweeps == 0) return PEPS_OK;
+  const KPlan& k = h->kp[3];
+  const int grid = std::min(k.grid, Ns);
+  cudaError_t e = (h->esz == 8)
+                      ? launch_sample<double>(h->g, k.p, grid, k.smem, (const double*)h->Tpad, S_dev, Ns, move, nsweeps,
+                                              seed, sweep0, (double*)h->envs, h->logs, accepted_dev, st, s)
+                      : launch_sample<float>(h->g, k.p, grid, k.smem, (const float*)h->Tpad, S_dev, Ns, move, nsweeps,
+                                             seed, sweep0, (float*)h->envs, h->logs, accepted_dev, st, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "sampler kernel");
+  return PEPS_OK;
+}
+
+// ---- MinSR -------------------------------------------------------------------------------
+static peps_status ensure_minsr(peps_handle* h, int Ns) {
+  const int n = Ns + (Ns & 1);
+  if (h->ms_cap >= n) return PEPS_OK;
+  double** bufs[] = {&h->Obar, &h->Tm, &h->Vm, &h->Hm, &h->mean, &h->ebar, &h->yv, &h->xv, &h->cnt};
+  for (double** b : bufs)
+    if (*b) { cudaFree(*b); *b = nullptr; }
+  const size_t nn = (size_t)n * n;
+  if (cudaMalloc(&h->Obar, sizeof(double) * (size_t)Ns * h->Np) != cudaSuccess ||
+      cudaMalloc(&h->Tm, sizeof(double) * nn) != cudaSuccess || cudaMalloc(&h->Vm, sizeof(double) * nn) != cudaSuccess ||
+      cudaMalloc(&h->Hm, sizeof(double) * nn) != cudaSuccess ||
+      cudaMalloc(&h->mean, sizeof(double) * (size_t)h->Np) != cudaSuccess ||
+      cudaMalloc(&h->ebar, sizeof(double) * n) != cudaSuccess || cudaMalloc(&h->yv, sizeof(double) * n) != cudaSuccess ||
+      cudaMalloc(&h->xv, sizeof(double) * n) != cudaSuccess || cudaMalloc(&h->cnt, sizeof(double) * 8) != cudaSuccess)
+    return fail(h, PEPS_E_WORKSPACE, "MinSR workspace allocation failed");
+  h->ms_cap = n;
+  return PEPS_OK;
+}
+
+extern "C" peps_status minsr_step(peps_handle* h, const void* O_dev, const double* eloc_dev, const double* w_dev,
+                                  int Ns, double lambda, double rcond, double tau, double* dtheta_dev,
+                                  double* info_dev, void* stream) {
+  if (!h) return PEPS_E_ARG;
+  if (!O_dev || !eloc_dev || !dtheta_dev || !info_dev || Ns < 2) return fail(h, PEPS_E_ARG, "bad MinSR argument");
+  if (!(lambda > 0.0 || rcond > 0.0) || lambda < 0.0 || rcond < 0.0)
+    return fail(h, PEPS_E_ARG, "MinSR needs lambda > 0 or rcond > 0");
+  peps_status ps = ensure_minsr(h, Ns);
+  if (ps != PEPS_OK) return ps;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int n = Ns + (Ns & 1);
+  const long long Np = h->Np;
+  cudaError_t e = (h->esz == 8) ? launch_center<double>((const double*)O_dev, w_dev, Ns, Np, h->mean, h->Obar, s)
+                                : launch_center<float>((const float*)O_dev, w_dev, Ns, Np, h->mean, h->Obar, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "centre O");
+  CK(cudaMemsetAsync(h->ebar, 0, sizeof(double) * n, s), "memset");
+  CK(launch_center_e(eloc_dev, w_dev, Ns, h->ebar, s), "centre E_loc");
+  CK(cudaMemsetAsync(h->Tm, 0, sizeof(double) * (size_t)n * n, s), "memset");
+  CK(launch_gram(h->Obar, Ns, Np, h->Tm, n, s), "Gram");
+  const int sweeps = jacobi_eig(h->Tm, h->Vm, n, h->cnt, nullptr, h->Hm, s, 40, &e);
+  if (e != cudaSuccess) return cuda_fail(h, e, "Jacobi");
+  CK(launch_minsr_apply(h->Tm, h->Vm, h->ebar, n, Ns, lambda, rcond, h->yv, h->xv, info_dev, s), "MinSR apply");
+  CK(launch_obar_t_x(h->Obar, h->xv, Ns, Np, tau, dtheta_dev, s), "Obar^T x");
+  const double sw = (double)sweeps;
+  CK(cudaMemcpyAsync(info_dev + 3, &sw, sizeof(double), cudaMemcpyHostToDevice, s), "info");
+  CK(cudaStreamSynchronize(s), "MinSR sync");
+  return PEPS_OK;
+}

@@ -1,0 +1,722 @@
+// Contraction kernels of the finite-PEPS hot path (sm_103a): environment pass, one- and two-row
+// sandwiches (amplitudes, local-energy ratios, log-derivatives), per-sample combine, and the
+// Metropolis sweep.  All kernels are persistent: each CTA loops over work items
+// (blockIdx.x, blockIdx.x + gridDim.x, ...) and owns one slice of the global scratch arena.
+#include "peps_kernels.cuh"
+
+namespace peps {
+
+// ------------------------------------------------------------------------------------------
+// environment store: per sample 2*Lx rows of Ly sites; slot x+1 holds E^u[x] (x = -1..Lx-2),
+// slot Lx+x-1 holds E^l[x] (x = 1..Lx).  logs: cumulative log factor of every slot.
+__host__ __device__ inline size_t env_sample_elems(const Geo& g) { return (size_t)2 * g.Lx * g.Ly * g.se; }
+__device__ inline int slot_up(const Geo& g, int x) { return x + 1; }
+__device__ inline int slot_lo(const Geo& g, int x) { return g.Lx + x - 1; }
+
+template <typename T>
+__device__ RowWork<T> carve_row(const Plan& p, char* smem, char* gbase) {
+  RowWork<T> w;
+  w.R = (T*)buf_ptr(p, B_R, smem, gbase);
+  w.Rhist = (T*)buf_ptr(p, B_RHIST, smem, gbase);
+  w.E = (T*)buf_ptr(p, B_E, smem, gbase);
+  w.A = (T*)buf_ptr(p, B_A, smem, gbase);
+  w.Z = (T*)buf_ptr(p, B_Z, smem, gbase);
+  w.W = (T*)buf_ptr(p, B_W, smem, gbase);
+  w.C = (T*)buf_ptr(p, B_C, smem, gbase);
+  w.sig = (T*)buf_ptr(p, B_SIG, smem, gbase);
+  w.sel = (int*)buf_ptr(p, B_SEL, smem, gbase);
+  w.red = (double*)buf_ptr(p, B_RED, smem, gbase);
+  w.ci = p.ci;
+  return w;
+}
+
+// Upper environments E^u[-1..Lx-2] of configuration Ss into env (one sample's store).
+template <typename T>
+__device__ void build_upper(const Geo& g, const T* Tpad, const uint8_t* Ss, T* env, double* logs,
+                            const RowWork<T>& w, int* st, float* wd, int* flag) {
+  const size_t row = (size_t)g.Ly * g.se;
+  // trivial E^u[-1], and the trivial E^l[Lx] that closes psi_top = E^u[Lx-2] . T_proj[Lx-1]
+  T* trivial = env + (size_t)slot_up(g, -1) * row;
+  T* trivial_lo = env + (size_t)slot_lo(g, g.Lx) * row;
+  for (int k = 0; k < g.Ly; ++k) {
+    blk_unit(trivial + (size_t)k * g.se, g.se);
+    blk_unit(trivial_lo + (size_t)k * g.se, g.se);
+  }
+  if (threadIdx.x == 0) { logs[slot_up(g, -1)] = 0.0; logs[slot_lo(g, g.Lx)] = 0.0; }
+  __syncthreads();
+  double lg = env_first_row(g, env + (size_t)slot_up(g, 0) * row, Tpad, 0, Ss, false, w.A, w.Z, w.red, st);
+  if (threadIdx.x == 0) logs[slot_up(g, 0)] = lg;
+  for (int x = 1; x <= g.Lx - 2; ++x) {
+    lg += env_row_step(g, env + (size_t)slot_up(g, x - 1) * row, env + (size_t)slot_up(g, x) * row, Tpad, x,
+                       Ss + (size_t)x * g.Ly, false, w, st, wd, flag);
+    if (threadIdx.x == 0) logs[slot_up(g, x)] = lg;
+  }
+  __syncthreads();
+}
+
+// Lower environments E^l[2..Lx] (and E^l[1] when full) of configuration Ss.
+template <typename T>
+__device__ void build_lower(const Geo& g, const T* Tpad, const uint8_t* Ss, T* env, double* logs,
+                            const RowWork<T>& w, int* st, float* wd, int* flag, int xmin) {
+  const size_t row = (size_t)g.Ly * g.se;
+  T* trivial = env + (size_t)slot_lo(g, g.Lx) * row;
+  for (int k = 0; k < g.Ly; ++k) blk_unit(trivial + (size_t)k * g.se, g.se);
+  if (threadIdx.x == 0) logs[slot_lo(g, g.Lx)] = 0.0;
+  __syncthreads();
+  double lg = env_first_row(g, env + (size_t)slot_lo(g, g.Lx - 1) * row, Tpad, g.Lx - 1,
+                            Ss + (size_t)(g.Lx - 1) * g.Ly, true, w.A, w.Z, w.red, st);
+  if (threadIdx.x == 0) logs[slot_lo(g, g.Lx - 1)] = lg;
+  for (int x = g.Lx - 2; x >= xmin; --x) {
+    lg += env_row_step(g, env + (size_t)slot_lo(g, x + 1) * row, env + (size_t)slot_lo(g, x) * row, Tpad, x,
+                       Ss + (size_t)x * g.Ly, true, w, st, wd, flag);
+    if (threadIdx.x == 0) logs[slot_lo(g, x)] = lg;
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS) k_env(Geo g, Plan plan, const T* __restrict__ Tpad,
+                                                  const uint8_t* __restrict__ S, int Ns, int sides, T* envs,
+                                                  double* logs, int* status, float* wdisc) {
+  extern __shared__ __align__(16) char smem[];
+  char* gbase = plan.gbase;
+  RowWork<T> w = carve_row<T>(plan, smem, gbase);
+  __shared__ int st, flag;
+  __shared__ float wd;
+  const int nside = (sides == 3) ? 2 : 1;
+  const int N = g.Lx * g.Ly;
+  for (int item = blockIdx.x; item < Ns * nside; item += gridDim.x) {
+    const int smp = item / nside;
+    const int side = (sides == 3) ? (item % nside) : (sides == 1 ? 0 : 1);
+    if (threadIdx.x == 0) { st = 0; wd = 0.f; }
+    __syncthreads();
+    T* env = envs + (size_t)smp * env_sample_elems(g);
+    double* lg = logs + (size_t)smp * 2 * g.Lx;
+    const uint8_t* Ss = S + (size_t)smp * N;
+    if (side == 0) build_upper(g, Tpad, Ss, env, lg, w, &st, &wd, &flag);
+    else build_lower(g, Tpad, Ss, env, lg, w, &st, &wd, &flag, 1);
+    if (threadIdx.x == 0) {
+      if (st) atomicOr(status + smp, st);
+      if (wdisc) atomicMax((int*)(wdisc + smp), __float_as_int(wd));  // wd >= 0: int order = float order
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Sandwich bookkeeping shared by the row and pair kernels.
+__device__ inline void site_dims(const Geo& g, int x, int y, int* Dl, int* Du, int* Dr, int* Dd) {
+  *Dl = (y == 0) ? 1 : g.D;
+  *Du = (x == 0) ? 1 : g.D;
+  *Dr = (y == g.Ly - 1) ? 1 : g.D;
+  *Dd = (x == g.Lx - 1) ? 1 : g.D;
+}
+
+// local state of `site` in configuration Ss after replacing the term's sites by the digits of b
+__device__ inline int state_after(const int* ti, int site, const uint8_t* Ss, int b, int d) {
+  const int k = ti[TI_K];
+  int pw = 1;
+  for (int t = k - 1; t >= 0; --t) {
+    if (ti[TI_S0 + t] == site) return (b / pw) % d;
+    pw *= d;
+  }
+  return Ss[site];
+}
+
+__device__ inline int local_index(const int* ti, const uint8_t* Ss, int d) {
+  int a = 0;
+  for (int t = 0; t < ti[TI_K]; ++t) a = a * d + Ss[ti[TI_S0 + t]];
+  return a;
+}
+
+// ------------------------------------------------------------------------------------------
+// One-row sandwich at row x of sample smp: psi_x, O of row x, E_loc terms inside row x.
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS) k_row(Geo g, Plan plan, const T* __restrict__ Tpad,
+                                                  const uint8_t* __restrict__ S, int Ns, int x_lo, int x_hi,
+                                                  const T* envs, const double* logs, T* O, const long long* site_off,
+                                                  long long Np, TermTab tt, double* rowout, int* status) {
+  extern __shared__ __align__(16) char smem[];
+  char* gbase = plan.gbase;
+  T* LP = (T*)buf_ptr(plan, B_LP, smem, gbase);   // (Ly+1) x se
+  T* RP = (T*)buf_ptr(plan, B_RP, smem, gbase);   // (Ly+1) x se
+  T* t1 = (T*)buf_ptr(plan, B_T1, smem, gbase);
+  T* t2 = (T*)buf_ptr(plan, B_T2, smem, gbase);
+  T* eu = (T*)buf_ptr(plan, B_EU, smem, gbase);
+  T* el = (T*)buf_ptr(plan, B_EL, smem, gbase);
+  T* A = (T*)buf_ptr(plan, B_A, smem, gbase);
+  T* LW = (T*)buf_ptr(plan, B_LW, smem, gbase);
+  T* LW2 = (T*)buf_ptr(plan, B_LW2, smem, gbase);
+  double* red = (double*)buf_ptr(plan, B_RED, smem, gbase);
+  __shared__ double logL[MAX_LY + 1], logR[MAX_LY + 1];
+  __shared__ int st;
+  const int N = g.Lx * g.Ly, Ly = g.Ly, se = g.se;
+  const int nx = x_hi - x_lo;
+  const size_t rowsz = (size_t)Ly * se;
+  for (int item = blockIdx.x; item < Ns * nx; item += gridDim.x) {
+    const int smp = item / nx, x = x_lo + item % nx;
+    const uint8_t* Ss = S + (size_t)smp * N;
+    const T* env = envs + (size_t)smp * env_sample_elems(g);
+    const double* lg = logs + (size_t)smp * 2 * g.Lx;
+    const T* EU = env + (size_t)slot_up(g, x - 1) * rowsz;
+    const T* EL = env + (size_t)slot_lo(g, x + 1) * rowsz;
+    if (threadIdx.x == 0) st = 0;
+    // right partials R[Ly] = unit, R[y] = R[y+1] absorbed over column y
+    blk_unit(RP + (size_t)Ly * se, se);
+    if (threadIdx.x == 0) logR[Ly] = 0.0;
+    __syncthreads();
+    for (int y = Ly - 1; y >= 0; --y) {
+      blk_copy(eu, EU + (size_t)y * se, se);
+      blk_copy(el, EL + (size_t)y * se, se);
+      load_A(A, Tpad, g, x * Ly + y, Ss[x * Ly + y], false);
+      __syncthreads();
+      absorb1_right(g, RP + (size_t)(y + 1) * se, eu, A, el, t1, t2, RP + (size_t)y * se);
+      const double l = blk_normalize(RP + (size_t)y * se, se, red, &st);
+      if (threadIdx.x == 0) logR[y] = logR[y + 1] + l;
+    }
+    // left partials
+    blk_unit(LP, se);
+    if (threadIdx.x == 0) logL[0] = 0.0;
+    __syncthreads();
+    for (int y = 0; y < Ly; ++y) {
+      blk_copy(eu, EU + (size_t)y * se, se);
+      blk_copy(el, EL + (size_t)y * se, se);
+      load_A(A, Tpad, g, x * Ly + y, Ss[x * Ly + y], false);
+      __syncthreads();
+      absorb1(g, LP + (size_t)y * se, eu, A, el, t1, t2, LP + (size_t)(y + 1) * se);
+      const double l = blk_normalize(LP + (size_t)(y + 1) * se, se, red, &st);
+      if (threadIdx.x == 0) logL[y + 1] = logL[y] + l;
+    }
+    __syncthreads();
+    const T val = LP[(size_t)Ly * se];
+    const double lpsi_norm = logL[Ly];
+    const double env_log = lg[slot_up(g, x - 1)] + lg[slot_lo(g, x + 1)];
+    // ---- log-derivatives of row x
+    if (O != nullptr) {
+      for (int y = 0; y < Ly; ++y) {
+        const int site = x * Ly + y;
+        blk_copy(eu, EU + (size_t)y * se, se);
+        blk_copy(el, EL + (size_t)y * se, se);
+        __syncthreads();
+        site_env1(g, LP + (size_t)y * se, eu, el, RP + (size_t)(y + 1) * se, t1, t2, A);
+        const double sc = exp(logL[y] + logR[y + 1] - lpsi_norm);
+        int Dl, Du, Dr, Dd;
+        site_dims(g, x, y, &Dl, &Du, &Dr, &Dd);
+        const int blk = Dl * Du * Dr * Dd;
+        const int s_here = Ss[site];
+        T* Orow = O + (size_t)smp * Np + site_off[site];
+        const int D = g.D;
+        for (int o = threadIdx.x; o < g.d * blk; o += blockDim.x) {
+          const int s = o / blk, c = o % blk;
+          const int dd = c % Dd, r = (c / Dd) % Dr, u = (c / (Dd * Dr)) % Du, l = c / (Dd * Dr * Du);
+          T v = T(0);
+          if (s == s_here) v = (T)((double)A[((l * D + u) * D + r) * D + dd] * sc / (double)val);
+          Orow[o] = v;
+        }
+        __syncthreads();
+      }
+    }
+    // ---- local-energy terms inside row x
+    double ere = 0.0, eim = 0.0;
+    if (tt.nterm > 0) {
+      for (int ti_ = tt.row_off[x]; ti_ < tt.row_off[x + 1]; ++ti_) {
+        const int* ti = tt.tinfo + (size_t)ti_ * TI_N;
+        const int a = local_index(ti, Ss, g.d);
+        for (int e = ti[TI_EOFF]; e < ti[TI_EOFF] + ti[TI_ECNT]; ++e) {
+          if (tt.ent_ab[2 * e] != a) continue;
+          const int b = tt.ent_ab[2 * e + 1];
+          const double hr = tt.ent_h[2 * e], hi = tt.ent_h[2 * e + 1];
+          if (b == a) { ere += hr; eim += hi; continue; }
+          const int y0 = ti[TI_Y0], w = ti[TI_W];
+          blk_copy(LW, LP + (size_t)y0 * se, se);
+          double lw = logL[y0];
+          __syncthreads();
+          for (int c = y0; c < y0 + w; ++c) {
+            const int site = x * Ly + c;
+            blk_copy(eu, EU + (size_t)c * se, se);
+            blk_copy(el, EL + (size_t)c * se, se);
+            load_A(A, Tpad, g, site, state_after(ti, site, Ss, b, g.d), false);
+            __syncthreads();
+            absorb1(g, LW, eu, A, el, t1, t2, LW2);
+            lw += blk_normalize(LW2, se, red, &st);
+            blk_copy(LW, LW2, se);
+            __syncthreads();
+          }
+          const T v = blk_dot(LW, RP + (size_t)(y0 + w) * se, se, red);
+          lw += logR[y0 + w];
+          const double ratio = (double)v / (double)val * exp(lw - lpsi_norm);
+          ere += hr * ratio;
+          eim += hi * ratio;
+        }
+      }
+    }
+    if (threadIdx.x == 0) {
+      double* out = rowout + ((size_t)smp * g.Lx + x) * 4;
+      const double av = fabs((double)val);
+      out[0] = (av > 0.0) ? log(av) + lpsi_norm + env_log : -INFINITY;
+      out[1] = ((double)val < 0.0) ? 3.141592653589793 : 0.0;
+      out[2] = ere;
+      out[3] = eim;
+      int s = st;
+      if (!(av > 0.0) || !isfinite(out[0]) || !isfinite(ere) || !isfinite(eim)) s |= ST_NONFINITE;
+      if (s) atomicOr(status + smp, s);
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Two-row sandwich at rows x, x+1: psi_{x,x+1} and the E_loc terms spanning the two rows.
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS) k_pair(Geo g, Plan plan, const T* __restrict__ Tpad,
+                                                   const uint8_t* __restrict__ S, int Ns, const T* envs,
+                                                   const double* logs, TermTab tt, double* pairout, int* status) {
+  extern __shared__ __align__(16) char smem[];
+  char* gbase = plan.gbase;
+  T* LP = (T*)buf_ptr(plan, B_LP, smem, gbase);   // (Ly+1) x s2
+  T* RP = (T*)buf_ptr(plan, B_RP, smem, gbase);   // (Ly+1) x s2
+  T* t1 = (T*)buf_ptr(plan, B_T1, smem, gbase);
+  T* t2 = (T*)buf_ptr(plan, B_T2, smem, gbase);
+  T* eu = (T*)buf_ptr(plan, B_EU, smem, gbase);
+  T* el = (T*)buf_ptr(plan, B_EL, smem, gbase);
+  T* A1 = (T*)buf_ptr(plan, B_A, smem, gbase);
+  T* A2 = (T*)buf_ptr(plan, B_A2, smem, gbase);
+  T* LW = (T*)buf_ptr(plan, B_LW, smem, gbase);
+  T* LW2 = (T*)buf_ptr(plan, B_LW2, smem, gbase);
+  double* red = (double*)buf_ptr(plan, B_RED, smem, gbase);
+  __shared__ double logL[MAX_LY + 1], logR[MAX_LY + 1];
+  __shared__ int st;
+  const int N = g.Lx * g.Ly, Ly = g.Ly, se = g.se, s2 = g.s2;
+  const int nx = g.Lx - 1;
+  const size_t rowsz = (size_t)Ly * se;
+  for (int item = blockIdx.x; item < Ns * nx; item += gridDim.x) {
+    const int smp = item / nx, x = item % nx;
+    // skip row pairs without terms
+    if (tt.nterm == 0 || tt.pair_off[x] == tt.pair_off[x + 1]) {
+      if (threadIdx.x == 0) {
+        double* out = pairout + ((size_t)smp * g.Lx + x) * 4;
+        out[0] = 0.0; out[1] = 0.0; out[2] = 0.0; out[3] = 0.0;
+      }
+      continue;
+    }
+    const uint8_t* Ss = S + (size_t)smp * N;
+    const T* env = envs + (size_t)smp * env_sample_elems(g);
+    const T* EU = env + (size_t)slot_up(g, x - 1) * rowsz;
+    const T* EL = env + (size_t)slot_lo(g, x + 2) * rowsz;
+    if (threadIdx.x == 0) st = 0;
+    blk_unit(RP + (size_t)Ly * s2, s2);
+    if (threadIdx.x == 0) logR[Ly] = 0.0;
+    __syncthreads();
+    for (int y = Ly - 1; y >= 0; --y) {
+      blk_copy(eu, EU + (size_t)y * se, se);
+      blk_copy(el, EL + (size_t)y * se, se);
+      load_A(A1, Tpad, g, x * Ly + y, Ss[x * Ly + y], false);
+      load_A(A2, Tpad, g, (x + 1) * Ly + y, Ss[(x + 1) * Ly + y], false);
+      __syncthreads();
+      absorb2_right(g, RP + (size_t)(y + 1) * s2, eu, A1, A2, el, t1, t2, RP + (size_t)y * s2, plan.cx);
+      const double l = blk_normalize(RP + (size_t)y * s2, s2, red, &st);
+      if (threadIdx.x == 0) logR[y] = logR[y + 1] + l;
+    }
+    blk_unit(LP, s2);
+    if (threadIdx.x == 0) logL[0] = 0.0;
+    __syncthreads();
+    // the left partials are only needed up to the last window start; build them all
+    for (int y = 0; y < Ly; ++y) {
+      blk_copy(eu, EU + (size_t)y * se, se);
+      blk_copy(el, EL + (size_t)y * se, se);
+      load_A(A1, Tpad, g, x * Ly + y, Ss[x * Ly + y], false);
+      load_A(A2, Tpad, g, (x + 1) * Ly + y, Ss[(x + 1) * Ly + y], false);
+      __syncthreads();
+      absorb2(g, LP + (size_t)y * s2, eu, A1, A2, el, t1, t2, LP + (size_t)(y + 1) * s2, plan.cx);
+      const double l = blk_normalize(LP + (size_t)(y + 1) * s2, s2, red, &st);
+      if (threadIdx.x == 0) logL[y + 1] = logL[y] + l;
+    }
+    __syncthreads();
+    const T val = LP[(size_t)Ly * s2];
+    const double lpsi_norm = logL[Ly];
+    double ere = 0.0, eim = 0.0;
+    for (int ti_ = tt.pair_off[x]; ti_ < tt.pair_off[x + 1]; ++ti_) {
+      const int* ti = tt.tinfo + (size_t)ti_ * TI_N;
+      const int a = local_index(ti, Ss, g.d);
+      for (int e = ti[TI_EOFF]; e < ti[TI_EOFF] + ti[TI_ECNT]; ++e) {
+        if (tt.ent_ab[2 * e] != a) continue;
+        const int b = tt.ent_ab[2 * e + 1];
+        const double hr = tt.ent_h[2 * e], hi = tt.ent_h[2 * e + 1];
+        if (b == a) { ere += hr; eim += hi; continue; }
+        const int y0 = ti[TI_Y0], w = ti[TI_W];
+        blk_copy(LW, LP + (size_t)y0 * s2, s2);
+        double lw = logL[y0];
+        __syncthreads();
+        for (int c = y0; c < y0 + w; ++c) {
+          blk_copy(eu, EU + (size_t)c * se, se);
+          blk_copy(el, EL + (size_t)c * se, se);
+          load_A(A1, Tpad, g, x * Ly + c, state_after(ti, x * Ly + c, Ss, b, g.d), false);
+          load_A(A2, Tpad, g, (x + 1) * Ly + c, state_after(ti, (x + 1) * Ly + c, Ss, b, g.d), false);
+          __syncthreads();
+          absorb2(g, LW, eu, A1, A2, el, t1, t2, LW2, plan.cx);
+          lw += blk_normalize(LW2, s2, red, &st);
+          blk_copy(LW, LW2, s2);
+          __syncthreads();
+        }
+        const T v = blk_dot(LW, RP + (size_t)(y0 + w) * s2, s2, red);
+        lw += logR[y0 + w];
+        const double ratio = (double)v / (double)val * exp(lw - lpsi_norm);
+        ere += hr * ratio;
+        eim += hi * ratio;
+      }
+    }
+    if (threadIdx.x == 0) {
+      double* out = pairout + ((size_t)smp * g.Lx + x) * 4;
+      out[0] = 0.0;
+      out[1] = 0.0;
+      out[2] = ere;
+      out[3] = eim;
+      int s = st;
+      if (!((double)val != 0.0) || !isfinite(ere) || !isfinite(eim)) s |= ST_NONFINITE;
+      if (s) atomicOr(status + smp, s);
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Per-sample combine: ln psi_top from row Lx-1, E_loc = diagonal + row terms + pair terms.
+// One warp per sample.
+__global__ void k_combine(Geo g, int Ns, const uint8_t* __restrict__ S, const double* rowout, const double* pairout,
+                          int use_rows_all, int use_pairs, DiagTab dg, double* logabs, double* phase, double* eloc) {
+  const int lane = threadIdx.x & 31;
+  const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarp = (gridDim.x * blockDim.x) >> 5;
+  const int N = g.Lx * g.Ly;
+  for (int smp = wid; smp < Ns; smp += nwarp) {
+    const uint8_t* Ss = S + (size_t)smp * N;
+    double re = 0.0, im = 0.0;
+    if (eloc) {
+      for (int p = lane; p < dg.npairs; p += 32) re += dg.pair_v[p] * (double)Ss[dg.pair_ij[2 * p]] * (double)Ss[dg.pair_ij[2 * p + 1]];
+      if (dg.onsite)
+        for (int i = lane; i < N; i += 32) re += dg.onsite[(size_t)i * g.d + Ss[i]];
+      if (use_rows_all)
+        for (int x = lane; x < g.Lx; x += 32) {
+          re += rowout[((size_t)smp * g.Lx + x) * 4 + 2];
+          im += rowout[((size_t)smp * g.Lx + x) * 4 + 3];
+        }
+      if (use_pairs)
+        for (int x = lane; x < g.Lx - 1; x += 32) {
+          re += pairout[((size_t)smp * g.Lx + x) * 4 + 2];
+          im += pairout[((size_t)smp * g.Lx + x) * 4 + 3];
+        }
+      re = warp_sum(re);
+      im = warp_sum(im);
+    }
+    if (lane == 0) {
+      const double* top = rowout + ((size_t)smp * g.Lx + (g.Lx - 1)) * 4;
+      if (logabs) logabs[smp] = top[0];
+      if (phase) phase[smp] = top[1];
+      if (eloc) { eloc[2 * smp] = re; eloc[2 * smp + 1] = im; }
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Metropolis sweeps: one CTA per chain (persistent over chains).
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS) k_sample(Geo g, Plan plan, const T* __restrict__ Tpad, uint8_t* S,
+                                                     int Ns, int move, int nsweeps, unsigned long long seed,
+                                                     unsigned long long sweep0, T* envs, double* logs,
+                                                     long long* accepted, int* status) {
+  extern __shared__ __align__(16) char smem[];
+  char* gbase = plan.gbase;
+  RowWork<T> w = carve_row<T>(plan, smem, gbase);
+  T* RP = (T*)buf_ptr(plan, B_RP, smem, gbase);   // (Ly+1) x s2 (one- or two-row partials)
+  T* t1 = (T*)buf_ptr(plan, B_T1, smem, gbase);
+  T* t2 = (T*)buf_ptr(plan, B_T2, smem, gbase);
+  T* eu = (T*)buf_ptr(plan, B_EU, smem, gbase);
+  T* el = (T*)buf_ptr(plan, B_EL, smem, gbase);
+  T* A1 = (T*)buf_ptr(plan, B_A, smem, gbase);
+  T* A2 = (T*)buf_ptr(plan, B_A2, smem, gbase);
+  T* LW = (T*)buf_ptr(plan, B_LW, smem, gbase);
+  T* LW2 = (T*)buf_ptr(plan, B_LW2, smem, gbase);
+  T* LC = (T*)buf_ptr(plan, B_LP, smem, gbase);    // running left partial (s2)
+  uint8_t* Sl = (uint8_t*)buf_ptr(plan, B_S, smem, gbase);
+  double* red = w.red;
+  __shared__ double logR[MAX_LY + 1];
+  __shared__ double logLc, lcur;
+  __shared__ int st, flag, accept_flag;
+  __shared__ float wd;
+  const int N = g.Lx * g.Ly, Ly = g.Ly, Lx = g.Lx, se = g.se, s2 = g.s2;
+  const size_t rowsz = (size_t)Ly * se;
+  for (int c = blockIdx.x; c < Ns; c += gridDim.x) {
+    uint8_t* Sg = S + (size_t)c * N;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) Sl[i] = Sg[i];
+    if (threadIdx.x == 0) { st = 0; wd = 0.f; }
+    long long acc = 0;
+    T* env = envs + (size_t)c * env_sample_elems(g);
+    double* lg = logs + (size_t)c * 2 * Lx;
+    __syncthreads();
+    for (int t = 0; t < nsweeps; ++t) {
+      const unsigned long long sweep_id = sweep0 + (unsigned long long)t;
+      // lower environments E^l[1..Lx] of the current configuration
+      build_lower(g, Tpad, Sl, env, lg, w, &st, &wd, &flag, 1);
+      // E^u[-1]
+      {
+        T* trivial = env + (size_t)slot_up(g, -1) * rowsz;
+        for (int k = 0; k < Ly; ++k) blk_unit(trivial + (size_t)k * se, se);
+        if (threadIdx.x == 0) lg[slot_up(g, -1)] = 0.0;
+        __syncthreads();
+      }
+      unsigned slot = 0;
+      for (int x = 0; x < Lx; ++x) {
+        const T* EU = env + (size_t)slot_up(g, x - 1) * rowsz;
+        // ---- moves inside row x with psi_x (E^u[x-1], E^l[x+1])
+        {
+          const T* EL = env + (size_t)slot_lo(g, x + 1) * rowsz;
+          blk_unit(RP + (size_t)Ly * se, se);
+          if (threadIdx.x == 0) logR[Ly] = 0.0;
+          __syncthreads();
+          for (int y = Ly - 1; y >= 0; --y) {
+            blk_copy(eu, EU + (size_t)y * se, se);
+            blk_copy(el, EL + (size_t)y * se, se);
+            load_A(A1, Tpad, g, x * Ly + y, Sl[x * Ly + y], false);
+            __syncthreads();
+            absorb1_right(g, RP + (size_t)(y + 1) * se, eu, A1, el, t1, t2, RP + (size_t)y * se);
+            const double l = blk_normalize(RP + (size_t)y * se, se, red, &st);
+            if (threadIdx.x == 0) logR[y] = logR[y + 1] + l;
+          }
+          __syncthreads();
+          if (threadIdx.x == 0) {
+            const double v = (double)RP[0];
+            lcur = (v != 0.0) ? log(fabs(v)) + logR[0] : -INFINITY;
+            logLc = 0.0;
+          }
+          blk_unit(LC, se);
+          __syncthreads();
+          const int nmv = (move == 0) ? Ly - 1 : Ly;
+          for (int y = 0; y < nmv; ++y) {
+            const double u = uniform53(slot, (uint32_t)sweep_id, (uint32_t)c, 0u, seed);
+            ++slot;
+            const int i0 = x * Ly + y, i1 = i0 + 1;
+            const bool possible = (move == 0) ? (Sl[i0] != Sl[i1]) : true;
+            if (possible) {
+              const int w_ = (move == 0) ? 2 : 1;
+              blk_copy(LW, LC, se);
+              __syncthreads();
+              double lw = logLc;
+              for (int cc = 0; cc < w_; ++cc) {
+                const int site = i0 + cc;
+                int s_new;
+                if (move == 0) s_new = (cc == 0) ? Sl[i1] : Sl[i0];
+                else s_new = g.d - 1 - Sl[site];
+                blk_copy(eu, EU + (size_t)(y + cc) * se, se);
+                blk_copy(el, EL + (size_t)(y + cc) * se, se);
+                load_A(A1, Tpad, g, site, s_new, false);
+                __syncthreads();
+                absorb1(g, LW, eu, A1, el, t1, t2, LW2);
+                lw += blk_normalize(LW2, se, red, &st);
+                blk_copy(LW, LW2, se);
+                __syncthreads();
+              }
+              const T v = blk_dot(LW, RP + (size_t)(y + w_) * se, se, red);
+              if (threadIdx.x == 0) {
+                const double l1 = ((double)v != 0.0) ? log(fabs((double)v)) + lw + logR[y + w_] : -INFINITY;
+                accept_flag = (isfinite(l1) && u < exp(2.0 * (l1 - lcur))) ? 1 : 0;
+                if (accept_flag) {
+                  lcur = l1;
+                  if (move == 0) { const uint8_t tmp = Sl[i0]; Sl[i0] = Sl[i1]; Sl[i1] = tmp; }
+                  else Sl[i0] = (uint8_t)(g.d - 1 - Sl[i0]);
+                }
+              }
+              __syncthreads();
+              acc += accept_flag;
+            }
+            // advance the running left partial over column y (current state)
+            blk_copy(eu, EU + (size_t)y * se, se);
+            blk_copy(el, EL + (size_t)y * se, se);
+            load_A(A1, Tpad, g, x * Ly + y, Sl[x * Ly + y], false);
+            __syncthreads();
+            absorb1(g, LC, eu, A1, el, t1, t2, LW2);
+            const double l = blk_normalize(LW2, se, red, &st);
+            blk_copy(LC, LW2, se);
+            if (threadIdx.x == 0) logLc += l;
+            __syncthreads();
+          }
+        }
+        // ---- vertical moves (x, y) <-> (x+1, y) with psi_{x,x+1} (E^u[x-1], E^l[x+2])
+        if (move == 0 && x < Lx - 1) {
+          const T* EL2 = env + (size_t)slot_lo(g, x + 2) * rowsz;
+          blk_unit(RP + (size_t)Ly * s2, s2);
+          if (threadIdx.x == 0) logR[Ly] = 0.0;
+          __syncthreads();
+          for (int y = Ly - 1; y >= 0; --y) {
+            blk_copy(eu, EU + (size_t)y * se, se);
+            blk_copy(el, EL2 + (size_t)y * se, se);
+            load_A(A1, Tpad, g, x * Ly + y, Sl[x * Ly + y], false);
+            load_A(A2, Tpad, g, (x + 1) * Ly + y, Sl[(x + 1) * Ly + y], false);
+            __syncthreads();
+            absorb2_right(g, RP + (size_t)(y + 1) * s2, eu, A1, A2, el, t1, t2, RP + (size_t)y * s2, plan.cx);
+            const double l = blk_normalize(RP + (size_t)y * s2, s2, red, &st);
+            if (threadIdx.x == 0) logR[y] = logR[y + 1] + l;
+          }
+          __syncthreads();
+          if (threadIdx.x == 0) {
+            const double v = (double)RP[0];
+            lcur = (v != 0.0) ? log(fabs(v)) + logR[0] : -INFINITY;
+            logLc = 0.0;
+          }
+          blk_unit(LC, s2);
+          __syncthreads();
+          for (int y = 0; y < Ly; ++y) {
+            const double u = uniform53(slot, (uint32_t)sweep_id, (uint32_t)c, 0u, seed);
+            ++slot;
+            const int i0 = x * Ly + y, i1 = (x + 1) * Ly + y;
+            blk_copy(eu, EU + (size_t)y * se, se);
+            blk_copy(el, EL2 + (size_t)y * se, se);
+            if (Sl[i0] != Sl[i1]) {
+              load_A(A1, Tpad, g, i0, Sl[i1], false);
+              load_A(A2, Tpad, g, i1, Sl[i0], false);
+              __syncthreads();
+              absorb2(g, LC, eu, A1, A2, el, t1, t2, LW2, plan.cx);
+              const double lw = logLc + blk_normalize(LW2, s2, red, &st);
+              const T v = blk_dot(LW2, RP + (size_t)(y + 1) * s2, s2, red);
+              if (threadIdx.x == 0) {
+                const double l1 = ((double)v != 0.0) ? log(fabs((double)v)) + lw + logR[y + 1] : -INFINITY;
+                accept_flag = (isfinite(l1) && u < exp(2.0 * (l1 - lcur))) ? 1 : 0;
+                if (accept_flag) {
+                  lcur = l1;
+                  const uint8_t tmp = Sl[i0]; Sl[i0] = Sl[i1]; Sl[i1] = tmp;
+                }
+              }
+              __syncthreads();
+              acc += accept_flag;
+            }
+            load_A(A1, Tpad, g, i0, Sl[i0], false);
+            load_A(A2, Tpad, g, i1, Sl[i1], false);
+            __syncthreads();
+            absorb2(g, LC, eu, A1, A2, el, t1, t2, LW2, plan.cx);
+            const double l = blk_normalize(LW2, s2, red, &st);
+            blk_copy(LC, LW2, s2);
+            if (threadIdx.x == 0) logLc += l;
+            __syncthreads();
+          }
+        }
+        // ---- E^u[x] from the updated row
+        if (x < Lx - 1) {
+          const size_t sl = (size_t)slot_up(g, x) * rowsz;
+          double l;
+          if (x == 0) l = env_first_row(g, env + sl, Tpad, 0, Sl, false, w.A, w.Z, red, &st);
+          else l = lg[slot_up(g, x - 1)] + env_row_step(g, env + (size_t)slot_up(g, x - 1) * rowsz, env + sl, Tpad, x,
+                                                         Sl + (size_t)x * Ly, false, w, &st, &wd, &flag);
+          if (threadIdx.x == 0) lg[slot_up(g, x)] = l;
+          __syncthreads();
+        }
+      }
+    }
+    for (int i = threadIdx.x; i < N; i += blockDim.x) Sg[i] = Sl[i];
+    if (threadIdx.x == 0) {
+      if (accepted) accepted[c] += acc;
+      if (st) atomicOr(status + c, st);
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// theta (compact, double) -> padded kernel layout [site][s][l][u][r][d] in T
+template <typename T>
+__global__ void k_pad_theta(Geo g, const double* __restrict__ theta, const long long* site_off, T* Tpad) {
+  const long long total = (long long)g.Lx * g.Ly * g.d * g.sT;
+  const int D = g.D;
+  for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < total; o += (long long)gridDim.x * blockDim.x) {
+    const int dd = o % D, r = (o / D) % D, u = (o / (D * D)) % D, l = (o / (D * D * D)) % D;
+    const int s = (o / g.sT) % g.d;
+    const int site = (int)(o / ((long long)g.sT * g.d));
+    const int x = site / g.Ly, y = site % g.Ly;
+    int Dl, Du, Dr, Dd;
+    site_dims(g, x, y, &Dl, &Du, &Dr, &Dd);
+    T v = T(0);
+    if (l < Dl && u < Du && r < Dr && dd < Dd)
+      v = (T)theta[site_off[site] + (((long long)s * Dl + l) * Du + u) * Dr * Dd + (long long)r * Dd + dd];
+    Tpad[o] = v;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// host-side launch wrappers (explicit instantiations for double and float)
+template <typename T>
+cudaError_t launch_env(const Geo& g, const Plan& p, int grid, size_t smem, const T* Tpad, const uint8_t* S, int Ns,
+                       int sides, T* envs, double* logs, int* status, float* wdisc, cudaStream_t s) {
+  k_env<T><<<grid, NTHREADS, smem, s>>>(g, p, Tpad, S, Ns, sides, envs, logs, status, wdisc);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_row(const Geo& g, const Plan& p, int grid, size_t smem, const T* Tpad, const uint8_t* S, int Ns,
+                       int x_lo, int x_hi, const T* envs, const double* logs, T* O, const long long* site_off,
+                       long long Np, const TermTab& tt, double* rowout, int* status, cudaStream_t s) {
+  k_row<T><<<grid, NTHREADS, smem, s>>>(g, p, Tpad, S, Ns, x_lo, x_hi, envs, logs, O, site_off, Np, tt, rowout, status);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_pair(const Geo& g, const Plan& p, int grid, size_t smem, const T* Tpad, const uint8_t* S, int Ns,
+                        const T* envs, const double* logs, const TermTab& tt, double* pairout, int* status, cudaStream_t s) {
+  k_pair<T><<<grid, NTHREADS, smem, s>>>(g, p, Tpad, S, Ns, envs, logs, tt, pairout, status);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_sample(const Geo& g, const Plan& p, int grid, size_t smem, const T* Tpad, uint8_t* S, int Ns,
+                          int move, int nsweeps, unsigned long long seed, unsigned long long sweep0, T* envs,
+                          double* logs, long long* accepted, int* status, cudaStream_t s) {
+  k_sample<T><<<grid, NTHREADS, smem, s>>>(g, p, Tpad, S, Ns, move, nsweeps, seed, sweep0, envs, logs, accepted, status);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_pad(const Geo& g, const double* theta, const long long* site_off, T* Tpad, cudaStream_t s) {
+  k_pad_theta<T><<<304, 256, 0, s>>>(g, theta, site_off, Tpad);
+  return cudaGetLastError();
+}
+cudaError_t launch_combine(const Geo& g, int Ns, const uint8_t* S, const double* rowout, const double* pairout,
+                           int use_rows_all, int use_pairs, const DiagTab& dg, double* logabs, double* phase,
+                           double* eloc, cudaStream_t s) {
+  const int blocks = (Ns * 32 + 255) / 256;
+  k_combine<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(g, Ns, S, rowout, pairout, use_rows_all, use_pairs, dg, logabs, phase, eloc);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t set_kernel_smem(size_t bytes) {
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_env<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_row<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_pair<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)) != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_sample<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <typename T>
+int occupancy(int which, size_t smem) {
+  int nb = 0;
+  switch (which) {
+    case 0: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_env<T>, NTHREADS, smem); break;
+    case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_row<T>, NTHREADS, smem); break;
+    case 2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pair<T>, NTHREADS, smem); break;
+    default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sample<T>, NTHREADS, smem); break;
+  }
+  return nb;
+}
+
+#define PEPS_INST(T)                                                                                              \
+  template cudaError_t launch_env<T>(const Geo&, const Plan&, int, size_t, const T*, const uint8_t*, int, int, T*, \
+                                     double*, int*, float*, cudaStream_t);                                        \
+  template cudaError_t launch_row<T>(const Geo&, const Plan&, int, size_t, const T*, const uint8_t*, int, int, int, \
+                                     const T*, const double*, T*, const long long*, long long, const TermTab&,    \
+                                     double*, int*, cudaStream_t);                                                \
+  template cudaError_t launch_pair<T>(const Geo&, const Plan&, int, size_t, const T*, const uint8_t*, int, const T*, \
+                                      const double*, const TermTab&, double*, int*, cudaStream_t);                \
+  template cudaError_t launch_sample<T>(const Geo&, const Plan&, int, size_t, const T*, uint8_t*, int, int, int,   \
+                                        unsigned long long, unsigned long long, T*, double*, long long*, int*,    \
+                                        cudaStream_t);                                                            \
+  template cudaError_t launch_pad<T>(const Geo&, const double*, const long long*, T*, cudaStream_t);              \
+  template cudaError_t set_kernel_smem<T>(size_t);                                                                \
+  template int occupancy<T>(int, size_t);
+
+PEPS_INST(double)
+PEPS_INST(float)
+
+}  // namespace peps

@@ -1,0 +1,74 @@
+// Declarations shared by the kernel translation units and the C-ABI layer.
+#pragma once
+#include "peps_tn.cuh"
+
+namespace peps {
+
+constexpr int NTHREADS = 256;
+constexpr int MAX_LY = 32;
+
+// term record (ints): number of sites, the sites, window (first row, first column, width,
+// two-row flag) and the entry range
+enum : int {
+  TI_K = 0, TI_S0 = 1, TI_X0 = 5, TI_Y0 = 6, TI_W = 7, TI_TWO = 8, TI_EOFF = 9, TI_ECNT = 10, TI_N = 11
+};
+
+struct TermTab {
+  int nterm;
+  const int* tinfo;     // nterm x TI_N, sorted: one-row terms by row, then two-row terms by row
+  const int* ent_ab;    // entries (a, b), h[a][b] != 0
+  const double* ent_h;  // entries (re, im)
+  const int* row_off;   // Lx+1: one-row terms of row x are [row_off[x], row_off[x+1])
+  const int* pair_off;  // Lx: two-row terms of rows x, x+1 are [pair_off[x], pair_off[x+1])
+};
+
+struct DiagTab {
+  int npairs;
+  const int* pair_ij;
+  const double* pair_v;
+  const double* onsite;  // N x d or null
+};
+
+template <typename T>
+cudaError_t launch_env(const Geo& g, const Plan& p, int grid, size_t smem, const T* Tpad, const uint8_t* S, int Ns,
+                       int sides, T* envs, double* logs, int* status, float* wdisc, cudaStream_t s);
+template <typename T>
+cudaError_t launch_row(const Geo& g, const Plan& p, int grid, size_t smem, const T* Tpad, const uint8_t* S, int Ns,
+                       int x_lo, int x_hi, const T* envs, const double* logs, T* O, const long long* site_off,
+                       long long Np, const TermTab& tt, double* rowout, int* status, cudaStream_t s);
+template <typename T>
+cudaError_t launch_pair(const Geo& g, const Plan& p, int grid, size_t smem, const T* Tpad, const uint8_t* S, int Ns,
+                        const T* envs, const double* logs, const TermTab& tt, double* pairout, int* status,
+                        cudaStream_t s);
+template <typename T>
+cudaError_t launch_sample(const Geo& g, const Plan& p, int grid, size_t smem, const T* Tpad, uint8_t* S, int Ns,
+                          int move, int nsweeps, unsigned long long seed, unsigned long long sweep0, T* envs,
+                          double* logs, long long* accepted, int* status, cudaStream_t s);
+template <typename T>
+cudaError_t launch_pad(const Geo& g, const double* theta, const long long* site_off, T* Tpad, cudaStream_t s);
+cudaError_t launch_combine(const Geo& g, int Ns, const uint8_t* S, const double* rowout, const double* pairout,
+                           int use_rows_all, int use_pairs, const DiagTab& dg, double* logabs, double* phase,
+                           double* eloc, cudaStream_t s);
+template <typename T>
+cudaError_t set_kernel_smem(size_t bytes);
+template <typename T>
+int occupancy(int which, size_t smem);
+
+// ---- MinSR (FP64)
+// column means m_k = sum_S w_S O_{S,k} (w normalised), and Obar = sqrt(w)(O - m) written as
+// double (Ns x Np)
+template <typename TO>
+cudaError_t launch_center(const TO* O, const double* w, int Ns, long long Np, double* mean, double* Obar,
+                          cudaStream_t s);
+cudaError_t launch_center_e(const double* eloc, const double* w, int Ns, double* ebar, cudaStream_t s);
+cudaError_t launch_gram(const double* Obar, int Ns, long long Np, double* Tm, int ld, cudaStream_t s);
+// cyclic Jacobi eigendecomposition of the symmetric Ns x Ns matrix A (overwritten by its
+// diagonal form), V accumulates the rotations; returns the sweeps used (host loop)
+int jacobi_eig(double* A, double* V, int n, double* rot, double* offn, double* hbuf, cudaStream_t s,
+               int max_sweeps, cudaError_t* err);
+cudaError_t launch_minsr_apply(const double* A, const double* V, const double* ebar, int n, int nreal, double lambda,
+                               double rcond, double* y, double* x, double* info, cudaStream_t s);
+cudaError_t launch_obar_t_x(const double* Obar, const double* x, int Ns, long long Np, double tau, double* dtheta,
+                            cudaStream_t s);
+
+}  // namespace peps

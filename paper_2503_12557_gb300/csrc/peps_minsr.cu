@@ -1,0 +1,284 @@
+// MinSR update in FP64 (paper Eq. (tdvp_fast)): T = Obar Obar^T (N_s x N_s), eigendecomposition
+// T = V diag(Lambda) V^T by cyclic Jacobi, pseudo-inverse with cutoff, dtheta = -tau Obar^T x.
+#include "peps_kernels.cuh"
+
+namespace peps {
+
+// ---- centring: mean_k = sum_S w_S O_{S,k}; Obar_{S,k} = sqrt(w_S) (O_{S,k} - mean_k)
+template <typename TO>
+__global__ void k_center(const TO* __restrict__ O, const double* __restrict__ w, int Ns, long long Np, double wsum,
+                         double* mean, double* Obar) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < Np; k += (long long)gridDim.x * blockDim.x) {
+    double m = 0.0;
+    for (int s = 0; s < Ns; ++s) m += (w ? w[s] / wsum : 1.0 / Ns) * (double)O[(size_t)s * Np + k];
+    mean[k] = m;
+    for (int s = 0; s < Ns; ++s) {
+      const double sw = sqrt(w ? w[s] / wsum : 1.0 / Ns);
+      Obar[(size_t)s * Np + k] = sw * ((double)O[(size_t)s * Np + k] - m);
+    }
+  }
+}
+
+__global__ void k_wsum(const double* w, int Ns, double* out) {
+  __shared__ double red[33];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < Ns; i += blockDim.x) s += w[i];
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) *out = s;
+}
+
+// ebar_S = sqrt(w_S) (Re E_loc(S) - sum_S' w_S' Re E_loc(S')); eloc is (re, im) interleaved
+__global__ void k_center_e(const double* eloc, const double* w, int Ns, double* ebar) {
+  __shared__ double red[33];
+  double ws = 0.0, m = 0.0;
+  for (int i = threadIdx.x; i < Ns; i += blockDim.x) {
+    const double wi = w ? w[i] : 1.0;
+    ws += wi;
+    m += wi * eloc[2 * i];
+  }
+  ws = block_sum(ws, red);
+  m = block_sum(m, red) / ws;
+  for (int i = threadIdx.x; i < Ns; i += blockDim.x) {
+    const double wi = (w ? w[i] : 1.0) / ws;
+    ebar[i] = sqrt(wi) * (eloc[2 * i] - m);
+  }
+}
+
+// ---- Gram T = Obar Obar^T, 64 x 64 output tiles, K staged through shared memory in chunks
+// of 16; only tiles with ti >= tj are computed, the upper triangle is mirrored.
+constexpr int GT = 64, GK = 16;
+__global__ void __launch_bounds__(256) k_gram(const double* __restrict__ Ob, int Ns, long long Np, double* Tm, int ld) {
+  __shared__ double As[GK][GT + 1], Bs[GK][GT + 1];
+  const int nt = (Ns + GT - 1) / GT;
+  // linear index over lower-triangle tiles
+  int t = blockIdx.x, ti = 0;
+  while (t >= ti + 1) { t -= ti + 1; ++ti; }
+  const int tj = t;
+  if (ti >= nt) return;
+  const int r0 = ti * GT, c0 = tj * GT;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;  // each thread: 4 x 4 outputs
+  double acc[4][4] = {};
+  for (long long k0 = 0; k0 < Np; k0 += GK) {
+    for (int o = threadIdx.x; o < GK * GT; o += blockDim.x) {
+      const int kk = o % GK, rr = o / GK;
+      const long long k = k0 + kk;
+      As[kk][rr] = (r0 + rr < Ns && k < Np) ? Ob[(size_t)(r0 + rr) * Np + k] : 0.0;
+      Bs[kk][rr] = (c0 + rr < Ns && k < Np) ? Ob[(size_t)(c0 + rr) * Np + k] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GK; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) { a[i] = As[kk][ty * 4 + i]; b[i] = Bs[kk][tx * 4 + i]; }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int r = r0 + ty * 4 + i, c = c0 + tx * 4 + j;
+      if (r < Ns && c < Ns) {
+        Tm[(size_t)r * ld + c] = acc[i][j];
+        Tm[(size_t)c * ld + r] = acc[i][j];
+      }
+    }
+}
+
+// ---- cyclic Jacobi, parallel round-robin ordering.  One launch per round: every thread owns
+// one 2x2 block (pair I, pair J) of the old matrix and writes the rotated block into the new
+// one; rotation parameters are recomputed from the old diagonal blocks (classical two-sided
+// Jacobi, Golub & Van Loan sym.schur2: tau = (a_qq - a_pp) / (2 a_pq), t = sign(tau) /
+// (|tau| + sqrt(1 + tau^2)), c = 1/sqrt(1+t^2), s = t c; B = J^T A J with J = [[c, s], [-s, c]]).
+__device__ __forceinline__ void jac_params(const double* A, int n, int p, int q, double* c, double* s) {
+  const double apq = A[(size_t)p * n + q];
+  const double app = A[(size_t)p * n + p], aqq = A[(size_t)q * n + q];
+  if (apq == 0.0 || fabs(apq) <= 1e-15 * sqrt(fabs(app * aqq))) { *c = 1.0; *s = 0.0; return; }
+  const double tau = (aqq - app) / (2.0 * apq);
+  double t;
+  if (fabs(tau) > 1e150) t = 0.5 / tau;
+  else t = copysign(1.0, tau) / (fabs(tau) + sqrt(1.0 + tau * tau));
+  *c = 1.0 / sqrt(1.0 + t * t);
+  *s = t * (*c);
+}
+
+__global__ void k_jacobi_round(const double* __restrict__ A, double* __restrict__ An, double* V, int n, int r,
+                               unsigned long long* nrot, double* offn) {
+  const int h = n / 2;
+  const long long nblk = (long long)h * h;
+  const long long nv = (long long)n * h;
+  for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < nblk + nv;
+       o += (long long)gridDim.x * blockDim.x) {
+    if (o < nblk) {
+      const int I = (int)(o / h), J = (int)(o % h);
+      const int pI = rr_player(I, r, n), qI = rr_player(n - 1 - I, r, n);
+      const int pJ = rr_player(J, r, n), qJ = rr_player(n - 1 - J, r, n);
+      double cI, sI, cJ, sJ;
+      jac_params(A, n, pI, qI, &cI, &sI);
+      jac_params(A, n, pJ, qJ, &cJ, &sJ);
+      const double a00 = A[(size_t)pI * n + pJ], a01 = A[(size_t)pI * n + qJ];
+      const double a10 = A[(size_t)qI * n + pJ], a11 = A[(size_t)qI * n + qJ];
+      // columns: (x, y) -> (c x - s y, s x + c y)
+      const double b00 = cJ * a00 - sJ * a01, b01 = sJ * a00 + cJ * a01;
+      const double b10 = cJ * a10 - sJ * a11, b11 = sJ * a10 + cJ * a11;
+      // rows
+      double d00 = cI * b00 - sI * b10, d01 = cI * b01 - sI * b11;
+      double d10 = sI * b00 + cI * b10, d11 = sI * b01 + cI * b11;
+      if (I == J && sI != 0.0) { d01 = 0.0; d10 = 0.0; }  // the annihilated pair
+      An[(size_t)pI * n + pJ] = d00;
+      An[(size_t)pI * n + qJ] = d01;
+      An[(size_t)qI * n + pJ] = d10;
+      An[(size_t)qI * n + qJ] = d11;
+      if (I == J && sI != 0.0) atomicAdd(nrot, 1ull);
+      if (offn && I != J) atomicAdd(offn, 2.0 * (a00 * a00 + a01 * a01 + a10 * a10 + a11 * a11));
+    } else {
+      const long long v = o - nblk;
+      const int i = (int)(v / h), J = (int)(v % h);
+      const int pJ = rr_player(J, r, n), qJ = rr_player(n - 1 - J, r, n);
+      double c, s;
+      jac_params(A, n, pJ, qJ, &c, &s);
+      if (s != 0.0) {
+        const double x = V[(size_t)i * n + pJ], y = V[(size_t)i * n + qJ];
+        V[(size_t)i * n + pJ] = c * x - s * y;
+        V[(size_t)i * n + qJ] = s * x + c * y;
+      }
+    }
+  }
+}
+
+__global__ void k_eye(double* V, int n) {
+  for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < (long long)n * n;
+       o += (long long)gridDim.x * blockDim.x)
+    V[o] = ((o / n) == (o % n)) ? 1.0 : 0.0;
+}
+
+// A (n x n, n even) -> diagonal form in place (ping-pong with hbuf), V = accumulated rotations.
+// Returns sweeps used (>= 1), or -1 when the sweep limit was reached.  Synchronises the stream
+// once per sweep to read the rotation count.
+int jacobi_eig(double* A, double* V, int n, double* rot, double* offn, double* hbuf, cudaStream_t s,
+               int max_sweeps, cudaError_t* err) {
+  (void)offn;
+  unsigned long long* dcount = (unsigned long long*)rot;
+  *err = cudaSuccess;
+  k_eye<<<304, 256, 0, s>>>(V, n);
+  double* cur = A;
+  double* nxt = hbuf;
+  const long long work = (long long)(n / 2) * (n / 2) + (long long)n * (n / 2);
+  const int blocks = (int)((work + 255) / 256 < 152 * 16 ? (work + 255) / 256 : 152 * 16);
+  int sweeps = -1;
+  for (int sw = 0; sw < max_sweeps; ++sw) {
+    cudaMemsetAsync(dcount, 0, sizeof(unsigned long long), s);
+    for (int r = 0; r < n - 1; ++r) {
+      k_jacobi_round<<<blocks, 256, 0, s>>>(cur, nxt, V, n, r, dcount, nullptr);
+      double* t = cur; cur = nxt; nxt = t;
+    }
+    unsigned long long h = 0;
+    cudaMemcpyAsync(&h, dcount, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if ((*err = cudaStreamSynchronize(s)) != cudaSuccess) return -1;
+    if (h == 0) { sweeps = sw + 1; break; }
+  }
+  if (cur != A) cudaMemcpyAsync(A, cur, sizeof(double) * (size_t)n * n, cudaMemcpyDeviceToDevice, s);
+  if ((*err = cudaGetLastError()) != cudaSuccess) return -1;
+  return sweeps;
+}
+
+// info: [rank kept, min Lambda, max Lambda]; y = f(Lambda) .* (V^T ebar); x = V y
+__global__ void k_minsr_scalars(const double* A, int n, int nreal, double rcond, double* info) {
+  __shared__ double red[33];
+  double mx = -INFINITY, mn = INFINITY;
+  // a padding index (n = nreal + 1) has a zero row and column and is never rotated: it stays last
+  for (int i = threadIdx.x; i < nreal; i += blockDim.x) {
+    const double l = A[(size_t)i * n + i];
+    mx = fmax(mx, l);
+    mn = fmin(mn, l);
+  }
+  mx = block_max(mx, red);
+  mn = -block_max(-mn, red);
+  int cnt = 0;
+  for (int i = threadIdx.x; i < nreal; i += blockDim.x) cnt += (rcond > 0.0) ? (A[(size_t)i * n + i] > rcond * mx) : 1;
+  const double c = block_sum((double)cnt, red);
+  if (threadIdx.x == 0) { info[0] = c; info[1] = mn; info[2] = mx; }
+}
+
+__global__ void k_vt_e(const double* A, const double* V, const double* ebar, int n, double lambda, double rcond,
+                       const double* info, double* y) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int j = 0; j < n; ++j) s += V[(size_t)j * n + i] * ebar[j];
+    const double l = A[(size_t)i * n + i];
+    const bool keep = (rcond > 0.0) ? (l > rcond * info[2]) : true;
+    y[i] = keep ? s / (l + lambda) : 0.0;
+  }
+}
+
+__global__ void k_v_y(const double* V, const double* y, int n, double* x) {
+  const int lane = threadIdx.x & 31;
+  for (int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < n; j += (gridDim.x * blockDim.x) >> 5) {
+    double s = 0.0;
+    for (int i = lane; i < n; i += 32) s += V[(size_t)j * n + i] * y[i];
+    s = warp_sum(s);
+    if (lane == 0) x[j] = s;
+  }
+}
+
+__global__ void k_obar_t_x(const double* __restrict__ Ob, const double* __restrict__ x, int Ns, long long Np,
+                           double tau, double* dtheta) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < Np; k += (long long)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int i = 0; i < Ns; ++i) s += Ob[(size_t)i * Np + k] * x[i];
+    dtheta[k] = -tau * s;
+  }
+}
+
+// ---- host wrappers
+template <typename TO>
+cudaError_t launch_center(const TO* O, const double* w, int Ns, long long Np, double* mean, double* Obar,
+                          cudaStream_t s) {
+  double wsum = 1.0;
+  if (w) {
+    double* d = mean;  // borrow the first element for the weight sum
+    k_wsum<<<1, 256, 0, s>>>(w, Ns, d);
+    cudaError_t e = cudaMemcpyAsync(&wsum, d, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+  }
+  const long long blocks = (Np + 255) / 256;
+  k_center<TO><<<(int)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(O, w, Ns, Np, wsum, mean, Obar);
+  return cudaGetLastError();
+}
+template cudaError_t launch_center<double>(const double*, const double*, int, long long, double*, double*, cudaStream_t);
+template cudaError_t launch_center<float>(const float*, const double*, int, long long, double*, double*, cudaStream_t);
+
+cudaError_t launch_center_e(const double* eloc, const double* w, int Ns, double* ebar, cudaStream_t s) {
+  k_center_e<<<1, 1024, 0, s>>>(eloc, w, Ns, ebar);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gram(const double* Obar, int Ns, long long Np, double* Tm, int ld, cudaStream_t s) {
+  const int nt = (Ns + GT - 1) / GT;
+  const int ntiles = nt * (nt + 1) / 2;
+  k_gram<<<ntiles, 256, 0, s>>>(Obar, Ns, Np, Tm, ld);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_minsr_apply(const double* A, const double* V, const double* ebar, int n, int nreal, double lambda,
+                               double rcond, double* y, double* x, double* info, cudaStream_t s) {
+  k_minsr_scalars<<<1, 1024, 0, s>>>(A, n, nreal, rcond, info);
+  k_vt_e<<<(n + 255) / 256, 256, 0, s>>>(A, V, ebar, n, lambda, rcond, info, y);
+  k_v_y<<<(n * 32 + 255) / 256, 256, 0, s>>>(V, y, n, x);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_obar_t_x(const double* Obar, const double* x, int Ns, long long Np, double tau, double* dtheta,
+                            cudaStream_t s) {
+  const long long blocks = (Np + 255) / 256;
+  k_obar_t_x<<<(int)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(Obar, x, Ns, Np, tau, dtheta);
+  return cudaGetLastError();
+}
+
+}  // namespace peps

@@ -1,0 +1,747 @@
+// Device building blocks of the single-layer boundary-MPS contraction (sm_103a).
+//
+// Paper: Sec. "On the boundary MPS method" -- E^u[i] approximates the i uppermost rows of the
+// network projected on a configuration as an MPS of bond D_c (chi here); each MPS-MPO product
+// (bond chi*D) is truncated back to chi.  Sec. "On Numerical Stability" -- every environment
+// tensor is divided by its largest modulus and the logarithms are accumulated.
+//
+// Every dimension is padded: boundary legs of dimension 1 are stored as D (or chi) with zeros,
+// so every environment site tensor is chi x D x chi and every projected PEPS tensor is D^4.
+// Zero padding changes no contraction value.
+//
+// Layouts (row major):
+//   projected PEPS tensor  A[l][u][r][d]     (for the lower side the u and d legs are swapped on
+//                                              load, so both sides run the same code)
+//   environment site       e[a][p][b]         a, b in chi (bonds), p in D (open leg)
+//   one-row partial        L[a][l][b]         a: E^u bond, l: PEPS bond, b: E^l bond
+//   two-row partial        L2[a][i][j][b]
+//
+// Truncation (the "density matrix algorithm" the paper names, in a QR-based form that never
+// squares singular values): left pass Z_k = R_{k-1} M_k, Householder QR of Z_k keeps only R_k
+// (R_k^T R_k is the exact left Gram environment of bond k); right pass Y_k = M_k C_k,
+// X_k = R_{k-1} Y_k, one-sided Jacobi on the rows of X_k gives its right singular vectors; the
+// top chi become the new site tensor and C_{k-1} = Y_k V.  The state it produces is the
+// sequential right-to-left SVD compression of the exact product.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <math.h>
+
+namespace peps {
+
+enum : int {
+  ST_NEAR_DEGENERATE = 1,
+  ST_ZERO_NORM = 2,
+  ST_NONFINITE = 4,
+  ST_NOCONV = 8
+};
+
+struct Geo {
+  int Lx, Ly, d, D, chi;
+  int n;   // chi*D, exact product bond
+  int se;  // chi*D*chi, one environment site
+  int sT;  // D^4, one projected PEPS tensor
+  int s2;  // chi*D*D*chi, one two-row partial
+};
+
+// ------------------------------------------------------------------------------------------
+// buffer plan: every kernel carves its buffers out of dynamic shared memory or out of a
+// per-CTA slice of a global scratch arena, as the host planner decided.
+enum Buf : int {
+  B_R = 0, B_E, B_A, B_A2, B_Z, B_W, B_C, B_SIG, B_SEL, B_RED,
+  B_RHIST, B_LP, B_RP, B_T1, B_T2, B_EU, B_EL, B_LW, B_LW2, B_S, B_NBUF
+};
+
+struct Plan {
+  unsigned long long off[B_NBUF];  // byte offset inside its arena
+  unsigned gmask;                  // bit b set: buffer b lives in the global arena
+  unsigned long long gstride;      // bytes of global arena per CTA
+  int ci;                          // row chunk of the left-pass W buffer
+  int cx;                          // chunk of the two-row contractions
+  char* gbase;                     // global arena (gstride bytes per CTA)
+};
+
+__device__ __forceinline__ char* buf_ptr(const Plan& p, int b, char* smem, char* gbase) {
+  if (p.gmask & (1u << b)) return gbase + (size_t)blockIdx.x * p.gstride + p.off[b];  // gbase = p.gbase
+  return smem + p.off[b];
+}
+
+// ------------------------------------------------------------------------------------------
+// block reductions (blockDim.x a multiple of 32, at most 1024)
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <typename T>
+__device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// red: at least 33 doubles of shared (or global) scratch.  All threads get the result.
+template <typename T>
+__device__ T block_sum(T v, double* red) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (l == 0) red[w] = (double)v;
+  __syncthreads();
+  if (w == 0) {
+    T t = (l < nw) ? (T)red[l] : T(0);
+    t = warp_sum(t);
+    if (l == 0) red[32] = (double)t;
+  }
+  __syncthreads();
+  return (T)red[32];
+}
+template <typename T>
+__device__ T block_max(T v, double* red) {
+  v = warp_max(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (l == 0) red[w] = (double)v;
+  __syncthreads();
+  if (w == 0) {
+    T t = (l < nw) ? (T)red[l] : T(0);
+    t = warp_max(t);
+    if (l == 0) red[32] = (double)t;
+  }
+  __syncthreads();
+  return (T)red[32];
+}
+
+template <typename T>
+__device__ void blk_copy(T* dst, const T* src, int n) {
+  for (int o = threadIdx.x; o < n; o += blockDim.x) dst[o] = src[o];
+}
+template <typename T>
+__device__ void blk_fill(T* dst, T v, int n) {
+  for (int o = threadIdx.x; o < n; o += blockDim.x) dst[o] = v;
+}
+// unit tensor: 1 at flat index 0, zeros elsewhere (trivial environments and partials)
+template <typename T>
+__device__ void blk_unit(T* dst, int n) {
+  for (int o = threadIdx.x; o < n; o += blockDim.x) dst[o] = (o == 0) ? T(1) : T(0);
+}
+
+// Divide v[0..n) by its largest modulus; returns ln(max) (or -inf with ZERO_NORM / NONFINITE
+// set in *st when the maximum is 0 or not finite).  Ends with a barrier.
+template <typename T>
+__device__ double blk_normalize(T* v, int n, double* red, int* st) {
+  T m = 0;
+  for (int o = threadIdx.x; o < n; o += blockDim.x) m = fmax(m, fabs(v[o]));
+  m = block_max(m, red);
+  if (!(m < INFINITY)) {  // NaN or Inf
+    if (threadIdx.x == 0) *st |= ST_NONFINITE;
+    __syncthreads();
+    return -INFINITY;
+  }
+  if (m == T(0)) {
+    if (threadIdx.x == 0) *st |= ST_ZERO_NORM;
+    __syncthreads();
+    return -INFINITY;
+  }
+  const T inv = T(1) / m;
+  for (int o = threadIdx.x; o < n; o += blockDim.x) v[o] *= inv;
+  __syncthreads();
+  return log((double)m);
+}
+
+// Projected PEPS tensor of site `site` with local state s, as A[l][u][r][d] (swap_ud: as
+// A[l][d][r][u], the lower-environment orientation).
+template <typename T>
+__device__ void load_A(T* As, const T* Tpad, const Geo& g, int site, int s, bool swap_ud) {
+  const T* src = Tpad + ((size_t)site * g.d + s) * g.sT;
+  const int D = g.D;
+  for (int o = threadIdx.x; o < g.sT; o += blockDim.x) {
+    if (!swap_ud) {
+      As[o] = src[o];
+    } else {
+      const int dd = o % D, r = (o / D) % D, u = (o / (D * D)) % D, l = o / (D * D * D);
+      As[o] = src[((l * D + dd) * D + r) * D + u];
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Householder QR of Z (m x nc, row major), keeping only R (nc x nc, upper triangular, zero
+// below the diagonal).  Reflector convention of LAPACK's xLARFG (H = I - tau v v^T, v_0 = 1).
+template <typename T>
+__device__ void qr_keep_r(T* Z, int m, int nc, T* R, double* red) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int steps = (m < nc) ? m : nc;
+  for (int j = 0; j < steps; ++j) {
+    T part = 0;
+    for (int i = j + 1 + tid; i < m; i += blockDim.x) {
+      const T z = Z[(size_t)i * nc + j];
+      part += z * z;
+    }
+    const T sigma = block_sum(part, red);
+    const T alpha = Z[(size_t)j * nc + j];
+    T tau = 0, beta = alpha;
+    if (sigma != T(0)) {
+      const T nrm = sqrt(alpha * alpha + sigma);
+      beta = (alpha >= T(0)) ? -nrm : nrm;
+      tau = (beta - alpha) / beta;
+      const T sc = T(1) / (alpha - beta);
+      for (int i = j + 1 + tid; i < m; i += blockDim.x) Z[(size_t)i * nc + j] *= sc;
+    }
+    __syncthreads();
+    if (tau != T(0)) {
+      for (int c = j + 1 + warp; c < nc; c += nw) {
+        T s = 0;
+        for (int i = j + 1 + lane; i < m; i += 32) s += Z[(size_t)i * nc + j] * Z[(size_t)i * nc + c];
+        s = warp_sum(s);
+        const T w = (s + Z[(size_t)j * nc + c]) * tau;
+        if (lane == 0) Z[(size_t)j * nc + c] -= w;
+        for (int i = j + 1 + lane; i < m; i += 32) Z[(size_t)i * nc + c] -= Z[(size_t)i * nc + j] * w;
+      }
+    }
+    __syncthreads();
+    if (tid == 0) Z[(size_t)j * nc + j] = beta;
+    __syncthreads();
+  }
+  for (int o = tid; o < nc * nc; o += blockDim.x) {
+    const int i = o / nc, c = o % nc;
+    R[o] = (i <= c && i < m) ? Z[(size_t)i * nc + c] : T(0);
+  }
+  __syncthreads();
+}
+
+// Round-robin ("chess tournament") ordering of m (even) players: player at position j in
+// round r.  Every round pairs position j with position m-1-j; the pairs of one round are
+// disjoint and every pair meets once per m-1 rounds.
+__device__ __forceinline__ int rr_player(int j, int r, int m) {
+  return (j == 0) ? 0 : ((j - 1 + r) % (m - 1)) + 1;
+}
+
+template <typename T> struct JacobiTol;
+template <> struct JacobiTol<double> { static constexpr double tol = 1e-15; static constexpr int sweeps = 40; };
+template <> struct JacobiTol<float> { static constexpr float tol = 2e-7f; static constexpr int sweeps = 30; };
+
+// One-sided (Hestenes) Jacobi on the rows of X (m rows, m even, row length L, leading dim
+// ldx): rotate pairs of rows until every pair is orthogonal to the relative tolerance.  On
+// return the rows are sigma_i v_i^T with v_i the right singular vectors of the input.
+// Returns the number of sweeps, or -1 when the sweep limit was hit.
+template <typename T>
+__device__ int hestenes_rows(T* X, int m, int L, int ldx, int* flag) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const T tol = JacobiTol<T>::tol;
+  for (int sweep = 0; sweep < JacobiTol<T>::sweeps; ++sweep) {
+    if (threadIdx.x == 0) *flag = 0;
+    __syncthreads();
+    int rotated = 0;
+    for (int r = 0; r < m - 1; ++r) {
+      for (int pi = warp; pi < m / 2; pi += nw) {
+        const int p = rr_player(pi, r, m), q = rr_player(m - 1 - pi, r, m);
+        T* xp = X + (size_t)p * ldx;
+        T* xq = X + (size_t)q * ldx;
+        T a = 0, b = 0, c = 0;
+        for (int i = lane; i < L; i += 32) {
+          const T u = xp[i], v = xq[i];
+          a += u * u;
+          b += v * v;
+          c += u * v;
+        }
+        a = warp_sum(a);
+        b = warp_sum(b);
+        c = warp_sum(c);
+        if (c != T(0) && fabs(c) > tol * sqrt(a * b)) {
+          // zeta = (b - a) / (2c); t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)) is the smaller
+          // root of t^2 + 2 zeta t - 1 = 0, which makes the rotated rows orthogonal.
+          const T zeta = (b - a) / (T(2) * c);
+          T t;
+          if (fabs(zeta) > T(1e15)) t = T(0.5) / zeta;
+          else t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+          const T cs = T(1) / sqrt(T(1) + t * t), sn = cs * t;
+          for (int i = lane; i < L; i += 32) {
+            const T u = xp[i], v = xq[i];
+            xp[i] = cs * u - sn * v;
+            xq[i] = sn * u + cs * v;
+          }
+          rotated = 1;
+        }
+      }
+      __syncthreads();
+    }
+    if (rotated) *flag = 1;  // benign race: every writer stores 1
+    __syncthreads();
+    const int any = *flag;
+    __syncthreads();
+    if (!any) return sweep + 1;
+  }
+  return -1;
+}
+
+// ------------------------------------------------------------------------------------------
+// Per-CTA working set of one boundary-MPS row step.
+template <typename T>
+struct RowWork {
+  T *R, *Rhist, *E, *A, *Z, *W, *C, *sig;
+  int* sel;
+  double* red;
+  int ci;
+};
+
+// One row step of the boundary MPS: Eout = normalise(truncate_chi(Eprev o T_proj[row])).
+//   Eprev, Eout: Ly environment sites (chi x D x chi each), may be global memory.
+//   Srow: the Ly local states of the applied row; lower: lower-environment orientation.
+// Returns the sum of the Ly log factors; *st collects status bits; *wdisc the largest
+// discarded weight (sum of discarded sigma^2 over sum of sigma^2) of any cut.
+template <typename T>
+__device__ double env_row_step(const Geo& g, const T* Eprev, T* Eout, const T* Tpad, int row,
+                               const uint8_t* Srow, bool lower, const RowWork<T>& w, int* st,
+                               float* wdisc, int* flag) {
+  const int chi = g.chi, D = g.D, n = g.n, Ly = g.Ly;
+  const int tid = threadIdx.x, NT = blockDim.x;
+  const int Lr = D * chi;           // row length of X, Y (open leg x truncated bond)
+  const int mX = n + (n & 1);       // Jacobi needs an even row count
+  // ---- left pass: R_{-1} = e00, R_k from QR(R_{k-1} M_k), k = 0..Ly-2
+  blk_unit(w.R, n * n);
+  __syncthreads();
+  for (int k = 0; k + 1 < Ly; ++k) {
+    blk_copy(w.E, Eprev + (size_t)k * g.se, g.se);
+    load_A(w.A, Tpad, g, row * Ly + k, Srow[k], lower);
+    __syncthreads();
+    for (int i0 = 0; i0 < n; i0 += w.ci) {
+      const int ci = (n - i0 < w.ci) ? (n - i0) : w.ci;
+      // W[ii][l][u][b] = sum_a R[i0+ii][(a,l)] E[a][u][b]
+      const int nW = ci * D * D * chi;
+      for (int o = tid; o < nW; o += NT) {
+        const int b = o % chi, u = (o / chi) % D, l = (o / (chi * D)) % D, ii = o / (chi * D * D);
+        const T* Rr = w.R + (size_t)(i0 + ii) * n + l;
+        const T* Ec = w.E + u * chi + b;
+        T s = 0;
+        for (int a = 0; a < chi; ++a) s += Rr[a * D] * Ec[a * D * chi];
+        w.W[o] = s;
+      }
+      __syncthreads();
+      // Z[(i0+ii, d)][(b, r)] = sum_{l,u} W[ii][l][u][b] A[l][u][r][d]
+      const int nZ = ci * D * n;
+      for (int o = tid; o < nZ; o += NT) {
+        const int r = o % D, b = (o / D) % chi, dd = (o / n) % D, ii = o / (n * D);
+        const T* Wr = w.W + (size_t)ii * D * D * chi + b;
+        T s = 0;
+        for (int lu = 0; lu < D * D; ++lu) s += Wr[lu * chi] * w.A[(lu * D + r) * D + dd];
+        w.Z[((size_t)(i0 + ii) * D + dd) * n + b * D + r] = s;
+      }
+      __syncthreads();
+    }
+    qr_keep_r(w.Z, n * D, n, w.R, w.red);
+    blk_copy(w.Rhist + (size_t)k * n * n, w.R, n * n);
+    __syncthreads();
+  }
+  // ---- right pass
+  T* P = w.Z;                              // chi*D*D*chi
+  T* Y = P + (size_t)chi * D * D * chi;    // n x Lr
+  T* X = Y + (size_t)n * Lr;               // mX x Lr
+  T* Vt = X + (size_t)mX * Lr;             // chi x Lr
+  T* Cn = Vt + (size_t)chi * Lr;           // n x chi
+  T* Bs = Cn + (size_t)n * chi;            // chi x D x chi (site being written)
+  // C_{Ly-1}[(b,r)][c] = delta_{(b,r),0} delta_{c,0}
+  blk_unit(w.C, n * chi);
+  __syncthreads();
+  double logsum = 0.0;
+  for (int k = Ly - 1; k >= 0; --k) {
+    blk_copy(w.E, Eprev + (size_t)k * g.se, g.se);
+    load_A(w.A, Tpad, g, row * Ly + k, Srow[k], lower);
+    __syncthreads();
+    // P[a][u][r][c] = sum_b E[a][u][b] C[(b,r)][c]
+    const int nP = chi * D * D * chi;
+    for (int o = tid; o < nP; o += NT) {
+      const int c = o % chi, r = (o / chi) % D, u = (o / (chi * D)) % D, a = o / (chi * D * D);
+      const T* Er = w.E + (a * D + u) * chi;
+      const T* Cc = w.C + r * chi + c;
+      T s = 0;
+      for (int b = 0; b < chi; ++b) s += Er[b] * Cc[b * D * chi];
+      P[o] = s;
+    }
+    __syncthreads();
+    if (k == 0) {
+      // first site: its left bond is trivial, keep only row (a,l) = (0,0) of Y = M_0 C_0
+      for (int o = tid; o < g.se; o += NT) {
+        const int c = o % chi, dd = (o / chi) % D, a = o / (chi * D);
+        T s = 0;
+        if (a == 0) {
+          for (int u = 0; u < D; ++u)
+            for (int r = 0; r < D; ++r) s += P[((0 * D + u) * D + r) * chi + c] * w.A[((0 * D + u) * D + r) * D + dd];
+        }
+        Bs[o] = s;
+      }
+      __syncthreads();
+      logsum += blk_normalize(Bs, g.se, w.red, st);
+      blk_copy(Eout, Bs, g.se);
+      __syncthreads();
+      break;
+    }
+    // Y[(a,l)][(d,c)] = sum_{u,r} P[a][u][r][c] A[l][u][r][d]
+    const int nY = n * Lr;
+    for (int o = tid; o < nY; o += NT) {
+      const int c = o % chi, dd = (o / chi) % D, l = (o / Lr) % D, a = o / (Lr * D);
+      const T* Pr = P + (size_t)a * D * D * chi + c;
+      const T* Ar = w.A + (size_t)l * D * D * D + dd;
+      T s = 0;
+      for (int ur = 0; ur < D * D; ++ur) s += Pr[ur * chi] * Ar[ur * D];
+      Y[o] = s;
+    }
+    // R_{k-1} from the left pass
+    blk_copy(w.R, w.Rhist + (size_t)(k - 1) * n * n, n * n);
+    __syncthreads();
+    // X = R_{k-1} Y  (R upper triangular), padded to mX rows
+    for (int o = tid; o < mX * Lr; o += NT) {
+      const int q = o % Lr, i = o / Lr;
+      T s = 0;
+      if (i < n)
+        for (int j = i; j < n; ++j) s += w.R[(size_t)i * n + j] * Y[(size_t)j * Lr + q];
+      X[o] = s;
+    }
+    __syncthreads();
+    const int sweeps = hestenes_rows(X, mX, Lr, Lr, flag);
+    if (sweeps < 0 && tid == 0) *st |= ST_NOCONV;
+    // singular values = row norms
+    {
+      const int lane = tid & 31, warp = tid >> 5, nw = NT >> 5;
+      for (int p = warp; p < mX; p += nw) {
+        T s = 0;
+        for (int i = lane; i < Lr; i += 32) s += X[(size_t)p * Lr + i] * X[(size_t)p * Lr + i];
+        s = warp_sum(s);
+        if (lane == 0) w.sig[p] = sqrt(s);
+      }
+    }
+    __syncthreads();
+    // stable descending rank; the first chi ranks are kept
+    for (int p = tid; p < mX; p += NT) {
+      const T sp = w.sig[p];
+      int rk = 0;
+      for (int q = 0; q < mX; ++q) {
+        const T sq = w.sig[q];
+        rk += (sq > sp) || (sq == sp && q < p);
+      }
+      w.sel[mX + p] = rk;          // rank of row p
+      if (rk < chi) w.sel[rk] = p; // row holding rank rk
+      if (rk == chi - 1) w.sig[mX + 0] = sp;  // sigma_(chi-1)
+      if (rk == chi) w.sig[mX + 1] = sp;      // sigma_(chi)
+      if (rk == 0) w.sig[mX + 2] = sp;        // sigma_(0)
+    }
+    if (tid == 0 && mX <= chi) { w.sig[mX + 1] = 0; }
+    __syncthreads();
+    if (mX > chi) {
+      // discarded weight and near-degenerate cut (same rule as the oracle)
+      T tot = 0, dis = 0;
+      for (int p = tid; p < mX; p += NT) {
+        const T s2 = w.sig[p] * w.sig[p];
+        tot += s2;
+        if (w.sel[mX + p] >= chi) dis += s2;
+      }
+      tot = block_sum(tot, w.red);
+      dis = block_sum(dis, w.red);
+      if (tid == 0) {
+        const T s0 = w.sig[mX + 2], sk = w.sig[mX + 0], sd = w.sig[mX + 1];
+        if (s0 > T(0) && (sk - sd) < T(1e-8) * s0 && sd > T(1e-12) * s0) *st |= ST_NEAR_DEGENERATE;
+        if (tot > T(0)) {
+          const float wd = (float)(dis / tot);
+          if (wd > *wdisc) *wdisc = wd;
+        }
+      }
+    }
+    // Vt[c'][q] = X[sel(c')][q] / sigma
+    const int nkeep = (mX < chi) ? mX : chi;
+    for (int o = tid; o < chi * Lr; o += NT) {
+      const int q = o % Lr, cp = o / Lr;
+      T v = 0;
+      if (cp < nkeep) {
+        const int p = w.sel[cp];
+        const T s = w.sig[p];
+        if (s > T(0)) v = X[(size_t)p * Lr + q] / s;
+      }
+      Vt[o] = v;
+    }
+    __syncthreads();
+    // C_{k-1}[j][c'] = sum_q Y[j][q] Vt[c'][q];  new site B[c'][d][c] = Vt[c'][(d,c)]
+    for (int o = tid; o < n * chi; o += NT) {
+      const int cp = o % chi, j = o / chi;
+      const T* Yr = Y + (size_t)j * Lr;
+      const T* Vr = Vt + (size_t)cp * Lr;
+      T s = 0;
+      for (int q = 0; q < Lr; ++q) s += Yr[q] * Vr[q];
+      Cn[o] = s;
+    }
+    for (int o = tid; o < g.se; o += NT) Bs[o] = Vt[o];  // layouts coincide: [c'][d][c]
+    __syncthreads();
+    logsum += blk_normalize(Bs, g.se, w.red, st);
+    blk_copy(Eout + (size_t)k * g.se, Bs, g.se);
+    blk_copy(w.C, Cn, n * chi);
+    __syncthreads();
+  }
+  return logsum;
+}
+
+// First environment row: row 0 read as an MPS (upper side, e[a=l][p=d][b=r] = A[l][0][r][d])
+// or row Lx-1 (lower side, e[l][u][r] = A[l][u][r][0]); every site normalised.
+template <typename T>
+__device__ double env_first_row(const Geo& g, T* Eout, const T* Tpad, int row, const uint8_t* Srow,
+                                bool lower, T* Abuf, T* Bs, double* red, int* st) {
+  const int chi = g.chi, D = g.D;
+  double logsum = 0.0;
+  for (int k = 0; k < g.Ly; ++k) {
+    load_A(Abuf, Tpad, g, row * g.Ly + k, Srow[k], lower);
+    __syncthreads();
+    for (int o = threadIdx.x; o < g.se; o += blockDim.x) {
+      const int b = o % chi, p = (o / chi) % D, a = o / (chi * D);
+      // with the lower orientation Abuf[l][d][r][u]: its "u" slot (index 1) holds the down leg
+      Bs[o] = (a < D && b < D) ? Abuf[((a * D + 0) * D + b) * D + p] : T(0);
+    }
+    __syncthreads();
+    logsum += blk_normalize(Bs, g.se, red, st);
+    blk_copy(Eout + (size_t)k * g.se, Bs, g.se);
+    __syncthreads();
+  }
+  return logsum;
+}
+
+// ------------------------------------------------------------------------------------------
+// One-row sandwich partials.  L[a][l][b] -> L'[x][r][z] over one column with eu[a][u][x],
+// A[l][u][r][d], el[b][d][z].  t1, t2: chi*chi*D*D each.
+template <typename T>
+__device__ void absorb1(const Geo& g, const T* L, const T* eu, const T* A, const T* el, T* t1, T* t2, T* out) {
+  const int chi = g.chi, D = g.D, NT = blockDim.x, tid = threadIdx.x;
+  const int n1 = D * chi * D * chi;
+  // t1[l][b][u][x] = sum_a L[a][l][b] eu[a][u][x]
+  for (int o = tid; o < n1; o += NT) {
+    const int x = o % chi, u = (o / chi) % D, b = (o / (chi * D)) % chi, l = o / (chi * D * chi);
+    T s = 0;
+    for (int a = 0; a < chi; ++a) s += L[(a * D + l) * chi + b] * eu[(a * D + u) * chi + x];
+    t1[o] = s;
+  }
+  __syncthreads();
+  // t2[b][x][r][d] = sum_{l,u} t1[l][b][u][x] A[l][u][r][d]
+  for (int o = tid; o < n1; o += NT) {
+    const int dd = o % D, r = (o / D) % D, x = (o / (D * D)) % chi, b = o / (D * D * chi);
+    T s = 0;
+    for (int l = 0; l < D; ++l)
+      for (int u = 0; u < D; ++u) s += t1[((l * chi + b) * D + u) * chi + x] * A[((l * D + u) * D + r) * D + dd];
+    t2[o] = s;
+  }
+  __syncthreads();
+  // out[x][r][z] = sum_{b,d} t2[b][x][r][d] el[b][d][z]
+  for (int o = tid; o < g.se; o += NT) {
+    const int z = o % chi, r = (o / chi) % D, x = o / (chi * D);
+    T s = 0;
+    for (int b = 0; b < chi; ++b)
+      for (int dd = 0; dd < D; ++dd) s += t2[((b * chi + x) * D + r) * D + dd] * el[(b * D + dd) * chi + z];
+    out[o] = s;
+  }
+  __syncthreads();
+}
+
+// R[x][r][z] -> R'[a][l][b] = sum eu[a][u][x] A[l][u][r][d] el[b][d][z] R[x][r][z]
+template <typename T>
+__device__ void absorb1_right(const Geo& g, const T* R, const T* eu, const T* A, const T* el, T* t1, T* t2, T* out) {
+  const int chi = g.chi, D = g.D, NT = blockDim.x, tid = threadIdx.x;
+  const int n1 = chi * D * D * chi;
+  // t1[a][u][r][z] = sum_x eu[a][u][x] R[x][r][z]
+  for (int o = tid; o < n1; o += NT) {
+    const int z = o % chi, r = (o / chi) % D, u = (o / (chi * D)) % D, a = o / (chi * D * D);
+    T s = 0;
+    for (int x = 0; x < chi; ++x) s += eu[(a * D + u) * chi + x] * R[(x * D + r) * chi + z];
+    t1[o] = s;
+  }
+  __syncthreads();
+  // t2[a][l][z][d] = sum_{u,r} t1[a][u][r][z] A[l][u][r][d]
+  for (int o = tid; o < n1; o += NT) {
+    const int dd = o % D, z = (o / D) % chi, l = (o / (D * chi)) % D, a = o / (D * chi * D);
+    T s = 0;
+    for (int u = 0; u < D; ++u)
+      for (int r = 0; r < D; ++r) s += t1[((a * D + u) * D + r) * chi + z] * A[((l * D + u) * D + r) * D + dd];
+    t2[o] = s;
+  }
+  __syncthreads();
+  // out[a][l][b] = sum_{z,d} t2[a][l][z][d] el[b][d][z]
+  for (int o = tid; o < g.se; o += NT) {
+    const int b = o % chi, l = (o / chi) % D, a = o / (chi * D);
+    T s = 0;
+    for (int z = 0; z < chi; ++z)
+      for (int dd = 0; dd < D; ++dd) s += t2[((a * D + l) * chi + z) * D + dd] * el[(b * D + dd) * chi + z];
+    out[o] = s;
+  }
+  __syncthreads();
+}
+
+// Site environment of the one-row sandwich: env[l][u][r][d] = sum L[a][l][b] eu[a][u][x]
+// el[b][d][z] R[x][r][z]  (= d psi_x / d A[l][u][r][d]).
+template <typename T>
+__device__ void site_env1(const Geo& g, const T* L, const T* eu, const T* el, const T* R, T* t1, T* t2, T* env) {
+  const int chi = g.chi, D = g.D, NT = blockDim.x, tid = threadIdx.x;
+  const int n1 = D * chi * D * chi;
+  // t1[l][b][u][x] = sum_a L[a][l][b] eu[a][u][x]
+  for (int o = tid; o < n1; o += NT) {
+    const int x = o % chi, u = (o / chi) % D, b = (o / (chi * D)) % chi, l = o / (chi * D * chi);
+    T s = 0;
+    for (int a = 0; a < chi; ++a) s += L[(a * D + l) * chi + b] * eu[(a * D + u) * chi + x];
+    t1[o] = s;
+  }
+  // t4[x][r][b][d] = sum_z R[x][r][z] el[b][d][z]
+  for (int o = tid; o < n1; o += NT) {
+    const int dd = o % D, b = (o / D) % chi, r = (o / (D * chi)) % D, x = o / (D * chi * D);
+    T s = 0;
+    for (int z = 0; z < chi; ++z) s += R[(x * D + r) * chi + z] * el[(b * D + dd) * chi + z];
+    t2[o] = s;
+  }
+  __syncthreads();
+  // env[l][u][r][d] = sum_{b,x} t1[l][b][u][x] t4[x][r][b][d]
+  for (int o = tid; o < g.sT; o += NT) {
+    const int dd = o % D, r = (o / D) % D, u = (o / (D * D)) % D, l = o / (D * D * D);
+    T s = 0;
+    for (int b = 0; b < chi; ++b)
+      for (int x = 0; x < chi; ++x) s += t1[((l * chi + b) * D + u) * chi + x] * t2[((x * D + r) * chi + b) * D + dd];
+    env[o] = s;
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__device__ T blk_dot(const T* a, const T* b, int n, double* red) {
+  T s = 0;
+  for (int o = threadIdx.x; o < n; o += blockDim.x) s += a[o] * b[o];
+  return block_sum(s, red);
+}
+
+// ------------------------------------------------------------------------------------------
+// Two-row sandwich partials, chunked over the new upper bond (absorb2) / the old upper bond
+// (absorb2_right) so that the temporaries hold D^3 chi cx elements.
+// L2[a][i][j][b] -> out[x][r1][r2][z] with eu[a][u][x], A1[i][u][r1][v], A2[j][v][r2][d], el[b][d][z]
+template <typename T>
+__device__ void absorb2(const Geo& g, const T* L2, const T* eu, const T* A1, const T* A2, const T* el,
+                        T* t1, T* t2, T* out, int cx) {
+  const int chi = g.chi, D = g.D, NT = blockDim.x, tid = threadIdx.x;
+  for (int x0 = 0; x0 < chi; x0 += cx) {
+    const int c = (chi - x0 < cx) ? chi - x0 : cx;
+    const int nt = D * D * chi * D * c;
+    // t1[i][j][b][u][xx] = sum_a L2[a][i][j][b] eu[a][u][x0+xx]
+    for (int o = tid; o < nt; o += NT) {
+      const int xx = o % c, u = (o / c) % D, b = (o / (c * D)) % chi, j = (o / (c * D * chi)) % D,
+                i = o / (c * D * chi * D);
+      T s = 0;
+      for (int a = 0; a < chi; ++a) s += L2[((a * D + i) * D + j) * chi + b] * eu[(a * D + u) * chi + x0 + xx];
+      t1[o] = s;
+    }
+    __syncthreads();
+    // t2[j][b][xx][r1][v] = sum_{i,u} t1[i][j][b][u][xx] A1[i][u][r1][v]
+    for (int o = tid; o < nt; o += NT) {
+      const int v = o % D, r1 = (o / D) % D, xx = (o / (D * D)) % c, b = (o / (D * D * c)) % chi,
+                j = o / (D * D * c * chi);
+      T s = 0;
+      for (int i = 0; i < D; ++i)
+        for (int u = 0; u < D; ++u)
+          s += t1[(((i * D + j) * chi + b) * D + u) * c + xx] * A1[((i * D + u) * D + r1) * D + v];
+      t2[o] = s;
+    }
+    __syncthreads();
+    // t3[b][xx][r1][r2][d] = sum_{j,v} t2[j][b][xx][r1][v] A2[j][v][r2][d]   (into t1)
+    for (int o = tid; o < nt; o += NT) {
+      const int dd = o % D, r2 = (o / D) % D, r1 = (o / (D * D)) % D, xx = (o / (D * D * D)) % c,
+                b = o / (D * D * D * c);
+      T s = 0;
+      for (int j = 0; j < D; ++j)
+        for (int v = 0; v < D; ++v)
+          s += t2[(((j * chi + b) * c + xx) * D + r1) * D + v] * A2[((j * D + v) * D + r2) * D + dd];
+      t1[o] = s;
+    }
+    __syncthreads();
+    // out[x0+xx][r1][r2][z] = sum_{b,d} t3[b][xx][r1][r2][d] el[b][d][z]
+    const int no = c * D * D * chi;
+    for (int o = tid; o < no; o += NT) {
+      const int z = o % chi, r2 = (o / chi) % D, r1 = (o / (chi * D)) % D, xx = o / (chi * D * D);
+      T s = 0;
+      for (int b = 0; b < chi; ++b)
+        for (int dd = 0; dd < D; ++dd)
+          s += t1[(((b * c + xx) * D + r1) * D + r2) * D + dd] * el[(b * D + dd) * chi + z];
+      out[(((x0 + xx) * D + r1) * D + r2) * chi + z] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// R2[x][r1][r2][z] -> out[a][i][j][b] = sum eu[a][u][x] A1[i][u][r1][v] A2[j][v][r2][d] el[b][d][z] R2[x][r1][r2][z]
+template <typename T>
+__device__ void absorb2_right(const Geo& g, const T* R2, const T* eu, const T* A1, const T* A2, const T* el,
+                              T* t1, T* t2, T* out, int ca) {
+  const int chi = g.chi, D = g.D, NT = blockDim.x, tid = threadIdx.x;
+  for (int a0 = 0; a0 < chi; a0 += ca) {
+    const int c = (chi - a0 < ca) ? chi - a0 : ca;
+    const int nt = c * D * D * D * chi;
+    // t1[aa][u][r1][r2][z] = sum_x eu[a0+aa][u][x] R2[x][r1][r2][z]
+    for (int o = tid; o < nt; o += NT) {
+      const int z = o % chi, r2 = (o / chi) % D, r1 = (o / (chi * D)) % D, u = (o / (chi * D * D)) % D,
+                aa = o / (chi * D * D * D);
+      T s = 0;
+      for (int x = 0; x < chi; ++x) s += eu[((a0 + aa) * D + u) * chi + x] * R2[((x * D + r1) * D + r2) * chi + z];
+      t1[o] = s;
+    }
+    __syncthreads();
+    // t2[aa][i][v][r2][z] = sum_{u,r1} t1[aa][u][r1][r2][z] A1[i][u][r1][v]
+    for (int o = tid; o < nt; o += NT) {
+      const int z = o % chi, r2 = (o / chi) % D, v = (o / (chi * D)) % D, i = (o / (chi * D * D)) % D,
+                aa = o / (chi * D * D * D);
+      T s = 0;
+      for (int u = 0; u < D; ++u)
+        for (int r1 = 0; r1 < D; ++r1)
+          s += t1[(((aa * D + u) * D + r1) * D + r2) * chi + z] * A1[((i * D + u) * D + r1) * D + v];
+      t2[o] = s;
+    }
+    __syncthreads();
+    // t3[aa][i][j][z][d] = sum_{v,r2} t2[aa][i][v][r2][z] A2[j][v][r2][d]   (into t1)
+    for (int o = tid; o < nt; o += NT) {
+      const int dd = o % D, z = (o / D) % chi, j = (o / (D * chi)) % D, i = (o / (D * chi * D)) % D,
+                aa = o / (D * chi * D * D);
+      T s = 0;
+      for (int v = 0; v < D; ++v)
+        for (int r2 = 0; r2 < D; ++r2)
+          s += t2[(((aa * D + i) * D + v) * D + r2) * chi + z] * A2[((j * D + v) * D + r2) * D + dd];
+      t1[o] = s;
+    }
+    __syncthreads();
+    // out[a0+aa][i][j][b] = sum_{z,d} t3[aa][i][j][z][d] el[b][d][z]
+    const int no = c * D * D * chi;
+    for (int o = tid; o < no; o += NT) {
+      const int b = o % chi, j = (o / chi) % D, i = (o / (chi * D)) % D, aa = o / (chi * D * D);
+      T s = 0;
+      for (int z = 0; z < chi; ++z)
+        for (int dd = 0; dd < D; ++dd)
+          s += t1[(((aa * D + i) * D + j) * chi + z) * D + dd] * el[(b * D + dd) * chi + z];
+      out[(((a0 + aa) * D + i) * D + j) * chi + b] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11), device side, from the published definition.
+struct Philox4 { uint32_t v[4]; };
+
+__device__ __forceinline__ Philox4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                                 uint32_t k0, uint32_t k1) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) { k0 += W0; k1 += W1; }
+    const uint32_t hi0 = __umulhi(M0, c0), lo0 = M0 * c0;
+    const uint32_t hi1 = __umulhi(M1, c2), lo1 = M1 * c2;
+    const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+  }
+  Philox4 o;
+  o.v[0] = c0; o.v[1] = c1; o.v[2] = c2; o.v[3] = c3;
+  return o;
+}
+
+// 53-bit uniform double in [0, 1) from the first two output words.
+__device__ __forceinline__ double uniform53(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint64_t seed) {
+  const Philox4 o = philox4x32_10(c0, c1, c2, c3, (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32));
+  return ((double)(o.v[0] >> 5) * 67108864.0 + (double)(o.v[1] >> 6)) * (1.0 / 9007199254740992.0);
+}
+
+}  // namespace peps

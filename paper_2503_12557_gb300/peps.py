@@ -1,0 +1,225 @@
+"""Thin ctypes binding over the C ABI in include/peps_gb300.h (argument marshalling only).
+
+Device buffers are torch CUDA tensors; every call is enqueued on torch's current CUDA stream.
+The shared library is loaded on first use from the package's _lib folder (built by
+``paper_2503_12557_gb300.build``); a missing library raises instead of falling back to anything.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+_LIB = None
+_LIBPATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libpeps_gb300.so")
+
+PREC_FP64, PREC_FP32 = 0, 1
+MOVE_EXCHANGE, MOVE_FLIP = 0, 1
+ST_NEAR_DEGENERATE, ST_ZERO_NORM, ST_NONFINITE, ST_NOCONV = 1, 2, 4, 8
+
+_ERRORS = {-1: "PEPS_E_ARG", -2: "PEPS_E_SHAPE", -3: "PEPS_E_WORKSPACE", -4: "PEPS_E_CUDA", -5: "PEPS_E_UNSUPPORTED"}
+
+
+class _Config(C.Structure):
+    _fields_ = [("Lx", C.c_int), ("Ly", C.c_int), ("d", C.c_int), ("D", C.c_int), ("chi", C.c_int),
+                ("prec", C.c_int), ("max_samples", C.c_int)]
+
+
+class _Term(C.Structure):
+    _fields_ = [("nsites", C.c_int), ("sites", C.c_int * 4), ("h_host", C.POINTER(C.c_double))]
+
+
+class _Ham(C.Structure):
+    _fields_ = [("nterms", C.c_int), ("terms", C.POINTER(_Term)), ("npairs", C.c_int),
+                ("pair_ij_host", C.POINTER(C.c_int)), ("pair_v_host", C.POINTER(C.c_double)),
+                ("onsite_host", C.POINTER(C.c_double))]
+
+
+def lib_path() -> str:
+    return _LIBPATH
+
+
+def load():
+    """Load the CUDA library (raises RuntimeError when it has not been built)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(_LIBPATH):
+        raise RuntimeError(f"CUDA library not built: {_LIBPATH} (run python -m paper_2503_12557_gb300.build)")
+    L = C.CDLL(_LIBPATH)
+    vp, i32, i64, dbl = C.c_void_p, C.c_int, C.c_longlong, C.c_double
+    sig = {
+        "peps_create": ([C.POINTER(vp), C.POINTER(_Config)], i32),
+        "peps_destroy": ([vp], i32),
+        "peps_num_params": ([vp], i64),
+        "peps_set_params": ([vp, vp, vp], i32),
+        "peps_amplitudes": ([vp, vp, i32, vp, vp, vp, vp], i32),
+        "peps_local_energy": ([vp, C.POINTER(_Ham), vp, i32, vp, vp, vp], i32),
+        "peps_logderiv": ([vp, vp, i32, vp, vp, vp], i32),
+        "peps_evaluate": ([vp, C.POINTER(_Ham), vp, i32, vp, vp, vp, vp, vp, vp], i32),
+        "minsr_step": ([vp, vp, vp, vp, i32, dbl, dbl, dbl, vp, vp, vp], i32),
+        "peps_sample": ([vp, i32, vp, i32, i32, C.c_uint64, C.c_uint64, vp, vp, vp], i32),
+        "peps_last_error": ([vp], C.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _LIB = L
+    return L
+
+
+def exported_symbols():
+    return ["peps_create", "peps_destroy", "peps_num_params", "peps_set_params", "peps_amplitudes",
+            "peps_local_energy", "peps_logderiv", "peps_evaluate", "minsr_step", "peps_sample", "peps_last_error"]
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Hamiltonian:
+    """ctypes view of a Hamiltonian dict from ``paper_2503_12557_gb300.inputs`` (host memory)."""
+
+    def __init__(self, H, nsites: int, d: int):
+        terms = H["terms"]
+        self._h = [np.ascontiguousarray(np.stack([np.asarray(h).real, np.asarray(h).imag], -1).ravel(),
+                                        dtype=np.float64) for _, h in terms]
+        self._terms = (_Term * max(1, len(terms)))()
+        for i, (sites, _) in enumerate(terms):
+            self._terms[i].nsites = len(sites)
+            for j in range(4):
+                self._terms[i].sites[j] = int(sites[j]) if j < len(sites) else -1
+            self._terms[i].h_host = self._h[i].ctypes.data_as(C.POINTER(C.c_double))
+        pairs = H.get("pairs", [])
+        self._pij = np.ascontiguousarray(np.array([[i, j] for i, j, _ in pairs], dtype=np.int32).reshape(-1))
+        self._pv = np.ascontiguousarray(np.array([v for _, _, v in pairs], dtype=np.float64))
+        on = H.get("onsite")
+        self._on = None if on is None else np.ascontiguousarray(np.asarray(on, dtype=np.float64).reshape(nsites, d))
+        self.c = _Ham()
+        self.c.nterms = len(terms)
+        self.c.terms = self._terms
+        self.c.npairs = len(pairs)
+        self.c.pair_ij_host = self._pij.ctypes.data_as(C.POINTER(C.c_int)) if len(pairs) else None
+        self.c.pair_v_host = self._pv.ctypes.data_as(C.POINTER(C.c_double)) if len(pairs) else None
+        self.c.onsite_host = self._on.ctypes.data_as(C.POINTER(C.c_double)) if self._on is not None else None
+
+
+class PEPS:
+    """One handle of the C library: a lattice, chi and a precision."""
+
+    def __init__(self, Lx, Ly, d, D, chi, prec=PREC_FP64, max_samples=4096):
+        self.L = load()
+        self.Lx, self.Ly, self.d, self.D, self.chi, self.prec = Lx, Ly, d, D, chi, prec
+        self.max_samples = max_samples
+        cfg = _Config(Lx, Ly, d, D, chi, prec, max_samples)
+        h = C.c_void_p()
+        st = self.L.peps_create(C.byref(h), C.byref(cfg))
+        if st != 0:
+            raise RuntimeError(f"peps_create failed: {_ERRORS.get(st, st)}")
+        self.h = h
+        self.Np = int(self.L.peps_num_params(h))
+        self._ham_cache = {}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.peps_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, what):
+        if st != 0:
+            msg = self.L.peps_last_error(self.h)
+            raise RuntimeError(f"{what} failed: {_ERRORS.get(st, st)}: {msg.decode() if msg else ''}")
+
+    @property
+    def odtype(self):
+        return torch.float64 if self.prec == PREC_FP64 else torch.float32
+
+    def set_params(self, theta: torch.Tensor):
+        assert theta.is_cuda and theta.dtype == torch.float64 and theta.numel() == self.Np
+        theta = theta.contiguous()
+        self._check(self.L.peps_set_params(self.h, _ptr(theta), _stream()), "peps_set_params")
+        self._theta_ref = theta
+
+    def hamiltonian(self, H):
+        key = id(H)
+        if key not in self._ham_cache:
+            self._ham_cache[key] = (H, Hamiltonian(H, self.Lx * self.Ly, self.d))
+        return self._ham_cache[key][1]
+
+    def _S(self, S):
+        assert S.is_cuda and S.dtype == torch.uint8 and S.dim() == 2 and S.shape[1] == self.Lx * self.Ly
+        return S.contiguous()
+
+    def amplitudes(self, S):
+        S = self._S(S)
+        ns = S.shape[0]
+        la = torch.empty(ns, dtype=torch.float64, device=S.device)
+        ph = torch.empty_like(la)
+        st = torch.empty(ns, dtype=torch.int32, device=S.device)
+        self._check(self.L.peps_amplitudes(self.h, _ptr(S), ns, _ptr(la), _ptr(ph), _ptr(st), _stream()),
+                    "peps_amplitudes")
+        return la, ph, st
+
+    def local_energy(self, H, S):
+        S = self._S(S)
+        ns = S.shape[0]
+        e = torch.empty(ns, 2, dtype=torch.float64, device=S.device)
+        st = torch.empty(ns, dtype=torch.int32, device=S.device)
+        hc = self.hamiltonian(H)
+        self._check(self.L.peps_local_energy(self.h, C.byref(hc.c), _ptr(S), ns, _ptr(e), _ptr(st), _stream()),
+                    "peps_local_energy")
+        return e, st
+
+    def logderiv(self, S, out=None):
+        S = self._S(S)
+        ns = S.shape[0]
+        O = out if out is not None else torch.empty(ns, self.Np, dtype=self.odtype, device=S.device)
+        st = torch.empty(ns, dtype=torch.int32, device=S.device)
+        self._check(self.L.peps_logderiv(self.h, _ptr(S), ns, _ptr(O), _ptr(st), _stream()), "peps_logderiv")
+        return O, st
+
+    def evaluate(self, H, S, want_logpsi=True, want_eloc=True, want_O=True, O_out=None):
+        S = self._S(S)
+        ns = S.shape[0]
+        dev = S.device
+        la = torch.empty(ns, dtype=torch.float64, device=dev) if want_logpsi else None
+        ph = torch.empty(ns, dtype=torch.float64, device=dev) if want_logpsi else None
+        e = torch.empty(ns, 2, dtype=torch.float64, device=dev) if want_eloc else None
+        O = (O_out if O_out is not None else torch.empty(ns, self.Np, dtype=self.odtype, device=dev)) if want_O else None
+        st = torch.empty(ns, dtype=torch.int32, device=dev)
+        hc = self.hamiltonian(H) if H is not None else None
+        self._check(self.L.peps_evaluate(self.h, C.byref(hc.c) if hc else None, _ptr(S), ns, _ptr(la), _ptr(ph),
+                                         _ptr(e), _ptr(O), _ptr(st), _stream()), "peps_evaluate")
+        return dict(logabs=la, phase=ph, eloc=e, O=O, status=st)
+
+    def minsr_step(self, O, eloc, w=None, lam=1e-4, rcond=0.0, tau=0.05):
+        ns = O.shape[0]
+        assert O.dtype == self.odtype and O.shape[1] == self.Np and eloc.shape == (ns, 2)
+        dth = torch.empty(self.Np, dtype=torch.float64, device=O.device)
+        info = torch.zeros(4, dtype=torch.float64, device=O.device)
+        self._check(self.L.minsr_step(self.h, _ptr(O.contiguous()), _ptr(eloc.contiguous()),
+                                      _ptr(w.contiguous()) if w is not None else None, ns, float(lam), float(rcond),
+                                      float(tau), _ptr(dth), _ptr(info), _stream()), "minsr_step")
+        return dth, info
+
+    def sample(self, S, move=MOVE_EXCHANGE, nsweeps=1, seed=0, sweep0=0, accepted=None):
+        S = self._S(S)
+        ns = S.shape[0]
+        acc = accepted if accepted is not None else torch.zeros(ns, dtype=torch.int64, device=S.device)
+        st = torch.empty(ns, dtype=torch.int32, device=S.device)
+        self._check(self.L.peps_sample(self.h, int(move), _ptr(S), ns, int(nsweeps), int(seed) & (2 ** 64 - 1),
+                                       int(sweep0), _ptr(acc), _ptr(st), _stream()), "peps_sample")
+        return S, acc, st

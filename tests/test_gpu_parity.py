@@ -1,0 +1,220 @@
+"""GPU path (through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+Tolerances (FP64 kernels): |d ln|psi|| <= 1e-10 (relative 1e-10 on psi), |d E_loc| <= 1e-10 max(1, |E|),
+O rows to 1e-10 of their largest entry, MinSR dtheta to 1e-10 in relative 2-norm.  Samples whose
+truncation hit a near-degenerate cut (status bit 1, same rule on both sides) are excluded from
+the element-wise gate and counted.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2503_12557_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2503_12557_gb300 import build, peps
+    build.build()
+    return peps
+
+
+def _oracle_eval(th, S, lat, chi, H, want_O=True):
+    from oracle import energy
+    return energy.evaluate(th, S, lat, chi, H=H, want_O=want_O)
+
+
+def _dev(x, dtype=None):
+    t = torch.as_tensor(np.ascontiguousarray(x))
+    return t.to("cuda", dtype=dtype) if dtype else t.cuda()
+
+
+def _handle(P, lat, chi, ns, prec=0):
+    return P.PEPS(lat.Lx, lat.Ly, lat.d, lat.D, chi, prec=prec, max_samples=max(ns, 1))
+
+
+def _compare_eval(P, lat, chi, th, S, H, check_O=True, tol=TOL):
+    ns = len(S)
+    h = _handle(P, lat, chi, ns)
+    h.set_params(_dev(th))
+    Sd = _dev(S)
+    res = h.evaluate(H, Sd, want_O=check_O)
+    torch.cuda.synchronize()
+    ref = _oracle_eval(th, S, lat, chi, H, want_O=check_O)
+    la = res["logabs"].cpu().numpy()
+    ph = res["phase"].cpu().numpy()
+    el = res["eloc"].cpu().numpy()
+    st = res["status"].cpu().numpy()
+    ok = (st & 1) == 0
+    assert np.array_equal(st & 6, np.zeros_like(st)), st  # no zero-norm / non-finite
+    assert np.array_equal((st & 1) != 0, (ref["status"] & 1) != 0)
+    assert ok.sum() >= max(1, int(0.8 * ns))
+    assert np.max(np.abs(la - ref["logabs"])[ok]) <= tol
+    assert np.all(np.cos(ph - ref["phase"])[ok] > 0.999)
+    de = np.abs(el[:, 0] + 1j * el[:, 1] - ref["eloc"]) / np.maximum(1.0, np.abs(ref["eloc"]))
+    assert np.max(de[ok]) <= tol, np.max(de)
+    if check_O:
+        O = res["O"].cpu().numpy()
+        Or = ref["O"].real
+        scale = np.maximum(1.0, np.max(np.abs(Or), axis=1))
+        dO = np.max(np.abs(O - Or), axis=1) / scale
+        assert np.max(dO[ok]) <= tol, np.max(dO)
+    return h, res
+
+
+def test_heisenberg_4x4_exact_chi_vs_oracle_and_bruteforce(P):
+    # 4x4 open Heisenberg, D=2, chi=4 (exact), 256 uniform Sz=0 configurations
+    w = I.WORKLOADS["heis4x4_D2_chi4"]
+    lat = I.Lattice(w["Lx"], w["Ly"], w["d"], w["D"])
+    th = I.peps_random(lat, w["seed_theta"], **w["init"])
+    S = I.configs_uniform_sz0(lat, w["ns"], w["seed_S"])
+    H = I.heisenberg(lat)
+    h, res = _compare_eval(P, lat, w["chi"], th, S, H)
+    from oracle import exact
+    psi = exact.state_vector(th, lat)
+    idx = [exact.config_index(s, 2) for s in S]
+    la = res["logabs"].cpu().numpy()
+    assert np.max(np.abs(la - np.log(np.abs(psi[idx])))) < 1e-10
+    Hm = exact.hamiltonian_sparse(H, lat)
+    eloc_ex = exact.exact_local_energy(psi, Hm)[idx]
+    el = res["eloc"].cpu().numpy()[:, 0]
+    assert np.max(np.abs(el - eloc_ex.real) / np.maximum(1, np.abs(eloc_ex))) < 1e-10
+
+
+@pytest.mark.parametrize("Lx,Ly,D,chi,ns,seed", [
+    (5, 6, 3, 5, 24, 7),     # truncating, non-square, ragged tiles
+    (3, 7, 2, 3, 16, 8),
+    (6, 4, 3, 9, 12, 9),     # chi = D^2 (exact for Ly=4)
+])
+def test_truncated_heisenberg_vs_oracle(P, Lx, Ly, D, chi, ns, seed):
+    lat = I.Lattice(Lx, Ly, 2, D)
+    th = I.peps_random(lat, seed, scale=0.5, bias=1.0)
+    S = I.configs_uniform_sz0(lat, ns, seed + 1)
+    _compare_eval(P, lat, chi, th, S, I.heisenberg(lat))
+
+
+def test_j1j2_two_by_two_windows_vs_oracle(P):
+    # J1-J2 (no chiral term, real PEPS): diagonal bonds use two-row, two-column windows
+    lat = I.Lattice(4, 5, 2, 2)
+    th = I.peps_random(lat, 21, scale=0.5, bias=1.0)
+    S = I.configs_uniform(lat, 16, 3)
+    H = I.j1j2_chiral(lat, J1=1.0, J2=0.5, Jchi=0.0)
+    H["terms"] = [t for t in H["terms"] if len(t[0]) == 2]
+    _compare_eval(P, lat, 3, th, S, H)
+
+
+def test_rydberg_flips_and_long_range_vs_oracle(P):
+    lat = I.Lattice(5, 5, 2, 3)
+    th = I.peps_random(lat, 31, scale=0.5, bias=1.0)
+    S = I.configs_uniform(lat, 12, 5)
+    _compare_eval(P, lat, 6, th, S, I.rydberg(lat, delta=2.0))
+
+
+def test_heisenberg_8x8_D4_chi16_sampled_vs_oracle(P):
+    # the 8x8 D=4 chi=16 workload's shapes, on a handful of its configurations
+    w = I.WORKLOADS["heis8x8_D4_chi16"]
+    lat = I.Lattice(w["Lx"], w["Ly"], w["d"], w["D"])
+    th = I.peps_random(lat, w["seed_theta"], **w["init"])
+    S = I.configs_uniform_sz0(lat, 6, w["seed_S"])
+    _compare_eval(P, lat, w["chi"], th, S, I.heisenberg(lat))
+
+
+def test_fp32_handle_close_to_oracle(P):
+    lat = I.Lattice(6, 6, 2, 3)
+    th = I.peps_random(lat, 41, scale=0.5, bias=1.0)
+    S = I.configs_uniform_sz0(lat, 16, 42)
+    H = I.heisenberg(lat)
+    h = _handle(P, lat, 9, len(S), prec=1)
+    h.set_params(_dev(th))
+    res = h.evaluate(H, _dev(S))
+    torch.cuda.synchronize()
+    ref = _oracle_eval(th, S, lat, 9, H)
+    la = res["logabs"].cpu().numpy()
+    assert np.max(np.abs(la - ref["logabs"])) < 1e-4
+    el = res["eloc"].cpu().numpy()[:, 0]
+    assert np.max(np.abs(el - ref["eloc"].real)) / lat.nsites < 1e-4
+    assert res["O"].dtype == torch.float32
+
+
+def test_amplitudes_and_logderiv_entry_points(P):
+    lat = I.Lattice(4, 4, 2, 2)
+    th = I.peps_random(lat, 1001)
+    S = I.configs_uniform_sz0(lat, 8, 2001)
+    h = _handle(P, lat, 4, 8)
+    h.set_params(_dev(th))
+    la, ph, st = h.amplitudes(_dev(S))
+    O, st2 = h.logderiv(_dev(S))
+    e, st3 = h.local_energy(I.heisenberg(lat), _dev(S))
+    torch.cuda.synchronize()
+    ref = _oracle_eval(th, S, lat, 4, I.heisenberg(lat))
+    assert np.max(np.abs(la.cpu().numpy() - ref["logabs"])) < TOL
+    assert np.max(np.abs(O.cpu().numpy() - ref["O"].real)) < TOL * max(1, np.abs(ref["O"]).max())
+    assert np.max(np.abs(e.cpu().numpy()[:, 0] - ref["eloc"].real)) < TOL * max(1, np.abs(ref["eloc"]).max())
+
+
+def test_empty_batch_and_argument_errors(P):
+    lat = I.Lattice(3, 3, 2, 2)
+    h = _handle(P, lat, 4, 4)
+    h.set_params(_dev(I.peps_random(lat, 1)))
+    la, ph, st = h.amplitudes(torch.zeros(0, 9, dtype=torch.uint8, device="cuda"))
+    assert la.numel() == 0
+    with pytest.raises(RuntimeError, match="PEPS_E_SHAPE"):
+        h.amplitudes(torch.zeros(5, 9, dtype=torch.uint8, device="cuda"))
+    bad = {"terms": [((0, 8), np.eye(4))], "pairs": [], "onsite": np.zeros((9, 2))}  # spans 3 rows
+    with pytest.raises(RuntimeError, match="PEPS_E_UNSUPPORTED"):
+        h.local_energy(bad, torch.zeros(2, 9, dtype=torch.uint8, device="cuda"))
+    with pytest.raises(RuntimeError):
+        P.PEPS(3, 3, 2, 4, 2)  # chi < D
+
+
+def test_minsr_step_vs_oracle(P):
+    from oracle import minsr
+    w = I.WORKLOADS["heis4x4_D2_chi4"]
+    lat = I.Lattice(w["Lx"], w["Ly"], w["d"], w["D"])
+    th = I.peps_random(lat, w["seed_theta"], **w["init"])
+    S = I.configs_uniform_sz0(lat, w["ns"], w["seed_S"])
+    H = I.heisenberg(lat)
+    ref = _oracle_eval(th, S, lat, w["chi"], H)
+    Od = _dev(ref["O"].real)
+    ed = _dev(np.stack([ref["eloc"].real, np.zeros(len(S))], 1))
+    h = _handle(P, lat, w["chi"], len(S))
+    for lam, rc in ((w["lam"], 0.0), (0.0, 1e-8), (1e-3, 1e-10)):
+        dth, info = h.minsr_step(Od, ed, lam=lam, rcond=rc, tau=w["tau"])
+        d_ref, inf_ref = minsr.minsr(ref["O"].real, ref["eloc"].real, lam=lam, rcond=rc, tau=w["tau"])
+        d = dth.cpu().numpy()
+        assert np.linalg.norm(d - d_ref) <= 1e-9 * np.linalg.norm(d_ref), (lam, rc)
+        inf = info.cpu().numpy()
+        assert int(inf[0]) == inf_ref["rank"]
+        assert abs(inf[2] - inf_ref["lmax"]) <= 1e-10 * inf_ref["lmax"]
+    # weighted, odd Ns (padding path)
+    wts = np.random.default_rng(3).uniform(0.5, 2.0, 255)
+    dth, info = h.minsr_step(Od[:255].contiguous(), ed[:255].contiguous(), w=_dev(wts), lam=1e-3, rcond=0.0, tau=0.1)
+    d_ref, _ = minsr.minsr(ref["O"].real[:255], ref["eloc"].real[:255], w=wts, lam=1e-3, tau=0.1)
+    assert np.linalg.norm(dth.cpu().numpy() - d_ref) <= 1e-9 * np.linalg.norm(d_ref)
+
+
+@pytest.mark.parametrize("move,lat,chi,H", [
+    ("exchange", I.Lattice(4, 4, 2, 2), 3, "heis"),
+    ("flip", I.Lattice(4, 5, 2, 2), 3, "ryd"),
+])
+def test_sampler_chains_match_oracle(P, move, lat, chi, H):
+    from oracle import sampler
+    th = I.peps_random(lat, 51, scale=0.5, bias=1.0)
+    nc = 6
+    S0 = I.configs_neel(lat, nc) if move == "exchange" else I.configs_uniform(lat, nc, 4)
+    h = _handle(P, lat, chi, nc)
+    h.set_params(_dev(th))
+    Sd = _dev(S0)
+    mv = P.MOVE_EXCHANGE if move == "exchange" else P.MOVE_FLIP
+    Sd, acc, st = h.sample(Sd, move=mv, nsweeps=3, seed=1234, sweep0=5)
+    torch.cuda.synchronize()
+    Sref, acc_ref, _ = sampler.run_chains(th, S0, lat, chi, move, 1234, 3, sweep0=5)
+    assert np.array_equal(Sd.cpu().numpy(), Sref)
+    assert np.array_equal(acc.cpu().numpy(), acc_ref)
+    assert acc_ref.sum() > 0
