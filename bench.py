@@ -1,0 +1,320 @@
+"""Benchmark of the finite-PEPS hot path on the 8x8 open Heisenberg workload (D=4, chi=16,
+N_s=4096 Metropolis chains).
+
+One step = 2 Metropolis exchange sweeps of every chain + psi, E_loc and O of every chain
+(boundary MPS) + one MinSR step + the parameter update, all through the C ABI.
+value = samples/s = N_s (x ranks) / device time of one step.  The MinSR step time is reported
+beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fp32|fp64] [--ns NS]
+    python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
+
+Under torchrun (N > 1) every rank runs an independent replica of the workload (weak scaling,
+no collective on the data path); rank 0 prints the JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "samples/sec (psi, E_loc, O_k via boundary MPS) & MinSR step s, vs FP64 plain"
+WORKLOAD = "heis8x8_D4_chi16"
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--ns", type=int, default=None)
+    ap.add_argument("--sweeps", type=int, default=2)
+    ap.add_argument("--burnin", type=int, default=2)
+    ap.add_argument("--cpu-samples", type=int, default=12)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def _config(w, ns, prec, sweeps):
+    return {"workload": f"{w['Lx']}x{w['Ly']} open Heisenberg J=1, D={w['D']}, chi={w['chi']}, "
+                        f"N_s={ns} Metropolis exchange chains ({WORKLOAD})",
+            "Lx": w["Lx"], "Ly": w["Ly"], "D": w["D"], "chi": w["chi"], "ns": ns, "precision": prec,
+            "sweeps_per_step": sweeps, "minsr": {"lambda": w["lam"], "rcond": w["rcond"], "tau": w["tau"]},
+            "l2": "inputs larger than L2 (environment store and O exceed 129 MB)"}
+
+
+# --------------------------------------------------------------------------------- CPU oracle
+def _oracle_sample_run(nsamp, sweeps, seed_off=0):
+    """The oracle as it stands on `nsamp` chains of the workload: `sweeps` sweeps, then
+    psi / E_loc / O, then one MinSR step.  Returns seconds."""
+    from paper_2503_12557_gb300 import inputs as I
+    from oracle import energy, minsr, sampler
+    w = I.WORKLOADS[WORKLOAD]
+    lat = I.Lattice(w["Lx"], w["Ly"], w["d"], w["D"])
+    th = I.peps_random(lat, w["seed_theta"], **w["init"])
+    H = I.heisenberg(lat)
+    S0 = I.configs_neel(lat, nsamp)
+    t = time.perf_counter()
+    S, _, _ = sampler.run_chains(th, S0, lat, w["chi"], "exchange", w["seed_chain"], sweeps, sweep0=seed_off)
+    res = energy.evaluate(th, S, lat, w["chi"], H=H)
+    minsr.minsr(res["O"].real, res["eloc"].real, lam=w["lam"], rcond=w["rcond"], tau=w["tau"])
+    return time.perf_counter() - t
+
+
+def _cpu_subprocess(nsamp, sweeps, reps=1):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import sys, json; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps([bench._oracle_sample_run(%d, %d, k) for k in range(%d)]))" % (ROOT, nsamp, sweeps, reps))
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, check=True)
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline(nsamp, sweeps):
+    secs = _cpu_subprocess(nsamp, sweeps)[0]
+    return {"value": nsamp / secs, "unit": "samples/s", "cores": 1, "kind": "oracle",
+            "sample": f"{nsamp} of the workload's chains: {sweeps} sweeps + psi/E_loc/O + MinSR on them "
+                      f"({secs:.1f} s, one host core)"}
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2503_12557_gb300 import inputs as I
+    w = I.WORKLOADS[WORKLOAD]
+    ns = a.ns or w["ns"]
+    nsamp = a.cpu_samples
+    secs = _cpu_subprocess(nsamp, a.sweeps, reps=a.warmup + a.steps)[a.warmup:]
+    t = float(np.mean(secs))
+    v = nsamp / t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "samples/s", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": _config(w, ns, "fp64", a.sweeps),
+            "cpu_baseline": {"value": v, "unit": "samples/s", "cores": 1, "kind": "oracle",
+                             "sample": f"each step: {nsamp} chains of the workload ({a.sweeps} sweeps + psi/E_loc/O "
+                                       f"+ MinSR), one host core"},
+            "e2e": {"value": v, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------------- GPU
+class _Clocks:
+    def __init__(self, path):
+        self.path = path
+        self.p = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "200",
+                                       "-i", str(int(os.environ.get("LOCAL_RANK", "0")))],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.p is not None:
+            self.p.terminate()
+            self.p.wait()
+            self.f.close()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+                for name, val in zip(["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"], f[5:9]):
+                    if val.lower() == "active":
+                        reasons.add(name)
+        except Exception:
+            pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons)}
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def run_gpu(a):
+    import torch
+    import torch.distributed as dist
+    from paper_2503_12557_gb300 import build, costmodel, inputs as I, peps as P
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    lrank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(lrank)
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    w = I.WORKLOADS[WORKLOAD]
+    lat = I.Lattice(w["Lx"], w["Ly"], w["d"], w["D"])
+    ns = a.ns or w["ns"]
+    prec = P.PREC_FP32 if a.prec == "fp32" else P.PREC_FP64
+    H = I.heisenberg(lat)
+    theta0 = I.peps_random(lat, w["seed_theta"], **w["init"])
+    S0 = I.configs_neel(lat, ns)
+    h = P.PEPS(lat.Lx, lat.Ly, lat.d, lat.D, w["chi"], prec=prec, max_samples=ns)
+    theta = torch.as_tensor(theta0).cuda()
+    h.set_params(theta)
+    S = torch.as_tensor(S0).cuda()
+    acc = torch.zeros(ns, dtype=torch.int64, device="cuda")
+    O = torch.empty(ns, h.Np, dtype=h.odtype, device="cuda")
+    stream = torch.cuda.current_stream()
+    sweep_ctr = [0]
+    info_hist = []
+
+    def step(O_out=O):
+        h.sample(S, P.MOVE_EXCHANGE, a.sweeps, seed=w["seed_chain"] + 7919 * rank, sweep0=sweep_ctr[0], accepted=acc)
+        sweep_ctr[0] += a.sweeps
+        r = h.evaluate(H, S, O_out=O_out)
+        dth, info = h.minsr_step(r["O"], r["eloc"], lam=w["lam"], rcond=w["rcond"], tau=w["tau"])
+        h.apply_update(theta, dth)
+        info_hist.append(info)
+        return r, dth
+
+    # burn-in sweeps from the Neel start, untimed
+    h.sample(S, P.MOVE_EXCHANGE, a.burnin, seed=w["seed_chain"] + 7919 * rank, sweep0=0, accepted=acc)
+    sweep_ctr[0] = a.burnin
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    # ---- timed region (device events on the launching stream)
+    h.timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    eloc_means = []
+    with _Clocks(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv") if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
+                 else f"/tmp/clocks_rank{rank}.csv") as clk:
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(a.steps):
+            r, _ = step()
+            eloc_means.append(r["eloc"][:, 0].mean())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+    ms_total = e0.elapsed_time(e1)
+    ms_cls, launches, ctr = h.timing_read()
+    h.timing(False)
+    ms_step = ms_total / a.steps
+    if world > 1:
+        t = torch.tensor([ms_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = ns * world / (ms_step / 1e3)
+    minsr_s = (ms_cls["minsr_gram"] + ms_cls["minsr_eig"] + ms_cls["minsr_other"]) / a.steps / 1e3
+    # ---- roofline of the dominant kernel class
+    peaks = _peaks()
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12   # TFLOP/s, FP32 FMA pipes at the max SM clock
+    fp64_peak = 1.25                                     # TFLOP/s, nominal GB300 FP64
+    alu_peak = fp32_peak if prec == P.PREC_FP32 else fp64_peak
+    hwin, vwin = costmodel.heisenberg_windows(lat.Lx, lat.Ly, ns)
+    # the Jacobi counters mix the sampler's and the environment kernel's SVDs; split them by SVD count
+    svd_env = a.steps * ns * 2 * (lat.Lx - 2) * (lat.Ly - 1)
+    svd_all = max(1, ctr["svds"])
+    fe = min(1.0, svd_env / svd_all)
+    flops = {
+        "env": costmodel.env_flops(lat.Lx, lat.Ly, w["chi"], w["D"], ns * a.steps, 2, ctr["jacobi_sweeps"] * fe,
+                                   ctr["jacobi_rotations"] * fe),
+        "sample": costmodel.sample_flops(lat.Lx, lat.Ly, w["chi"], w["D"], ns, a.sweeps * a.steps,
+                                         ctr["jacobi_sweeps"] * (1 - fe), ctr["jacobi_rotations"] * (1 - fe)),
+        "row": costmodel.row_kernel_flops(lat.Lx, lat.Ly, w["chi"], w["D"], ns * a.steps, True, hwin * a.steps),
+        "pair": costmodel.pair_kernel_flops(lat.Lx, lat.Ly, w["chi"], w["D"], ns * a.steps, vwin * a.steps),
+        "minsr_gram": costmodel.gram_flops(ns, h.Np) * a.steps,
+    }
+    dom = max(flops, key=lambda k: ms_cls.get(k, 0.0))
+    dom_launch_ms = ms_cls[dom] / max(1, launches[dom])
+    achieved = flops[dom] / max(1, launches[dom]) / (dom_launch_ms / 1e3) / 1e12
+    peak = fp64_peak if dom == "minsr_gram" else alu_peak
+    roof = {"kernel": {"env": "k_env", "sample": "k_sample", "row": "k_row", "pair": "k_pair",
+                       "minsr_gram": "k_gram"}[dom],
+            "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None,
+            "peak_source": ("FP32 FMA pipes: 152 SMs x 128 lanes x 2 flop x max SM clock (derived)" if peak == fp32_peak
+                            else "GB300 nominal FP64 1.25 TFLOP/s"),
+            "algorithmic_tflop_per_launch": flops[dom] / max(1, launches[dom]) / 1e12,
+            "launch_ms": dom_launch_ms}
+    gpu_launches = int(sum(launches.values())) + 3 * a.steps  # + memsets inside evaluate / minsr
+    line = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if prec == P.PREC_FP32 else "f64", "data": "synthetic",
+            "config": _config(w, ns, a.prec, a.sweeps), "minsr_step_s": minsr_s,
+            "kernel_ms_per_step": {k: v / a.steps for k, v in ms_cls.items()},
+            "roofline": roof, "gpu_launches": gpu_launches, "clocks": clk.summary(),
+            "acceptance": float(acc.sum().item()) / max(1.0, ns * (sweep_ctr[0]) * (2 * lat.Lx * lat.Ly - lat.Lx - lat.Ly) * 0.5),
+            "eloc_mean_per_site": [float(x) / lat.nsites for x in eloc_means]}
+    # ---- end to end through the public API with host buffers
+    if not a.no_e2e:
+        th_host = torch.empty(h.Np, dtype=torch.float64).pin_memory()
+        th_host.copy_(theta.cpu())
+        S_host = torch.empty(ns, lat.nsites, dtype=torch.uint8).pin_memory()
+        S_host.copy_(S.cpu())
+        dth_host = torch.empty(h.Np, dtype=torch.float64).pin_memory()
+        el_host = torch.empty(ns, 2, dtype=torch.float64).pin_memory()
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(a.steps):
+            theta.copy_(th_host, non_blocking=True)
+            S.copy_(S_host, non_blocking=True)
+            h.set_params(theta)
+            r, dth = step()
+            dth_host.copy_(dth, non_blocking=True)
+            el_host.copy_(r["eloc"], non_blocking=True)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = f0.elapsed_time(f1) / a.steps
+        line["e2e"] = {"value": ns * world / (e2e_ms / 1e3), "unit": "samples/s",
+                       "h2d_bytes_per_step": h.Np * 8 + ns * lat.nsites,
+                       "d2h_bytes_per_step": h.Np * 8 + ns * 16}
+    if rank == 0 and not a.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(a.cpu_samples, a.sweeps)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    h.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_gpu(a)
+
+
+if __name__ == "__main__":
+    main()

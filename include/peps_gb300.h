@@ -143,11 +143,20 @@ peps_status peps_evaluate(peps_handle* h, const peps_hamiltonian* H, const uint8
  *   dtheta = -tau Obar^T V diag(kept / (Lambda + lambda)) V^T ebar.
  * O_dev: Ns x N_p in the handle's precision (as written by peps_logderiv); eloc_dev: Ns x 2
  * doubles (the real parts are used: real PEPS); dtheta_dev: N_p doubles (written);
- * info_dev: 4 doubles (rank kept, min Lambda, max Lambda, Jacobi sweeps used).
- * Needs lambda > 0 or rcond > 0.  The Gram matrix and the eigendecomposition are FP64. */
+ * info_dev: 4 doubles.  rcond > 0: eigendecomposition by cyclic Jacobi, info = (rank kept,
+ * min Lambda, max Lambda, Jacobi sweeps).  rcond == 0 (nothing cut, lambda > 0): the same
+ * operator (T + lambda)^-1 applied through a Cholesky factorisation, info = (Ns, NaN, NaN, -1),
+ * info[0] = -1 when T + lambda was not positive definite in floating point.
+ * Needs lambda > 0 or rcond > 0.  The Gram matrix and the solve are FP64.  The call
+ * synchronises the stream before it returns. */
 peps_status minsr_step(peps_handle* h, const void* O_dev, const double* eloc_dev, const double* w_dev,
                        int Ns, double lambda, double rcond, double tau, double* dtheta_dev,
                        double* info_dev, void* stream);
+
+/* theta_dev (N_p doubles, device, updated in place) += dtheta_dev, then the handle's kernel
+ * copy is refreshed as by peps_set_params (the parameter update that closes an optimisation
+ * step, paper Sec. "Reformulation of the imaginary-time Schroedinger equation"). */
+peps_status peps_apply_update(peps_handle* h, double* theta_dev, const double* dtheta_dev, void* stream);
 
 /* nsweeps Metropolis sweeps of Ns independent chains (configurations updated in place).
  * One sweep: bottom environments of the current S; then for x = 0..Lx-1 the moves inside row
@@ -160,6 +169,19 @@ peps_status minsr_step(peps_handle* h, const void* O_dev, const double* eloc_dev
 peps_status peps_sample(peps_handle* h, int move, uint8_t* S_dev, int Ns, int nsweeps,
                         uint64_t seed, uint64_t sweep0, long long* accepted_dev,
                         int32_t* status_dev, void* stream);
+
+/* Device timing of the library's own kernels, for profiling.  peps_timing_enable(h, 1) starts
+ * recording a CUDA event pair around every launch the handle makes (on the call's stream) and
+ * clears the record and the work counters; 0 stops recording.  peps_timing_read synchronises
+ * with the recorded events and writes, for each kernel class i < n, the summed milliseconds
+ * (ms_host[i]) and the kernel launches (launches_host[i]).  Classes: 0 environment pass,
+ * 1 one-row sandwiches, 2 two-row sandwiches, 3 per-sample combine, 4 Metropolis sweeps,
+ * 5 MinSR Gram matrix, 6 MinSR eigendecomposition, 7 MinSR centring / apply, 8 parameter copy.
+ * counters_host (4 values, may be NULL): one-sided Jacobi sweeps, Jacobi rotations, truncation
+ * SVDs performed since the last enable (the counted work behind the flop rates). */
+peps_status peps_timing_enable(peps_handle* h, int enable);
+peps_status peps_timing_read(peps_handle* h, double* ms_host, long long* launches_host, int n,
+                             long long* counters_host);
 
 /* Text of the last error seen by this handle (never NULL). */
 const char* peps_last_error(const peps_handle* h);

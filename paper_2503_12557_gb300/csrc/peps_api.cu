@@ -56,8 +56,42 @@ struct peps_handle {
   long long ms_np = 0;
   double *Obar = nullptr, *Tm = nullptr, *Vm = nullptr, *Hm = nullptr, *mean = nullptr, *ebar = nullptr,
          *yv = nullptr, *xv = nullptr, *cnt = nullptr;
+  // timing: event pairs per kernel class, recorded on the call's stream when enabled
+  bool timing = false;
+  std::vector<cudaEvent_t> evpool;
+  std::vector<int> evclass;
+  std::vector<long long> evlaunches;
+  size_t evn = 0;
+  unsigned long long* ctr = nullptr;  // device work counters (8)
   std::string err;
 };
+
+enum { TC_ENV = 0, TC_ROW, TC_PAIR, TC_COMBINE, TC_SAMPLE, TC_GRAM, TC_EIG, TC_MINSR, TC_PAD, TC_N };
+
+// Record a start event for kernel class c (returns the slot, or -1 when timing is off).
+static int tstart(peps_handle* h, int c, cudaStream_t s) {
+  if (!h->timing) return -1;
+  if (h->evn + 2 > h->evpool.size()) {
+    for (int i = 0; i < 64; ++i) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      h->evpool.push_back(e);
+    }
+    h->evclass.resize(h->evpool.size() / 2);
+    h->evlaunches.resize(h->evpool.size() / 2);
+  }
+  const int slot = (int)(h->evn / 2);
+  cudaEventRecord(h->evpool[h->evn], s);
+  h->evclass[slot] = c;
+  h->evlaunches[slot] = 1;
+  h->evn += 2;
+  return slot;
+}
+static void tstop(peps_handle* h, int slot, cudaStream_t s, long long launches = 1) {
+  if (slot < 0) return;
+  cudaEventRecord(h->evpool[2 * slot + 1], s);
+  h->evlaunches[slot] = launches;
+}
 
 static peps_status fail(peps_handle* h, peps_status st, const std::string& msg) {
   if (h) h->err = msg;
@@ -102,8 +136,9 @@ static void plan_all(peps_handle* h) {
   const int n = g.n, chi = g.chi, D = g.D, Ly = g.Ly;
   const int mX = n + (n & 1);
   const int Lr = D * chi;
-  const size_t budget = (E == 8) ? 200 * 1024 : 100 * 1024;
-  int ci = std::min(n, 16);
+  // FP64: one CTA per SM (the FP64 pipe is the limit); FP32: two CTAs per SM
+  const size_t budget = (E == 8) ? 210 * 1024 : 110 * 1024;
+  int ci = std::min(n, 8);
   const size_t zleft = (size_t)n * D * n;
   const size_t zright = (size_t)chi * D * D * chi + (size_t)n * Lr + (size_t)mX * Lr + (size_t)chi * Lr +
                         (size_t)n * chi + (size_t)chi * D * chi;
@@ -182,7 +217,13 @@ static peps_status finish_plans(peps_handle* h) {
     if (e != cudaSuccess) return fail(h, PEPS_E_WORKSPACE, "scratch allocation failed");
     h->gscratch_bytes = gmax;
   }
-  for (auto& k : h->kp) k.p.gbase = h->gscratch;
+  if (cudaMalloc(&h->ctr, 8 * sizeof(unsigned long long)) != cudaSuccess)
+    return fail(h, PEPS_E_WORKSPACE, "counter allocation failed");
+  cudaMemset(h->ctr, 0, 8 * sizeof(unsigned long long));
+  for (auto& k : h->kp) {
+    k.p.gbase = h->gscratch;
+    k.p.ctr = h->ctr;
+  }
   return PEPS_OK;
 }
 
@@ -246,9 +287,10 @@ extern "C" peps_status peps_destroy(peps_handle* h) {
   if (!h) return PEPS_E_ARG;
   void* ptrs[] = {h->Tpad, h->site_off, h->envs, h->logs, h->wdisc, h->rowout, h->pairout, h->status_tmp,
                   h->gscratch, h->d_tinfo, h->d_ab, h->d_eh, h->d_rowoff, h->d_pairoff, h->d_pij, h->d_pv,
-                  h->d_onsite, h->Obar, h->Tm, h->Vm, h->Hm, h->mean, h->ebar, h->yv, h->xv, h->cnt};
+                  h->d_onsite, h->Obar, h->Tm, h->Vm, h->Hm, h->mean, h->ebar, h->yv, h->xv, h->cnt, h->ctr};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  for (cudaEvent_t e : h->evpool) cudaEventDestroy(e);
   delete h;
   return PEPS_OK;
 }
@@ -260,9 +302,11 @@ extern "C" const char* peps_last_error(const peps_handle* h) { return (h && !h->
 extern "C" peps_status peps_set_params(peps_handle* h, const double* theta_dev, void* stream) {
   if (!h || !theta_dev) return fail(h, PEPS_E_ARG, "null argument");
   cudaStream_t s = (cudaStream_t)stream;
+  const int ts = tstart(h, TC_PAD, s);
   cudaError_t e = (h->esz == 8) ? launch_pad<double>(h->g, theta_dev, h->site_off, (double*)h->Tpad, s)
                                 : launch_pad<float>(h->g, theta_dev, h->site_off, (float*)h->Tpad, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "pad theta");
+  tstop(h, ts, s);
   return PEPS_OK;
 }
 
@@ -419,23 +463,31 @@ static peps_status run_eval(peps_handle* h, const peps_hamiltonian* H, const uin
     if (ps != PEPS_OK) return ps;
   }
   const KPlan& ke = h->kp[0];
+  int ts = tstart(h, TC_ENV, s);
   CK(launch_env<T>(g, ke.p, std::min(ke.grid, Ns * (sides == 3 ? 2 : 1)), ke.smem, (const T*)h->Tpad, S, Ns, sides,
                    (T*)h->envs, h->logs, st, h->wdisc, s), "env kernel");
+  tstop(h, ts, s);
   const KPlan& kr = h->kp[1];
   const bool all_rows = want_e || (O != nullptr);
   const int x_lo = all_rows ? 0 : g.Lx - 1;
+  ts = tstart(h, TC_ROW, s);
   CK(launch_row<T>(g, kr.p, std::min(kr.grid, Ns * (g.Lx - x_lo)), kr.smem, (const T*)h->Tpad, S, Ns, x_lo, g.Lx,
                    (const T*)h->envs, h->logs, (T*)O, h->site_off, h->Np, want_e ? h->tt : none, h->rowout, st, s),
      "row kernel");
+  tstop(h, ts, s);
   const bool pairs = want_e && h->n_pair_terms > 0;
   if (pairs) {
     const KPlan& kq = h->kp[2];
+    ts = tstart(h, TC_PAIR, s);
     CK(launch_pair<T>(g, kq.p, std::min(kq.grid, Ns * (g.Lx - 1)), kq.smem, (const T*)h->Tpad, S, Ns,
                       (const T*)h->envs, h->logs, h->tt, h->pairout, st, s), "pair kernel");
+    tstop(h, ts, s);
   }
   DiagTab dg = want_e ? h->dg : DiagTab{};
+  ts = tstart(h, TC_COMBINE, s);
   CK(launch_combine(g, Ns, S, h->rowout, h->pairout, want_e ? 1 : 0, pairs ? 1 : 0, dg, logabs, phase, eloc, s),
      "combine kernel");
+  tstop(h, ts, s);
   return PEPS_OK;
 }
 
@@ -489,12 +541,14 @@ extern "C" peps_status peps_sample(peps_handle* h, int move, uint8_t* S_dev, int
   if (Ns == 0 || nsweeps == 0) return PEPS_OK;
   const KPlan& k = h->kp[3];
   const int grid = std::min(k.grid, Ns);
+  const int ts = tstart(h, TC_SAMPLE, s);
   cudaError_t e = (h->esz == 8)
                       ? launch_sample<double>(h->g, k.p, grid, k.smem, (const double*)h->Tpad, S_dev, Ns, move, nsweeps,
                                               seed, sweep0, (double*)h->envs, h->logs, accepted_dev, st, s)
                       : launch_sample<float>(h->g, k.p, grid, k.smem, (const float*)h->Tpad, S_dev, Ns, move, nsweeps,
                                              seed, sweep0, (float*)h->envs, h->logs, accepted_dev, st, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "sampler kernel");
+  tstop(h, ts, s);
   return PEPS_OK;
 }
 
@@ -529,19 +583,77 @@ extern "C" peps_status minsr_step(peps_handle* h, const void* O_dev, const doubl
   cudaStream_t s = (cudaStream_t)stream;
   const int n = Ns + (Ns & 1);
   const long long Np = h->Np;
+  int ts = tstart(h, TC_MINSR, s);
   cudaError_t e = (h->esz == 8) ? launch_center<double>((const double*)O_dev, w_dev, Ns, Np, h->mean, h->Obar, s)
                                 : launch_center<float>((const float*)O_dev, w_dev, Ns, Np, h->mean, h->Obar, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "centre O");
   CK(cudaMemsetAsync(h->ebar, 0, sizeof(double) * n, s), "memset");
   CK(launch_center_e(eloc_dev, w_dev, Ns, h->ebar, s), "centre E_loc");
   CK(cudaMemsetAsync(h->Tm, 0, sizeof(double) * (size_t)n * n, s), "memset");
+  tstop(h, ts, s, w_dev ? 3 : 2);
+  ts = tstart(h, TC_GRAM, s);
   CK(launch_gram(h->Obar, Ns, Np, h->Tm, n, s), "Gram");
-  const int sweeps = jacobi_eig(h->Tm, h->Vm, n, h->cnt, nullptr, h->Hm, s, 40, &e);
-  if (e != cudaSuccess) return cuda_fail(h, e, "Jacobi");
-  CK(launch_minsr_apply(h->Tm, h->Vm, h->ebar, n, Ns, lambda, rcond, h->yv, h->xv, info_dev, s), "MinSR apply");
+  tstop(h, ts, s);
+  double sw = -1.0;
+  if (rcond > 0.0) {
+    // eigendecomposition with the pseudo-inverse cutoff
+    ts = tstart(h, TC_EIG, s);
+    const int sweeps = jacobi_eig(h->Tm, h->Vm, n, h->cnt, nullptr, h->Hm, s, 40, &e);
+    if (e != cudaSuccess) return cuda_fail(h, e, "Jacobi");
+    tstop(h, ts, s, 1 + (long long)(sweeps > 0 ? sweeps : 40) * (n - 1));
+    ts = tstart(h, TC_MINSR, s);
+    CK(launch_minsr_apply(h->Tm, h->Vm, h->ebar, n, Ns, lambda, rcond, h->yv, h->xv, info_dev, s), "MinSR apply");
+    tstop(h, ts, s, 3);
+    sw = (double)sweeps;
+  } else {
+    // nothing is cut: (T + lambda)^+ = (T + lambda)^-1, solved by Cholesky
+    ts = tstart(h, TC_EIG, s);
+    const long long nl = chol_solve(h->Tm, n, Ns, lambda, h->ebar, h->xv, (int*)h->cnt, info_dev, s, &e);
+    if (e != cudaSuccess) return cuda_fail(h, e, "Cholesky");
+    tstop(h, ts, s, nl);
+  }
+  ts = tstart(h, TC_MINSR, s);
   CK(launch_obar_t_x(h->Obar, h->xv, Ns, Np, tau, dtheta_dev, s), "Obar^T x");
-  const double sw = (double)sweeps;
+  tstop(h, ts, s, 1);
   CK(cudaMemcpyAsync(info_dev + 3, &sw, sizeof(double), cudaMemcpyHostToDevice, s), "info");
   CK(cudaStreamSynchronize(s), "MinSR sync");
   return PEPS_OK;
+}
+
+// ---- timing and work counters ----------------------------------------------------------
+extern "C" peps_status peps_timing_enable(peps_handle* h, int enable) {
+  if (!h) return PEPS_E_ARG;
+  h->timing = (enable != 0);
+  h->evn = 0;
+  if (h->ctr) CK(cudaMemset(h->ctr, 0, 8 * sizeof(unsigned long long)), "reset counters");
+  return PEPS_OK;
+}
+
+extern "C" peps_status peps_timing_read(peps_handle* h, double* ms_host, long long* launches_host, int n,
+                                        long long* counters_host) {
+  if (!h || n < 0 || (n > 0 && (!ms_host || !launches_host))) return PEPS_E_ARG;
+  for (int i = 0; i < n; ++i) { ms_host[i] = 0.0; launches_host[i] = 0; }
+  for (size_t k = 0; k < h->evn / 2; ++k) {
+    CK(cudaEventSynchronize(h->evpool[2 * k + 1]), "event sync");
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, h->evpool[2 * k], h->evpool[2 * k + 1]), "event time");
+    const int c = h->evclass[k];
+    if (c < n) { ms_host[c] += ms; launches_host[c] += h->evlaunches[k]; }
+  }
+  if (counters_host) {
+    unsigned long long c[8];
+    CK(cudaMemcpy(c, h->ctr, sizeof(c), cudaMemcpyDeviceToHost), "read counters");
+    for (int i = 0; i < 4; ++i) counters_host[i] = (long long)c[i];
+  }
+  return PEPS_OK;
+}
+
+// ---- parameter update --------------------------------------------------------------------
+extern "C" peps_status peps_apply_update(peps_handle* h, double* theta_dev, const double* dtheta_dev, void* stream) {
+  if (!h || !theta_dev || !dtheta_dev) return fail(h, PEPS_E_ARG, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int ts = tstart(h, TC_PAD, s);
+  CK(launch_axpy(theta_dev, dtheta_dev, h->Np, s), "theta update");
+  tstop(h, ts, s);
+  return peps_set_params(h, theta_dev, stream);
 }

@@ -27,6 +27,7 @@ __device__ RowWork<T> carve_row(const Plan& p, char* smem, char* gbase) {
   w.sel = (int*)buf_ptr(p, B_SEL, smem, gbase);
   w.red = (double*)buf_ptr(p, B_RED, smem, gbase);
   w.ci = p.ci;
+  w.ctr = p.ctr;
   return w;
 }
 

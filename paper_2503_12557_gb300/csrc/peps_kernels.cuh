@@ -70,5 +70,10 @@ cudaError_t launch_minsr_apply(const double* A, const double* V, const double* e
                                double rcond, double* y, double* x, double* info, cudaStream_t s);
 cudaError_t launch_obar_t_x(const double* Obar, const double* x, int Ns, long long Np, double tau, double* dtheta,
                             cudaStream_t s);
+// x = (A + lambda I)^-1 ebar by blocked Cholesky (A overwritten by its factor); returns launches
+long long chol_solve(double* A, int n, int nreal, double lambda, const double* ebar, double* x, int* bad,
+                     double* info, cudaStream_t s, cudaError_t* err);
+// y += x (n doubles)
+cudaError_t launch_axpy(double* y, const double* x, long long n, cudaStream_t s);
 
 }  // namespace peps

@@ -59,6 +59,7 @@ struct Plan {
   int ci;                          // row chunk of the left-pass W buffer
   int cx;                          // chunk of the two-row contractions
   char* gbase;                     // global arena (gstride bytes per CTA)
+  unsigned long long* ctr;         // work counters: [0] Jacobi sweeps, [1] rotations, [2] SVDs
 };
 
 __device__ __forceinline__ char* buf_ptr(const Plan& p, int b, char* smem, char* gbase) {
@@ -219,17 +220,45 @@ __device__ __forceinline__ int rr_player(int j, int r, int m) {
 }
 
 template <typename T> struct JacobiTol;
-template <> struct JacobiTol<double> { static constexpr double tol = 1e-15; static constexpr int sweeps = 40; };
-template <> struct JacobiTol<float> { static constexpr float tol = 2e-7f; static constexpr int sweeps = 30; };
+template <> struct JacobiTol<double> { static constexpr double eps = 1.1102230246251565e-16; static constexpr int sweeps = 30; };
+template <> struct JacobiTol<float> { static constexpr float eps = 5.9604645e-8f; static constexpr int sweeps = 30; };
+
+// Rows whose squared norm is at most `tiny` are numerically zero singular values: the Jacobi
+// sweeps never rotate them against the others, so they are not orthogonal to the kept
+// directions and must not enter the kept basis.  Set them to exactly zero.  Ends with a barrier.
+template <typename T>
+__device__ void zero_tiny_rows(T* X, int m, int L, int ldx, T tiny) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int p = warp; p < m; p += nw) {
+    T s = 0;
+    for (int i = lane; i < L; i += 32) s += X[(size_t)p * ldx + i] * X[(size_t)p * ldx + i];
+    s = warp_sum(s);
+    if (s <= tiny)
+      for (int i = lane; i < L; i += 32) X[(size_t)p * ldx + i] = T(0);
+  }
+  __syncthreads();
+}
 
 // One-sided (Hestenes) Jacobi on the rows of X (m rows, m even, row length L, leading dim
-// ldx): rotate pairs of rows until every pair is orthogonal to the relative tolerance.  On
-// return the rows are sigma_i v_i^T with v_i the right singular vectors of the input.
-// Returns the number of sweeps, or -1 when the sweep limit was hit.
+// ldx): rotate pairs of rows until every pair is orthogonal to the relative tolerance
+// 2 sqrt(L) eps (the rounding floor of a length-L dot product), skipping pairs where one row is
+// numerically zero (squared norm below (L eps)^2 of the largest).  On return the rows are
+// sigma_i v_i^T with v_i the right singular vectors of the input.  Returns the number of
+// sweeps, or -1 when the sweep limit was hit.
 template <typename T>
-__device__ int hestenes_rows(T* X, int m, int L, int ldx, int* flag) {
+__device__ int hestenes_rows(T* X, int m, int L, int ldx, int* flag, unsigned long long* ctr, double* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const T tol = JacobiTol<T>::tol;
+  const T eps = JacobiTol<T>::eps;
+  const T tol = T(2) * sqrt(T(L)) * eps;
+  T nmax = 0;
+  for (int p = warp; p < m; p += nw) {
+    T s = 0;
+    for (int i = lane; i < L; i += 32) s += X[(size_t)p * ldx + i] * X[(size_t)p * ldx + i];
+    nmax = fmax(nmax, warp_sum(s));
+  }
+  nmax = block_max(nmax, red);
+  const T tiny = nmax * (T(L) * eps) * (T(L) * eps);
+  unsigned long long nrot = 0;
   for (int sweep = 0; sweep < JacobiTol<T>::sweeps; ++sweep) {
     if (threadIdx.x == 0) *flag = 0;
     __syncthreads();
@@ -249,7 +278,7 @@ __device__ int hestenes_rows(T* X, int m, int L, int ldx, int* flag) {
         a = warp_sum(a);
         b = warp_sum(b);
         c = warp_sum(c);
-        if (c != T(0) && fabs(c) > tol * sqrt(a * b)) {
+        if (c != T(0) && a > tiny && b > tiny && fabs(c) > tol * sqrt(a * b)) {
           // zeta = (b - a) / (2c); t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)) is the smaller
           // root of t^2 + 2 zeta t - 1 = 0, which makes the rotated rows orthogonal.
           const T zeta = (b - a) / (T(2) * c);
@@ -263,6 +292,7 @@ __device__ int hestenes_rows(T* X, int m, int L, int ldx, int* flag) {
             xq[i] = sn * u + cs * v;
           }
           rotated = 1;
+          ++nrot;
         }
       }
       __syncthreads();
@@ -271,8 +301,16 @@ __device__ int hestenes_rows(T* X, int m, int L, int ldx, int* flag) {
     __syncthreads();
     const int any = *flag;
     __syncthreads();
-    if (!any) return sweep + 1;
+    if (!any) {
+      zero_tiny_rows(X, m, L, ldx, tiny);
+      if (ctr && lane == 0 && nrot) atomicAdd(ctr + 1, nrot);
+      if (ctr && threadIdx.x == 0) { atomicAdd(ctr + 0, (unsigned long long)(sweep + 1)); atomicAdd(ctr + 2, 1ull); }
+      return sweep + 1;
+    }
   }
+  zero_tiny_rows(X, m, L, ldx, tiny);
+  if (ctr && lane == 0 && nrot) atomicAdd(ctr + 1, nrot);
+  if (ctr && threadIdx.x == 0) { atomicAdd(ctr + 0, (unsigned long long)JacobiTol<T>::sweeps); atomicAdd(ctr + 2, 1ull); }
   return -1;
 }
 
@@ -284,6 +322,7 @@ struct RowWork {
   int* sel;
   double* red;
   int ci;
+  unsigned long long* ctr;
 };
 
 // One row step of the boundary MPS: Eout = normalise(truncate_chi(Eprev o T_proj[row])).
@@ -399,7 +438,7 @@ __device__ double env_row_step(const Geo& g, const T* Eprev, T* Eout, const T* T
       X[o] = s;
     }
     __syncthreads();
-    const int sweeps = hestenes_rows(X, mX, Lr, Lr, flag);
+    const int sweeps = hestenes_rows(X, mX, Lr, Lr, flag, w.ctr, w.red);
     if (sweeps < 0 && tid == 0) *st |= ST_NOCONV;
     // singular values = row norms
     {

@@ -62,6 +62,9 @@ def load():
         "minsr_step": ([vp, vp, vp, vp, i32, dbl, dbl, dbl, vp, vp, vp], i32),
         "peps_sample": ([vp, i32, vp, i32, i32, C.c_uint64, C.c_uint64, vp, vp, vp], i32),
         "peps_last_error": ([vp], C.c_char_p),
+        "peps_apply_update": ([vp, vp, vp, vp], i32),
+        "peps_timing_enable": ([vp, i32], i32),
+        "peps_timing_read": ([vp, vp, vp, i32, vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -73,7 +76,11 @@ def load():
 
 def exported_symbols():
     return ["peps_create", "peps_destroy", "peps_num_params", "peps_set_params", "peps_amplitudes",
-            "peps_local_energy", "peps_logderiv", "peps_evaluate", "minsr_step", "peps_sample", "peps_last_error"]
+            "peps_local_energy", "peps_logderiv", "peps_evaluate", "minsr_step", "peps_sample", "peps_last_error",
+            "peps_timing_enable", "peps_timing_read", "peps_apply_update"]
+
+
+TIMING_CLASSES = ["env", "row", "pair", "combine", "sample", "minsr_gram", "minsr_eig", "minsr_other", "pad"]
 
 
 def _ptr(t):
@@ -214,6 +221,25 @@ class PEPS:
                                       _ptr(w.contiguous()) if w is not None else None, ns, float(lam), float(rcond),
                                       float(tau), _ptr(dth), _ptr(info), _stream()), "minsr_step")
         return dth, info
+
+    def apply_update(self, theta: torch.Tensor, dtheta: torch.Tensor):
+        """theta += dtheta on the device (in place) and refresh the handle's kernel copy."""
+        assert theta.is_cuda and theta.dtype == torch.float64 and theta.is_contiguous()
+        self._check(self.L.peps_apply_update(self.h, _ptr(theta), _ptr(dtheta.contiguous()), _stream()),
+                    "peps_apply_update")
+        self._theta_ref = theta
+
+    def timing(self, enable=True):
+        self._check(self.L.peps_timing_enable(self.h, 1 if enable else 0), "peps_timing_enable")
+
+    def timing_read(self):
+        n = len(TIMING_CLASSES)
+        ms = (C.c_double * n)()
+        la = (C.c_longlong * n)()
+        ctr = (C.c_longlong * 4)()
+        self._check(self.L.peps_timing_read(self.h, ms, la, n, ctr), "peps_timing_read")
+        return ({k: ms[i] for i, k in enumerate(TIMING_CLASSES)}, {k: la[i] for i, k in enumerate(TIMING_CLASSES)},
+                dict(jacobi_sweeps=ctr[0], jacobi_rotations=ctr[1], svds=ctr[2]))
 
     def sample(self, S, move=MOVE_EXCHANGE, nsweeps=1, seed=0, sweep0=0, accepted=None):
         S = self._S(S)
