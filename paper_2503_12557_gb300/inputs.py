@@ -266,3 +266,23 @@ WORKLOADS = {
                                    init=dict(kind="normal", scale=0.5, bias=1.0),
                                    seed_theta=1004, seed_S=2004, seed_chain=3004, lam=1e-4, rcond=0.0, tau=0.05),
 }
+
+
+# ----------------------------------------------------------------------------- learned proposal
+
+PROPOSAL_CHANNELS = 16
+
+
+def proposal_init(seed: int, C: int = PROPOSAL_CHANNELS, scale: float = 1.0):
+    """Seeded initial weights of the 3-layer 3x3 convolutional proposal network, packed in one
+    float64 vector: W1 (C,1,3,3), b1 (C), W2 (C,C,3,3), b2 (C), W3 (1,C,3,3), b3 (1).
+    Entries N(0, scale^2 / fan_in), biases zero."""
+    rng = np.random.default_rng(seed)
+    parts = [rng.standard_normal((C, 1, 3, 3)) * scale / 3.0, np.zeros(C),
+             rng.standard_normal((C, C, 3, 3)) * scale / math.sqrt(9.0 * C), np.zeros(C),
+             rng.standard_normal((1, C, 3, 3)) * scale / math.sqrt(9.0 * C), np.zeros(1)]
+    return np.concatenate([p.ravel() for p in parts])
+
+
+def proposal_shapes(C: int = PROPOSAL_CHANNELS):
+    return [(C, 1, 3, 3), (C,), (C, C, 3, 3), (C,), (1, C, 3, 3), (1,)]
