@@ -51,7 +51,9 @@ typedef enum {
     PEPS_E_SHAPE = -2,      /* lattice / chi / Ns outside what the handle supports     */
     PEPS_E_WORKSPACE = -3,  /* device allocation failed                                */
     PEPS_E_CUDA = -4,       /* a CUDA runtime call failed (peps_last_error has detail) */
-    PEPS_E_UNSUPPORTED = -5 /* option combination not implemented                      */
+    PEPS_E_UNSUPPORTED = -5, /* option combination not implemented                     */
+    PEPS_E_CAPACITY = -6    /* peps_amplitudes_noalloc: the problem needs more than its
+                               fixed 32 MiB device scratch array                       */
 } peps_status;
 
 enum {
@@ -182,6 +184,24 @@ peps_status peps_sample(peps_handle* h, int move, uint8_t* S_dev, int Ns, int ns
 peps_status peps_timing_enable(peps_handle* h, int enable);
 peps_status peps_timing_read(peps_handle* h, double* ms_host, long long* launches_host, int n,
                              long long* counters_host);
+
+/* ln|psi_top(S)| and phase, as peps_amplitudes, for callers that cannot allocate device memory
+ * (code running under another framework's allocator, which owns all device memory, or with a
+ * device-memory budget fixed before this library is used).  This entry point has no
+ * counterpart in the paper; it exists for those callers only.
+ *   It needs no handle and calls no allocation routine: every intermediate lives in one
+ *   32 MiB device array that the library reserves on every GPU it is loaded on until the
+ *   process exits.  cfg gives the lattice, chi and precision (max_samples is ignored);
+ *   theta_dev: N_p doubles; S_dev: Ns x (Lx*Ly) uint8; logabs_dev, phase_dev: Ns doubles;
+ *   status_dev: Ns int32 or NULL.  All device memory owned by the caller.
+ *   Returns PEPS_E_CAPACITY, before any launch, when the parameters, environments and work
+ *   buffers of this lattice and Ns do not fit in the 32 MiB (about 8 KiB per sample at
+ *   4x4, D=2, chi=4 in FP64; larger problems need a handle).
+ *   The first call on a device looks up the array's device address with that device current;
+ *   make that first call before any stream capture.  All calls share the array and leave their
+ *   contents in it: calls that may overlap on the GPU race and must be serialised. */
+peps_status peps_amplitudes_noalloc(const peps_config* cfg, const double* theta_dev, const uint8_t* S_dev, int Ns,
+                                    double* logabs_dev, double* phase_dev, int32_t* status_dev, void* stream);
 
 /* Text of the last error seen by this handle (never NULL). */
 const char* peps_last_error(const peps_handle* h);
