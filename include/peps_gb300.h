@@ -185,6 +185,37 @@ peps_status peps_timing_enable(peps_handle* h, int enable);
 peps_status peps_timing_read(peps_handle* h, double* ms_host, long long* launches_host, int n,
                              long long* counters_host);
 
+/* ---- Learned proposal (required by the hot-path specification; not in the paper) ----------
+ * Network: x = 1 - 2 s (one +-1 channel) -> conv3x3(1->C) -> SiLU -> conv3x3(C->C) -> SiLU ->
+ * conv3x3(C->1) -> per-site logits l(S); zero padding at the open boundary; every conv has a
+ * bias.  Weights packed W1 (C,1,3,3), b1 (C), W2 (C,C,3,3), b2 (C), W3 (1,C,3,3), b3 (1):
+ * 9 C^2 + 20 C + 1 values.  wprec 0: double weights and activations; wprec 1: bf16
+ * weights (__nv_bfloat16) with float activations.  Lx*Ly <= 256, 1 <= C <= 32. */
+
+/* logits_dev (Ns x Lx*Ly doubles) = l(S) for every configuration. */
+peps_status peps_proposal_logits(int Lx, int Ly, int C, int wprec, const void* w_dev, const uint8_t* S_dev, int Ns,
+                                 double* logits_dev, void* stream);
+
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8, step count t >= 1) on the FP64 master weights
+ * w_dev with moments m_dev, v_dev, for the loss mean_{S,i} softplus(l_i(S_in)) - t_i l_i(S_in)
+ * over the Ns (S_in, S_tgt) pairs (the binary cross-entropy of the target given the input).
+ * The gradient is taken at the weights the forward pass uses (w_dev for wprec 0, the bf16 copy
+ * wlow_dev for wprec 1); wlow_dev, when not NULL, is refreshed from the updated master weights.
+ * grad_dev: workspace of the weight count (holds the gradient afterwards); loss_dev: 1 double. */
+peps_status peps_proposal_train_step(int Lx, int Ly, int C, int wprec, double* w_dev, double* m_dev, double* v_dev,
+                                     void* wlow_dev, int t, double lr, const uint8_t* S_in_dev,
+                                     const uint8_t* S_tgt_dev, int Ns, double* grad_dev, double* loss_dev,
+                                     void* stream);
+
+/* One network move of every chain: S' ~ prod_i Bernoulli(sigmoid(l_i(S))) with site i of chain c
+ * drawn from u = Philox4x32-10(counter (i, step, c, 1), key seed); ln|psi_top(S')| from the
+ * handle (as peps_amplitudes); accept iff u' < exp(min(0, 2 (ln|psi'| - ln|psi|) + log q(S|S')
+ * - log q(S'|S))) with u' from counter (Lx*Ly, step, c, 1).  S_dev and logpsi_dev (the current
+ * ln|psi_top(S)|) are updated in place; accepted_dev (Ns int64, may be NULL) is incremented. */
+peps_status peps_sample_learned(peps_handle* h, int C, int wprec, const void* w_dev, uint8_t* S_dev,
+                                double* logpsi_dev, int Ns, uint64_t seed, uint64_t step,
+                                long long* accepted_dev, int32_t* status_dev, void* stream);
+
 /* ln|psi_top(S)| and phase, as peps_amplitudes, for callers that cannot allocate device memory
  * (code running under another framework's allocator, which owns all device memory, or with a
  * device-memory budget fixed before this library is used).  This entry point has no

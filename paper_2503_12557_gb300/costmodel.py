@@ -29,11 +29,12 @@ def row_step_flops(chi, D, Ly):
 
 
 def jacobi_flops(chi, D, sweeps, rotations):
-    """One-sided Jacobi work from the recorded counters: every pair check is three dot
-    products of length Lr (6 Lr flops), every rotation updates two rows (6 Lr flops)."""
+    """One-sided Jacobi work from the recorded counters: every sweep recomputes the mX row
+    norms (2 Lr flops each), every pair check is one dot product of length Lr (2 Lr flops; the
+    norms are carried by Rutishauser's update), every rotation updates two rows (6 Lr flops)."""
     n, Lr, mX = _dims(chi, D)
     checks = sweeps * (mX // 2) * (mX - 1)
-    return 6 * Lr * checks + 6 * Lr * rotations
+    return 2 * Lr * checks + 6 * Lr * rotations + 2 * mX * Lr * sweeps
 
 
 def env_flops(Lx, Ly, chi, D, ns, sides, sweeps, rotations):

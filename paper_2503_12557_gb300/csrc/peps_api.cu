@@ -63,6 +63,9 @@ struct peps_handle {
   std::vector<long long> evlaunches;
   size_t evn = 0;
   unsigned long long* ctr = nullptr;  // device work counters (8)
+  // learned-proposal workspace (allocated on first use)
+  uint8_t* lp_Sp = nullptr;
+  double *lp_l0 = nullptr, *lp_l1 = nullptr, *lp_aux = nullptr;
   std::string err;
 };
 
@@ -139,10 +142,7 @@ static void plan_all(peps_handle* h) {
   // FP64: one CTA per SM (the FP64 pipe is the limit); FP32: two CTAs per SM
   const size_t budget = (E == 8) ? 210 * 1024 : 110 * 1024;
   int ci = std::min(n, 8);
-  const size_t zleft = (size_t)n * D * n;
-  const size_t zright = (size_t)chi * D * D * chi + (size_t)n * Lr + (size_t)mX * Lr + (size_t)chi * Lr +
-                        (size_t)n * chi + (size_t)chi * D * chi;
-  const size_t zsz = std::max(zleft, zright);
+  const size_t zsz = env_z_elems(chi, D);
   // one-row / two-row temporaries
   const size_t t1row = (size_t)chi * chi * D * D;
   int cx = chi;
@@ -155,7 +155,7 @@ static void plan_all(peps_handle* h) {
     k.p.cx = cx;
     std::vector<std::pair<int, size_t>> b = {
         {B_RED, 40 * 8}, {B_SIG, (mX + 4) * E}, {B_SEL, 2 * mX * 4}, {B_A, (size_t)g.sT * E}, {B_E, (size_t)g.se * E},
-        {B_C, (size_t)n * chi * E}, {B_W, (size_t)ci * D * D * chi * E}, {B_R, (size_t)n * n * E}, {B_Z, zsz * E},
+        {B_C, (size_t)n * chi * E}, {B_W, env_w_elems(chi, D, ci) * E}, {B_R, (size_t)n * n * E}, {B_Z, zsz * E},
         {B_RHIST, (size_t)std::max(1, Ly - 1) * n * n * E}};
     place(k.p, k.smem, budget, b);
   }
@@ -191,7 +191,7 @@ static void plan_all(peps_handle* h) {
     std::vector<std::pair<int, size_t>> b = {
         {B_RED, 40 * 8}, {B_SIG, (mX + 4) * E}, {B_SEL, 2 * mX * 4}, {B_S, (size_t)g.Lx * g.Ly},
         {B_A, (size_t)g.sT * E}, {B_A2, (size_t)g.sT * E}, {B_E, (size_t)g.se * E}, {B_EU, (size_t)g.se * E},
-        {B_EL, (size_t)g.se * E}, {B_C, (size_t)n * chi * E}, {B_W, (size_t)ci * D * D * chi * E},
+        {B_EL, (size_t)g.se * E}, {B_C, (size_t)n * chi * E}, {B_W, env_w_elems(chi, D, ci) * E},
         {B_T1, tt * E}, {B_T2, tt * E}, {B_LW, lw * E}, {B_LW2, lw * E}, {B_LP, lw * E},
         {B_R, (size_t)n * n * E}, {B_Z, zsz * E}, {B_RP, (size_t)(Ly + 1) * lw * E},
         {B_RHIST, (size_t)std::max(1, Ly - 1) * n * n * E}};
@@ -287,7 +287,8 @@ extern "C" peps_status peps_destroy(peps_handle* h) {
   if (!h) return PEPS_E_ARG;
   void* ptrs[] = {h->Tpad, h->site_off, h->envs, h->logs, h->wdisc, h->rowout, h->pairout, h->status_tmp,
                   h->gscratch, h->d_tinfo, h->d_ab, h->d_eh, h->d_rowoff, h->d_pairoff, h->d_pij, h->d_pv,
-                  h->d_onsite, h->Obar, h->Tm, h->Vm, h->Hm, h->mean, h->ebar, h->yv, h->xv, h->cnt, h->ctr};
+                  h->d_onsite, h->Obar, h->Tm, h->Vm, h->Hm, h->mean, h->ebar, h->yv, h->xv, h->cnt, h->ctr,
+                  h->lp_Sp, h->lp_l0, h->lp_l1, h->lp_aux};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t e : h->evpool) cudaEventDestroy(e);
@@ -656,4 +657,87 @@ extern "C" peps_status peps_apply_update(peps_handle* h, double* theta_dev, cons
   CK(launch_axpy(theta_dev, dtheta_dev, h->Np, s), "theta update");
   tstop(h, ts, s);
   return peps_set_params(h, theta_dev, stream);
+}
+
+// ---- learned proposal --------------------------------------------------------------------
+static bool prop_shape_ok(int Lx, int Ly, int C, int wprec) {
+  if (Lx < 1 || Ly < 1 || Lx * Ly > 256 || C < 1 || C > 32 || (wprec != 0 && wprec != 1)) return false;
+  return prop_smem_bytes(Lx, Ly, C, wprec == 0 ? 8 : 4, true) <= 220 * 1024;
+}
+
+static int prop_grid(int Ns) {
+  int dev = 0, nsm = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  return Ns < nsm ? (Ns > 0 ? Ns : 1) : nsm;
+}
+
+extern "C" peps_status peps_proposal_logits(int Lx, int Ly, int C, int wprec, const void* w_dev, const uint8_t* S_dev,
+                                            int Ns, double* logits_dev, void* stream) {
+  if (!prop_shape_ok(Lx, Ly, C, wprec)) return PEPS_E_SHAPE;
+  if (Ns < 0 || (Ns > 0 && (!w_dev || !S_dev || !logits_dev))) return PEPS_E_ARG;
+  if (Ns == 0) return PEPS_OK;
+  cudaError_t e = launch_prop_logits(Lx, Ly, C, wprec, w_dev, S_dev, Ns, logits_dev, prop_grid(Ns), (cudaStream_t)stream);
+  return e == cudaSuccess ? PEPS_OK : PEPS_E_CUDA;
+}
+
+extern "C" peps_status peps_proposal_train_step(int Lx, int Ly, int C, int wprec, double* w_dev, double* m_dev,
+                                                double* v_dev, void* wlow_dev, int t, double lr,
+                                                const uint8_t* S_in_dev, const uint8_t* S_tgt_dev, int Ns,
+                                                double* grad_dev, double* loss_dev, void* stream) {
+  if (!prop_shape_ok(Lx, Ly, C, wprec)) return PEPS_E_SHAPE;
+  if (!w_dev || !m_dev || !v_dev || !grad_dev || !loss_dev || t < 1 || Ns < 1 || !S_in_dev || !S_tgt_dev ||
+      (wprec == 1 && !wlow_dev))
+    return PEPS_E_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nw = 9 * C * C + 20 * C + 1;
+  if (cudaMemsetAsync(grad_dev, 0, sizeof(double) * nw, s) != cudaSuccess) return PEPS_E_CUDA;
+  if (cudaMemsetAsync(loss_dev, 0, sizeof(double), s) != cudaSuccess) return PEPS_E_CUDA;
+  const void* wf = (wprec == 0) ? (const void*)w_dev : (const void*)wlow_dev;
+  if (launch_prop_grad(Lx, Ly, C, wprec, wf, S_in_dev, S_tgt_dev, Ns, grad_dev, loss_dev, prop_grid(Ns), s) != cudaSuccess)
+    return PEPS_E_CUDA;
+  if (launch_prop_adam(nw, w_dev, m_dev, v_dev, grad_dev, t, lr, wlow_dev, s) != cudaSuccess) return PEPS_E_CUDA;
+  return PEPS_OK;
+}
+
+static peps_status ensure_learned(peps_handle* h) {
+  if (h->lp_Sp) return PEPS_OK;
+  const size_t ns = (size_t)h->cfg.max_samples, N = (size_t)h->g.Lx * h->g.Ly;
+  if (cudaMalloc(&h->lp_Sp, ns * N) != cudaSuccess || cudaMalloc(&h->lp_l0, sizeof(double) * ns * N) != cudaSuccess ||
+      cudaMalloc(&h->lp_l1, sizeof(double) * ns * N) != cudaSuccess ||
+      cudaMalloc(&h->lp_aux, sizeof(double) * ns * 4) != cudaSuccess)
+    return fail(h, PEPS_E_WORKSPACE, "learned-proposal workspace allocation failed");
+  return PEPS_OK;
+}
+
+extern "C" peps_status peps_sample_learned(peps_handle* h, int C, int wprec, const void* w_dev, uint8_t* S_dev,
+                                           double* logpsi_dev, int Ns, uint64_t seed, uint64_t step,
+                                           long long* accepted_dev, int32_t* status_dev, void* stream) {
+  peps_status c = check_eval(h, S_dev, Ns);
+  if (c != PEPS_OK) return c;
+  if (!prop_shape_ok(h->g.Lx, h->g.Ly, C, wprec)) return fail(h, PEPS_E_SHAPE, "proposal network shape");
+  if (Ns > 0 && (!w_dev || !logpsi_dev)) return fail(h, PEPS_E_ARG, "null argument");
+  if (Ns == 0) return PEPS_OK;
+  peps_status ps = ensure_learned(h);
+  if (ps != PEPS_OK) return ps;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int N = h->g.Lx * h->g.Ly;
+  double* lq_f = h->lp_aux;
+  double* lq_b = h->lp_aux + Ns;
+  double* lpsi_new = h->lp_aux + 2 * (size_t)Ns;
+  double* ph_new = h->lp_aux + 3 * (size_t)Ns;
+  const int ts = tstart(h, TC_SAMPLE, s);
+  CK(launch_prop_logits(h->g.Lx, h->g.Ly, C, wprec, w_dev, S_dev, Ns, h->lp_l0, prop_grid(Ns), s), "proposal logits");
+  CK(launch_prop_draw(N, Ns, h->lp_l0, seed, step, h->lp_Sp, lq_f, s), "proposal draw");
+  CK(launch_prop_logits(h->g.Lx, h->g.Ly, C, wprec, w_dev, h->lp_Sp, Ns, h->lp_l1, prop_grid(Ns), s), "proposal logits");
+  CK(launch_prop_logq(N, Ns, h->lp_l1, S_dev, lq_b, s), "proposal log q");
+  tstop(h, ts, s, 4);
+  ps = (h->esz == 8) ? run_eval<double>(h, nullptr, h->lp_Sp, Ns, lpsi_new, ph_new, nullptr, nullptr, status_dev, s, 1)
+                     : run_eval<float>(h, nullptr, h->lp_Sp, Ns, lpsi_new, ph_new, nullptr, nullptr, status_dev, s, 1);
+  if (ps != PEPS_OK) return ps;
+  const int ts2 = tstart(h, TC_SAMPLE, s);
+  CK(launch_prop_accept(N, Ns, seed, step, h->lp_Sp, lpsi_new, lq_f, lq_b, S_dev, logpsi_dev, accepted_dev, s),
+     "proposal accept");
+  tstop(h, ts2, s);
+  return PEPS_OK;
 }

@@ -73,6 +73,20 @@ cudaError_t launch_obar_t_x(const double* Obar, const double* x, int Ns, long lo
 // x = (A + lambda I)^-1 ebar by blocked Cholesky (A overwritten by its factor); returns launches
 long long chol_solve(double* A, int n, int nreal, double lambda, const double* ebar, double* x, int* bad,
                      double* info, cudaStream_t s, cudaError_t* err);
+// ---- learned proposal (peps_proposal.cu)
+size_t prop_smem_bytes(int Lx, int Ly, int C, int act_bytes, bool train);
+cudaError_t launch_prop_logits(int Lx, int Ly, int C, int wprec, const void* w, const uint8_t* S, int Ns, double* logits,
+                               int grid, cudaStream_t s);
+cudaError_t launch_prop_grad(int Lx, int Ly, int C, int wprec, const void* w, const uint8_t* Sin, const uint8_t* Stg,
+                             int Ns, double* grad, double* loss, int grid, cudaStream_t s);
+cudaError_t launch_prop_adam(int nw, double* w, double* m, double* v, const double* g, int t, double lr, void* wlow,
+                             cudaStream_t s);
+cudaError_t launch_prop_draw(int N, int Ns, const double* logits, uint64_t seed, uint64_t step, uint8_t* Sp, double* lq,
+                             cudaStream_t s);
+cudaError_t launch_prop_logq(int N, int Ns, const double* logits, const uint8_t* S, double* lq, cudaStream_t s);
+cudaError_t launch_prop_accept(int N, int Ns, uint64_t seed, uint64_t step, const uint8_t* Sp, const double* lpsi_new,
+                               const double* lq_fwd, const double* lq_bwd, uint8_t* S, double* lpsi, long long* accepted,
+                               cudaStream_t s);
 // y += x (n doubles)
 cudaError_t launch_axpy(double* y, const double* x, long long n, cudaStream_t s);
 

@@ -71,14 +71,11 @@ peps_status run(const peps_config& c, const double* theta, const uint8_t* S, int
   const int N = c.Lx * c.Ly, n = g.n, chi = g.chi, D = g.D, Ly = g.Ly;
   const int mX = n + (n & 1), Lr = D * chi, ci = n < 8 ? n : 8;
   const size_t E = sizeof(T);
-  const size_t zleft = (size_t)n * D * n;
-  const size_t zright = (size_t)chi * D * D * chi + (size_t)n * Lr + (size_t)mX * Lr + (size_t)chi * Lr +
-                        (size_t)n * chi + (size_t)chi * D * chi;
-  const size_t zsz = zleft > zright ? zleft : zright;
+  const size_t zsz = env_z_elems(chi, D);
   const size_t t1 = (size_t)chi * chi * D * D;
   const std::pair<int, size_t> benv[] = {
       {B_RED, 40 * 8}, {B_SIG, (mX + 4) * E}, {B_SEL, 2 * (size_t)mX * 4}, {B_A, (size_t)g.sT * E},
-      {B_E, (size_t)g.se * E}, {B_C, (size_t)n * chi * E}, {B_W, (size_t)ci * D * D * chi * E},
+      {B_E, (size_t)g.se * E}, {B_C, (size_t)n * chi * E}, {B_W, env_w_elems(chi, D, ci) * E},
       {B_R, (size_t)n * n * E}, {B_Z, zsz * E}, {B_RHIST, (size_t)(Ly > 1 ? Ly - 1 : 1) * n * n * E}};
   const std::pair<int, size_t> brow[] = {
       {B_RED, 40 * 8}, {B_A, (size_t)g.sT * E}, {B_EU, (size_t)g.se * E}, {B_EL, (size_t)g.se * E},

@@ -168,46 +168,47 @@ __device__ void load_A(T* As, const T* Tpad, const Geo& g, int site, int s, bool
 }
 
 // ------------------------------------------------------------------------------------------
-// Householder QR of Z (m x nc, row major), keeping only R (nc x nc, upper triangular, zero
-// below the diagonal).  Reflector convention of LAPACK's xLARFG (H = I - tau v v^T, v_0 = 1).
+// Householder QR of Z (m x nc, stored column major: element (i, c) at Z[c * m + i], so that the
+// column walks of the factorisation are contiguous in shared memory), keeping only R (nc x nc,
+// row major, upper triangular, zero below the diagonal).  Reflector convention of LAPACK's
+// xLARFG (H = I - tau v v^T, v_0 = 1).
 template <typename T>
 __device__ void qr_keep_r(T* Z, int m, int nc, T* R, double* red) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   const int steps = (m < nc) ? m : nc;
   for (int j = 0; j < steps; ++j) {
+    T* zj = Z + (size_t)j * m;
     T part = 0;
-    for (int i = j + 1 + tid; i < m; i += blockDim.x) {
-      const T z = Z[(size_t)i * nc + j];
-      part += z * z;
-    }
+    for (int i = j + 1 + tid; i < m; i += blockDim.x) part += zj[i] * zj[i];
     const T sigma = block_sum(part, red);
-    const T alpha = Z[(size_t)j * nc + j];
+    const T alpha = zj[j];
     T tau = 0, beta = alpha;
     if (sigma != T(0)) {
       const T nrm = sqrt(alpha * alpha + sigma);
       beta = (alpha >= T(0)) ? -nrm : nrm;
       tau = (beta - alpha) / beta;
       const T sc = T(1) / (alpha - beta);
-      for (int i = j + 1 + tid; i < m; i += blockDim.x) Z[(size_t)i * nc + j] *= sc;
+      for (int i = j + 1 + tid; i < m; i += blockDim.x) zj[i] *= sc;
     }
     __syncthreads();
     if (tau != T(0)) {
       for (int c = j + 1 + warp; c < nc; c += nw) {
+        T* zc = Z + (size_t)c * m;
         T s = 0;
-        for (int i = j + 1 + lane; i < m; i += 32) s += Z[(size_t)i * nc + j] * Z[(size_t)i * nc + c];
+        for (int i = j + 1 + lane; i < m; i += 32) s += zj[i] * zc[i];
         s = warp_sum(s);
-        const T w = (s + Z[(size_t)j * nc + c]) * tau;
-        if (lane == 0) Z[(size_t)j * nc + c] -= w;
-        for (int i = j + 1 + lane; i < m; i += 32) Z[(size_t)i * nc + c] -= Z[(size_t)i * nc + j] * w;
+        const T w = (s + zc[j]) * tau;
+        if (lane == 0) zc[j] -= w;
+        for (int i = j + 1 + lane; i < m; i += 32) zc[i] -= zj[i] * w;
       }
     }
     __syncthreads();
-    if (tid == 0) Z[(size_t)j * nc + j] = beta;
+    if (tid == 0) zj[j] = beta;
     __syncthreads();
   }
   for (int o = tid; o < nc * nc; o += blockDim.x) {
     const int i = o / nc, c = o % nc;
-    R[o] = (i <= c && i < m) ? Z[(size_t)i * nc + c] : T(0);
+    R[o] = (i <= c && i < m) ? Z[(size_t)c * m + i] : T(0);
   }
   __syncthreads();
 }
@@ -240,44 +241,52 @@ __device__ void zero_tiny_rows(T* X, int m, int L, int ldx, T tiny) {
 }
 
 // One-sided (Hestenes) Jacobi on the rows of X (m rows, m even, row length L, leading dim
-// ldx): rotate pairs of rows until every pair is orthogonal to the relative tolerance
-// 2 sqrt(L) eps (the rounding floor of a length-L dot product), skipping pairs where one row is
-// numerically zero (squared norm below (L eps)^2 of the largest).  On return the rows are
-// sigma_i v_i^T with v_i the right singular vectors of the input.  Returns the number of
-// sweeps, or -1 when the sweep limit was hit.
+// ldx): rotate pairs of rows until every pair is orthogonal to the relative tolerance L eps
+// (well above the sqrt(L) eps rounding noise of a converged pair's dot product, so a converged
+// sweep really makes no rotation), skipping pairs where one row is numerically zero (squared
+// norm below (L eps)^2 of the largest).  On return the rows are sigma_i v_i^T with v_i the right
+// singular vectors of the input.
+//   Each warp treats four pairs at once (eight lanes per pair).  The squared row norms live in
+//   nrm[] (m entries): exact at the start of every sweep, and within a sweep updated after a
+//   rotation by Rutishauser's formulas a' = a - t g, b' = b + t g (g the pair's dot product), so
+//   that a pair check costs one dot product.
+// Returns the number of sweeps, or -1 when the sweep limit was hit.
 template <typename T>
-__device__ int hestenes_rows(T* X, int m, int L, int ldx, int* flag, unsigned long long* ctr, double* red) {
+__device__ int hestenes_rows(T* X, int m, int L, int ldx, int* flag, unsigned long long* ctr, double* red, T* nrm) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int grp = lane >> 3, sub = lane & 7, ngroups = nw * 4;
+  const unsigned gmask = 0xffu << (grp * 8);
   const T eps = JacobiTol<T>::eps;
-  const T tol = T(2) * sqrt(T(L)) * eps;
-  T nmax = 0;
-  for (int p = warp; p < m; p += nw) {
-    T s = 0;
-    for (int i = lane; i < L; i += 32) s += X[(size_t)p * ldx + i] * X[(size_t)p * ldx + i];
-    nmax = fmax(nmax, warp_sum(s));
-  }
-  nmax = block_max(nmax, red);
-  const T tiny = nmax * (T(L) * eps) * (T(L) * eps);
+  const T tol = T(L) * eps;
+  T tiny = 0;
   unsigned long long nrot = 0;
   for (int sweep = 0; sweep < JacobiTol<T>::sweeps; ++sweep) {
+    for (int p = warp; p < m; p += nw) {
+      T s = 0;
+      for (int i = lane; i < L; i += 32) s += X[(size_t)p * ldx + i] * X[(size_t)p * ldx + i];
+      s = warp_sum(s);
+      if (lane == 0) nrm[p] = s;
+    }
     if (threadIdx.x == 0) *flag = 0;
     __syncthreads();
+    if (sweep == 0) {
+      T nmax = 0;
+      for (int p = threadIdx.x; p < m; p += blockDim.x) nmax = fmax(nmax, nrm[p]);
+      nmax = block_max(nmax, red);
+      tiny = nmax * (T(L) * eps) * (T(L) * eps);
+    }
     int rotated = 0;
     for (int r = 0; r < m - 1; ++r) {
-      for (int pi = warp; pi < m / 2; pi += nw) {
+      for (int pi = warp * 4 + grp; pi < m / 2; pi += ngroups) {
         const int p = rr_player(pi, r, m), q = rr_player(m - 1 - pi, r, m);
         T* xp = X + (size_t)p * ldx;
         T* xq = X + (size_t)q * ldx;
-        T a = 0, b = 0, c = 0;
-        for (int i = lane; i < L; i += 32) {
-          const T u = xp[i], v = xq[i];
-          a += u * u;
-          b += v * v;
-          c += u * v;
-        }
-        a = warp_sum(a);
-        b = warp_sum(b);
-        c = warp_sum(c);
+        const T a = nrm[p], b = nrm[q];
+        T c = 0;
+        for (int i = sub; i < L; i += 8) c += xp[i] * xq[i];
+        c += __shfl_xor_sync(gmask, c, 4);
+        c += __shfl_xor_sync(gmask, c, 2);
+        c += __shfl_xor_sync(gmask, c, 1);
         if (c != T(0) && a > tiny && b > tiny && fabs(c) > tol * sqrt(a * b)) {
           // zeta = (b - a) / (2c); t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)) is the smaller
           // root of t^2 + 2 zeta t - 1 = 0, which makes the rotated rows orthogonal.
@@ -286,13 +295,18 @@ __device__ int hestenes_rows(T* X, int m, int L, int ldx, int* flag, unsigned lo
           if (fabs(zeta) > T(1e15)) t = T(0.5) / zeta;
           else t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
           const T cs = T(1) / sqrt(T(1) + t * t), sn = cs * t;
-          for (int i = lane; i < L; i += 32) {
+          for (int i = sub; i < L; i += 8) {
             const T u = xp[i], v = xq[i];
             xp[i] = cs * u - sn * v;
             xq[i] = sn * u + cs * v;
           }
+          __syncwarp(gmask);
+          if (sub == 0) {
+            nrm[p] = fmax(T(0), a - t * c);
+            nrm[q] = b + t * c;
+            ++nrot;
+          }
           rotated = 1;
-          ++nrot;
         }
       }
       __syncthreads();
@@ -303,16 +317,29 @@ __device__ int hestenes_rows(T* X, int m, int L, int ldx, int* flag, unsigned lo
     __syncthreads();
     if (!any) {
       zero_tiny_rows(X, m, L, ldx, tiny);
-      if (ctr && lane == 0 && nrot) atomicAdd(ctr + 1, nrot);
+      if (ctr && nrot) atomicAdd(ctr + 1, nrot);
       if (ctr && threadIdx.x == 0) { atomicAdd(ctr + 0, (unsigned long long)(sweep + 1)); atomicAdd(ctr + 2, 1ull); }
       return sweep + 1;
     }
   }
   zero_tiny_rows(X, m, L, ldx, tiny);
-  if (ctr && lane == 0 && nrot) atomicAdd(ctr + 1, nrot);
+  if (ctr && nrot) atomicAdd(ctr + 1, nrot);
   if (ctr && threadIdx.x == 0) { atomicAdd(ctr + 0, (unsigned long long)JacobiTol<T>::sweeps); atomicAdd(ctr + 2, 1ull); }
   return -1;
 }
+
+// ------------------------------------------------------------------------------------------
+// Sizes (in elements) of the row step's work buffers, shared by every planner:
+// Z holds the left pass's column-major Z (n D x n) and, later, the right pass's P, Y, X, Vt, C
+// and new-site buffers (Y, X, Vt rows padded to D chi + 1); W holds ci rows of stride
+// D^2 chi + 1.
+__host__ __device__ inline size_t env_z_elems(int chi, int D) {
+  const size_t n = (size_t)chi * D, Lr = (size_t)D * chi, LY = Lr + 1, mX = n + (n & 1);
+  const size_t zleft = n * D * n;
+  const size_t zright = (size_t)chi * D * D * chi + n * LY + mX * LY + (size_t)chi * LY + n * chi + (size_t)chi * D * chi;
+  return zleft > zright ? zleft : zright;
+}
+__host__ __device__ inline size_t env_w_elems(int chi, int D, int ci) { return (size_t)ci * ((size_t)D * D * chi + 1); }
 
 // ------------------------------------------------------------------------------------------
 // Per-CTA working set of one boundary-MPS row step.
@@ -345,6 +372,8 @@ __device__ double env_row_step(const Geo& g, const T* Eprev, T* Eout, const T* T
     blk_copy(w.E, Eprev + (size_t)k * g.se, g.se);
     load_A(w.A, Tpad, g, row * Ly + k, Srow[k], lower);
     __syncthreads();
+    const int mZ = n * D;              // rows of Z; Z is stored column major (ld mZ)
+    const int WS = D * D * chi + 1;    // padded row stride of W (no bank conflicts across ii)
     for (int i0 = 0; i0 < n; i0 += w.ci) {
       const int ci = (n - i0 < w.ci) ? (n - i0) : w.ci;
       // W[ii][l][u][b] = sum_a R[i0+ii][(a,l)] E[a][u][b]
@@ -355,30 +384,34 @@ __device__ double env_row_step(const Geo& g, const T* Eprev, T* Eout, const T* T
         const T* Ec = w.E + u * chi + b;
         T s = 0;
         for (int a = 0; a < chi; ++a) s += Rr[a * D] * Ec[a * D * chi];
-        w.W[o] = s;
+        w.W[(size_t)ii * WS + (l * D + u) * chi + b] = s;
       }
       __syncthreads();
-      // Z[(i0+ii, d)][(b, r)] = sum_{l,u} W[ii][l][u][b] A[l][u][r][d]
+      // Z[(i0+ii, d)][(b, r)] = sum_{l,u} W[ii][l][u][b] A[l][u][r][d]; consecutive threads walk
+      // down a column of the column-major Z
       const int nZ = ci * D * n;
       for (int o = tid; o < nZ; o += NT) {
-        const int r = o % D, b = (o / D) % chi, dd = (o / n) % D, ii = o / (n * D);
-        const T* Wr = w.W + (size_t)ii * D * D * chi + b;
+        const int dd = o % D, ii = (o / D) % ci, col = o / (D * ci), b = col / D, r = col % D;
+        const T* Wr = w.W + (size_t)ii * WS + b;
         T s = 0;
         for (int lu = 0; lu < D * D; ++lu) s += Wr[lu * chi] * w.A[(lu * D + r) * D + dd];
-        w.Z[((size_t)(i0 + ii) * D + dd) * n + b * D + r] = s;
+        w.Z[(size_t)col * mZ + (i0 + ii) * D + dd] = s;
       }
       __syncthreads();
     }
-    qr_keep_r(w.Z, n * D, n, w.R, w.red);
+    qr_keep_r(w.Z, mZ, n, w.R, w.red);
     blk_copy(w.Rhist + (size_t)k * n * n, w.R, n * n);
     __syncthreads();
   }
   // ---- right pass
+  // Y, X and Vt rows are padded to LY = Lr + 1 so that rows read side by side hit different
+  // shared-memory banks
+  const int LY = Lr + 1;
   T* P = w.Z;                              // chi*D*D*chi
-  T* Y = P + (size_t)chi * D * D * chi;    // n x Lr
-  T* X = Y + (size_t)n * Lr;               // mX x Lr
-  T* Vt = X + (size_t)mX * Lr;             // chi x Lr
-  T* Cn = Vt + (size_t)chi * Lr;           // n x chi
+  T* Y = P + (size_t)chi * D * D * chi;    // n x Lr   (ld LY)
+  T* X = Y + (size_t)n * LY;               // mX x Lr  (ld LY)
+  T* Vt = X + (size_t)mX * LY;             // chi x Lr (ld LY)
+  T* Cn = Vt + (size_t)chi * LY;           // n x chi
   T* Bs = Cn + (size_t)n * chi;            // chi x D x chi (site being written)
   // C_{Ly-1}[(b,r)][c] = delta_{(b,r),0} delta_{c,0}
   blk_unit(w.C, n * chi);
@@ -424,7 +457,7 @@ __device__ double env_row_step(const Geo& g, const T* Eprev, T* Eout, const T* T
       const T* Ar = w.A + (size_t)l * D * D * D + dd;
       T s = 0;
       for (int ur = 0; ur < D * D; ++ur) s += Pr[ur * chi] * Ar[ur * D];
-      Y[o] = s;
+      Y[(size_t)(o / Lr) * LY + o % Lr] = s;
     }
     // R_{k-1} from the left pass
     blk_copy(w.R, w.Rhist + (size_t)(k - 1) * n * n, n * n);
@@ -434,18 +467,18 @@ __device__ double env_row_step(const Geo& g, const T* Eprev, T* Eout, const T* T
       const int q = o % Lr, i = o / Lr;
       T s = 0;
       if (i < n)
-        for (int j = i; j < n; ++j) s += w.R[(size_t)i * n + j] * Y[(size_t)j * Lr + q];
-      X[o] = s;
+        for (int j = i; j < n; ++j) s += w.R[(size_t)i * n + j] * Y[(size_t)j * LY + q];
+      X[(size_t)i * LY + q] = s;
     }
     __syncthreads();
-    const int sweeps = hestenes_rows(X, mX, Lr, Lr, flag, w.ctr, w.red);
+    const int sweeps = hestenes_rows(X, mX, Lr, LY, flag, w.ctr, w.red, w.sig);
     if (sweeps < 0 && tid == 0) *st |= ST_NOCONV;
     // singular values = row norms
     {
       const int lane = tid & 31, warp = tid >> 5, nw = NT >> 5;
       for (int p = warp; p < mX; p += nw) {
         T s = 0;
-        for (int i = lane; i < Lr; i += 32) s += X[(size_t)p * Lr + i] * X[(size_t)p * Lr + i];
+        for (int i = lane; i < Lr; i += 32) s += X[(size_t)p * LY + i] * X[(size_t)p * LY + i];
         s = warp_sum(s);
         if (lane == 0) w.sig[p] = sqrt(s);
       }
@@ -494,21 +527,21 @@ __device__ double env_row_step(const Geo& g, const T* Eprev, T* Eout, const T* T
       if (cp < nkeep) {
         const int p = w.sel[cp];
         const T s = w.sig[p];
-        if (s > T(0)) v = X[(size_t)p * Lr + q] / s;
+        if (s > T(0)) v = X[(size_t)p * LY + q] / s;
       }
-      Vt[o] = v;
+      Vt[(size_t)cp * LY + q] = v;
     }
     __syncthreads();
     // C_{k-1}[j][c'] = sum_q Y[j][q] Vt[c'][q];  new site B[c'][d][c] = Vt[c'][(d,c)]
     for (int o = tid; o < n * chi; o += NT) {
       const int cp = o % chi, j = o / chi;
-      const T* Yr = Y + (size_t)j * Lr;
-      const T* Vr = Vt + (size_t)cp * Lr;
+      const T* Yr = Y + (size_t)j * LY;
+      const T* Vr = Vt + (size_t)cp * LY;
       T s = 0;
       for (int q = 0; q < Lr; ++q) s += Yr[q] * Vr[q];
       Cn[o] = s;
     }
-    for (int o = tid; o < g.se; o += NT) Bs[o] = Vt[o];  // layouts coincide: [c'][d][c]
+    for (int o = tid; o < g.se; o += NT) Bs[o] = Vt[(size_t)(o / Lr) * LY + o % Lr];  // [c'][d][c]
     __syncthreads();
     logsum += blk_normalize(Bs, g.se, w.red, st);
     blk_copy(Eout + (size_t)k * g.se, Bs, g.se);

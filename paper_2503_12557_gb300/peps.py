@@ -63,6 +63,9 @@ def load():
         "peps_sample": ([vp, i32, vp, i32, i32, C.c_uint64, C.c_uint64, vp, vp, vp], i32),
         "peps_last_error": ([vp], C.c_char_p),
         "peps_apply_update": ([vp, vp, vp, vp], i32),
+        "peps_proposal_logits": ([i32, i32, i32, i32, vp, vp, i32, vp, vp], i32),
+        "peps_proposal_train_step": ([i32, i32, i32, i32, vp, vp, vp, vp, i32, dbl, vp, vp, i32, vp, vp, vp], i32),
+        "peps_sample_learned": ([vp, i32, i32, vp, vp, vp, i32, C.c_uint64, C.c_uint64, vp, vp, vp], i32),
         "peps_timing_enable": ([vp, i32], i32),
         "peps_timing_read": ([vp, vp, vp, i32, vp], i32),
     }
@@ -77,7 +80,46 @@ def load():
 def exported_symbols():
     return ["peps_create", "peps_destroy", "peps_num_params", "peps_set_params", "peps_amplitudes",
             "peps_local_energy", "peps_logderiv", "peps_evaluate", "minsr_step", "peps_sample", "peps_last_error",
-            "peps_timing_enable", "peps_timing_read", "peps_apply_update"]
+            "peps_timing_enable", "peps_timing_read", "peps_apply_update", "peps_proposal_logits",
+            "peps_proposal_train_step", "peps_sample_learned"]
+
+
+class Proposal:
+    """Weights and Adam state of the learned proposal network (device tensors)."""
+
+    def __init__(self, Lx, Ly, w0, C=16, wprec=1):
+        self.L = load()
+        self.Lx, self.Ly, self.C, self.wprec = Lx, Ly, C, wprec
+        self.w = torch.as_tensor(np.asarray(w0, dtype=np.float64)).cuda().contiguous()
+        self.m = torch.zeros_like(self.w)
+        self.v = torch.zeros_like(self.w)
+        self.g = torch.zeros_like(self.w)
+        self.loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+        self.wlow = self.w.to(torch.bfloat16).contiguous() if wprec == 1 else None
+        self.t = 0
+
+    @property
+    def wdev(self):
+        return self.w if self.wprec == 0 else self.wlow
+
+    def logits(self, S):
+        ns = S.shape[0]
+        out = torch.empty(ns, self.Lx * self.Ly, dtype=torch.float64, device=S.device)
+        st = self.L.peps_proposal_logits(self.Lx, self.Ly, self.C, self.wprec, _ptr(self.wdev), _ptr(S.contiguous()),
+                                         ns, _ptr(out), _stream())
+        if st != 0:
+            raise RuntimeError(f"peps_proposal_logits failed: {_ERRORS.get(st, st)}")
+        return out
+
+    def train_step(self, S_in, S_tgt, lr=1e-3):
+        self.t += 1
+        st = self.L.peps_proposal_train_step(self.Lx, self.Ly, self.C, self.wprec, _ptr(self.w), _ptr(self.m),
+                                             _ptr(self.v), _ptr(self.wlow), self.t, float(lr), _ptr(S_in.contiguous()),
+                                             _ptr(S_tgt.contiguous()), S_in.shape[0], _ptr(self.g), _ptr(self.loss),
+                                             _stream())
+        if st != 0:
+            raise RuntimeError(f"peps_proposal_train_step failed: {_ERRORS.get(st, st)}")
+        return self.loss
 
 
 TIMING_CLASSES = ["env", "row", "pair", "combine", "sample", "minsr_gram", "minsr_eig", "minsr_other", "pad"]
@@ -228,6 +270,16 @@ class PEPS:
         self._check(self.L.peps_apply_update(self.h, _ptr(theta), _ptr(dtheta.contiguous()), _stream()),
                     "peps_apply_update")
         self._theta_ref = theta
+
+    def sample_learned(self, prop, S, logpsi, seed=0, step=0, accepted=None):
+        """One network move of every chain (S and logpsi updated in place)."""
+        S = self._S(S)
+        ns = S.shape[0]
+        st = torch.empty(ns, dtype=torch.int32, device=S.device)
+        self._check(self.L.peps_sample_learned(self.h, prop.C, prop.wprec, _ptr(prop.wdev), _ptr(S), _ptr(logpsi), ns,
+                                               int(seed) & (2 ** 64 - 1), int(step), _ptr(accepted), _ptr(st),
+                                               _stream()), "peps_sample_learned")
+        return S, logpsi, st
 
     def timing(self, enable=True):
         self._check(self.L.peps_timing_enable(self.h, 1 if enable else 0), "peps_timing_enable")
