@@ -133,6 +133,33 @@ static void place(Plan& p, size_t& smem, size_t budget, const std::vector<std::p
   p.gstride = gl;
 }
 
+// As place(), for the sampler: the `common` buffers first, then two groups that are never live
+// at the same time (the boundary-MPS row step and the sandwich partials) overlaid on the same
+// shared-memory region.
+static void place_overlay(Plan& p, size_t& smem, size_t budget, const std::vector<std::pair<int, size_t>>& common,
+                          const std::vector<std::pair<int, size_t>>& ga, const std::vector<std::pair<int, size_t>>& gb) {
+  p.gmask = 0;
+  for (int b = 0; b < B_NBUF; ++b) p.off[b] = 0;
+  size_t s = 0, gl = 0;
+  auto put1 = [&](const std::pair<int, size_t>& b, size_t& cur) {
+    const size_t sz = al(b.second, 16);
+    if (cur + sz <= budget) {
+      p.off[b.first] = cur;
+      cur += sz;
+    } else {
+      p.gmask |= 1u << b.first;
+      p.off[b.first] = gl;
+      gl += al(sz, 256);
+    }
+  };
+  for (auto& b : common) put1(b, s);
+  size_t sa = s, sb = s;
+  for (auto& b : ga) put1(b, sa);
+  for (auto& b : gb) put1(b, sb);
+  smem = std::max(sa, sb);
+  p.gstride = gl;
+}
+
 static void plan_all(peps_handle* h) {
   const Geo& g = h->g;
   const size_t E = h->esz;
@@ -186,28 +213,33 @@ static void plan_all(peps_handle* h) {
     KPlan& k = h->kp[3];
     k.p.ci = ci;
     k.p.cx = cx;
-    const size_t tt = std::max(t1row, t2row);
+    int cxs = cx;
+    while (cxs > 1 && (size_t)D * D * D * chi * cxs > 4096) cxs = (cxs + 1) / 2;
+    k.p.cx = cxs;
+    const size_t tt = std::max(t1row, (size_t)D * D * D * chi * cxs);
     const size_t lw = std::max((size_t)g.s2, (size_t)g.se);
-    std::vector<std::pair<int, size_t>> b = {
-        {B_RED, 40 * 8}, {B_SIG, (mX + 4) * E}, {B_SEL, 2 * mX * 4}, {B_S, (size_t)g.Lx * g.Ly},
-        {B_A, (size_t)g.sT * E}, {B_A2, (size_t)g.sT * E}, {B_E, (size_t)g.se * E}, {B_EU, (size_t)g.se * E},
-        {B_EL, (size_t)g.se * E}, {B_C, (size_t)n * chi * E}, {B_W, env_w_elems(chi, D, ci) * E},
-        {B_T1, tt * E}, {B_T2, tt * E}, {B_LW, lw * E}, {B_LW2, lw * E}, {B_LP, lw * E},
-        {B_R, (size_t)n * n * E}, {B_Z, zsz * E}, {B_RP, (size_t)(Ly + 1) * lw * E},
-        {B_RHIST, (size_t)std::max(1, Ly - 1) * n * n * E}};
-    place(k.p, k.smem, budget, b);
+    // the row step (E^u / E^l updates) and the move sandwiches never overlap in time
+    std::vector<std::pair<int, size_t>> common = {
+        {B_RED, 40 * 8}, {B_SIG, (mX + 4) * E}, {B_SEL, 2 * mX * 4}, {B_S, (size_t)g.Lx * g.Ly}, {B_A, (size_t)g.sT * E}};
+    std::vector<std::pair<int, size_t>> rowstep = {
+        {B_E, (size_t)g.se * E}, {B_C, (size_t)n * chi * E}, {B_W, env_w_elems(chi, D, ci) * E},
+        {B_R, (size_t)n * n * E}, {B_Z, zsz * E}, {B_RHIST, (size_t)std::max(1, Ly - 1) * n * n * E}};
+    std::vector<std::pair<int, size_t>> sandwich = {
+        {B_A2, (size_t)g.sT * E}, {B_EU, (size_t)g.se * E}, {B_EL, (size_t)g.se * E}, {B_T1, tt * E},
+        {B_T2, tt * E}, {B_LW, lw * E}, {B_LW2, lw * E}, {B_LP, lw * E}, {B_RP, (size_t)(Ly + 1) * lw * E}};
+    place_overlay(k.p, k.smem, budget, common, rowstep, sandwich);
   }
 }
 
 static peps_status finish_plans(peps_handle* h) {
   size_t maxsmem = 0;
   for (auto& k : h->kp) maxsmem = std::max(maxsmem, k.smem);
-  cudaError_t e = (h->esz == 8) ? set_kernel_smem<double>(maxsmem) : set_kernel_smem<float>(maxsmem);
+  cudaError_t e = (h->esz == 8) ? set_kernel_smem<double>(h->g, maxsmem) : set_kernel_smem<float>(h->g, maxsmem);
   if (e != cudaSuccess) return cuda_fail(h, e, "cudaFuncSetAttribute");
   size_t gmax = 0;
   for (int i = 0; i < 4; ++i) {
     KPlan& k = h->kp[i];
-    int occ = (h->esz == 8) ? occupancy<double>(i, k.smem) : occupancy<float>(i, k.smem);
+    int occ = (h->esz == 8) ? occupancy<double>(h->g, i, k.smem) : occupancy<float>(h->g, i, k.smem);
     if (occ < 1) return fail(h, PEPS_E_SHAPE, "kernel does not fit on an SM");
     k.grid = h->nsm * occ;
     gmax = std::max(gmax, (size_t)k.grid * (size_t)k.p.gstride);

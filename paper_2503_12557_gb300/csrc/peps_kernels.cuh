@@ -50,9 +50,9 @@ cudaError_t launch_combine(const Geo& g, int Ns, const uint8_t* S, const double*
                            int use_rows_all, int use_pairs, const DiagTab& dg, double* logabs, double* phase,
                            double* eloc, cudaStream_t s);
 template <typename T>
-cudaError_t set_kernel_smem(size_t bytes);
+cudaError_t set_kernel_smem(const Geo& g, size_t bytes);
 template <typename T>
-int occupancy(int which, size_t smem);
+int occupancy(const Geo& g, int which, size_t smem);
 
 // ---- MinSR (FP64)
 // column means m_k = sum_S w_S O_{S,k} (w normalised), and Obar = sqrt(w)(O - m) written as

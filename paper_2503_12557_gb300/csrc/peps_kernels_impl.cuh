@@ -2,6 +2,9 @@
 // sandwiches (amplitudes, local-energy ratios, log-derivatives), per-sample combine, and the
 // Metropolis sweep.  All kernels are persistent: each CTA loops over work items
 // (blockIdx.x, blockIdx.x + gridDim.x, ...) and owns one slice of the global scratch arena.
+// Included by peps_kernels_f64.cu and peps_kernels_f32.cu, which instantiate it for one real
+// type each (two translation units compile in parallel).
+#pragma once
 #include "peps_kernels.cuh"
 
 namespace peps {
@@ -9,9 +12,12 @@ namespace peps {
 // ------------------------------------------------------------------------------------------
 // environment store: per sample 2*Lx rows of Ly sites; slot x+1 holds E^u[x] (x = -1..Lx-2),
 // slot Lx+x-1 holds E^l[x] (x = 1..Lx).  logs: cumulative log factor of every slot.
-__host__ __device__ inline size_t env_sample_elems(const Geo& g) { return (size_t)2 * g.Lx * g.Ly * g.se; }
-__device__ inline int slot_up(const Geo& g, int x) { return x + 1; }
-__device__ inline int slot_lo(const Geo& g, int x) { return g.Lx + x - 1; }
+template <typename G>
+__host__ __device__ inline size_t env_sample_elems(const G& g) { return (size_t)2 * g.Lx * g.Ly * g.se; }
+template <typename G>
+__device__ inline int slot_up(const G& g, int x) { return x + 1; }
+template <typename G>
+__device__ inline int slot_lo(const G& g, int x) { return g.Lx + x - 1; }
 
 template <typename T>
 __device__ RowWork<T> carve_row(const Plan& p, char* smem, char* gbase) {
@@ -32,8 +38,8 @@ __device__ RowWork<T> carve_row(const Plan& p, char* smem, char* gbase) {
 }
 
 // Upper environments E^u[-1..Lx-2] of configuration Ss into env (one sample's store).
-template <typename T>
-__device__ void build_upper(const Geo& g, const T* Tpad, const uint8_t* Ss, T* env, double* logs,
+template <typename T, typename G>
+__device__ void build_upper(const G& g, const T* Tpad, const uint8_t* Ss, T* env, double* logs,
                             const RowWork<T>& w, int* st, float* wd, int* flag) {
   const size_t row = (size_t)g.Ly * g.se;
   // trivial E^u[-1], and the trivial E^l[Lx] that closes psi_top = E^u[Lx-2] . T_proj[Lx-1]
@@ -56,8 +62,8 @@ __device__ void build_upper(const Geo& g, const T* Tpad, const uint8_t* Ss, T* e
 }
 
 // Lower environments E^l[2..Lx] (and E^l[1] when full) of configuration Ss.
-template <typename T>
-__device__ void build_lower(const Geo& g, const T* Tpad, const uint8_t* Ss, T* env, double* logs,
+template <typename T, typename G>
+__device__ void build_lower(const G& g, const T* Tpad, const uint8_t* Ss, T* env, double* logs,
                             const RowWork<T>& w, int* st, float* wd, int* flag, int xmin) {
   const size_t row = (size_t)g.Ly * g.se;
   T* trivial = env + (size_t)slot_lo(g, g.Lx) * row;
@@ -75,8 +81,8 @@ __device__ void build_lower(const Geo& g, const T* Tpad, const uint8_t* Ss, T* e
   __syncthreads();
 }
 
-template <typename T>
-__global__ void __launch_bounds__(NTHREADS) k_env(Geo g, Plan plan, const T* __restrict__ Tpad,
+template <typename T, typename G>
+__global__ void __launch_bounds__(NTHREADS) k_env(G g, Plan plan, const T* __restrict__ Tpad,
                                                   const uint8_t* __restrict__ S, int Ns, int sides, T* envs,
                                                   double* logs, int* status, float* wdisc) {
   extern __shared__ __align__(16) char smem[];
@@ -106,7 +112,8 @@ __global__ void __launch_bounds__(NTHREADS) k_env(Geo g, Plan plan, const T* __r
 
 // ------------------------------------------------------------------------------------------
 // Sandwich bookkeeping shared by the row and pair kernels.
-__device__ inline void site_dims(const Geo& g, int x, int y, int* Dl, int* Du, int* Dr, int* Dd) {
+template <typename G>
+__device__ inline void site_dims(const G& g, int x, int y, int* Dl, int* Du, int* Dr, int* Dd) {
   *Dl = (y == 0) ? 1 : g.D;
   *Du = (x == 0) ? 1 : g.D;
   *Dr = (y == g.Ly - 1) ? 1 : g.D;
@@ -132,8 +139,8 @@ __device__ inline int local_index(const int* ti, const uint8_t* Ss, int d) {
 
 // ------------------------------------------------------------------------------------------
 // One-row sandwich at row x of sample smp: psi_x, O of row x, E_loc terms inside row x.
-template <typename T>
-__global__ void __launch_bounds__(NTHREADS) k_row(Geo g, Plan plan, const T* __restrict__ Tpad,
+template <typename T, typename G>
+__global__ void __launch_bounds__(NTHREADS) k_row(G g, Plan plan, const T* __restrict__ Tpad,
                                                   const uint8_t* __restrict__ S, int Ns, int x_lo, int x_hi,
                                                   const T* envs, const double* logs, T* O, const long long* site_off,
                                                   long long Np, TermTab tt, double* rowout, int* status) {
@@ -268,8 +275,8 @@ __global__ void __launch_bounds__(NTHREADS) k_row(Geo g, Plan plan, const T* __r
 
 // ------------------------------------------------------------------------------------------
 // Two-row sandwich at rows x, x+1: psi_{x,x+1} and the E_loc terms spanning the two rows.
-template <typename T>
-__global__ void __launch_bounds__(NTHREADS) k_pair(Geo g, Plan plan, const T* __restrict__ Tpad,
+template <typename T, typename G>
+__global__ void __launch_bounds__(NTHREADS) k_pair(G g, Plan plan, const T* __restrict__ Tpad,
                                                    const uint8_t* __restrict__ S, int Ns, const T* envs,
                                                    const double* logs, TermTab tt, double* pairout, int* status) {
   extern __shared__ __align__(16) char smem[];
@@ -380,6 +387,7 @@ __global__ void __launch_bounds__(NTHREADS) k_pair(Geo g, Plan plan, const T* __
   }
 }
 
+#ifdef PEPS_DEFINE_COMMON
 // ------------------------------------------------------------------------------------------
 // Per-sample combine: ln psi_top from row Lx-1, E_loc = diagonal + row terms + pair terms.
 // One warp per sample.
@@ -417,11 +425,12 @@ __global__ void k_combine(Geo g, int Ns, const uint8_t* __restrict__ S, const do
     }
   }
 }
+#endif
 
 // ------------------------------------------------------------------------------------------
 // Metropolis sweeps: one CTA per chain (persistent over chains).
-template <typename T>
-__global__ void __launch_bounds__(NTHREADS) k_sample(Geo g, Plan plan, const T* __restrict__ Tpad, uint8_t* S,
+template <typename T, typename G>
+__global__ void __launch_bounds__(NTHREADS) k_sample(G g, Plan plan, const T* __restrict__ Tpad, uint8_t* S,
                                                      int Ns, int move, int nsweeps, unsigned long long seed,
                                                      unsigned long long sweep0, T* envs, double* logs,
                                                      long long* accepted, int* status) {
@@ -641,38 +650,58 @@ __global__ void k_pad_theta(Geo g, const double* __restrict__ theta, const long 
 }
 
 // ------------------------------------------------------------------------------------------
-// host-side launch wrappers (explicit instantiations for double and float)
+// host-side launch wrappers (explicit instantiations for double and float).  Every launch goes
+// to the kernel instantiated for the handle's (chi, D) when one exists, else to the runtime-
+// geometry kernel.
+template <typename F>
+static cudaError_t with_geo(const Geo& g, F&& f) {
+  if (g.chi == 16 && g.D == 4) return f(GeoS<16, 4>{g.Lx, g.Ly, g.d});
+  if (g.chi == 24 && g.D == 4) return f(GeoS<24, 4>{g.Lx, g.Ly, g.d});
+  return f(g);
+}
+
 template <typename T>
 cudaError_t launch_env(const Geo& g, const Plan& p, int grid, size_t smem, const T* Tpad, const uint8_t* S, int Ns,
                        int sides, T* envs, double* logs, int* status, float* wdisc, cudaStream_t s) {
-  k_env<T><<<grid, NTHREADS, smem, s>>>(g, p, Tpad, S, Ns, sides, envs, logs, status, wdisc);
-  return cudaGetLastError();
+  return with_geo(g, [&](auto gg) {
+    k_env<T, decltype(gg)><<<grid, NTHREADS, smem, s>>>(gg, p, Tpad, S, Ns, sides, envs, logs, status, wdisc);
+    return cudaGetLastError();
+  });
 }
 template <typename T>
 cudaError_t launch_row(const Geo& g, const Plan& p, int grid, size_t smem, const T* Tpad, const uint8_t* S, int Ns,
                        int x_lo, int x_hi, const T* envs, const double* logs, T* O, const long long* site_off,
                        long long Np, const TermTab& tt, double* rowout, int* status, cudaStream_t s) {
-  k_row<T><<<grid, NTHREADS, smem, s>>>(g, p, Tpad, S, Ns, x_lo, x_hi, envs, logs, O, site_off, Np, tt, rowout, status);
-  return cudaGetLastError();
+  return with_geo(g, [&](auto gg) {
+    k_row<T, decltype(gg)><<<grid, NTHREADS, smem, s>>>(gg, p, Tpad, S, Ns, x_lo, x_hi, envs, logs, O, site_off, Np,
+                                                        tt, rowout, status);
+    return cudaGetLastError();
+  });
 }
 template <typename T>
 cudaError_t launch_pair(const Geo& g, const Plan& p, int grid, size_t smem, const T* Tpad, const uint8_t* S, int Ns,
                         const T* envs, const double* logs, const TermTab& tt, double* pairout, int* status, cudaStream_t s) {
-  k_pair<T><<<grid, NTHREADS, smem, s>>>(g, p, Tpad, S, Ns, envs, logs, tt, pairout, status);
-  return cudaGetLastError();
+  return with_geo(g, [&](auto gg) {
+    k_pair<T, decltype(gg)><<<grid, NTHREADS, smem, s>>>(gg, p, Tpad, S, Ns, envs, logs, tt, pairout, status);
+    return cudaGetLastError();
+  });
 }
 template <typename T>
 cudaError_t launch_sample(const Geo& g, const Plan& p, int grid, size_t smem, const T* Tpad, uint8_t* S, int Ns,
                           int move, int nsweeps, unsigned long long seed, unsigned long long sweep0, T* envs,
                           double* logs, long long* accepted, int* status, cudaStream_t s) {
-  k_sample<T><<<grid, NTHREADS, smem, s>>>(g, p, Tpad, S, Ns, move, nsweeps, seed, sweep0, envs, logs, accepted, status);
-  return cudaGetLastError();
+  return with_geo(g, [&](auto gg) {
+    k_sample<T, decltype(gg)><<<grid, NTHREADS, smem, s>>>(gg, p, Tpad, S, Ns, move, nsweeps, seed, sweep0, envs, logs,
+                                                           accepted, status);
+    return cudaGetLastError();
+  });
 }
 template <typename T>
 cudaError_t launch_pad(const Geo& g, const double* theta, const long long* site_off, T* Tpad, cudaStream_t s) {
   k_pad_theta<T><<<304, 256, 0, s>>>(g, theta, site_off, Tpad);
   return cudaGetLastError();
 }
+#ifdef PEPS_DEFINE_COMMON
 cudaError_t launch_combine(const Geo& g, int Ns, const uint8_t* S, const double* rowout, const double* pairout,
                            int use_rows_all, int use_pairs, const DiagTab& dg, double* logabs, double* phase,
                            double* eloc, cudaStream_t s) {
@@ -680,25 +709,33 @@ cudaError_t launch_combine(const Geo& g, int Ns, const uint8_t* S, const double*
   k_combine<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(g, Ns, S, rowout, pairout, use_rows_all, use_pairs, dg, logabs, phase, eloc);
   return cudaGetLastError();
 }
+#endif
 
 template <typename T>
-cudaError_t set_kernel_smem(size_t bytes) {
-  cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_env<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(k_row<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(k_pair<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)) != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_sample<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+cudaError_t set_kernel_smem(const Geo& g, size_t bytes) {
+  return with_geo(g, [&](auto gg) {
+    using GG = decltype(gg);
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_env<T, GG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_row<T, GG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_pair<T, GG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)) != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_sample<T, GG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  });
 }
 
 template <typename T>
-int occupancy(int which, size_t smem) {
+int occupancy(const Geo& g, int which, size_t smem) {
   int nb = 0;
-  switch (which) {
-    case 0: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_env<T>, NTHREADS, smem); break;
-    case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_row<T>, NTHREADS, smem); break;
-    case 2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pair<T>, NTHREADS, smem); break;
-    default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sample<T>, NTHREADS, smem); break;
-  }
+  with_geo(g, [&](auto gg) {
+    using GG = decltype(gg);
+    switch (which) {
+      case 0: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_env<T, GG>, NTHREADS, smem); break;
+      case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_row<T, GG>, NTHREADS, smem); break;
+      case 2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pair<T, GG>, NTHREADS, smem); break;
+      default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sample<T, GG>, NTHREADS, smem); break;
+    }
+    return cudaSuccess;
+  });
   return nb;
 }
 
@@ -714,10 +751,7 @@ int occupancy(int which, size_t smem) {
                                         unsigned long long, unsigned long long, T*, double*, long long*, int*,    \
                                         cudaStream_t);                                                            \
   template cudaError_t launch_pad<T>(const Geo&, const double*, const long long*, T*, cudaStream_t);              \
-  template cudaError_t set_kernel_smem<T>(size_t);                                                                \
-  template int occupancy<T>(int, size_t);
-
-PEPS_INST(double)
-PEPS_INST(float)
+  template cudaError_t set_kernel_smem<T>(const Geo&, size_t);                                                    \
+  template int occupancy<T>(const Geo&, int, size_t);
 
 }  // namespace peps

@@ -44,6 +44,16 @@ struct Geo {
   int s2;  // chi*D*D*chi, one two-row partial
 };
 
+// The same geometry with (chi, D) fixed at compile time: every device routine below is a
+// template over the geometry type, so with GeoS the index arithmetic and loop bounds fold to
+// constants.  Used for the configurations the library is tuned for; Geo covers the rest.
+template <int CHI, int DD>
+struct GeoS {
+  int Lx, Ly, d;
+  static constexpr int D = DD, chi = CHI, n = CHI * DD, se = CHI * DD * CHI, sT = DD * DD * DD * DD,
+                       s2 = CHI * DD * DD * CHI;
+};
+
 // ------------------------------------------------------------------------------------------
 // buffer plan: every kernel carves its buffers out of dynamic shared memory or out of a
 // per-CTA slice of a global scratch arena, as the host planner decided.
@@ -153,8 +163,8 @@ __device__ double blk_normalize(T* v, int n, double* red, int* st) {
 
 // Projected PEPS tensor of site `site` with local state s, as A[l][u][r][d] (swap_ud: as
 // A[l][d][r][u], the lower-environment orientation).
-template <typename T>
-__device__ void load_A(T* As, const T* Tpad, const Geo& g, int site, int s, bool swap_ud) {
+template <typename T, typename G>
+__device__ void load_A(T* As, const T* Tpad, const G& g, int site, int s, bool swap_ud) {
   const T* src = Tpad + ((size_t)site * g.d + s) * g.sT;
   const int D = g.D;
   for (int o = threadIdx.x; o < g.sT; o += blockDim.x) {
@@ -357,8 +367,8 @@ struct RowWork {
 //   Srow: the Ly local states of the applied row; lower: lower-environment orientation.
 // Returns the sum of the Ly log factors; *st collects status bits; *wdisc the largest
 // discarded weight (sum of discarded sigma^2 over sum of sigma^2) of any cut.
-template <typename T>
-__device__ double env_row_step(const Geo& g, const T* Eprev, T* Eout, const T* Tpad, int row,
+template <typename T, typename G>
+__device__ double env_row_step(const G& g, const T* Eprev, T* Eout, const T* Tpad, int row,
                                const uint8_t* Srow, bool lower, const RowWork<T>& w, int* st,
                                float* wdisc, int* flag) {
   const int chi = g.chi, D = g.D, n = g.n, Ly = g.Ly;
@@ -553,8 +563,8 @@ __device__ double env_row_step(const Geo& g, const T* Eprev, T* Eout, const T* T
 
 // First environment row: row 0 read as an MPS (upper side, e[a=l][p=d][b=r] = A[l][0][r][d])
 // or row Lx-1 (lower side, e[l][u][r] = A[l][u][r][0]); every site normalised.
-template <typename T>
-__device__ double env_first_row(const Geo& g, T* Eout, const T* Tpad, int row, const uint8_t* Srow,
+template <typename T, typename G>
+__device__ double env_first_row(const G& g, T* Eout, const T* Tpad, int row, const uint8_t* Srow,
                                 bool lower, T* Abuf, T* Bs, double* red, int* st) {
   const int chi = g.chi, D = g.D;
   double logsum = 0.0;
@@ -577,8 +587,8 @@ __device__ double env_first_row(const Geo& g, T* Eout, const T* Tpad, int row, c
 // ------------------------------------------------------------------------------------------
 // One-row sandwich partials.  L[a][l][b] -> L'[x][r][z] over one column with eu[a][u][x],
 // A[l][u][r][d], el[b][d][z].  t1, t2: chi*chi*D*D each.
-template <typename T>
-__device__ void absorb1(const Geo& g, const T* L, const T* eu, const T* A, const T* el, T* t1, T* t2, T* out) {
+template <typename T, typename G>
+__device__ void absorb1(const G& g, const T* L, const T* eu, const T* A, const T* el, T* t1, T* t2, T* out) {
   const int chi = g.chi, D = g.D, NT = blockDim.x, tid = threadIdx.x;
   const int n1 = D * chi * D * chi;
   // t1[l][b][u][x] = sum_a L[a][l][b] eu[a][u][x]
@@ -610,8 +620,8 @@ __device__ void absorb1(const Geo& g, const T* L, const T* eu, const T* A, const
 }
 
 // R[x][r][z] -> R'[a][l][b] = sum eu[a][u][x] A[l][u][r][d] el[b][d][z] R[x][r][z]
-template <typename T>
-__device__ void absorb1_right(const Geo& g, const T* R, const T* eu, const T* A, const T* el, T* t1, T* t2, T* out) {
+template <typename T, typename G>
+__device__ void absorb1_right(const G& g, const T* R, const T* eu, const T* A, const T* el, T* t1, T* t2, T* out) {
   const int chi = g.chi, D = g.D, NT = blockDim.x, tid = threadIdx.x;
   const int n1 = chi * D * D * chi;
   // t1[a][u][r][z] = sum_x eu[a][u][x] R[x][r][z]
@@ -644,8 +654,8 @@ __device__ void absorb1_right(const Geo& g, const T* R, const T* eu, const T* A,
 
 // Site environment of the one-row sandwich: env[l][u][r][d] = sum L[a][l][b] eu[a][u][x]
 // el[b][d][z] R[x][r][z]  (= d psi_x / d A[l][u][r][d]).
-template <typename T>
-__device__ void site_env1(const Geo& g, const T* L, const T* eu, const T* el, const T* R, T* t1, T* t2, T* env) {
+template <typename T, typename G>
+__device__ void site_env1(const G& g, const T* L, const T* eu, const T* el, const T* R, T* t1, T* t2, T* env) {
   const int chi = g.chi, D = g.D, NT = blockDim.x, tid = threadIdx.x;
   const int n1 = D * chi * D * chi;
   // t1[l][b][u][x] = sum_a L[a][l][b] eu[a][u][x]
@@ -685,8 +695,8 @@ __device__ T blk_dot(const T* a, const T* b, int n, double* red) {
 // Two-row sandwich partials, chunked over the new upper bond (absorb2) / the old upper bond
 // (absorb2_right) so that the temporaries hold D^3 chi cx elements.
 // L2[a][i][j][b] -> out[x][r1][r2][z] with eu[a][u][x], A1[i][u][r1][v], A2[j][v][r2][d], el[b][d][z]
-template <typename T>
-__device__ void absorb2(const Geo& g, const T* L2, const T* eu, const T* A1, const T* A2, const T* el,
+template <typename T, typename G>
+__device__ void absorb2(const G& g, const T* L2, const T* eu, const T* A1, const T* A2, const T* el,
                         T* t1, T* t2, T* out, int cx) {
   const int chi = g.chi, D = g.D, NT = blockDim.x, tid = threadIdx.x;
   for (int x0 = 0; x0 < chi; x0 += cx) {
@@ -738,8 +748,8 @@ __device__ void absorb2(const Geo& g, const T* L2, const T* eu, const T* A1, con
 }
 
 // R2[x][r1][r2][z] -> out[a][i][j][b] = sum eu[a][u][x] A1[i][u][r1][v] A2[j][v][r2][d] el[b][d][z] R2[x][r1][r2][z]
-template <typename T>
-__device__ void absorb2_right(const Geo& g, const T* R2, const T* eu, const T* A1, const T* A2, const T* el,
+template <typename T, typename G>
+__device__ void absorb2_right(const G& g, const T* R2, const T* eu, const T* A1, const T* A2, const T* el,
                               T* t1, T* t2, T* out, int ca) {
   const int chi = g.chi, D = g.D, NT = blockDim.x, tid = threadIdx.x;
   for (int a0 = 0; a0 < chi; a0 += ca) {

@@ -126,6 +126,18 @@ def peps_random(lat: Lattice, seed: int, kind: str = "normal", scale: float = 1.
     return tensors_to_theta(lat, T)
 
 
+def peps_near_product(lat: Lattice, seed: int, amp: float = 0.3, noise: float = 0.05) -> np.ndarray:
+    """A PEPS close to a product state with a polarised local distribution: every tensor is
+    1.0 on the all-zero virtual index plus noise * N(0, 1), and the s = 1 slice is scaled by
+    `amp` (so P(s = 1) is about amp^2 / (1 + amp^2) per site, weakly correlated)."""
+    theta = peps_random(lat, seed, scale=noise, bias=1.0)
+    T = theta_to_tensors(lat, theta)
+    for x in range(lat.Lx):
+        for y in range(lat.Ly):
+            T[x][y][1:] *= amp
+    return theta
+
+
 # ----------------------------------------------------------------------------- configurations
 
 def configs_uniform_sz0(lat: Lattice, ns: int, seed: int) -> np.ndarray:
