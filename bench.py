@@ -40,6 +40,7 @@ def _args():
     ap.add_argument("--ns", type=int, default=None)
     ap.add_argument("--sweeps", type=int, default=2)
     ap.add_argument("--burnin", type=int, default=2)
+    ap.add_argument("--mode", default="step", choices=["step", "learned"])
     ap.add_argument("--cpu-samples", type=int, default=12)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -308,10 +309,69 @@ def run_gpu(a):
         dist.destroy_process_group()
 
 
+def run_learned(a):
+    """12x12 Rydberg (delta = 3, R_b = 1.7, D = 4, chi = 24) chains: local single-flip sweeps
+    against trained network moves (FP32 contractions, bf16 network), and local sweeps in FP64
+    as the plain comparator.  Prints one JSON line with tau_int of the Rydberg density, the
+    network's acceptance and effective samples per second (chains x steps / (2 tau_int x time))."""
+    import torch
+    from paper_2503_12557_gb300 import build, inputs as I, learned as Lr, peps as P
+    build.build()
+    w = I.WORKLOADS["rydberg12x12_D4_chi24"]
+    lat = I.Lattice(w["Lx"], w["Ly"], w["d"], w["D"])
+    ns = a.ns or 1024
+    theta = torch.as_tensor(I.peps_random(lat, w["seed_theta"], **w["init"])).cuda()
+    density = lambda s: s.float().mean(dim=1).cpu().numpy()  # noqa: E731
+    out = {"mode": "learned", "workload": f"12x12 Rydberg, D=4, chi=24, {ns} chains", "steps": a.steps}
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3, r
+
+    precs = ((P.PREC_FP32, "fp32"),) + (((P.PREC_FP64, "fp64"),) if a.prec == "fp64" else ())
+    for prec, tag in precs:
+        h = P.PEPS(lat.Lx, lat.Ly, 2, lat.D, w["chi"], prec=prec, max_samples=ns)
+        h.set_params(theta)
+        S = torch.zeros(ns, lat.nsites, dtype=torch.uint8, device="cuda")
+        S, _, _ = Lr.run_local(h, S, a.burnin, seed=w["seed_chain"], sweep0=0)
+        t, (S2, obs, acc) = timed(lambda: Lr.run_local(h, S.clone(), a.steps, seed=w["seed_chain"], sweep0=100,
+                                                     observe=density))
+        tau = Lr.tau_int(np.array(obs))
+        out[f"local_{tag}"] = {"tau_int": tau, "s_per_step": t / a.steps,
+                               "ess_per_s": ns * a.steps / (2 * tau * t), "density": float(np.mean(obs))}
+        if prec == P.PREC_FP32:
+            S_in, S_out, S = Lr.collect_pairs(h, S, 4, 2, seed=w["seed_chain"] + 1, sweep0=1000)
+            prop = P.Proposal(lat.Lx, lat.Ly, I.proposal_init(5), C=16, wprec=1)
+            tt, losses = timed(lambda: Lr.train(prop, S_in, S_out, 200, lr=3e-3, batch=4096))
+            lpsi, _, _ = h.amplitudes(S)
+            accn = torch.zeros(ns, dtype=torch.int64, device="cuda")
+            obsn = []
+
+            def net():
+                for k in range(a.steps):
+                    h.sample_learned(prop, S, lpsi, seed=w["seed_chain"] + 2, step=k, accepted=accn)
+                    obsn.append(density(S))
+
+            t, _ = timed(net)
+            tau = Lr.tau_int(np.array(obsn))
+            out["network_fp32_bf16"] = {"tau_int": tau, "s_per_step": t / a.steps,
+                                        "ess_per_s": ns * a.steps / (2 * tau * t), "density": float(np.mean(obsn)),
+                                        "acceptance": accn.sum().item() / (ns * a.steps),
+                                        "train_s": tt, "loss_first_last": [losses[0], losses[-1]]}
+        h.close()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     a = _args()
     if a.impl == "reference":
         run_reference(a)
+    elif a.mode == "learned":
+        run_learned(a)
     else:
         run_gpu(a)
 

@@ -183,37 +183,62 @@ __device__ void load_A(T* As, const T* Tpad, const G& g, int site, int s, bool s
 // row major, upper triangular, zero below the diagonal).  Reflector convention of LAPACK's
 // xLARFG (H = I - tau v v^T, v_0 = 1).
 template <typename T>
-__device__ void qr_keep_r(T* Z, int m, int nc, T* R, double* red) {
+__device__ __forceinline__ void qr_apply_reflector(const T* zj, int j, T tau, T* zc, int m, int lane) {
+  // zc <- (I - tau v v^T) zc with v = (1, zj[j+1..m))
+  T s = 0;
+  for (int i = j + 1 + lane; i < m; i += 32) s += zj[i] * zc[i];
+  s = warp_sum(s);
+  const T w = (s + zc[j]) * tau;
+  __syncwarp();
+  if (lane == 0) zc[j] -= w;
+  for (int i = j + 1 + lane; i < m; i += 32) zc[i] -= zj[i] * w;
+  __syncwarp();
+}
+
+// Blocked by panels of QB columns: warp 0 computes the panel's reflectors (applying each to
+// the rest of the panel), then every warp applies the panel's reflectors, in order, to the
+// trailing columns it owns.  Two block barriers per panel.  taus: at least nc entries.
+template <typename T>
+__device__ void qr_keep_r(T* Z, int m, int nc, T* R, T* taus) {
+  constexpr int QB = 8;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   const int steps = (m < nc) ? m : nc;
-  for (int j = 0; j < steps; ++j) {
-    T* zj = Z + (size_t)j * m;
-    T part = 0;
-    for (int i = j + 1 + tid; i < m; i += blockDim.x) part += zj[i] * zj[i];
-    const T sigma = block_sum(part, red);
-    const T alpha = zj[j];
-    T tau = 0, beta = alpha;
-    if (sigma != T(0)) {
-      const T nrm = sqrt(alpha * alpha + sigma);
-      beta = (alpha >= T(0)) ? -nrm : nrm;
-      tau = (beta - alpha) / beta;
-      const T sc = T(1) / (alpha - beta);
-      for (int i = j + 1 + tid; i < m; i += blockDim.x) zj[i] *= sc;
-    }
-    __syncthreads();
-    if (tau != T(0)) {
-      for (int c = j + 1 + warp; c < nc; c += nw) {
-        T* zc = Z + (size_t)c * m;
-        T s = 0;
-        for (int i = j + 1 + lane; i < m; i += 32) s += zj[i] * zc[i];
-        s = warp_sum(s);
-        const T w = (s + zc[j]) * tau;
-        if (lane == 0) zc[j] -= w;
-        for (int i = j + 1 + lane; i < m; i += 32) zc[i] -= zj[i] * w;
+  for (int j0 = 0; j0 < steps; j0 += QB) {
+    const int pb = (steps - j0 < QB) ? steps - j0 : QB;
+    if (warp == 0) {
+      for (int jj = 0; jj < pb; ++jj) {
+        const int j = j0 + jj;
+        T* zj = Z + (size_t)j * m;
+        T part = 0;
+        for (int i = j + 1 + lane; i < m; i += 32) part += zj[i] * zj[i];
+        const T sigma = warp_sum(part);
+        const T alpha = zj[j];
+        T tau = 0, beta = alpha;
+        if (sigma != T(0)) {
+          const T nrm = sqrt(alpha * alpha + sigma);
+          beta = (alpha >= T(0)) ? -nrm : nrm;
+          tau = (beta - alpha) / beta;
+          const T sc = T(1) / (alpha - beta);
+          for (int i = j + 1 + lane; i < m; i += 32) zj[i] *= sc;
+        }
+        __syncwarp();
+        if (tau != T(0))
+          for (int c = j + 1; c < j0 + pb; ++c) qr_apply_reflector(zj, j, tau, Z + (size_t)c * m, m, lane);
+        if (lane == 0) {
+          taus[j] = tau;
+          zj[j] = beta;
+        }
+        __syncwarp();
       }
     }
     __syncthreads();
-    if (tid == 0) zj[j] = beta;
+    for (int c = j0 + pb + warp; c < nc; c += nw) {
+      T* zc = Z + (size_t)c * m;
+      for (int jj = 0; jj < pb; ++jj) {
+        const T tau = taus[j0 + jj];
+        if (tau != T(0)) qr_apply_reflector(Z + (size_t)(j0 + jj) * m, j0 + jj, tau, zc, m, lane);
+      }
+    }
     __syncthreads();
   }
   for (int o = tid; o < nc * nc; o += blockDim.x) {
@@ -409,7 +434,7 @@ __device__ double env_row_step(const G& g, const T* Eprev, T* Eout, const T* Tpa
       }
       __syncthreads();
     }
-    qr_keep_r(w.Z, mZ, n, w.R, w.red);
+    qr_keep_r(w.Z, mZ, n, w.R, w.sig);
     blk_copy(w.Rhist + (size_t)k * n * n, w.R, n * n);
     __syncthreads();
   }
