@@ -76,6 +76,9 @@ typedef struct {
     int chi;      /* boundary-MPS bond dimension D_c (paper's notation), D <= chi <= 64      */
     int prec;     /* peps_prec                                                               */
     int max_samples; /* largest Ns any later call may pass (sizes the environment store)     */
+    int gram;     /* MinSR Gram matrix: 0 = FP64 on CUDA cores; 1 = split BF16 on the tcgen05
+                     tensor cores (Obar = hi + lo, T ~ hi hi^T + hi lo^T + lo hi^T, FP32
+                     accumulation; about 1e-5 relative error per entry)                    */
 } peps_config;
 
 /* One local Hamiltonian term: h is a d^k x d^k complex matrix, row major, interleaved

@@ -66,6 +66,8 @@ struct peps_handle {
   // learned-proposal workspace (allocated on first use)
   uint8_t* lp_Sp = nullptr;
   double *lp_l0 = nullptr, *lp_l1 = nullptr, *lp_aux = nullptr;
+  // split-BF16 operands of the tensor-core Gram
+  void *g_hi = nullptr, *g_lo = nullptr;
   std::string err;
 };
 
@@ -267,6 +269,7 @@ extern "C" peps_status peps_create(peps_handle** out, const peps_config* cfg) {
       c.chi > 64 || c.max_samples < 1)
     return PEPS_E_SHAPE;
   if (c.prec != PEPS_PREC_FP64 && c.prec != PEPS_PREC_FP32) return PEPS_E_ARG;
+  if (c.gram != 0 && c.gram != 1) return PEPS_E_ARG;
   peps_handle* h = new peps_handle();
   h->cfg = c;
   h->esz = (c.prec == PEPS_PREC_FP64) ? 8 : 4;
@@ -320,7 +323,7 @@ extern "C" peps_status peps_destroy(peps_handle* h) {
   void* ptrs[] = {h->Tpad, h->site_off, h->envs, h->logs, h->wdisc, h->rowout, h->pairout, h->status_tmp,
                   h->gscratch, h->d_tinfo, h->d_ab, h->d_eh, h->d_rowoff, h->d_pairoff, h->d_pij, h->d_pv,
                   h->d_onsite, h->Obar, h->Tm, h->Vm, h->Hm, h->mean, h->ebar, h->yv, h->xv, h->cnt, h->ctr,
-                  h->lp_Sp, h->lp_l0, h->lp_l1, h->lp_aux};
+                  h->lp_Sp, h->lp_l0, h->lp_l1, h->lp_aux, h->g_hi, h->g_lo};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t e : h->evpool) cudaEventDestroy(e);
@@ -600,6 +603,13 @@ static peps_status ensure_minsr(peps_handle* h, int Ns) {
       cudaMalloc(&h->ebar, sizeof(double) * n) != cudaSuccess || cudaMalloc(&h->yv, sizeof(double) * n) != cudaSuccess ||
       cudaMalloc(&h->xv, sizeof(double) * n) != cudaSuccess || cudaMalloc(&h->cnt, sizeof(double) * 8) != cudaSuccess)
     return fail(h, PEPS_E_WORKSPACE, "MinSR workspace allocation failed");
+  if (h->cfg.gram == 1) {
+    if (h->g_hi) { cudaFree(h->g_hi); h->g_hi = nullptr; }
+    if (h->g_lo) { cudaFree(h->g_lo); h->g_lo = nullptr; }
+    const size_t e = (size_t)gram_tc_pad_rows(Ns) * (size_t)gram_tc_pad_k(h->Np) * 2;
+    if (cudaMalloc(&h->g_hi, e) != cudaSuccess || cudaMalloc(&h->g_lo, e) != cudaSuccess)
+      return fail(h, PEPS_E_WORKSPACE, "tensor-core Gram workspace allocation failed");
+  }
   h->ms_cap = n;
   return PEPS_OK;
 }
@@ -625,8 +635,15 @@ extern "C" peps_status minsr_step(peps_handle* h, const void* O_dev, const doubl
   CK(cudaMemsetAsync(h->Tm, 0, sizeof(double) * (size_t)n * n, s), "memset");
   tstop(h, ts, s, w_dev ? 3 : 2);
   ts = tstart(h, TC_GRAM, s);
-  CK(launch_gram(h->Obar, Ns, Np, h->Tm, n, s), "Gram");
-  tstop(h, ts, s);
+  if (h->cfg.gram == 1) {
+    CK(cudaMemsetAsync(h->cnt + 4, 0, sizeof(int), s), "memset");
+    CK(launch_gram_tc(h->Obar, Ns, Np, h->g_hi, h->g_lo, h->Tm, n, rcond > 0.0, (int*)(h->cnt + 4), s),
+       "tensor-core Gram");
+    tstop(h, ts, s, rcond > 0.0 ? 3 : 2);
+  } else {
+    CK(launch_gram(h->Obar, Ns, Np, h->Tm, n, s), "Gram");
+    tstop(h, ts, s);
+  }
   double sw = -1.0;
   if (rcond > 0.0) {
     // eigendecomposition with the pseudo-inverse cutoff
@@ -650,6 +667,11 @@ extern "C" peps_status minsr_step(peps_handle* h, const void* O_dev, const doubl
   tstop(h, ts, s, 1);
   CK(cudaMemcpyAsync(info_dev + 3, &sw, sizeof(double), cudaMemcpyHostToDevice, s), "info");
   CK(cudaStreamSynchronize(s), "MinSR sync");
+  if (h->cfg.gram == 1) {
+    int gerr = 0;
+    CK(cudaMemcpy(&gerr, h->cnt + 4, sizeof(int), cudaMemcpyDeviceToHost), "read Gram status");
+    if (gerr) return fail(h, PEPS_E_CUDA, "tensor-core Gram: a pipeline wait timed out");
+  }
   return PEPS_OK;
 }
 

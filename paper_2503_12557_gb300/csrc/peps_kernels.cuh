@@ -87,6 +87,11 @@ cudaError_t launch_prop_logq(int N, int Ns, const double* logits, const uint8_t*
 cudaError_t launch_prop_accept(int N, int Ns, uint64_t seed, uint64_t step, const uint8_t* Sp, const double* lpsi_new,
                                const double* lq_fwd, const double* lq_bwd, uint8_t* S, double* lpsi, long long* accepted,
                                cudaStream_t s);
+// ---- tensor-core Gram (peps_gram_tc.cu)
+int gram_tc_pad_rows(int Ns);
+long long gram_tc_pad_k(long long Np);
+cudaError_t launch_gram_tc(const double* Obar, int Ns, long long Np, void* hi, void* lo, double* Tm, int ld, bool mirror,
+                           int* err, cudaStream_t s);
 // y += x (n doubles)
 cudaError_t launch_axpy(double* y, const double* x, long long n, cudaStream_t s);
 

@@ -24,7 +24,7 @@ _ERRORS = {-1: "PEPS_E_ARG", -2: "PEPS_E_SHAPE", -3: "PEPS_E_WORKSPACE", -4: "PE
 
 class _Config(C.Structure):
     _fields_ = [("Lx", C.c_int), ("Ly", C.c_int), ("d", C.c_int), ("D", C.c_int), ("chi", C.c_int),
-                ("prec", C.c_int), ("max_samples", C.c_int)]
+                ("prec", C.c_int), ("max_samples", C.c_int), ("gram", C.c_int)]
 
 
 class _Term(C.Structure):
@@ -163,11 +163,12 @@ class Hamiltonian:
 class PEPS:
     """One handle of the C library: a lattice, chi and a precision."""
 
-    def __init__(self, Lx, Ly, d, D, chi, prec=PREC_FP64, max_samples=4096):
+    def __init__(self, Lx, Ly, d, D, chi, prec=PREC_FP64, max_samples=4096, gram=0):
         self.L = load()
         self.Lx, self.Ly, self.d, self.D, self.chi, self.prec = Lx, Ly, d, D, chi, prec
         self.max_samples = max_samples
-        cfg = _Config(Lx, Ly, d, D, chi, prec, max_samples)
+        self.gram = gram
+        cfg = _Config(Lx, Ly, d, D, chi, prec, max_samples, gram)
         h = C.c_void_p()
         st = self.L.peps_create(C.byref(h), C.byref(cfg))
         if st != 0:

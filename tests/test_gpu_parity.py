@@ -222,8 +222,8 @@ def test_minsr_step_ragged_blocks_vs_oracle(P, ns, npar, rc, lam):
     assert int(info[0]) == inf_ref["rank"]
 
 
-def _minsr_raw(P, O, e, lam, rc, tau):
-    """minsr_step on a handle whose N_p equals O's column count (a 1 x Ly chain of sites)."""
+def _minsr_raw(P, O, e, lam, rc, tau, gram=0):
+    """minsr_step on a handle whose N_p covers O's column count (zero-padded columns)."""
     ns, npar = O.shape
     # choose a lattice with exactly npar parameters is not always possible; use a handle on a
     # lattice with N_p >= npar and zero-pad O's columns (zero columns change no MinSR value)
@@ -234,12 +234,29 @@ def _minsr_raw(P, O, e, lam, rc, tau):
                 break
         if I.num_params(lat) >= npar:
             break
-    h = P.PEPS(lat.Lx, lat.Ly, 2, lat.D, lat.D, max_samples=2)
+    h = P.PEPS(lat.Lx, lat.Ly, 2, lat.D, lat.D, max_samples=2, gram=gram)
     Op = np.zeros((ns, h.Np))
     Op[:, :npar] = O
     dth, info = h.minsr_step(_dev(Op), _dev(np.stack([e, np.zeros(ns)], 1)), lam=lam, rcond=rc, tau=tau)
     torch.cuda.synchronize()
     return dth.cpu().numpy()[:npar], info.cpu().numpy()
+
+
+@pytest.mark.parametrize("ns,npar,rc,lam", [(700, 300, 0.0, 1e-2), (333, 500, 1e-9, 1e-3), (1030, 1200, 0.0, 1e-2)])
+def test_minsr_tensor_core_gram_vs_oracle(P, ns, npar, rc, lam):
+    # split-BF16 tcgen05 Gram: T ~ hi hi^T + hi lo^T + lo hi^T with FP32 accumulation (about
+    # 1e-5 relative per entry); dtheta error then scales with the conditioning of T + lambda
+    from oracle import minsr
+    rng = np.random.default_rng(ns + 1)
+    O = rng.standard_normal((ns, npar)) + 0.1 * rng.standard_normal(npar)
+    e = rng.standard_normal(ns) - 3.0
+    d_ref, inf_ref = minsr.minsr(O, e, lam=lam, rcond=rc, tau=0.1)
+    dth, info = _minsr_raw(P, O, e, lam, rc, 0.1, gram=1)
+    rel = np.linalg.norm(dth - d_ref) / np.linalg.norm(d_ref)
+    print(f"tensor-core Gram: relative dtheta error {rel:.2e}")
+    assert rel <= 1e-2
+    if rc > 0:
+        assert abs(info[2] - inf_ref["lmax"]) <= 1e-4 * inf_ref["lmax"]
 
 
 @pytest.mark.parametrize("move,lat,chi,H", [
