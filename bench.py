@@ -40,7 +40,7 @@ def _args():
     ap.add_argument("--ns", type=int, default=None)
     ap.add_argument("--sweeps", type=int, default=2)
     ap.add_argument("--burnin", type=int, default=2)
-    ap.add_argument("--mode", default="step", choices=["step", "learned"])
+    ap.add_argument("--mode", default="step", choices=["step", "learned", "gram"])
     ap.add_argument("--cpu-samples", type=int, default=12)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -366,12 +366,63 @@ def run_learned(a):
     print(json.dumps(out), flush=True)
 
 
+def run_gram(a):
+    """MinSR step on a synthetic O (N_s x N_p, entries N(0,1) plus a 0.1 column offset so that
+    centring matters) with the FP64 CUDA-core Gram and with the split-BF16 tcgen05 Gram; reports
+    the Gram time, its tensor-pipe rate (3 BF16 products per algorithmic multiply-add) and the
+    relative difference of the two dtheta."""
+    import torch
+    from paper_2503_12557_gb300 import build, inputs as I, peps as P
+    build.build()
+    ns = a.ns or 16384
+    lat = I.Lattice(14, 14, 2, 4)  # N_p = 80 000, the smallest square open lattice above 73 728
+    peaks = _peaks()
+    out = {"mode": "gram", "ns": ns}
+    res = {}
+    g = torch.Generator(device="cuda").manual_seed(5005)
+    for gram, tag in ((1, "tcgen05_split_bf16"), (0, "fp64_cuda_cores")):
+        h = P.PEPS(lat.Lx, lat.Ly, 2, lat.D, lat.D, prec=P.PREC_FP64, max_samples=2, gram=gram)
+        out["np"] = h.Np
+        g.manual_seed(5005)
+        O = torch.randn(ns, h.Np, dtype=torch.float64, device="cuda", generator=g)
+        O += 0.1 * torch.randn(h.Np, dtype=torch.float64, device="cuda", generator=g)
+        e = torch.zeros(ns, 2, dtype=torch.float64, device="cuda")
+        e[:, 0] = torch.randn(ns, dtype=torch.float64, device="cuda", generator=g) - 3.0
+        reps = 1 if gram == 0 else 3
+        h.minsr_step(O, e, lam=1e-2, tau=0.1)  # warm-up (allocations)
+        h.timing(True)
+        for _ in range(reps):
+            dth, info = h.minsr_step(O, e, lam=1e-2, tau=0.1)
+        ms, la, _ = h.timing_read()
+        h.timing(False)
+        gram_ms = ms["minsr_gram"] / reps
+        mac = ns * (ns + 1) / 2 * h.Np  # algorithmic multiply-adds of one triangle
+        r = {"gram_ms": gram_ms, "solve_ms": ms["minsr_eig"] / reps, "step_s": sum(ms.values()) / reps / 1e3}
+        if gram == 1:
+            tflops = 3 * 2 * mac / (gram_ms / 1e3) / 1e12
+            r["tensor_tflops_bf16"] = tflops
+            r["roofline"] = {"bound": "tensor", "achieved": tflops, "peak": peaks.get("bf16_tflops", 1900.0),
+                             "unit": "TFLOP/s", "frac": tflops / peaks.get("bf16_tflops", 1900.0)}
+        else:
+            r["fp64_tflops"] = 2 * mac / (gram_ms / 1e3) / 1e12
+        res[tag] = dth
+        out[tag] = r
+        del O
+        h.close()
+        torch.cuda.empty_cache()
+    d = res["tcgen05_split_bf16"] - res["fp64_cuda_cores"]
+    out["dtheta_rel_diff"] = float(d.norm() / res["fp64_cuda_cores"].norm())
+    print(json.dumps(out), flush=True)
+
+
 def main():
     a = _args()
     if a.impl == "reference":
         run_reference(a)
     elif a.mode == "learned":
         run_learned(a)
+    elif a.mode == "gram":
+        run_gram(a)
     else:
         run_gpu(a)
 

@@ -8,7 +8,7 @@
 #include <algorithm>
 
 #include "peps_kernels.cuh"
-#include "../../include/peps_gb300.h"
+#include "peps_gb300.h"
 
 using namespace peps;
 

@@ -17,7 +17,7 @@
 #include <utility>
 
 #include "peps_kernels.cuh"
-#include "../../include/peps_gb300.h"
+#include "peps_gb300.h"
 
 namespace {
 
