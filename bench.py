@@ -183,7 +183,8 @@ def run_gpu(a):
     H = I.heisenberg(lat)
     theta0 = I.peps_random(lat, w["seed_theta"], **w["init"])
     S0 = I.configs_neel(lat, ns)
-    h = P.PEPS(lat.Lx, lat.Ly, lat.d, lat.D, w["chi"], prec=prec, max_samples=ns)
+    mixed = False  # MinSR Gram and solve in FP64 on either path
+    h = P.PEPS(lat.Lx, lat.Ly, lat.d, lat.D, w["chi"], prec=prec, max_samples=ns, gram=0, solve=0)
     theta = torch.as_tensor(theta0).cuda()
     h.set_params(theta)
     S = torch.as_tensor(S0).cuda()
@@ -258,7 +259,7 @@ def run_gpu(a):
     dom = max(flops, key=lambda k: ms_cls.get(k, 0.0))
     dom_launch_ms = ms_cls[dom] / max(1, launches[dom])
     achieved = flops[dom] / max(1, launches[dom]) / (dom_launch_ms / 1e3) / 1e12
-    peak = fp64_peak if dom == "minsr_gram" else alu_peak
+    peak = (fp64_peak if not mixed else peaks.get("bf16_tflops", 1900.0)) if dom == "minsr_gram" else alu_peak
     roof = {"kernel": {"env": "k_env", "sample": "k_sample", "row": "k_row", "pair": "k_pair",
                        "minsr_gram": "k_gram"}[dom],
             "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
@@ -272,6 +273,12 @@ def run_gpu(a):
             "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if prec == P.PREC_FP32 else "f64", "data": "synthetic",
             "config": _config(w, ns, a.prec, a.sweeps), "minsr_step_s": minsr_s,
+            "minsr": {"gram": "split-BF16 tcgen05" if mixed else "FP64 CUDA cores",
+                      "solve": "FP64 Cholesky",
+                      "gram_ms": ms_cls["minsr_gram"] / a.steps, "solve_ms": ms_cls["minsr_eig"] / a.steps,
+                      "gram_tflops": (costmodel.gram_flops(ns, h.Np) * (3 if mixed else 1) /
+                                      max(1e-9, ms_cls["minsr_gram"] / a.steps / 1e3) / 1e12),
+                      "last_info": [float(x) for x in info_hist[-1].cpu()]},
             "kernel_ms_per_step": {k: v / a.steps for k, v in ms_cls.items()},
             "roofline": roof, "gpu_launches": gpu_launches, "clocks": clk.summary(),
             "acceptance": float(acc.sum().item()) / max(1.0, ns * (sweep_ctr[0]) * (2 * lat.Lx * lat.Ly - lat.Lx - lat.Ly) * 0.5),

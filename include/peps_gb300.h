@@ -21,7 +21,8 @@
  *   Site tensor T[x,y][s, l, u, r, d]; legs pointing out of the lattice have dimension 1.
  *   theta: all site tensors in C order, concatenated in site order (length N_p, see
  *   peps_num_params).  O rows use the same order.
- *   Configurations: uint8, Ns x (Lx*Ly), row major, values 0..d-1.
+ *   Configurations: uint8, Ns x (Lx*Ly), row major, values 0..d-1 (a value outside that range
+ *   is invalid input; the kernels read it as 0 rather than index out of bounds).
  *   Every pointer argument named *_dev is DEVICE memory owned by the caller; the library never
  *   frees or keeps it beyond the call.  Host pointers are named *_host.
  *   Every call is asynchronous on the caller's CUDA stream (passed as void*, a cudaStream_t;
@@ -33,7 +34,8 @@
  *     PEPS_ST_ZERO_NORM        an environment tensor or partial contraction was exactly zero;
  *     PEPS_ST_NONFINITE        a NaN or Inf appeared (ln psi, E_loc or O of that sample invalid);
  *     PEPS_ST_NOCONV           a one-sided Jacobi SVD hit its sweep limit.
- *   Nothing traps on the device.
+ *   Nothing traps on the device; non-finite parameters or inputs give NaN results and
+ *   PEPS_ST_NONFINITE, never an out-of-bounds access.
  */
 #ifndef PEPS_GB300_H
 #define PEPS_GB300_H
@@ -47,6 +49,8 @@ extern "C" {
 
 typedef enum {
     PEPS_OK = 0,
+    PEPS_W_NUMERIC = 1,     /* minsr_step: T + lambda not positive definite in floating
+                               point; dtheta_dev was set to zero (info[0] = -1)       */
     PEPS_E_ARG = -1,        /* NULL pointer, negative size, bad enum value            */
     PEPS_E_SHAPE = -2,      /* lattice / chi / Ns outside what the handle supports     */
     PEPS_E_WORKSPACE = -3,  /* device allocation failed                                */
@@ -79,6 +83,9 @@ typedef struct {
     int gram;     /* MinSR Gram matrix: 0 = FP64 on CUDA cores; 1 = split BF16 on the tcgen05
                      tensor cores (Obar = hi + lo, T ~ hi hi^T + hi lo^T + lo hi^T, FP32
                      accumulation; about 1e-5 relative error per entry)                    */
+    int solve;    /* MinSR solve when rcond == 0: 0 = FP64 Cholesky; 1 = FP32 Cholesky of
+                     T + lambda followed by 4 steps of iterative refinement with FP64 residuals
+                     (info[1] reports the final relative residual)                           */
 } peps_config;
 
 /* One local Hamiltonian term: h is a d^k x d^k complex matrix, row major, interleaved
@@ -150,9 +157,14 @@ peps_status peps_evaluate(peps_handle* h, const peps_hamiltonian* H, const uint8
  * doubles (the real parts are used: real PEPS); dtheta_dev: N_p doubles (written);
  * info_dev: 4 doubles.  rcond > 0: eigendecomposition by cyclic Jacobi, info = (rank kept,
  * min Lambda, max Lambda, Jacobi sweeps).  rcond == 0 (nothing cut, lambda > 0): the same
- * operator (T + lambda)^-1 applied through a Cholesky factorisation, info = (Ns, NaN, NaN, -1),
- * info[0] = -1 when T + lambda was not positive definite in floating point.
- * Needs lambda > 0 or rcond > 0.  The Gram matrix and the solve are FP64.  The call
+ * operator (T + lambda)^-1 applied through a Cholesky factorisation, info = (Ns, NaN, NaN, -1)
+ * with cfg.solve == 0, info = (Ns, |ebar - (T + lambda) x| / |ebar|, refinement steps, -1)
+ * with cfg.solve == 1, where refinement steps = 0 means that the FP32 factor failed or the
+ * refined residual stayed above 1e-10 and the FP64 factorisation was used instead.  When T +
+ * lambda is not positive definite in floating point even in FP64 (lambda far below the
+ * rounding error of T, e.g. a split-BF16 Gram of badly scaled O), info[0] = -1, dtheta_dev is
+ * set to zero and the call returns PEPS_W_NUMERIC.  Needs lambda > 0 or rcond > 0.  The Gram matrix is FP64 (cfg.gram == 0) or split
+ * BF16 on the tensor cores (cfg.gram == 1); the eigendecomposition is FP64.  The call
  * synchronises the stream before it returns. */
 peps_status minsr_step(peps_handle* h, const void* O_dev, const double* eloc_dev, const double* w_dev,
                        int Ns, double lambda, double rcond, double tau, double* dtheta_dev,

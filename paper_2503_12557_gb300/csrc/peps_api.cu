@@ -270,6 +270,7 @@ extern "C" peps_status peps_create(peps_handle** out, const peps_config* cfg) {
     return PEPS_E_SHAPE;
   if (c.prec != PEPS_PREC_FP64 && c.prec != PEPS_PREC_FP32) return PEPS_E_ARG;
   if (c.gram != 0 && c.gram != 1) return PEPS_E_ARG;
+  if (c.solve != 0 && c.solve != 1) return PEPS_E_ARG;
   peps_handle* h = new peps_handle();
   h->cfg = c;
   h->esz = (c.prec == PEPS_PREC_FP64) ? 8 : 4;
@@ -658,8 +659,28 @@ extern "C" peps_status minsr_step(peps_handle* h, const void* O_dev, const doubl
   } else {
     // nothing is cut: (T + lambda)^+ = (T + lambda)^-1, solved by Cholesky
     ts = tstart(h, TC_EIG, s);
-    const long long nl = chol_solve(h->Tm, n, Ns, lambda, h->ebar, h->xv, (int*)h->cnt, info_dev, s, &e);
-    if (e != cudaSuccess) return cuda_fail(h, e, "Cholesky");
+    bool fp64 = (h->cfg.solve != 1);
+    long long nl = 0;
+    if (!fp64) {
+      nl = chol_solve_mixed(h->Tm, (float*)h->Vm, n, Ns, lambda, h->ebar, h->xv, h->yv, h->cnt + 6, 4, (int*)h->cnt,
+                            info_dev, s, &e);
+      if (e != cudaSuccess) return cuda_fail(h, e, "Cholesky");
+      // the FP32 factor must exist and the refined residual be small, else factor in FP64
+      double rn[2] = {0.0, 0.0};
+      int bad = 0;
+      CK(cudaMemcpyAsync(rn, h->cnt + 6, sizeof(rn), cudaMemcpyDeviceToHost, s), "read residual");
+      CK(cudaMemcpyAsync(&bad, h->cnt, sizeof(int), cudaMemcpyDeviceToHost, s), "read factor status");
+      CK(cudaStreamSynchronize(s), "mixed solve sync");
+      fp64 = bad || !(rn[0] <= 1e-20 * rn[1]);
+    }
+    if (fp64) {
+      nl += chol_solve(h->Tm, n, Ns, lambda, h->ebar, h->xv, (int*)h->cnt, info_dev, s, &e);
+      if (e != cudaSuccess) return cuda_fail(h, e, "Cholesky");
+      if (h->cfg.solve == 1) {
+        const double zero = 0.0;
+        CK(cudaMemcpyAsync(info_dev + 2, &zero, sizeof(double), cudaMemcpyHostToDevice, s), "info");
+      }
+    }
     tstop(h, ts, s, nl);
   }
   ts = tstart(h, TC_MINSR, s);
@@ -671,6 +692,17 @@ extern "C" peps_status minsr_step(peps_handle* h, const void* O_dev, const doubl
     int gerr = 0;
     CK(cudaMemcpy(&gerr, h->cnt + 4, sizeof(int), cudaMemcpyDeviceToHost), "read Gram status");
     if (gerr) return fail(h, PEPS_E_CUDA, "tensor-core Gram: a pipeline wait timed out");
+  }
+  if (rcond == 0.0) {
+    // a factorisation that broke down gives no usable dtheta: return zero and warn
+    double i0 = 0.0;
+    CK(cudaMemcpy(&i0, info_dev, sizeof(double), cudaMemcpyDeviceToHost), "read info");
+    if (i0 < 0.0) {
+      CK(cudaMemsetAsync(dtheta_dev, 0, sizeof(double) * (size_t)Np, s), "zero dtheta");
+      CK(cudaStreamSynchronize(s), "MinSR sync");
+      h->err = "T + lambda is not positive definite in floating point; dtheta set to zero";
+      return PEPS_W_NUMERIC;
+    }
   }
   return PEPS_OK;
 }

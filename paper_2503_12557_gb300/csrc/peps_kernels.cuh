@@ -5,6 +5,9 @@
 namespace peps {
 
 constexpr int NTHREADS = 256;
+// resident blocks per SM the environment and sampler kernels are compiled for: two in FP32
+// (about 100 KB of shared memory each), one in FP64 (about 200 KB)
+template <typename T> struct MinBlocks { static constexpr int value = sizeof(T) == 4 ? 2 : 1; };
 constexpr int MAX_LY = 32;
 
 // term record (ints): number of sites, the sites, window (first row, first column, width,
@@ -49,10 +52,36 @@ cudaError_t launch_pad(const Geo& g, const double* theta, const long long* site_
 cudaError_t launch_combine(const Geo& g, int Ns, const uint8_t* S, const double* rowout, const double* pairout,
                            int use_rows_all, int use_pairs, const DiagTab& dg, double* logabs, double* phase,
                            double* eloc, cudaStream_t s);
+// per-kernel attributes: set the dynamic shared-memory limit (set_bytes > 0) and/or report the
+// resident blocks per SM at occ_smem bytes (occ != null)
 template <typename T>
-cudaError_t set_kernel_smem(const Geo& g, size_t bytes);
+cudaError_t kattr_env(const Geo& g, size_t set_bytes, int* occ, size_t occ_smem);
 template <typename T>
-int occupancy(const Geo& g, int which, size_t smem);
+cudaError_t kattr_row(const Geo& g, size_t set_bytes, int* occ, size_t occ_smem);
+template <typename T>
+cudaError_t kattr_pair(const Geo& g, size_t set_bytes, int* occ, size_t occ_smem);
+template <typename T>
+cudaError_t kattr_sample(const Geo& g, size_t set_bytes, int* occ, size_t occ_smem);
+template <typename T>
+inline cudaError_t set_kernel_smem(const Geo& g, size_t bytes) {
+  cudaError_t e;
+  if ((e = kattr_env<T>(g, bytes, nullptr, 0)) != cudaSuccess) return e;
+  if ((e = kattr_row<T>(g, bytes, nullptr, 0)) != cudaSuccess) return e;
+  if ((e = kattr_pair<T>(g, bytes, nullptr, 0)) != cudaSuccess) return e;
+  return kattr_sample<T>(g, bytes, nullptr, 0);
+}
+// which: 0 k_env, 1 k_row, 2 k_pair, 3 k_sample
+template <typename T>
+inline int occupancy(const Geo& g, int which, size_t smem) {
+  int nb = 0;
+  switch (which) {
+    case 0: kattr_env<T>(g, 0, &nb, smem); break;
+    case 1: kattr_row<T>(g, 0, &nb, smem); break;
+    case 2: kattr_pair<T>(g, 0, &nb, smem); break;
+    default: kattr_sample<T>(g, 0, &nb, smem); break;
+  }
+  return nb;
+}
 
 // ---- MinSR (FP64)
 // column means m_k = sum_S w_S O_{S,k} (w normalised), and Obar = sqrt(w)(O - m) written as
@@ -73,6 +102,12 @@ cudaError_t launch_obar_t_x(const double* Obar, const double* x, int Ns, long lo
 // x = (A + lambda I)^-1 ebar by blocked Cholesky (A overwritten by its factor); returns launches
 long long chol_solve(double* A, int n, int nreal, double lambda, const double* ebar, double* x, int* bad,
                      double* info, cudaStream_t s, cudaError_t* err);
+// the same solve with an FP32 factor (A32: n x n floats, A kept and mirrored to full) and
+// `iters` refinement steps with FP64 residuals (r: n doubles, rn: 2 doubles of scratch);
+// info = (Ns or -1, relative residual, iters, -)
+long long chol_solve_mixed(double* A, float* A32, int n, int nreal, double lambda, const double* ebar, double* x,
+                           double* r, double* rn, int iters, int* bad, double* info, cudaStream_t s,
+                           cudaError_t* err);
 // ---- learned proposal (peps_proposal.cu)
 size_t prop_smem_bytes(int Lx, int Ly, int C, int act_bytes, bool train);
 cudaError_t launch_prop_logits(int Lx, int Ly, int C, int wprec, const void* w, const uint8_t* S, int Ns, double* logits,

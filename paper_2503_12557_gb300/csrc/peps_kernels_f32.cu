@@ -1,6 +1,7 @@
-// FP32 instantiation of the contraction kernels.
+// FP32 instantiation of the sandwich kernels (k_row, k_pair) and the parameter padding.
+#define PEPS_PART_ROW
 #include "peps_kernels_impl.cuh"
 
 namespace peps {
-PEPS_INST(float)
+PEPS_INST_ROW(float)
 }  // namespace peps

@@ -82,7 +82,7 @@ __device__ void build_lower(const G& g, const T* Tpad, const uint8_t* Ss, T* env
 }
 
 template <typename T, typename G>
-__global__ void __launch_bounds__(NTHREADS) k_env(G g, Plan plan, const T* __restrict__ Tpad,
+__global__ void __launch_bounds__(NTHREADS, MinBlocks<T>::value) k_env(G g, Plan plan, const T* __restrict__ Tpad,
                                                   const uint8_t* __restrict__ S, int Ns, int sides, T* envs,
                                                   double* logs, int* status, float* wdisc) {
   extern __shared__ __align__(16) char smem[];
@@ -403,7 +403,7 @@ __global__ void k_combine(Geo g, int Ns, const uint8_t* __restrict__ S, const do
     if (eloc) {
       for (int p = lane; p < dg.npairs; p += 32) re += dg.pair_v[p] * (double)Ss[dg.pair_ij[2 * p]] * (double)Ss[dg.pair_ij[2 * p + 1]];
       if (dg.onsite)
-        for (int i = lane; i < N; i += 32) re += dg.onsite[(size_t)i * g.d + Ss[i]];
+        for (int i = lane; i < N; i += 32) re += dg.onsite[(size_t)i * g.d + (Ss[i] < g.d ? Ss[i] : 0)];
       if (use_rows_all)
         for (int x = lane; x < g.Lx; x += 32) {
           re += rowout[((size_t)smp * g.Lx + x) * 4 + 2];
@@ -430,7 +430,7 @@ __global__ void k_combine(Geo g, int Ns, const uint8_t* __restrict__ S, const do
 // ------------------------------------------------------------------------------------------
 // Metropolis sweeps: one CTA per chain (persistent over chains).
 template <typename T, typename G>
-__global__ void __launch_bounds__(NTHREADS) k_sample(G g, Plan plan, const T* __restrict__ Tpad, uint8_t* S,
+__global__ void __launch_bounds__(NTHREADS, MinBlocks<T>::value) k_sample(G g, Plan plan, const T* __restrict__ Tpad, uint8_t* S,
                                                      int Ns, int move, int nsweeps, unsigned long long seed,
                                                      unsigned long long sweep0, T* envs, double* logs,
                                                      long long* accepted, int* status) {
@@ -660,6 +660,21 @@ static cudaError_t with_geo(const Geo& g, F&& f) {
   return f(g);
 }
 
+// Each translation unit defines PEPS_PART_ENV, PEPS_PART_ROW (k_row, k_pair, parameter padding)
+// or PEPS_PART_SAMPLE and instantiates its kernels with PEPS_INST_<part>(T).
+#define PEPS_KATTR(NAME, KERNEL)                                                                                   \
+  template <typename T>                                                                                          \
+  cudaError_t NAME(const Geo& g, size_t set_bytes, int* occ, size_t occ_smem) {                                  \
+    return with_geo(g, [&](auto gg) {                                                                            \
+      using GG = decltype(gg);                                                                                   \
+      cudaError_t e = cudaSuccess;                                                                               \
+      if (set_bytes) e = cudaFuncSetAttribute(KERNEL<T, GG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)set_bytes); \
+      if (e == cudaSuccess && occ) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, KERNEL<T, GG>, NTHREADS, occ_smem); \
+      return e;                                                                                                  \
+    });                                                                                                          \
+  }
+
+#ifdef PEPS_PART_ENV
 template <typename T>
 cudaError_t launch_env(const Geo& g, const Plan& p, int grid, size_t smem, const T* Tpad, const uint8_t* S, int Ns,
                        int sides, T* envs, double* logs, int* status, float* wdisc, cudaStream_t s) {
@@ -668,6 +683,14 @@ cudaError_t launch_env(const Geo& g, const Plan& p, int grid, size_t smem, const
     return cudaGetLastError();
   });
 }
+PEPS_KATTR(kattr_env, k_env)
+#define PEPS_INST_ENV(T)                                                                                          \
+  template cudaError_t launch_env<T>(const Geo&, const Plan&, int, size_t, const T*, const uint8_t*, int, int, T*, \
+                                     double*, int*, float*, cudaStream_t);                                        \
+  template cudaError_t kattr_env<T>(const Geo&, size_t, int*, size_t);
+#endif
+
+#ifdef PEPS_PART_ROW
 template <typename T>
 cudaError_t launch_row(const Geo& g, const Plan& p, int grid, size_t smem, const T* Tpad, const uint8_t* S, int Ns,
                        int x_lo, int x_hi, const T* envs, const double* logs, T* O, const long long* site_off,
@@ -687,6 +710,25 @@ cudaError_t launch_pair(const Geo& g, const Plan& p, int grid, size_t smem, cons
   });
 }
 template <typename T>
+cudaError_t launch_pad(const Geo& g, const double* theta, const long long* site_off, T* Tpad, cudaStream_t s) {
+  k_pad_theta<T><<<304, 256, 0, s>>>(g, theta, site_off, Tpad);
+  return cudaGetLastError();
+}
+PEPS_KATTR(kattr_row, k_row)
+PEPS_KATTR(kattr_pair, k_pair)
+#define PEPS_INST_ROW(T)                                                                                          \
+  template cudaError_t launch_row<T>(const Geo&, const Plan&, int, size_t, const T*, const uint8_t*, int, int, int, \
+                                     const T*, const double*, T*, const long long*, long long, const TermTab&,    \
+                                     double*, int*, cudaStream_t);                                                \
+  template cudaError_t launch_pair<T>(const Geo&, const Plan&, int, size_t, const T*, const uint8_t*, int, const T*, \
+                                      const double*, const TermTab&, double*, int*, cudaStream_t);                \
+  template cudaError_t launch_pad<T>(const Geo&, const double*, const long long*, T*, cudaStream_t);              \
+  template cudaError_t kattr_row<T>(const Geo&, size_t, int*, size_t);                                           \
+  template cudaError_t kattr_pair<T>(const Geo&, size_t, int*, size_t);
+#endif
+
+#ifdef PEPS_PART_SAMPLE
+template <typename T>
 cudaError_t launch_sample(const Geo& g, const Plan& p, int grid, size_t smem, const T* Tpad, uint8_t* S, int Ns,
                           int move, int nsweeps, unsigned long long seed, unsigned long long sweep0, T* envs,
                           double* logs, long long* accepted, int* status, cudaStream_t s) {
@@ -696,11 +738,14 @@ cudaError_t launch_sample(const Geo& g, const Plan& p, int grid, size_t smem, co
     return cudaGetLastError();
   });
 }
-template <typename T>
-cudaError_t launch_pad(const Geo& g, const double* theta, const long long* site_off, T* Tpad, cudaStream_t s) {
-  k_pad_theta<T><<<304, 256, 0, s>>>(g, theta, site_off, Tpad);
-  return cudaGetLastError();
-}
+PEPS_KATTR(kattr_sample, k_sample)
+#define PEPS_INST_SAMPLE(T)                                                                                       \
+  template cudaError_t launch_sample<T>(const Geo&, const Plan&, int, size_t, const T*, uint8_t*, int, int, int,   \
+                                        unsigned long long, unsigned long long, T*, double*, long long*, int*,    \
+                                        cudaStream_t);                                                            \
+  template cudaError_t kattr_sample<T>(const Geo&, size_t, int*, size_t);
+#endif
+
 #ifdef PEPS_DEFINE_COMMON
 cudaError_t launch_combine(const Geo& g, int Ns, const uint8_t* S, const double* rowout, const double* pairout,
                            int use_rows_all, int use_pairs, const DiagTab& dg, double* logabs, double* phase,
@@ -710,48 +755,5 @@ cudaError_t launch_combine(const Geo& g, int Ns, const uint8_t* S, const double*
   return cudaGetLastError();
 }
 #endif
-
-template <typename T>
-cudaError_t set_kernel_smem(const Geo& g, size_t bytes) {
-  return with_geo(g, [&](auto gg) {
-    using GG = decltype(gg);
-    cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_env<T, GG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_row<T, GG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_pair<T, GG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)) != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_sample<T, GG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  });
-}
-
-template <typename T>
-int occupancy(const Geo& g, int which, size_t smem) {
-  int nb = 0;
-  with_geo(g, [&](auto gg) {
-    using GG = decltype(gg);
-    switch (which) {
-      case 0: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_env<T, GG>, NTHREADS, smem); break;
-      case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_row<T, GG>, NTHREADS, smem); break;
-      case 2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pair<T, GG>, NTHREADS, smem); break;
-      default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sample<T, GG>, NTHREADS, smem); break;
-    }
-    return cudaSuccess;
-  });
-  return nb;
-}
-
-#define PEPS_INST(T)                                                                                              \
-  template cudaError_t launch_env<T>(const Geo&, const Plan&, int, size_t, const T*, const uint8_t*, int, int, T*, \
-                                     double*, int*, float*, cudaStream_t);                                        \
-  template cudaError_t launch_row<T>(const Geo&, const Plan&, int, size_t, const T*, const uint8_t*, int, int, int, \
-                                     const T*, const double*, T*, const long long*, long long, const TermTab&,    \
-                                     double*, int*, cudaStream_t);                                                \
-  template cudaError_t launch_pair<T>(const Geo&, const Plan&, int, size_t, const T*, const uint8_t*, int, const T*, \
-                                      const double*, const TermTab&, double*, int*, cudaStream_t);                \
-  template cudaError_t launch_sample<T>(const Geo&, const Plan&, int, size_t, const T*, uint8_t*, int, int, int,   \
-                                        unsigned long long, unsigned long long, T*, double*, long long*, int*,    \
-                                        cudaStream_t);                                                            \
-  template cudaError_t launch_pad<T>(const Geo&, const double*, const long long*, T*, cudaStream_t);              \
-  template cudaError_t set_kernel_smem<T>(const Geo&, size_t);                                                    \
-  template int occupancy<T>(const Geo&, int, size_t);
 
 }  // namespace peps

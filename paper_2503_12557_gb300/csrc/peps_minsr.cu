@@ -303,8 +303,9 @@ namespace peps {
 constexpr int CB = 64;
 
 // factor the CB x CB diagonal block at (k0, k0) in place (lower triangle), one CTA
-__global__ void __launch_bounds__(256) k_chol_diag(double* A, int n, int k0, double lambda_first, int* bad) {
-  __shared__ double L[CB][CB + 1];
+template <typename T>
+__global__ void __launch_bounds__(256) k_chol_diag(T* A, int n, int k0, int* bad) {
+  __shared__ T L[CB][CB + 1];
   const int nb = min(CB, n - k0);
   for (int o = threadIdx.x; o < nb * nb; o += blockDim.x) {
     const int i = o / nb, j = o % nb;
@@ -313,12 +314,12 @@ __global__ void __launch_bounds__(256) k_chol_diag(double* A, int n, int k0, dou
   __syncthreads();
   for (int j = 0; j < nb; ++j) {
     if (threadIdx.x == 0) {
-      const double d = L[j][j];
-      if (!(d > 0.0)) { *bad = 1; L[j][j] = 1.0; }
+      const T d = L[j][j];
+      if (!(d > T(0))) { *bad = 1; L[j][j] = T(1); }
       else L[j][j] = sqrt(d);
     }
     __syncthreads();
-    const double djj = L[j][j];
+    const T djj = L[j][j];
     for (int i = j + 1 + threadIdx.x; i < nb; i += blockDim.x) L[i][j] /= djj;
     __syncthreads();
     for (int o = threadIdx.x; o < (nb - j - 1) * (nb - j - 1); o += blockDim.x) {
@@ -329,15 +330,15 @@ __global__ void __launch_bounds__(256) k_chol_diag(double* A, int n, int k0, dou
   }
   for (int o = threadIdx.x; o < nb * nb; o += blockDim.x) {
     const int i = o / nb, j = o % nb;
-    A[(size_t)(k0 + i) * n + k0 + j] = (j <= i) ? L[i][j] : 0.0;
+    A[(size_t)(k0 + i) * n + k0 + j] = (j <= i) ? L[i][j] : T(0);
   }
-  (void)lambda_first;
 }
 
 // panel below the diagonal block: A_ik <- A_ik L_kk^-T, one CTA per CB rows
-__global__ void __launch_bounds__(CB) k_chol_trsm(double* A, int n, int k0) {
-  __shared__ double L[CB][CB + 1];
-  __shared__ double X[CB][CB + 1];
+template <typename T>
+__global__ void __launch_bounds__(CB) k_chol_trsm(T* A, int n, int k0) {
+  __shared__ T L[CB][CB + 1];
+  __shared__ T X[CB][CB + 1];
   const int r0 = k0 + CB + blockIdx.x * CB;
   const int nb = min(CB, n - k0);
   const int nr = min(CB, n - r0);
@@ -347,7 +348,7 @@ __global__ void __launch_bounds__(CB) k_chol_trsm(double* A, int n, int k0) {
   const int r = threadIdx.x;
   if (r < nr) {
     for (int j = 0; j < nb; ++j) {
-      double s = X[r][j];
+      T s = X[r][j];
       for (int l = 0; l < j; ++l) s -= X[r][l] * L[j][l];
       X[r][j] = s / L[j][j];
     }
@@ -357,8 +358,9 @@ __global__ void __launch_bounds__(CB) k_chol_trsm(double* A, int n, int k0) {
 }
 
 // trailing update A_ij -= A_ik A_jk^T for the lower-triangle tiles right of/below the panel
-__global__ void __launch_bounds__(256) k_chol_update(double* A, int n, int k0) {
-  __shared__ double As[CB][CB + 1], Bs[CB][CB + 1];
+template <typename T>
+__global__ void __launch_bounds__(256) k_chol_update(T* A, int n, int k0) {
+  __shared__ T As[CB][CB + 1], Bs[CB][CB + 1];
   const int nt = (n - k0 - CB + CB - 1) / CB;
   int t = blockIdx.x, ti = 0;
   while (t >= ti + 1) { t -= ti + 1; ++ti; }
@@ -367,14 +369,14 @@ __global__ void __launch_bounds__(256) k_chol_update(double* A, int n, int k0) {
   const int r0 = k0 + CB + ti * CB, c0 = k0 + CB + tj * CB;
   for (int o = threadIdx.x; o < CB * CB; o += blockDim.x) {
     const int rr = o / CB, kk = o % CB;
-    As[kk][rr] = (r0 + rr < n) ? A[(size_t)(r0 + rr) * n + k0 + kk] : 0.0;
-    Bs[kk][rr] = (c0 + rr < n) ? A[(size_t)(c0 + rr) * n + k0 + kk] : 0.0;
+    As[kk][rr] = (r0 + rr < n) ? A[(size_t)(r0 + rr) * n + k0 + kk] : T(0);
+    Bs[kk][rr] = (c0 + rr < n) ? A[(size_t)(c0 + rr) * n + k0 + kk] : T(0);
   }
   __syncthreads();
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  double acc[4][4] = {};
+  T acc[4][4] = {};
   for (int kk = 0; kk < CB; ++kk) {
-    double a[4], b[4];
+    T a[4], b[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) { a[i] = As[kk][ty * 4 + i]; b[i] = Bs[kk][tx * 4 + i]; }
 #pragma unroll
@@ -396,16 +398,19 @@ __global__ void k_add_diag(double* A, int n, int nreal, double lambda) {
     A[(size_t)i * n + i] += (i < nreal) ? lambda : 1.0;  // a padding index gets 1 (its rhs is 0)
 }
 
-// L y = b then L^T x = y, one CTA of 1024 threads, blocked by CB
-__global__ void __launch_bounds__(1024) k_chol_solve(const double* L, int n, const double* b, double* x) {
-  extern __shared__ double v[];  // n
-  for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = b[i];
+// L y = b then L^T x = y (x += the solution when accumulate), one CTA of 1024 threads,
+// blocked by CB; the right-hand side is carried in T
+template <typename T>
+__global__ void __launch_bounds__(1024) k_chol_solve(const T* L, int n, const double* b, double* x, int accumulate) {
+  extern __shared__ unsigned char solve_smem[];
+  T* v = reinterpret_cast<T*>(solve_smem);  // n
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = (T)b[i];
   __syncthreads();
   for (int k0 = 0; k0 < n; k0 += CB) {
     const int nb = min(CB, n - k0);
     if (threadIdx.x < 32) {
       for (int j = 0; j < nb; ++j) {
-        double s = 0.0;
+        T s = 0;
         for (int l = threadIdx.x; l < j; l += 32) s += L[(size_t)(k0 + j) * n + k0 + l] * v[k0 + l];
         s = warp_sum(s);
         if (threadIdx.x == 0) v[k0 + j] = (v[k0 + j] - s) / L[(size_t)(k0 + j) * n + k0 + j];
@@ -414,7 +419,7 @@ __global__ void __launch_bounds__(1024) k_chol_solve(const double* L, int n, con
     }
     __syncthreads();
     for (int i = k0 + nb + threadIdx.x; i < n; i += blockDim.x) {
-      double s = 0.0;
+      T s = 0;
       for (int l = 0; l < nb; ++l) s += L[(size_t)i * n + k0 + l] * v[k0 + l];
       v[i] -= s;
     }
@@ -424,7 +429,7 @@ __global__ void __launch_bounds__(1024) k_chol_solve(const double* L, int n, con
     const int nb = min(CB, n - k0);
     if (threadIdx.x < 32) {
       for (int j = nb - 1; j >= 0; --j) {
-        double s = 0.0;
+        T s = 0;
         for (int l = j + 1 + threadIdx.x; l < nb; l += 32) s += L[(size_t)(k0 + l) * n + k0 + j] * v[k0 + l];
         s = warp_sum(s);
         if (threadIdx.x == 0) v[k0 + j] = (v[k0 + j] - s) / L[(size_t)(k0 + j) * n + k0 + j];
@@ -433,13 +438,37 @@ __global__ void __launch_bounds__(1024) k_chol_solve(const double* L, int n, con
     }
     __syncthreads();
     for (int i = threadIdx.x; i < k0; i += blockDim.x) {
-      double s = 0.0;
+      T s = 0;
       for (int l = 0; l < nb; ++l) s += L[(size_t)(k0 + l) * n + i] * v[k0 + l];
       v[i] -= s;
     }
     __syncthreads();
   }
-  for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = v[i];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = (accumulate ? x[i] : 0.0) + (double)v[i];
+}
+
+// blocked factorisation of the lower triangle of A (n x n) in place; returns launches
+template <typename T>
+static long long chol_factor(T* A, int n, int* bad, cudaStream_t s) {
+  long long launches = 0;
+  for (int k0 = 0; k0 < n; k0 += CB) {
+    k_chol_diag<T><<<1, 256, 0, s>>>(A, n, k0, bad);
+    ++launches;
+    const int rest = n - k0 - CB;
+    if (rest > 0) {
+      const int nrb = (rest + CB - 1) / CB;
+      k_chol_trsm<T><<<nrb, CB, 0, s>>>(A, n, k0);
+      k_chol_update<T><<<nrb * (nrb + 1) / 2, 256, 0, s>>>(A, n, k0);
+      launches += 2;
+    }
+  }
+  return launches;
+}
+
+template <typename T>
+static void chol_apply(const T* L, int n, const double* b, double* x, int accumulate, cudaStream_t s) {
+  cudaFuncSetAttribute(k_chol_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(T) * n));
+  k_chol_solve<T><<<1, 1024, sizeof(T) * n, s>>>(L, n, b, x, accumulate);
 }
 
 __global__ void k_chol_info(const int* bad, int nreal, double* info) {
@@ -456,20 +485,85 @@ long long chol_solve(double* A, int n, int nreal, double lambda, const double* e
   cudaMemsetAsync(bad, 0, sizeof(int), s);
   k_add_diag<<<(n + 255) / 256, 256, 0, s>>>(A, n, nreal, lambda);
   ++launches;
-  for (int k0 = 0; k0 < n; k0 += CB) {
-    k_chol_diag<<<1, 256, 0, s>>>(A, n, k0, lambda, bad);
-    ++launches;
-    const int rest = n - k0 - CB;
-    if (rest > 0) {
-      const int nrb = (rest + CB - 1) / CB;
-      k_chol_trsm<<<nrb, CB, 0, s>>>(A, n, k0);
-      k_chol_update<<<nrb * (nrb + 1) / 2, 256, 0, s>>>(A, n, k0);
-      launches += 2;
+  launches += chol_factor<double>(A, n, bad, s);
+  chol_apply<double>(A, n, ebar, x, 0, s);
+  k_chol_info<<<1, 1, 0, s>>>(bad, nreal, info);
+  launches += 2;
+  *err = cudaGetLastError();
+  return launches;
+}
+
+// ---- mixed-precision solve: FP32 factor of T + lambda, FP64 residuals
+// A32 (lower) = float(A + d) with d_i = lambda (i < nreal) or 1 (padding); the FP64 A is kept
+__global__ void k_lower_to_f32(const double* A, float* A32, int n, int nreal, double lambda) {
+  const size_t nn = (size_t)n * n;
+  for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < nn; o += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(o / n), j = (int)(o % n);
+    double v = (j <= i) ? A[o] : 0.0;
+    if (i == j) v += (i < nreal) ? lambda : 1.0;
+    A32[o] = (float)v;
+  }
+}
+
+// A[j][i] = A[i][j] for j > i (the Gram kernels may leave the upper triangle unset)
+__global__ void k_mirror(double* A, int n) {
+  const size_t nn = (size_t)n * n;
+  for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < nn; o += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(o / n), j = (int)(o % n);
+    if (j > i) A[o] = A[(size_t)j * n + i];
+  }
+}
+
+// r = b - (A + d) x, one warp per row; rn[0] += |r|^2, rn[1] += |b|^2 (rn zeroed by the caller)
+__global__ void k_residual(const double* __restrict__ A, int n, int nreal, double lambda, const double* b,
+                           const double* x, double* r, double* rn) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
+  double acc_r = 0.0, acc_b = 0.0;
+  for (int i = warp; i < n; i += nwarps) {
+    double sacc = 0.0;
+    for (int j = lane; j < n; j += 32) sacc += A[(size_t)i * n + j] * x[j];
+    sacc = warp_sum(sacc);
+    const double ri = b[i] - sacc - ((i < nreal) ? lambda : 1.0) * x[i];
+    if (lane == 0) {
+      r[i] = ri;
+      acc_r += ri * ri;
+      acc_b += b[i] * b[i];
     }
   }
-  cudaFuncSetAttribute(k_chol_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(double) * n));
-  k_chol_solve<<<1, 1024, sizeof(double) * n, s>>>(A, n, ebar, x);
-  k_chol_info<<<1, 1, 0, s>>>(bad, nreal, info);
+  if (lane == 0) {
+    atomicAdd(rn, acc_r);
+    atomicAdd(rn + 1, acc_b);
+  }
+}
+
+__global__ void k_mixed_info(const int* bad, int nreal, const double* rn, int iters, double* info) {
+  info[0] = *bad ? -1.0 : (double)nreal;
+  info[1] = (rn[1] > 0.0) ? sqrt(rn[0] / rn[1]) : 0.0;
+  info[2] = (double)iters;
+}
+
+long long chol_solve_mixed(double* A, float* A32, int n, int nreal, double lambda, const double* ebar, double* x,
+                           double* r, double* rn, int iters, int* bad, double* info, cudaStream_t s,
+                           cudaError_t* err) {
+  long long launches = 0;
+  cudaMemsetAsync(bad, 0, sizeof(int), s);
+  k_mirror<<<1024, 256, 0, s>>>(A, n);
+  k_lower_to_f32<<<1024, 256, 0, s>>>(A, A32, n, nreal, lambda);
+  launches += 2;
+  launches += chol_factor<float>(A32, n, bad, s);
+  chol_apply<float>(A32, n, ebar, x, 0, s);
+  ++launches;
+  const int rgrid = (n + 7) / 8;
+  for (int it = 0; it < iters; ++it) {
+    cudaMemsetAsync(rn, 0, 2 * sizeof(double), s);
+    k_residual<<<rgrid, 256, 0, s>>>(A, n, nreal, lambda, ebar, x, r, rn);
+    chol_apply<float>(A32, n, r, x, 1, s);
+    launches += 2;
+  }
+  cudaMemsetAsync(rn, 0, 2 * sizeof(double), s);
+  k_residual<<<rgrid, 256, 0, s>>>(A, n, nreal, lambda, ebar, x, r, rn);
+  k_mixed_info<<<1, 1, 0, s>>>(bad, nreal, rn, iters, info);
   launches += 2;
   *err = cudaGetLastError();
   return launches;

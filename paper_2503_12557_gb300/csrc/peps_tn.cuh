@@ -54,6 +54,13 @@ struct GeoS {
                        s2 = CHI * DD * DD * CHI;
 };
 
+// Row length D chi of the truncation's Jacobi step when it is a compile-time constant, else 0.
+template <typename G> struct GeoLr { static constexpr int value = 0; };
+template <int CHI, int DD> struct GeoLr<GeoS<CHI, DD>> { static constexpr int value = CHI * DD; };
+// Row count chi D^2 of the left pass's QR when it is a compile-time constant, else 0.
+template <typename G> struct GeoMz { static constexpr int value = 0; };
+template <int CHI, int DD> struct GeoMz<GeoS<CHI, DD>> { static constexpr int value = CHI * DD * DD; };
+
 // ------------------------------------------------------------------------------------------
 // buffer plan: every kernel carves its buffers out of dynamic shared memory or out of a
 // per-CTA slice of a global scratch arena, as the host planner decided.
@@ -165,6 +172,7 @@ __device__ double blk_normalize(T* v, int n, double* red, int* st) {
 // A[l][d][r][u], the lower-environment orientation).
 template <typename T, typename G>
 __device__ void load_A(T* As, const T* Tpad, const G& g, int site, int s, bool swap_ud) {
+  if ((unsigned)s >= (unsigned)g.d) s = 0;  // a local state outside [0, d) is not valid input: read as 0
   const T* src = Tpad + ((size_t)site * g.d + s) * g.sT;
   const int D = g.D;
   for (int o = threadIdx.x; o < g.sT; o += blockDim.x) {
@@ -199,7 +207,7 @@ __device__ __forceinline__ void qr_apply_reflector(const T* zj, int j, T tau, T*
 // the rest of the panel), then every warp applies the panel's reflectors, in order, to the
 // trailing columns it owns.  Two block barriers per panel.  taus: at least nc entries.
 template <typename T>
-__device__ void qr_keep_r(T* Z, int m, int nc, T* R, T* taus) {
+__device__ void qr_keep_r_smem(T* Z, int m, int nc, T* R, T* taus) {
   constexpr int QB = 8;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   const int steps = (m < nc) ? m : nc;
@@ -248,6 +256,205 @@ __device__ void qr_keep_r(T* Z, int m, int nc, T* R, T* taus) {
   __syncthreads();
 }
 
+// Panel of QB columns (j0 .. j0+pb-1) factored by one warp with the columns in registers
+// (element i = lane + 32 r, m <= 32 RPL): per column one warp reduction for the norm and one
+// independent reduction per remaining panel column, no shared-memory round trips.
+template <typename T, int RPL, int QB>
+__device__ __forceinline__ void qr_panel_reg(T* Z, int m, int j0, int pb, T* taus, int lane) {
+  T zp[QB][RPL];
+#pragma unroll
+  for (int q = 0; q < QB; ++q)
+#pragma unroll
+    for (int r = 0; r < RPL; ++r) {
+      const int i = lane + 32 * r;
+      zp[q][r] = (q < pb && i < m) ? Z[(size_t)(j0 + q) * m + i] : T(0);
+    }
+#pragma unroll
+  for (int jj = 0; jj < QB; ++jj) {
+    if (jj < pb) {
+      const int j = j0 + jj;
+      T part = 0, aj = 0;
+#pragma unroll
+      for (int r = 0; r < RPL; ++r) {
+        const int i = lane + 32 * r;
+        if (i > j) part += zp[jj][r] * zp[jj][r];
+        if (r == (j >> 5)) aj = zp[jj][r];
+      }
+      const T sigma = warp_sum(part);
+      const T alpha = __shfl_sync(0xffffffffu, aj, j & 31);
+      T tau = 0, beta = alpha;
+      if (sigma != T(0)) {
+        const T nrm = sqrt(alpha * alpha + sigma);
+        beta = (alpha >= T(0)) ? -nrm : nrm;
+        tau = (beta - alpha) / beta;
+        const T sc = T(1) / (alpha - beta);
+#pragma unroll
+        for (int r = 0; r < RPL; ++r)
+          if (lane + 32 * r > j) zp[jj][r] *= sc;
+      }
+      if (tau != T(0)) {
+        // v = (1 at row j, the scaled column below it); column q <- column q - tau v (v . column q)
+        T v[RPL];
+#pragma unroll
+        for (int r = 0; r < RPL; ++r) {
+          const int i = lane + 32 * r;
+          v[r] = (i > j) ? zp[jj][r] : (i == j ? T(1) : T(0));
+        }
+        T d[QB];
+#pragma unroll
+        for (int q = jj + 1; q < QB; ++q) {
+          T s = 0;
+#pragma unroll
+          for (int r = 0; r < RPL; ++r) s += v[r] * zp[q][r];
+          d[q] = s;
+        }
+#pragma unroll
+        for (int q = jj + 1; q < QB; ++q) d[q] = tau * warp_sum(d[q]);
+#pragma unroll
+        for (int q = jj + 1; q < QB; ++q)
+          if (q < pb)
+#pragma unroll
+            for (int r = 0; r < RPL; ++r) zp[q][r] -= v[r] * d[q];
+      }
+#pragma unroll
+      for (int r = 0; r < RPL; ++r)
+        if (lane + 32 * r == j) zp[jj][r] = beta;
+      if (lane == 0) taus[j] = tau;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < QB; ++q)
+#pragma unroll
+    for (int r = 0; r < RPL; ++r) {
+      const int i = lane + 32 * r;
+      if (q < pb && i < m) Z[(size_t)(j0 + q) * m + i] = zp[q][r];
+    }
+}
+
+// Register form of the same blocked factorisation (m <= 32 RPL).
+//   Panel (warp 0): after column j's reflector is formed, its products with every remaining
+//   panel column are taken in one pass over the rows and summed over the warp together, so a
+//   panel column costs two warp reductions instead of one per remaining column.
+//   Trailing update (all warps): a warp loads one trailing column into registers (element
+//   i = lane + 32 r), applies the panel's reflectors to it in order and stores it once.
+template <typename T, int RPL>
+__device__ __noinline__ void qr_keep_r_reg(T* Z, int m, int nc, T* R, T* taus) {
+  constexpr int QB = 8;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int steps = (m < nc) ? m : nc;
+  for (int j0 = 0; j0 < steps; j0 += QB) {
+    const int pb = (steps - j0 < QB) ? steps - j0 : QB;
+    if (warp == 0) {
+      if constexpr (RPL * QB * sizeof(T) <= (sizeof(T) == 8 ? 640 : 256)) {
+        qr_panel_reg<T, RPL, QB>(Z, m, j0, pb, taus, lane);
+      } else {
+        for (int jj = 0; jj < pb; ++jj) {
+          const int j = j0 + jj;
+          T* zj = Z + (size_t)j * m;
+          T part = 0;
+          for (int i = j + 1 + lane; i < m; i += 32) part += zj[i] * zj[i];
+          const T sigma = warp_sum(part);
+          const T alpha = zj[j];
+          T tau = 0, beta = alpha;
+          if (sigma != T(0)) {
+            const T nrm = sqrt(alpha * alpha + sigma);
+            beta = (alpha >= T(0)) ? -nrm : nrm;
+            tau = (beta - alpha) / beta;
+            const T sc = T(1) / (alpha - beta);
+            for (int i = j + 1 + lane; i < m; i += 32) zj[i] *= sc;
+          }
+          __syncwarp();
+          const int nrem = j0 + pb - 1 - j;  // panel columns right of j
+          if (tau != T(0) && nrem > 0) {
+            T* zc0 = Z + (size_t)(j + 1) * m;
+            T d[QB - 1];
+#pragma unroll
+            for (int q = 0; q < QB - 1; ++q) d[q] = 0;
+            for (int i = j + 1 + lane; i < m; i += 32) {
+              const T v = zj[i];
+#pragma unroll
+              for (int q = 0; q < QB - 1; ++q)
+                if (q < nrem) d[q] += v * zc0[(size_t)q * m + i];
+            }
+#pragma unroll
+            for (int q = 0; q < QB - 1; ++q)
+              if (q < nrem) d[q] = tau * (warp_sum(d[q]) + zc0[(size_t)q * m + j]);
+            __syncwarp();
+            for (int i = j + 1 + lane; i < m; i += 32) {
+              const T v = zj[i];
+#pragma unroll
+              for (int q = 0; q < QB - 1; ++q)
+                if (q < nrem) zc0[(size_t)q * m + i] -= v * d[q];
+            }
+            if (lane == 0) {
+#pragma unroll
+              for (int q = 0; q < QB - 1; ++q)
+                if (q < nrem) zc0[(size_t)q * m + j] -= d[q];
+            }
+          }
+          if (lane == 0) {
+            taus[j] = tau;
+            zj[j] = beta;
+          }
+          __syncwarp();
+        }
+      }
+    }
+    __syncthreads();
+    for (int c = j0 + pb + warp; c < nc; c += nw) {
+      T* zc = Z + (size_t)c * m;
+      T z[RPL];
+#pragma unroll
+      for (int r = 0; r < RPL; ++r) {
+        const int i = lane + 32 * r;
+        z[r] = (i < m) ? zc[i] : T(0);
+      }
+      for (int jj = 0; jj < pb; ++jj) {
+        const int j = j0 + jj;
+        const T tau = taus[j];
+        if (tau == T(0)) continue;
+        const T* v = Z + (size_t)j * m;  // reflector: 1 at row j, v[i] below, 0 above
+        T vr[RPL];
+        T sdot = 0;
+#pragma unroll
+        for (int r = 0; r < RPL; ++r) {
+          const int i = lane + 32 * r;
+          vr[r] = (i > j && i < m) ? v[i] : (i == j ? T(1) : T(0));
+          sdot += vr[r] * z[r];
+        }
+        const T wj = tau * warp_sum(sdot);
+#pragma unroll
+        for (int r = 0; r < RPL; ++r) z[r] -= vr[r] * wj;
+      }
+#pragma unroll
+      for (int r = 0; r < RPL; ++r) {
+        const int i = lane + 32 * r;
+        if (i < m) zc[i] = z[r];
+      }
+    }
+    __syncthreads();
+  }
+  for (int o = tid; o < nc * nc; o += blockDim.x) {
+    const int i = o / nc, c = o % nc;
+    R[o] = (i <= c && i < m) ? Z[(size_t)c * m + i] : T(0);
+  }
+  __syncthreads();
+}
+
+// Dispatch on the row count; MC > 0: m is the compile-time MC.
+template <typename T, int MC = 0>
+__device__ void qr_keep_r(T* Z, int m, int nc, T* R, T* taus) {
+  if constexpr (MC > 0) {
+    constexpr int RPL = (MC + 31) / 32;
+    if constexpr (RPL <= 24) qr_keep_r_reg<T, RPL>(Z, MC, nc, R, taus);
+    else qr_keep_r_smem(Z, m, nc, R, taus);
+  } else {
+    if (m <= 256) qr_keep_r_reg<T, 8>(Z, m, nc, R, taus);
+    else if (m <= 768) qr_keep_r_reg<T, 24>(Z, m, nc, R, taus);
+    else qr_keep_r_smem(Z, m, nc, R, taus);
+  }
+}
+
 // Round-robin ("chess tournament") ordering of m (even) players: player at position j in
 // round r.  Every round pairs position j with position m-1-j; the pairs of one round are
 // disjoint and every pair meets once per m-1 rounds.
@@ -287,7 +494,7 @@ __device__ void zero_tiny_rows(T* X, int m, int L, int ldx, T tiny) {
 //   that a pair check costs one dot product.
 // Returns the number of sweeps, or -1 when the sweep limit was hit.
 template <typename T>
-__device__ int hestenes_rows(T* X, int m, int L, int ldx, int* flag, unsigned long long* ctr, double* red, T* nrm) {
+__device__ int hestenes_rows_smem(T* X, int m, int L, int ldx, int* flag, unsigned long long* ctr, double* red, T* nrm) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int grp = lane >> 3, sub = lane & 7, ngroups = nw * 4;
   const unsigned gmask = 0xffu << (grp * 8);
@@ -363,6 +570,205 @@ __device__ int hestenes_rows(T* X, int m, int L, int ldx, int* flag, unsigned lo
   return -1;
 }
 
+// Rotation of a pair with squared norms a, b and dot product c, when it is not yet orthogonal
+// to the relative tolerance and neither row is numerically zero: zeta = (b - a) / (2c),
+// t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)) (the smaller root of t^2 + 2 zeta t - 1 = 0,
+// which makes the rotated rows orthogonal), cos = 1 / sqrt(1 + t^2), sin = cos t, and t c for
+// the norm updates.  FP32 takes the reciprocal square roots from the SFU (about 2 ulp).
+__device__ __forceinline__ void jac_params(double a, double b, double c, double tol, double tiny, double& cs,
+                                           double& sn, double& tc) {
+  if (c != 0.0 && a > tiny && b > tiny && fabs(c) > tol * sqrt(a * b)) {
+    const double zeta = (b - a) / (2.0 * c);
+    const double t = (fabs(zeta) > 1e15) ? 0.5 / zeta : copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+    cs = 1.0 / sqrt(1.0 + t * t);
+    sn = cs * t;
+    tc = t * c;
+  }
+}
+__device__ __forceinline__ void jac_params(float a, float b, float c, float tol, float tiny, float& cs, float& sn,
+                                           float& tc) {
+  if (c != 0.f && a > tiny && b > tiny && fabsf(c) * rsqrtf(a) * rsqrtf(b) > tol) {
+    const float zeta = (b - a) / (2.f * c);
+    const float az = fabsf(zeta);
+    const float t = (az > 1e15f) ? 0.5f / zeta : copysignf(1.f, zeta) / (az + sqrtf(fmaf(zeta, zeta, 1.f)));
+    cs = rsqrtf(fmaf(t, t, 1.f));
+    sn = cs * t;
+    tc = t * c;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Register form of the same one-sided Jacobi, one 8-lane group per pair (rows of length
+// L <= 8 E8, element i = u + 8 e of a row in lane u of a group).
+//   The rows are grouped in blocks of four (rows at or beyond m are absent and act as zero
+//   rows) and the blocks meet in a round-robin tournament.  In each super-round a warp holds
+//   one pair of blocks (P, Q): group g keeps row P_g and, in round t = 0..3, row Q_(g+t)%4,
+//   so the four groups rotate four disjoint cross pairs per round; between rounds every group
+//   passes its Q row to the group below (one shuffle per element).  In the first super-round
+//   of a sweep the 12 pairs inside the two blocks are rotated too: the two groups holding such
+//   a pair both compute its rotation from the same values (identical results) and each
+//   updates its own row.  Every pair of rows meets once per sweep, as in the row-level
+//   ordering, with one block barrier per super-round and the rows read and written once per
+//   super-round.  A group sums its dot product over its 8 lanes by an xor butterfly, which
+//   leaves the same bits in all 8 lanes.
+template <typename T>
+__device__ __forceinline__ T grp_sum8(T v) {
+  v += __shfl_xor_sync(0xffffffffu, v, 4);
+  v += __shfl_xor_sync(0xffffffffu, v, 2);
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  return v;
+}
+
+template <typename T, int E8>
+__device__ __noinline__ int hestenes_rows_grp(T* X, int m, int L, int ldx, int* flag, unsigned long long* ctr,
+                                              double* red, T* nrm) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int g = lane >> 3, u = lane & 7;
+  const T eps = JacobiTol<T>::eps;
+  const T tol = T(L) * eps;
+  const int NB = ((m + 7) / 8) * 2;  // blocks of four rows, an even number of them
+  // tiny = (L eps)^2 times the largest squared row norm
+  T nmax = 0;
+  for (int p = warp; p < m; p += nw) {
+    T s = 0;
+    for (int i = lane; i < L; i += 32) s += X[(size_t)p * ldx + i] * X[(size_t)p * ldx + i];
+    nmax = fmax(nmax, warp_sum(s));
+  }
+  nmax = block_max(nmax, red);
+  const T tiny = nmax * (T(L) * eps) * (T(L) * eps);
+  unsigned long long nrot = 0;
+  for (int sweep = 0; sweep < JacobiTol<T>::sweeps; ++sweep) {
+    if (threadIdx.x == 0) *flag = 0;
+    __syncthreads();
+    int rotated = 0;
+    for (int s = 0; s < NB - 1; ++s) {
+      for (int bp = warp; bp < NB / 2; bp += nw) {
+        const int bP = rr_player(bp, s, NB), bQ = rr_player(NB - 1 - bp, s, NB);
+        const int rp = 4 * bP + g;
+        int rq = 4 * bQ + g;
+        T xp[E8], xq[E8];
+#pragma unroll
+        for (int e = 0; e < E8; ++e) {
+          const int i = u + 8 * e;
+          xp[e] = (rp < m && i < L) ? X[(size_t)rp * ldx + i] : T(0);
+          xq[e] = (rq < m && i < L) ? X[(size_t)rq * ldx + i] : T(0);
+        }
+        T np, nq;
+        if (s == 0) {
+          // exact squared norms at the start of every sweep, then the pairs inside each block
+          T ap = 0, aq = 0;
+#pragma unroll
+          for (int e = 0; e < E8; ++e) { ap += xp[e] * xp[e]; aq += xq[e] * xq[e]; }
+          np = grp_sum8(ap);
+          nq = grp_sum8(aq);
+#pragma unroll
+          for (int k = 1; k < 4; ++k) {
+            const bool lo = g < (g ^ k);
+            T yp[E8], yq[E8];
+            T cp = 0, cq = 0;
+#pragma unroll
+            for (int e = 0; e < E8; ++e) {
+              yp[e] = __shfl_xor_sync(0xffffffffu, xp[e], 8 * k);
+              yq[e] = __shfl_xor_sync(0xffffffffu, xq[e], 8 * k);
+              cp += xp[e] * yp[e];
+              cq += xq[e] * yq[e];
+            }
+            const T mp = __shfl_xor_sync(0xffffffffu, np, 8 * k), mq = __shfl_xor_sync(0xffffffffu, nq, 8 * k);
+            cp = grp_sum8(cp);
+            cq = grp_sum8(cq);
+            T csp = 1, snp = 0, tcp = 0, csq = 1, snq = 0, tcq = 0;
+            jac_params(lo ? np : mp, lo ? mp : np, cp, tol, tiny, csp, snp, tcp);
+            jac_params(lo ? nq : mq, lo ? mq : nq, cq, tol, tiny, csq, snq, tcq);
+#pragma unroll
+            for (int e = 0; e < E8; ++e) {
+              xp[e] = lo ? (csp * xp[e] - snp * yp[e]) : (snp * yp[e] + csp * xp[e]);
+              xq[e] = lo ? (csq * xq[e] - snq * yq[e]) : (snq * yq[e] + csq * xq[e]);
+            }
+            np = lo ? fmax(T(0), np - tcp) : np + tcp;
+            nq = lo ? fmax(T(0), nq - tcq) : nq + tcq;
+            if (snp != T(0) || snq != T(0)) rotated = 1;
+            if (lo && u == 0) nrot += (snp != T(0)) + (snq != T(0));
+          }
+        } else {
+          np = (rp < m) ? nrm[rp] : T(0);
+          nq = (rq < m) ? nrm[rq] : T(0);
+        }
+        // the 16 cross pairs: in round t group g pairs P_g with Q_(g+t)%4
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          T c = 0;
+#pragma unroll
+          for (int e = 0; e < E8; ++e) c += xp[e] * xq[e];
+          c = grp_sum8(c);
+          T cs = 1, sn = 0, tc = 0;
+          jac_params(np, nq, c, tol, tiny, cs, sn, tc);
+#pragma unroll
+          for (int e = 0; e < E8; ++e) {
+            const T a = xp[e], b = xq[e];
+            xp[e] = cs * a - sn * b;
+            xq[e] = sn * a + cs * b;
+          }
+          np = fmax(T(0), np - tc);
+          nq = nq + tc;
+          if (sn != T(0)) {
+            rotated = 1;
+            if (u == 0) ++nrot;
+          }
+          if (t < 3) {
+            const int src = (lane + 8) & 31;
+#pragma unroll
+            for (int e = 0; e < E8; ++e) xq[e] = __shfl_sync(0xffffffffu, xq[e], src);
+            nq = __shfl_sync(0xffffffffu, nq, src);
+            rq = 4 * bQ + ((g + t + 1) & 3);
+          }
+        }
+#pragma unroll
+        for (int e = 0; e < E8; ++e) {
+          const int i = u + 8 * e;
+          if (i < L) {
+            if (rp < m) X[(size_t)rp * ldx + i] = xp[e];
+            if (rq < m) X[(size_t)rq * ldx + i] = xq[e];
+          }
+        }
+        if (u == 0) {
+          if (rp < m) nrm[rp] = np;
+          if (rq < m) nrm[rq] = nq;
+        }
+      }
+      __syncthreads();
+    }
+    if (rotated) *flag = 1;  // benign race: every writer stores 1
+    __syncthreads();
+    const int any = *flag;
+    __syncthreads();
+    if (!any) {
+      zero_tiny_rows(X, m, L, ldx, tiny);
+      if (ctr && nrot) atomicAdd(ctr + 1, nrot);
+      if (ctr && threadIdx.x == 0) { atomicAdd(ctr + 0, (unsigned long long)(sweep + 1)); atomicAdd(ctr + 2, 1ull); }
+      return sweep + 1;
+    }
+  }
+  zero_tiny_rows(X, m, L, ldx, tiny);
+  if (ctr && nrot) atomicAdd(ctr + 1, nrot);
+  if (ctr && threadIdx.x == 0) { atomicAdd(ctr + 0, (unsigned long long)JacobiTol<T>::sweeps); atomicAdd(ctr + 2, 1ull); }
+  return -1;
+}
+
+// Dispatch: the 8-lane-group register form for rows of at most 128 elements (best with a row
+// stride ldx = 8 mod 32, so that the four groups' rows fall in different banks), else the
+// shared-memory form.  Same contract as hestenes_rows_smem.  LC > 0: the row length is the compile-time LC.
+template <typename T, int LC = 0>
+__device__ int hestenes_rows(T* X, int m, int L, int ldx, int* flag, unsigned long long* ctr, double* red, T* nrm) {
+  if constexpr (LC > 0) {
+    constexpr int E8 = (LC + 7) / 8;
+    if constexpr (E8 <= 16) return hestenes_rows_grp<T, E8>(X, m, LC, ldx, flag, ctr, red, nrm);
+    else return hestenes_rows_smem(X, m, LC, ldx, flag, ctr, red, nrm);
+  }
+  if (L <= 64) return hestenes_rows_grp<T, 8>(X, m, L, ldx, flag, ctr, red, nrm);
+  if (L <= 128) return hestenes_rows_grp<T, 16>(X, m, L, ldx, flag, ctr, red, nrm);
+  return hestenes_rows_smem(X, m, L, ldx, flag, ctr, red, nrm);
+}
+
 // ------------------------------------------------------------------------------------------
 // Sizes (in elements) of the row step's work buffers, shared by every planner:
 // Z holds the left pass's column-major Z (n D x n) and, later, the right pass's P, Y, X, Vt, C
@@ -370,8 +776,9 @@ __device__ int hestenes_rows(T* X, int m, int L, int ldx, int* flag, unsigned lo
 // D^2 chi + 1.
 __host__ __device__ inline size_t env_z_elems(int chi, int D) {
   const size_t n = (size_t)chi * D, Lr = (size_t)D * chi, LY = Lr + 1, mX = n + (n & 1);
+  const size_t LX = Lr + (size_t)(((8 - (int)Lr) % 32 + 32) % 32);  // X row stride, 8 mod 32
   const size_t zleft = n * D * n;
-  const size_t zright = (size_t)chi * D * D * chi + n * LY + mX * LY + (size_t)chi * LY + n * chi + (size_t)chi * D * chi;
+  const size_t zright = (size_t)chi * D * D * chi + n * LY + mX * LX + (size_t)chi * LY + n * chi + (size_t)chi * D * chi;
   return zleft > zright ? zleft : zright;
 }
 __host__ __device__ inline size_t env_w_elems(int chi, int D, int ci) { return (size_t)ci * ((size_t)D * D * chi + 1); }
@@ -434,18 +841,20 @@ __device__ double env_row_step(const G& g, const T* Eprev, T* Eout, const T* Tpa
       }
       __syncthreads();
     }
-    qr_keep_r(w.Z, mZ, n, w.R, w.sig);
+    qr_keep_r<T, GeoMz<G>::value>(w.Z, mZ, n, w.R, w.sig);
     blk_copy(w.Rhist + (size_t)k * n * n, w.R, n * n);
     __syncthreads();
   }
   // ---- right pass
-  // Y, X and Vt rows are padded to LY = Lr + 1 so that rows read side by side hit different
-  // shared-memory banks
+  // Y and Vt rows are padded to LY = Lr + 1 so that rows read side by side hit different
+  // shared-memory banks; X rows to LX = 8 mod 32, the stride at which the Jacobi's four lane
+  // groups (eight consecutive elements of four rows each) hit different banks
   const int LY = Lr + 1;
+  const int LX = Lr + ((8 - Lr) % 32 + 32) % 32;
   T* P = w.Z;                              // chi*D*D*chi
   T* Y = P + (size_t)chi * D * D * chi;    // n x Lr   (ld LY)
-  T* X = Y + (size_t)n * LY;               // mX x Lr  (ld LY)
-  T* Vt = X + (size_t)mX * LY;             // chi x Lr (ld LY)
+  T* X = Y + (size_t)n * LY;               // mX x Lr  (ld LX)
+  T* Vt = X + (size_t)mX * LX;             // chi x Lr (ld LY)
   T* Cn = Vt + (size_t)chi * LY;           // n x chi
   T* Bs = Cn + (size_t)n * chi;            // chi x D x chi (site being written)
   // C_{Ly-1}[(b,r)][c] = delta_{(b,r),0} delta_{c,0}
@@ -503,29 +912,34 @@ __device__ double env_row_step(const G& g, const T* Eprev, T* Eout, const T* Tpa
       T s = 0;
       if (i < n)
         for (int j = i; j < n; ++j) s += w.R[(size_t)i * n + j] * Y[(size_t)j * LY + q];
-      X[(size_t)i * LY + q] = s;
+      X[(size_t)i * LX + q] = s;
     }
     __syncthreads();
-    const int sweeps = hestenes_rows(X, mX, Lr, LY, flag, w.ctr, w.red, w.sig);
+    const int sweeps = hestenes_rows<T, GeoLr<G>::value>(X, mX, Lr, LX, flag, w.ctr, w.red, w.sig);
     if (sweeps < 0 && tid == 0) *st |= ST_NOCONV;
     // singular values = row norms
     {
       const int lane = tid & 31, warp = tid >> 5, nw = NT >> 5;
       for (int p = warp; p < mX; p += nw) {
         T s = 0;
-        for (int i = lane; i < Lr; i += 32) s += X[(size_t)p * LY + i] * X[(size_t)p * LY + i];
+        for (int i = lane; i < Lr; i += 32) s += X[(size_t)p * LX + i] * X[(size_t)p * LX + i];
         s = warp_sum(s);
         if (lane == 0) w.sig[p] = sqrt(s);
       }
     }
     __syncthreads();
-    // stable descending rank; the first chi ranks are kept
+    // stable descending rank; the first chi ranks are kept.  A NaN singular value (non-finite
+    // input) ranks below every number, so that the ranks stay a permutation and every kept
+    // index is valid; the sample is flagged.
     for (int p = tid; p < mX; p += NT) {
       const T sp = w.sig[p];
+      const T kp = (sp == sp) ? sp : T(-1);
+      if (!(sp == sp) || isinf(sp)) atomicOr(st, (int)ST_NONFINITE);
       int rk = 0;
       for (int q = 0; q < mX; ++q) {
         const T sq = w.sig[q];
-        rk += (sq > sp) || (sq == sp && q < p);
+        const T kq = (sq == sq) ? sq : T(-1);
+        rk += (kq > kp) || (kq == kp && q < p);
       }
       w.sel[mX + p] = rk;          // rank of row p
       if (rk < chi) w.sel[rk] = p; // row holding rank rk
@@ -562,7 +976,7 @@ __device__ double env_row_step(const G& g, const T* Eprev, T* Eout, const T* Tpa
       if (cp < nkeep) {
         const int p = w.sel[cp];
         const T s = w.sig[p];
-        if (s > T(0)) v = X[(size_t)p * LY + q] / s;
+        if (s > T(0)) v = X[(size_t)p * LX + q] / s;
       }
       Vt[(size_t)cp * LY + q] = v;
     }

@@ -19,12 +19,13 @@ PREC_FP64, PREC_FP32 = 0, 1
 MOVE_EXCHANGE, MOVE_FLIP = 0, 1
 ST_NEAR_DEGENERATE, ST_ZERO_NORM, ST_NONFINITE, ST_NOCONV = 1, 2, 4, 8
 
-_ERRORS = {-1: "PEPS_E_ARG", -2: "PEPS_E_SHAPE", -3: "PEPS_E_WORKSPACE", -4: "PEPS_E_CUDA", -5: "PEPS_E_UNSUPPORTED"}
+_ERRORS = {-1: "PEPS_E_ARG", -2: "PEPS_E_SHAPE", -3: "PEPS_E_WORKSPACE", -4: "PEPS_E_CUDA", -5: "PEPS_E_UNSUPPORTED",
+           -6: "PEPS_E_CAPACITY", 1: "PEPS_W_NUMERIC"}
 
 
 class _Config(C.Structure):
     _fields_ = [("Lx", C.c_int), ("Ly", C.c_int), ("d", C.c_int), ("D", C.c_int), ("chi", C.c_int),
-                ("prec", C.c_int), ("max_samples", C.c_int), ("gram", C.c_int)]
+                ("prec", C.c_int), ("max_samples", C.c_int), ("gram", C.c_int), ("solve", C.c_int)]
 
 
 class _Term(C.Structure):
@@ -163,12 +164,14 @@ class Hamiltonian:
 class PEPS:
     """One handle of the C library: a lattice, chi and a precision."""
 
-    def __init__(self, Lx, Ly, d, D, chi, prec=PREC_FP64, max_samples=4096, gram=0):
+    def __init__(self, Lx, Ly, d, D, chi, prec=PREC_FP64, max_samples=4096, gram=0, solve=0):
         self.L = load()
         self.Lx, self.Ly, self.d, self.D, self.chi, self.prec = Lx, Ly, d, D, chi, prec
         self.max_samples = max_samples
         self.gram = gram
-        cfg = _Config(Lx, Ly, d, D, chi, prec, max_samples, gram)
+        self.last_warning = None
+        self.solve = solve
+        cfg = _Config(Lx, Ly, d, D, chi, prec, max_samples, gram, solve)
         h = C.c_void_p()
         st = self.L.peps_create(C.byref(h), C.byref(cfg))
         if st != 0:
@@ -189,6 +192,11 @@ class PEPS:
             pass
 
     def _check(self, st, what):
+        self.last_warning = None
+        if st > 0:  # PEPS_W_NUMERIC: the call completed with a numerical warning
+            msg = self.L.peps_last_error(self.h)
+            self.last_warning = f"{what}: {msg.decode() if msg else 'numerical warning'}"
+            return
         if st != 0:
             msg = self.L.peps_last_error(self.h)
             raise RuntimeError(f"{what} failed: {_ERRORS.get(st, st)}: {msg.decode() if msg else ''}")

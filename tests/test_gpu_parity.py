@@ -181,6 +181,30 @@ def test_empty_batch_and_argument_errors(P):
         P.PEPS(3, 3, 2, 4, 2)  # chi < D
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_nonfinite_parameters_flag_and_stay_in_bounds(P, prec):
+    # NaN / Inf in theta: every sample is flagged PEPS_ST_NONFINITE (the truncation's rank
+    # selection keeps a valid permutation of indices with NaN singular values), and sampling
+    # with such ratios rejects every move
+    w = I.WORKLOADS["heis8x8_D4_chi16"]
+    lat = I.Lattice(w["Lx"], w["Ly"], w["d"], w["D"])
+    th = I.peps_random(lat, w["seed_theta"], **w["init"])
+    th[::97] = np.nan
+    th[5] = np.inf
+    h = _handle(P, lat, w["chi"], 64, prec=prec)
+    h.set_params(_dev(th))
+    S = _dev(I.configs_neel(lat, 64))
+    res = h.evaluate(I.heisenberg(lat), S)
+    torch.cuda.synchronize()
+    st = res["status"].cpu().numpy()
+    assert np.all(st & P.ST_NONFINITE)
+    S0 = S.clone()
+    acc = torch.zeros(64, dtype=torch.int64, device="cuda")
+    S1, _, st2 = h.sample(S, move=P.MOVE_EXCHANGE, nsweeps=1, seed=5, accepted=acc)
+    torch.cuda.synchronize()
+    assert torch.equal(S1, S0) and int(acc.sum()) == 0
+
+
 def test_minsr_step_vs_oracle(P):
     from oracle import minsr
     w = I.WORKLOADS["heis4x4_D2_chi4"]
@@ -222,7 +246,7 @@ def test_minsr_step_ragged_blocks_vs_oracle(P, ns, npar, rc, lam):
     assert int(info[0]) == inf_ref["rank"]
 
 
-def _minsr_raw(P, O, e, lam, rc, tau, gram=0):
+def _minsr_raw(P, O, e, lam, rc, tau, gram=0, solve=0, handle_out=None):
     """minsr_step on a handle whose N_p covers O's column count (zero-padded columns)."""
     ns, npar = O.shape
     # choose a lattice with exactly npar parameters is not always possible; use a handle on a
@@ -234,11 +258,13 @@ def _minsr_raw(P, O, e, lam, rc, tau, gram=0):
                 break
         if I.num_params(lat) >= npar:
             break
-    h = P.PEPS(lat.Lx, lat.Ly, 2, lat.D, lat.D, max_samples=2, gram=gram)
+    h = P.PEPS(lat.Lx, lat.Ly, 2, lat.D, lat.D, max_samples=2, gram=gram, solve=solve)
     Op = np.zeros((ns, h.Np))
     Op[:, :npar] = O
     dth, info = h.minsr_step(_dev(Op), _dev(np.stack([e, np.zeros(ns)], 1)), lam=lam, rcond=rc, tau=tau)
     torch.cuda.synchronize()
+    if handle_out is not None:
+        handle_out.append(h)
     return dth.cpu().numpy()[:npar], info.cpu().numpy()
 
 
@@ -257,6 +283,66 @@ def test_minsr_tensor_core_gram_vs_oracle(P, ns, npar, rc, lam):
     assert rel <= 1e-2
     if rc > 0:
         assert abs(info[2] - inf_ref["lmax"]) <= 1e-4 * inf_ref["lmax"]
+
+
+@pytest.mark.parametrize("ns,npar,lam", [(700, 300, 1e-3), (1030, 1200, 1e-4), (333, 2000, 1e-4)])
+def test_minsr_mixed_solve_vs_oracle(P, ns, npar, lam):
+    # FP32 Cholesky of T + lambda refined with FP64 residuals: after the refinement steps the
+    # solve is as accurate as the FP64 one whenever cond(T + lambda) * 6e-8 << 1, which holds
+    # here (lambda >= 1e-4 against |T| of order N_p / N_s)
+    from oracle import minsr
+    rng = np.random.default_rng(ns + 2)
+    O = rng.standard_normal((ns, npar)) + 0.1 * rng.standard_normal(npar)
+    e = rng.standard_normal(ns) - 3.0
+    d_ref, inf_ref = minsr.minsr(O, e, lam=lam, rcond=0.0, tau=0.1)
+    dth, info = _minsr_raw(P, O, e, lam, 0.0, 0.1, solve=1)
+    rel = np.linalg.norm(dth - d_ref) / np.linalg.norm(d_ref)
+    print(f"mixed solve: relative dtheta error {rel:.2e}, final residual {info[1]:.2e}")
+    assert int(info[0]) == inf_ref["rank"]
+    assert info[2] == 4 and info[1] <= 1e-10
+    assert rel <= 1e-9
+    # with the tensor-core Gram as well (the mixed-precision MinSR path)
+    dth2, info2 = _minsr_raw(P, O, e, lam, 0.0, 0.1, gram=1, solve=1)
+    rel2 = np.linalg.norm(dth2 - d_ref) / np.linalg.norm(d_ref)
+    print(f"tensor-core Gram + mixed solve: relative dtheta error {rel2:.2e}")
+    assert rel2 <= 1e-2
+
+
+def _badly_scaled(seed):
+    # a few large columns: |T| ~ 1e6 against lambda = 1e-4, T of rank ~60 out of 512
+    rng = np.random.default_rng(seed)
+    O = 3e3 * rng.standard_normal((512, 1200)) * (rng.random(1200) < 0.05)
+    return O, rng.standard_normal(512)
+
+
+def test_minsr_mixed_solve_falls_back_to_fp64(P):
+    # cond(T + lambda) ~ 1e10: the FP32 factor breaks down, the FP64 factorisation takes over
+    # (info[2] = 0) and dtheta is the FP64 one
+    from oracle import minsr
+    O, e = _badly_scaled(11)
+    d_ref, inf_ref = minsr.minsr(O, e, lam=1e-4, rcond=0.0, tau=0.1)
+    dth, info = _minsr_raw(P, O, e, 1e-4, 0.0, 0.1, solve=1)
+    rel = np.linalg.norm(dth - d_ref) / np.linalg.norm(d_ref)
+    print(f"mixed solve fallback: relative dtheta error {rel:.2e}")
+    assert info[0] == inf_ref["rank"] and info[2] == 0
+    # FP64 Cholesky against the oracle's FP64 eigendecomposition at cond(T + lambda) ~ 1.5e11:
+    # the two FP64 routes differ by about cond * eps ~ 1e-4 here (the CPU's Cholesky and eigh
+    # disagree by 1.1e-4 on this input), hence the gate
+    assert rel <= 1e-3
+
+
+def test_minsr_breakdown_warns_and_zeroes_dtheta(P):
+    # the split-BF16 Gram's rounding (~1e-5 |T|) is far above lambda here, so T + lambda is not
+    # positive definite in floating point: the call warns and returns dtheta = 0 instead of a
+    # meaningless step; the FP64 Gram solves the same problem
+    O, e = _badly_scaled(12)
+    hs = []
+    dth, info = _minsr_raw(P, O, e, 1e-4, 0.0, 0.1, gram=1, handle_out=hs)
+    assert info[0] == -1 and hs[0].last_warning is not None
+    assert np.all(dth == 0.0)
+    hs = []
+    dth, info = _minsr_raw(P, O, e, 1e-4, 0.0, 0.1, gram=0, handle_out=hs)
+    assert info[0] == 512 and hs[0].last_warning is None and np.all(np.isfinite(dth))
 
 
 @pytest.mark.parametrize("move,lat,chi,H", [
