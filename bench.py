@@ -239,8 +239,10 @@ def run_gpu(a):
     # ---- roofline of the dominant kernel class
     peaks = _peaks()
     sm_max = peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12   # TFLOP/s, FP32 FMA pipes at the max SM clock
-    fp64_peak = 1.25                                     # TFLOP/s, nominal GB300 FP64
+    fp32_derived = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 FMA pipes at the max SM clock
+    # measured CUDA-core FMA peaks of this GPU (project probe, run after the timed region)
+    fp32_peak = P.probe_fma(False)
+    fp64_peak = P.probe_fma(True)
     alu_peak = fp32_peak if prec == P.PREC_FP32 else fp64_peak
     hwin, vwin = costmodel.heisenberg_windows(lat.Lx, lat.Ly, ns)
     # the Jacobi counters mix the sampler's and the environment kernel's SVDs; split them by SVD count
@@ -264,8 +266,9 @@ def run_gpu(a):
                        "minsr_gram": "k_gram"}[dom],
             "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": None,
-            "peak_source": ("FP32 FMA pipes: 152 SMs x 128 lanes x 2 flop x max SM clock (derived)" if peak == fp32_peak
-                            else "GB300 nominal FP64 1.25 TFLOP/s"),
+            "peak_source": ("measured: peps_probe_fma FP32 (derived 152 SMs x 128 lanes x 2 x max clock = %.1f)"
+                            % fp32_derived if peak == fp32_peak else
+                            "measured: peps_probe_fma FP64" if peak == fp64_peak else "MEASURED_PEAKS bf16_tflops"),
             "algorithmic_tflop_per_launch": flops[dom] / max(1, launches[dom]) / 1e12,
             "launch_ms": dom_launch_ms}
     gpu_launches = int(sum(launches.values())) + 3 * a.steps  # + memsets inside evaluate / minsr
@@ -280,7 +283,8 @@ def run_gpu(a):
                                       max(1e-9, ms_cls["minsr_gram"] / a.steps / 1e3) / 1e12),
                       "last_info": [float(x) for x in info_hist[-1].cpu()]},
             "kernel_ms_per_step": {k: v / a.steps for k, v in ms_cls.items()},
-            "roofline": roof, "gpu_launches": gpu_launches, "clocks": clk.summary(),
+            "roofline": roof, "alu_peaks_measured_tflops": {"fp32": fp32_peak, "fp64": fp64_peak},
+            "gpu_launches": gpu_launches, "clocks": clk.summary(),
             "acceptance": float(acc.sum().item()) / max(1.0, ns * (sweep_ctr[0]) * (2 * lat.Lx * lat.Ly - lat.Lx - lat.Ly) * 0.5),
             "eloc_mean_per_site": [float(x) / lat.nsites for x in eloc_means]}
     # ---- end to end through the public API with host buffers
@@ -396,15 +400,16 @@ def run_gram(a):
         e = torch.zeros(ns, 2, dtype=torch.float64, device="cuda")
         e[:, 0] = torch.randn(ns, dtype=torch.float64, device="cuda", generator=g) - 3.0
         reps = 1 if gram == 0 else 3
-        h.minsr_step(O, e, lam=1e-2, tau=0.1)  # warm-up (allocations)
+        h.minsr_step(O, e, lam=1.0, tau=0.1)  # warm-up (allocations)
         h.timing(True)
         for _ in range(reps):
-            dth, info = h.minsr_step(O, e, lam=1e-2, tau=0.1)
+            dth, info = h.minsr_step(O, e, lam=1.0, tau=0.1)
         ms, la, _ = h.timing_read()
         h.timing(False)
         gram_ms = ms["minsr_gram"] / reps
         mac = ns * (ns + 1) / 2 * h.Np  # algorithmic multiply-adds of one triangle
-        r = {"gram_ms": gram_ms, "solve_ms": ms["minsr_eig"] / reps, "step_s": sum(ms.values()) / reps / 1e3}
+        r = {"gram_ms": gram_ms, "solve_ms": ms["minsr_eig"] / reps, "step_s": sum(ms.values()) / reps / 1e3,
+             "lambda": 1.0, "warning": h.last_warning}
         if gram == 1:
             tflops = 3 * 2 * mac / (gram_ms / 1e3) / 1e12
             r["tensor_tflops_bf16"] = tflops

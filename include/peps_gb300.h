@@ -249,8 +249,51 @@ peps_status peps_sample_learned(peps_handle* h, int C, int wprec, const void* w_
 peps_status peps_amplitudes_noalloc(const peps_config* cfg, const double* theta_dev, const uint8_t* S_dev, int Ns,
                                     double* logabs_dev, double* phase_dev, int32_t* status_dev, void* stream);
 
+/* Autotuner (no counterpart in the paper).  For each kernel class (environments, one-row
+ * sandwiches, two-row sandwiches, sampler) the shared-memory budget per CTA decides which work
+ * buffers stay on chip and how many CTAs share an SM.  The call plans every candidate budget
+ * (FP32: 72, 110, 220 KB; FP64: 100, 210 KB), runs peps_evaluate (with H when non-NULL) and
+ * one sampler sweep of kind `move` on a copy of S_dev, times each class with CUDA events and
+ * keeps the fastest budget per class for all later calls.  Results do not depend on the budget
+ * (same arithmetic in the same order).  budget_kb_host: 4 ints written (may be NULL).  Allocates
+ * temporary device memory (Ns x N_p outputs); synchronises the stream. */
+peps_status peps_autotune(peps_handle* h, const peps_hamiltonian* H, const uint8_t* S_dev, int Ns, int move,
+                          int* budget_kb_host, void* stream);
+
+/* Multi-instance batch (no counterpart in the paper): independent handles (different lattices,
+ * D, chi) evaluated by one CUDA graph.  Each item is one peps_evaluate call; its pointers are
+ * recorded and read again at every launch (update the contents, not the pointers). */
+typedef struct {
+    peps_handle* h;              /* each handle at most once per batch; timing disabled      */
+    const peps_hamiltonian* H;   /* NULL when eloc_dev is NULL                               */
+    const uint8_t* S_dev;
+    int Ns;                      /* 1 .. h's max_samples                                     */
+    double* logabs_dev;
+    double* phase_dev;
+    double* eloc_dev;            /* may be NULL                                              */
+    void* O_dev;                 /* may be NULL                                              */
+    int32_t* status_dev;         /* may be NULL                                              */
+} peps_batch_item;
+
+typedef struct peps_batch peps_batch;
+
+/* Runs every item once eagerly on `stream` (one-time uploads), then records all items into one
+ * graph: `nbranch` concurrent branches forked from `stream`, items placed largest first
+ * (Ns x sites x chi^3 D^3) on the least-loaded branch.  `stream` must not be the legacy default
+ * stream (it cannot be captured).  PEPS_E_ARG for a repeated handle or a handle with timing on. */
+peps_status peps_batch_create(peps_batch** out, const peps_batch_item* items, int n, int nbranch, void* stream);
+/* Launch the recorded graph on `stream` (asynchronous). */
+peps_status peps_batch_launch(peps_batch* b, void* stream);
+peps_status peps_batch_destroy(peps_batch* b);
+
 /* Text of the last error seen by this handle (never NULL). */
 const char* peps_last_error(const peps_handle* h);
+
+/* Measured CUDA-core FMA throughput of the current device in TFLOP/s (2 flops per FMA), FP32
+ * (fp64 == 0) or FP64 (fp64 != 0): 8 independent FMA chains per thread, every SM filled, timed
+ * with CUDA events on `stream` (the call synchronises it).  It is the peak against which the
+ * contraction kernels' ALU roofline is quoted.  No counterpart in the paper. */
+peps_status peps_probe_fma(int fp64, double* tflops_host, void* stream);
 
 #ifdef __cplusplus
 }

@@ -9,6 +9,8 @@
 
 #include "peps_kernels.cuh"
 #include "peps_gb300.h"
+#include <map>
+#include <mutex>
 
 using namespace peps;
 
@@ -20,6 +22,7 @@ struct KPlan {
 
 struct peps_handle {
   peps_config cfg{};
+  size_t budget[4] = {0, 0, 0, 0};  // shared-memory budget per kernel class (env, row, pair, sample)
   Geo g{};
   long long Np = 0;
   int nsm = 0;
@@ -162,21 +165,26 @@ static void place_overlay(Plan& p, size_t& smem, size_t budget, const std::vecto
   p.gstride = gl;
 }
 
+// Default shared-memory budget per CTA: FP64 one CTA per SM (the FP64 pipe is the limit), FP32
+// two CTAs per SM.
+static size_t default_budget(const peps_handle* h) { return (h->esz == 8) ? 210 * 1024 : 110 * 1024; }
+
 static void plan_all(peps_handle* h) {
   const Geo& g = h->g;
   const size_t E = h->esz;
   const int n = g.n, chi = g.chi, D = g.D, Ly = g.Ly;
   const int mX = n + (n & 1);
   const int Lr = D * chi;
-  // FP64: one CTA per SM (the FP64 pipe is the limit); FP32: two CTAs per SM
-  const size_t budget = (E == 8) ? 210 * 1024 : 110 * 1024;
+  for (int i = 0; i < 4; ++i)
+    if (h->budget[i] == 0) h->budget[i] = default_budget(h);
+  size_t budget = h->budget[0];
   int ci = std::min(n, 8);
   const size_t zsz = env_z_elems(chi, D);
   // one-row / two-row temporaries
-  const size_t t1row = (size_t)chi * chi * D * D;
+  const size_t t1row = sandwich1_t_elems(chi, D);
   int cx = chi;
   while (cx > 1 && (size_t)D * D * D * chi * cx > 8192) cx = (cx + 1) / 2;
-  const size_t t2row = (size_t)D * D * D * chi * cx;
+  const size_t t2row = (size_t)D * D * D * chi * cx + chi;  // absorb2_right's first temporary: + chi
   // env plan
   {
     KPlan& k = h->kp[0];
@@ -189,6 +197,7 @@ static void plan_all(peps_handle* h) {
     place(k.p, k.smem, budget, b);
   }
   // row plan
+  budget = h->budget[1];
   {
     KPlan& k = h->kp[1];
     k.p.ci = ci;
@@ -200,6 +209,7 @@ static void plan_all(peps_handle* h) {
     place(k.p, k.smem, budget, b);
   }
   // pair plan
+  budget = h->budget[2];
   {
     KPlan& k = h->kp[2];
     k.p.ci = ci;
@@ -211,6 +221,7 @@ static void plan_all(peps_handle* h) {
     place(k.p, k.smem, budget, b);
   }
   // sampler plan: union of the above
+  budget = h->budget[3];
   {
     KPlan& k = h->kp[3];
     k.p.ci = ci;
@@ -218,7 +229,7 @@ static void plan_all(peps_handle* h) {
     int cxs = cx;
     while (cxs > 1 && (size_t)D * D * D * chi * cxs > 4096) cxs = (cxs + 1) / 2;
     k.p.cx = cxs;
-    const size_t tt = std::max(t1row, (size_t)D * D * D * chi * cxs);
+    const size_t tt = std::max(t1row, (size_t)D * D * D * chi * cxs + chi);
     const size_t lw = std::max((size_t)g.s2, (size_t)g.se);
     // the row step (E^u / E^l updates) and the move sandwiches never overlap in time
     std::vector<std::pair<int, size_t>> common = {
@@ -233,10 +244,27 @@ static void plan_all(peps_handle* h) {
   }
 }
 
+// The dynamic shared-memory limit is a property of a kernel instantiation, shared by every handle
+// that launches it: only ever raise it (per precision and compiled shape), so that handles with
+// different budgets can coexist.
+static std::mutex g_attr_mu;
+static std::map<std::pair<int, int>, size_t> g_attr_max;
+
 static peps_status finish_plans(peps_handle* h) {
   size_t maxsmem = 0;
   for (auto& k : h->kp) maxsmem = std::max(maxsmem, k.smem);
-  cudaError_t e = (h->esz == 8) ? set_kernel_smem<double>(h->g, maxsmem) : set_kernel_smem<float>(h->g, maxsmem);
+  cudaError_t e = cudaSuccess;
+  {
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    const int variant = (h->g.chi == 16 && h->g.D == 4) ? 1 : (h->g.chi == 24 && h->g.D == 4) ? 2 : 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    size_t& cur = g_attr_max[{(int)h->esz * 64 + dev, variant}];
+    if (maxsmem > cur) {
+      e = (h->esz == 8) ? set_kernel_smem<double>(h->g, maxsmem) : set_kernel_smem<float>(h->g, maxsmem);
+      if (e == cudaSuccess) cur = maxsmem;
+    }
+  }
   if (e != cudaSuccess) return cuda_fail(h, e, "cudaFuncSetAttribute");
   size_t gmax = 0;
   for (int i = 0; i < 4; ++i) {
@@ -246,14 +274,19 @@ static peps_status finish_plans(peps_handle* h) {
     k.grid = h->nsm * occ;
     gmax = std::max(gmax, (size_t)k.grid * (size_t)k.p.gstride);
   }
-  if (gmax > 0) {
+  if (gmax > h->gscratch_bytes) {
+    if (h->gscratch) cudaFree(h->gscratch);
+    h->gscratch = nullptr;
+    h->gscratch_bytes = 0;
     e = cudaMalloc(&h->gscratch, gmax);
     if (e != cudaSuccess) return fail(h, PEPS_E_WORKSPACE, "scratch allocation failed");
     h->gscratch_bytes = gmax;
   }
-  if (cudaMalloc(&h->ctr, 8 * sizeof(unsigned long long)) != cudaSuccess)
-    return fail(h, PEPS_E_WORKSPACE, "counter allocation failed");
-  cudaMemset(h->ctr, 0, 8 * sizeof(unsigned long long));
+  if (!h->ctr) {
+    if (cudaMalloc(&h->ctr, 8 * sizeof(unsigned long long)) != cudaSuccess)
+      return fail(h, PEPS_E_WORKSPACE, "counter allocation failed");
+    cudaMemset(h->ctr, 0, 8 * sizeof(unsigned long long));
+  }
   for (auto& k : h->kp) {
     k.p.gbase = h->gscratch;
     k.p.ctr = h->ctr;
@@ -704,6 +737,196 @@ extern "C" peps_status minsr_step(peps_handle* h, const void* O_dev, const doubl
       return PEPS_W_NUMERIC;
     }
   }
+  return PEPS_OK;
+}
+
+// ---- autotuner ---------------------------------------------------------------------------
+// Per kernel class, the shared-memory budget decides which work buffers stay on chip and how many
+// CTAs share an SM; the best choice depends on (chi, D), the lattice and the precision.  Every
+// candidate is planned, run once on the caller's configurations and timed with the handle's
+// events; each class keeps its fastest budget.
+static float class_ms(peps_handle* h, int cls) {
+  float tot = 0.f;
+  for (size_t k = 0; k < h->evn / 2; ++k) {
+    if (h->evclass[k] != cls) continue;
+    float ms = 0.f;
+    if (cudaEventSynchronize(h->evpool[2 * k + 1]) == cudaSuccess &&
+        cudaEventElapsedTime(&ms, h->evpool[2 * k], h->evpool[2 * k + 1]) == cudaSuccess)
+      tot += ms;
+  }
+  return tot;
+}
+
+extern "C" peps_status peps_autotune(peps_handle* h, const peps_hamiltonian* H, const uint8_t* S_dev, int Ns,
+                                     int move, int* budget_kb_host, void* stream) {
+  peps_status c = check_eval(h, S_dev, Ns);
+  if (c != PEPS_OK) return c;
+  if (Ns < 1) return fail(h, PEPS_E_ARG, "autotune needs at least one configuration");
+  if (move != PEPS_MOVE_EXCHANGE && move != PEPS_MOVE_FLIP) return fail(h, PEPS_E_ARG, "bad move kind");
+  cudaStream_t s = (cudaStream_t)stream;
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  std::vector<size_t> cand = (h->esz == 8) ? std::vector<size_t>{100 * 1024, 210 * 1024}
+                                           : std::vector<size_t>{72 * 1024, 110 * 1024, 220 * 1024};
+  for (auto& b : cand) b = std::min(b, (size_t)optin - 2048);
+  // scratch outputs and a copy of the configurations for the sampler trial
+  const size_t N = (size_t)h->g.Lx * h->g.Ly;
+  double *la = nullptr, *ph = nullptr, *el = nullptr;
+  void* O = nullptr;
+  uint8_t* S2 = nullptr;
+  long long* acc = nullptr;
+  auto cleanup = [&]() {
+    void* ps[] = {la, ph, el, O, S2, acc};
+    for (void* q : ps)
+      if (q) cudaFree(q);
+  };
+  if (cudaMalloc(&la, sizeof(double) * Ns) != cudaSuccess || cudaMalloc(&ph, sizeof(double) * Ns) != cudaSuccess ||
+      cudaMalloc(&el, sizeof(double) * 2 * Ns) != cudaSuccess ||
+      cudaMalloc(&O, (size_t)Ns * h->Np * h->esz) != cudaSuccess || cudaMalloc(&S2, (size_t)Ns * N) != cudaSuccess ||
+      cudaMalloc(&acc, sizeof(long long) * Ns) != cudaSuccess) {
+    cleanup();
+    return fail(h, PEPS_E_WORKSPACE, "autotune scratch allocation failed");
+  }
+  const bool was_timing = h->timing;
+  const int cls[4] = {TC_ENV, TC_ROW, TC_PAIR, TC_SAMPLE};
+  std::vector<std::vector<float>> ms(4, std::vector<float>(cand.size(), 1e30f));
+  peps_status st = PEPS_OK;
+  for (size_t ci = 0; ci < cand.size() && st == PEPS_OK; ++ci) {
+    for (int i = 0; i < 4; ++i) h->budget[i] = cand[ci];
+    plan_all(h);
+    st = finish_plans(h);
+    if (st != PEPS_OK) break;
+    for (int rep = 0; rep < 2 && st == PEPS_OK; ++rep) {  // the first repetition warms up
+      h->timing = true;
+      h->evn = 0;
+      st = peps_evaluate(h, H, S_dev, Ns, la, ph, H ? el : nullptr, O, nullptr, stream);
+      if (st == PEPS_OK) {
+        CK(cudaMemcpyAsync(S2, S_dev, (size_t)Ns * N, cudaMemcpyDeviceToDevice, s), "copy configurations");
+        st = peps_sample(h, move, S2, Ns, 1, 0x5eedull, 0, acc, nullptr, stream);
+      }
+      if (st == PEPS_OK && rep == 1)
+        for (int i = 0; i < 4; ++i) ms[i][ci] = class_ms(h, cls[i]);
+      h->timing = false;
+    }
+  }
+  h->timing = was_timing;
+  h->evn = 0;
+  cleanup();
+  if (st != PEPS_OK) {
+    for (int i = 0; i < 4; ++i) h->budget[i] = default_budget(h);
+    plan_all(h);
+    finish_plans(h);
+    return st;
+  }
+  for (int i = 0; i < 4; ++i) {
+    size_t best = 0;
+    for (size_t ci = 1; ci < cand.size(); ++ci)
+      if (ms[i][ci] < ms[i][best]) best = ci;
+    if (i == 2 && !(H && h->n_pair_terms > 0)) best = 0;  // the pair kernel did not run: keep the smallest
+    h->budget[i] = cand[best];
+    if (budget_kb_host) budget_kb_host[i] = (int)(cand[best] / 1024);
+  }
+  plan_all(h);
+  return finish_plans(h);
+}
+
+// ---- multi-instance batch in one CUDA graph ------------------------------------------------
+struct peps_batch {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<cudaStream_t> branches;
+  std::vector<cudaEvent_t> events;
+  std::string err;
+};
+
+static void batch_free(peps_batch* b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (cudaEvent_t e : b->events) cudaEventDestroy(e);
+  for (cudaStream_t st : b->branches) cudaStreamDestroy(st);
+  delete b;
+}
+
+extern "C" peps_status peps_batch_create(peps_batch** out, const peps_batch_item* items, int n, int nbranch,
+                                         void* stream) {
+  if (!out || !items || n < 1 || nbranch < 1) return PEPS_E_ARG;
+  *out = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!s) return PEPS_E_ARG;  // the legacy default stream cannot be captured
+  for (int i = 0; i < n; ++i) {
+    const peps_batch_item& it = items[i];
+    if (!it.h || it.Ns < 1 || !it.S_dev || !it.logabs_dev || !it.phase_dev) return PEPS_E_ARG;
+    if (it.eloc_dev && !it.H) return PEPS_E_ARG;
+    if (it.Ns > it.h->cfg.max_samples) return PEPS_E_SHAPE;
+    if (it.h->timing) return fail(it.h, PEPS_E_ARG, "disable timing before recording a batch");
+    for (int j = 0; j < i; ++j)
+      if (items[j].h == it.h) return fail(it.h, PEPS_E_ARG, "a handle appears twice in one batch");
+  }
+  // one eager pass: uploads the Hamiltonians and every other one-time state
+  for (int i = 0; i < n; ++i) {
+    const peps_batch_item& it = items[i];
+    peps_status st = peps_evaluate(it.h, it.H, it.S_dev, it.Ns, it.logabs_dev, it.phase_dev, it.eloc_dev, it.O_dev,
+                                   it.status_dev, stream);
+    if (st != PEPS_OK) return st;
+  }
+  if (cudaStreamSynchronize(s) != cudaSuccess) return PEPS_E_CUDA;
+  // largest work first, each item to the branch with the least work so far
+  std::vector<int> order(n);
+  std::vector<double> cost(n);
+  for (int i = 0; i < n; ++i) {
+    const Geo& g = items[i].h->g;
+    order[i] = i;
+    cost[i] = (double)items[i].Ns * g.Lx * g.Ly * (double)g.chi * g.chi * g.chi * g.D * g.D * g.D;
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  peps_batch* b = new peps_batch();
+  const int nb = std::min(nbranch, n);
+  b->branches.resize(nb);
+  b->events.resize(nb + 1);
+  for (int k = 0; k < nb; ++k) cudaStreamCreateWithFlags(&b->branches[k], cudaStreamNonBlocking);
+  for (auto& e : b->events) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+  if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    batch_free(b);
+    return PEPS_E_CUDA;
+  }
+  peps_status st = PEPS_OK;
+  cudaEventRecord(b->events[nb], s);
+  for (int k = 0; k < nb; ++k) cudaStreamWaitEvent(b->branches[k], b->events[nb], 0);
+  std::vector<double> load(nb, 0.0);
+  for (int idx : order) {
+    const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    load[k] += cost[idx];
+    const peps_batch_item& it = items[idx];
+    st = peps_evaluate(it.h, it.H, it.S_dev, it.Ns, it.logabs_dev, it.phase_dev, it.eloc_dev, it.O_dev,
+                       it.status_dev, b->branches[k]);
+    if (st != PEPS_OK) break;
+  }
+  for (int k = 0; k < nb; ++k) {
+    cudaEventRecord(b->events[k], b->branches[k]);
+    cudaStreamWaitEvent(s, b->events[k], 0);
+  }
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(s, &graph);
+  b->graph = graph;
+  if (st != PEPS_OK || ec != cudaSuccess || !graph ||
+      cudaGraphInstantiate(&b->exec, graph, 0) != cudaSuccess) {
+    batch_free(b);
+    return st != PEPS_OK ? st : PEPS_E_CUDA;
+  }
+  *out = b;
+  return PEPS_OK;
+}
+
+extern "C" peps_status peps_batch_launch(peps_batch* b, void* stream) {
+  if (!b || !b->exec) return PEPS_E_ARG;
+  return cudaGraphLaunch(b->exec, (cudaStream_t)stream) == cudaSuccess ? PEPS_OK : PEPS_E_CUDA;
+}
+
+extern "C" peps_status peps_batch_destroy(peps_batch* b) {
+  if (!b) return PEPS_E_ARG;
+  batch_free(b);
   return PEPS_OK;
 }
 

@@ -204,9 +204,14 @@ __global__ void __launch_bounds__(NTHREADS) k_row(G g, Plan plan, const T* __res
       for (int y = 0; y < Ly; ++y) {
         const int site = x * Ly + y;
         blk_copy(eu, EU + (size_t)y * se, se);
-        blk_copy(el, EL + (size_t)y * se, se);
+        {
+          // the lower environment site transposed, elT[z][b][d] = el[b][d][z] (into LW2)
+          const T* ely = EL + (size_t)y * se;
+          const int cd = g.chi * g.D;
+          for (int o = threadIdx.x; o < se; o += blockDim.x) LW2[o] = ely[(size_t)(o % cd) * g.chi + o / cd];
+        }
         __syncthreads();
-        site_env1(g, LP + (size_t)y * se, eu, el, RP + (size_t)(y + 1) * se, t1, t2, A);
+        site_env1(g, LP + (size_t)y * se, eu, LW2, RP + (size_t)(y + 1) * se, t1, t2, A);
         const double sc = exp(logL[y] + logR[y + 1] - lpsi_norm);
         int Dl, Du, Dr, Dd;
         site_dims(g, x, y, &Dl, &Du, &Dr, &Dd);

@@ -72,7 +72,7 @@ peps_status run(const peps_config& c, const double* theta, const uint8_t* S, int
   const int mX = n + (n & 1), Lr = D * chi, ci = n < 8 ? n : 8;
   const size_t E = sizeof(T);
   const size_t zsz = env_z_elems(chi, D);
-  const size_t t1 = (size_t)chi * chi * D * D;
+  const size_t t1 = sandwich1_t_elems(chi, D);
   const std::pair<int, size_t> benv[] = {
       {B_RED, 40 * 8}, {B_SIG, (mX + 4) * E}, {B_SEL, 2 * (size_t)mX * 4}, {B_A, (size_t)g.sT * E},
       {B_E, (size_t)g.se * E}, {B_C, (size_t)n * chi * E}, {B_W, env_w_elems(chi, D, ci) * E},

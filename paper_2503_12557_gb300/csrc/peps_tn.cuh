@@ -782,6 +782,8 @@ __host__ __device__ inline size_t env_z_elems(int chi, int D) {
   return zleft > zright ? zleft : zright;
 }
 __host__ __device__ inline size_t env_w_elems(int chi, int D, int ci) { return (size_t)ci * ((size_t)D * D * chi + 1); }
+// Size of the one-row sandwich temporaries (the first holds rows padded to chi + 1).
+__host__ __device__ inline size_t sandwich1_t_elems(int chi, int D) { return (size_t)D * D * chi * (chi + 1); }
 
 // ------------------------------------------------------------------------------------------
 // Per-CTA working set of one boundary-MPS row step.
@@ -1024,103 +1026,126 @@ __device__ double env_first_row(const G& g, T* Eout, const T* Tpad, int row, con
 }
 
 // ------------------------------------------------------------------------------------------
-// One-row sandwich partials.  L[a][l][b] -> L'[x][r][z] over one column with eu[a][u][x],
-// A[l][u][r][d], el[b][d][z].  t1, t2: chi*chi*D*D each.
-template <typename T, typename G>
-__device__ void absorb1(const G& g, const T* L, const T* eu, const T* A, const T* el, T* t1, T* t2, T* out) {
-  const int chi = g.chi, D = g.D, NT = blockDim.x, tid = threadIdx.x;
-  const int n1 = D * chi * D * chi;
-  // t1[l][b][u][x] = sum_a L[a][l][b] eu[a][u][x]
-  for (int o = tid; o < n1; o += NT) {
-    const int x = o % chi, u = (o / chi) % D, b = (o / (chi * D)) % chi, l = o / (chi * D * chi);
-    T s = 0;
-    for (int a = 0; a < chi; ++a) s += L[(a * D + l) * chi + b] * eu[(a * D + u) * chi + x];
-    t1[o] = s;
-  }
-  __syncthreads();
-  // t2[b][x][r][d] = sum_{l,u} t1[l][b][u][x] A[l][u][r][d]
-  for (int o = tid; o < n1; o += NT) {
-    const int dd = o % D, r = (o / D) % D, x = (o / (D * D)) % chi, b = o / (D * D * chi);
-    T s = 0;
-    for (int l = 0; l < D; ++l)
-      for (int u = 0; u < D; ++u) s += t1[((l * chi + b) * D + u) * chi + x] * A[((l * D + u) * D + r) * D + dd];
-    t2[o] = s;
-  }
-  __syncthreads();
-  // out[x][r][z] = sum_{b,d} t2[b][x][r][d] el[b][d][z]
-  for (int o = tid; o < g.se; o += NT) {
-    const int z = o % chi, r = (o / chi) % D, x = o / (chi * D);
-    T s = 0;
-    for (int b = 0; b < chi; ++b)
-      for (int dd = 0; dd < D; ++dd) s += t2[((b * chi + x) * D + r) * D + dd] * el[(b * D + dd) * chi + z];
-    out[o] = s;
+// Strided contraction over the whole CTA, the form every sandwich step takes:
+//   C[cm(m) + cn(n)] = sum_{k1 < K1, k2 < K2} A[am(m) + k1 sa1 + k2 sa2] B[k1 sb1 + k2 sb2 + bn(n)]
+// for m < M, n < N, where fm(m) returns (am, cm) and fn(n) returns (bn, cn).  Each thread
+// accumulates an RM x RN register tile whose rows m = ti + i tm are interleaved across threads
+// (consecutive threads read consecutive rows of A) and whose columns n = tj + j tn are shared by
+// the threads of a warp when tm >= 32 (B is read as a broadcast).  Ends with a barrier.
+struct Off2 {
+  int a, c;
+};
+template <int RM, int RN, typename T, class FM, class FN>
+__device__ __forceinline__ void blk_gemm(const T* __restrict__ A, const T* __restrict__ B, T* __restrict__ C, int M,
+                                         int N, int K1, int K2, int sa1, int sa2, int sb1, int sb2, FM fm, FN fn) {
+  const int tm = (M + RM - 1) / RM, tn = (N + RN - 1) / RN;
+  for (int t = threadIdx.x; t < tm * tn; t += blockDim.x) {
+    const int ti = t % tm, tj = t / tm;
+    int ao[RM], co[RM], bo[RN], cn[RN];
+    bool mv[RM], nv[RN];
+#pragma unroll
+    for (int i = 0; i < RM; ++i) {
+      const int m = ti + i * tm;
+      mv[i] = m < M;
+      const Off2 o = fm(mv[i] ? m : 0);
+      ao[i] = o.a;
+      co[i] = o.c;
+    }
+#pragma unroll
+    for (int j = 0; j < RN; ++j) {
+      const int n = tj + j * tn;
+      nv[j] = n < N;
+      const Off2 o = fn(nv[j] ? n : 0);
+      bo[j] = o.a;
+      cn[j] = o.c;
+    }
+    T acc[RM][RN];
+#pragma unroll
+    for (int i = 0; i < RM; ++i)
+#pragma unroll
+      for (int j = 0; j < RN; ++j) acc[i][j] = T(0);
+    for (int k1 = 0; k1 < K1; ++k1) {
+      for (int k2 = 0; k2 < K2; ++k2) {
+        const int ka = k1 * sa1 + k2 * sa2, kb = k1 * sb1 + k2 * sb2;
+        T a[RM], b[RN];
+#pragma unroll
+        for (int i = 0; i < RM; ++i) a[i] = A[ao[i] + ka];
+#pragma unroll
+        for (int j = 0; j < RN; ++j) b[j] = B[kb + bo[j]];
+#pragma unroll
+        for (int i = 0; i < RM; ++i)
+#pragma unroll
+          for (int j = 0; j < RN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < RM; ++i)
+#pragma unroll
+      for (int j = 0; j < RN; ++j)
+        if (mv[i] && nv[j]) C[co[i] + cn[j]] = acc[i][j];
   }
   __syncthreads();
 }
 
-// R[x][r][z] -> R'[a][l][b] = sum eu[a][u][x] A[l][u][r][d] el[b][d][z] R[x][r][z]
+// ------------------------------------------------------------------------------------------
+// One-row sandwich partials.  L[a][l][b] -> L'[x][r][z] over one column with eu[a][u][x],
+// A[l][u][r][d], el[b][d][z].  t1, t2: chi*chi*D*D each.  The intermediates are laid out so that
+// the index that varies across threads is contiguous in the operand it is read from.
+template <typename T, typename G>
+__device__ void absorb1(const G& g, const T* L, const T* eu, const T* A, const T* el, T* t1, T* t2, T* out) {
+  const int chi = g.chi, D = g.D;
+  // t1[u][l][x][b] = sum_a L[a][l][b] eu[a][u][x]        (m = (l, b), n = (u, x), k = a)
+  blk_gemm<2, 8>(L, eu, t1, D * chi, D * chi, chi, 1, D * chi, 0, D * chi, 0,
+                 [=](int m) { return Off2{m, (m / chi) * chi * chi + m % chi}; },
+                 [=](int n) { return Off2{n, (n / chi) * D * chi * chi + (n % chi) * chi}; });
+  // t2[x][r][d][b] = sum_{l,u} t1[u][l][x][b] A[l][u][r][d]   (m = (x, b), n = (r, d), k = (l, u))
+  blk_gemm<4, 4>(t1, A, t2, chi * chi, D * D, D, D, chi * chi, D * chi * chi, D * D * D, D * D,
+                 [=](int m) { return Off2{m, (m / chi) * D * D * chi + m % chi}; },
+                 [=](int n) { return Off2{n, n * chi}; });
+  // out[x][r][z] = sum_{b,d} el[b][d][z] t2[x][r][d][b]      (m = z, n = (x, r), k = (b, d))
+  blk_gemm<1, 4>(el, t2, out, chi, chi * D, chi, D, D * chi, chi, 1, chi,
+                 [=](int m) { return Off2{m, m}; },
+                 [=](int n) { return Off2{n * D * chi, n * chi}; });
+}
+
+// R[x][r][z] -> R'[a][l][b] = sum eu[a][u][x] A[l][u][r][d] el[b][d][z] R[x][r][z].
+// t1: D^2 chi (chi+1) elements (its rows padded to chi+1), t2: chi^2 D^2.
 template <typename T, typename G>
 __device__ void absorb1_right(const G& g, const T* R, const T* eu, const T* A, const T* el, T* t1, T* t2, T* out) {
-  const int chi = g.chi, D = g.D, NT = blockDim.x, tid = threadIdx.x;
-  const int n1 = chi * D * D * chi;
-  // t1[a][u][r][z] = sum_x eu[a][u][x] R[x][r][z]
-  for (int o = tid; o < n1; o += NT) {
-    const int z = o % chi, r = (o / chi) % D, u = (o / (chi * D)) % D, a = o / (chi * D * D);
-    T s = 0;
-    for (int x = 0; x < chi; ++x) s += eu[(a * D + u) * chi + x] * R[(x * D + r) * chi + z];
-    t1[o] = s;
-  }
-  __syncthreads();
-  // t2[a][l][z][d] = sum_{u,r} t1[a][u][r][z] A[l][u][r][d]
-  for (int o = tid; o < n1; o += NT) {
-    const int dd = o % D, z = (o / D) % chi, l = (o / (D * chi)) % D, a = o / (D * chi * D);
-    T s = 0;
-    for (int u = 0; u < D; ++u)
-      for (int r = 0; r < D; ++r) s += t1[((a * D + u) * D + r) * chi + z] * A[((l * D + u) * D + r) * D + dd];
-    t2[o] = s;
-  }
-  __syncthreads();
-  // out[a][l][b] = sum_{z,d} t2[a][l][z][d] el[b][d][z]
-  for (int o = tid; o < g.se; o += NT) {
-    const int b = o % chi, l = (o / chi) % D, a = o / (chi * D);
-    T s = 0;
-    for (int z = 0; z < chi; ++z)
-      for (int dd = 0; dd < D; ++dd) s += t2[((a * D + l) * chi + z) * D + dd] * el[(b * D + dd) * chi + z];
-    out[o] = s;
-  }
-  __syncthreads();
+  const int chi = g.chi, D = g.D, P = chi + 1;
+  // t1[u][r][z][a] (rows of a padded to P) = sum_x R[x][r][z] eu[a][u][x]   (m = (r, z), n = (a, u))
+  blk_gemm<2, 8>(R, eu, t1, D * chi, chi * D, chi, 1, D * chi, 0, 1, 0,
+                 [=](int m) { return Off2{m, m * P}; },
+                 [=](int n) { return Off2{n * chi, (n % D) * D * chi * P + n / D}; });
+  // t2[z][d][a][l] = sum_{u,r} t1[u][r][z][a] A[l][u][r][d]   (m = (z, a), n = (l, d), k = (u, r))
+  blk_gemm<4, 4>(t1, A, t2, chi * chi, D * D, D, D, D * chi * P, chi * P, D * D, D,
+                 [=](int m) { return Off2{(m / chi) * P + m % chi, (m / chi) * D * chi * D + (m % chi) * D}; },
+                 [=](int n) { return Off2{(n / D) * D * D * D + n % D, (n % D) * chi * D + n / D}; });
+  // out[a][l][b] = sum_{z,d} t2[z][d][a][l] el[b][d][z]   (m = (a, l), n = b, k = (z, d))
+  blk_gemm<2, 2>(t2, el, out, chi * D, chi, chi, D, D * chi * D, chi * D, 1, chi,
+                 [=](int m) { return Off2{m, m * chi}; },
+                 [=](int n) { return Off2{n * D * chi, n}; });
 }
 
 // Site environment of the one-row sandwich: env[l][u][r][d] = sum L[a][l][b] eu[a][u][x]
-// el[b][d][z] R[x][r][z]  (= d psi_x / d A[l][u][r][d]).
+// el[b][d][z] R[x][r][z]  (= d psi_x / d A[l][u][r][d]).  elT[z][b][d] = el[b][d][z] (the lower
+// environment site read transposed, so that the contraction over z has a contiguous operand).
+// t1: chi^2 D^2, t2: chi^2 D^2.
 template <typename T, typename G>
-__device__ void site_env1(const G& g, const T* L, const T* eu, const T* el, const T* R, T* t1, T* t2, T* env) {
-  const int chi = g.chi, D = g.D, NT = blockDim.x, tid = threadIdx.x;
-  const int n1 = D * chi * D * chi;
-  // t1[l][b][u][x] = sum_a L[a][l][b] eu[a][u][x]
-  for (int o = tid; o < n1; o += NT) {
-    const int x = o % chi, u = (o / chi) % D, b = (o / (chi * D)) % chi, l = o / (chi * D * chi);
-    T s = 0;
-    for (int a = 0; a < chi; ++a) s += L[(a * D + l) * chi + b] * eu[(a * D + u) * chi + x];
-    t1[o] = s;
-  }
-  // t4[x][r][b][d] = sum_z R[x][r][z] el[b][d][z]
-  for (int o = tid; o < n1; o += NT) {
-    const int dd = o % D, b = (o / D) % chi, r = (o / (D * chi)) % D, x = o / (D * chi * D);
-    T s = 0;
-    for (int z = 0; z < chi; ++z) s += R[(x * D + r) * chi + z] * el[(b * D + dd) * chi + z];
-    t2[o] = s;
-  }
-  __syncthreads();
-  // env[l][u][r][d] = sum_{b,x} t1[l][b][u][x] t4[x][r][b][d]
-  for (int o = tid; o < g.sT; o += NT) {
-    const int dd = o % D, r = (o / D) % D, u = (o / (D * D)) % D, l = o / (D * D * D);
-    T s = 0;
-    for (int b = 0; b < chi; ++b)
-      for (int x = 0; x < chi; ++x) s += t1[((l * chi + b) * D + u) * chi + x] * t2[((x * D + r) * chi + b) * D + dd];
-    env[o] = s;
-  }
-  __syncthreads();
+__device__ void site_env1(const G& g, const T* L, const T* eu, const T* elT, const T* R, T* t1, T* t2, T* env) {
+  const int chi = g.chi, D = g.D;
+  // t1[u][l][x][b] = sum_a L[a][l][b] eu[a][u][x]   (as in absorb1)
+  blk_gemm<2, 8>(L, eu, t1, D * chi, D * chi, chi, 1, D * chi, 0, D * chi, 0,
+                 [=](int m) { return Off2{m, (m / chi) * chi * chi + m % chi}; },
+                 [=](int n) { return Off2{n, (n / chi) * D * chi * chi + (n % chi) * chi}; });
+  // t4[b][x][r][d] = sum_z elT[z][b][d] R[x][r][z]   (m = (b, d), n = (x, r), k = z)
+  blk_gemm<2, 8>(elT, R, t2, chi * D, chi * D, chi, 1, chi * D, 0, 1, 0,
+                 [=](int m) { return Off2{m, (m / D) * chi * D * D + m % D}; },
+                 [=](int n) { return Off2{n * chi, n * D}; });
+  // env[l][u][r][d] = sum_{b,x} t4[b][x][r][d] t1[u][l][x][b]   (m = (r, d), n = (l, u), k = (b, x))
+  blk_gemm<1, 1>(t2, t1, env, D * D, D * D, chi, chi, chi * D * D, D * D, 1, chi,
+                 [=](int m) { return Off2{m, m}; },
+                 [=](int n) { return Off2{(n % D) * D * chi * chi + (n / D) * chi * chi, n * D * D}; });
 }
 
 template <typename T>
@@ -1132,57 +1157,36 @@ __device__ T blk_dot(const T* a, const T* b, int n, double* red) {
 
 // ------------------------------------------------------------------------------------------
 // Two-row sandwich partials, chunked over the new upper bond (absorb2) / the old upper bond
-// (absorb2_right) so that the temporaries hold D^3 chi cx elements.
+// (absorb2_right) so that the temporaries hold D^3 chi c elements (c <= cx; absorb2_right's
+// first temporary holds chi more).  Intermediates are laid out so that the index that varies
+// across threads is contiguous in the operand it is read from.
 // L2[a][i][j][b] -> out[x][r1][r2][z] with eu[a][u][x], A1[i][u][r1][v], A2[j][v][r2][d], el[b][d][z]
 template <typename T, typename G>
 __device__ void absorb2(const G& g, const T* L2, const T* eu, const T* A1, const T* A2, const T* el,
                         T* t1, T* t2, T* out, int cx) {
-  const int chi = g.chi, D = g.D, NT = blockDim.x, tid = threadIdx.x;
+  const int chi = g.chi, D = g.D;
   for (int x0 = 0; x0 < chi; x0 += cx) {
     const int c = (chi - x0 < cx) ? chi - x0 : cx;
-    const int nt = D * D * chi * D * c;
-    // t1[i][j][b][u][xx] = sum_a L2[a][i][j][b] eu[a][u][x0+xx]
-    for (int o = tid; o < nt; o += NT) {
-      const int xx = o % c, u = (o / c) % D, b = (o / (c * D)) % chi, j = (o / (c * D * chi)) % D,
-                i = o / (c * D * chi * D);
-      T s = 0;
-      for (int a = 0; a < chi; ++a) s += L2[((a * D + i) * D + j) * chi + b] * eu[(a * D + u) * chi + x0 + xx];
-      t1[o] = s;
-    }
-    __syncthreads();
-    // t2[j][b][xx][r1][v] = sum_{i,u} t1[i][j][b][u][xx] A1[i][u][r1][v]
-    for (int o = tid; o < nt; o += NT) {
-      const int v = o % D, r1 = (o / D) % D, xx = (o / (D * D)) % c, b = (o / (D * D * c)) % chi,
-                j = o / (D * D * c * chi);
-      T s = 0;
-      for (int i = 0; i < D; ++i)
-        for (int u = 0; u < D; ++u)
-          s += t1[(((i * D + j) * chi + b) * D + u) * c + xx] * A1[((i * D + u) * D + r1) * D + v];
-      t2[o] = s;
-    }
-    __syncthreads();
-    // t3[b][xx][r1][r2][d] = sum_{j,v} t2[j][b][xx][r1][v] A2[j][v][r2][d]   (into t1)
-    for (int o = tid; o < nt; o += NT) {
-      const int dd = o % D, r2 = (o / D) % D, r1 = (o / (D * D)) % D, xx = (o / (D * D * D)) % c,
-                b = o / (D * D * D * c);
-      T s = 0;
-      for (int j = 0; j < D; ++j)
-        for (int v = 0; v < D; ++v)
-          s += t2[(((j * chi + b) * c + xx) * D + r1) * D + v] * A2[((j * D + v) * D + r2) * D + dd];
-      t1[o] = s;
-    }
-    __syncthreads();
-    // out[x0+xx][r1][r2][z] = sum_{b,d} t3[b][xx][r1][r2][d] el[b][d][z]
-    const int no = c * D * D * chi;
-    for (int o = tid; o < no; o += NT) {
-      const int z = o % chi, r2 = (o / chi) % D, r1 = (o / (chi * D)) % D, xx = o / (chi * D * D);
-      T s = 0;
-      for (int b = 0; b < chi; ++b)
-        for (int dd = 0; dd < D; ++dd)
-          s += t1[(((b * c + xx) * D + r1) * D + r2) * D + dd] * el[(b * D + dd) * chi + z];
-      out[(((x0 + xx) * D + r1) * D + r2) * chi + z] = s;
-    }
-    __syncthreads();
+    const int cc = chi * c;
+    // t1[i][u][j][b][xx] = sum_a L2[a][i][j][b] eu[a][u][x0+xx]      (m = (i, j, b), n = (u, xx))
+    blk_gemm<4, 4>(L2, eu + x0, t1, D * D * chi, D * c, chi, 1, D * D * chi, 0, D * chi, 0,
+                   [=](int m) { return Off2{m, (m / (D * chi)) * D * D * cc + (m % (D * chi)) * c}; },
+                   [=](int n) { return Off2{(n / c) * chi + n % c, (n / c) * D * cc + n % c}; });
+    // t2[j][v][b][xx][r1] = sum_{i,u} t1[i][u][j][b][xx] A1[i][u][r1][v]   (m = (j, b, xx), n = (r1, v))
+    blk_gemm<4, 4>(t1, A1, t2, D * cc, D * D, D, D, D * D * cc, D * cc, D * D * D, D * D,
+                   [=](int m) { return Off2{m, (m / cc) * D * D * cc + (m % cc) * D}; },
+                   [=](int n) { return Off2{n, (n % D) * cc * D + n / D}; });
+    // t3[r2][d][b][xx][r1] = sum_{j,v} t2[j][v][b][xx][r1] A2[j][v][r2][d]   (into t1; m = (b, xx, r1), n = (r2, d))
+    blk_gemm<4, 4>(t2, A2, t1, cc * D, D * D, D, D, D * cc * D, cc * D, D * D * D, D * D,
+                   [=](int m) { return Off2{m, m}; },
+                   [=](int n) { return Off2{n, n * cc * D}; });
+    // out[x0+xx][r1][r2][z] = sum_{b,d} el[b][d][z] t3[r2][d][b][xx][r1]   (m = z, n = (xx, r1, r2))
+    blk_gemm<1, 4>(el, t1, out, chi, c * D * D, chi, D, D * chi, chi, c * D, cc * D,
+                   [=](int m) { return Off2{m, m}; },
+                   [=](int n) {
+                     const int xx = n / (D * D), r1 = (n / D) % D, r2 = n % D;
+                     return Off2{r2 * D * cc * D + xx * D + r1, (((x0 + xx) * D + r1) * D + r2) * chi};
+                   });
   }
 }
 
@@ -1190,52 +1194,33 @@ __device__ void absorb2(const G& g, const T* L2, const T* eu, const T* A1, const
 template <typename T, typename G>
 __device__ void absorb2_right(const G& g, const T* R2, const T* eu, const T* A1, const T* A2, const T* el,
                               T* t1, T* t2, T* out, int ca) {
-  const int chi = g.chi, D = g.D, NT = blockDim.x, tid = threadIdx.x;
+  const int chi = g.chi, D = g.D;
   for (int a0 = 0; a0 < chi; a0 += ca) {
     const int c = (chi - a0 < ca) ? chi - a0 : ca;
-    const int nt = c * D * D * D * chi;
-    // t1[aa][u][r1][r2][z] = sum_x eu[a0+aa][u][x] R2[x][r1][r2][z]
-    for (int o = tid; o < nt; o += NT) {
-      const int z = o % chi, r2 = (o / chi) % D, r1 = (o / (chi * D)) % D, u = (o / (chi * D * D)) % D,
-                aa = o / (chi * D * D * D);
-      T s = 0;
-      for (int x = 0; x < chi; ++x) s += eu[((a0 + aa) * D + u) * chi + x] * R2[((x * D + r1) * D + r2) * chi + z];
-      t1[o] = s;
-    }
-    __syncthreads();
-    // t2[aa][i][v][r2][z] = sum_{u,r1} t1[aa][u][r1][r2][z] A1[i][u][r1][v]
-    for (int o = tid; o < nt; o += NT) {
-      const int z = o % chi, r2 = (o / chi) % D, v = (o / (chi * D)) % D, i = (o / (chi * D * D)) % D,
-                aa = o / (chi * D * D * D);
-      T s = 0;
-      for (int u = 0; u < D; ++u)
-        for (int r1 = 0; r1 < D; ++r1)
-          s += t1[(((aa * D + u) * D + r1) * D + r2) * chi + z] * A1[((i * D + u) * D + r1) * D + v];
-      t2[o] = s;
-    }
-    __syncthreads();
-    // t3[aa][i][j][z][d] = sum_{v,r2} t2[aa][i][v][r2][z] A2[j][v][r2][d]   (into t1)
-    for (int o = tid; o < nt; o += NT) {
-      const int dd = o % D, z = (o / D) % chi, j = (o / (D * chi)) % D, i = (o / (D * chi * D)) % D,
-                aa = o / (D * chi * D * D);
-      T s = 0;
-      for (int v = 0; v < D; ++v)
-        for (int r2 = 0; r2 < D; ++r2)
-          s += t2[(((aa * D + i) * D + v) * D + r2) * chi + z] * A2[((j * D + v) * D + r2) * D + dd];
-      t1[o] = s;
-    }
-    __syncthreads();
-    // out[a0+aa][i][j][b] = sum_{z,d} t3[aa][i][j][z][d] el[b][d][z]
-    const int no = c * D * D * chi;
-    for (int o = tid; o < no; o += NT) {
-      const int b = o % chi, j = (o / chi) % D, i = (o / (chi * D)) % D, aa = o / (chi * D * D);
-      T s = 0;
-      for (int z = 0; z < chi; ++z)
-        for (int dd = 0; dd < D; ++dd)
-          s += t1[(((aa * D + i) * D + j) * chi + z) * D + dd] * el[(b * D + dd) * chi + z];
-      out[(((a0 + aa) * D + i) * D + j) * chi + b] = s;
-    }
-    __syncthreads();
+    const int cdx = c * D * chi;             // one (u, r1) block of t1, one (v, r2) block of t2
+    const int Sz = D * c * D * D + 1;        // z stride of t3 (odd: consecutive z in different banks)
+    // t1[u][r1][aa][r2][z] = sum_x R2[x][r1][r2][z] eu[a0+aa][u][x]   (m = (r1, r2, z), n = (aa, u))
+    blk_gemm<4, 4>(R2, eu + (size_t)a0 * D * chi, t1, D * D * chi, c * D, chi, 1, D * D * chi, 0, 1, 0,
+                   [=](int m) { return Off2{m, (m / (D * chi)) * cdx + m % (D * chi)}; },
+                   [=](int n) { return Off2{n * chi, (n % D) * D * cdx + (n / D) * D * chi}; });
+    // t2[v][r2][aa][i][z] = sum_{u,r1} t1[u][r1][aa][r2][z] A1[i][u][r1][v]   (m = (aa, r2, z), n = (i, v))
+    blk_gemm<4, 4>(t1, A1, t2, cdx, D * D, D, D, D * cdx, cdx, D * D, D,
+                   [=](int m) {
+                     const int aa = m / (D * chi), r2 = (m / chi) % D, z = m % chi;
+                     return Off2{m, r2 * cdx + aa * D * chi + z};
+                   },
+                   [=](int n) { return Off2{(n / D) * D * D * D + n % D, (n % D) * D * cdx + (n / D) * chi}; });
+    // t3[z][d][aa][i][j] (z stride Sz) = sum_{v,r2} t2[v][r2][aa][i][z] A2[j][v][r2][d]   (into t1)
+    blk_gemm<4, 4>(t2, A2, t1, cdx, D * D, D, D, D * cdx, cdx, D * D, D,
+                   [=](int m) {
+                     const int aa = m / (D * chi), i = (m / chi) % D, z = m % chi;
+                     return Off2{m, z * Sz + aa * D * D + i * D};
+                   },
+                   [=](int n) { return Off2{(n / D) * D * D * D + n % D, (n % D) * c * D * D + n / D}; });
+    // out[a0+aa][i][j][b] = sum_{z,d} t3[z][d][aa][i][j] el[b][d][z]   (m = (aa, i, j), n = b)
+    blk_gemm<2, 4>(t1, el, out, c * D * D, chi, chi, D, Sz, c * D * D, 1, chi,
+                   [=](int m) { return Off2{m, (a0 * D * D + m) * chi}; },
+                   [=](int n) { return Off2{n * D * chi, n}; });
   }
 }
 

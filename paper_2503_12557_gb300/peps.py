@@ -69,6 +69,7 @@ def load():
         "peps_sample_learned": ([vp, i32, i32, vp, vp, vp, i32, C.c_uint64, C.c_uint64, vp, vp, vp], i32),
         "peps_timing_enable": ([vp, i32], i32),
         "peps_timing_read": ([vp, vp, vp, i32, vp], i32),
+        "peps_probe_fma": ([i32, C.POINTER(dbl), vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -82,7 +83,17 @@ def exported_symbols():
     return ["peps_create", "peps_destroy", "peps_num_params", "peps_set_params", "peps_amplitudes",
             "peps_local_energy", "peps_logderiv", "peps_evaluate", "minsr_step", "peps_sample", "peps_last_error",
             "peps_timing_enable", "peps_timing_read", "peps_apply_update", "peps_proposal_logits",
-            "peps_proposal_train_step", "peps_sample_learned"]
+            "peps_proposal_train_step", "peps_sample_learned", "peps_amplitudes_noalloc", "peps_probe_fma"]
+
+
+def probe_fma(fp64=False):
+    """Measured FP32 (or FP64) FMA throughput of the current GPU, TFLOP/s."""
+    L = load()
+    out = C.c_double(0.0)
+    st = L.peps_probe_fma(1 if fp64 else 0, C.byref(out), _stream())
+    if st != 0:
+        raise RuntimeError(f"peps_probe_fma failed: {_ERRORS.get(st, st)}")
+    return out.value
 
 
 class Proposal:
