@@ -40,7 +40,9 @@ def _args():
     ap.add_argument("--ns", type=int, default=None)
     ap.add_argument("--sweeps", type=int, default=2)
     ap.add_argument("--burnin", type=int, default=2)
-    ap.add_argument("--mode", default="step", choices=["step", "learned", "gram"])
+    ap.add_argument("--mode", default="step", choices=["step", "learned", "gram", "batch"])
+    ap.add_argument("--branches", type=int, default=8)
+    ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--cpu-samples", type=int, default=12)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -427,6 +429,66 @@ def run_gram(a):
     print(json.dumps(out), flush=True)
 
 
+def run_batch(a):
+    """Ragged multi-instance batch in one CUDA graph: 64 independent open Heisenberg PEPS with
+    (L, D) drawn uniformly from {6, 8, 10, 12} x {3, 4, 5} (seed 5005), chi = D^2, tensors as the
+    8x8 workload (0.5 N(0,1) + 1.0 bias), N_s configurations each (uniform S^z = 0); psi, E_loc and
+    O of every instance.  Reports samples/s of the graph replay, of the same calls issued one
+    after another, and (with --autotune) after tuning each handle."""
+    import torch
+    from paper_2503_12557_gb300 import build, inputs as I, peps as P
+    build.build()
+    ns = a.ns or 256
+    rng = np.random.default_rng(5005)
+    shapes = [(int(rng.choice([6, 8, 10, 12])), int(rng.choice([3, 4, 5]))) for _ in range(64)]
+    prec = P.PREC_FP32 if a.prec == "fp32" else P.PREC_FP64
+    items = []
+    for k, (L, D) in enumerate(shapes):
+        lat = I.Lattice(L, L, 2, D)
+        h = P.PEPS(L, L, 2, D, D * D, prec=prec, max_samples=ns)
+        h.set_params(torch.as_tensor(I.peps_random(lat, 5005 + k, scale=0.5, bias=1.0)).cuda())
+        S = torch.as_tensor(I.configs_uniform_sz0(lat, ns, 6005 + k)).cuda()
+        items.append((h, I.heisenberg(lat), S, True))
+    out = {"mode": "batch", "instances": 64, "ns_per_instance": ns, "precision": a.prec,
+           "shapes": {f"{L}x{L}_D{D}": sum(1 for s in shapes if s == (L, D)) for (L, D) in sorted(set(shapes))}}
+    if a.autotune:
+        kbs = {}
+        for (h, H, S, _) in items:
+            kbs[f"{h.Lx}x{h.Ly}_D{h.D}"] = h.autotune(S, H)
+        torch.cuda.synchronize()
+        out["autotune_kb"] = kbs
+    # one instance after another (eager), then the recorded graph
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        outs = [h.evaluate(H, S, want_O=True) for (h, H, S, _) in items]  # warm-up
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(a.steps):
+            outs = [h.evaluate(H, S, want_O=True) for (h, H, S, _) in items]
+        e1.record(stream)
+        stream.synchronize()
+    eager_ms = e0.elapsed_time(e1) / a.steps
+    batch = P.Batch(items, nbranch=a.branches, stream=stream)
+    for _ in range(a.warmup):
+        batch.launch()
+    stream.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(a.steps):
+        batch.launch()
+    f1.record(stream)
+    stream.synchronize()
+    graph_ms = f0.elapsed_time(f1) / a.steps
+    same = all(torch.equal(o["logabs"], r["logabs"]) and torch.equal(o["eloc"], r["eloc"])
+               for o, r in zip(batch.out, outs))
+    tot = 64 * ns
+    out.update({"graph_ms": graph_ms, "eager_ms": eager_ms, "graph_samples_per_s": tot / (graph_ms / 1e3),
+                "eager_samples_per_s": tot / (eager_ms / 1e3), "branches": a.branches,
+                "graph_equals_eager": bool(same)})
+    print(json.dumps(out), flush=True)
+
+
 def main():
     a = _args()
     if a.impl == "reference":
@@ -435,6 +497,8 @@ def main():
         run_learned(a)
     elif a.mode == "gram":
         run_gram(a)
+    elif a.mode == "batch":
+        run_batch(a)
     else:
         run_gpu(a)
 

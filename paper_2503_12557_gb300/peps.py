@@ -38,6 +38,12 @@ class _Ham(C.Structure):
                 ("onsite_host", C.POINTER(C.c_double))]
 
 
+class _BatchItem(C.Structure):
+    _fields_ = [("h", C.c_void_p), ("H", C.POINTER(_Ham)), ("S_dev", C.c_void_p), ("Ns", C.c_int),
+                ("logabs_dev", C.c_void_p), ("phase_dev", C.c_void_p), ("eloc_dev", C.c_void_p), ("O_dev", C.c_void_p),
+                ("status_dev", C.c_void_p)]
+
+
 def lib_path() -> str:
     return _LIBPATH
 
@@ -70,6 +76,10 @@ def load():
         "peps_timing_enable": ([vp, i32], i32),
         "peps_timing_read": ([vp, vp, vp, i32, vp], i32),
         "peps_probe_fma": ([i32, C.POINTER(dbl), vp], i32),
+        "peps_autotune": ([vp, C.POINTER(_Ham), vp, i32, i32, vp, vp], i32),
+        "peps_batch_create": ([C.POINTER(vp), C.POINTER(_BatchItem), i32, i32, vp], i32),
+        "peps_batch_launch": ([vp, vp], i32),
+        "peps_batch_destroy": ([vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -83,7 +93,8 @@ def exported_symbols():
     return ["peps_create", "peps_destroy", "peps_num_params", "peps_set_params", "peps_amplitudes",
             "peps_local_energy", "peps_logderiv", "peps_evaluate", "minsr_step", "peps_sample", "peps_last_error",
             "peps_timing_enable", "peps_timing_read", "peps_apply_update", "peps_proposal_logits",
-            "peps_proposal_train_step", "peps_sample_learned", "peps_amplitudes_noalloc", "peps_probe_fma"]
+            "peps_proposal_train_step", "peps_sample_learned", "peps_amplitudes_noalloc", "peps_probe_fma",
+            "peps_autotune", "peps_batch_create", "peps_batch_launch", "peps_batch_destroy"]
 
 
 def probe_fma(fp64=False):
@@ -232,6 +243,17 @@ class PEPS:
         assert S.is_cuda and S.dtype == torch.uint8 and S.dim() == 2 and S.shape[1] == self.Lx * self.Ly
         return S.contiguous()
 
+    def autotune(self, S, H=None, move=None):
+        """Pick the shared-memory budget of each kernel class by timing the candidates on S
+        (peps_autotune); returns the chosen budgets in KB (env, row, pair, sampler)."""
+        S = self._S(S)
+        mv = MOVE_EXCHANGE if move is None else move
+        kb = (C.c_int * 4)()
+        hc = self.hamiltonian(H) if H is not None else None
+        self._check(self.L.peps_autotune(self.h, C.byref(hc.c) if hc is not None else None, _ptr(S), S.shape[0], mv,
+                                         kb, _stream()), "peps_autotune")
+        return list(kb)
+
     def amplitudes(self, S):
         S = self._S(S)
         ns = S.shape[0]
@@ -321,3 +343,56 @@ class PEPS:
         self._check(self.L.peps_sample(self.h, int(move), _ptr(S), ns, int(nsweeps), int(seed) & (2 ** 64 - 1),
                                        int(sweep0), _ptr(acc), _ptr(st), _stream()), "peps_sample")
         return S, acc, st
+
+
+class Batch:
+    """Independent handles evaluated by one recorded CUDA graph (peps_batch_*).  items: a list of
+    (PEPS handle, H or None, S (device uint8), want_O); the output tensors are allocated here and
+    refreshed in place at every launch()."""
+
+    def __init__(self, items, nbranch=4, stream=None):
+        self.L = load()
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.keep, arr = [], (_BatchItem * len(items))()
+        self.out = []
+        for k, (h, H, S, want_O) in enumerate(items):
+            S = h._S(S)
+            ns = S.shape[0]
+            o = dict(S=S, logabs=torch.empty(ns, dtype=torch.float64, device=S.device),
+                     phase=torch.empty(ns, dtype=torch.float64, device=S.device),
+                     status=torch.zeros(ns, dtype=torch.int32, device=S.device))
+            o["eloc"] = torch.empty(ns, 2, dtype=torch.float64, device=S.device) if H is not None else None
+            o["O"] = torch.empty(ns, h.Np, dtype=h.odtype, device=S.device) if want_O else None
+            hc = h.hamiltonian(H) if H is not None else None
+            arr[k].h = h.h
+            arr[k].H = C.pointer(hc.c) if hc is not None else None
+            arr[k].S_dev = _ptr(S)
+            arr[k].Ns = ns
+            arr[k].logabs_dev, arr[k].phase_dev = _ptr(o["logabs"]), _ptr(o["phase"])
+            arr[k].eloc_dev = _ptr(o["eloc"]) if o["eloc"] is not None else None
+            arr[k].O_dev = _ptr(o["O"]) if o["O"] is not None else None
+            arr[k].status_dev = _ptr(o["status"])
+            self.keep.append((h, hc))
+            self.out.append(o)
+        self.b = C.c_void_p()
+        torch.cuda.current_stream().synchronize()
+        st = self.L.peps_batch_create(C.byref(self.b), arr, len(items), nbranch, C.c_void_p(self.stream.cuda_stream))
+        if st != 0:
+            raise RuntimeError(f"peps_batch_create failed: {_ERRORS.get(st, st)}")
+        self.stream.synchronize()
+
+    def launch(self):
+        st = self.L.peps_batch_launch(self.b, C.c_void_p(self.stream.cuda_stream))
+        if st != 0:
+            raise RuntimeError(f"peps_batch_launch failed: {_ERRORS.get(st, st)}")
+
+    def close(self):
+        if getattr(self, "b", None) and self.b.value:
+            self.L.peps_batch_destroy(self.b)
+            self.b = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -91,6 +91,7 @@ def test_heisenberg_4x4_exact_chi_vs_oracle_and_bruteforce(P):
     (5, 6, 3, 5, 24, 7),     # truncating, non-square, ragged tiles
     (3, 7, 2, 3, 16, 8),
     (6, 4, 3, 9, 12, 9),     # chi = D^2 (exact for Ly=4)
+    (4, 6, 5, 25, 6, 10),    # D = 5, chi = D^2 (the largest multi-instance shape; truncating)
 ])
 def test_truncated_heisenberg_vs_oracle(P, Lx, Ly, D, chi, ns, seed):
     lat = I.Lattice(Lx, Ly, 2, D)
