@@ -40,7 +40,7 @@ def _args():
     ap.add_argument("--ns", type=int, default=None)
     ap.add_argument("--sweeps", type=int, default=2)
     ap.add_argument("--burnin", type=int, default=2)
-    ap.add_argument("--mode", default="step", choices=["step", "learned", "gram", "batch"])
+    ap.add_argument("--mode", default="step", choices=["step", "learned", "gram", "batch", "complex"])
     ap.add_argument("--branches", type=int, default=8)
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--cpu-samples", type=int, default=12)
@@ -489,6 +489,51 @@ def run_batch(a):
     print(json.dumps(out), flush=True)
 
 
+def run_complex(a):
+    """10x10 open J1-J2-chiral model (J1 = 1, J2 = 0.5, chiral J_chi = 0.3 on every elementary
+    triangle) on a complex PEPS, D = 6, chi = 36, entries complex Gaussian with std 0.3 (real and
+    imaginary parts N(0, 0.045); mean-zero tensors, so the truncation error is large: this measures
+    throughput and the reduced-precision error, not physics), N_s uniform S^z = 0 configurations:
+    one exchange sweep, psi / E_loc / O, and one MinSR step with
+    the pseudo-inverse cutoff 1e-8.  complex64 contractions; a complex128 handle on the first 8
+    configurations gives the reduced-precision error."""
+    import torch
+    from paper_2503_12557_gb300 import build, inputs as I, peps as P
+    build.build()
+    ns = a.ns or 304
+    lat = I.Lattice(10, 10, 2, 6)
+    th = torch.as_tensor(I.peps_random(lat, 1003, scale=0.3, complex_=True)).cuda()
+    H = I.j1j2_chiral(lat)
+    S = torch.as_tensor(I.configs_uniform_sz0(lat, ns, 2003)).cuda()
+    h = P.PEPS(10, 10, 2, 6, 36, prec=P.PREC_FP32, max_samples=ns, cplx=True)
+    h.set_params(th)
+    out = {"mode": "complex", "workload": "10x10 J1-J2-chiral, complex PEPS D=6 chi=36", "ns": ns, "np": h.Np}
+    r = h.evaluate(H, S[:8])  # warm-up
+    torch.cuda.synchronize()
+    h.timing(True)
+    t0 = time.perf_counter()
+    h.sample(S, move=P.MOVE_EXCHANGE, nsweeps=1, seed=3003)
+    r = h.evaluate(H, S)
+    dth, info = h.minsr_step(r["O"], r["eloc"], lam=0.0, rcond=1e-8, tau=0.05)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    ms, la, ctr = h.timing_read()
+    h.timing(False)
+    eval_ms = ms["env"] + ms["row"] + ms["pair"] + ms["combine"]
+    out.update({"sweep_ms": ms["sample"], "eval_ms": eval_ms, "minsr_s": (ms["minsr_gram"] + ms["minsr_eig"] + ms["minsr_other"]) / 1e3,
+                "eval_samples_per_s": ns / (eval_ms / 1e3), "step_wall_s": wall, "minsr_info": [float(x) for x in info.cpu()],
+                "status_nonzero": int((r["status"] != 0).sum().item())})
+    h64 = P.PEPS(10, 10, 2, 6, 36, prec=P.PREC_FP64, max_samples=8, cplx=True)
+    h64.set_params(th)
+    r64 = h64.evaluate(H, S[:8])
+    torch.cuda.synchronize()
+    dl = (r["logabs"][:8] - r64["logabs"]).abs().max().item()
+    e32 = torch.complex(r["eloc"][:8, 0], r["eloc"][:8, 1])
+    e64 = torch.complex(r64["eloc"][:, 0], r64["eloc"][:, 1])
+    out["complex64_vs_complex128"] = {"max_dlogpsi": dl, "max_deloc_per_site": ((e32 - e64).abs().max().item()) / 100}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     a = _args()
     if a.impl == "reference":
@@ -499,6 +544,8 @@ def main():
         run_gram(a)
     elif a.mode == "batch":
         run_batch(a)
+    elif a.mode == "complex":
+        run_complex(a)
     else:
         run_gpu(a)
 

@@ -86,6 +86,10 @@ typedef struct {
     int solve;    /* MinSR solve when rcond == 0: 0 = FP64 Cholesky; 1 = FP32 Cholesky of
                      T + lambda followed by 4 steps of iterative refinement with FP64 residuals
                      (info[1] reports the final relative residual)                           */
+    int cplx;     /* 0 = real PEPS; 1 = complex PEPS: theta is N_p (re, im) pairs of doubles,
+                     O is N_s x N_p complex numbers in the handle's precision ((re, im) pairs
+                     of doubles or floats), phases and E_loc are complex.  Not with gram = 1,
+                     the learned proposal or peps_amplitudes_noalloc (PEPS_E_UNSUPPORTED). */
 } peps_config;
 
 /* One local Hamiltonian term: h is a d^k x d^k complex matrix, row major, interleaved
@@ -121,7 +125,8 @@ peps_status peps_destroy(peps_handle* h);
 /* N_p = sum over sites of d * Dl * Du * Dr * Dd (boundary legs of dimension 1). */
 long long peps_num_params(const peps_handle* h);
 
-/* Copy theta (N_p doubles, device) into the handle's padded kernel layout (converted to the
+/* Copy theta (N_p doubles, or N_p (re, im) pairs of doubles for a complex PEPS; device) into the
+ * handle's padded kernel layout (converted to the
  * handle's precision).  Later calls use this copy until the next peps_set_params. */
 peps_status peps_set_params(peps_handle* h, const double* theta_dev, void* stream);
 
@@ -154,7 +159,10 @@ peps_status peps_evaluate(peps_handle* h, const peps_hamiltonian* H, const uint8
  *   T = Obar Obar^T = V diag(Lambda) V^T;  kept = Lambda_i > rcond * max Lambda (all when rcond == 0);
  *   dtheta = -tau Obar^T V diag(kept / (Lambda + lambda)) V^T ebar.
  * O_dev: Ns x N_p in the handle's precision (as written by peps_logderiv); eloc_dev: Ns x 2
- * doubles (the real parts are used: real PEPS); dtheta_dev: N_p doubles (written);
+ * doubles (the real parts are used by a real PEPS, both by a complex one); dtheta_dev: N_p
+ * doubles, or N_p (re, im) pairs for a complex PEPS (written).  A complex PEPS runs the same
+ * steps on the real embedding W = [[Re Obar, -Im Obar], [Im Obar, Re Obar]] (W W^T is the real
+ * form of the Hermitian T = Obar Obar^H), with the rank in info[0] counted once per eigenvalue;
  * info_dev: 4 doubles.  rcond > 0: eigendecomposition by cyclic Jacobi, info = (rank kept,
  * min Lambda, max Lambda, Jacobi sweeps).  rcond == 0 (nothing cut, lambda > 0): the same
  * operator (T + lambda)^-1 applied through a Cholesky factorisation, info = (Ns, NaN, NaN, -1)

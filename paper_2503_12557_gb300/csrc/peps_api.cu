@@ -22,6 +22,7 @@ struct KPlan {
 
 struct peps_handle {
   peps_config cfg{};
+  int elem = 0;  // scalar of the kernels: 0 double, 1 float, 2 cplx<double>, 3 cplx<float>
   size_t budget[4] = {0, 0, 0, 0};  // shared-memory budget per kernel class (env, row, pair, sample)
   Geo g{};
   long long Np = 0;
@@ -73,6 +74,17 @@ struct peps_handle {
   void *g_hi = nullptr, *g_lo = nullptr;
   std::string err;
 };
+
+// Run f(T{}) with T the handle's kernel scalar.
+template <typename F>
+static auto dispatch_elem(const peps_handle* h, F&& f) {
+  switch (h->elem) {
+    case 0: return f(double{});
+    case 1: return f(float{});
+    case 2: return f(cplx<double>{});
+    default: return f(cplx<float>{});
+  }
+}
 
 enum { TC_ENV = 0, TC_ROW, TC_PAIR, TC_COMBINE, TC_SAMPLE, TC_GRAM, TC_EIG, TC_MINSR, TC_PAD, TC_N };
 
@@ -167,7 +179,7 @@ static void place_overlay(Plan& p, size_t& smem, size_t budget, const std::vecto
 
 // Default shared-memory budget per CTA: FP64 one CTA per SM (the FP64 pipe is the limit), FP32
 // two CTAs per SM.
-static size_t default_budget(const peps_handle* h) { return (h->esz == 8) ? 210 * 1024 : 110 * 1024; }
+static size_t default_budget(const peps_handle* h) { return (h->esz >= 8) ? 210 * 1024 : 110 * 1024; }
 
 static void plan_all(peps_handle* h) {
   const Geo& g = h->g;
@@ -246,7 +258,8 @@ static void plan_all(peps_handle* h) {
 
 // The dynamic shared-memory limit is a property of a kernel instantiation, shared by every handle
 // that launches it: only ever raise it (per precision and compiled shape), so that handles with
-// different budgets can coexist.
+// different budgets can coexist.  Keyed by the scalar type (float and complex<float> kernels are
+// different instantiations of the same size).
 static std::mutex g_attr_mu;
 static std::map<std::pair<int, int>, size_t> g_attr_max;
 
@@ -259,9 +272,9 @@ static peps_status finish_plans(peps_handle* h) {
     const int variant = (h->g.chi == 16 && h->g.D == 4) ? 1 : (h->g.chi == 24 && h->g.D == 4) ? 2 : 0;
     int dev = 0;
     cudaGetDevice(&dev);
-    size_t& cur = g_attr_max[{(int)h->esz * 64 + dev, variant}];
+    size_t& cur = g_attr_max[{h->elem * 64 + dev, variant}];  // per kernel scalar type
     if (maxsmem > cur) {
-      e = (h->esz == 8) ? set_kernel_smem<double>(h->g, maxsmem) : set_kernel_smem<float>(h->g, maxsmem);
+      e = dispatch_elem(h, [&](auto z) { return set_kernel_smem<decltype(z)>(h->g, maxsmem); });
       if (e == cudaSuccess) cur = maxsmem;
     }
   }
@@ -269,7 +282,7 @@ static peps_status finish_plans(peps_handle* h) {
   size_t gmax = 0;
   for (int i = 0; i < 4; ++i) {
     KPlan& k = h->kp[i];
-    int occ = (h->esz == 8) ? occupancy<double>(h->g, i, k.smem) : occupancy<float>(h->g, i, k.smem);
+    int occ = dispatch_elem(h, [&](auto z) { return occupancy<decltype(z)>(h->g, i, k.smem); });
     if (occ < 1) return fail(h, PEPS_E_SHAPE, "kernel does not fit on an SM");
     k.grid = h->nsm * occ;
     gmax = std::max(gmax, (size_t)k.grid * (size_t)k.p.gstride);
@@ -304,9 +317,12 @@ extern "C" peps_status peps_create(peps_handle** out, const peps_config* cfg) {
   if (c.prec != PEPS_PREC_FP64 && c.prec != PEPS_PREC_FP32) return PEPS_E_ARG;
   if (c.gram != 0 && c.gram != 1) return PEPS_E_ARG;
   if (c.solve != 0 && c.solve != 1) return PEPS_E_ARG;
+  if (c.cplx != 0 && c.cplx != 1) return PEPS_E_ARG;
+  if (c.cplx && c.gram != 0) return PEPS_E_UNSUPPORTED;  // the split-BF16 Gram is real only
   peps_handle* h = new peps_handle();
   h->cfg = c;
-  h->esz = (c.prec == PEPS_PREC_FP64) ? 8 : 4;
+  h->elem = (c.cplx ? 2 : 0) + (c.prec == PEPS_PREC_FP64 ? 0 : 1);
+  h->esz = (size_t)((c.prec == PEPS_PREC_FP64) ? 8 : 4) * (c.cplx ? 2 : 1);
   Geo& g = h->g;
   g.Lx = c.Lx; g.Ly = c.Ly; g.d = c.d; g.D = c.D; g.chi = c.chi;
   g.n = c.chi * c.D;
@@ -373,8 +389,10 @@ extern "C" peps_status peps_set_params(peps_handle* h, const double* theta_dev, 
   if (!h || !theta_dev) return fail(h, PEPS_E_ARG, "null argument");
   cudaStream_t s = (cudaStream_t)stream;
   const int ts = tstart(h, TC_PAD, s);
-  cudaError_t e = (h->esz == 8) ? launch_pad<double>(h->g, theta_dev, h->site_off, (double*)h->Tpad, s)
-                                : launch_pad<float>(h->g, theta_dev, h->site_off, (float*)h->Tpad, s);
+  cudaError_t e = dispatch_elem(h, [&](auto z) {
+    using T = decltype(z);
+    return launch_pad<T>(h->g, theta_dev, h->site_off, (T*)h->Tpad, s);
+  });
   if (e != cudaSuccess) return cuda_fail(h, e, "pad theta");
   tstop(h, ts, s);
   return PEPS_OK;
@@ -575,9 +593,10 @@ extern "C" peps_status peps_evaluate(peps_handle* h, const peps_hamiltonian* H, 
   if (c != PEPS_OK) return c;
   if (eloc_dev && !H) return fail(h, PEPS_E_ARG, "eloc requested without a Hamiltonian");
   const int sides = (eloc_dev || O_dev) ? 3 : 1;
-  if (h->esz == 8)
-    return run_eval<double>(h, H, S_dev, Ns, logabs_dev, phase_dev, eloc_dev, O_dev, status_dev, (cudaStream_t)stream, sides);
-  return run_eval<float>(h, H, S_dev, Ns, logabs_dev, phase_dev, eloc_dev, O_dev, status_dev, (cudaStream_t)stream, sides);
+  return dispatch_elem(h, [&](auto z) {
+    return run_eval<decltype(z)>(h, H, S_dev, Ns, logabs_dev, phase_dev, eloc_dev, O_dev, status_dev,
+                                 (cudaStream_t)stream, sides);
+  });
 }
 
 extern "C" peps_status peps_amplitudes(peps_handle* h, const uint8_t* S_dev, int Ns, double* logabs_dev,
@@ -612,28 +631,30 @@ extern "C" peps_status peps_sample(peps_handle* h, int move, uint8_t* S_dev, int
   const KPlan& k = h->kp[3];
   const int grid = std::min(k.grid, Ns);
   const int ts = tstart(h, TC_SAMPLE, s);
-  cudaError_t e = (h->esz == 8)
-                      ? launch_sample<double>(h->g, k.p, grid, k.smem, (const double*)h->Tpad, S_dev, Ns, move, nsweeps,
-                                              seed, sweep0, (double*)h->envs, h->logs, accepted_dev, st, s)
-                      : launch_sample<float>(h->g, k.p, grid, k.smem, (const float*)h->Tpad, S_dev, Ns, move, nsweeps,
-                                             seed, sweep0, (float*)h->envs, h->logs, accepted_dev, st, s);
+  cudaError_t e = dispatch_elem(h, [&](auto z) {
+    using T = decltype(z);
+    return launch_sample<T>(h->g, k.p, grid, k.smem, (const T*)h->Tpad, S_dev, Ns, move, nsweeps, seed, sweep0,
+                            (T*)h->envs, h->logs, accepted_dev, st, s);
+  });
   if (e != cudaSuccess) return cuda_fail(h, e, "sampler kernel");
   tstop(h, ts, s);
   return PEPS_OK;
 }
 
 // ---- MinSR -------------------------------------------------------------------------------
-static peps_status ensure_minsr(peps_handle* h, int Ns) {
+// MinSR workspace for Ns rows of Np real columns (a complex handle passes its real embedding:
+// 2 Ns x 2 Np)
+static peps_status ensure_minsr(peps_handle* h, int Ns, long long Np) {
   const int n = Ns + (Ns & 1);
-  if (h->ms_cap >= n) return PEPS_OK;
+  if (h->ms_cap >= n && h->ms_np >= Np) return PEPS_OK;
   double** bufs[] = {&h->Obar, &h->Tm, &h->Vm, &h->Hm, &h->mean, &h->ebar, &h->yv, &h->xv, &h->cnt};
   for (double** b : bufs)
     if (*b) { cudaFree(*b); *b = nullptr; }
   const size_t nn = (size_t)n * n;
-  if (cudaMalloc(&h->Obar, sizeof(double) * (size_t)Ns * h->Np) != cudaSuccess ||
+  if (cudaMalloc(&h->Obar, sizeof(double) * (size_t)Ns * Np) != cudaSuccess ||
       cudaMalloc(&h->Tm, sizeof(double) * nn) != cudaSuccess || cudaMalloc(&h->Vm, sizeof(double) * nn) != cudaSuccess ||
       cudaMalloc(&h->Hm, sizeof(double) * nn) != cudaSuccess ||
-      cudaMalloc(&h->mean, sizeof(double) * (size_t)h->Np) != cudaSuccess ||
+      cudaMalloc(&h->mean, sizeof(double) * (size_t)Np) != cudaSuccess ||
       cudaMalloc(&h->ebar, sizeof(double) * n) != cudaSuccess || cudaMalloc(&h->yv, sizeof(double) * n) != cudaSuccess ||
       cudaMalloc(&h->xv, sizeof(double) * n) != cudaSuccess || cudaMalloc(&h->cnt, sizeof(double) * 8) != cudaSuccess)
     return fail(h, PEPS_E_WORKSPACE, "MinSR workspace allocation failed");
@@ -645,6 +666,7 @@ static peps_status ensure_minsr(peps_handle* h, int Ns) {
       return fail(h, PEPS_E_WORKSPACE, "tensor-core Gram workspace allocation failed");
   }
   h->ms_cap = n;
+  h->ms_np = Np;
   return PEPS_OK;
 }
 
@@ -655,17 +677,30 @@ extern "C" peps_status minsr_step(peps_handle* h, const void* O_dev, const doubl
   if (!O_dev || !eloc_dev || !dtheta_dev || !info_dev || Ns < 2) return fail(h, PEPS_E_ARG, "bad MinSR argument");
   if (!(lambda > 0.0 || rcond > 0.0) || lambda < 0.0 || rcond < 0.0)
     return fail(h, PEPS_E_ARG, "MinSR needs lambda > 0 or rcond > 0");
-  peps_status ps = ensure_minsr(h, Ns);
+  // a complex handle solves the real embedding (2 Ns rows, 2 N_p columns), see launch_center_cplx
+  const bool cx = h->cfg.cplx != 0;
+  const int Ns_c = Ns;
+  const long long Np_c = h->Np;
+  if (cx) Ns = 2 * Ns;
+  const long long Np = cx ? 2 * h->Np : h->Np;
+  peps_status ps = ensure_minsr(h, Ns, Np);
   if (ps != PEPS_OK) return ps;
   cudaStream_t s = (cudaStream_t)stream;
   const int n = Ns + (Ns & 1);
-  const long long Np = h->Np;
   int ts = tstart(h, TC_MINSR, s);
-  cudaError_t e = (h->esz == 8) ? launch_center<double>((const double*)O_dev, w_dev, Ns, Np, h->mean, h->Obar, s)
-                                : launch_center<float>((const float*)O_dev, w_dev, Ns, Np, h->mean, h->Obar, s);
-  if (e != cudaSuccess) return cuda_fail(h, e, "centre O");
   CK(cudaMemsetAsync(h->ebar, 0, sizeof(double) * n, s), "memset");
-  CK(launch_center_e(eloc_dev, w_dev, Ns, h->ebar, s), "centre E_loc");
+  cudaError_t e = dispatch_elem(h, [&](auto z) {
+    using T = decltype(z);
+    using R = typename Scal<T>::R;
+    if constexpr (Scal<T>::complex) {
+      const cudaError_t e1 = launch_center_cplx<R>((const R*)O_dev, w_dev, Ns_c, Np_c, h->Obar, s);
+      return e1 != cudaSuccess ? e1 : launch_center_e_cplx(eloc_dev, w_dev, Ns_c, h->ebar, s);
+    } else {
+      const cudaError_t e1 = launch_center<T>((const T*)O_dev, w_dev, Ns, Np, h->mean, h->Obar, s);
+      return e1 != cudaSuccess ? e1 : launch_center_e(eloc_dev, w_dev, Ns, h->ebar, s);
+    }
+  });
+  if (e != cudaSuccess) return cuda_fail(h, e, "centre O and E_loc");
   CK(cudaMemsetAsync(h->Tm, 0, sizeof(double) * (size_t)n * n, s), "memset");
   tstop(h, ts, s, w_dev ? 3 : 2);
   ts = tstart(h, TC_GRAM, s);
@@ -717,7 +752,8 @@ extern "C" peps_status minsr_step(peps_handle* h, const void* O_dev, const doubl
     tstop(h, ts, s, nl);
   }
   ts = tstart(h, TC_MINSR, s);
-  CK(launch_obar_t_x(h->Obar, h->xv, Ns, Np, tau, dtheta_dev, s), "Obar^T x");
+  CK(launch_obar_t_x(h->Obar, h->xv, Ns, Np, tau, cx ? h->mean : dtheta_dev, s), "Obar^T x");
+  if (cx) CK(launch_unembed(h->mean, Np_c, dtheta_dev, s), "dtheta");
   tstop(h, ts, s, 1);
   CK(cudaMemcpyAsync(info_dev + 3, &sw, sizeof(double), cudaMemcpyHostToDevice, s), "info");
   CK(cudaStreamSynchronize(s), "MinSR sync");
@@ -725,6 +761,15 @@ extern "C" peps_status minsr_step(peps_handle* h, const void* O_dev, const doubl
     int gerr = 0;
     CK(cudaMemcpy(&gerr, h->cnt + 4, sizeof(int), cudaMemcpyDeviceToHost), "read Gram status");
     if (gerr) return fail(h, PEPS_E_CUDA, "tensor-core Gram: a pipeline wait timed out");
+  }
+  if (cx) {
+    // the embedding counts every eigenvalue of T twice
+    double i0 = 0.0;
+    CK(cudaMemcpy(&i0, info_dev, sizeof(double), cudaMemcpyDeviceToHost), "read info");
+    if (i0 > 0.0) {
+      i0 *= 0.5;
+      CK(cudaMemcpy(info_dev, &i0, sizeof(double), cudaMemcpyHostToDevice), "write info");
+    }
   }
   if (rcond == 0.0) {
     // a factorisation that broke down gives no usable dtheta: return zero and warn
@@ -767,7 +812,7 @@ extern "C" peps_status peps_autotune(peps_handle* h, const peps_hamiltonian* H, 
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  std::vector<size_t> cand = (h->esz == 8) ? std::vector<size_t>{100 * 1024, 210 * 1024}
+  std::vector<size_t> cand = (h->esz >= 8) ? std::vector<size_t>{100 * 1024, 210 * 1024}
                                            : std::vector<size_t>{72 * 1024, 110 * 1024, 220 * 1024};
   for (auto& b : cand) b = std::min(b, (size_t)optin - 2048);
   // scratch outputs and a copy of the configurations for the sampler trial
@@ -963,7 +1008,7 @@ extern "C" peps_status peps_apply_update(peps_handle* h, double* theta_dev, cons
   if (!h || !theta_dev || !dtheta_dev) return fail(h, PEPS_E_ARG, "null argument");
   cudaStream_t s = (cudaStream_t)stream;
   const int ts = tstart(h, TC_PAD, s);
-  CK(launch_axpy(theta_dev, dtheta_dev, h->Np, s), "theta update");
+  CK(launch_axpy(theta_dev, dtheta_dev, h->Np * (h->cfg.cplx ? 2 : 1), s), "theta update");
   tstop(h, ts, s);
   return peps_set_params(h, theta_dev, stream);
 }
@@ -1026,6 +1071,7 @@ extern "C" peps_status peps_sample_learned(peps_handle* h, int C, int wprec, con
   if (c != PEPS_OK) return c;
   if (!prop_shape_ok(h->g.Lx, h->g.Ly, C, wprec)) return fail(h, PEPS_E_SHAPE, "proposal network shape");
   if (Ns > 0 && (!w_dev || !logpsi_dev)) return fail(h, PEPS_E_ARG, "null argument");
+  if (h->cfg.cplx) return fail(h, PEPS_E_UNSUPPORTED, "learned proposal: real PEPS only");
   if (Ns == 0) return PEPS_OK;
   peps_status ps = ensure_learned(h);
   if (ps != PEPS_OK) return ps;

@@ -90,6 +90,12 @@ template <typename TO>
 cudaError_t launch_center(const TO* O, const double* w, int Ns, long long Np, double* mean, double* Obar,
                           cudaStream_t s);
 cudaError_t launch_center_e(const double* eloc, const double* w, int Ns, double* ebar, cudaStream_t s);
+// complex O (Ns x Np (re, im) pairs of TO): the real embedding W (2Ns x 2Np), [Re ebar; Im ebar]
+// (2Ns), and dtheta back from [Re; Im] (2Np) to Np (re, im) pairs
+template <typename TO>
+cudaError_t launch_center_cplx(const TO* O, const double* w, int Ns, long long Np, double* W, cudaStream_t s);
+cudaError_t launch_center_e_cplx(const double* eloc, const double* w, int Ns, double* ebar2, cudaStream_t s);
+cudaError_t launch_unembed(const double* d2, long long Np, double* dtheta, cudaStream_t s);
 cudaError_t launch_gram(const double* Obar, int Ns, long long Np, double* Tm, int ld, cudaStream_t s);
 // cyclic Jacobi eigendecomposition of the symmetric Ns x Ns matrix A (overwritten by its
 // diagonal form), V accumulates the rotations; returns the sweeps used (host loop)

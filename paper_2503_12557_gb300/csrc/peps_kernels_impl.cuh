@@ -223,7 +223,10 @@ __global__ void __launch_bounds__(NTHREADS) k_row(G g, Plan plan, const T* __res
           const int s = o / blk, c = o % blk;
           const int dd = c % Dd, r = (c / Dd) % Dr, u = (c / (Dd * Dr)) % Du, l = c / (Dd * Dr * Du);
           T v = T(0);
-          if (s == s_here) v = (T)((double)A[((l * D + u) * D + r) * D + dd] * sc / (double)val);
+          if (s == s_here) {
+            const dz e = to_dz(A[((l * D + u) * D + r) * D + dd]);
+            v = from_dz<T>(dz_div(dz{e.re * sc, e.im * sc}, to_dz(val)));
+          }
           Orow[o] = v;
         }
         __syncthreads();
@@ -257,17 +260,19 @@ __global__ void __launch_bounds__(NTHREADS) k_row(G g, Plan plan, const T* __res
           }
           const T v = blk_dot(LW, RP + (size_t)(y0 + w) * se, se, red);
           lw += logR[y0 + w];
-          const double ratio = (double)v / (double)val * exp(lw - lpsi_norm);
-          ere += hr * ratio;
-          eim += hi * ratio;
+          const dz q = dz_div(to_dz(v), to_dz(val));
+          const double f = exp(lw - lpsi_norm);
+          ere += (hr * q.re - hi * q.im) * f;
+          eim += (hr * q.im + hi * q.re) * f;
         }
       }
     }
     if (threadIdx.x == 0) {
       double* out = rowout + ((size_t)smp * g.Lx + x) * 4;
-      const double av = fabs((double)val);
+      const dz vz = to_dz(val);
+      const double av = dz_abs(vz);
       out[0] = (av > 0.0) ? log(av) + lpsi_norm + env_log : -INFINITY;
-      out[1] = ((double)val < 0.0) ? 3.141592653589793 : 0.0;
+      out[1] = (vz.im == 0.0) ? ((vz.re < 0.0) ? 3.141592653589793 : 0.0) : atan2(vz.im, vz.re);
       out[2] = ere;
       out[3] = eim;
       int s = st;
@@ -373,9 +378,10 @@ __global__ void __launch_bounds__(NTHREADS) k_pair(G g, Plan plan, const T* __re
         }
         const T v = blk_dot(LW, RP + (size_t)(y0 + w) * s2, s2, red);
         lw += logR[y0 + w];
-        const double ratio = (double)v / (double)val * exp(lw - lpsi_norm);
-        ere += hr * ratio;
-        eim += hi * ratio;
+        const dz q = dz_div(to_dz(v), to_dz(val));
+        const double f = exp(lw - lpsi_norm);
+        ere += (hr * q.re - hi * q.im) * f;
+        eim += (hr * q.im + hi * q.re) * f;
       }
     }
     if (threadIdx.x == 0) {
@@ -385,7 +391,7 @@ __global__ void __launch_bounds__(NTHREADS) k_pair(G g, Plan plan, const T* __re
       out[2] = ere;
       out[3] = eim;
       int s = st;
-      if (!((double)val != 0.0) || !isfinite(ere) || !isfinite(eim)) s |= ST_NONFINITE;
+      if (!(dz_abs(to_dz(val)) != 0.0) || !isfinite(ere) || !isfinite(eim)) s |= ST_NONFINITE;
       if (s) atomicOr(status + smp, s);
     }
     __syncthreads();
@@ -499,8 +505,8 @@ __global__ void __launch_bounds__(NTHREADS, MinBlocks<T>::value) k_sample(G g, P
           }
           __syncthreads();
           if (threadIdx.x == 0) {
-            const double v = (double)RP[0];
-            lcur = (v != 0.0) ? log(fabs(v)) + logR[0] : -INFINITY;
+            const double v = dz_abs(to_dz(RP[0]));
+            lcur = (v != 0.0) ? log(v) + logR[0] : -INFINITY;
             logLc = 0.0;
           }
           blk_unit(LC, se);
@@ -532,7 +538,8 @@ __global__ void __launch_bounds__(NTHREADS, MinBlocks<T>::value) k_sample(G g, P
               }
               const T v = blk_dot(LW, RP + (size_t)(y + w_) * se, se, red);
               if (threadIdx.x == 0) {
-                const double l1 = ((double)v != 0.0) ? log(fabs((double)v)) + lw + logR[y + w_] : -INFINITY;
+                const double av = dz_abs(to_dz(v));
+                const double l1 = (av != 0.0) ? log(av) + lw + logR[y + w_] : -INFINITY;
                 accept_flag = (isfinite(l1) && u < exp(2.0 * (l1 - lcur))) ? 1 : 0;
                 if (accept_flag) {
                   lcur = l1;
@@ -573,8 +580,8 @@ __global__ void __launch_bounds__(NTHREADS, MinBlocks<T>::value) k_sample(G g, P
           }
           __syncthreads();
           if (threadIdx.x == 0) {
-            const double v = (double)RP[0];
-            lcur = (v != 0.0) ? log(fabs(v)) + logR[0] : -INFINITY;
+            const double v = dz_abs(to_dz(RP[0]));
+            lcur = (v != 0.0) ? log(v) + logR[0] : -INFINITY;
             logLc = 0.0;
           }
           blk_unit(LC, s2);
@@ -593,7 +600,8 @@ __global__ void __launch_bounds__(NTHREADS, MinBlocks<T>::value) k_sample(G g, P
               const double lw = logLc + blk_normalize(LW2, s2, red, &st);
               const T v = blk_dot(LW2, RP + (size_t)(y + 1) * s2, s2, red);
               if (threadIdx.x == 0) {
-                const double l1 = ((double)v != 0.0) ? log(fabs((double)v)) + lw + logR[y + 1] : -INFINITY;
+                const double av = dz_abs(to_dz(v));
+                const double l1 = (av != 0.0) ? log(av) + lw + logR[y + 1] : -INFINITY;
                 accept_flag = (isfinite(l1) && u < exp(2.0 * (l1 - lcur))) ? 1 : 0;
                 if (accept_flag) {
                   lcur = l1;
@@ -648,8 +656,11 @@ __global__ void k_pad_theta(Geo g, const double* __restrict__ theta, const long 
     int Dl, Du, Dr, Dd;
     site_dims(g, x, y, &Dl, &Du, &Dr, &Dd);
     T v = T(0);
-    if (l < Dl && u < Du && r < Dr && dd < Dd)
-      v = (T)theta[site_off[site] + (((long long)s * Dl + l) * Du + u) * Dr * Dd + (long long)r * Dd + dd];
+    if (l < Dl && u < Du && r < Dr && dd < Dd) {
+      const long long k = site_off[site] + (((long long)s * Dl + l) * Du + u) * Dr * Dd + (long long)r * Dd + dd;
+      if constexpr (Scal<T>::complex) v = from_dz<T>(dz{theta[2 * k], theta[2 * k + 1]});  // (re, im) pairs
+      else v = (T)theta[k];
+    }
     Tpad[o] = v;
   }
 }
@@ -664,13 +675,19 @@ static cudaError_t with_geo(const Geo& g, F&& f) {
   if (g.chi == 24 && g.D == 4) return f(GeoS<24, 4>{g.Lx, g.Ly, g.d});
   return f(g);
 }
+// complex PEPS run the runtime-shape kernels only
+template <typename T, typename F>
+static cudaError_t with_geo_for(const Geo& g, F&& f) {
+  if constexpr (Scal<T>::complex) return f(g);
+  else return with_geo(g, f);
+}
 
 // Each translation unit defines PEPS_PART_ENV, PEPS_PART_ROW (k_row, k_pair, parameter padding)
 // or PEPS_PART_SAMPLE and instantiates its kernels with PEPS_INST_<part>(T).
 #define PEPS_KATTR(NAME, KERNEL)                                                                                   \
   template <typename T>                                                                                          \
   cudaError_t NAME(const Geo& g, size_t set_bytes, int* occ, size_t occ_smem) {                                  \
-    return with_geo(g, [&](auto gg) {                                                                            \
+    return with_geo_for<T>(g, [&](auto gg) {                                                                            \
       using GG = decltype(gg);                                                                                   \
       cudaError_t e = cudaSuccess;                                                                               \
       if (set_bytes) e = cudaFuncSetAttribute(KERNEL<T, GG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)set_bytes); \
@@ -683,7 +700,7 @@ static cudaError_t with_geo(const Geo& g, F&& f) {
 template <typename T>
 cudaError_t launch_env(const Geo& g, const Plan& p, int grid, size_t smem, const T* Tpad, const uint8_t* S, int Ns,
                        int sides, T* envs, double* logs, int* status, float* wdisc, cudaStream_t s) {
-  return with_geo(g, [&](auto gg) {
+  return with_geo_for<T>(g, [&](auto gg) {
     k_env<T, decltype(gg)><<<grid, NTHREADS, smem, s>>>(gg, p, Tpad, S, Ns, sides, envs, logs, status, wdisc);
     return cudaGetLastError();
   });
@@ -700,7 +717,7 @@ template <typename T>
 cudaError_t launch_row(const Geo& g, const Plan& p, int grid, size_t smem, const T* Tpad, const uint8_t* S, int Ns,
                        int x_lo, int x_hi, const T* envs, const double* logs, T* O, const long long* site_off,
                        long long Np, const TermTab& tt, double* rowout, int* status, cudaStream_t s) {
-  return with_geo(g, [&](auto gg) {
+  return with_geo_for<T>(g, [&](auto gg) {
     k_row<T, decltype(gg)><<<grid, NTHREADS, smem, s>>>(gg, p, Tpad, S, Ns, x_lo, x_hi, envs, logs, O, site_off, Np,
                                                         tt, rowout, status);
     return cudaGetLastError();
@@ -709,7 +726,7 @@ cudaError_t launch_row(const Geo& g, const Plan& p, int grid, size_t smem, const
 template <typename T>
 cudaError_t launch_pair(const Geo& g, const Plan& p, int grid, size_t smem, const T* Tpad, const uint8_t* S, int Ns,
                         const T* envs, const double* logs, const TermTab& tt, double* pairout, int* status, cudaStream_t s) {
-  return with_geo(g, [&](auto gg) {
+  return with_geo_for<T>(g, [&](auto gg) {
     k_pair<T, decltype(gg)><<<grid, NTHREADS, smem, s>>>(gg, p, Tpad, S, Ns, envs, logs, tt, pairout, status);
     return cudaGetLastError();
   });
@@ -737,7 +754,7 @@ template <typename T>
 cudaError_t launch_sample(const Geo& g, const Plan& p, int grid, size_t smem, const T* Tpad, uint8_t* S, int Ns,
                           int move, int nsweeps, unsigned long long seed, unsigned long long sweep0, T* envs,
                           double* logs, long long* accepted, int* status, cudaStream_t s) {
-  return with_geo(g, [&](auto gg) {
+  return with_geo_for<T>(g, [&](auto gg) {
     k_sample<T, decltype(gg)><<<grid, NTHREADS, smem, s>>>(gg, p, Tpad, S, Ns, move, nsweeps, seed, sweep0, envs, logs,
                                                            accepted, status);
     return cudaGetLastError();

@@ -19,6 +19,62 @@ __global__ void k_center(const TO* __restrict__ O, const double* __restrict__ w,
   }
 }
 
+// ---- complex PEPS: the MinSR of complex O runs as the real MinSR of its embedding.
+// With Obar complex (Ns x Np), W = [[Re Obar, -Im Obar], [Im Obar, Re Obar]] (2Ns x 2Np) has
+// W W^T = [[Re T, -Im T], [Im T, Re T]], the real form of T = Obar Obar^H, and
+// W^T [Re x; Im x] = [Re(Obar^H x); Im(Obar^H x)]: the real pipeline on (W, [Re ebar; Im ebar])
+// returns [Re dtheta; Im dtheta].  O: Ns x Np (re, im) pairs of TO.
+template <typename TO>
+__global__ void k_center_cplx(const TO* __restrict__ O, const double* __restrict__ w, int Ns, long long Np,
+                              double wsum, double* W) {
+  const long long Np2 = 2 * Np;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < Np; k += (long long)gridDim.x * blockDim.x) {
+    double mr = 0.0, mi = 0.0;
+    for (int s = 0; s < Ns; ++s) {
+      const double ws = w ? w[s] / wsum : 1.0 / Ns;
+      mr += ws * (double)O[2 * ((size_t)s * Np + k)];
+      mi += ws * (double)O[2 * ((size_t)s * Np + k) + 1];
+    }
+    for (int s = 0; s < Ns; ++s) {
+      const double sw = sqrt(w ? w[s] / wsum : 1.0 / Ns);
+      const double re = sw * ((double)O[2 * ((size_t)s * Np + k)] - mr);
+      const double im = sw * ((double)O[2 * ((size_t)s * Np + k) + 1] - mi);
+      W[(size_t)s * Np2 + k] = re;
+      W[(size_t)s * Np2 + Np + k] = -im;
+      W[(size_t)(Ns + s) * Np2 + k] = im;
+      W[(size_t)(Ns + s) * Np2 + Np + k] = re;
+    }
+  }
+}
+
+// [Re ebar; Im ebar] with ebar = sqrt(w) (E_loc - w^T E_loc) (complex E_loc)
+__global__ void k_center_e_cplx(const double* eloc, const double* w, int Ns, double* ebar2) {
+  __shared__ double red[33];
+  double ws = 0.0, mr = 0.0, mi = 0.0;
+  for (int i = threadIdx.x; i < Ns; i += blockDim.x) {
+    const double wi = w ? w[i] : 1.0;
+    ws += wi;
+    mr += wi * eloc[2 * i];
+    mi += wi * eloc[2 * i + 1];
+  }
+  ws = block_sum(ws, red);
+  mr = block_sum(mr, red) / ws;
+  mi = block_sum(mi, red) / ws;
+  for (int i = threadIdx.x; i < Ns; i += blockDim.x) {
+    const double sw = sqrt((w ? w[i] : 1.0) / ws);
+    ebar2[i] = sw * (eloc[2 * i] - mr);
+    ebar2[Ns + i] = sw * (eloc[2 * i + 1] - mi);
+  }
+}
+
+// dtheta (Np (re, im) pairs) from the embedding's [Re; Im] (2Np)
+__global__ void k_unembed(const double* d2, long long Np, double* dtheta) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < Np; k += (long long)gridDim.x * blockDim.x) {
+    dtheta[2 * k] = d2[k];
+    dtheta[2 * k + 1] = d2[Np + k];
+  }
+}
+
 __global__ void k_wsum(const double* w, int Ns, double* out) {
   __shared__ double red[33];
   double s = 0.0;
@@ -253,6 +309,34 @@ cudaError_t launch_center(const TO* O, const double* w, int Ns, long long Np, do
 }
 template cudaError_t launch_center<double>(const double*, const double*, int, long long, double*, double*, cudaStream_t);
 template cudaError_t launch_center<float>(const float*, const double*, int, long long, double*, double*, cudaStream_t);
+
+template <typename TO>
+cudaError_t launch_center_cplx(const TO* O, const double* w, int Ns, long long Np, double* W, cudaStream_t s) {
+  double wsum = 1.0;
+  if (w) {
+    double* d = W;  // borrow the first element for the weight sum
+    k_wsum<<<1, 256, 0, s>>>(w, Ns, d);
+    cudaError_t e = cudaMemcpyAsync(&wsum, d, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+  }
+  const long long blocks = (Np + 255) / 256;
+  k_center_cplx<TO><<<(int)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(O, w, Ns, Np, wsum, W);
+  return cudaGetLastError();
+}
+template cudaError_t launch_center_cplx<double>(const double*, const double*, int, long long, double*, cudaStream_t);
+template cudaError_t launch_center_cplx<float>(const float*, const double*, int, long long, double*, cudaStream_t);
+
+cudaError_t launch_center_e_cplx(const double* eloc, const double* w, int Ns, double* ebar2, cudaStream_t s) {
+  k_center_e_cplx<<<1, 1024, 0, s>>>(eloc, w, Ns, ebar2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unembed(const double* d2, long long Np, double* dtheta, cudaStream_t s) {
+  const long long b = (Np + 255) / 256;
+  k_unembed<<<(int)(b < 4096 ? (b > 0 ? b : 1) : 4096), 256, 0, s>>>(d2, Np, dtheta);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_center_e(const double* eloc, const double* w, int Ns, double* ebar, cudaStream_t s) {
   k_center_e<<<1, 1024, 0, s>>>(eloc, w, Ns, ebar);

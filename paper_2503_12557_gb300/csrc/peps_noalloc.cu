@@ -132,6 +132,7 @@ extern "C" peps_status peps_amplitudes_noalloc(const peps_config* cfg, const dou
       c.chi > 64)
     return PEPS_E_SHAPE;
   if (c.prec != PEPS_PREC_FP64 && c.prec != PEPS_PREC_FP32) return PEPS_E_ARG;
+  if (c.cplx) return PEPS_E_UNSUPPORTED;  // real PEPS only
   if (Ns == 0) return PEPS_OK;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PEPS_E_CUDA;

@@ -29,6 +29,89 @@
 
 namespace peps {
 
+// ------------------------------------------------------------------------------------------
+// Scalars.  Every kernel is instantiated for float, double (real PEPS) and cplx<float>,
+// cplx<double> (complex PEPS).  The contractions need only +, * and multiply-add; the
+// truncation needs conjugates and moduli, provided by the overloads below (identities for
+// real types).
+template <typename R>
+struct cplx {
+  R re, im;
+  cplx() = default;
+  __host__ __device__ constexpr cplx(R r, R i) : re(r), im(i) {}
+  __host__ __device__ constexpr cplx(R r) : re(r), im(R(0)) {}
+  __host__ __device__ constexpr cplx(int r) : re(R(r)), im(R(0)) {}
+  __host__ __device__ cplx& operator+=(const cplx& o) { re += o.re; im += o.im; return *this; }
+  __host__ __device__ cplx& operator-=(const cplx& o) { re -= o.re; im -= o.im; return *this; }
+  __host__ __device__ cplx& operator*=(R f) { re *= f; im *= f; return *this; }
+  __host__ __device__ cplx& operator*=(const cplx& o) {
+    const R r = re * o.re - im * o.im;
+    im = re * o.im + im * o.re;
+    re = r;
+    return *this;
+  }
+};
+template <typename R> __host__ __device__ inline cplx<R> operator+(cplx<R> a, const cplx<R>& b) { return a += b; }
+template <typename R> __host__ __device__ inline cplx<R> operator-(cplx<R> a, const cplx<R>& b) { return a -= b; }
+template <typename R> __host__ __device__ inline cplx<R> operator-(const cplx<R>& a) { return cplx<R>(-a.re, -a.im); }
+template <typename R> __host__ __device__ inline cplx<R> operator*(cplx<R> a, const cplx<R>& b) { return a *= b; }
+template <typename R> __host__ __device__ inline cplx<R> operator*(cplx<R> a, R f) { return a *= f; }
+template <typename R> __host__ __device__ inline cplx<R> operator*(R f, cplx<R> a) { return a *= f; }
+template <typename R> __host__ __device__ inline cplx<R> operator/(const cplx<R>& a, R f) { return cplx<R>(a.re / f, a.im / f); }
+template <typename R> __host__ __device__ inline bool operator==(const cplx<R>& a, const cplx<R>& b) { return a.re == b.re && a.im == b.im; }
+template <typename R> __host__ __device__ inline bool operator!=(const cplx<R>& a, const cplx<R>& b) { return !(a == b); }
+
+template <typename T> struct Scal { using R = T; static constexpr bool complex = false; };
+template <typename Q> struct Scal<cplx<Q>> { using R = Q; static constexpr bool complex = true; };
+
+__device__ __forceinline__ float conj_(float x) { return x; }
+__device__ __forceinline__ double conj_(double x) { return x; }
+template <typename R> __device__ __forceinline__ cplx<R> conj_(const cplx<R>& z) { return cplx<R>(z.re, -z.im); }
+__device__ __forceinline__ float abs2_(float x) { return x * x; }
+__device__ __forceinline__ double abs2_(double x) { return x * x; }
+template <typename R> __device__ __forceinline__ R abs2_(const cplx<R>& z) { return z.re * z.re + z.im * z.im; }
+__device__ __forceinline__ float abs_(float x) { return fabsf(x); }
+__device__ __forceinline__ double abs_(double x) { return fabs(x); }
+template <typename R> __device__ __forceinline__ R abs_(const cplx<R>& z) { return hypot(z.re, z.im); }
+// acc + a b
+__device__ __forceinline__ float mad(float acc, float a, float b) { return fmaf(a, b, acc); }
+__device__ __forceinline__ double mad(double acc, double a, double b) { return fma(a, b, acc); }
+template <typename R>
+__device__ __forceinline__ cplx<R> mad(const cplx<R>& acc, const cplx<R>& a, const cplx<R>& b) {
+  return cplx<R>(fma(a.re, b.re, fma(-a.im, b.im, acc.re)), fma(a.re, b.im, fma(a.im, b.re, acc.im)));
+}
+// value as (re, im) in double
+struct dz { double re, im; };
+__device__ __forceinline__ dz to_dz(float x) { return dz{(double)x, 0.0}; }
+__device__ __forceinline__ dz to_dz(double x) { return dz{x, 0.0}; }
+template <typename R> __device__ __forceinline__ dz to_dz(const cplx<R>& z) { return dz{(double)z.re, (double)z.im}; }
+__device__ __forceinline__ double dz_abs(dz a) { return hypot(a.re, a.im); }
+__device__ __forceinline__ dz dz_mul(dz a, dz b) { return dz{a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+// a / b (b != 0)
+__device__ __forceinline__ dz dz_div(dz a, dz b) {
+  const double n = b.re * b.re + b.im * b.im;
+  return dz{(a.re * b.re + a.im * b.im) / n, (a.im * b.re - a.re * b.im) / n};
+}
+// a scalar of type T from a double pair (the imaginary part dropped for real T)
+template <typename T> __device__ __forceinline__ T from_dz(dz a) { return (T)a.re; }
+template <> __device__ __forceinline__ cplx<float> from_dz<cplx<float>>(dz a) { return cplx<float>((float)a.re, (float)a.im); }
+template <> __device__ __forceinline__ cplx<double> from_dz<cplx<double>>(dz a) { return cplx<double>(a.re, a.im); }
+__device__ __forceinline__ float re_(float x) { return x; }
+__device__ __forceinline__ double re_(double x) { return x; }
+template <typename R> __device__ __forceinline__ R re_(const cplx<R>& z) { return z.re; }
+// 1 / z
+__device__ __forceinline__ float inv_(float x) { return 1.f / x; }
+__device__ __forceinline__ double inv_(double x) { return 1.0 / x; }
+template <typename R> __device__ __forceinline__ cplx<R> inv_(const cplx<R>& z) {
+  const R n = z.re * z.re + z.im * z.im;
+  return cplx<R>(z.re / n, -z.im / n);
+}
+// warp shuffles of any scalar
+template <typename T> __device__ __forceinline__ T shfl_xor_(unsigned mask, T v, int m) { return __shfl_xor_sync(mask, v, m); }
+template <typename R> __device__ __forceinline__ cplx<R> shfl_xor_(unsigned mask, cplx<R> v, int m) {
+  return cplx<R>(__shfl_xor_sync(mask, v.re, m), __shfl_xor_sync(mask, v.im, m));
+}
+
 enum : int {
   ST_NEAR_DEGENERATE = 1,
   ST_ZERO_NORM = 2,
@@ -92,6 +175,10 @@ __device__ __forceinline__ T warp_sum(T v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+template <typename R>
+__device__ __forceinline__ cplx<R> warp_sum(cplx<R> v) {
+  return cplx<R>(warp_sum(v.re), warp_sum(v.im));
+}
 template <typename T>
 __device__ __forceinline__ T warp_max(T v) {
 #pragma unroll
@@ -131,6 +218,13 @@ __device__ T block_max(T v, double* red) {
   return (T)red[32];
 }
 
+template <typename R>
+__device__ cplx<R> block_sum(cplx<R> v, double* red) {
+  const R re = block_sum(v.re, red);
+  const R im = block_sum(v.im, red);
+  return cplx<R>(re, im);
+}
+
 template <typename T>
 __device__ void blk_copy(T* dst, const T* src, int n) {
   for (int o = threadIdx.x; o < n; o += blockDim.x) dst[o] = src[o];
@@ -149,20 +243,21 @@ __device__ void blk_unit(T* dst, int n) {
 // set in *st when the maximum is 0 or not finite).  Ends with a barrier.
 template <typename T>
 __device__ double blk_normalize(T* v, int n, double* red, int* st) {
-  T m = 0;
-  for (int o = threadIdx.x; o < n; o += blockDim.x) m = fmax(m, fabs(v[o]));
+  using R = typename Scal<T>::R;
+  R m = 0;
+  for (int o = threadIdx.x; o < n; o += blockDim.x) m = fmax(m, abs_(v[o]));
   m = block_max(m, red);
   if (!(m < INFINITY)) {  // NaN or Inf
     if (threadIdx.x == 0) *st |= ST_NONFINITE;
     __syncthreads();
     return -INFINITY;
   }
-  if (m == T(0)) {
+  if (m == R(0)) {
     if (threadIdx.x == 0) *st |= ST_ZERO_NORM;
     __syncthreads();
     return -INFINITY;
   }
-  const T inv = T(1) / m;
+  const R inv = R(1) / m;
   for (int o = threadIdx.x; o < n; o += blockDim.x) v[o] *= inv;
   __syncthreads();
   return log((double)m);
@@ -192,11 +287,12 @@ __device__ void load_A(T* As, const T* Tpad, const G& g, int site, int s, bool s
 // xLARFG (H = I - tau v v^T, v_0 = 1).
 template <typename T>
 __device__ __forceinline__ void qr_apply_reflector(const T* zj, int j, T tau, T* zc, int m, int lane) {
-  // zc <- (I - tau v v^T) zc with v = (1, zj[j+1..m))
+  // zc <- (I - conj(tau) v v^H) zc with v = (1, zj[j+1..m))  (H^H of H = I - tau v v^H; real:
+  // I - tau v v^T)
   T s = 0;
-  for (int i = j + 1 + lane; i < m; i += 32) s += zj[i] * zc[i];
+  for (int i = j + 1 + lane; i < m; i += 32) s = mad(s, conj_(zj[i]), zc[i]);
   s = warp_sum(s);
-  const T w = (s + zc[j]) * tau;
+  const T w = (s + zc[j]) * conj_(tau);
   __syncwarp();
   if (lane == 0) zc[j] -= w;
   for (int i = j + 1 + lane; i < m; i += 32) zc[i] -= zj[i] * w;
@@ -217,16 +313,19 @@ __device__ void qr_keep_r_smem(T* Z, int m, int nc, T* R, T* taus) {
       for (int jj = 0; jj < pb; ++jj) {
         const int j = j0 + jj;
         T* zj = Z + (size_t)j * m;
-        T part = 0;
-        for (int i = j + 1 + lane; i < m; i += 32) part += zj[i] * zj[i];
-        const T sigma = warp_sum(part);
+        typename Scal<T>::R part = 0;
+        for (int i = j + 1 + lane; i < m; i += 32) part += abs2_(zj[i]);
+        const typename Scal<T>::R sigma = warp_sum(part);
         const T alpha = zj[j];
         T tau = 0, beta = alpha;
-        if (sigma != T(0)) {
-          const T nrm = sqrt(alpha * alpha + sigma);
-          beta = (alpha >= T(0)) ? -nrm : nrm;
-          tau = (beta - alpha) / beta;
-          const T sc = T(1) / (alpha - beta);
+        if (sigma != 0) {
+          // LAPACK's xLARFG: beta = -sign(Re alpha) sqrt(|alpha|^2 + sigma) (real),
+          // tau = (beta - alpha) / beta, v = x / (alpha - beta)
+          const typename Scal<T>::R nrm = sqrt(abs2_(alpha) + sigma);
+          const typename Scal<T>::R bt = (re_(alpha) >= 0) ? -nrm : nrm;
+          beta = T(bt);
+          tau = (beta - alpha) * (typename Scal<T>::R(1) / bt);
+          const T sc = inv_(alpha - beta);
           for (int i = j + 1 + lane; i < m; i += 32) zj[i] *= sc;
         }
         __syncwarp();
@@ -444,7 +543,9 @@ __device__ __noinline__ void qr_keep_r_reg(T* Z, int m, int nc, T* R, T* taus) {
 // Dispatch on the row count; MC > 0: m is the compile-time MC.
 template <typename T, int MC = 0>
 __device__ void qr_keep_r(T* Z, int m, int nc, T* R, T* taus) {
-  if constexpr (MC > 0) {
+  if constexpr (Scal<T>::complex) {
+    qr_keep_r_smem(Z, m, nc, R, taus);
+  } else if constexpr (MC > 0) {
     constexpr int RPL = (MC + 31) / 32;
     if constexpr (RPL <= 24) qr_keep_r_reg<T, RPL>(Z, MC, nc, R, taus);
     else qr_keep_r_smem(Z, m, nc, R, taus);
@@ -470,11 +571,11 @@ template <> struct JacobiTol<float> { static constexpr float eps = 5.9604645e-8f
 // sweeps never rotate them against the others, so they are not orthogonal to the kept
 // directions and must not enter the kept basis.  Set them to exactly zero.  Ends with a barrier.
 template <typename T>
-__device__ void zero_tiny_rows(T* X, int m, int L, int ldx, T tiny) {
+__device__ void zero_tiny_rows(T* X, int m, int L, int ldx, typename Scal<T>::R tiny) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int p = warp; p < m; p += nw) {
-    T s = 0;
-    for (int i = lane; i < L; i += 32) s += X[(size_t)p * ldx + i] * X[(size_t)p * ldx + i];
+    typename Scal<T>::R s = 0;
+    for (int i = lane; i < L; i += 32) s += abs2_(X[(size_t)p * ldx + i]);
     s = warp_sum(s);
     if (s <= tiny)
       for (int i = lane; i < L; i += 32) X[(size_t)p * ldx + i] = T(0);
@@ -494,28 +595,30 @@ __device__ void zero_tiny_rows(T* X, int m, int L, int ldx, T tiny) {
 //   that a pair check costs one dot product.
 // Returns the number of sweeps, or -1 when the sweep limit was hit.
 template <typename T>
-__device__ int hestenes_rows_smem(T* X, int m, int L, int ldx, int* flag, unsigned long long* ctr, double* red, T* nrm) {
+__device__ int hestenes_rows_smem(T* X, int m, int L, int ldx, int* flag, unsigned long long* ctr, double* red,
+                                  typename Scal<T>::R* nrm) {
+  using R = typename Scal<T>::R;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int grp = lane >> 3, sub = lane & 7, ngroups = nw * 4;
   const unsigned gmask = 0xffu << (grp * 8);
-  const T eps = JacobiTol<T>::eps;
-  const T tol = T(L) * eps;
-  T tiny = 0;
+  const R eps = JacobiTol<R>::eps;
+  const R tol = R(L) * eps;
+  R tiny = 0;
   unsigned long long nrot = 0;
-  for (int sweep = 0; sweep < JacobiTol<T>::sweeps; ++sweep) {
+  for (int sweep = 0; sweep < JacobiTol<R>::sweeps; ++sweep) {
     for (int p = warp; p < m; p += nw) {
-      T s = 0;
-      for (int i = lane; i < L; i += 32) s += X[(size_t)p * ldx + i] * X[(size_t)p * ldx + i];
+      R s = 0;
+      for (int i = lane; i < L; i += 32) s += abs2_(X[(size_t)p * ldx + i]);
       s = warp_sum(s);
       if (lane == 0) nrm[p] = s;
     }
     if (threadIdx.x == 0) *flag = 0;
     __syncthreads();
     if (sweep == 0) {
-      T nmax = 0;
+      R nmax = 0;
       for (int p = threadIdx.x; p < m; p += blockDim.x) nmax = fmax(nmax, nrm[p]);
       nmax = block_max(nmax, red);
-      tiny = nmax * (T(L) * eps) * (T(L) * eps);
+      tiny = nmax * (R(L) * eps) * (R(L) * eps);
     }
     int rotated = 0;
     for (int r = 0; r < m - 1; ++r) {
@@ -523,29 +626,32 @@ __device__ int hestenes_rows_smem(T* X, int m, int L, int ldx, int* flag, unsign
         const int p = rr_player(pi, r, m), q = rr_player(m - 1 - pi, r, m);
         T* xp = X + (size_t)p * ldx;
         T* xq = X + (size_t)q * ldx;
-        const T a = nrm[p], b = nrm[q];
+        const R a = nrm[p], b = nrm[q];
         T c = 0;
-        for (int i = sub; i < L; i += 8) c += xp[i] * xq[i];
-        c += __shfl_xor_sync(gmask, c, 4);
-        c += __shfl_xor_sync(gmask, c, 2);
-        c += __shfl_xor_sync(gmask, c, 1);
-        if (c != T(0) && a > tiny && b > tiny && fabs(c) > tol * sqrt(a * b)) {
-          // zeta = (b - a) / (2c); t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)) is the smaller
-          // root of t^2 + 2 zeta t - 1 = 0, which makes the rotated rows orthogonal.
-          const T zeta = (b - a) / (T(2) * c);
-          T t;
-          if (fabs(zeta) > T(1e15)) t = T(0.5) / zeta;
-          else t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
-          const T cs = T(1) / sqrt(T(1) + t * t), sn = cs * t;
+        for (int i = sub; i < L; i += 8) c = mad(c, xp[i], conj_(xq[i]));
+        c += shfl_xor_(gmask, c, 4);
+        c += shfl_xor_(gmask, c, 2);
+        c += shfl_xor_(gmask, c, 1);
+        const R ac = abs_(c);
+        if (ac != R(0) && a > tiny && b > tiny && ac > tol * sqrt(a * b)) {
+          // with c = |c| e^{i phi}: rotate (x_p, e^{i phi} x_q), whose product is |c|;
+          // zeta = (b - a) / (2|c|); t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)) is the smaller
+          // root of t^2 + 2 zeta t - 1 = 0, which makes the rotated rows orthogonal
+          const R zeta = (b - a) / (R(2) * ac);
+          R t;
+          if (fabs(zeta) > R(1e15)) t = R(0.5) / zeta;
+          else t = copysign(R(1), zeta) / (fabs(zeta) + sqrt(R(1) + zeta * zeta));
+          const R cs = R(1) / sqrt(R(1) + t * t), sn = cs * t;
+          const T ph = c * (R(1) / ac);
           for (int i = sub; i < L; i += 8) {
-            const T u = xp[i], v = xq[i];
+            const T u = xp[i], v = ph * xq[i];
             xp[i] = cs * u - sn * v;
             xq[i] = sn * u + cs * v;
           }
           __syncwarp(gmask);
           if (sub == 0) {
-            nrm[p] = fmax(T(0), a - t * c);
-            nrm[q] = b + t * c;
+            nrm[p] = fmax(R(0), a - t * ac);
+            nrm[q] = b + t * ac;
             ++nrot;
           }
           rotated = 1;
@@ -566,7 +672,7 @@ __device__ int hestenes_rows_smem(T* X, int m, int L, int ldx, int* flag, unsign
   }
   zero_tiny_rows(X, m, L, ldx, tiny);
   if (ctr && nrot) atomicAdd(ctr + 1, nrot);
-  if (ctr && threadIdx.x == 0) { atomicAdd(ctr + 0, (unsigned long long)JacobiTol<T>::sweeps); atomicAdd(ctr + 2, 1ull); }
+  if (ctr && threadIdx.x == 0) { atomicAdd(ctr + 0, (unsigned long long)JacobiTol<R>::sweeps); atomicAdd(ctr + 2, 1ull); }
   return -1;
 }
 
@@ -758,15 +864,19 @@ __device__ __noinline__ int hestenes_rows_grp(T* X, int m, int L, int ldx, int* 
 // stride ldx = 8 mod 32, so that the four groups' rows fall in different banks), else the
 // shared-memory form.  Same contract as hestenes_rows_smem.  LC > 0: the row length is the compile-time LC.
 template <typename T, int LC = 0>
-__device__ int hestenes_rows(T* X, int m, int L, int ldx, int* flag, unsigned long long* ctr, double* red, T* nrm) {
-  if constexpr (LC > 0) {
+__device__ int hestenes_rows(T* X, int m, int L, int ldx, int* flag, unsigned long long* ctr, double* red,
+                             typename Scal<T>::R* nrm) {
+  if constexpr (Scal<T>::complex) {
+    return hestenes_rows_smem(X, m, L, ldx, flag, ctr, red, nrm);
+  } else if constexpr (LC > 0) {
     constexpr int E8 = (LC + 7) / 8;
     if constexpr (E8 <= 16) return hestenes_rows_grp<T, E8>(X, m, LC, ldx, flag, ctr, red, nrm);
     else return hestenes_rows_smem(X, m, LC, ldx, flag, ctr, red, nrm);
+  } else {
+    if (L <= 64) return hestenes_rows_grp<T, 8>(X, m, L, ldx, flag, ctr, red, nrm);
+    if (L <= 128) return hestenes_rows_grp<T, 16>(X, m, L, ldx, flag, ctr, red, nrm);
+    return hestenes_rows_smem(X, m, L, ldx, flag, ctr, red, nrm);
   }
-  if (L <= 64) return hestenes_rows_grp<T, 8>(X, m, L, ldx, flag, ctr, red, nrm);
-  if (L <= 128) return hestenes_rows_grp<T, 16>(X, m, L, ldx, flag, ctr, red, nrm);
-  return hestenes_rows_smem(X, m, L, ldx, flag, ctr, red, nrm);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -917,16 +1027,20 @@ __device__ double env_row_step(const G& g, const T* Eprev, T* Eout, const T* Tpa
       X[(size_t)i * LX + q] = s;
     }
     __syncthreads();
-    const int sweeps = hestenes_rows<T, GeoLr<G>::value>(X, mX, Lr, LX, flag, w.ctr, w.red, w.sig);
+    // norms, singular values and the selection in the real type (the QR's taus, in the same
+    // buffer, are no longer needed)
+    using RT = typename Scal<T>::R;
+    RT* sig = reinterpret_cast<RT*>(w.sig);
+    const int sweeps = hestenes_rows<T, GeoLr<G>::value>(X, mX, Lr, LX, flag, w.ctr, w.red, sig);
     if (sweeps < 0 && tid == 0) *st |= ST_NOCONV;
     // singular values = row norms
     {
       const int lane = tid & 31, warp = tid >> 5, nw = NT >> 5;
       for (int p = warp; p < mX; p += nw) {
-        T s = 0;
-        for (int i = lane; i < Lr; i += 32) s += X[(size_t)p * LX + i] * X[(size_t)p * LX + i];
+        RT s = 0;
+        for (int i = lane; i < Lr; i += 32) s += abs2_(X[(size_t)p * LX + i]);
         s = warp_sum(s);
-        if (lane == 0) w.sig[p] = sqrt(s);
+        if (lane == 0) sig[p] = sqrt(s);
       }
     }
     __syncthreads();
@@ -934,62 +1048,62 @@ __device__ double env_row_step(const G& g, const T* Eprev, T* Eout, const T* Tpa
     // input) ranks below every number, so that the ranks stay a permutation and every kept
     // index is valid; the sample is flagged.
     for (int p = tid; p < mX; p += NT) {
-      const T sp = w.sig[p];
-      const T kp = (sp == sp) ? sp : T(-1);
+      const RT sp = sig[p];
+      const RT kp = (sp == sp) ? sp : RT(-1);
       if (!(sp == sp) || isinf(sp)) atomicOr(st, (int)ST_NONFINITE);
       int rk = 0;
       for (int q = 0; q < mX; ++q) {
-        const T sq = w.sig[q];
-        const T kq = (sq == sq) ? sq : T(-1);
+        const RT sq = sig[q];
+        const RT kq = (sq == sq) ? sq : RT(-1);
         rk += (kq > kp) || (kq == kp && q < p);
       }
       w.sel[mX + p] = rk;          // rank of row p
       if (rk < chi) w.sel[rk] = p; // row holding rank rk
-      if (rk == chi - 1) w.sig[mX + 0] = sp;  // sigma_(chi-1)
-      if (rk == chi) w.sig[mX + 1] = sp;      // sigma_(chi)
-      if (rk == 0) w.sig[mX + 2] = sp;        // sigma_(0)
+      if (rk == chi - 1) sig[mX + 0] = sp;  // sigma_(chi-1)
+      if (rk == chi) sig[mX + 1] = sp;      // sigma_(chi)
+      if (rk == 0) sig[mX + 2] = sp;        // sigma_(0)
     }
-    if (tid == 0 && mX <= chi) { w.sig[mX + 1] = 0; }
+    if (tid == 0 && mX <= chi) { sig[mX + 1] = 0; }
     __syncthreads();
     if (mX > chi) {
       // discarded weight and near-degenerate cut (same rule as the oracle)
-      T tot = 0, dis = 0;
+      RT tot = 0, dis = 0;
       for (int p = tid; p < mX; p += NT) {
-        const T s2 = w.sig[p] * w.sig[p];
+        const RT s2 = sig[p] * sig[p];
         tot += s2;
         if (w.sel[mX + p] >= chi) dis += s2;
       }
       tot = block_sum(tot, w.red);
       dis = block_sum(dis, w.red);
       if (tid == 0) {
-        const T s0 = w.sig[mX + 2], sk = w.sig[mX + 0], sd = w.sig[mX + 1];
-        if (s0 > T(0) && (sk - sd) < T(1e-8) * s0 && sd > T(1e-12) * s0) *st |= ST_NEAR_DEGENERATE;
-        if (tot > T(0)) {
+        const RT s0 = sig[mX + 2], sk = sig[mX + 0], sd = sig[mX + 1];
+        if (s0 > RT(0) && (sk - sd) < RT(1e-8) * s0 && sd > RT(1e-12) * s0) *st |= ST_NEAR_DEGENERATE;
+        if (tot > RT(0)) {
           const float wd = (float)(dis / tot);
           if (wd > *wdisc) *wdisc = wd;
         }
       }
     }
-    // Vt[c'][q] = X[sel(c')][q] / sigma
+    // Vt[c'][q] = X[sel(c')][q] / sigma  (the rows of V^H)
     const int nkeep = (mX < chi) ? mX : chi;
     for (int o = tid; o < chi * Lr; o += NT) {
       const int q = o % Lr, cp = o / Lr;
       T v = 0;
       if (cp < nkeep) {
         const int p = w.sel[cp];
-        const T s = w.sig[p];
-        if (s > T(0)) v = X[(size_t)p * LX + q] / s;
+        const RT s = sig[p];
+        if (s > RT(0)) v = X[(size_t)p * LX + q] * (RT(1) / s);
       }
       Vt[(size_t)cp * LY + q] = v;
     }
     __syncthreads();
-    // C_{k-1}[j][c'] = sum_q Y[j][q] Vt[c'][q];  new site B[c'][d][c] = Vt[c'][(d,c)]
+    // C_{k-1} = Y V: C[j][c'] = sum_q Y[j][q] conj(Vt[c'][q]);  new site B[c'][d][c] = Vt[c'][(d,c)]
     for (int o = tid; o < n * chi; o += NT) {
       const int cp = o % chi, j = o / chi;
       const T* Yr = Y + (size_t)j * LY;
       const T* Vr = Vt + (size_t)cp * LY;
       T s = 0;
-      for (int q = 0; q < Lr; ++q) s += Yr[q] * Vr[q];
+      for (int q = 0; q < Lr; ++q) s = mad(s, Yr[q], conj_(Vr[q]));
       Cn[o] = s;
     }
     for (int o = tid; o < g.se; o += NT) Bs[o] = Vt[(size_t)(o / Lr) * LY + o % Lr];  // [c'][d][c]
@@ -1075,7 +1189,7 @@ __device__ __forceinline__ void blk_gemm(const T* __restrict__ A, const T* __res
 #pragma unroll
         for (int i = 0; i < RM; ++i)
 #pragma unroll
-          for (int j = 0; j < RN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+          for (int j = 0; j < RN; ++j) acc[i][j] = mad(acc[i][j], a[i], b[j]);
       }
     }
 #pragma unroll

@@ -25,7 +25,8 @@ _ERRORS = {-1: "PEPS_E_ARG", -2: "PEPS_E_SHAPE", -3: "PEPS_E_WORKSPACE", -4: "PE
 
 class _Config(C.Structure):
     _fields_ = [("Lx", C.c_int), ("Ly", C.c_int), ("d", C.c_int), ("D", C.c_int), ("chi", C.c_int),
-                ("prec", C.c_int), ("max_samples", C.c_int), ("gram", C.c_int), ("solve", C.c_int)]
+                ("prec", C.c_int), ("max_samples", C.c_int), ("gram", C.c_int), ("solve", C.c_int),
+                ("cplx", C.c_int)]
 
 
 class _Term(C.Structure):
@@ -186,14 +187,15 @@ class Hamiltonian:
 class PEPS:
     """One handle of the C library: a lattice, chi and a precision."""
 
-    def __init__(self, Lx, Ly, d, D, chi, prec=PREC_FP64, max_samples=4096, gram=0, solve=0):
+    def __init__(self, Lx, Ly, d, D, chi, prec=PREC_FP64, max_samples=4096, gram=0, solve=0, cplx=False):
         self.L = load()
         self.Lx, self.Ly, self.d, self.D, self.chi, self.prec = Lx, Ly, d, D, chi, prec
         self.max_samples = max_samples
         self.gram = gram
         self.last_warning = None
         self.solve = solve
-        cfg = _Config(Lx, Ly, d, D, chi, prec, max_samples, gram, solve)
+        self.cplx = bool(cplx)
+        cfg = _Config(Lx, Ly, d, D, chi, prec, max_samples, gram, solve, int(self.cplx))
         h = C.c_void_p()
         st = self.L.peps_create(C.byref(h), C.byref(cfg))
         if st != 0:
@@ -225,10 +227,17 @@ class PEPS:
 
     @property
     def odtype(self):
+        if self.cplx:
+            return torch.complex128 if self.prec == PREC_FP64 else torch.complex64
         return torch.float64 if self.prec == PREC_FP64 else torch.float32
 
+    @property
+    def tdtype(self):
+        """dtype of theta and dtheta."""
+        return torch.complex128 if self.cplx else torch.float64
+
     def set_params(self, theta: torch.Tensor):
-        assert theta.is_cuda and theta.dtype == torch.float64 and theta.numel() == self.Np
+        assert theta.is_cuda and theta.dtype == self.tdtype and theta.numel() == self.Np
         theta = theta.contiguous()
         self._check(self.L.peps_set_params(self.h, _ptr(theta), _stream()), "peps_set_params")
         self._theta_ref = theta
@@ -299,7 +308,7 @@ class PEPS:
     def minsr_step(self, O, eloc, w=None, lam=1e-4, rcond=0.0, tau=0.05):
         ns = O.shape[0]
         assert O.dtype == self.odtype and O.shape[1] == self.Np and eloc.shape == (ns, 2)
-        dth = torch.empty(self.Np, dtype=torch.float64, device=O.device)
+        dth = torch.empty(self.Np, dtype=self.tdtype, device=O.device)
         info = torch.zeros(4, dtype=torch.float64, device=O.device)
         self._check(self.L.minsr_step(self.h, _ptr(O.contiguous()), _ptr(eloc.contiguous()),
                                       _ptr(w.contiguous()) if w is not None else None, ns, float(lam), float(rcond),
@@ -308,7 +317,8 @@ class PEPS:
 
     def apply_update(self, theta: torch.Tensor, dtheta: torch.Tensor):
         """theta += dtheta on the device (in place) and refresh the handle's kernel copy."""
-        assert theta.is_cuda and theta.dtype == torch.float64 and theta.is_contiguous()
+        assert theta.is_cuda and theta.dtype == self.tdtype and theta.is_contiguous()
+        assert dtheta.dtype == self.tdtype
         self._check(self.L.peps_apply_update(self.h, _ptr(theta), _ptr(dtheta.contiguous()), _stream()),
                     "peps_apply_update")
         self._theta_ref = theta
