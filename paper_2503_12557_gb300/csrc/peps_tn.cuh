@@ -808,11 +808,14 @@ __device__ __noinline__ int hestenes_rows_grp(T* X, int m, int L, int ldx, int* 
           c = grp_sum8(c);
           T cs = 1, sn = 0, tc = 0;
           jac_params(np, nq, c, tol, tiny, cs, sn, tc);
+          // late sweeps rotate few pairs: skip the update when no group of the warp rotates
+          if (__any_sync(0xffffffffu, sn != T(0))) {
 #pragma unroll
-          for (int e = 0; e < E8; ++e) {
-            const T a = xp[e], b = xq[e];
-            xp[e] = cs * a - sn * b;
-            xq[e] = sn * a + cs * b;
+            for (int e = 0; e < E8; ++e) {
+              const T a = xp[e], b = xq[e];
+              xp[e] = cs * a - sn * b;
+              xq[e] = sn * a + cs * b;
+            }
           }
           np = fmax(T(0), np - tc);
           nq = nq + tc;
