@@ -40,7 +40,7 @@ def _args():
     ap.add_argument("--ns", type=int, default=None)
     ap.add_argument("--sweeps", type=int, default=2)
     ap.add_argument("--burnin", type=int, default=2)
-    ap.add_argument("--mode", default="step", choices=["step", "learned", "gram", "batch", "complex"])
+    ap.add_argument("--mode", default="step", choices=["step", "learned", "gram", "batch", "complex", "bound"])
     ap.add_argument("--branches", type=int, default=8)
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--cpu-samples", type=int, default=12)
@@ -534,6 +534,64 @@ def run_complex(a):
     print(json.dumps(out), flush=True)
 
 
+def run_bound(a):
+    """Variational-bound estimator on the bench workload (8x8 open Heisenberg, D=4, chi=16,
+    biased Gaussian tensors) with the cut in the middle (i = 4): N_s configurations after
+    a.burnin exchange sweeps from the Neel state; the fast estimator (ratios from the
+    neighbouring environments) and E_loc^bound on the same configurations, their times, the
+    rebuilt row steps per sample, and the elementwise difference <E_bound - E_loc>."""
+    import numpy as np
+    import torch
+    from paper_2503_12557_gb300 import build, inputs as I, peps as P
+    build.build()
+    w = I.WORKLOADS[WORKLOAD]
+    lat = I.Lattice(w["Lx"], w["Ly"], w["d"], w["D"])
+    ns = a.ns or 1216
+    cut = lat.Lx // 2
+    prec = P.PREC_FP32 if a.prec == "fp32" else P.PREC_FP64
+    H = I.heisenberg(lat)
+    h = P.PEPS(lat.Lx, lat.Ly, lat.d, lat.D, w["chi"], prec=prec, max_samples=ns)
+    h.set_params(torch.as_tensor(I.peps_random(lat, w["seed_theta"], **w["init"])).cuda())
+    S = torch.as_tensor(I.configs_neel(lat, ns)).cuda()
+    h.sample(S, P.MOVE_EXCHANGE, max(a.burnin, 4), seed=w["seed_chain"])
+    h.local_energy_bound(H, S[:8], cut)  # warm-up
+    torch.cuda.synchronize()
+    h.timing(True)
+    fast = h.evaluate(H, S, want_O=False)
+    b = h.local_energy_bound(H, S, cut)
+    torch.cuda.synchronize()
+    ms, la, _ = h.timing_read()
+    h.timing(False)
+    # rebuilt row steps per sample: every antiparallel bond rebuilds the rows between the
+    # first row it changes and the cut, on its side of the cut
+    Sh = S.cpu().numpy().astype(np.int64)
+    steps = np.zeros(ns)
+    for sites, _ in H["terms"]:
+        i, j = sites
+        anti = Sh[:, i] != Sh[:, j]
+        ri, rj = i // lat.Ly, j // lat.Ly
+        up = [r for r in (ri, rj) if r < cut]
+        lo = [r for r in (ri, rj) if r >= cut]
+        n = (cut - min(up) if up else 0) + (max(lo) - cut + 1 if lo else 0)
+        steps += anti * n
+    ef = fast["eloc"][:, 0].double().cpu().numpy()
+    eb = b["eloc"][:, 0].double().cpu().numpy()
+    diff = eb - ef
+    env_ms_per_rowstep = ms["env"] / 2 / (ns * 2 * (lat.Lx - 1))   # two env passes, Lx-1 rows per side
+    out = {"mode": "bound", "workload": f"8x8 open Heisenberg, D=4, chi=16, N_s={ns}, cut i={cut}",
+           "precision": a.prec, "bound_kernel_ms": ms["bound"], "bound_total_ms": ms["bound"] + ms["env"] / 2 + ms["combine"] / 2,
+           "fast_eval_ms": ms["env"] / 2 + ms["row"] + ms["pair"] + ms["combine"] / 2,
+           "bound_samples_per_s": ns / ((ms["bound"] + ms["env"] / 2) / 1e3),
+           "fast_samples_per_s": ns / ((ms["env"] / 2 + ms["row"] + ms["pair"]) / 1e3),
+           "rebuilt_row_steps_per_sample": float(steps.mean()),
+           "bound_ms_per_row_step": ms["bound"] / max(1.0, float(steps.sum())),
+           "env_ms_per_row_step": env_ms_per_rowstep,
+           "E_fast_per_site": float(ef.mean() / lat.nsites), "E_bound_per_site": float(eb.mean() / lat.nsites),
+           "mean_diff_bound_minus_fast": float(diff.mean()), "stderr_diff": float(diff.std() / np.sqrt(ns)),
+           "status_nonzero": int((b["status"] != 0).sum().item())}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     a = _args()
     if a.impl == "reference":
@@ -546,6 +604,8 @@ def main():
         run_batch(a)
     elif a.mode == "complex":
         run_complex(a)
+    elif a.mode == "bound":
+        run_bound(a)
     else:
         run_gpu(a)
 

@@ -90,6 +90,12 @@ typedef struct {
                      O is N_s x N_p complex numbers in the handle's precision ((re, im) pairs
                      of doubles or floats), phases and E_loc are complex.  Not with gram = 1,
                      the learned proposal or peps_amplitudes_noalloc (PEPS_E_UNSUPPORTED). */
+    double trunc_weight; /* 0: every truncation keeps min(chi, rank) singular values.  > 0: the
+                     truncated-weight rule of Sec. "On the boundary MPS method" (the paper uses
+                     1e-4): each cut keeps the fewest singular values, at most chi, whose
+                     discarded share of sum sigma^2 is at most trunc_weight (the bond stays
+                     padded to chi with zeros).  A cut whose boundary share lies within 1e-9
+                     (relative) of trunc_weight is flagged PEPS_ST_NEAR_DEGENERATE.  In [0, 1). */
 } peps_config;
 
 /* One local Hamiltonian term: h is a d^k x d^k complex matrix, row major, interleaved
@@ -152,6 +158,23 @@ peps_status peps_logderiv(peps_handle* h, const uint8_t* S_dev, int Ns, void* O_
 peps_status peps_evaluate(peps_handle* h, const peps_hamiltonian* H, const uint8_t* S_dev, int Ns,
                           double* logabs_dev, double* phase_dev, double* eloc_dev, void* O_dev,
                           int32_t* status_dev, void* stream);
+
+/* Variational-bound local energy (Sec. "On Variational Upper Bound to the Ground State Energy"
+ * and the appendix on variational upper bounds).  One cut i (1 <= cut <= Lx-1, the paper's
+ * row index: the upper boundary MPS holds rows 1..i) fixes every amplitude to
+ *   psi_i(S) = E^u[i](S) . E^l[i+1](S)
+ * (the plain overlap of the two boundary MPS, no conjugation), and
+ *   E_loc^bound(S) = sum_S' <S|H|S'> psi_i(S') / psi_i(S),
+ * whose |psi_i|^2-weighted mean is the energy <psi_i|H|psi_i> / <psi_i|psi_i> of one state,
+ * an upper bound of the ground-state energy.  For every off-diagonal S' the environments
+ * are rebuilt (truncated as in peps_amplitudes) on the rows between the first row S' changes
+ * and the cut, from S's environments; this costs up to Lx/2 row steps per off-diagonal term.
+ * eloc_dev: Ns x 2 doubles (re, im); logabs_dev, phase_dev: ln|psi_i(S)| and its phase (each
+ * may be NULL); status_dev: as peps_evaluate, also collecting the bits of every S' row step.
+ * Same term restrictions as peps_local_energy; PEPS_E_ARG for a cut outside 1 .. Lx-1. */
+peps_status peps_local_energy_bound(peps_handle* h, const peps_hamiltonian* H, const uint8_t* S_dev, int Ns,
+                                    int cut, double* eloc_dev, double* logabs_dev, double* phase_dev,
+                                    int32_t* status_dev, void* stream);
 
 /* MinSR step (Eq. (tdvp_fast)):
  *   w_S = w_dev[S] / sum w (uniform 1/Ns when w_dev is NULL);

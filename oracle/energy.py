@@ -117,9 +117,11 @@ def log_derivative(theta, S, lat: Lattice, chi: int, env_ap=None):
 
 
 def evaluate(theta, S_batch, lat: Lattice, chi: int, H=None, want_O=True):
-    """ln|psi_top|, phase, E_loc, O and status for a batch of configurations."""
+    """ln|psi_top|, phase, E_loc, O, status and the smallest cutoff-decision margin
+    (tn.cut_margin; inf at fixed chi) for a batch of configurations."""
     T = theta_to_tensors(lat, theta)
     ns = len(S_batch)
+    margin = np.full(ns, math.inf)
     la = np.zeros(ns)
     ph = np.zeros(ns)
     el = np.zeros(ns, dtype=np.complex128)
@@ -132,8 +134,9 @@ def evaluate(theta, S_batch, lat: Lattice, chi: int, H=None, want_O=True):
         env, Ap = env_ap
         la[i], ph[i] = tn.log_psi_row(env, Ap, lat.Lx - 1)
         st[i] = env.status
+        margin[i] = env.cut_margin
         if H is not None:
             el[i], _ = local_energy(theta, S, lat, chi, H, env_ap=env_ap)
         if want_O:
             O[i] = log_derivative(theta, S, lat, chi, env_ap=env_ap)
-    return dict(logabs=la, phase=ph, eloc=el, O=O, status=st)
+    return dict(logabs=la, phase=ph, eloc=el, O=O, status=st, cut_margin=margin)

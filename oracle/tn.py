@@ -44,6 +44,7 @@ class Env:
         self.logl = {}
         self.status = 0
         self.max_discarded = 0.0
+        self.cut_margin = math.inf
 
 
 def project(T, S, lat: Lattice):
@@ -114,9 +115,60 @@ def _cut_flags(s, keep):
     return 0
 
 
-def truncate_svd(mps, chi):
+def chi_cut(chi):
+    """chi as an int (fixed bond dimension) or a pair (chi_max, cutoff) for the truncated-weight
+    rule of Sec. "On the boundary MPS method" (the paper truncates at a discarded weight 1e-4)."""
+    if np.isscalar(chi):
+        return int(chi), 0.0
+    return int(chi[0]), float(chi[1])
+
+
+def keep_count(s, chi, cut):
+    """Number of singular values kept at one bond (s sorted descending): min(chi, len(s)), and
+    with cut > 0 at most the smallest k >= 1 whose relative discarded weight
+    sum_{i >= k} s_i^2 / sum_i s_i^2 is at most cut.  Also returns NEAR_DEGENERATE when that
+    weight comparison is within 1e-9 (relative) of the cutoff at the chosen boundary, where the
+    decision is not stable under rounding."""
+    keep = min(chi, len(s))
+    if cut <= 0.0:
+        return keep, 0
+    w = np.asarray(s, dtype=float) ** 2
+    tot = float(np.sum(w))
+    if tot <= 0.0:
+        return keep, 0
+    tail = np.concatenate([np.cumsum(w[::-1])[::-1], [0.0]]) / tot  # tail[k] = sum_{i>=k} w_i / tot
+    kcut = next(k for k in range(1, len(s) + 1) if tail[k] <= cut)
+    flag = 0
+    for k in (kcut - 1, kcut):
+        if 1 <= k <= len(s) and abs(tail[k] - cut) <= 1e-9 * cut:
+            flag = NEAR_DEGENERATE
+    if kcut >= keep:
+        return keep, 0
+    return kcut, flag
+
+
+def cut_margin(s, chi, cut):
+    """How far the cutoff decision of keep_count is from changing: the smallest relative
+    distance |tail[k] - cut| / cut over the comparisons k = 1 .. min(chi, kcut) (a superset of
+    those that decide the kept count; inf without a cutoff).  A computation whose tails carry a
+    relative rounding error below this margin keeps the same number of singular values."""
+    if cut <= 0.0:
+        return math.inf
+    w = np.asarray(s, dtype=float) ** 2
+    tot = float(np.sum(w))
+    if tot <= 0.0:
+        return math.inf
+    tail = np.concatenate([np.cumsum(w[::-1])[::-1], [0.0]]) / tot
+    kcut = next(k for k in range(1, len(s) + 1) if tail[k] <= cut)
+    last = min(chi, kcut, len(s))
+    return float(min(abs(tail[k] - cut) for k in range(1, last + 1)) / cut)
+
+
+def truncate_svd(mps, chi, stats=None):
     """Sequential SVD compression to bond dimension chi (QR left-canonicalisation, then
-    right-to-left SVDs).  Returns (mps, status, max discarded weight)."""
+    right-to-left SVDs); chi may be (chi_max, cutoff), see keep_count.  Returns (mps, status,
+    max discarded weight); a dict passed as stats receives the smallest cut_margin."""
+    chi, cut = chi_cut(chi)
     A = [e.copy() for e in mps]
     n = len(A)
     for k in range(n - 1):
@@ -128,8 +180,10 @@ def truncate_svd(mps, chi):
     for k in range(n - 1, 0, -1):
         a, p, b = A[k].shape
         U, s, Vh = np.linalg.svd(A[k].reshape(a, p * b), full_matrices=False)
-        keep = min(chi, len(s))
-        st |= _cut_flags(s, keep)
+        keep, fl = keep_count(s, chi, cut)
+        st |= _cut_flags(s, keep) | fl
+        if stats is not None:
+            stats["cut_margin"] = min(stats.get("cut_margin", math.inf), cut_margin(s, chi, cut))
         tot = float(np.sum(s ** 2))
         if tot > 0.0:
             wmax = max(wmax, float(np.sum(s[keep:] ** 2)) / tot)
@@ -142,6 +196,7 @@ def truncate_dm(mps, chi):
     """The same truncation in density-matrix form: exact left Gram environments G, then from
     the right: Y = M C, rho = Y^dag G Y, keep the top-chi eigenvectors.  Independent cross-check
     of truncate_svd (the two agree whenever the kept subspace is separated by a gap)."""
+    chi, cut = chi_cut(chi)
     n = len(mps)
     G = [np.ones((1, 1), dtype=mps[0].dtype)]
     for k in range(n - 1):
@@ -155,6 +210,9 @@ def truncate_dm(mps, chi):
         w, V = np.linalg.eigh(rho)
         order = np.argsort(-w, kind="stable")
         keep = min(chi, p * c, a)
+        if cut > 0.0:
+            ev = np.sqrt(np.clip(w[order], 0.0, None))
+            keep = min(keep, keep_count(ev, p * c, cut)[0])
         Vk = V[:, order[:keep]]
         out[k] = np.conj(Vk.T).reshape(keep, p, c)
         C = Y.reshape(a, p * c) @ Vk
@@ -175,11 +233,14 @@ def environments(T, S, lat: Lattice, chi: int, sides=("u", "l"), trunc=truncate_
         env.Eu[0], env.logu[0] = e, lg
         for x in range(1, lat.Lx - 1):
             prod = apply_down(env.Eu[x - 1], Ap[x])
-            tr = trunc(prod, chi)
             if trunc is truncate_svd:
-                tr, st, w = tr
+                stats = {}
+                tr, st, w = trunc(prod, chi, stats)
                 env.status |= st
                 env.max_discarded = max(env.max_discarded, w)
+                env.cut_margin = min(env.cut_margin, stats.get("cut_margin", math.inf))
+            else:
+                tr = trunc(prod, chi)
             e, lg, st = normalize(tr)
             env.status |= st
             env.Eu[x], env.logu[x] = e, env.logu[x - 1] + lg
@@ -189,11 +250,14 @@ def environments(T, S, lat: Lattice, chi: int, sides=("u", "l"), trunc=truncate_
         env.El[lat.Lx - 1], env.logl[lat.Lx - 1] = e, lg
         for x in range(lat.Lx - 2, 0, -1):
             prod = apply_up(env.El[x + 1], Ap[x])
-            tr = trunc(prod, chi)
             if trunc is truncate_svd:
-                tr, st, w = tr
+                stats = {}
+                tr, st, w = trunc(prod, chi, stats)
                 env.status |= st
                 env.max_discarded = max(env.max_discarded, w)
+                env.cut_margin = min(env.cut_margin, stats.get("cut_margin", math.inf))
+            else:
+                tr = trunc(prod, chi)
             e, lg, st = normalize(tr)
             env.status |= st
             env.El[x], env.logl[x] = e, env.logl[x + 1] + lg

@@ -40,6 +40,9 @@ struct peps_handle {
   char* gscratch = nullptr;
   size_t gscratch_bytes = 0;
   KPlan kp[4];  // env, row, pair, sample
+  KPlan kb;     // variational-bound estimator (row-step buffers of the env budget)
+  double* bout = nullptr;  // k_bound's per-(sample, term) sums
+  size_t bout_cap = 0;
   // Hamiltonian cache
   std::vector<char> ham_key;
   std::vector<int> h_tinfo, h_ab, h_rowoff, h_pairoff, h_pij;
@@ -86,7 +89,7 @@ static auto dispatch_elem(const peps_handle* h, F&& f) {
   }
 }
 
-enum { TC_ENV = 0, TC_ROW, TC_PAIR, TC_COMBINE, TC_SAMPLE, TC_GRAM, TC_EIG, TC_MINSR, TC_PAD, TC_N };
+enum { TC_ENV = 0, TC_ROW, TC_PAIR, TC_COMBINE, TC_SAMPLE, TC_GRAM, TC_EIG, TC_MINSR, TC_PAD, TC_BOUND, TC_N };
 
 // Record a start event for kernel class c (returns the slot, or -1 when timing is off).
 static int tstart(peps_handle* h, int c, cudaStream_t s) {
@@ -208,6 +211,20 @@ static void plan_all(peps_handle* h) {
         {B_RHIST, (size_t)std::max(1, Ly - 1) * n * n * E}};
     place(k.p, k.smem, budget, b);
   }
+  // bound plan: the env plan's row-step buffers, then S', the overlap partials and the
+  // rebuilt environment rows (two per side, used alternately)
+  {
+    KPlan& k = h->kb;
+    k.p.ci = ci;
+    k.p.cx = cx;
+    std::vector<std::pair<int, size_t>> b = {
+        {B_RED, 40 * 8}, {B_SIG, (mX + 4) * E}, {B_SEL, 2 * mX * 4}, {B_A, (size_t)g.sT * E}, {B_E, (size_t)g.se * E},
+        {B_C, (size_t)n * chi * E}, {B_W, env_w_elems(chi, D, ci) * E}, {B_R, (size_t)n * n * E}, {B_Z, zsz * E},
+        {B_RHIST, (size_t)std::max(1, Ly - 1) * n * n * E}, {B_S, (size_t)g.Lx * g.Ly},
+        {B_LW, (size_t)2 * chi * chi * E}, {B_LW2, (size_t)g.se * E}, {B_LP, (size_t)2 * Ly * g.se * E},
+        {B_RP, (size_t)2 * Ly * g.se * E}};
+    place(k.p, k.smem, budget, b);
+  }
   // row plan
   budget = h->budget[1];
   {
@@ -264,7 +281,7 @@ static std::mutex g_attr_mu;
 static std::map<std::pair<int, int>, size_t> g_attr_max;
 
 static peps_status finish_plans(peps_handle* h) {
-  size_t maxsmem = 0;
+  size_t maxsmem = h->kb.smem;
   for (auto& k : h->kp) maxsmem = std::max(maxsmem, k.smem);
   cudaError_t e = cudaSuccess;
   {
@@ -287,6 +304,13 @@ static peps_status finish_plans(peps_handle* h) {
     k.grid = h->nsm * occ;
     gmax = std::max(gmax, (size_t)k.grid * (size_t)k.p.gstride);
   }
+  {
+    KPlan& k = h->kb;
+    int occ = dispatch_elem(h, [&](auto z) { return occupancy<decltype(z)>(h->g, 4, k.smem); });
+    if (occ < 1) return fail(h, PEPS_E_SHAPE, "bound kernel does not fit on an SM");
+    k.grid = h->nsm * occ;
+    gmax = std::max(gmax, (size_t)k.grid * (size_t)k.p.gstride);
+  }
   if (gmax > h->gscratch_bytes) {
     if (h->gscratch) cudaFree(h->gscratch);
     h->gscratch = nullptr;
@@ -304,6 +328,8 @@ static peps_status finish_plans(peps_handle* h) {
     k.p.gbase = h->gscratch;
     k.p.ctr = h->ctr;
   }
+  h->kb.p.gbase = h->gscratch;
+  h->kb.p.ctr = h->ctr;
   return PEPS_OK;
 }
 
@@ -318,6 +344,7 @@ extern "C" peps_status peps_create(peps_handle** out, const peps_config* cfg) {
   if (c.gram != 0 && c.gram != 1) return PEPS_E_ARG;
   if (c.solve != 0 && c.solve != 1) return PEPS_E_ARG;
   if (c.cplx != 0 && c.cplx != 1) return PEPS_E_ARG;
+  if (!(c.trunc_weight >= 0.0 && c.trunc_weight < 1.0)) return PEPS_E_ARG;
   if (c.cplx && c.gram != 0) return PEPS_E_UNSUPPORTED;  // the split-BF16 Gram is real only
   peps_handle* h = new peps_handle();
   h->cfg = c;
@@ -329,6 +356,7 @@ extern "C" peps_status peps_create(peps_handle** out, const peps_config* cfg) {
   g.se = c.chi * c.D * c.chi;
   g.sT = c.D * c.D * c.D * c.D;
   g.s2 = c.chi * c.D * c.D * c.chi;
+  g.cut = c.trunc_weight;
   const int N = c.Lx * c.Ly;
   h->site_off_h.assign(N + 1, 0);
   for (int x = 0; x < c.Lx; ++x)
@@ -373,7 +401,7 @@ extern "C" peps_status peps_destroy(peps_handle* h) {
   void* ptrs[] = {h->Tpad, h->site_off, h->envs, h->logs, h->wdisc, h->rowout, h->pairout, h->status_tmp,
                   h->gscratch, h->d_tinfo, h->d_ab, h->d_eh, h->d_rowoff, h->d_pairoff, h->d_pij, h->d_pv,
                   h->d_onsite, h->Obar, h->Tm, h->Vm, h->Hm, h->mean, h->ebar, h->yv, h->xv, h->cnt, h->ctr,
-                  h->lp_Sp, h->lp_l0, h->lp_l1, h->lp_aux, h->g_hi, h->g_lo};
+                  h->lp_Sp, h->lp_l0, h->lp_l1, h->lp_aux, h->g_hi, h->g_lo, h->bout};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t e : h->evpool) cudaEventDestroy(e);
@@ -615,6 +643,55 @@ extern "C" peps_status peps_logderiv(peps_handle* h, const uint8_t* S_dev, int N
                                      void* stream) {
   if (h && !O_dev && Ns > 0) return fail(h, PEPS_E_ARG, "null output");
   return peps_evaluate(h, nullptr, S_dev, Ns, nullptr, nullptr, nullptr, O_dev, status_dev, stream);
+}
+
+// ---- variational-bound estimator ---------------------------------------------------------
+extern "C" peps_status peps_local_energy_bound(peps_handle* h, const peps_hamiltonian* H, const uint8_t* S_dev,
+                                               int Ns, int cut, double* eloc_dev, double* logabs_dev,
+                                               double* phase_dev, int32_t* status_dev, void* stream) {
+  peps_status c = check_eval(h, S_dev, Ns);
+  if (c != PEPS_OK) return c;
+  if (!H || (!eloc_dev && Ns > 0)) return fail(h, PEPS_E_ARG, "null argument");
+  if (cut < 1 || cut > h->g.Lx - 1) return fail(h, PEPS_E_ARG, "cut outside 1 .. Lx-1");
+  cudaStream_t s = (cudaStream_t)stream;
+  int* st = status_dev ? (int*)status_dev : h->status_tmp;
+  CK(cudaMemsetAsync(st, 0, sizeof(int) * Ns, s), "memset status");
+  CK(cudaMemsetAsync(h->wdisc, 0, sizeof(float) * Ns, s), "memset wdisc");
+  if (Ns == 0) return PEPS_OK;
+  peps_status ps = set_hamiltonian(h, H, s);
+  if (ps != PEPS_OK) return ps;
+  const int nt = std::max(h->tt.nterm, 1);
+  const size_t need = (size_t)h->cfg.max_samples * nt * 2;
+  if (need > h->bout_cap) {
+    if (h->bout) cudaFree(h->bout);
+    h->bout = nullptr;
+    h->bout_cap = 0;
+    if (cudaMalloc(&h->bout, need * sizeof(double)) != cudaSuccess) return fail(h, PEPS_E_WORKSPACE, "bound buffer");
+    h->bout_cap = need;
+  }
+  const KPlan& ke = h->kp[0];
+  const KPlan& kb = h->kb;
+  int ts = tstart(h, TC_ENV, s);
+  cudaError_t e = dispatch_elem(h, [&](auto z) {
+    using T = decltype(z);
+    return launch_env<T>(h->g, ke.p, std::min(ke.grid, Ns * 2), ke.smem, (const T*)h->Tpad, S_dev, Ns, 3, (T*)h->envs,
+                         h->logs, st, h->wdisc, s);
+  });
+  if (e != cudaSuccess) return cuda_fail(h, e, "env kernel");
+  tstop(h, ts, s);
+  ts = tstart(h, TC_BOUND, s);
+  e = dispatch_elem(h, [&](auto z) {
+    using T = decltype(z);
+    const long long items = (long long)Ns * nt;
+    return launch_bound<T>(h->g, kb.p, (int)std::min<long long>(kb.grid, items), kb.smem, (const T*)h->Tpad, S_dev, Ns,
+                           cut, (const T*)h->envs, h->logs, h->tt, h->bout, logabs_dev, phase_dev, st, s);
+  });
+  if (e != cudaSuccess) return cuda_fail(h, e, "bound kernel");
+  tstop(h, ts, s);
+  ts = tstart(h, TC_COMBINE, s);
+  CK(launch_bound_combine(h->g, Ns, nt, S_dev, h->bout, h->dg, eloc_dev, s), "bound combine kernel");
+  tstop(h, ts, s);
+  return PEPS_OK;
 }
 
 // ---- sampler -----------------------------------------------------------------------------

@@ -48,6 +48,12 @@ cudaError_t launch_sample(const Geo& g, const Plan& p, int grid, size_t smem, co
                           int move, int nsweeps, unsigned long long seed, unsigned long long sweep0, T* envs,
                           double* logs, long long* accepted, int* status, cudaStream_t s);
 template <typename T>
+cudaError_t launch_bound(const Geo& g, const Plan& p, int grid, size_t smem, const T* Tpad, const uint8_t* S, int Ns,
+                         int cut, const T* envs, const double* logs, const TermTab& tt, double* bout, double* logabs,
+                         double* phase, int* status, cudaStream_t s);
+cudaError_t launch_bound_combine(const Geo& g, int Ns, int nt, const uint8_t* S, const double* bout, const DiagTab& dg,
+                                 double* eloc, cudaStream_t s);
+template <typename T>
 cudaError_t launch_pad(const Geo& g, const double* theta, const long long* site_off, T* Tpad, cudaStream_t s);
 cudaError_t launch_combine(const Geo& g, int Ns, const uint8_t* S, const double* rowout, const double* pairout,
                            int use_rows_all, int use_pairs, const DiagTab& dg, double* logabs, double* phase,
@@ -63,14 +69,17 @@ cudaError_t kattr_pair(const Geo& g, size_t set_bytes, int* occ, size_t occ_smem
 template <typename T>
 cudaError_t kattr_sample(const Geo& g, size_t set_bytes, int* occ, size_t occ_smem);
 template <typename T>
+cudaError_t kattr_bound(const Geo& g, size_t set_bytes, int* occ, size_t occ_smem);
+template <typename T>
 inline cudaError_t set_kernel_smem(const Geo& g, size_t bytes) {
   cudaError_t e;
   if ((e = kattr_env<T>(g, bytes, nullptr, 0)) != cudaSuccess) return e;
   if ((e = kattr_row<T>(g, bytes, nullptr, 0)) != cudaSuccess) return e;
   if ((e = kattr_pair<T>(g, bytes, nullptr, 0)) != cudaSuccess) return e;
+  if ((e = kattr_bound<T>(g, bytes, nullptr, 0)) != cudaSuccess) return e;
   return kattr_sample<T>(g, bytes, nullptr, 0);
 }
-// which: 0 k_env, 1 k_row, 2 k_pair, 3 k_sample
+// which: 0 k_env, 1 k_row, 2 k_pair, 3 k_sample, 4 k_bound
 template <typename T>
 inline int occupancy(const Geo& g, int which, size_t smem) {
   int nb = 0;
@@ -78,6 +87,7 @@ inline int occupancy(const Geo& g, int which, size_t smem) {
     case 0: kattr_env<T>(g, 0, &nb, smem); break;
     case 1: kattr_row<T>(g, 0, &nb, smem); break;
     case 2: kattr_pair<T>(g, 0, &nb, smem); break;
+    case 4: kattr_bound<T>(g, 0, &nb, smem); break;
     default: kattr_sample<T>(g, 0, &nb, smem); break;
   }
   return nb;

@@ -436,6 +436,28 @@ __global__ void k_combine(Geo g, int Ns, const uint8_t* __restrict__ S, const do
     }
   }
 }
+// E_loc^bound = diagonal pairs + on-site terms + the per-term sums of k_bound.  One warp per sample.
+__global__ void k_bound_combine(Geo g, int Ns, int nt, const uint8_t* __restrict__ S, const double* bout, DiagTab dg,
+                                double* eloc) {
+  const int lane = threadIdx.x & 31;
+  const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarp = (gridDim.x * blockDim.x) >> 5;
+  const int N = g.Lx * g.Ly;
+  for (int smp = wid; smp < Ns; smp += nwarp) {
+    const uint8_t* Ss = S + (size_t)smp * N;
+    double re = 0.0, im = 0.0;
+    for (int p = lane; p < dg.npairs; p += 32) re += dg.pair_v[p] * (double)Ss[dg.pair_ij[2 * p]] * (double)Ss[dg.pair_ij[2 * p + 1]];
+    if (dg.onsite)
+      for (int i = lane; i < N; i += 32) re += dg.onsite[(size_t)i * g.d + (Ss[i] < g.d ? Ss[i] : 0)];
+    for (int t = lane; t < nt; t += 32) {
+      re += bout[((size_t)smp * nt + t) * 2];
+      im += bout[((size_t)smp * nt + t) * 2 + 1];
+    }
+    re = warp_sum(re);
+    im = warp_sum(im);
+    if (lane == 0) { eloc[2 * smp] = re; eloc[2 * smp + 1] = im; }
+  }
+}
 #endif
 
 // ------------------------------------------------------------------------------------------
@@ -643,6 +665,117 @@ __global__ void __launch_bounds__(NTHREADS, MinBlocks<T>::value) k_sample(G g, P
 }
 
 // ------------------------------------------------------------------------------------------
+// Variational-bound local energy with one fixed cut: every amplitude is
+// psi_i(S) = E^u[i-1](S) . E^l[i](S) (0-based rows; the upper MPS holds rows 0..i-1).  One work
+// item per (sample, term): for every off-diagonal entry h[a][b] of the term the environments of
+// S' (the term's sites set to the digits of b) are rebuilt only on the rows between the first
+// changed row and the cut, starting from S's stored environments (rows farther from the cut
+// are identical for S and S'), then overlapped.  bout[(smp nt + t)]: the term's sum
+// h[a][b] psi_i(S') / psi_i(S) (diagonal entries included) as (re, im); item t = 0 also writes
+// ln|psi_i(S)| and its phase.
+template <typename T, typename G>
+__global__ void __launch_bounds__(NTHREADS, MinBlocks<T>::value) k_bound(G g, Plan plan, const T* __restrict__ Tpad,
+                                                    const uint8_t* __restrict__ S, int Ns, int cut,
+                                                    const T* envs, const double* logs, TermTab tt, double* bout,
+                                                    double* logabs, double* phase, int* status) {
+  extern __shared__ __align__(16) char smem[];
+  char* gbase = plan.gbase;
+  RowWork<T> w = carve_row<T>(plan, smem, gbase);
+  uint8_t* Sl = (uint8_t*)buf_ptr(plan, B_S, smem, gbase);
+  T* EUb = (T*)buf_ptr(plan, B_LP, smem, gbase);   // 2 rows: rebuilt upper environments
+  T* ELb = (T*)buf_ptr(plan, B_RP, smem, gbase);   // 2 rows: rebuilt lower environments
+  T* Lb = (T*)buf_ptr(plan, B_LW, smem, gbase);    // 2 chi^2: overlap partials
+  T* tb = (T*)buf_ptr(plan, B_LW2, smem, gbase);   // chi D chi
+  T* Lb2 = Lb + (size_t)g.chi * g.chi;
+  __shared__ int st, flag;
+  __shared__ float wd;
+  const int N = g.Lx * g.Ly, Ly = g.Ly, Lx = g.Lx;
+  const size_t rowsz = (size_t)Ly * g.se;
+  const int nt = tt.nterm > 0 ? tt.nterm : 1;
+  const int su = slot_up(g, cut - 1), sl = slot_lo(g, cut);
+  for (int item = blockIdx.x; item < Ns * nt; item += gridDim.x) {
+    const int smp = item / nt, t = item % nt;
+    const uint8_t* Ss = S + (size_t)smp * N;
+    const T* env = envs + (size_t)smp * env_sample_elems(g);
+    const double* lg = logs + (size_t)smp * 2 * Lx;
+    if (threadIdx.x == 0) { st = 0; wd = 0.f; }
+    __syncthreads();
+    double l0 = lg[su] + lg[sl];
+    const dz z0 = to_dz(mps_overlap(g, env + (size_t)su * rowsz, env + (size_t)sl * rowsz, Lb, Lb2, tb, w.red, &st, &l0));
+    double ere = 0.0, eim = 0.0;
+    if (t < tt.nterm) {
+      const int* ti = tt.tinfo + (size_t)t * TI_N;
+      const int a = local_index(ti, Ss, g.d);
+      for (int e = ti[TI_EOFF]; e < ti[TI_EOFF] + ti[TI_ECNT]; ++e) {
+        if (tt.ent_ab[2 * e] != a) continue;
+        const int b = tt.ent_ab[2 * e + 1];
+        const double hr = tt.ent_h[2 * e], hi = tt.ent_h[2 * e + 1];
+        if (b == a) { ere += hr; eim += hi; continue; }
+        // S' and the rows it changes on each side of the cut
+        for (int i = threadIdx.x; i < N; i += blockDim.x) Sl[i] = (uint8_t)state_after(ti, i, Ss, b, g.d);
+        int rlo = Lx, rhi = -1;
+        for (int k = 0; k < ti[TI_K]; ++k) {
+          const int site = ti[TI_S0 + k], r = site / Ly;
+          if (state_after(ti, site, Ss, b, g.d) == Ss[site]) continue;
+          if (r < cut) rlo = min(rlo, r);
+          else rhi = max(rhi, r);
+        }
+        __syncthreads();
+        const T* EU = env + (size_t)su * rowsz;
+        double lu = lg[su];
+        if (rlo < cut) {
+          const T* prev = env + (size_t)slot_up(g, rlo - 1) * rowsz;
+          lu = lg[slot_up(g, rlo - 1)];
+          for (int r = rlo; r < cut; ++r) {
+            T* out = EUb + (size_t)((r - rlo) & 1) * rowsz;
+            if (r == 0) lu = env_first_row(g, out, Tpad, 0, Sl, false, w.A, w.Z, w.red, &st);
+            else lu += env_row_step(g, prev, out, Tpad, r, Sl + (size_t)r * Ly, false, w, &st, &wd, &flag);
+            prev = out;
+          }
+          EU = prev;
+        }
+        const T* EL = env + (size_t)sl * rowsz;
+        double ll = lg[sl];
+        if (rhi >= cut) {
+          const T* prev = env + (size_t)slot_lo(g, rhi + 1) * rowsz;
+          ll = lg[slot_lo(g, rhi + 1)];
+          for (int r = rhi; r >= cut; --r) {
+            T* out = ELb + (size_t)((rhi - r) & 1) * rowsz;
+            if (r == Lx - 1) ll = env_first_row(g, out, Tpad, Lx - 1, Sl + (size_t)(Lx - 1) * Ly, true, w.A, w.Z, w.red, &st);
+            else ll += env_row_step(g, prev, out, Tpad, r, Sl + (size_t)r * Ly, true, w, &st, &wd, &flag);
+            prev = out;
+          }
+          EL = prev;
+        }
+        double l1 = lu + ll;
+        const dz z1 = to_dz(mps_overlap(g, EU, EL, Lb, Lb2, tb, w.red, &st, &l1));
+        if (z1.re != 0.0 || z1.im != 0.0) {
+          const dz q = dz_div(z1, z0);
+          const double f = exp(l1 - l0);
+          ere += (hr * q.re - hi * q.im) * f;
+          eim += (hr * q.im + hi * q.re) * f;
+        }
+      }
+    }
+    if (threadIdx.x == 0) {
+      double* o = bout + ((size_t)smp * nt + t) * 2;
+      o[0] = ere;
+      o[1] = eim;
+      const double av = dz_abs(z0);
+      int s = st;
+      if (t == 0) {
+        const double la = (av > 0.0) ? log(av) + l0 : -INFINITY;
+        if (logabs) logabs[smp] = la;
+        if (phase) phase[smp] = (z0.im == 0.0) ? ((z0.re < 0.0) ? 3.141592653589793 : 0.0) : atan2(z0.im, z0.re);
+      }
+      if (!(av > 0.0) || !isfinite(ere) || !isfinite(eim)) s |= ST_NONFINITE;
+      if (s) atomicOr(status + smp, s);
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------------------------------
 // theta (compact, double) -> padded kernel layout [site][s][l][u][r][d] in T
 template <typename T>
 __global__ void k_pad_theta(Geo g, const double* __restrict__ theta, const long long* site_off, T* Tpad) {
@@ -671,8 +804,8 @@ __global__ void k_pad_theta(Geo g, const double* __restrict__ theta, const long 
 // geometry kernel.
 template <typename F>
 static cudaError_t with_geo(const Geo& g, F&& f) {
-  if (g.chi == 16 && g.D == 4) return f(GeoS<16, 4>{g.Lx, g.Ly, g.d});
-  if (g.chi == 24 && g.D == 4) return f(GeoS<24, 4>{g.Lx, g.Ly, g.d});
+  if (g.chi == 16 && g.D == 4) return f(GeoS<16, 4>{g.Lx, g.Ly, g.d, g.cut});
+  if (g.chi == 24 && g.D == 4) return f(GeoS<24, 4>{g.Lx, g.Ly, g.d, g.cut});
   return f(g);
 }
 // complex PEPS run the runtime-shape kernels only
@@ -768,7 +901,32 @@ PEPS_KATTR(kattr_sample, k_sample)
   template cudaError_t kattr_sample<T>(const Geo&, size_t, int*, size_t);
 #endif
 
+#ifdef PEPS_PART_BOUND
+template <typename T>
+cudaError_t launch_bound(const Geo& g, const Plan& p, int grid, size_t smem, const T* Tpad, const uint8_t* S, int Ns,
+                         int cut, const T* envs, const double* logs, const TermTab& tt, double* bout, double* logabs,
+                         double* phase, int* status, cudaStream_t s) {
+  return with_geo_for<T>(g, [&](auto gg) {
+    k_bound<T, decltype(gg)><<<grid, NTHREADS, smem, s>>>(gg, p, Tpad, S, Ns, cut, envs, logs, tt, bout, logabs, phase,
+                                                          status);
+    return cudaGetLastError();
+  });
+}
+PEPS_KATTR(kattr_bound, k_bound)
+#define PEPS_INST_BOUND(T)                                                                                        \
+  template cudaError_t launch_bound<T>(const Geo&, const Plan&, int, size_t, const T*, const uint8_t*, int, int,  \
+                                       const T*, const double*, const TermTab&, double*, double*, double*, int*,  \
+                                       cudaStream_t);                                                             \
+  template cudaError_t kattr_bound<T>(const Geo&, size_t, int*, size_t);
+#endif
+
 #ifdef PEPS_DEFINE_COMMON
+cudaError_t launch_bound_combine(const Geo& g, int Ns, int nt, const uint8_t* S, const double* bout, const DiagTab& dg,
+                                 double* eloc, cudaStream_t s) {
+  const int blocks = (Ns * 32 + 255) / 256;
+  k_bound_combine<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(g, Ns, nt, S, bout, dg, eloc);
+  return cudaGetLastError();
+}
 cudaError_t launch_combine(const Geo& g, int Ns, const uint8_t* S, const double* rowout, const double* pairout,
                            int use_rows_all, int use_pairs, const DiagTab& dg, double* logabs, double* phase,
                            double* eloc, cudaStream_t s) {

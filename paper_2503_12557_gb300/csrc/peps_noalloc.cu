@@ -68,6 +68,7 @@ peps_status run(const peps_config& c, const double* theta, const uint8_t* S, int
   g.se = c.chi * c.D * c.chi;
   g.sT = c.D * c.D * c.D * c.D;
   g.s2 = c.chi * c.D * c.D * c.chi;
+  g.cut = c.trunc_weight;
   const int N = c.Lx * c.Ly, n = g.n, chi = g.chi, D = g.D, Ly = g.Ly;
   const int mX = n + (n & 1), Lr = D * chi, ci = n < 8 ? n : 8;
   const size_t E = sizeof(T);
@@ -133,6 +134,7 @@ extern "C" peps_status peps_amplitudes_noalloc(const peps_config* cfg, const dou
     return PEPS_E_SHAPE;
   if (c.prec != PEPS_PREC_FP64 && c.prec != PEPS_PREC_FP32) return PEPS_E_ARG;
   if (c.cplx) return PEPS_E_UNSUPPORTED;  // real PEPS only
+  if (!(c.trunc_weight >= 0.0 && c.trunc_weight < 1.0)) return PEPS_E_ARG;
   if (Ns == 0) return PEPS_OK;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PEPS_E_CUDA;

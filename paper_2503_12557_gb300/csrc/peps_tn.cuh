@@ -125,6 +125,7 @@ struct Geo {
   int se;  // chi*D*chi, one environment site
   int sT;  // D^4, one projected PEPS tensor
   int s2;  // chi*D*D*chi, one two-row partial
+  double cut = 0.0;  // truncated-weight cutoff (0: fixed chi)
 };
 
 // The same geometry with (chi, D) fixed at compile time: every device routine below is a
@@ -133,6 +134,7 @@ struct Geo {
 template <int CHI, int DD>
 struct GeoS {
   int Lx, Ly, d;
+  double cut;  // truncated-weight cutoff (0: fixed chi)
   static constexpr int D = DD, chi = CHI, n = CHI * DD, se = CHI * DD * CHI, sT = DD * DD * DD * DD,
                        s2 = CHI * DD * DD * CHI;
 };
@@ -1068,7 +1070,57 @@ __device__ double env_row_step(const G& g, const T* Eprev, T* Eout, const T* Tpa
     }
     if (tid == 0 && mX <= chi) { sig[mX + 1] = 0; }
     __syncthreads();
-    if (mX > chi) {
+    int nkeep = (mX < chi) ? mX : chi;
+    if (g.cut > 0.0) {
+      // truncated-weight rule: keep the fewest singular values (at most chi) whose discarded
+      // share of sum sigma^2 is at most cut; tail(r) = sum over ranks >= r of sigma^2
+      __shared__ int kc_s;
+      if (tid == 0) kc_s = mX;
+      double part = 0.0;
+      for (int p = tid; p < mX; p += NT) part += (double)sig[p] * (double)sig[p];
+      const double tot_s = block_sum(part, w.red);  // ends with a barrier
+      const double thr = g.cut * tot_s;
+      for (int r = tid + 1; r < mX; r += NT) {
+        double tail = 0.0;
+        for (int p = 0; p < mX; ++p)
+          if (w.sel[mX + p] >= r) tail += (double)sig[p] * (double)sig[p];
+        if (tail <= thr) atomicMin(&kc_s, r);
+      }
+      __syncthreads();
+      const int kc = kc_s;
+      if (tot_s > 0.0 && kc < nkeep) {
+        if (tid == 0) {
+          // a boundary weight within 1e-9 of the cutoff: the choice is not stable under rounding
+          for (int k = kc - 1; k <= kc; ++k) {
+            if (k < 1) continue;
+            double tail = 0.0;
+            for (int p = 0; p < mX; ++p)
+              if (w.sel[mX + p] >= k) tail += (double)sig[p] * (double)sig[p];
+            if (fabs(tail - thr) <= 1e-9 * thr) *st |= ST_NEAR_DEGENERATE;
+          }
+        }
+        nkeep = kc;
+      }
+      // discarded weight and near-degenerate cut at the chosen boundary (the oracle's rule)
+      RT tot = 0, dis = 0;
+      for (int p = tid; p < mX; p += NT) {
+        const RT s2 = sig[p] * sig[p];
+        tot += s2;
+        if (w.sel[mX + p] >= nkeep) dis += s2;
+      }
+      tot = block_sum(tot, w.red);
+      dis = block_sum(dis, w.red);
+      if (tid == 0 && nkeep < mX) {
+        const RT s0 = sig[mX + 2], sk = sig[w.sel[nkeep - 1]];
+        const RT sd = (nkeep < chi) ? sig[w.sel[nkeep]] : sig[mX + 1];
+        if (s0 > RT(0) && (sk - sd) < RT(1e-8) * s0 && sd > RT(1e-12) * s0) *st |= ST_NEAR_DEGENERATE;
+        if (tot > RT(0)) {
+          const float wd = (float)(dis / tot);
+          if (wd > *wdisc) *wdisc = wd;
+        }
+      }
+      __syncthreads();
+    } else if (mX > chi) {
       // discarded weight and near-degenerate cut (same rule as the oracle)
       RT tot = 0, dis = 0;
       for (int p = tid; p < mX; p += NT) {
@@ -1087,8 +1139,7 @@ __device__ double env_row_step(const G& g, const T* Eprev, T* Eout, const T* Tpa
         }
       }
     }
-    // Vt[c'][q] = X[sel(c')][q] / sigma  (the rows of V^H)
-    const int nkeep = (mX < chi) ? mX : chi;
+    // Vt[c'][q] = X[sel(c')][q] / sigma  (the rows of V^H); rows from nkeep on are zero
     for (int o = tid; o < chi * Lr; o += NT) {
       const int q = o % Lr, cp = o / Lr;
       T v = 0;
@@ -1270,6 +1321,45 @@ __device__ T blk_dot(const T* a, const T* b, int n, double* red) {
   T s = 0;
   for (int o = threadIdx.x; o < n; o += blockDim.x) s += a[o] * b[o];
   return block_sum(s, red);
+}
+
+// ------------------------------------------------------------------------------------------
+// Overlap of an upper and a lower boundary MPS across the cut between two rows (the amplitude
+// psi_i = E^u[i] . E^l[i+1] of the variational-bound estimator): the plain contraction (no
+// conjugation) over the shared physical legs, column by column from the left,
+//   L'[x][z] = sum_{a, b, p} L[a][b] eu[a][p][x] el[b][p][z],
+// each partial divided by its largest modulus, the log factors added to *lg (the same value
+// in every thread).  Lb, Lb2: chi^2 elements; tb: chi D chi.  Returns the last partial.
+template <typename T, typename G>
+__device__ T mps_overlap(const G& g, const T* EU, const T* EL, T* Lb, T* Lb2, T* tb, double* red, int* st,
+                         double* lg) {
+  const int chi = g.chi, cd = g.chi * g.D, cc = g.chi * g.chi;
+  blk_unit(Lb, cc);
+  __syncthreads();
+  for (int y = 0; y < g.Ly; ++y) {
+    const T* eu = EU + (size_t)y * g.se;
+    const T* el = EL + (size_t)y * g.se;
+    // tb[b][p][x] = sum_a L[a][b] eu[a][p][x]
+    for (int o = threadIdx.x; o < chi * cd; o += blockDim.x) {
+      const int b = o / cd, px = o % cd;
+      T acc = T(0);
+      for (int a = 0; a < chi; ++a) acc += Lb[a * chi + b] * eu[(size_t)a * cd + px];
+      tb[o] = acc;
+    }
+    __syncthreads();
+    // L'[x][z] = sum_{b, p} tb[b][p][x] el[b][p][z]
+    for (int o = threadIdx.x; o < cc; o += blockDim.x) {
+      const int x = o / chi, z = o % chi;
+      T acc = T(0);
+      for (int bp = 0; bp < cd; ++bp) acc += tb[(size_t)bp * chi + x] * el[(size_t)bp * chi + z];
+      Lb2[o] = acc;
+    }
+    __syncthreads();
+    *lg += blk_normalize(Lb2, cc, red, st);
+    blk_copy(Lb, Lb2, cc);
+    __syncthreads();
+  }
+  return Lb[0];
 }
 
 // ------------------------------------------------------------------------------------------

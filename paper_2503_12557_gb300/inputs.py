@@ -243,6 +243,42 @@ def j1j2_chiral(lat: Lattice, J1: float = 1.0, J2: float = 0.5, Jchi: float = 0.
     return {"terms": terms, "pairs": [], "onsite": np.zeros((lat.nsites, lat.d))}
 
 
+def _cyclic_permutation4(d: int = 2):
+    """P on four sites in their listed order: P |s1 s2 s3 s4> = |s4 s1 s2 s3> (the local state of
+    site k moves to site k + 1, that of site 4 to site 1).  Matrix element order <out|P|in>."""
+    P = np.zeros((d ** 4, d ** 4))
+    for a in range(d ** 4):
+        s1, s2, s3, s4 = (a // d ** 3) % d, (a // d ** 2) % d, (a // d) % d, a % d
+        b = ((s4 * d + s1) * d + s2) * d + s3
+        P[b, a] = 1.0
+    return P
+
+
+CSL_J1 = 2.0 * math.cos(0.06 * math.pi) * math.cos(0.14 * math.pi)
+CSL_J2 = 2.0 * math.cos(0.06 * math.pi) * math.sin(0.14 * math.pi)
+CSL_LAMBDA = 2.0 * math.sin(0.06 * math.pi)
+
+
+def csl(lat: Lattice, J1: float = CSL_J1, J2: float = CSL_J2, lam: float = CSL_LAMBDA):
+    """The chiral-spin-liquid model of Eq. (CSL_Model): J1 on nearest-neighbour bonds, J2 on both
+    diagonals of every plaquette, and i lam (P_ijkl - P_ijkl^-1) on every plaquette, P the cyclic
+    permutation of the four local states, the corners listed counter-clockwise in the drawing
+    plane (y to the right, x downwards: top-left, bottom-left, bottom-right, top-right).  The
+    default couplings are the values at which the paper's ground state is a chiral spin liquid."""
+    Ly = lat.Ly
+    P = _cyclic_permutation4(lat.d)
+    ring = 1j * lam * (P - P.T)
+    terms = [((i, j), J1 * _sdots()) for (i, j) in _nn_bonds(lat.Lx, lat.Ly)]
+    for x in range(lat.Lx - 1):
+        for y in range(Ly - 1):
+            tl, tr = x * Ly + y, x * Ly + y + 1
+            bl, br = (x + 1) * Ly + y, (x + 1) * Ly + y + 1
+            terms.append(((tl, br), J2 * _sdots()))
+            terms.append(((tr, bl), J2 * _sdots()))
+            terms.append(((tl, bl, br, tr), ring.copy()))
+    return {"terms": terms, "pairs": [], "onsite": np.zeros((lat.nsites, lat.d))}
+
+
 def rydberg(lat: Lattice, omega: float = 1.0, delta: float = 3.0, Rb: float = 1.7, rmax: float = 4.0):
     """H = (Omega/2) sum_i sigma^x_i - delta sum_i n_i + sum_{i<j, r_ij <= rmax} V0 / r_ij^6 n_i n_j,
     V0 = Omega * Rb^6, lattice spacing 1, each unordered pair once."""

@@ -26,7 +26,7 @@ _ERRORS = {-1: "PEPS_E_ARG", -2: "PEPS_E_SHAPE", -3: "PEPS_E_WORKSPACE", -4: "PE
 class _Config(C.Structure):
     _fields_ = [("Lx", C.c_int), ("Ly", C.c_int), ("d", C.c_int), ("D", C.c_int), ("chi", C.c_int),
                 ("prec", C.c_int), ("max_samples", C.c_int), ("gram", C.c_int), ("solve", C.c_int),
-                ("cplx", C.c_int)]
+                ("cplx", C.c_int), ("trunc_weight", C.c_double)]
 
 
 class _Term(C.Structure):
@@ -67,6 +67,7 @@ def load():
         "peps_local_energy": ([vp, C.POINTER(_Ham), vp, i32, vp, vp, vp], i32),
         "peps_logderiv": ([vp, vp, i32, vp, vp, vp], i32),
         "peps_evaluate": ([vp, C.POINTER(_Ham), vp, i32, vp, vp, vp, vp, vp, vp], i32),
+        "peps_local_energy_bound": ([vp, C.POINTER(_Ham), vp, i32, i32, vp, vp, vp, vp, vp], i32),
         "minsr_step": ([vp, vp, vp, vp, i32, dbl, dbl, dbl, vp, vp, vp], i32),
         "peps_sample": ([vp, i32, vp, i32, i32, C.c_uint64, C.c_uint64, vp, vp, vp], i32),
         "peps_last_error": ([vp], C.c_char_p),
@@ -95,7 +96,8 @@ def exported_symbols():
             "peps_local_energy", "peps_logderiv", "peps_evaluate", "minsr_step", "peps_sample", "peps_last_error",
             "peps_timing_enable", "peps_timing_read", "peps_apply_update", "peps_proposal_logits",
             "peps_proposal_train_step", "peps_sample_learned", "peps_amplitudes_noalloc", "peps_probe_fma",
-            "peps_autotune", "peps_batch_create", "peps_batch_launch", "peps_batch_destroy"]
+            "peps_autotune", "peps_batch_create", "peps_batch_launch", "peps_batch_destroy",
+            "peps_local_energy_bound"]
 
 
 def probe_fma(fp64=False):
@@ -146,7 +148,7 @@ class Proposal:
         return self.loss
 
 
-TIMING_CLASSES = ["env", "row", "pair", "combine", "sample", "minsr_gram", "minsr_eig", "minsr_other", "pad"]
+TIMING_CLASSES = ["env", "row", "pair", "combine", "sample", "minsr_gram", "minsr_eig", "minsr_other", "pad", "bound"]
 
 
 def _ptr(t):
@@ -187,7 +189,7 @@ class Hamiltonian:
 class PEPS:
     """One handle of the C library: a lattice, chi and a precision."""
 
-    def __init__(self, Lx, Ly, d, D, chi, prec=PREC_FP64, max_samples=4096, gram=0, solve=0, cplx=False):
+    def __init__(self, Lx, Ly, d, D, chi, prec=PREC_FP64, max_samples=4096, gram=0, solve=0, cplx=False, trunc_weight=0.0):
         self.L = load()
         self.Lx, self.Ly, self.d, self.D, self.chi, self.prec = Lx, Ly, d, D, chi, prec
         self.max_samples = max_samples
@@ -195,7 +197,8 @@ class PEPS:
         self.last_warning = None
         self.solve = solve
         self.cplx = bool(cplx)
-        cfg = _Config(Lx, Ly, d, D, chi, prec, max_samples, gram, solve, int(self.cplx))
+        self.trunc_weight = float(trunc_weight)
+        cfg = _Config(Lx, Ly, d, D, chi, prec, max_samples, gram, solve, int(self.cplx), self.trunc_weight)
         h = C.c_void_p()
         st = self.L.peps_create(C.byref(h), C.byref(cfg))
         if st != 0:
@@ -304,6 +307,21 @@ class PEPS:
         self._check(self.L.peps_evaluate(self.h, C.byref(hc.c) if hc else None, _ptr(S), ns, _ptr(la), _ptr(ph),
                                          _ptr(e), _ptr(O), _ptr(st), _stream()), "peps_evaluate")
         return dict(logabs=la, phase=ph, eloc=e, O=O, status=st)
+
+    def local_energy_bound(self, H, S, cut):
+        """Variational-bound E_loc with every amplitude taken at one cut (1 <= cut <= Lx-1):
+        dict of eloc (Ns x 2), logabs and phase of psi_cut(S), status."""
+        S = self._S(S)
+        ns = S.shape[0]
+        dev = S.device
+        la = torch.empty(ns, dtype=torch.float64, device=dev)
+        ph = torch.empty(ns, dtype=torch.float64, device=dev)
+        e = torch.empty(ns, 2, dtype=torch.float64, device=dev)
+        st = torch.empty(ns, dtype=torch.int32, device=dev)
+        hc = self.hamiltonian(H)
+        self._check(self.L.peps_local_energy_bound(self.h, C.byref(hc.c), _ptr(S), ns, int(cut), _ptr(e), _ptr(la),
+                                                   _ptr(ph), _ptr(st), _stream()), "peps_local_energy_bound")
+        return dict(eloc=e, logabs=la, phase=ph, status=st)
 
     def minsr_step(self, O, eloc, w=None, lam=1e-4, rcond=0.0, tau=0.05):
         ns = O.shape[0]

@@ -1,0 +1,138 @@
+"""The variational-bound estimator through the C ABI (peps_local_energy_bound) against the FP64
+oracle: E_loc^bound with every amplitude taken at one cut, ln|psi_i| and its phase, for real
+and complex PEPS, one- and two-row terms, every cut, the compiled (chi, D) = (16, 4) shape and
+FP32; at exact chi it equals the fast estimator."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2503_12557_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2503_12557_gb300 import build, peps
+    build.build()
+    return peps
+
+
+def _run(P, lat, chi, th, S, H, cut, prec=0, cplx=False):
+    h = P.PEPS(lat.Lx, lat.Ly, lat.d, lat.D, chi, prec=prec, max_samples=len(S), cplx=cplx)
+    h.set_params(torch.as_tensor(th).cuda())
+    r = h.local_energy_bound(H, torch.as_tensor(S).cuda(), cut)
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in r.items()}
+
+
+def _compare(res, ref, tol=TOL):
+    ok = ((res["status"] & 1) == 0) & ((ref["status"] & 1) == 0)
+    assert ok.sum() >= max(1, int(0.75 * len(ok)))
+    assert np.max(np.abs(res["logabs"] - ref["logabs"])[ok]) <= tol
+    dph = np.angle(np.exp(1j * (res["phase"] - ref["phase"])))
+    assert np.max(np.abs(dph)[ok]) <= 10 * tol
+    e = res["eloc"][:, 0] + 1j * res["eloc"][:, 1]
+    de = np.abs(e - ref["eloc"]) / np.maximum(1.0, np.abs(ref["eloc"]))
+    assert np.max(de[ok]) <= tol, np.max(de)
+
+
+@pytest.mark.parametrize("cut", [1, 2, 3])
+def test_bound_heisenberg_every_cut(P, cut):
+    from oracle import bound
+    lat = I.Lattice(4, 4, 2, 2)
+    th = I.peps_random(lat, 51, scale=0.5, bias=1.0)
+    S = I.configs_uniform_sz0(lat, 10, 52)
+    H = I.heisenberg(lat)
+    res = _run(P, lat, 3, th, S, H, cut)
+    _compare(res, bound.evaluate_bound(th, S, lat, 3, H, cut))
+
+
+def test_bound_two_row_terms_and_ragged_shape(P):
+    # J1-J2: diagonal bonds over two rows, some of them across the cut; 5 x 4, D = 3, chi = 5
+    from oracle import bound
+    lat = I.Lattice(5, 4, 2, 3)
+    th = I.peps_random(lat, 53, scale=0.5, bias=1.0)
+    S = I.configs_uniform_sz0(lat, 8, 54)
+    H = I.j1j2_chiral(lat, J1=1.0, J2=0.5, Jchi=0.0)
+    H["terms"] = [t for t in H["terms"] if len(t[0]) == 2]
+    res = _run(P, lat, 5, th, S, H, 2)
+    _compare(res, bound.evaluate_bound(th, S, lat, 5, H, 2))
+
+
+def test_bound_complex_chiral(P):
+    from oracle import bound
+    lat = I.Lattice(4, 4, 2, 2)
+    th = I.peps_random(lat, 55, scale=0.6, bias=1.0, complex_=True)
+    S = I.configs_uniform_sz0(lat, 8, 56)
+    H = I.j1j2_chiral(lat)
+    res = _run(P, lat, 3, th, S, H, 2, cplx=True)
+    ref = bound.evaluate_bound(th, S, lat, 3, H, 2)
+    assert np.max(np.abs(ref["eloc"].imag)) > 1e-3
+    _compare(res, ref)
+
+
+def test_bound_rydberg_flips(P):
+    # one-site sigma^x terms (flips) and long-range diagonal pairs
+    from oracle import bound
+    lat = I.Lattice(4, 5, 2, 2)
+    th = I.peps_random(lat, 57, scale=0.5, bias=1.0)
+    S = I.configs_uniform(lat, 8, 58)
+    H = I.rydberg(lat, delta=1.5)
+    res = _run(P, lat, 4, th, S, H, 2)
+    _compare(res, bound.evaluate_bound(th, S, lat, 4, H, 2))
+
+
+def test_bound_compiled_shape_8x8_chi16(P):
+    # the (chi, D) = (16, 4) specialisation of the bench workload, two samples
+    from oracle import bound
+    lat = I.Lattice(8, 8, 2, 4)
+    th = I.peps_random(lat, 59, scale=0.5, bias=1.0)
+    S = I.configs_uniform_sz0(lat, 2, 60)
+    H = I.heisenberg(lat)
+    res = _run(P, lat, 16, th, S, H, 4)
+    _compare(res, bound.evaluate_bound(th, S, lat, 16, H, 4), tol=1e-9)
+
+
+def test_bound_fp32_close(P):
+    from oracle import bound
+    lat = I.Lattice(5, 5, 2, 3)
+    th = I.peps_random(lat, 61, scale=0.5, bias=1.0)
+    S = I.configs_uniform_sz0(lat, 8, 62)
+    H = I.heisenberg(lat)
+    res = _run(P, lat, 9, th, S, H, 2, prec=1)
+    ref = bound.evaluate_bound(th, S, lat, 9, H, 2)
+    dl = np.abs(res["logabs"] - ref["logabs"])
+    print(f"fp32 bound |d ln psi_i| max {dl.max():.2e}")
+    assert dl.max() < 1e-4
+    e = res["eloc"][:, 0]
+    assert abs(np.mean(e) - np.mean(ref["eloc"].real)) / lat.nsites < 1e-4
+
+
+def test_bound_equals_fast_estimator_at_exact_chi(P):
+    # chi = D^(Ly/2) is exact for every cut: both estimators give the exact local energy
+    lat = I.Lattice(4, 4, 2, 2)
+    th = I.peps_random(lat, 63, scale=0.5, bias=1.0)
+    S = torch.as_tensor(I.configs_uniform_sz0(lat, 12, 64)).cuda()
+    H = I.heisenberg(lat)
+    h = P.PEPS(4, 4, 2, 2, 4, max_samples=12)
+    h.set_params(torch.as_tensor(th).cuda())
+    fast = h.evaluate(H, S, want_O=False)
+    for cut in (1, 2, 3):
+        b = h.local_energy_bound(H, S, cut)
+        torch.cuda.synchronize()
+        e0, e1 = fast["eloc"].cpu().numpy()[:, 0], b["eloc"].cpu().numpy()[:, 0]
+        assert np.max(np.abs(e0 - e1) / np.maximum(1.0, np.abs(e0))) < 1e-10
+        assert np.max(np.abs(fast["logabs"].cpu().numpy() - b["logabs"].cpu().numpy())) < 1e-10
+
+
+def test_bound_rejects_bad_cut(P):
+    lat = I.Lattice(4, 4, 2, 2)
+    h = P.PEPS(4, 4, 2, 2, 3, max_samples=2)
+    S = torch.as_tensor(I.configs_uniform_sz0(lat, 2, 1)).cuda()
+    for cut in (0, 4):
+        with pytest.raises(RuntimeError):
+            h.local_energy_bound(I.heisenberg(lat), S, cut)

@@ -63,6 +63,27 @@ def test_complex_evaluate_vs_oracle(P, Lx, Ly, D, chi, ns, seed):
     assert np.max(dO[ok]) <= TOL, np.max(dO)
 
 
+@pytest.mark.parametrize("Lx,Ly,D,chi,ns,seed", [(3, 3, 2, 4, 16, 31), (4, 4, 2, 3, 12, 32)])
+def test_csl_model_vs_oracle(P, Lx, Ly, D, chi, ns, seed):
+    # the chiral-spin-liquid model of Eq. (CSL_Model): four-site plaquette ring terms
+    # i lam (P - P^-1) over two rows and two columns, next to J1 and J2 bonds
+    from oracle import energy
+    lat = I.Lattice(Lx, Ly, 2, D)
+    th = _theta(lat, seed)
+    S = I.configs_uniform_sz0(lat, ns, seed + 10)
+    H = I.csl(lat)
+    h = _handle(P, lat, chi, ns)
+    h.set_params(torch.as_tensor(th).cuda())
+    res = h.evaluate(H, torch.as_tensor(S).cuda(), want_O=False)
+    torch.cuda.synchronize()
+    ref = energy.evaluate(th, S, lat, chi, H=H, want_O=False)
+    ok = (res["status"].cpu().numpy() & 1) == 0
+    el = res["eloc"].cpu().numpy()
+    de = np.abs(el[:, 0] + 1j * el[:, 1] - ref["eloc"]) / np.maximum(1.0, np.abs(ref["eloc"]))
+    assert ok.sum() >= max(1, int(0.8 * ns))
+    assert np.max(de[ok]) <= TOL, np.max(de)
+
+
 def test_complex64_reduced_precision(P):
     from oracle import energy
     lat = I.Lattice(5, 5, 2, 3)

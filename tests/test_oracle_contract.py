@@ -124,6 +124,65 @@ def test_truncate_dm_equals_svd(n, p, bond, chi):
     assert np.linalg.norm(va - vb) <= 1e-9 * np.linalg.norm(va)
 
 
+def _bruteforce_truncate_cut(vec, n, p, chi, cut):
+    """As _bruteforce_truncate with the truncated-weight rule: at every cut keep the fewest
+    Schmidt values (at most chi) whose discarded share of sum s^2 is at most cut."""
+    v = vec.copy()
+    kept = []
+    for k in range(n - 1, 0, -1):
+        M = v.reshape(p ** k, p ** (n - k))
+        U, s, Vh = np.linalg.svd(M, full_matrices=False)
+        tot = float(np.sum(s ** 2))
+        keep = 1
+        while keep < len(s) and float(np.sum(s[keep:] ** 2)) / tot > cut:
+            keep += 1
+        keep = min(keep, chi)
+        kept.append(keep)
+        P = np.conj(Vh[:keep].T) @ Vh[:keep]
+        v = (M @ P).reshape(-1)
+    return v, kept
+
+
+@pytest.mark.parametrize("n,p,bond,chi,cut", [(6, 2, 8, 8, 1e-2), (5, 3, 9, 9, 5e-3), (6, 2, 8, 3, 1e-4)])
+def test_truncate_cutoff_equals_bruteforce(n, p, bond, chi, cut):
+    # decaying spectra, so that the cutoff, not chi, sets most bond dimensions
+    mps = _random_mps(n, p, bond, seed=31 * n + bond)
+    for k, e in enumerate(mps):
+        mps[k] = e * (0.45 ** np.arange(e.shape[2]))[None, None, :]
+    vec = tn.mps_to_vector(mps)
+    ref, kept = _bruteforce_truncate_cut(vec, n, p, chi, cut)
+    got, st, w = tn.truncate_svd(mps, (chi, cut))
+    assert st == 0
+    assert [e.shape[0] for e in got[1:]][::-1] == kept
+    assert min(kept) < min(chi, bond)  # the cutoff, not the cap, sets some bond
+    assert np.linalg.norm(tn.mps_to_vector(got) - ref) <= 1e-10 * np.linalg.norm(ref)
+    assert w <= cut
+    # the density-matrix form applies the same rule
+    b = tn.truncate_dm(mps, (chi, cut))
+    assert np.linalg.norm(tn.mps_to_vector(b) - ref) <= 1e-9 * np.linalg.norm(ref)
+
+
+def test_truncate_cutoff_zero_is_fixed_chi():
+    mps = _random_mps(5, 2, 6, seed=8)
+    a, _, _ = tn.truncate_svd(mps, 3)
+    b, _, _ = tn.truncate_svd(mps, (3, 0.0))
+    assert all(np.array_equal(x, y) for x, y in zip(a, b))
+
+
+def test_cut_margin_hand_computed():
+    # s^2 = (0.9, 0.08, 0.015, 0.005), cutoff 0.01: tails 0.1, 0.02, 0.005 -> three kept; the
+    # comparisons that decide it sit 9, 1 and 0.5 cutoffs away from it (0.5 the smallest)
+    s = np.sqrt([0.9, 0.08, 0.015, 0.005])
+    assert tn.keep_count(s, 4, 0.01) == (3, 0)
+    assert abs(tn.cut_margin(s, 4, 0.01) - 0.5) < 1e-12
+    assert abs(tn.cut_margin(s, 2, 0.01) - 1.0) < 1e-12      # chi = 2 caps it: only k = 1, 2 decide
+    assert tn.cut_margin(s, 4, 0.0) == math.inf
+    # a tail sitting on the cutoff (up to rounding): zero margin and the near-cutoff flag
+    s2 = np.sqrt([0.97, 0.02, 0.01, 0.0])
+    assert tn.cut_margin(s2, 4, 0.01) < 1e-12
+    assert tn.keep_count(s2, 4, 0.01)[1] == tn.NEAR_DEGENERATE
+
+
 def test_truncate_at_full_rank_is_identity():
     mps = _random_mps(5, 2, 4, seed=3)
     got, st, w = tn.truncate_svd(mps, 64)

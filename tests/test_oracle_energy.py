@@ -12,7 +12,7 @@ import math
 import numpy as np
 import pytest
 
-from paper_2503_12557_gb300.inputs import (Lattice, peps_random, configs_uniform_sz0, configs_uniform,
+from paper_2503_12557_gb300.inputs import (Lattice, csl, peps_random, configs_uniform_sz0, configs_uniform,
                                            heisenberg, j1j2_chiral, rydberg, site_offsets, theta_to_tensors)
 from oracle import energy, exact, tn
 
@@ -47,10 +47,11 @@ def test_eloc_rydberg_3x3():
     _check_eloc_exact(lat, th, H, 8, configs_uniform(lat, 8, 5))
 
 
-def test_energy_average_equals_expectation_complex():
+@pytest.mark.parametrize("model", ["j1j2_chiral", "csl"])
+def test_energy_average_equals_expectation_complex(model):
     lat = Lattice(2, 3, 2, 2)
     th = peps_random(lat, 41, complex_=True)
-    H = j1j2_chiral(lat)
+    H = j1j2_chiral(lat) if model == "j1j2_chiral" else csl(lat)
     psi = exact.state_vector(th, lat)
     Hm = exact.hamiltonian_sparse(H, lat)
     Sall = exact.index_configs(lat.nsites, 2).astype(np.uint8)
