@@ -34,7 +34,7 @@ __all__ = [
     "Lattice", "leg_dims", "num_params", "site_offsets",
     "peps_random", "theta_to_tensors", "tensors_to_theta",
     "configs_uniform_sz0", "configs_neel", "configs_uniform", "configs_constant",
-    "heisenberg", "j1j2_chiral", "rydberg", "pauli",
+    "heisenberg", "j1j2_chiral", "rydberg", "pauli", "spin_bonds", "axis_bases", "axis_parts",
     "WORKLOADS",
 ]
 
@@ -277,6 +277,45 @@ def csl(lat: Lattice, J1: float = CSL_J1, J2: float = CSL_J2, lam: float = CSL_L
             terms.append(((tr, bl), J2 * _sdots()))
             terms.append(((tl, bl, br, tr), ring.copy()))
     return {"terms": terms, "pairs": [], "onsite": np.zeros((lat.nsites, lat.d))}
+
+
+def spin_bonds(lat: Lattice, J1: float = 1.0, J2: float = 0.0):
+    """(i, j, J) for the J1 nearest-neighbour bonds and, when J2 != 0, both diagonals of every
+    plaquette with J2: the bonds of the Heisenberg-type H = sum_b J_b S_i . S_j."""
+    out = [(i, j, J1) for (i, j) in _nn_bonds(lat.Lx, lat.Ly)]
+    if J2 != 0.0:
+        Ly = lat.Ly
+        for x in range(lat.Lx - 1):
+            for y in range(Ly - 1):
+                out.append((x * Ly + y, (x + 1) * Ly + y + 1, J2))
+                out.append((x * Ly + y + 1, (x + 1) * Ly + y, J2))
+    return out
+
+
+def axis_bases():
+    """For alpha = x, y, z the unitary V_alpha whose column s is the eigenvector of sigma^alpha
+    with eigenvalue +1 (s = 0) or -1 (s = 1), so that S^alpha acts as m_s = 1/2 - s on the
+    rotated basis state |s>_alpha = V_alpha[:, s]."""
+    r = 1.0 / np.sqrt(2.0)
+    return [np.array([[r, r], [r, -r]], dtype=np.complex128),
+            np.array([[r, r], [1j * r, -1j * r]], dtype=np.complex128),
+            np.eye(2, dtype=np.complex128)]
+
+
+def axis_parts(lat: Lattice, bonds):
+    """H = sum_b J_b S_i . S_j split as H_x + H_y + H_z, H_alpha = sum_b J_b S^alpha_i S^alpha_j,
+    each written as a diagonal Hamiltonian of its own rotated basis (Sec. "On reusing
+    environments": terms diagonal in a rotated basis need no amplitude ratios).  With
+    m_s = 1/2 - s:  J m_s m_s' = J (s s' - s/2 - s'/2 + 1/4), i.e. a pair J, on-site -J/2 on
+    state 1 of both sites and +J/4 on both states of site i.  Returns [(V_alpha, H_alpha)]
+    for alpha = x, y, z, the H_alpha in this module's Hamiltonian format (no terms)."""
+    pairs = [(i, j, float(J)) for (i, j, J) in bonds]
+    onsite = np.zeros((lat.nsites, lat.d))
+    for (i, j, J) in bonds:
+        onsite[i, 1] -= 0.5 * J
+        onsite[j, 1] -= 0.5 * J
+        onsite[i, :] += 0.25 * J
+    return [(V, {"terms": [], "pairs": list(pairs), "onsite": onsite.copy()}) for V in axis_bases()]
 
 
 def rydberg(lat: Lattice, omega: float = 1.0, delta: float = 3.0, Rb: float = 1.7, rmax: float = 4.0):
