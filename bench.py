@@ -40,7 +40,7 @@ def _args():
     ap.add_argument("--ns", type=int, default=None)
     ap.add_argument("--sweeps", type=int, default=2)
     ap.add_argument("--burnin", type=int, default=2)
-    ap.add_argument("--mode", default="step", choices=["step", "learned", "gram", "batch", "complex", "bound"])
+    ap.add_argument("--mode", default="step", choices=["step", "learned", "gram", "batch", "complex", "bound", "rotated"])
     ap.add_argument("--branches", type=int, default=8)
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--cpu-samples", type=int, default=12)
@@ -592,6 +592,50 @@ def run_bound(a):
     print(json.dumps(out), flush=True)
 
 
+def run_rotated(a):
+    """Rotated-basis (unbiased) energy estimator on the bench workload's PEPS (8x8 open
+    Heisenberg, D=4, chi=16, biased Gaussian tensors): the PEPS rotated into the x, y and z
+    eigenbases of the spin (complex handle), N_s flip chains per basis for a.burnin (at least
+    10) sweeps, the diagonal part of H averaged per basis; beside it the fast estimator on
+    exchange chains of the unrotated PEPS.  Times per basis from CUDA events."""
+    import numpy as np
+    import torch
+    from paper_2503_12557_gb300 import build, estimators, inputs as I, peps as P
+    build.build()
+    w = I.WORKLOADS[WORKLOAD]
+    lat = I.Lattice(w["Lx"], w["Ly"], w["d"], w["D"])
+    ns = a.ns or 1216
+    sweeps = max(a.burnin, 10)
+    prec = P.PREC_FP32 if a.prec == "fp32" else P.PREC_FP64
+    th = torch.as_tensor(I.peps_random(lat, w["seed_theta"], **w["init"])).cuda()
+    bonds = I.spin_bonds(lat)
+    S0 = I.configs_uniform(lat, ns, w["seed_S"])
+    hc = P.PEPS(lat.Lx, lat.Ly, 2, lat.D, w["chi"], prec=prec, max_samples=ns, cplx=True)
+    estimators.rotated_basis_energy(lat.Lx, lat.Ly, lat.D, w["chi"], th, bonds, S0[:8], burn_in=1, handle=hc)  # warm-up
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    e, se, per = estimators.rotated_basis_energy(lat.Lx, lat.Ly, lat.D, w["chi"], th, bonds, S0, burn_in=sweeps,
+                                                 seed=w["seed_chain"], handle=hc)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_rot = e0.elapsed_time(e1)
+    hr = P.PEPS(lat.Lx, lat.Ly, 2, lat.D, w["chi"], prec=prec, max_samples=ns)
+    hr.set_params(th)
+    S = torch.as_tensor(I.configs_neel(lat, ns)).cuda()
+    hr.sample(S, P.MOVE_EXCHANGE, sweeps, seed=w["seed_chain"])
+    r = hr.evaluate(I.heisenberg(lat), S, want_O=False)
+    ef = r["eloc"][:, 0].double()
+    out = {"mode": "rotated", "workload": f"8x8 open Heisenberg, D=4, chi=16, N_s={ns} flip chains per basis, "
+                                          f"{sweeps} sweeps", "precision": a.prec,
+           "E_rotated_per_site": e / lat.nsites, "stderr_per_site": se / lat.nsites,
+           "per_basis": [{"basis": b, "mean": m, "stderr": s_, "acceptance": acc} for b, (m, s_, acc) in zip("xyz", per)],
+           "E_fast_per_site_exchange_chains": float(ef.mean()) / lat.nsites,
+           "stderr_fast_per_site": float(ef.std() / np.sqrt(ns)) / lat.nsites,
+           "rotated_ms_total": ms_rot, "rotated_samples_per_s": 3 * ns / (ms_rot / 1e3)}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     a = _args()
     if a.impl == "reference":
@@ -606,6 +650,8 @@ def main():
         run_complex(a)
     elif a.mode == "bound":
         run_bound(a)
+    elif a.mode == "rotated":
+        run_rotated(a)
     else:
         run_gpu(a)
 

@@ -154,10 +154,22 @@ peps_status peps_logderiv(peps_handle* h, const uint8_t* S_dev, int Ns, void* O_
                           int32_t* status_dev, void* stream);
 
 /* All of the above from one environment pass: any of logabs/phase/eloc/O may be NULL
- * (H must be non-NULL when eloc_dev is). */
+ * (H must be non-NULL when eloc_dev is).  With a diagonal H (pairs and on-site terms only)
+ * and logabs, phase and O all NULL, E_loc needs no amplitude and no contraction runs (the
+ * status bits are then all 0). */
 peps_status peps_evaluate(peps_handle* h, const peps_hamiltonian* H, const uint8_t* S_dev, int Ns,
                           double* logabs_dev, double* phase_dev, double* eloc_dev, void* O_dev,
                           int32_t* status_dev, void* stream);
+
+/* Global rotation of the physical index (Sec. "On reusing environments": a Hamiltonian term
+ * diagonal in a rotated basis is evaluated on the PEPS rotated into that basis, sampled on
+ * its own).  theta_out[site][s][l,u,r,d] = sum_t M[s][t] theta_in[site][t][l,u,r,d] over the
+ * compact N_p layout of h's lattice.  M_host: d x d complex, row major, (re, im) pairs (for the
+ * amplitudes <S_alpha|psi> in the basis |s>_alpha = V[:, s], M = V^dagger).  theta_in_dev: N_p
+ * doubles (in_cplx = 0) or N_p (re, im) pairs (in_cplx = 1); theta_out_dev: N_p (re, im) pairs
+ * (written; must not alias the input).  Feed it to a complex handle (cfg.cplx = 1). */
+peps_status peps_rotate_params(const peps_handle* h, const double* M_host, const double* theta_in_dev,
+                               int in_cplx, double* theta_out_dev, void* stream);
 
 /* Variational-bound local energy (Sec. "On Variational Upper Bound to the Ground State Energy"
  * and the appendix on variational upper bounds).  One cut i (1 <= cut <= Lx-1, the paper's

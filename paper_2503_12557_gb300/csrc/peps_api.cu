@@ -578,6 +578,13 @@ static peps_status run_eval(peps_handle* h, const peps_hamiltonian* H, const uin
     peps_status ps = set_hamiltonian(h, H, s);
     if (ps != PEPS_OK) return ps;
   }
+  if (want_e && h->tt.nterm == 0 && !O && !logabs && !phase) {
+    // a diagonal Hamiltonian and no amplitude requested: E_loc(S) needs no contraction
+    const int ts = tstart(h, TC_COMBINE, s);
+    CK(launch_combine(g, Ns, S, h->rowout, h->pairout, 0, 0, h->dg, nullptr, nullptr, eloc, s), "combine kernel");
+    tstop(h, ts, s);
+    return PEPS_OK;
+  }
   const KPlan& ke = h->kp[0];
   int ts = tstart(h, TC_ENV, s);
   CK(launch_env<T>(g, ke.p, std::min(ke.grid, Ns * (sides == 3 ? 2 : 1)), ke.smem, (const T*)h->Tpad, S, Ns, sides,
@@ -643,6 +650,22 @@ extern "C" peps_status peps_logderiv(peps_handle* h, const uint8_t* S_dev, int N
                                      void* stream) {
   if (h && !O_dev && Ns > 0) return fail(h, PEPS_E_ARG, "null output");
   return peps_evaluate(h, nullptr, S_dev, Ns, nullptr, nullptr, nullptr, O_dev, status_dev, stream);
+}
+
+// ---- global rotation of the physical index ------------------------------------------------
+extern "C" peps_status peps_rotate_params(const peps_handle* h, const double* M_host, const double* theta_in_dev,
+                                          int in_cplx, double* theta_out_dev, void* stream) {
+  peps_handle* hh = const_cast<peps_handle*>(h);
+  if (!h || !M_host || !theta_in_dev || !theta_out_dev) return fail(hh, PEPS_E_ARG, "null argument");
+  if (in_cplx != 0 && in_cplx != 1) return fail(hh, PEPS_E_ARG, "in_cplx must be 0 or 1");
+  if ((const void*)theta_in_dev == (const void*)theta_out_dev) return fail(hh, PEPS_E_ARG, "in and out must differ");
+  RotM M{};
+  const int d = h->g.d;
+  for (int i = 0; i < 2 * d * d; ++i) M.m[i] = M_host[i];
+  cudaError_t e = launch_rotate(h->g.Lx * h->g.Ly, d, h->site_off, M, theta_in_dev, in_cplx, theta_out_dev,
+                                (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(hh, e, "rotate kernel");
+  return PEPS_OK;
 }
 
 // ---- variational-bound estimator ---------------------------------------------------------

@@ -51,6 +51,10 @@ template <typename T>
 cudaError_t launch_bound(const Geo& g, const Plan& p, int grid, size_t smem, const T* Tpad, const uint8_t* S, int Ns,
                          int cut, const T* envs, const double* logs, const TermTab& tt, double* bout, double* logabs,
                          double* phase, int* status, cudaStream_t s);
+// d x d complex matrix (d <= 4), row major (re, im) pairs, passed by value
+struct RotM { double m[32]; };
+cudaError_t launch_rotate(int N, int d, const long long* site_off, const RotM& M, const double* in, int in_cplx,
+                          double* out, cudaStream_t s);
 cudaError_t launch_bound_combine(const Geo& g, int Ns, int nt, const uint8_t* S, const double* bout, const DiagTab& dg,
                                  double* eloc, cudaStream_t s);
 template <typename T>

@@ -436,6 +436,31 @@ __global__ void k_combine(Geo g, int Ns, const uint8_t* __restrict__ S, const do
     }
   }
 }
+// Global rotation of the physical index: out[site][s][c] = sum_t M[s][t] in[site][t][c] for the
+// compact parameter layout (site blocks [s][l][u][r][d]); in: real or (re, im) pairs, out:
+// (re, im) pairs.  One CTA per site (persistent over sites).
+__global__ void k_rotate_theta(int N, int d, const long long* __restrict__ site_off, RotM M,
+                               const double* __restrict__ in, int in_cplx, double* __restrict__ out) {
+  for (int site = blockIdx.x; site < N; site += gridDim.x) {
+    const long long off = site_off[site];
+    const long long blk = (site_off[site + 1] - off) / d;
+    for (long long o = threadIdx.x; o < d * blk; o += blockDim.x) {
+      const int s = (int)(o / blk);
+      const long long c = o % blk;
+      double re = 0.0, im = 0.0;
+      for (int t = 0; t < d; ++t) {
+        const long long k = off + t * blk + c;
+        const double xr = in_cplx ? in[2 * k] : in[k], xi = in_cplx ? in[2 * k + 1] : 0.0;
+        const double mr = M.m[2 * (s * d + t)], mi = M.m[2 * (s * d + t) + 1];
+        re += mr * xr - mi * xi;
+        im += mr * xi + mi * xr;
+      }
+      out[2 * (off + o)] = re;
+      out[2 * (off + o) + 1] = im;
+    }
+  }
+}
+
 // E_loc^bound = diagonal pairs + on-site terms + the per-term sums of k_bound.  One warp per sample.
 __global__ void k_bound_combine(Geo g, int Ns, int nt, const uint8_t* __restrict__ S, const double* bout, DiagTab dg,
                                 double* eloc) {
@@ -921,6 +946,11 @@ PEPS_KATTR(kattr_bound, k_bound)
 #endif
 
 #ifdef PEPS_DEFINE_COMMON
+cudaError_t launch_rotate(int N, int d, const long long* site_off, const RotM& M, const double* in, int in_cplx,
+                          double* out, cudaStream_t s) {
+  k_rotate_theta<<<N < 1024 ? N : 1024, 256, 0, s>>>(N, d, site_off, M, in, in_cplx, out);
+  return cudaGetLastError();
+}
 cudaError_t launch_bound_combine(const Geo& g, int Ns, int nt, const uint8_t* S, const double* bout, const DiagTab& dg,
                                  double* eloc, cudaStream_t s) {
   const int blocks = (Ns * 32 + 255) / 256;

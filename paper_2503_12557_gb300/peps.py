@@ -68,6 +68,7 @@ def load():
         "peps_logderiv": ([vp, vp, i32, vp, vp, vp], i32),
         "peps_evaluate": ([vp, C.POINTER(_Ham), vp, i32, vp, vp, vp, vp, vp, vp], i32),
         "peps_local_energy_bound": ([vp, C.POINTER(_Ham), vp, i32, i32, vp, vp, vp, vp, vp], i32),
+        "peps_rotate_params": ([vp, vp, vp, i32, vp, vp], i32),
         "minsr_step": ([vp, vp, vp, vp, i32, dbl, dbl, dbl, vp, vp, vp], i32),
         "peps_sample": ([vp, i32, vp, i32, i32, C.c_uint64, C.c_uint64, vp, vp, vp], i32),
         "peps_last_error": ([vp], C.c_char_p),
@@ -97,7 +98,7 @@ def exported_symbols():
             "peps_timing_enable", "peps_timing_read", "peps_apply_update", "peps_proposal_logits",
             "peps_proposal_train_step", "peps_sample_learned", "peps_amplitudes_noalloc", "peps_probe_fma",
             "peps_autotune", "peps_batch_create", "peps_batch_launch", "peps_batch_destroy",
-            "peps_local_energy_bound"]
+            "peps_local_energy_bound", "peps_rotate_params"]
 
 
 def probe_fma(fp64=False):
@@ -322,6 +323,19 @@ class PEPS:
         self._check(self.L.peps_local_energy_bound(self.h, C.byref(hc.c), _ptr(S), ns, int(cut), _ptr(e), _ptr(la),
                                                    _ptr(ph), _ptr(st), _stream()), "peps_local_energy_bound")
         return dict(eloc=e, logabs=la, phase=ph, status=st)
+
+    def rotate_params(self, M, theta):
+        """theta' (complex128, N_p) with the physical index of every site tensor multiplied by the
+        d x d matrix M; theta: a device tensor, real or complex."""
+        M = np.ascontiguousarray(np.asarray(M, dtype=np.complex128))
+        assert M.shape == (self.d, self.d)
+        Mh = np.ascontiguousarray(M.view(np.float64).reshape(-1))
+        cplx_in = 1 if theta.is_complex() else 0
+        theta = theta.to(torch.complex128 if cplx_in else torch.float64).contiguous()
+        out = torch.empty(self.Np, dtype=torch.complex128, device=theta.device)
+        self._check(self.L.peps_rotate_params(self.h, Mh.ctypes.data, _ptr(theta), cplx_in, _ptr(out), _stream()),
+                    "peps_rotate_params")
+        return out
 
     def minsr_step(self, O, eloc, w=None, lam=1e-4, rcond=0.0, tau=0.05):
         ns = O.shape[0]
