@@ -88,13 +88,17 @@ def _row_walk(Trow, eu, dl, Srow=None, key=None, ctr=None):
     R = [None] * (Ly + 1)
     R[Ly] = np.ones((1, 1, 1), dtype=np.result_type(K[0], Dg[0]))
     for y in range(Ly - 1, -1, -1):
-        t = np.einsum("AsdB,cdDe,asDb,Beb->Aca", K[y], Dg[y], np.conj(K[y]), R[y + 1], optimize=True)
+        t = np.einsum("AsdB,Beb->Asdeb", K[y], R[y + 1])          # pairwise stages: a
+        t = np.einsum("Asdeb,cdDe->AscDb", t, Dg[y])               # contraction order chosen
+        t = np.einsum("AscDb,asDb->Aca", t, np.conj(K[y]))         # for small intermediates
         m = float(np.max(np.abs(t)))
         R[y] = t / m if m > 0 else t
     L = np.ones((1, 1, 1), dtype=R[Ly].dtype)
     states, logp, zero = [], 0.0, False
     for y in range(Ly):
-        cand = np.einsum("Aca,AsdB,cdDe,asDb->sBeb", L, K[y], Dg[y], np.conj(K[y]), optimize=True)
+        t = np.einsum("Aca,AsdB->casdB", L, K[y])
+        t = np.einsum("casdB,cdDe->asDeB", t, Dg[y])
+        cand = np.einsum("asDeB,asDb->sBeb", t, np.conj(K[y]))
         w = np.array([max(0.0, float(np.real(np.sum(cand[s] * R[y + 1])))) for s in range(cand.shape[0])])
         tot = float(np.sum(w))
         if not tot > 0.0:
