@@ -40,7 +40,7 @@ def _args():
     ap.add_argument("--ns", type=int, default=None)
     ap.add_argument("--sweeps", type=int, default=2)
     ap.add_argument("--burnin", type=int, default=2)
-    ap.add_argument("--mode", default="step", choices=["step", "learned", "gram", "batch", "complex", "bound", "rotated"])
+    ap.add_argument("--mode", default="step", choices=["step", "learned", "gram", "batch", "complex", "bound", "rotated", "direct"])
     ap.add_argument("--branches", type=int, default=8)
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--cpu-samples", type=int, default=12)
@@ -636,6 +636,55 @@ def run_rotated(a):
     print(json.dumps(out), flush=True)
 
 
+def run_direct(a):
+    """Direct sampling on the bench workload (8x8 open Heisenberg, D=4, chi=16, biased Gaussian
+    tensors): double-layer environments at chi_d = D = 4 (the paper's D_c^double ~ D), N_s
+    independent configurations drawn row by row, then psi and E_loc of the drawn
+    configurations; the importance-weighted energy with weights |psi|^2 / p, its effective
+    sample size, and the times of each part (CUDA events of the library's timing record)."""
+    import numpy as np
+    import torch
+    from paper_2503_12557_gb300 import build, inputs as I, peps as P
+    build.build()
+    w = I.WORKLOADS[WORKLOAD]
+    lat = I.Lattice(w["Lx"], w["Ly"], w["d"], w["D"])
+    ns = a.ns or 4096
+    chid = lat.D
+    prec = P.PREC_FP32 if a.prec == "fp32" else P.PREC_FP64
+    H = I.heisenberg(lat)
+    h = P.PEPS(lat.Lx, lat.Ly, lat.d, lat.D, w["chi"], prec=prec, max_samples=ns)
+    h.set_params(torch.as_tensor(I.peps_random(lat, w["seed_theta"], **w["init"])).cuda())
+    h.direct_prepare(chid)
+    h.direct_sample(min(ns, 8), seed=w["seed_chain"], draw=0)  # warm-up
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    h.direct_prepare(chid)
+    e1.record()
+    torch.cuda.synchronize()
+    prep_ms = e0.elapsed_time(e1)
+    h.timing(True)
+    S, lp, st = h.direct_sample(ns, seed=w["seed_chain"], draw=1)
+    r = h.evaluate(H, S, want_O=False)
+    torch.cuda.synchronize()
+    ms, la, _ = h.timing_read()
+    h.timing(False)
+    lw = (2 * r["logabs"] - lp).cpu().numpy()
+    e = r["eloc"][:, 0].cpu().numpy()
+    wt = np.exp(lw - lw.max())
+    wt /= wt.sum()
+    est = float(np.sum(wt * e))
+    ess = float(1.0 / np.sum(wt ** 2))
+    out = {"mode": "direct", "workload": f"8x8 open Heisenberg, D=4, chi=16, chi_d={chid}, N_s={ns}",
+           "precision": a.prec, "double_layer_prepare_ms": prep_ms, "direct_sample_ms": ms["direct"], "eval_ms": ms["env"] + ms["row"] + ms["pair"] + ms["combine"],
+           "direct_samples_per_s": ns / (ms["direct"] / 1e3), "launches": {"direct": la["direct"]},
+           "E_weighted_per_site": est / lat.nsites,
+           "stderr_per_site": float(np.sqrt(np.sum(wt ** 2 * (e - est) ** 2))) / lat.nsites,
+           "ess": ess, "ess_fraction": ess / ns, "ess_per_s": ess / ((ms["direct"] + ms["env"] + ms["row"] + ms["pair"]) / 1e3),
+           "status_nonzero": int((st != 0).sum().item()), "distinct_configurations": int(len(set(map(bytes, S.cpu().numpy()))))}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     a = _args()
     if a.impl == "reference":
@@ -652,6 +701,8 @@ def main():
         run_bound(a)
     elif a.mode == "rotated":
         run_rotated(a)
+    elif a.mode == "direct":
+        run_direct(a)
     else:
         run_gpu(a)
 

@@ -161,6 +161,25 @@ peps_status peps_evaluate(peps_handle* h, const peps_hamiltonian* H, const uint8
                           double* logabs_dev, double* phase_dev, double* eloc_dev, void* O_dev,
                           int32_t* status_dev, void* stream);
 
+/* Direct sampling (Sec. "On Direct Sampling" and the appendix "Direct sampling of PEPS",
+ * Alg. `sampling`): independent configurations drawn row by row from the conditional reduced
+ * density matrix rho_{S<i}[i] = T^u . D^l[i+1] . T^u*, with T^u = E^u[i-1](S) . T[i] (kept
+ * exact) and D^l the double-layer lower boundary MPS.
+ * peps_direct_prepare builds D^l[2..Lx] for the parameters last set (one CTA; once per
+ * parameter set, reused by every later peps_direct_sample), compressed to chi_double
+ * (1 <= chi_double, chi_double D^2 <= 1024; the paper's D_c^double ~ D).  Environments from
+ * earlier parameters are allowed: p(S) stays a normalised distribution and the importance
+ * weights |psi(S)|^2 / p(S) correct for them. */
+peps_status peps_direct_prepare(peps_handle* h, int chi_double, void* stream);
+/* peps_direct_sample: Ns configurations (S_dev: Ns x Lx Ly, written) and log p(S) (logp_dev:
+ * Ns doubles, the sum of the logs of the drawn conditionals), chain c of draw round `draw`
+ * taking its uniforms from Philox4x32-10 at counters (x Ly + y, draw, c, 2) with key seed.
+ * A conditional weight below zero (truncated D^l) counts as zero; a site whose weights all
+ * vanish is drawn uniformly and sets PEPS_ST_ZERO_NORM.  Ns <= cfg.max_samples.  The
+ * importance weight of S for the estimators is |psi(S)|^2 / p(S) (psi from peps_amplitudes). */
+peps_status peps_direct_sample(peps_handle* h, uint8_t* S_dev, int Ns, uint64_t seed, uint64_t draw,
+                               double* logp_dev, int32_t* status_dev, void* stream);
+
 /* Global rotation of the physical index (Sec. "On reusing environments": a Hamiltonian term
  * diagonal in a rotated basis is evaluated on the PEPS rotated into that basis, sampled on
  * its own).  theta_out[site][s][l,u,r,d] = sum_t M[s][t] theta_in[site][t][l,u,r,d] over the

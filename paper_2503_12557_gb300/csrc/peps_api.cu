@@ -43,6 +43,16 @@ struct peps_handle {
   KPlan kb;     // variational-bound estimator (row-step buffers of the env budget)
   double* bout = nullptr;  // k_bound's per-(sample, term) sums
   size_t bout_cap = 0;
+  // direct sampling: double-layer environments, their work buffers, the sampler's plan and arena
+  int dl_chid = 0;
+  void* DL = nullptr;
+  size_t DL_bytes = 0;
+  void* dl_work = nullptr;
+  size_t dl_work_bytes = 0;
+  int* dl_status = nullptr;
+  KPlan kd;
+  char* dscratch = nullptr;
+  size_t dscratch_bytes = 0;
   // Hamiltonian cache
   std::vector<char> ham_key;
   std::vector<int> h_tinfo, h_ab, h_rowoff, h_pairoff, h_pij;
@@ -89,7 +99,7 @@ static auto dispatch_elem(const peps_handle* h, F&& f) {
   }
 }
 
-enum { TC_ENV = 0, TC_ROW, TC_PAIR, TC_COMBINE, TC_SAMPLE, TC_GRAM, TC_EIG, TC_MINSR, TC_PAD, TC_BOUND, TC_N };
+enum { TC_ENV = 0, TC_ROW, TC_PAIR, TC_COMBINE, TC_SAMPLE, TC_GRAM, TC_EIG, TC_MINSR, TC_PAD, TC_BOUND, TC_DIRECT, TC_N };
 
 // Record a start event for kernel class c (returns the slot, or -1 when timing is off).
 static int tstart(peps_handle* h, int c, cudaStream_t s) {
@@ -401,7 +411,8 @@ extern "C" peps_status peps_destroy(peps_handle* h) {
   void* ptrs[] = {h->Tpad, h->site_off, h->envs, h->logs, h->wdisc, h->rowout, h->pairout, h->status_tmp,
                   h->gscratch, h->d_tinfo, h->d_ab, h->d_eh, h->d_rowoff, h->d_pairoff, h->d_pij, h->d_pv,
                   h->d_onsite, h->Obar, h->Tm, h->Vm, h->Hm, h->mean, h->ebar, h->yv, h->xv, h->cnt, h->ctr,
-                  h->lp_Sp, h->lp_l0, h->lp_l1, h->lp_aux, h->g_hi, h->g_lo, h->bout};
+                  h->lp_Sp, h->lp_l0, h->lp_l1, h->lp_aux, h->g_hi, h->g_lo, h->bout, h->DL, h->dl_work,
+                  h->dl_status, h->dscratch};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t e : h->evpool) cudaEventDestroy(e);
@@ -650,6 +661,121 @@ extern "C" peps_status peps_logderiv(peps_handle* h, const uint8_t* S_dev, int N
                                      void* stream) {
   if (h && !O_dev && Ns > 0) return fail(h, PEPS_E_ARG, "null output");
   return peps_evaluate(h, nullptr, S_dev, Ns, nullptr, nullptr, nullptr, O_dev, status_dev, stream);
+}
+
+// ---- direct sampling ---------------------------------------------------------------------
+static std::mutex g_direct_mu;
+static std::map<std::pair<int, int>, size_t> g_direct_attr;
+
+extern "C" peps_status peps_direct_prepare(peps_handle* h, int chi_double, void* stream) {
+  if (!h) return PEPS_E_ARG;
+  const Geo& g = h->g;
+  const int D = g.D, Ly = g.Ly, Lx = g.Lx;
+  if (chi_double < 1 || chi_double * D * D > 1024) return fail(h, PEPS_E_ARG, "chi_double outside 1 .. 1024 / D^2");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t E = h->esz;
+  const DlDims dd = dl_dims(D, chi_double);
+  const size_t sd = (size_t)chi_double * dd.P * chi_double;
+  // double-layer rows and the compression's work buffers
+  const size_t dlb = (size_t)(Lx + 1) * Ly * sd * E;
+  size_t n8[8];
+  dl_work_elems(Ly, D, chi_double, n8);
+  size_t wb = 0;
+  for (int i = 0; i < 8; ++i) wb += al(n8[i] * E);
+  if (dlb > h->DL_bytes) {
+    if (h->DL) cudaFree(h->DL);
+    h->DL = nullptr;
+    h->DL_bytes = 0;
+    if (cudaMalloc(&h->DL, dlb) != cudaSuccess) return fail(h, PEPS_E_WORKSPACE, "double-layer environments");
+    h->DL_bytes = dlb;
+  }
+  if (wb > h->dl_work_bytes) {
+    if (h->dl_work) cudaFree(h->dl_work);
+    h->dl_work = nullptr;
+    h->dl_work_bytes = 0;
+    if (cudaMalloc(&h->dl_work, wb) != cudaSuccess) return fail(h, PEPS_E_WORKSPACE, "double-layer work buffers");
+    h->dl_work_bytes = wb;
+  }
+  if (!h->dl_status && cudaMalloc(&h->dl_status, sizeof(int)) != cudaSuccess)
+    return fail(h, PEPS_E_WORKSPACE, "status");
+  // the sampler's buffer plan: the row step's buffers, then the configuration, two E^u rows,
+  // the ket sites (two layouts), the right partials and the contraction temporaries
+  const int n = g.n, chi = g.chi, mX = n + (n & 1), ci = std::min(n, 8);
+  const size_t AB = (size_t)chi * D, rsz = AB * chi_double * AB, ksz = (size_t)g.d * D * AB * AB;
+  const size_t tsz = (size_t)g.d * D * chi_double * AB * AB;
+  KPlan& k = h->kd;
+  k.p.ci = ci;
+  k.p.cx = h->kp[0].p.cx;
+  std::vector<std::pair<int, size_t>> b = {
+      {B_RED, 40 * 8}, {B_SIG, (mX + 4) * E}, {B_SEL, 2 * mX * 4}, {B_A, (size_t)g.sT * E}, {B_E, (size_t)g.se * E},
+      {B_C, (size_t)n * chi * E}, {B_W, env_w_elems(chi, D, ci) * E}, {B_R, (size_t)n * n * E},
+      {B_Z, env_z_elems(chi, D) * E}, {B_RHIST, (size_t)std::max(1, Ly - 1) * n * n * E}, {B_S, (size_t)Lx * Ly},
+      {B_EU, (size_t)2 * Ly * g.se * E}, {B_LW2, (size_t)(g.d + 1) * rsz * E}, {B_RP, (size_t)(Ly + 1) * rsz * E},
+      {B_LP, tsz * E}, {B_LW, tsz * E}, {B_T1, (size_t)Ly * ksz * E}, {B_T2, (size_t)Ly * ksz * E}};
+  place(k.p, k.smem, h->budget[0], b);
+  cudaError_t e = cudaSuccess;
+  {
+    std::lock_guard<std::mutex> lk(g_direct_mu);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    size_t& cur = g_direct_attr[{h->elem, dev}];
+    if (k.smem > cur) {
+      e = dispatch_elem(h, [&](auto z) { return kattr_direct<decltype(z)>(g, k.smem, nullptr, 0); });
+      if (e == cudaSuccess) cur = k.smem;
+    }
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaFuncSetAttribute (direct)");
+  int occ = 0;
+  e = dispatch_elem(h, [&](auto z) { return kattr_direct<decltype(z)>(g, 0, &occ, k.smem); });
+  if (e != cudaSuccess || occ < 1) return fail(h, PEPS_E_SHAPE, "direct-sampling kernel does not fit on an SM");
+  k.grid = h->nsm * occ;
+  const size_t ab = (size_t)k.grid * k.p.gstride;
+  if (ab > h->dscratch_bytes) {
+    if (h->dscratch) cudaFree(h->dscratch);
+    h->dscratch = nullptr;
+    h->dscratch_bytes = 0;
+    if (cudaMalloc(&h->dscratch, ab) != cudaSuccess) return fail(h, PEPS_E_WORKSPACE, "direct-sampling arena");
+    h->dscratch_bytes = ab;
+  }
+  k.p.gbase = h->dscratch;
+  k.p.ctr = h->ctr;
+  h->dl_chid = chi_double;
+  const int ts = tstart(h, TC_DIRECT, s);
+  e = dispatch_elem(h, [&](auto z) {
+    using T = decltype(z);
+    DlWork<T> w;
+    T** ptrs[8] = {&w.B, &w.Rh, &w.Z, &w.Y, &w.X, &w.Vt, &w.C, &w.Cn};
+    char* base = (char*)h->dl_work;
+    for (int i = 0; i < 8; ++i) {
+      *ptrs[i] = (T*)base;
+      base += al(n8[i] * E);
+    }
+    return launch_dl_env<T>(g, chi_double, (const T*)h->Tpad, (T*)h->DL, w, h->dl_status, s);
+  });
+  if (e != cudaSuccess) return cuda_fail(h, e, "double-layer kernel");
+  tstop(h, ts, s);
+  return PEPS_OK;
+}
+
+extern "C" peps_status peps_direct_sample(peps_handle* h, uint8_t* S_dev, int Ns, uint64_t seed, uint64_t draw,
+                                          double* logp_dev, int32_t* status_dev, void* stream) {
+  peps_status c = check_eval(h, S_dev, Ns);
+  if (c != PEPS_OK) return c;
+  if (!h->DL || h->dl_chid < 1) return fail(h, PEPS_E_ARG, "peps_direct_prepare has not been called");
+  if (!logp_dev && Ns > 0) return fail(h, PEPS_E_ARG, "null log p output");
+  cudaStream_t s = (cudaStream_t)stream;
+  int* st = status_dev ? (int*)status_dev : h->status_tmp;
+  if (Ns == 0) return PEPS_OK;
+  const KPlan& k = h->kd;
+  const int ts = tstart(h, TC_DIRECT, s);
+  cudaError_t e = dispatch_elem(h, [&](auto z) {
+    using T = decltype(z);
+    return launch_direct<T>(h->g, k.p, std::min(k.grid, Ns), k.smem, h->dl_chid, (const T*)h->Tpad, (const T*)h->DL,
+                            S_dev, Ns, seed, draw, logp_dev, st, s);
+  });
+  if (e != cudaSuccess) return cuda_fail(h, e, "direct-sampling kernel");
+  tstop(h, ts, s);
+  return PEPS_OK;
 }
 
 // ---- global rotation of the physical index ------------------------------------------------

@@ -1,0 +1,428 @@
+// Direct sampling of a finite PEPS (Sec. "On Direct Sampling", appendix "Direct sampling of
+// PEPS", Alg. `sampling`): double-layer lower boundary MPS D^l built once per parameter set,
+// then every configuration drawn row by row from the conditional reduced density matrix
+//   rho_{S<i}[i] = T^u_{S<i}[i] . D^l[i+1] . (T^u_{S<i}[i])^*,
+// T^u = E^u[i-1](S) . T[i] with the physical legs open (kept exact), sites left to right.
+// Included by peps_direct_{f32,f64,c32,c64}.cu, one scalar type each.
+#pragma once
+#include "peps_kernels_impl.cuh"
+
+namespace peps {
+
+// ------------------------------------------------------------------------------------------
+// Double-layer lower environments D^l[x], x = Lx .. 1 (0-based rows x .. Lx-1 traced), one CTA.
+// D^l[x] site y: [c][(u, u')][e] (chi_d x D^2 x chi_d, padded), (u, u') the up legs of row x
+// in the ket and the bra; D^l[Lx] is the trivial row.  Row x: the exact product
+//   B_y[(c, L)][U][(f, R)] = sum_{p=(d,d')} D^l[x+1]_y[c][p][f] M_y[L][U][R][p],
+//   M_y[(l,l')][(u,u')][(r,r')][(d,d')] = sum_s T[s][l][u][r][d] conj(T[s][l'][u'][r'][d']),
+// compressed to chi_d by the QR-based density-matrix truncation (left pass: R factors of
+// R_{k-1} B_k; right pass: one-sided Jacobi of X = R_{k-1} Y_k, the top chi_d right singular
+// vectors kept), every site divided by its largest modulus.  *status: status bits.
+template <typename T, typename G>
+__global__ void __launch_bounds__(NTHREADS) k_dl_env(G g, int chid, const T* __restrict__ Tpad, T* DL, DlWork<T> w,
+                                                     int* status) {
+  using RT = typename Scal<T>::R;
+  extern __shared__ __align__(16) char smem[];
+  const DlDims dd = dl_dims(g.D, chid);
+  double* red = (double*)smem;
+  RT* sig = (RT*)(smem + 40 * 8);
+  size_t off = 40 * 8 + (size_t)(dd.mX + 4) * sizeof(RT);
+  off = (off + 15) / 16 * 16;
+  int* sel = (int*)(smem + off);
+  off += (size_t)2 * dd.mX * 4;
+  off = (off + 15) / 16 * 16;
+  T* taus = (T*)(smem + off);
+  __shared__ int st, flag;
+  const int tid = threadIdx.x, NT = blockDim.x;
+  const int Ly = g.Ly, D = g.D, d = g.d, P = dd.P, nb = dd.nb, Lr = dd.Lr, LY = dd.LY, LX = dd.LX, mX = dd.mX;
+  const size_t sd = (size_t)chid * P * chid, rowsz = (size_t)Ly * sd, bsz = (size_t)nb * P * nb;
+  if (tid == 0) st = 0;
+  T* last = DL + (size_t)g.Lx * rowsz;
+  for (int k = 0; k < Ly; ++k) blk_unit(last + (size_t)k * sd, (int)sd);
+  __syncthreads();
+  for (int x = g.Lx - 1; x >= 1; --x) {
+    const T* Dn = DL + (size_t)(x + 1) * rowsz;
+    T* Dx = DL + (size_t)x * rowsz;
+    // ---- exact double-layer product
+    for (int y = 0; y < Ly; ++y) {
+      const T* Ts = Tpad + (size_t)(x * Ly + y) * d * g.sT;
+      const T* Dy = Dn + (size_t)y * sd;
+      T* By = w.B + (size_t)y * bsz;
+      for (size_t o = tid; o < bsz; o += NT) {
+        const int b = (int)(o % nb), U = (int)((o / nb) % P), a = (int)(o / ((size_t)nb * P));
+        const int c = a / P, L = a % P, f = b / P, R = b % P;
+        const int l = L / D, l2 = L % D, u = U / D, u2 = U % D, r = R / D, r2 = R % D;
+        T acc = T(0);
+        for (int p = 0; p < P; ++p) {
+          const T dv = Dy[((size_t)c * P + p) * chid + f];
+          if (dv == T(0)) continue;
+          const int dn = p / D, dn2 = p % D;
+          T m = T(0);
+          for (int s = 0; s < d; ++s)
+            m += Ts[(size_t)s * g.sT + ((l * D + u) * D + r) * D + dn] *
+                 conj_(Ts[(size_t)s * g.sT + ((l2 * D + u2) * D + r2) * D + dn2]);
+          acc += dv * m;
+        }
+        By[o] = acc;
+      }
+    }
+    __syncthreads();
+    // ---- left pass: R_k from the QR of Z = R_{k-1} B_k ((i, p) rows, b columns; column major)
+    const int mZ = nb * P;
+    for (int k = 0; k + 1 < Ly; ++k) {
+      const T* Bk = w.B + (size_t)k * bsz;
+      const T* Rp = w.Rh + (size_t)(k - 1) * nb * nb;
+      for (size_t o = tid; o < (size_t)mZ * nb; o += NT) {
+        const int row = (int)(o % mZ), b = (int)(o / mZ);
+        const int i = row / P, p = row % P;
+        T acc = T(0);
+        if (k == 0) {
+          if (i == 0) acc = Bk[(size_t)p * nb + b];   // R_{-1} = e_00: the left boundary bond
+        } else {
+          for (int a = i; a < nb; ++a) acc += Rp[(size_t)i * nb + a] * Bk[((size_t)a * P + p) * nb + b];
+        }
+        w.Z[o] = acc;
+      }
+      __syncthreads();
+      qr_keep_r_smem(w.Z, mZ, nb, w.Rh + (size_t)k * nb * nb, taus);
+    }
+    // ---- right pass
+    blk_unit(w.C, nb * chid);
+    __syncthreads();
+    for (int k = Ly - 1; k >= 0; --k) {
+      const T* Bk = w.B + (size_t)k * bsz;
+      // Y[a][(p, c)] = sum_b B_k[a][p][b] C[b][c]
+      for (int o = tid; o < nb * Lr; o += NT) {
+        const int c = o % chid, p = (o / chid) % P, a = o / Lr;
+        const T* Br = Bk + ((size_t)a * P + p) * nb;
+        T acc = T(0);
+        for (int b = 0; b < nb; ++b) acc += Br[b] * w.C[(size_t)b * chid + c];
+        w.Y[(size_t)a * LY + p * chid + c] = acc;
+      }
+      __syncthreads();
+      T* site = Dx + (size_t)k * sd;
+      if (k == 0) {
+        // first site: its left bond is trivial, keep row a = 0 of Y
+        for (int o = tid; o < (int)sd; o += NT) {
+          const int c = o % chid, p = (o / chid) % P, ap = o / (P * chid);
+          site[o] = (ap == 0) ? w.Y[p * chid + c] : T(0);
+        }
+        __syncthreads();
+        blk_normalize(site, (int)sd, red, &st);
+        break;
+      }
+      const T* Rp = w.Rh + (size_t)(k - 1) * nb * nb;
+      for (int o = tid; o < mX * Lr; o += NT) {
+        const int q = o % Lr, i = o / Lr;
+        T acc = T(0);
+        if (i < nb)
+          for (int j = i; j < nb; ++j) acc += Rp[(size_t)i * nb + j] * w.Y[(size_t)j * LY + q];
+        w.X[(size_t)i * LX + q] = acc;
+      }
+      __syncthreads();
+      const int sweeps = hestenes_rows<T, 0>(w.X, mX, Lr, LX, &flag, nullptr, red, sig);
+      if (sweeps < 0 && tid == 0) st |= ST_NOCONV;
+      {
+        const int lane = tid & 31, warp = tid >> 5, nw = NT >> 5;
+        for (int p = warp; p < mX; p += nw) {
+          RT s = 0;
+          for (int i = lane; i < Lr; i += 32) s += abs2_(w.X[(size_t)p * LX + i]);
+          s = warp_sum(s);
+          if (lane == 0) sig[p] = sqrt(s);
+        }
+      }
+      __syncthreads();
+      // stable descending ranks (NaN below every number)
+      for (int p = tid; p < mX; p += NT) {
+        const RT sp = sig[p];
+        const RT kp = (sp == sp) ? sp : RT(-1);
+        if (!(sp == sp) || isinf(sp)) atomicOr(&st, (int)ST_NONFINITE);
+        int rk = 0;
+        for (int q = 0; q < mX; ++q) {
+          const RT sq = sig[q];
+          const RT kq = (sq == sq) ? sq : RT(-1);
+          rk += (kq > kp) || (kq == kp && q < p);
+        }
+        if (rk < chid) sel[rk] = p;
+      }
+      __syncthreads();
+      const int nkeep = (mX < chid) ? mX : chid;
+      // Vt[c'][q] = X[sel(c')][q] / sigma: the kept rows of V^H
+      for (int o = tid; o < chid * Lr; o += NT) {
+        const int q = o % Lr, cp = o / Lr;
+        T v = T(0);
+        if (cp < nkeep) {
+          const int p = sel[cp];
+          const RT s = sig[p];
+          if (s > RT(0)) v = w.X[(size_t)p * LX + q] * (RT(1) / s);
+        }
+        w.Vt[(size_t)cp * LY + q] = v;
+      }
+      __syncthreads();
+      for (int o = tid; o < nb * chid; o += NT) {
+        const int cp = o % chid, j = o / chid;
+        T acc = T(0);
+        for (int q = 0; q < Lr; ++q) acc = mad(acc, w.Y[(size_t)j * LY + q], conj_(w.Vt[(size_t)cp * LY + q]));
+        w.Cn[o] = acc;
+      }
+      for (int o = tid; o < (int)sd; o += NT) site[o] = w.Vt[(size_t)(o / Lr) * LY + o % Lr];
+      __syncthreads();
+      blk_normalize(site, (int)sd, red, &st);
+      blk_copy(w.C, w.Cn, nb * chid);
+      __syncthreads();
+    }
+  }
+  if (tid == 0) *status = st;
+}
+
+// ------------------------------------------------------------------------------------------
+// Direct sampling: one CTA per configuration (persistent).  Row x of chain c in draw round t:
+//   K_y[s][dd][B][A] = sum_u E^u[x-1]_y[a][u][b] T[s][l][u][r][dd]   (A = (a, l), B = (b, r)),
+//   the ket sites of T^u, also stored as K2_y[s][dd][A][B];
+//   right partials with the physical legs traced, R_y[A][c][A'] (c the D^l bond), from the
+//   right; then left to right, for every candidate s of site y,
+//   cand_s[B][e][B'] = sum L[A][c][A'] K[A][s][d][B] D^l[c][(d, d')][e] conj(K[A'][s][d'][B']),
+//   w_s = Re <cand_s, R_{y+1}> (negative weights count as zero), s drawn with
+//   u = uniform53(Philox(x Ly + y, t, c, 2; seed)), L = cand_s normalised.  After the row,
+//   E^u[x] = truncate_chi(E^u[x-1] . T_proj[x]) by the environment kernels' row step.
+// logp[c] = sum of the logs of the drawn conditionals (FP64).
+template <typename T, typename G>
+__global__ void __launch_bounds__(NTHREADS) k_direct(G g, Plan plan, int chid, const T* __restrict__ Tpad,
+                                                     const T* __restrict__ DL, uint8_t* S, int Ns,
+                                                     unsigned long long seed, unsigned long long draw, double* logp,
+                                                     int* status) {
+  extern __shared__ __align__(16) char smem[];
+  char* gbase = plan.gbase;
+  RowWork<T> w = carve_row<T>(plan, smem, gbase);
+  uint8_t* Sl = (uint8_t*)buf_ptr(plan, B_S, smem, gbase);
+  T* EU = (T*)buf_ptr(plan, B_EU, smem, gbase);    // two E^u rows, used alternately
+  T* KT = (T*)buf_ptr(plan, B_T1, smem, gbase);    // Ly x [s][dd][B][A]
+  T* K2 = (T*)buf_ptr(plan, B_T2, smem, gbase);    // Ly x [s][dd][A][B]
+  T* RP = (T*)buf_ptr(plan, B_RP, smem, gbase);    // (Ly+1) x [A][c][A']
+  T* V1 = (T*)buf_ptr(plan, B_LP, smem, gbase);
+  T* V2 = (T*)buf_ptr(plan, B_LW, smem, gbase);
+  T* LC = (T*)buf_ptr(plan, B_LW2, smem, gbase);   // d candidates + the running left partial
+  double* red = w.red;
+  __shared__ int st, flag;
+  __shared__ float wd;
+  __shared__ double pw[8];
+  __shared__ int pick;
+  const int tid = threadIdx.x, NT = blockDim.x;
+  const int Ly = g.Ly, Lx = g.Lx, D = g.D, d = g.d, chi = g.chi, N = Lx * Ly;
+  const int AB = chi * D, P = D * D;
+  const size_t rowsz = (size_t)Ly * g.se, sd = (size_t)chid * P * chid;
+  const size_t ksz = (size_t)d * D * AB * AB, rsz = (size_t)AB * chid * AB;
+  T* Lp = LC + (size_t)d * rsz;
+  for (int c = blockIdx.x; c < Ns; c += gridDim.x) {
+    if (tid == 0) { st = 0; wd = 0.f; }
+    // E^u[-1]: the trivial row
+    for (int k = 0; k < Ly; ++k) blk_unit(EU + (size_t)k * g.se, g.se);
+    __syncthreads();
+    double lp = 0.0;
+    int cur = 0;
+    for (int x = 0; x < Lx; ++x) {
+      const T* Eu = EU + (size_t)cur * rowsz;
+      const T* Dn = DL + (size_t)(x + 1) * Ly * sd;
+      // ket sites of T^u
+      for (int y = 0; y < Ly; ++y) {
+        const T* Ts = Tpad + (size_t)(x * Ly + y) * d * g.sT;
+        const T* E = Eu + (size_t)y * g.se;
+        T* Ky = KT + (size_t)y * ksz;
+        T* K2y = K2 + (size_t)y * ksz;
+        for (size_t o = tid; o < ksz; o += NT) {
+          // o = ((s * D + dd) * AB + B) * AB + A
+          const int A = (int)(o % AB), B = (int)((o / AB) % AB), dd = (int)((o / ((size_t)AB * AB)) % D),
+                    s = (int)(o / ((size_t)AB * AB * D));
+          const int a = A / D, l = A % D, b = B / D, r = B % D;
+          T acc = T(0);
+          for (int u = 0; u < D; ++u)
+            acc += E[((size_t)a * D + u) * chi + b] * Ts[(size_t)s * g.sT + ((l * D + u) * D + r) * D + dd];
+          Ky[o] = acc;
+          K2y[(((size_t)s * D + dd) * AB + A) * AB + B] = acc;
+        }
+      }
+      // right partials, physical legs traced
+      T* Rl = RP + (size_t)Ly * rsz;
+      blk_unit(Rl, (int)rsz);
+      __syncthreads();
+      for (int y = Ly - 1; y >= 0; --y) {
+        const T* Ky = KT + (size_t)y * ksz;
+        const T* Dg = Dn + (size_t)y * sd;
+        const T* Rn = RP + (size_t)(y + 1) * rsz;
+        // V1[A][s][dd][e][B'] = sum_B K[A][s][dd][B] R[B][e][B']
+        const size_t n1 = (size_t)AB * d * D * chid * AB;
+        for (size_t o = tid; o < n1; o += NT) {
+          const int Bp = (int)(o % AB), e = (int)((o / AB) % chid);
+          const size_t t = o / ((size_t)AB * chid);
+          const int dd = (int)(t % D), s = (int)((t / D) % d), A = (int)(t / ((size_t)D * d));
+          const T* Kr = Ky + ((size_t)s * D + dd) * AB * AB + A;
+          T acc = T(0);
+          for (int B = 0; B < AB; ++B) acc += Kr[(size_t)B * AB] * Rn[((size_t)B * chid + e) * AB + Bp];
+          V1[o] = acc;
+        }
+        __syncthreads();
+        // V2[A][s][c][d'][B'] = sum_{dd, e} V1[A][s][dd][e][B'] D^l[c][(dd, d')][e]
+        const size_t n2 = (size_t)AB * d * chid * D * AB;
+        for (size_t o = tid; o < n2; o += NT) {
+          const int Bp = (int)(o % AB), dp = (int)((o / AB) % D);
+          const size_t t = o / ((size_t)AB * D);
+          const int cc = (int)(t % chid), s = (int)((t / chid) % d), A = (int)(t / ((size_t)chid * d));
+          T acc = T(0);
+          for (int dd = 0; dd < D; ++dd)
+            for (int e = 0; e < chid; ++e) {
+              const T dv = Dg[((size_t)cc * P + dd * D + dp) * chid + e];
+              acc += V1[((((size_t)A * d + s) * D + dd) * chid + e) * AB + Bp] * dv;
+            }
+          V2[o] = acc;
+        }
+        __syncthreads();
+        // R_y[A][c][A'] = sum_{s, d', B'} V2[A][s][c][d'][B'] conj(K[A'][s][d'][B'])
+        T* Ry = RP + (size_t)y * rsz;
+        for (size_t o = tid; o < rsz; o += NT) {
+          const int Ap = (int)(o % AB), cc = (int)((o / AB) % chid), A = (int)(o / ((size_t)AB * chid));
+          T acc = T(0);
+          for (int s = 0; s < d; ++s)
+            for (int dp = 0; dp < D; ++dp) {
+              const T* Vr = V2 + ((((size_t)A * d + s) * chid + cc) * D + dp) * AB;
+              const T* Kr = Ky + ((size_t)s * D + dp) * AB * AB + Ap;
+              for (int Bp = 0; Bp < AB; ++Bp) acc = mad(acc, Vr[Bp], conj_(Kr[(size_t)Bp * AB]));
+            }
+          Ry[o] = acc;
+        }
+        __syncthreads();
+        blk_normalize(Ry, (int)rsz, red, &st);
+      }
+      // left to right: draw the row
+      blk_unit(Lp, (int)rsz);
+      __syncthreads();
+      for (int y = 0; y < Ly; ++y) {
+        const T* Ky = KT + (size_t)y * ksz;
+        const T* K2y = K2 + (size_t)y * ksz;
+        const T* Dg = Dn + (size_t)y * sd;
+        const T* Rn = RP + (size_t)(y + 1) * rsz;
+        // W1[c][s][dd][B][A'] = sum_A L[A][c][A'] K[A][s][dd][B]
+        const size_t n1 = (size_t)chid * d * D * AB * AB;
+        for (size_t o = tid; o < n1; o += NT) {
+          const int Ap = (int)(o % AB), B = (int)((o / AB) % AB);
+          const size_t t = o / ((size_t)AB * AB);
+          const int dd = (int)(t % D), s = (int)((t / D) % d), cc = (int)(t / ((size_t)D * d));
+          const T* Kr = Ky + (((size_t)s * D + dd) * AB + B) * AB;
+          T acc = T(0);
+          for (int A = 0; A < AB; ++A) acc += Lp[((size_t)A * chid + cc) * AB + Ap] * Kr[A];
+          V1[o] = acc;
+        }
+        __syncthreads();
+        // W2[s][d'][e][B][A'] = sum_{c, dd} W1[c][s][dd][B][A'] D^l[c][(dd, d')][e]
+        const size_t n2 = (size_t)d * D * chid * AB * AB;
+        for (size_t o = tid; o < n2; o += NT) {
+          const int Ap = (int)(o % AB), B = (int)((o / AB) % AB);
+          const size_t t = o / ((size_t)AB * AB);
+          const int e = (int)(t % chid), dp = (int)((t / chid) % D), s = (int)(t / ((size_t)chid * D));
+          T acc = T(0);
+          for (int cc = 0; cc < chid; ++cc)
+            for (int dd = 0; dd < D; ++dd)
+              acc += V1[((((size_t)cc * d + s) * D + dd) * AB + B) * AB + Ap] *
+                     Dg[((size_t)cc * P + dd * D + dp) * chid + e];
+          V2[o] = acc;
+        }
+        __syncthreads();
+        // cand[s][B][e][B'] = sum_{A', d'} W2[s][d'][e][B][A'] conj(K[A'][s][d'][B'])
+        const size_t n3 = (size_t)d * rsz;
+        for (size_t o = tid; o < n3; o += NT) {
+          const int Bp = (int)(o % AB), e = (int)((o / AB) % chid);
+          const size_t t = o / ((size_t)AB * chid);
+          const int B = (int)(t % AB), s = (int)(t / AB);
+          T acc = T(0);
+          for (int dp = 0; dp < D; ++dp) {
+            const T* Wr = V2 + ((((size_t)s * D + dp) * chid + e) * AB + B) * AB;
+            const T* Kr = K2y + ((size_t)s * D + dp) * AB * AB + Bp;
+            for (int Ap = 0; Ap < AB; ++Ap) acc = mad(acc, Wr[Ap], conj_(Kr[(size_t)Ap * AB]));
+          }
+          LC[o] = acc;
+        }
+        __syncthreads();
+        // weights, then the draw
+        for (int s = 0; s < d; ++s) {
+          double part = 0.0;
+          for (size_t o = tid; o < rsz; o += NT) part += (double)re_(LC[(size_t)s * rsz + o] * Rn[o]);
+          const double ws = block_sum(part, red);
+          if (tid == 0) pw[s] = (ws > 0.0) ? ws : 0.0;
+        }
+        if (tid == 0) {
+          double tot = 0.0;
+          for (int s = 0; s < d; ++s) tot += pw[s];
+          if (!(tot > 0.0) || !isfinite(tot)) {
+            st |= ST_ZERO_NORM;
+            for (int s = 0; s < d; ++s) pw[s] = 1.0;
+            tot = (double)d;
+          }
+          const double u = uniform53((uint32_t)(x * Ly + y), (uint32_t)draw, (uint32_t)c, 2u, seed);
+          double acc = 0.0;
+          int s_pick = d - 1;
+          for (int s = 0; s < d; ++s) {
+            acc += pw[s] / tot;
+            if (u < acc) { s_pick = s; break; }
+          }
+          pick = s_pick;
+          const double ps = pw[s_pick] / tot;
+          pw[d] = (ps > 0.0) ? log(ps) : -INFINITY;
+          Sl[x * Ly + y] = (uint8_t)s_pick;
+        }
+        __syncthreads();
+        lp += pw[d];
+        blk_copy(Lp, LC + (size_t)pick * rsz, (int)rsz);
+        __syncthreads();
+        blk_normalize(Lp, (int)rsz, red, &st);
+      }
+      // E^u[x] from the drawn row
+      if (x < Lx - 1) {
+        T* out = EU + (size_t)(cur ^ 1) * rowsz;
+        if (x == 0) env_first_row(g, out, Tpad, 0, Sl, false, w.A, w.Z, red, &st);
+        else env_row_step(g, Eu, out, Tpad, x, Sl + (size_t)x * Ly, false, w, &st, &wd, &flag);
+        cur ^= 1;
+        __syncthreads();
+      }
+    }
+    uint8_t* Sg = S + (size_t)c * N;
+    for (int i = tid; i < N; i += NT) Sg[i] = Sl[i];
+    if (tid == 0) {
+      logp[c] = lp;
+      status[c] = st;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+cudaError_t launch_dl_env(const Geo& g, int chid, const T* Tpad, T* DL, const DlWork<T>& w, int* status,
+                          cudaStream_t s) {
+  const size_t sm = dl_smem_bytes(g.D, chid, sizeof(T), sizeof(typename Scal<T>::R));
+  cudaError_t e = cudaFuncSetAttribute(k_dl_env<T, Geo>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k_dl_env<T, Geo><<<1, NTHREADS, sm, s>>>(g, chid, Tpad, DL, w, status);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_direct(const Geo& g, const Plan& p, int grid, size_t smem, int chid, const T* Tpad, const T* DL,
+                          uint8_t* S, int Ns, unsigned long long seed, unsigned long long draw, double* logp,
+                          int* status, cudaStream_t s) {
+  k_direct<T, Geo><<<grid, NTHREADS, smem, s>>>(g, p, chid, Tpad, DL, S, Ns, seed, draw, logp, status);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t kattr_direct(const Geo& g, size_t set_bytes, int* occ, size_t occ_smem) {
+  cudaError_t e = cudaSuccess;
+  if (set_bytes) e = cudaFuncSetAttribute(k_direct<T, Geo>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)set_bytes);
+  if (e == cudaSuccess && occ) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_direct<T, Geo>, NTHREADS, occ_smem);
+  return e;
+}
+
+#define PEPS_INST_DIRECT(T)                                                                                        \
+  template cudaError_t launch_dl_env<T>(const Geo&, int, const T*, T*, const DlWork<T>&, int*, cudaStream_t);      \
+  template cudaError_t launch_direct<T>(const Geo&, const Plan&, int, size_t, int, const T*, const T*, uint8_t*,   \
+                                        int, unsigned long long, unsigned long long, double*, int*, cudaStream_t); \
+  template cudaError_t kattr_direct<T>(const Geo&, size_t, int*, size_t);
+
+}  // namespace peps

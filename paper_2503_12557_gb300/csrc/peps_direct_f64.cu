@@ -1,0 +1,6 @@
+// double instantiation of the direct-sampling kernels (k_dl_env, k_direct).
+#include "peps_direct.cuh"
+
+namespace peps {
+PEPS_INST_DIRECT(double)
+}  // namespace peps

@@ -97,6 +97,62 @@ inline int occupancy(const Geo& g, int which, size_t smem) {
   return nb;
 }
 
+// ---- direct sampling (peps_direct.cuh)
+// Index sizes of the double-layer compression: product bond nb = chi_d D^2, physical P = D^2,
+// Jacobi rows mX (even), row length Lr = P chi_d with strides LY (Y, Vt) and LX (X).
+struct DlDims {
+  int nb, P, chid, Lr, LY, LX, mX;
+};
+__host__ __device__ inline DlDims dl_dims(int D, int chid) {
+  DlDims d;
+  d.P = D * D;
+  d.chid = chid;
+  d.nb = chid * d.P;
+  d.Lr = d.P * chid;
+  d.LY = d.Lr + 1;
+  d.LX = d.Lr + ((8 - d.Lr) % 32 + 32) % 32;
+  d.mX = d.nb + (d.nb & 1);
+  return d;
+}
+// element counts of the global work buffers of k_dl_env, in the order B, Rh, Z, Y, X, Vt, C, Cn
+__host__ __device__ inline void dl_work_elems(int Ly, int D, int chid, size_t* n8) {
+  const DlDims d = dl_dims(D, chid);
+  n8[0] = (size_t)Ly * d.nb * d.P * d.nb;
+  n8[1] = (size_t)(Ly > 1 ? Ly - 1 : 1) * d.nb * d.nb;
+  n8[2] = (size_t)d.nb * d.P * d.nb;
+  n8[3] = (size_t)d.nb * d.LY;
+  n8[4] = (size_t)d.mX * d.LX;
+  n8[5] = (size_t)chid * d.LY;
+  n8[6] = (size_t)d.nb * chid;
+  n8[7] = (size_t)d.nb * chid;
+}
+// dynamic shared memory of k_dl_env: reduction scratch, singular values, ranks, Householder taus
+__host__ __device__ inline size_t dl_smem_bytes(int D, int chid, size_t esz, size_t rsz) {
+  const DlDims d = dl_dims(D, chid);
+  size_t b = 40 * 8;
+  b += (size_t)(d.mX + 4) * rsz;
+  b = (b + 15) / 16 * 16;
+  b += (size_t)2 * d.mX * 4;
+  b = (b + 15) / 16 * 16;
+  b += (size_t)d.nb * esz;
+  return b;
+}
+
+template <typename T>
+struct DlWork {
+  T *B, *Rh, *Z, *Y, *X, *Vt, *C, *Cn;
+};
+
+template <typename T>
+cudaError_t launch_dl_env(const Geo& g, int chid, const T* Tpad, T* DL, const DlWork<T>& w, int* status,
+                          cudaStream_t s);
+template <typename T>
+cudaError_t launch_direct(const Geo& g, const Plan& p, int grid, size_t smem, int chid, const T* Tpad, const T* DL,
+                          uint8_t* S, int Ns, unsigned long long seed, unsigned long long draw, double* logp,
+                          int* status, cudaStream_t s);
+template <typename T>
+cudaError_t kattr_direct(const Geo& g, size_t set_bytes, int* occ, size_t occ_smem);
+
 // ---- MinSR (FP64)
 // column means m_k = sum_S w_S O_{S,k} (w normalised), and Obar = sqrt(w)(O - m) written as
 // double (Ns x Np)

@@ -69,6 +69,8 @@ def load():
         "peps_evaluate": ([vp, C.POINTER(_Ham), vp, i32, vp, vp, vp, vp, vp, vp], i32),
         "peps_local_energy_bound": ([vp, C.POINTER(_Ham), vp, i32, i32, vp, vp, vp, vp, vp], i32),
         "peps_rotate_params": ([vp, vp, vp, i32, vp, vp], i32),
+        "peps_direct_prepare": ([vp, i32, vp], i32),
+        "peps_direct_sample": ([vp, vp, i32, C.c_uint64, C.c_uint64, vp, vp, vp], i32),
         "minsr_step": ([vp, vp, vp, vp, i32, dbl, dbl, dbl, vp, vp, vp], i32),
         "peps_sample": ([vp, i32, vp, i32, i32, C.c_uint64, C.c_uint64, vp, vp, vp], i32),
         "peps_last_error": ([vp], C.c_char_p),
@@ -98,7 +100,7 @@ def exported_symbols():
             "peps_timing_enable", "peps_timing_read", "peps_apply_update", "peps_proposal_logits",
             "peps_proposal_train_step", "peps_sample_learned", "peps_amplitudes_noalloc", "peps_probe_fma",
             "peps_autotune", "peps_batch_create", "peps_batch_launch", "peps_batch_destroy",
-            "peps_local_energy_bound", "peps_rotate_params"]
+            "peps_local_energy_bound", "peps_rotate_params", "peps_direct_prepare", "peps_direct_sample"]
 
 
 def probe_fma(fp64=False):
@@ -149,7 +151,7 @@ class Proposal:
         return self.loss
 
 
-TIMING_CLASSES = ["env", "row", "pair", "combine", "sample", "minsr_gram", "minsr_eig", "minsr_other", "pad", "bound"]
+TIMING_CLASSES = ["env", "row", "pair", "combine", "sample", "minsr_gram", "minsr_eig", "minsr_other", "pad", "bound", "direct"]
 
 
 def _ptr(t):
@@ -323,6 +325,20 @@ class PEPS:
         self._check(self.L.peps_local_energy_bound(self.h, C.byref(hc.c), _ptr(S), ns, int(cut), _ptr(e), _ptr(la),
                                                    _ptr(ph), _ptr(st), _stream()), "peps_local_energy_bound")
         return dict(eloc=e, logabs=la, phase=ph, status=st)
+
+    def direct_prepare(self, chi_double):
+        """Double-layer lower environments of the current parameters for direct sampling."""
+        self._check(self.L.peps_direct_prepare(self.h, int(chi_double), _stream()), "peps_direct_prepare")
+
+    def direct_sample(self, ns, seed=0, draw=0, S_out=None):
+        """ns independent configurations drawn row by row; returns (S, log p(S), status)."""
+        dev = torch.device("cuda")
+        S = S_out if S_out is not None else torch.empty(ns, self.Lx * self.Ly, dtype=torch.uint8, device=dev)
+        lp = torch.empty(ns, dtype=torch.float64, device=dev)
+        st = torch.empty(ns, dtype=torch.int32, device=dev)
+        self._check(self.L.peps_direct_sample(self.h, _ptr(S), ns, int(seed) & (2 ** 64 - 1), int(draw), _ptr(lp),
+                                              _ptr(st), _stream()), "peps_direct_sample")
+        return S, lp, st
 
     def rotate_params(self, M, theta):
         """theta' (complex128, N_p) with the physical index of every site tensor multiplied by the
