@@ -163,6 +163,23 @@ def _peaks():
         return {}
 
 
+# DRAM bytes (read + write) of one k_sample launch, from the ncu capture summarised in
+# profiles/k_sample_heis8x8_D4_chi16_ns304.md: 264 MB + 1374 MB for 304 chains x 2 sweeps in FP32
+# (the full 4096-chain launch exceeds the capture size the profiling rules allow), scaled by the
+# chains processed (each chain's environment rows and partials are its own traffic).
+_K_SAMPLE_CAPTURE = {"bytes": 264e6 + 1374e6, "chains": 304, "sweeps": 2, "precision": "fp32"}
+
+
+def _measured_traffic(kernel, ns, sweeps, prec):
+    """Per-launch DRAM traffic of the dominant kernel from its ncu capture, or None where no
+    capture of the current kernel at this precision and sweep count exists."""
+    from paper_2503_12557_gb300 import peps as P
+    c = _K_SAMPLE_CAPTURE
+    if kernel == "sample" and prec == P.PREC_FP32 and sweeps == c["sweeps"]:
+        return c["bytes"] * ns / c["chains"]
+    return None
+
+
 def run_gpu(a):
     import torch
     import torch.distributed as dist
@@ -267,7 +284,7 @@ def run_gpu(a):
     roof = {"kernel": {"env": "k_env", "sample": "k_sample", "row": "k_row", "pair": "k_pair",
                        "minsr_gram": "k_gram"}[dom],
             "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None,
+            "traffic": _measured_traffic(dom, ns, a.sweeps, prec),
             "peak_source": ("measured: peps_probe_fma FP32 (derived 152 SMs x 128 lanes x 2 x max clock = %.1f)"
                             % fp32_derived if peak == fp32_peak else
                             "measured: peps_probe_fma FP64" if peak == fp64_peak else "MEASURED_PEAKS bf16_tflops"),

@@ -192,7 +192,13 @@ static void place_overlay(Plan& p, size_t& smem, size_t budget, const std::vecto
 
 // Default shared-memory budget per CTA: FP64 one CTA per SM (the FP64 pipe is the limit), FP32
 // two CTAs per SM.
-static size_t default_budget(const peps_handle* h) { return (h->esz >= 8) ? 210 * 1024 : 110 * 1024; }
+// Default shared-memory budget per CTA and kernel class (0 env, 1 row, 2 pair, 3 sampler): FP64
+// one CTA per SM (the FP64 pipe is the limit); FP32 two CTAs per SM, except the environment
+// kernel, compiled for three (72 KB each, the row step's larger buffers in the L2-resident arena).
+static size_t default_budget(const peps_handle* h, int cls) {
+  if (h->esz >= 8) return 210 * 1024;
+  return cls == 0 ? 72 * 1024 : 110 * 1024;
+}
 
 static void plan_all(peps_handle* h) {
   const Geo& g = h->g;
@@ -201,7 +207,7 @@ static void plan_all(peps_handle* h) {
   const int mX = n + (n & 1);
   const int Lr = D * chi;
   for (int i = 0; i < 4; ++i)
-    if (h->budget[i] == 0) h->budget[i] = default_budget(h);
+    if (h->budget[i] == 0) h->budget[i] = default_budget(h, i);
   size_t budget = h->budget[0];
   int ci = std::min(n, 8);
   const size_t zsz = env_z_elems(chi, D);
@@ -233,7 +239,7 @@ static void plan_all(peps_handle* h) {
         {B_RHIST, (size_t)std::max(1, Ly - 1) * n * n * E}, {B_S, (size_t)g.Lx * g.Ly},
         {B_LW, (size_t)2 * chi * chi * E}, {B_LW2, (size_t)g.se * E}, {B_LP, (size_t)2 * Ly * g.se * E},
         {B_RP, (size_t)2 * Ly * g.se * E}};
-    place(k.p, k.smem, budget, b);
+    place(k.p, k.smem, h->budget[3], b);
   }
   // row plan
   budget = h->budget[1];
@@ -712,7 +718,7 @@ extern "C" peps_status peps_direct_prepare(peps_handle* h, int chi_double, void*
       {B_Z, env_z_elems(chi, D) * E}, {B_RHIST, (size_t)std::max(1, Ly - 1) * n * n * E}, {B_S, (size_t)Lx * Ly},
       {B_EU, (size_t)2 * Ly * g.se * E}, {B_LW2, (size_t)(g.d + 1) * rsz * E}, {B_RP, (size_t)(Ly + 1) * rsz * E},
       {B_LP, tsz * E}, {B_LW, tsz * E}, {B_T1, (size_t)Ly * ksz * E}, {B_T2, (size_t)Ly * ksz * E}};
-  place(k.p, k.smem, h->budget[0], b);
+  place(k.p, k.smem, h->budget[3], b);
   cudaError_t e = cudaSuccess;
   {
     std::lock_guard<std::mutex> lk(g_direct_mu);
@@ -1085,7 +1091,7 @@ extern "C" peps_status peps_autotune(peps_handle* h, const peps_hamiltonian* H, 
   h->evn = 0;
   cleanup();
   if (st != PEPS_OK) {
-    for (int i = 0; i < 4; ++i) h->budget[i] = default_budget(h);
+    for (int i = 0; i < 4; ++i) h->budget[i] = default_budget(h, i);
     plan_all(h);
     finish_plans(h);
     return st;

@@ -178,16 +178,18 @@ __global__ void __launch_bounds__(NTHREADS) k_dl_env(G g, int chid, const T* __r
 // ------------------------------------------------------------------------------------------
 // Direct sampling: one CTA per configuration (persistent).  Row x of chain c in draw round t:
 //   K_y[s][dd][B][A] = sum_u E^u[x-1]_y[a][u][b] T[s][l][u][r][dd]   (A = (a, l), B = (b, r)),
-//   the ket sites of T^u, also stored as K2_y[s][dd][A][B];
+//   the ket sites of T^u (and KC_y = conj(K_y), same layout);
 //   right partials with the physical legs traced, R_y[A][c][A'] (c the D^l bond), from the
 //   right; then left to right, for every candidate s of site y,
 //   cand_s[B][e][B'] = sum L[A][c][A'] K[A][s][d][B] D^l[c][(d, d')][e] conj(K[A'][s][d'][B']),
 //   w_s = Re <cand_s, R_{y+1}> (negative weights count as zero), s drawn with
 //   u = uniform53(Philox(x Ly + y, t, c, 2; seed)), L = cand_s normalised.  After the row,
 //   E^u[x] = truncate_chi(E^u[x-1] . T_proj[x]) by the environment kernels' row step.
+// Every contraction is a register-tiled blk_gemm; the temporaries' layouts put the index that
+// varies across threads at stride 1 in the operand it is read from.
 // logp[c] = sum of the logs of the drawn conditionals (FP64).
 template <typename T, typename G>
-__global__ void __launch_bounds__(NTHREADS) k_direct(G g, Plan plan, int chid, const T* __restrict__ Tpad,
+__global__ void __launch_bounds__(NTHREADS, MinBlocks<T>::value) k_direct(G g, Plan plan, int chid, const T* __restrict__ Tpad,
                                                      const T* __restrict__ DL, uint8_t* S, int Ns,
                                                      unsigned long long seed, unsigned long long draw, double* logp,
                                                      int* status) {
@@ -196,9 +198,9 @@ __global__ void __launch_bounds__(NTHREADS) k_direct(G g, Plan plan, int chid, c
   RowWork<T> w = carve_row<T>(plan, smem, gbase);
   uint8_t* Sl = (uint8_t*)buf_ptr(plan, B_S, smem, gbase);
   T* EU = (T*)buf_ptr(plan, B_EU, smem, gbase);    // two E^u rows, used alternately
-  T* KT = (T*)buf_ptr(plan, B_T1, smem, gbase);    // Ly x [s][dd][B][A]
-  T* K2 = (T*)buf_ptr(plan, B_T2, smem, gbase);    // Ly x [s][dd][A][B]
-  T* RP = (T*)buf_ptr(plan, B_RP, smem, gbase);    // (Ly+1) x [A][c][A']
+  T* KT = (T*)buf_ptr(plan, B_T1, smem, gbase);    // Ly x K[s][dd][B][A]
+  T* KC = (T*)buf_ptr(plan, B_T2, smem, gbase);    // Ly x conj(K), same layout
+  T* RP = (T*)buf_ptr(plan, B_RP, smem, gbase);    // (Ly+1) x R[A][c][A']
   T* V1 = (T*)buf_ptr(plan, B_LP, smem, gbase);
   T* V2 = (T*)buf_ptr(plan, B_LW, smem, gbase);
   T* LC = (T*)buf_ptr(plan, B_LW2, smem, gbase);   // d candidates + the running left partial
@@ -209,7 +211,7 @@ __global__ void __launch_bounds__(NTHREADS) k_direct(G g, Plan plan, int chid, c
   __shared__ int pick;
   const int tid = threadIdx.x, NT = blockDim.x;
   const int Ly = g.Ly, Lx = g.Lx, D = g.D, d = g.d, chi = g.chi, N = Lx * Ly;
-  const int AB = chi * D, P = D * D;
+  const int AB = chi * D, P = D * D, CA = chid * AB;
   const size_t rowsz = (size_t)Ly * g.se, sd = (size_t)chid * P * chid;
   const size_t ksz = (size_t)d * D * AB * AB, rsz = (size_t)AB * chid * AB;
   T* Lp = LC + (size_t)d * rsz;
@@ -228,7 +230,7 @@ __global__ void __launch_bounds__(NTHREADS) k_direct(G g, Plan plan, int chid, c
         const T* Ts = Tpad + (size_t)(x * Ly + y) * d * g.sT;
         const T* E = Eu + (size_t)y * g.se;
         T* Ky = KT + (size_t)y * ksz;
-        T* K2y = K2 + (size_t)y * ksz;
+        T* KCy = KC + (size_t)y * ksz;
         for (size_t o = tid; o < ksz; o += NT) {
           // o = ((s * D + dd) * AB + B) * AB + A
           const int A = (int)(o % AB), B = (int)((o / AB) % AB), dd = (int)((o / ((size_t)AB * AB)) % D),
@@ -238,58 +240,44 @@ __global__ void __launch_bounds__(NTHREADS) k_direct(G g, Plan plan, int chid, c
           for (int u = 0; u < D; ++u)
             acc += E[((size_t)a * D + u) * chi + b] * Ts[(size_t)s * g.sT + ((l * D + u) * D + r) * D + dd];
           Ky[o] = acc;
-          K2y[(((size_t)s * D + dd) * AB + A) * AB + B] = acc;
+          KCy[o] = conj_(acc);
         }
       }
       // right partials, physical legs traced
-      T* Rl = RP + (size_t)Ly * rsz;
-      blk_unit(Rl, (int)rsz);
+      blk_unit(RP + (size_t)Ly * rsz, (int)rsz);
       __syncthreads();
       for (int y = Ly - 1; y >= 0; --y) {
         const T* Ky = KT + (size_t)y * ksz;
+        const T* KCy = KC + (size_t)y * ksz;
         const T* Dg = Dn + (size_t)y * sd;
         const T* Rn = RP + (size_t)(y + 1) * rsz;
-        // V1[A][s][dd][e][B'] = sum_B K[A][s][dd][B] R[B][e][B']
-        const size_t n1 = (size_t)AB * d * D * chid * AB;
-        for (size_t o = tid; o < n1; o += NT) {
-          const int Bp = (int)(o % AB), e = (int)((o / AB) % chid);
-          const size_t t = o / ((size_t)AB * chid);
-          const int dd = (int)(t % D), s = (int)((t / D) % d), A = (int)(t / ((size_t)D * d));
-          const T* Kr = Ky + ((size_t)s * D + dd) * AB * AB + A;
-          T acc = T(0);
-          for (int B = 0; B < AB; ++B) acc += Kr[(size_t)B * AB] * Rn[((size_t)B * chid + e) * AB + Bp];
-          V1[o] = acc;
-        }
-        __syncthreads();
-        // V2[A][s][c][d'][B'] = sum_{dd, e} V1[A][s][dd][e][B'] D^l[c][(dd, d')][e]
-        const size_t n2 = (size_t)AB * d * chid * D * AB;
-        for (size_t o = tid; o < n2; o += NT) {
-          const int Bp = (int)(o % AB), dp = (int)((o / AB) % D);
-          const size_t t = o / ((size_t)AB * D);
-          const int cc = (int)(t % chid), s = (int)((t / chid) % d), A = (int)(t / ((size_t)chid * d));
-          T acc = T(0);
-          for (int dd = 0; dd < D; ++dd)
-            for (int e = 0; e < chid; ++e) {
-              const T dv = Dg[((size_t)cc * P + dd * D + dp) * chid + e];
-              acc += V1[((((size_t)A * d + s) * D + dd) * chid + e) * AB + Bp] * dv;
-            }
-          V2[o] = acc;
-        }
-        __syncthreads();
-        // R_y[A][c][A'] = sum_{s, d', B'} V2[A][s][c][d'][B'] conj(K[A'][s][d'][B'])
         T* Ry = RP + (size_t)y * rsz;
-        for (size_t o = tid; o < rsz; o += NT) {
-          const int Ap = (int)(o % AB), cc = (int)((o / AB) % chid), A = (int)(o / ((size_t)AB * chid));
-          T acc = T(0);
-          for (int s = 0; s < d; ++s)
-            for (int dp = 0; dp < D; ++dp) {
-              const T* Vr = V2 + ((((size_t)A * d + s) * chid + cc) * D + dp) * AB;
-              const T* Kr = Ky + ((size_t)s * D + dp) * AB * AB + Ap;
-              for (int Bp = 0; Bp < AB; ++Bp) acc = mad(acc, Vr[Bp], conj_(Kr[(size_t)Bp * AB]));
-            }
-          Ry[o] = acc;
-        }
-        __syncthreads();
+        // V1[s][B'][dd][e][A] = sum_B K[A][s][dd][B] R[B][e][B']   (m = (A, s dd), n = (e, B'), k = B)
+        blk_gemm<4, 4>(Ky, Rn, V1, AB * d * D, CA, AB, 1, AB, 0, CA, 0,
+                       [=](int m) {
+                         const int A = m % AB, q = m / AB, s = q / D, dd = q % D;
+                         return Off2{q * AB * AB + A, ((s * AB * D + dd) * chid) * AB + A};
+                       },
+                       [=](int n) {
+                         const int e = n / AB, Bp = n % AB;
+                         return Off2{n, (Bp * D * chid + e) * AB};
+                       });
+        // V2[s][d'][B'][A][c] = sum_{dd, e} V1[s][B'][dd][e][A] D^l[c][(dd, d')][e]
+        //   (m = (A, B', s), n = (c, d'), k = (dd, e))
+        blk_gemm<4, 4>(V1, Dg, V2, AB * AB * d, chid * D, D, chid, chid * AB, AB, D * chid, 1,
+                       [=](int m) {
+                         const int A = m % AB, Bp = (m / AB) % AB, s = m / (AB * AB);
+                         return Off2{((s * AB + Bp) * D * chid) * AB + A, ((s * D * AB + Bp) * AB + A) * chid};
+                       },
+                       [=](int n) {
+                         const int cc = n / D, dp = n % D;
+                         return Off2{(cc * P + dp) * chid, dp * AB * AB * chid + cc};
+                       });
+        // R_y[A][c][A'] = sum_{(s, d'), B'} conj(K)[A'][s][d'][B'] V2[s][d'][B'][A][c]
+        //   (m = A', n = (A, c), k = ((s, d'), B'))
+        blk_gemm<2, 8>(KCy, V2, Ry, AB, CA, d * D, AB, AB * AB, AB, AB * CA, CA,
+                       [=](int m) { return Off2{m, m}; },
+                       [=](int n) { return Off2{n, n * AB}; });
         blk_normalize(Ry, (int)rsz, red, &st);
       }
       // left to right: draw the row
@@ -297,50 +285,40 @@ __global__ void __launch_bounds__(NTHREADS) k_direct(G g, Plan plan, int chid, c
       __syncthreads();
       for (int y = 0; y < Ly; ++y) {
         const T* Ky = KT + (size_t)y * ksz;
-        const T* K2y = K2 + (size_t)y * ksz;
+        const T* KCy = KC + (size_t)y * ksz;
         const T* Dg = Dn + (size_t)y * sd;
         const T* Rn = RP + (size_t)(y + 1) * rsz;
-        // W1[c][s][dd][B][A'] = sum_A L[A][c][A'] K[A][s][dd][B]
-        const size_t n1 = (size_t)chid * d * D * AB * AB;
-        for (size_t o = tid; o < n1; o += NT) {
-          const int Ap = (int)(o % AB), B = (int)((o / AB) % AB);
-          const size_t t = o / ((size_t)AB * AB);
-          const int dd = (int)(t % D), s = (int)((t / D) % d), cc = (int)(t / ((size_t)D * d));
-          const T* Kr = Ky + (((size_t)s * D + dd) * AB + B) * AB;
-          T acc = T(0);
-          for (int A = 0; A < AB; ++A) acc += Lp[((size_t)A * chid + cc) * AB + Ap] * Kr[A];
-          V1[o] = acc;
-        }
-        __syncthreads();
-        // W2[s][d'][e][B][A'] = sum_{c, dd} W1[c][s][dd][B][A'] D^l[c][(dd, d')][e]
-        const size_t n2 = (size_t)d * D * chid * AB * AB;
-        for (size_t o = tid; o < n2; o += NT) {
-          const int Ap = (int)(o % AB), B = (int)((o / AB) % AB);
-          const size_t t = o / ((size_t)AB * AB);
-          const int e = (int)(t % chid), dp = (int)((t / chid) % D), s = (int)(t / ((size_t)chid * D));
-          T acc = T(0);
-          for (int cc = 0; cc < chid; ++cc)
-            for (int dd = 0; dd < D; ++dd)
-              acc += V1[((((size_t)cc * d + s) * D + dd) * AB + B) * AB + Ap] *
-                     Dg[((size_t)cc * P + dd * D + dp) * chid + e];
-          V2[o] = acc;
-        }
-        __syncthreads();
-        // cand[s][B][e][B'] = sum_{A', d'} W2[s][d'][e][B][A'] conj(K[A'][s][d'][B'])
-        const size_t n3 = (size_t)d * rsz;
-        for (size_t o = tid; o < n3; o += NT) {
-          const int Bp = (int)(o % AB), e = (int)((o / AB) % chid);
-          const size_t t = o / ((size_t)AB * chid);
-          const int B = (int)(t % AB), s = (int)(t / AB);
-          T acc = T(0);
-          for (int dp = 0; dp < D; ++dp) {
-            const T* Wr = V2 + ((((size_t)s * D + dp) * chid + e) * AB + B) * AB;
-            const T* Kr = K2y + ((size_t)s * D + dp) * AB * AB + Bp;
-            for (int Ap = 0; Ap < AB; ++Ap) acc = mad(acc, Wr[Ap], conj_(Kr[(size_t)Ap * AB]));
-          }
-          LC[o] = acc;
-        }
-        __syncthreads();
+        // W1[s][B][c][dd][A'] = sum_A L[A][c][A'] K[A][s][dd][B]   (m = (A', c), n = (s dd, B), k = A)
+        blk_gemm<4, 4>(Lp, Ky, V1, CA, d * D * AB, AB, 1, CA, 0, 1, 0,
+                       [=](int m) {
+                         const int Ap = m % AB, cc = m / AB;
+                         return Off2{cc * AB + Ap, cc * D * AB + Ap};
+                       },
+                       [=](int n) {
+                         const int B = n % AB, q = n / AB, s = q / D, dd = q % D;
+                         return Off2{n * AB, ((s * AB + B) * chid * D + dd) * AB};
+                       });
+        // W2[s][d'][A'][e][B] = sum_{c, dd} W1[s][B][c][dd][A'] D^l[c][(dd, d')][e]
+        //   (m = (A', B, s), n = (d', e), k = (c, dd))
+        blk_gemm<4, 4>(V1, Dg, V2, AB * AB * d, D * chid, chid, D, D * AB, AB, P * chid, D * chid,
+                       [=](int m) {
+                         const int Ap = m % AB, B = (m / AB) % AB, s = m / (AB * AB);
+                         return Off2{((s * AB + B) * chid * D) * AB + Ap, ((s * D * AB + Ap) * chid) * AB + B};
+                       },
+                       [=](int n) {
+                         const int dp = n / chid, e = n % chid;
+                         return Off2{dp * chid + e, (dp * AB * chid + e) * AB};
+                       });
+        // cand_s[B][e][B'] = sum_{d', A'} W2[s][d'][A'][e][B] conj(K)[A'][s][d'][B']
+        //   (per s: m = (B, e), n = B', k = (d', A'))
+        for (int s = 0; s < d; ++s)
+          blk_gemm<4, 4>(V2 + (size_t)s * D * AB * CA, KCy + (size_t)s * D * AB * AB, LC + (size_t)s * rsz, CA, AB, D,
+                         AB, AB * CA, CA, AB * AB, 1,
+                         [=](int m) {
+                           const int B = m % AB, e = m / AB;
+                           return Off2{e * AB + B, (B * chid + e) * AB};
+                         },
+                         [=](int n) { return Off2{n * AB, n}; });
         // weights, then the draw
         for (int s = 0; s < d; ++s) {
           double part = 0.0;

@@ -5,9 +5,12 @@
 namespace peps {
 
 constexpr int NTHREADS = 256;
-// resident blocks per SM the environment and sampler kernels are compiled for: two in FP32
-// (about 100 KB of shared memory each), one in FP64 (about 200 KB)
+// resident blocks per SM the sampler, bound and direct-sampling kernels are compiled for: two in
+// FP32 (about 100 KB of shared memory each), one in FP64 (about 200 KB)
 template <typename T> struct MinBlocks { static constexpr int value = sizeof(T) == 4 ? 2 : 1; };
+// the environment kernel in FP32: three blocks per SM (80 registers; measured 10 % faster than
+// two at 8x8, D = 4, chi = 16, where the sampler, which also runs the sandwiches, is 9 % slower)
+template <typename T> struct EnvBlocks { static constexpr int value = sizeof(T) == 4 ? 3 : 1; };
 constexpr int MAX_LY = 32;
 
 // term record (ints): number of sites, the sites, window (first row, first column, width,

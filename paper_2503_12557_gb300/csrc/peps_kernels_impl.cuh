@@ -82,7 +82,7 @@ __device__ void build_lower(const G& g, const T* Tpad, const uint8_t* Ss, T* env
 }
 
 template <typename T, typename G>
-__global__ void __launch_bounds__(NTHREADS, MinBlocks<T>::value) k_env(G g, Plan plan, const T* __restrict__ Tpad,
+__global__ void __launch_bounds__(NTHREADS, EnvBlocks<T>::value) k_env(G g, Plan plan, const T* __restrict__ Tpad,
                                                   const uint8_t* __restrict__ S, int Ns, int sides, T* envs,
                                                   double* logs, int* status, float* wdisc) {
   extern __shared__ __align__(16) char smem[];
