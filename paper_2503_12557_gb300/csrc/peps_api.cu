@@ -705,7 +705,8 @@ extern "C" peps_status peps_direct_prepare(peps_handle* h, int chi_double, void*
   if (!h->dl_status && cudaMalloc(&h->dl_status, sizeof(int)) != cudaSuccess)
     return fail(h, PEPS_E_WORKSPACE, "status");
   // the sampler's buffer plan: the row step's buffers, then the configuration, two E^u rows,
-  // the ket sites (two layouts), the right partials and the contraction temporaries
+  // the candidates, the right partials, the contraction temporaries and one ket site (and its
+  // conjugate)
   const int n = g.n, chi = g.chi, mX = n + (n & 1), ci = std::min(n, 8);
   const size_t AB = (size_t)chi * D, rsz = AB * chi_double * AB, ksz = (size_t)g.d * D * AB * AB;
   const size_t tsz = (size_t)g.d * D * chi_double * AB * AB;
@@ -717,7 +718,7 @@ extern "C" peps_status peps_direct_prepare(peps_handle* h, int chi_double, void*
       {B_C, (size_t)n * chi * E}, {B_W, env_w_elems(chi, D, ci) * E}, {B_R, (size_t)n * n * E},
       {B_Z, env_z_elems(chi, D) * E}, {B_RHIST, (size_t)std::max(1, Ly - 1) * n * n * E}, {B_S, (size_t)Lx * Ly},
       {B_EU, (size_t)2 * Ly * g.se * E}, {B_LW2, (size_t)(g.d + 1) * rsz * E}, {B_RP, (size_t)(Ly + 1) * rsz * E},
-      {B_LP, tsz * E}, {B_LW, tsz * E}, {B_T1, (size_t)Ly * ksz * E}, {B_T2, (size_t)Ly * ksz * E}};
+      {B_LP, tsz * E}, {B_LW, tsz * E}, {B_T1, ksz * E}, {B_T2, ksz * E}};
   place(k.p, k.smem, h->budget[3], b);
   cudaError_t e = cudaSuccess;
   {

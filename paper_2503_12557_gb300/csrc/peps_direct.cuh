@@ -175,6 +175,25 @@ __global__ void __launch_bounds__(NTHREADS) k_dl_env(G g, int chid, const T* __r
   if (tid == 0) *status = st;
 }
 
+// Ket site y of T^u, K[s][dd][B][A] = sum_u E^u_y[a][u][b] T[s][l][u][r][dd] (A = (a, l),
+// B = (b, r)), and its complex conjugate in the same layout.  Ends with a barrier.
+template <typename T, typename G>
+__device__ void ket_site(const G& g, const T* E, const T* Ts, T* K, T* KCj) {
+  const int D = g.D, chi = g.chi, AB = chi * D;
+  const size_t ksz = (size_t)g.d * D * AB * AB;
+  for (size_t o = threadIdx.x; o < ksz; o += blockDim.x) {
+    const int A = (int)(o % AB), B = (int)((o / AB) % AB), dd = (int)((o / ((size_t)AB * AB)) % D),
+              s = (int)(o / ((size_t)AB * AB * D));
+    const int a = A / D, l = A % D, b = B / D, r = B % D;
+    T acc = T(0);
+    for (int u = 0; u < D; ++u)
+      acc += E[((size_t)a * D + u) * chi + b] * Ts[(size_t)s * g.sT + ((l * D + u) * D + r) * D + dd];
+    K[o] = acc;
+    KCj[o] = conj_(acc);
+  }
+  __syncthreads();
+}
+
 // ------------------------------------------------------------------------------------------
 // Direct sampling: one CTA per configuration (persistent).  Row x of chain c in draw round t:
 //   K_y[s][dd][B][A] = sum_u E^u[x-1]_y[a][u][b] T[s][l][u][r][dd]   (A = (a, l), B = (b, r)),
@@ -198,8 +217,8 @@ __global__ void __launch_bounds__(NTHREADS, MinBlocks<T>::value) k_direct(G g, P
   RowWork<T> w = carve_row<T>(plan, smem, gbase);
   uint8_t* Sl = (uint8_t*)buf_ptr(plan, B_S, smem, gbase);
   T* EU = (T*)buf_ptr(plan, B_EU, smem, gbase);    // two E^u rows, used alternately
-  T* KT = (T*)buf_ptr(plan, B_T1, smem, gbase);    // Ly x K[s][dd][B][A]
-  T* KC = (T*)buf_ptr(plan, B_T2, smem, gbase);    // Ly x conj(K), same layout
+  T* Ky = (T*)buf_ptr(plan, B_T1, smem, gbase);    // K[s][dd][B][A] of the current site
+  T* KCy = (T*)buf_ptr(plan, B_T2, smem, gbase);   // conj(K), same layout
   T* RP = (T*)buf_ptr(plan, B_RP, smem, gbase);    // (Ly+1) x R[A][c][A']
   T* V1 = (T*)buf_ptr(plan, B_LP, smem, gbase);
   T* V2 = (T*)buf_ptr(plan, B_LW, smem, gbase);
@@ -215,6 +234,8 @@ __global__ void __launch_bounds__(NTHREADS, MinBlocks<T>::value) k_direct(G g, P
   const size_t rowsz = (size_t)Ly * g.se, sd = (size_t)chid * P * chid;
   const size_t ksz = (size_t)d * D * AB * AB, rsz = (size_t)AB * chid * AB;
   T* Lp = LC + (size_t)d * rsz;
+  // register-tile edge of the large contractions (complex double: smaller, to stay in registers)
+  constexpr int TE = sizeof(T) >= 16 ? 4 : 8;
   for (int c = blockIdx.x; c < Ns; c += gridDim.x) {
     if (tid == 0) { st = 0; wd = 0.f; }
     // E^u[-1]: the trivial row
@@ -225,35 +246,16 @@ __global__ void __launch_bounds__(NTHREADS, MinBlocks<T>::value) k_direct(G g, P
     for (int x = 0; x < Lx; ++x) {
       const T* Eu = EU + (size_t)cur * rowsz;
       const T* Dn = DL + (size_t)(x + 1) * Ly * sd;
-      // ket sites of T^u
-      for (int y = 0; y < Ly; ++y) {
-        const T* Ts = Tpad + (size_t)(x * Ly + y) * d * g.sT;
-        const T* E = Eu + (size_t)y * g.se;
-        T* Ky = KT + (size_t)y * ksz;
-        T* KCy = KC + (size_t)y * ksz;
-        for (size_t o = tid; o < ksz; o += NT) {
-          // o = ((s * D + dd) * AB + B) * AB + A
-          const int A = (int)(o % AB), B = (int)((o / AB) % AB), dd = (int)((o / ((size_t)AB * AB)) % D),
-                    s = (int)(o / ((size_t)AB * AB * D));
-          const int a = A / D, l = A % D, b = B / D, r = B % D;
-          T acc = T(0);
-          for (int u = 0; u < D; ++u)
-            acc += E[((size_t)a * D + u) * chi + b] * Ts[(size_t)s * g.sT + ((l * D + u) * D + r) * D + dd];
-          Ky[o] = acc;
-          KCy[o] = conj_(acc);
-        }
-      }
       // right partials, physical legs traced
       blk_unit(RP + (size_t)Ly * rsz, (int)rsz);
       __syncthreads();
       for (int y = Ly - 1; y >= 0; --y) {
-        const T* Ky = KT + (size_t)y * ksz;
-        const T* KCy = KC + (size_t)y * ksz;
+        ket_site(g, Eu + (size_t)y * g.se, Tpad + (size_t)(x * Ly + y) * d * g.sT, Ky, KCy);
         const T* Dg = Dn + (size_t)y * sd;
         const T* Rn = RP + (size_t)(y + 1) * rsz;
         T* Ry = RP + (size_t)y * rsz;
         // V1[s][B'][dd][e][A] = sum_B K[A][s][dd][B] R[B][e][B']   (m = (A, s dd), n = (e, B'), k = B)
-        blk_gemm<4, 4>(Ky, Rn, V1, AB * d * D, CA, AB, 1, AB, 0, CA, 0,
+        blk_gemm<TE, TE>(Ky, Rn, V1, AB * d * D, CA, AB, 1, AB, 0, CA, 0,
                        [=](int m) {
                          const int A = m % AB, q = m / AB, s = q / D, dd = q % D;
                          return Off2{q * AB * AB + A, ((s * AB * D + dd) * chid) * AB + A};
@@ -264,7 +266,7 @@ __global__ void __launch_bounds__(NTHREADS, MinBlocks<T>::value) k_direct(G g, P
                        });
         // V2[s][d'][B'][A][c] = sum_{dd, e} V1[s][B'][dd][e][A] D^l[c][(dd, d')][e]
         //   (m = (A, B', s), n = (c, d'), k = (dd, e))
-        blk_gemm<4, 4>(V1, Dg, V2, AB * AB * d, chid * D, D, chid, chid * AB, AB, D * chid, 1,
+        blk_gemm<2, 16>(V1, Dg, V2, AB * AB * d, chid * D, D, chid, chid * AB, AB, D * chid, 1,
                        [=](int m) {
                          const int A = m % AB, Bp = (m / AB) % AB, s = m / (AB * AB);
                          return Off2{((s * AB + Bp) * D * chid) * AB + A, ((s * D * AB + Bp) * AB + A) * chid};
@@ -275,7 +277,7 @@ __global__ void __launch_bounds__(NTHREADS, MinBlocks<T>::value) k_direct(G g, P
                        });
         // R_y[A][c][A'] = sum_{(s, d'), B'} conj(K)[A'][s][d'][B'] V2[s][d'][B'][A][c]
         //   (m = A', n = (A, c), k = ((s, d'), B'))
-        blk_gemm<2, 8>(KCy, V2, Ry, AB, CA, d * D, AB, AB * AB, AB, AB * CA, CA,
+        blk_gemm<TE, TE>(KCy, V2, Ry, AB, CA, d * D, AB, AB * AB, AB, AB * CA, CA,
                        [=](int m) { return Off2{m, m}; },
                        [=](int n) { return Off2{n, n * AB}; });
         blk_normalize(Ry, (int)rsz, red, &st);
@@ -284,12 +286,11 @@ __global__ void __launch_bounds__(NTHREADS, MinBlocks<T>::value) k_direct(G g, P
       blk_unit(Lp, (int)rsz);
       __syncthreads();
       for (int y = 0; y < Ly; ++y) {
-        const T* Ky = KT + (size_t)y * ksz;
-        const T* KCy = KC + (size_t)y * ksz;
+        ket_site(g, Eu + (size_t)y * g.se, Tpad + (size_t)(x * Ly + y) * d * g.sT, Ky, KCy);
         const T* Dg = Dn + (size_t)y * sd;
         const T* Rn = RP + (size_t)(y + 1) * rsz;
         // W1[s][B][c][dd][A'] = sum_A L[A][c][A'] K[A][s][dd][B]   (m = (A', c), n = (s dd, B), k = A)
-        blk_gemm<4, 4>(Lp, Ky, V1, CA, d * D * AB, AB, 1, CA, 0, 1, 0,
+        blk_gemm<TE, TE>(Lp, Ky, V1, CA, d * D * AB, AB, 1, CA, 0, 1, 0,
                        [=](int m) {
                          const int Ap = m % AB, cc = m / AB;
                          return Off2{cc * AB + Ap, cc * D * AB + Ap};
@@ -300,7 +301,7 @@ __global__ void __launch_bounds__(NTHREADS, MinBlocks<T>::value) k_direct(G g, P
                        });
         // W2[s][d'][A'][e][B] = sum_{c, dd} W1[s][B][c][dd][A'] D^l[c][(dd, d')][e]
         //   (m = (A', B, s), n = (d', e), k = (c, dd))
-        blk_gemm<4, 4>(V1, Dg, V2, AB * AB * d, D * chid, chid, D, D * AB, AB, P * chid, D * chid,
+        blk_gemm<2, 16>(V1, Dg, V2, AB * AB * d, D * chid, chid, D, D * AB, AB, P * chid, D * chid,
                        [=](int m) {
                          const int Ap = m % AB, B = (m / AB) % AB, s = m / (AB * AB);
                          return Off2{((s * AB + B) * chid * D) * AB + Ap, ((s * D * AB + Ap) * chid) * AB + B};
@@ -312,7 +313,7 @@ __global__ void __launch_bounds__(NTHREADS, MinBlocks<T>::value) k_direct(G g, P
         // cand_s[B][e][B'] = sum_{d', A'} W2[s][d'][A'][e][B] conj(K)[A'][s][d'][B']
         //   (per s: m = (B, e), n = B', k = (d', A'))
         for (int s = 0; s < d; ++s)
-          blk_gemm<4, 4>(V2 + (size_t)s * D * AB * CA, KCy + (size_t)s * D * AB * AB, LC + (size_t)s * rsz, CA, AB, D,
+          blk_gemm<TE, TE>(V2 + (size_t)s * D * AB * CA, KCy + (size_t)s * D * AB * AB, LC + (size_t)s * rsz, CA, AB, D,
                          AB, AB * CA, CA, AB * AB, 1,
                          [=](int m) {
                            const int B = m % AB, e = m / AB;
