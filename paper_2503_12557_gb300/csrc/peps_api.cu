@@ -193,11 +193,12 @@ static void place_overlay(Plan& p, size_t& smem, size_t budget, const std::vecto
 // Default shared-memory budget per CTA: FP64 one CTA per SM (the FP64 pipe is the limit), FP32
 // two CTAs per SM.
 // Default shared-memory budget per CTA and kernel class (0 env, 1 row, 2 pair, 3 sampler): FP64
-// one CTA per SM (the FP64 pipe is the limit); FP32 two CTAs per SM, except the environment
-// kernel, compiled for three (72 KB each, the row step's larger buffers in the L2-resident arena).
+// one CTA per SM (the FP64 pipe is the limit); FP32 two CTAs per SM, except the environment and
+// one-row sandwich kernels, which run three (72 KB each, the larger buffers in the L2-resident
+// arena; measured 10 % and 13 % faster at 8x8, D = 4, chi = 16).
 static size_t default_budget(const peps_handle* h, int cls) {
   if (h->esz >= 8) return 210 * 1024;
-  return cls == 0 ? 72 * 1024 : 110 * 1024;
+  return (cls == 0 || cls == 1) ? 72 * 1024 : 110 * 1024;
 }
 
 static void plan_all(peps_handle* h) {

@@ -9,6 +9,10 @@ mixture of boundary-MPS approximations can bias it.
 
 bound_energy: the mean of the variational-bound local energy (peps_local_energy_bound) over a
 configuration batch, with its standard error.
+
+contraction_error: the relative contraction error of Sec. "Contraction complexity indicators",
+Delta psi(D_c, D_c^max) = (psi(D_c^max) - psi(D_c)) / psi(D_c^max), from the amplitudes of two
+handles that differ only in the boundary bond dimension (or truncated-weight cutoff).
 """
 from __future__ import annotations
 
@@ -44,3 +48,13 @@ def bound_energy(h, H, S, cut):
     r = h.local_energy_bound(H, S, cut)
     e = r["eloc"][:, 0].double()
     return float(e.mean()), float(e.std() / np.sqrt(e.numel())), r
+
+
+def contraction_error(h_c, h_max, S):
+    """Delta psi(D_c, D_c^max) per configuration (complex), from peps_amplitudes of the handle
+    h_c (bond D_c) and h_max (bond D_c^max, the same parameters set on both):
+    1 - psi_c / psi_max = 1 - exp(ln|psi_c| - ln|psi_max|) e^{i (phase_c - phase_max)}."""
+    la, pa, sa = h_c.amplitudes(S)
+    lb, pb, sb = h_max.amplitudes(S)
+    z = torch.exp(la - lb) * torch.exp(1j * (pa - pb))
+    return 1.0 - z, sa | sb

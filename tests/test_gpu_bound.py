@@ -136,3 +136,26 @@ def test_bound_rejects_bad_cut(P):
     for cut in (0, 4):
         with pytest.raises(RuntimeError):
             h.local_energy_bound(I.heisenberg(lat), S, cut)
+
+
+def test_contraction_error_vs_oracle(P):
+    # Delta psi(D_c, D_c^max) = 1 - psi(D_c) / psi(D_c^max), the paper's relative contraction error
+    from oracle import tn
+    from paper_2503_12557_gb300 import estimators
+    lat = I.Lattice(5, 6, 2, 3)
+    th = I.peps_random(lat, 65, scale=0.5, bias=1.0)
+    S = I.configs_uniform_sz0(lat, 10, 66)
+    hs, hl = P.PEPS(5, 6, 2, 3, 3, max_samples=10), P.PEPS(5, 6, 2, 3, 12, max_samples=10)
+    for h in (hs, hl):
+        h.set_params(torch.as_tensor(th).cuda())
+    dpsi, st = estimators.contraction_error(hs, hl, torch.as_tensor(S).cuda())
+    torch.cuda.synchronize()
+    ref = []
+    for s in S:
+        a = tn.log_amplitude(th, s, lat, 3)
+        b = tn.log_amplitude(th, s, lat, 12)
+        ref.append(1.0 - np.exp(a[0] - b[0]) * np.exp(1j * (a[1] - b[1])))
+    ref = np.array(ref)
+    ok = (st.cpu().numpy() & 1) == 0
+    assert np.max(np.abs(dpsi.cpu().numpy() - ref)[ok]) <= 1e-9
+    assert np.max(np.abs(ref)) > 1e-6      # chi = 3 is a real truncation here
