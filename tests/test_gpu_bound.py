@@ -159,3 +159,39 @@ def test_contraction_error_vs_oracle(P):
     ok = (st.cpu().numpy() & 1) == 0
     assert np.max(np.abs(dpsi.cpu().numpy() - ref)[ok]) <= 1e-9
     assert np.max(np.abs(ref)) > 1e-6      # chi = 3 is a real truncation here
+
+
+def test_bound_with_truncated_weight_cutoff(P):
+    from oracle import bound
+    lat = I.Lattice(5, 4, 2, 3)
+    th = I.peps_random(lat, 67, scale=0.5, bias=1.0)
+    S = I.configs_uniform_sz0(lat, 8, 68)
+    H = I.heisenberg(lat)
+    h = P.PEPS(5, 4, 2, 3, 7, max_samples=8, trunc_weight=2e-3)
+    h.set_params(torch.as_tensor(th).cuda())
+    r = h.local_energy_bound(H, torch.as_tensor(S).cuda(), 2)
+    torch.cuda.synchronize()
+    res = {k: v.cpu().numpy() for k, v in r.items()}
+    _compare(res, bound.evaluate_bound(th, S, lat, (7, 2e-3), H, 2))
+
+
+def test_bound_complex64(P):
+    from oracle import bound
+    lat = I.Lattice(4, 4, 2, 2)
+    th = I.peps_random(lat, 69, scale=0.6, bias=1.0, complex_=True)
+    S = I.configs_uniform_sz0(lat, 8, 70)
+    H = I.j1j2_chiral(lat)
+    res = _run(P, lat, 3, th, S, H, 2, prec=1, cplx=True)
+    ref = bound.evaluate_bound(th, S, lat, 3, H, 2)
+    assert np.max(np.abs(res["logabs"] - ref["logabs"])) < 1e-4
+    e = res["eloc"][:, 0] + 1j * res["eloc"][:, 1]
+    assert np.max(np.abs(e - ref["eloc"]) / np.maximum(1.0, np.abs(ref["eloc"]))) < 1e-3
+
+
+def test_bound_empty_batch(P):
+    lat = I.Lattice(4, 4, 2, 2)
+    h = P.PEPS(4, 4, 2, 2, 3, max_samples=4)
+    h.set_params(torch.as_tensor(I.peps_random(lat, 1)).cuda())
+    r = h.local_energy_bound(I.heisenberg(lat), torch.zeros(0, 16, dtype=torch.uint8).cuda(), 2)
+    torch.cuda.synchronize()
+    assert r["eloc"].shape == (0, 2)

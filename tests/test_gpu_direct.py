@@ -119,3 +119,39 @@ def test_direct_errors(P):
         h.direct_sample(2)            # no double-layer environments yet
     with pytest.raises(RuntimeError):
         h.direct_prepare(0)
+
+
+def test_direct_with_truncated_weight_cutoff(P):
+    # the upper environments of the drawn rows under the truncated-weight rule (dynamic chi)
+    from oracle import direct
+    lat = I.Lattice(4, 5, 2, 2)
+    th = I.peps_random(lat, 99, scale=0.6, bias=1.0)
+    h = P.PEPS(4, 5, 2, 2, 4, max_samples=16, trunc_weight=2e-3)
+    h.set_params(torch.as_tensor(th).cuda())
+    h.direct_prepare(3)
+    S, lp, _ = h.direct_sample(16, seed=21, draw=3)
+    torch.cuda.synchronize()
+    Sr, lpr, _ = direct.sample(th, lat, (4, 2e-3), 3, 16, seed=21, draw=3)
+    assert np.array_equal(S.cpu().numpy(), Sr)
+    assert np.max(np.abs(lp.cpu().numpy() - lpr)) <= 1e-10
+
+
+def test_direct_complex64(P):
+    from oracle import direct
+    lat = I.Lattice(4, 3, 2, 2)
+    th = I.peps_random(lat, 101, scale=0.6, bias=1.0, complex_=True)
+    _, S, lp, _ = _draw(P, lat, 3, 2, th, 24, seed=5, draw=1, prec=1, cplx=True)
+    Sr, lpr, _ = direct.sample(th, lat, 3, 2, 24, seed=5, draw=1)
+    same = np.all(S == Sr, axis=1)
+    assert same.sum() >= 0.9 * len(S)
+    assert np.max(np.abs(lp - lpr)[same]) < 1e-4
+
+
+def test_direct_empty_batch(P):
+    lat = I.Lattice(4, 4, 2, 2)
+    h = P.PEPS(4, 4, 2, 2, 3, max_samples=4)
+    h.set_params(torch.as_tensor(I.peps_random(lat, 1)).cuda())
+    h.direct_prepare(2)
+    S, lp, st = h.direct_sample(0)
+    torch.cuda.synchronize()
+    assert S.shape == (0, 16) and lp.numel() == 0
