@@ -127,6 +127,14 @@ class _Clocks:
             self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "200",
                                        "-i", str(int(os.environ.get("LOCAL_RANK", "0")))],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
+            # nvidia-smi's start-up (NVML initialisation) can stall the GPU briefly: let it reach
+            # its first reading before the timed region starts (at most 5 s)
+            t0 = time.time()
+            while time.time() - t0 < 5.0 and self.p.poll() is None:
+                if os.path.getsize(self.path) > 0:
+                    break
+                time.sleep(0.05)
+            time.sleep(0.3)
         except Exception:
             self.p = None
         return self
