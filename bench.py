@@ -233,8 +233,13 @@ def run_gpu(a):
     # burn-in sweeps from the Neel start, untimed
     h.sample(S, P.MOVE_EXCHANGE, a.burnin, seed=w["seed_chain"] + 7919 * rank, sweep0=0, accepted=acc)
     sweep_ctr[0] = a.burnin
-    for _ in range(a.warmup):
-        step()
+    for i in range(a.warmup):
+        if i == a.warmup - 1:
+            h.timing(True)  # the library's event pool and counters come up outside the timed region
+        r, _ = step()
+        # the timed loop's reduction too: torch loads its kernel module on first use, which on a
+        # freshly started machine can take most of a second
+        eloc_warm = r["eloc"][:, 0].mean()
     torch.cuda.synchronize()
     # ---- timed region (device events on the launching stream)
     h.timing(True)
@@ -245,15 +250,18 @@ def run_gpu(a):
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
+        marks = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
         e0.record(stream)
-        for _ in range(a.steps):
+        for k in range(a.steps):
             r, _ = step()
             eloc_means.append(r["eloc"][:, 0].mean())
+            marks[k].record(stream)
         e1.record(stream)
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
     ms_total = e0.elapsed_time(e1)
+    step_ms = [e0.elapsed_time(marks[0])] + [marks[k - 1].elapsed_time(marks[k]) for k in range(1, a.steps)]
     ms_cls, launches, ctr = h.timing_read()
     h.timing(False)
     ms_step = ms_total / a.steps
@@ -302,7 +310,7 @@ def run_gpu(a):
     line = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if prec == P.PREC_FP32 else "f64", "data": "synthetic",
-            "config": _config(w, ns, a.prec, a.sweeps), "minsr_step_s": minsr_s,
+            "config": _config(w, ns, a.prec, a.sweeps), "step_ms": step_ms, "minsr_step_s": minsr_s,
             "minsr": {"gram": "split-BF16 tcgen05" if mixed else "FP64 CUDA cores",
                       "solve": "FP64 Cholesky",
                       "gram_ms": ms_cls["minsr_gram"] / a.steps, "solve_ms": ms_cls["minsr_eig"] / a.steps,
