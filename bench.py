@@ -171,19 +171,19 @@ def _peaks():
         return {}
 
 
-# DRAM bytes (read + write) of one k_sample launch, from the ncu capture summarised in
-# profiles/k_sample_heis8x8_D4_chi16_ns304.md: 264 MB + 1374 MB for 304 chains x 2 sweeps in FP32
-# (the full 4096-chain launch exceeds the capture size the profiling rules allow), scaled by the
-# chains processed (each chain's environment rows and partials are its own traffic).
-_K_SAMPLE_CAPTURE = {"bytes": 264e6 + 1374e6, "chains": 304, "sweeps": 2, "precision": "fp32"}
+# DRAM bytes (read + write) of one sampler call of 2 sweeps in FP32 (every kernel of the split
+# sweep), from an ncu capture of 304 chains, scaled by the chains processed (each chain's
+# environment rows and partials are its own traffic); None until such a capture of the current
+# kernels exists.
+_SAMPLER_CAPTURE = None
 
 
 def _measured_traffic(kernel, ns, sweeps, prec):
-    """Per-launch DRAM traffic of the dominant kernel from its ncu capture, or None where no
-    capture of the current kernel at this precision and sweep count exists."""
+    """Per-call DRAM traffic of the dominant kernel (set) from its ncu capture, or None where no
+    capture of the current kernels at this precision and sweep count exists."""
     from paper_2503_12557_gb300 import peps as P
-    c = _K_SAMPLE_CAPTURE
-    if kernel == "sample" and prec == P.PREC_FP32 and sweeps == c["sweeps"]:
+    c = _SAMPLER_CAPTURE
+    if c and kernel == "sample" and prec == P.PREC_FP32 and sweeps == c["sweeps"]:
         return c["bytes"] * ns / c["chains"]
     return None
 
@@ -297,7 +297,9 @@ def run_gpu(a):
     dom_launch_ms = ms_cls[dom] / max(1, launches[dom])
     achieved = flops[dom] / max(1, launches[dom]) / (dom_launch_ms / 1e3) / 1e12
     peak = (fp64_peak if not mixed else peaks.get("bf16_tflops", 1900.0)) if dom == "minsr_gram" else alu_peak
-    roof = {"kernel": {"env": "k_env", "sample": "k_sample", "row": "k_row", "pair": "k_pair",
+    sampler_name = ("sampler sweeps (per sweep: k_env lower, then k_sweep_moves and k_env_row per row)"
+                    if prec == P.PREC_FP32 else "k_sample")
+    roof = {"kernel": {"env": "k_env", "sample": sampler_name, "row": "k_row", "pair": "k_pair",
                        "minsr_gram": "k_gram"}[dom],
             "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": _measured_traffic(dom, ns, a.sweeps, prec),

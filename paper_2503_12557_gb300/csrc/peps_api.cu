@@ -867,8 +867,9 @@ extern "C" peps_status peps_sample(peps_handle* h, int move, uint8_t* S_dev, int
   const int ts = tstart(h, TC_SAMPLE, s);
   cudaError_t e = dispatch_elem(h, [&](auto z) {
     using T = decltype(z);
-    return launch_sample<T>(h->g, k.p, grid, k.smem, (const T*)h->Tpad, S_dev, Ns, move, nsweeps, seed, sweep0,
-                            (T*)h->envs, h->logs, accepted_dev, st, s);
+    const KPlan& ke = h->kp[0];
+    return launch_sample<T>(h->g, k.p, grid, k.smem, ke.p, std::min(ke.grid, Ns), ke.smem, (const T*)h->Tpad, S_dev, Ns,
+                            move, nsweeps, seed, sweep0, (T*)h->envs, h->logs, accepted_dev, st, s);
   });
   if (e != cudaSuccess) return cuda_fail(h, e, "sampler kernel");
   tstop(h, ts, s);

@@ -47,9 +47,10 @@ cudaError_t launch_pair(const Geo& g, const Plan& p, int grid, size_t smem, cons
                         const T* envs, const double* logs, const TermTab& tt, double* pairout, int* status,
                         cudaStream_t s);
 template <typename T>
-cudaError_t launch_sample(const Geo& g, const Plan& p, int grid, size_t smem, const T* Tpad, uint8_t* S, int Ns,
-                          int move, int nsweeps, unsigned long long seed, unsigned long long sweep0, T* envs,
-                          double* logs, long long* accepted, int* status, cudaStream_t s);
+cudaError_t launch_sample(const Geo& g, const Plan& p, int grid, size_t smem, const Plan& pe, int grid_e,
+                          size_t smem_e, const T* Tpad, uint8_t* S, int Ns, int move, int nsweeps,
+                          unsigned long long seed, unsigned long long sweep0, T* envs, double* logs,
+                          long long* accepted, int* status, cudaStream_t s);
 template <typename T>
 cudaError_t launch_bound(const Geo& g, const Plan& p, int grid, size_t smem, const T* Tpad, const uint8_t* S, int Ns,
                          int cut, const T* envs, const double* logs, const TermTab& tt, double* bout, double* logabs,

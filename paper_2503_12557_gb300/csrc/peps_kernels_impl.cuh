@@ -690,6 +690,225 @@ __global__ void __launch_bounds__(NTHREADS, MinBlocks<T>::value) k_sample(G g, P
 }
 
 // ------------------------------------------------------------------------------------------
+// The Metropolis sweep split by rows (FP32: the row steps then run at the environment kernel's
+// occupancy).  One sweep = k_env (lower environments of every chain), then for x = 0 .. Lx-1:
+// k_sweep_moves(x) (the in-row moves with psi_x and the vertical moves of rows x, x+1, exactly
+// as in k_sample) and k_env_row(x) (E^u[x] from the updated row).  The random slots continue
+// across rows as in k_sample: row x starts at x (moves per row + vertical moves per row).
+template <typename T, typename G>
+__global__ void __launch_bounds__(NTHREADS, MinBlocks<T>::value) k_sweep_moves(G g, Plan plan,
+                                                        const T* __restrict__ Tpad, uint8_t* S, int Ns, int move,
+                                                        int x, unsigned long long seed, unsigned long long sweep_id,
+                                                        T* envs, double* logs, long long* accepted, int* status) {
+  extern __shared__ __align__(16) char smem[];
+  char* gbase = plan.gbase;
+  T* RP = (T*)buf_ptr(plan, B_RP, smem, gbase);
+  T* t1 = (T*)buf_ptr(plan, B_T1, smem, gbase);
+  T* t2 = (T*)buf_ptr(plan, B_T2, smem, gbase);
+  T* eu = (T*)buf_ptr(plan, B_EU, smem, gbase);
+  T* el = (T*)buf_ptr(plan, B_EL, smem, gbase);
+  T* A1 = (T*)buf_ptr(plan, B_A, smem, gbase);
+  T* A2 = (T*)buf_ptr(plan, B_A2, smem, gbase);
+  T* LW = (T*)buf_ptr(plan, B_LW, smem, gbase);
+  T* LW2 = (T*)buf_ptr(plan, B_LW2, smem, gbase);
+  T* LC = (T*)buf_ptr(plan, B_LP, smem, gbase);
+  uint8_t* Sl = (uint8_t*)buf_ptr(plan, B_S, smem, gbase);
+  double* red = (double*)buf_ptr(plan, B_RED, smem, gbase);
+  __shared__ double logR[MAX_LY + 1];
+  __shared__ double logLc, lcur;
+  __shared__ int st, accept_flag;
+  const int N = g.Lx * g.Ly, Ly = g.Ly, Lx = g.Lx, se = g.se, s2 = g.s2;
+  const size_t rowsz = (size_t)Ly * se;
+  const int nmv = (move == 0) ? Ly - 1 : Ly;
+  unsigned slot0 = (unsigned)x * (unsigned)(nmv + ((move == 0) ? Ly : 0));
+  for (int c = blockIdx.x; c < Ns; c += gridDim.x) {
+    uint8_t* Sg = S + (size_t)c * N;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) Sl[i] = Sg[i];
+    if (threadIdx.x == 0) st = 0;
+    long long acc = 0;
+    T* env = envs + (size_t)c * env_sample_elems(g);
+    double* lg = logs + (size_t)c * 2 * Lx;
+    if (x == 0) {
+      T* trivial = env + (size_t)slot_up(g, -1) * rowsz;
+      for (int k = 0; k < Ly; ++k) blk_unit(trivial + (size_t)k * se, se);
+      if (threadIdx.x == 0) lg[slot_up(g, -1)] = 0.0;
+    }
+    __syncthreads();
+    unsigned slot = slot0;
+    const T* EU = env + (size_t)slot_up(g, x - 1) * rowsz;
+    // ---- moves inside row x with psi_x (E^u[x-1], E^l[x+1])
+    {
+      const T* EL = env + (size_t)slot_lo(g, x + 1) * rowsz;
+      blk_unit(RP + (size_t)Ly * se, se);
+      if (threadIdx.x == 0) logR[Ly] = 0.0;
+      __syncthreads();
+      for (int y = Ly - 1; y >= 0; --y) {
+        blk_copy(eu, EU + (size_t)y * se, se);
+        blk_copy(el, EL + (size_t)y * se, se);
+        load_A(A1, Tpad, g, x * Ly + y, Sl[x * Ly + y], false);
+        __syncthreads();
+        absorb1_right(g, RP + (size_t)(y + 1) * se, eu, A1, el, t1, t2, RP + (size_t)y * se);
+        const double l = blk_normalize(RP + (size_t)y * se, se, red, &st);
+        if (threadIdx.x == 0) logR[y] = logR[y + 1] + l;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        const double v = dz_abs(to_dz(RP[0]));
+        lcur = (v != 0.0) ? log(v) + logR[0] : -INFINITY;
+        logLc = 0.0;
+      }
+      blk_unit(LC, se);
+      __syncthreads();
+      for (int y = 0; y < nmv; ++y) {
+        const double u = uniform53(slot, (uint32_t)sweep_id, (uint32_t)c, 0u, seed);
+        ++slot;
+        const int i0 = x * Ly + y, i1 = i0 + 1;
+        const bool possible = (move == 0) ? (Sl[i0] != Sl[i1]) : true;
+        if (possible) {
+          const int w_ = (move == 0) ? 2 : 1;
+          blk_copy(LW, LC, se);
+          __syncthreads();
+          double lw = logLc;
+          for (int cc = 0; cc < w_; ++cc) {
+            const int site = i0 + cc;
+            int s_new;
+            if (move == 0) s_new = (cc == 0) ? Sl[i1] : Sl[i0];
+            else s_new = g.d - 1 - Sl[site];
+            blk_copy(eu, EU + (size_t)(y + cc) * se, se);
+            blk_copy(el, EL + (size_t)(y + cc) * se, se);
+            load_A(A1, Tpad, g, site, s_new, false);
+            __syncthreads();
+            absorb1(g, LW, eu, A1, el, t1, t2, LW2);
+            lw += blk_normalize(LW2, se, red, &st);
+            blk_copy(LW, LW2, se);
+            __syncthreads();
+          }
+          const T v = blk_dot(LW, RP + (size_t)(y + w_) * se, se, red);
+          if (threadIdx.x == 0) {
+            const double av = dz_abs(to_dz(v));
+            const double l1 = (av != 0.0) ? log(av) + lw + logR[y + w_] : -INFINITY;
+            accept_flag = (isfinite(l1) && u < exp(2.0 * (l1 - lcur))) ? 1 : 0;
+            if (accept_flag) {
+              lcur = l1;
+              if (move == 0) { const uint8_t tmp = Sl[i0]; Sl[i0] = Sl[i1]; Sl[i1] = tmp; }
+              else Sl[i0] = (uint8_t)(g.d - 1 - Sl[i0]);
+            }
+          }
+          __syncthreads();
+          acc += accept_flag;
+        }
+        blk_copy(eu, EU + (size_t)y * se, se);
+        blk_copy(el, EL + (size_t)y * se, se);
+        load_A(A1, Tpad, g, x * Ly + y, Sl[x * Ly + y], false);
+        __syncthreads();
+        absorb1(g, LC, eu, A1, el, t1, t2, LW2);
+        const double l = blk_normalize(LW2, se, red, &st);
+        blk_copy(LC, LW2, se);
+        if (threadIdx.x == 0) logLc += l;
+        __syncthreads();
+      }
+    }
+    // ---- vertical moves (x, y) <-> (x+1, y) with psi_{x,x+1} (E^u[x-1], E^l[x+2])
+    if (move == 0 && x < Lx - 1) {
+      const T* EL2 = env + (size_t)slot_lo(g, x + 2) * rowsz;
+      blk_unit(RP + (size_t)Ly * s2, s2);
+      if (threadIdx.x == 0) logR[Ly] = 0.0;
+      __syncthreads();
+      for (int y = Ly - 1; y >= 0; --y) {
+        blk_copy(eu, EU + (size_t)y * se, se);
+        blk_copy(el, EL2 + (size_t)y * se, se);
+        load_A(A1, Tpad, g, x * Ly + y, Sl[x * Ly + y], false);
+        load_A(A2, Tpad, g, (x + 1) * Ly + y, Sl[(x + 1) * Ly + y], false);
+        __syncthreads();
+        absorb2_right(g, RP + (size_t)(y + 1) * s2, eu, A1, A2, el, t1, t2, RP + (size_t)y * s2, plan.cx);
+        const double l = blk_normalize(RP + (size_t)y * s2, s2, red, &st);
+        if (threadIdx.x == 0) logR[y] = logR[y + 1] + l;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        const double v = dz_abs(to_dz(RP[0]));
+        lcur = (v != 0.0) ? log(v) + logR[0] : -INFINITY;
+        logLc = 0.0;
+      }
+      blk_unit(LC, s2);
+      __syncthreads();
+      for (int y = 0; y < Ly; ++y) {
+        const double u = uniform53(slot, (uint32_t)sweep_id, (uint32_t)c, 0u, seed);
+        ++slot;
+        const int i0 = x * Ly + y, i1 = (x + 1) * Ly + y;
+        blk_copy(eu, EU + (size_t)y * se, se);
+        blk_copy(el, EL2 + (size_t)y * se, se);
+        if (Sl[i0] != Sl[i1]) {
+          load_A(A1, Tpad, g, i0, Sl[i1], false);
+          load_A(A2, Tpad, g, i1, Sl[i0], false);
+          __syncthreads();
+          absorb2(g, LC, eu, A1, A2, el, t1, t2, LW2, plan.cx);
+          const double lw = logLc + blk_normalize(LW2, s2, red, &st);
+          const T v = blk_dot(LW2, RP + (size_t)(y + 1) * s2, s2, red);
+          if (threadIdx.x == 0) {
+            const double av = dz_abs(to_dz(v));
+            const double l1 = (av != 0.0) ? log(av) + lw + logR[y + 1] : -INFINITY;
+            accept_flag = (isfinite(l1) && u < exp(2.0 * (l1 - lcur))) ? 1 : 0;
+            if (accept_flag) {
+              lcur = l1;
+              const uint8_t tmp = Sl[i0]; Sl[i0] = Sl[i1]; Sl[i1] = tmp;
+            }
+          }
+          __syncthreads();
+          acc += accept_flag;
+        }
+        load_A(A1, Tpad, g, i0, Sl[i0], false);
+        load_A(A2, Tpad, g, i1, Sl[i1], false);
+        __syncthreads();
+        absorb2(g, LC, eu, A1, A2, el, t1, t2, LW2, plan.cx);
+        const double l = blk_normalize(LW2, s2, red, &st);
+        blk_copy(LC, LW2, s2);
+        if (threadIdx.x == 0) logLc += l;
+        __syncthreads();
+      }
+    }
+    for (int i = threadIdx.x; i < N; i += blockDim.x) Sg[i] = Sl[i];
+    if (threadIdx.x == 0) {
+      if (accepted) accepted[c] += acc;
+      if (st) atomicOr(status + c, st);
+    }
+    __syncthreads();
+  }
+}
+
+// E^u[x] of every chain from its (updated) row x: the first row for x = 0, else one row step
+// from E^u[x-1]; compiled for the environment kernel's occupancy.
+template <typename T, typename G>
+__global__ void __launch_bounds__(NTHREADS, EnvBlocks<T>::value) k_env_row(G g, Plan plan, const T* __restrict__ Tpad,
+                                                      const uint8_t* __restrict__ S, int Ns, int x, T* envs,
+                                                      double* logs, int* status) {
+  extern __shared__ __align__(16) char smem[];
+  char* gbase = plan.gbase;
+  RowWork<T> w = carve_row<T>(plan, smem, gbase);
+  __shared__ int st, flag;
+  __shared__ float wd;
+  const int N = g.Lx * g.Ly;
+  const size_t rowsz = (size_t)g.Ly * g.se;
+  for (int c = blockIdx.x; c < Ns; c += gridDim.x) {
+    if (threadIdx.x == 0) { st = 0; wd = 0.f; }
+    __syncthreads();
+    T* env = envs + (size_t)c * env_sample_elems(g);
+    double* lg = logs + (size_t)c * 2 * g.Lx;
+    const uint8_t* Ss = S + (size_t)c * N;
+    const size_t sl = (size_t)slot_up(g, x) * rowsz;
+    double l;
+    if (x == 0) l = env_first_row(g, env + sl, Tpad, 0, Ss, false, w.A, w.Z, w.red, &st);
+    else l = lg[slot_up(g, x - 1)] + env_row_step(g, env + (size_t)slot_up(g, x - 1) * rowsz, env + sl, Tpad, x,
+                                                  Ss + (size_t)x * g.Ly, false, w, &st, &wd, &flag);
+    if (threadIdx.x == 0) {
+      lg[slot_up(g, x)] = l;
+      if (st) atomicOr(status + c, st);
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------------------------------
 // Variational-bound local energy with one fixed cut: every amplitude is
 // psi_i(S) = E^u[i-1](S) . E^l[i](S) (0-based rows; the upper MPS holds rows 0..i-1).  One work
 // item per (sample, term): for every off-diagonal entry h[a][b] of the term the environments of
@@ -908,21 +1127,59 @@ PEPS_KATTR(kattr_pair, k_pair)
 #endif
 
 #ifdef PEPS_PART_SAMPLE
+// FP32 runs the sweep split by rows (k_env for the lower environments, then k_sweep_moves and
+// k_env_row per row; the environment plan pe / grid_e / smem_e for the row steps); the other
+// precisions run the single-launch k_sample.
 template <typename T>
-cudaError_t launch_sample(const Geo& g, const Plan& p, int grid, size_t smem, const T* Tpad, uint8_t* S, int Ns,
-                          int move, int nsweeps, unsigned long long seed, unsigned long long sweep0, T* envs,
-                          double* logs, long long* accepted, int* status, cudaStream_t s) {
+cudaError_t launch_sample(const Geo& g, const Plan& p, int grid, size_t smem, const Plan& pe, int grid_e,
+                          size_t smem_e, const T* Tpad, uint8_t* S, int Ns, int move, int nsweeps,
+                          unsigned long long seed, unsigned long long sweep0, T* envs, double* logs,
+                          long long* accepted, int* status, cudaStream_t s) {
   return with_geo_for<T>(g, [&](auto gg) {
-    k_sample<T, decltype(gg)><<<grid, NTHREADS, smem, s>>>(gg, p, Tpad, S, Ns, move, nsweeps, seed, sweep0, envs, logs,
-                                                           accepted, status);
+    using GG = decltype(gg);
+    if constexpr (sizeof(T) == 4) {
+      for (int t = 0; t < nsweeps; ++t) {
+        k_env<T, GG><<<grid_e, NTHREADS, smem_e, s>>>(gg, pe, Tpad, S, Ns, 2, envs, logs, status, nullptr);
+        for (int x = 0; x < g.Lx; ++x) {
+          k_sweep_moves<T, GG><<<grid, NTHREADS, smem, s>>>(gg, p, Tpad, S, Ns, move, x, seed, sweep0 + t, envs, logs,
+                                                            accepted, status);
+          if (x < g.Lx - 1) k_env_row<T, GG><<<grid_e, NTHREADS, smem_e, s>>>(gg, pe, Tpad, S, Ns, x, envs, logs, status);
+        }
+      }
+    } else {
+      k_sample<T, GG><<<grid, NTHREADS, smem, s>>>(gg, p, Tpad, S, Ns, move, nsweeps, seed, sweep0, envs, logs,
+                                                   accepted, status);
+    }
     return cudaGetLastError();
   });
 }
-PEPS_KATTR(kattr_sample, k_sample)
+template <typename T>
+cudaError_t kattr_sample(const Geo& g, size_t set_bytes, int* occ, size_t occ_smem) {
+  return with_geo_for<T>(g, [&](auto gg) {
+    using GG = decltype(gg);
+    cudaError_t e = cudaSuccess;
+    if (set_bytes) {
+      e = cudaFuncSetAttribute(k_sample<T, GG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)set_bytes);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_sweep_moves<T, GG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)set_bytes);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_env_row<T, GG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)set_bytes);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_env<T, GG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)set_bytes);
+    }
+    if (e == cudaSuccess && occ) {
+      if constexpr (sizeof(T) == 4)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_sweep_moves<T, GG>, NTHREADS, occ_smem);
+      else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_sample<T, GG>, NTHREADS, occ_smem);
+    }
+    return e;
+  });
+}
 #define PEPS_INST_SAMPLE(T)                                                                                       \
-  template cudaError_t launch_sample<T>(const Geo&, const Plan&, int, size_t, const T*, uint8_t*, int, int, int,   \
-                                        unsigned long long, unsigned long long, T*, double*, long long*, int*,    \
-                                        cudaStream_t);                                                            \
+  template cudaError_t launch_sample<T>(const Geo&, const Plan&, int, size_t, const Plan&, int, size_t, const T*, \
+                                        uint8_t*, int, int, int, unsigned long long, unsigned long long, T*,      \
+                                        double*, long long*, int*, cudaStream_t);                                 \
   template cudaError_t kattr_sample<T>(const Geo&, size_t, int*, size_t);
 #endif
 

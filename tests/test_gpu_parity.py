@@ -434,3 +434,27 @@ def test_sampler_chains_match_oracle(P, move, lat, chi, H):
     assert np.array_equal(Sd.cpu().numpy(), Sref)
     assert np.array_equal(acc.cpu().numpy(), acc_ref)
     assert acc_ref.sum() > 0
+
+
+def test_fp32_sampler_chains_close_to_oracle(P):
+    # the FP32 sampler (the sweep split by rows: lower environments, per-row moves, per-row
+    # E^u steps) against the FP64 oracle's chains: FP32 ratios decide like the oracle's except
+    # where a uniform falls within rounding of an acceptance probability
+    from oracle import sampler
+    lat = I.Lattice(4, 5, 2, 2)
+    th = I.peps_random(lat, 43, scale=0.5, bias=1.0)
+    S0 = I.configs_neel(lat, 24)
+    h = _handle(P, lat, 3, 24, prec=1)
+    h.set_params(_dev(th))
+    Sd, acc, st = h.sample(_dev(S0), move=P.MOVE_EXCHANGE, nsweeps=2, seed=19, sweep0=3)
+    torch.cuda.synchronize()
+    Sref, acc_ref, _ = sampler.run_chains(th, S0, lat, 3, "exchange", 19, 2, sweep0=3)
+    same = np.all(Sd.cpu().numpy() == Sref, axis=1)
+    assert same.sum() >= 22, same.sum()
+    assert np.array_equal(acc.cpu().numpy()[same], acc_ref[same])
+    assert acc_ref.sum() > 0
+    # flips (the Rydberg move) through the same path
+    Sf, accf, _ = h.sample(_dev(S0), move=P.MOVE_FLIP, nsweeps=1, seed=23)
+    torch.cuda.synchronize()
+    Sfr, accfr, _ = sampler.run_chains(th, S0, lat, 3, "flip", 23, 1)
+    assert np.all(Sf.cpu().numpy() == Sfr, axis=1).sum() >= 22
