@@ -215,6 +215,7 @@ def run_gpu(a):
     h = P.PEPS(lat.Lx, lat.Ly, lat.d, lat.D, w["chi"], prec=prec, max_samples=ns, gram=0, solve=0)
     theta = torch.as_tensor(theta0).cuda()
     h.set_params(theta)
+    h.set_env_reuse(True)  # the evaluation takes the sampler's upper environments (cached, unchanged S)
     S = torch.as_tensor(S0).cuda()
     acc = torch.zeros(ns, dtype=torch.int64, device="cuda")
     O = torch.empty(ns, h.Np, dtype=h.odtype, device="cuda")

@@ -161,6 +161,19 @@ peps_status peps_evaluate(peps_handle* h, const peps_hamiltonian* H, const uint8
                           double* logabs_dev, double* phase_dev, double* eloc_dev, void* O_dev,
                           int32_t* status_dev, void* stream);
 
+/* Reuse of cached environments between sampling and evaluation (Sec. "On reusing environments";
+ * opt-in, off by default).  After a Metropolis sweep of the FP32 real-PEPS sampler the stored
+ * upper environments E^u[0..Lx-2] are those of the final configurations (every row is final
+ * once its own moves are done).  With enable = 1, a peps_evaluate / peps_local_energy /
+ * peps_amplitudes / peps_logderiv call whose S_dev and Ns are those of the last peps_sample on
+ * this handle, with no parameter change (peps_set_params / peps_apply_update) and no other
+ * call that rewrites the environments in between, takes them from the store and contracts
+ * only the lower side (peps_amplitudes: nothing); the status bits of the upper row steps
+ * come from the sampler's last sweep.  The caller promises that S_dev was not modified in
+ * between.  Results equal those of a full evaluation.  Other precisions and complex handles
+ * always recompute.  PEPS_E_ARG for enable outside {0, 1}. */
+peps_status peps_set_env_reuse(peps_handle* h, int enable);
+
 /* Direct sampling (Sec. "On Direct Sampling" and the appendix "Direct sampling of PEPS",
  * Alg. `sampling`): independent configurations drawn row by row from the conditional reduced
  * density matrix rho_{S<i}[i] = T^u . D^l[i+1] . T^u*, with T^u = E^u[i-1](S) . T[i] (kept

@@ -53,6 +53,13 @@ struct peps_handle {
   KPlan kd;
   char* dscratch = nullptr;
   size_t dscratch_bytes = 0;
+  // reuse of the sampler's upper environments by the next evaluation (opt-in): the last
+  // sampled batch (pointer, size, parameter generation) and the upper row steps' status bits
+  int env_reuse = 0;
+  const uint8_t* rs_S = nullptr;
+  int rs_Ns = 0;
+  long long param_gen = 0, rs_gen = -1;
+  int* ustat = nullptr;
   // Hamiltonian cache
   std::vector<char> ham_key;
   std::vector<int> h_tinfo, h_ab, h_rowoff, h_pairoff, h_pij;
@@ -401,6 +408,7 @@ extern "C" peps_status peps_create(peps_handle** out, const peps_config* cfg) {
   if (cudaMalloc(&h->rowout, sizeof(double) * 4 * (size_t)c.max_samples * c.Lx) != cudaSuccess) return bad(PEPS_E_WORKSPACE, "rowout");
   if (cudaMalloc(&h->pairout, sizeof(double) * 4 * (size_t)c.max_samples * c.Lx) != cudaSuccess) return bad(PEPS_E_WORKSPACE, "pairout");
   if (cudaMalloc(&h->status_tmp, sizeof(int) * (size_t)c.max_samples) != cudaSuccess) return bad(PEPS_E_WORKSPACE, "status");
+  if (cudaMalloc(&h->ustat, sizeof(int) * (size_t)c.max_samples) != cudaSuccess) return bad(PEPS_E_WORKSPACE, "status");
   cudaMemset(h->Tpad, 0, (size_t)N * c.d * g.sT * h->esz);
   plan_all(h);
   peps_status st = finish_plans(h);
@@ -419,7 +427,7 @@ extern "C" peps_status peps_destroy(peps_handle* h) {
                   h->gscratch, h->d_tinfo, h->d_ab, h->d_eh, h->d_rowoff, h->d_pairoff, h->d_pij, h->d_pv,
                   h->d_onsite, h->Obar, h->Tm, h->Vm, h->Hm, h->mean, h->ebar, h->yv, h->xv, h->cnt, h->ctr,
                   h->lp_Sp, h->lp_l0, h->lp_l1, h->lp_aux, h->g_hi, h->g_lo, h->bout, h->DL, h->dl_work,
-                  h->dl_status, h->dscratch};
+                  h->dl_status, h->dscratch, h->ustat};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t e : h->evpool) cudaEventDestroy(e);
@@ -433,6 +441,7 @@ extern "C" const char* peps_last_error(const peps_handle* h) { return (h && !h->
 
 extern "C" peps_status peps_set_params(peps_handle* h, const double* theta_dev, void* stream) {
   if (!h || !theta_dev) return fail(h, PEPS_E_ARG, "null argument");
+  ++h->param_gen;  // stored environments no longer belong to the parameters
   cudaStream_t s = (cudaStream_t)stream;
   const int ts = tstart(h, TC_PAD, s);
   cudaError_t e = dispatch_elem(h, [&](auto z) {
@@ -587,9 +596,19 @@ static peps_status run_eval(peps_handle* h, const peps_hamiltonian* H, const uin
                             double* phase, double* eloc, void* O, int32_t* status, cudaStream_t s, int sides) {
   const Geo& g = h->g;
   int* st = status ? (int*)status : h->status_tmp;
-  CK(cudaMemsetAsync(st, 0, sizeof(int) * Ns, s), "memset status");
+  // the sampler's upper environments belong to S when S is the unmodified output of the last
+  // peps_sample on this handle (caller's promise, enabled by peps_set_env_reuse) and the
+  // parameters have not changed since
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cap);
+  const bool reuse = h->env_reuse && cap == cudaStreamCaptureStatusNone && Ns > 0 && S == h->rs_S && Ns == h->rs_Ns &&
+                     h->rs_gen == h->param_gen;
+  if (reuse) CK(cudaMemcpyAsync(st, h->ustat, sizeof(int) * Ns, cudaMemcpyDeviceToDevice, s), "copy status");
+  else CK(cudaMemsetAsync(st, 0, sizeof(int) * Ns, s), "memset status");
   CK(cudaMemsetAsync(h->wdisc, 0, sizeof(float) * Ns, s), "memset wdisc");
   if (Ns == 0) return PEPS_OK;
+  if (reuse) sides = (sides == 3) ? 2 : 0;
+  else h->rs_gen = -1;  // the store's upper rows now belong to this batch
   TermTab none{};
   const bool want_e = (eloc != nullptr);
   if (want_e) {
@@ -604,10 +623,13 @@ static peps_status run_eval(peps_handle* h, const peps_hamiltonian* H, const uin
     return PEPS_OK;
   }
   const KPlan& ke = h->kp[0];
-  int ts = tstart(h, TC_ENV, s);
-  CK(launch_env<T>(g, ke.p, std::min(ke.grid, Ns * (sides == 3 ? 2 : 1)), ke.smem, (const T*)h->Tpad, S, Ns, sides,
-                   (T*)h->envs, h->logs, st, h->wdisc, s), "env kernel");
-  tstop(h, ts, s);
+  int ts = -1;
+  if (sides != 0) {
+    ts = tstart(h, TC_ENV, s);
+    CK(launch_env<T>(g, ke.p, std::min(ke.grid, Ns * (sides == 3 ? 2 : 1)), ke.smem, (const T*)h->Tpad, S, Ns, sides,
+                     (T*)h->envs, h->logs, st, h->wdisc, s), "env kernel");
+    tstop(h, ts, s);
+  }
   const KPlan& kr = h->kp[1];
   const bool all_rows = want_e || (O != nullptr);
   const int x_lo = all_rows ? 0 : g.Lx - 1;
@@ -771,6 +793,7 @@ extern "C" peps_status peps_direct_sample(peps_handle* h, uint8_t* S_dev, int Ns
   if (c != PEPS_OK) return c;
   if (!h->DL || h->dl_chid < 1) return fail(h, PEPS_E_ARG, "peps_direct_prepare has not been called");
   if (!logp_dev && Ns > 0) return fail(h, PEPS_E_ARG, "null log p output");
+  h->rs_gen = -1;  // S_dev is overwritten
   cudaStream_t s = (cudaStream_t)stream;
   int* st = status_dev ? (int*)status_dev : h->status_tmp;
   if (Ns == 0) return PEPS_OK;
@@ -802,6 +825,13 @@ extern "C" peps_status peps_rotate_params(const peps_handle* h, const double* M_
   return PEPS_OK;
 }
 
+extern "C" peps_status peps_set_env_reuse(peps_handle* h, int enable) {
+  if (!h || (enable != 0 && enable != 1)) return fail(h, PEPS_E_ARG, "enable must be 0 or 1");
+  h->env_reuse = enable;
+  h->rs_gen = -1;
+  return PEPS_OK;
+}
+
 // ---- variational-bound estimator ---------------------------------------------------------
 extern "C" peps_status peps_local_energy_bound(peps_handle* h, const peps_hamiltonian* H, const uint8_t* S_dev,
                                                int Ns, int cut, double* eloc_dev, double* logabs_dev,
@@ -817,6 +847,7 @@ extern "C" peps_status peps_local_energy_bound(peps_handle* h, const peps_hamilt
   if (Ns == 0) return PEPS_OK;
   peps_status ps = set_hamiltonian(h, H, s);
   if (ps != PEPS_OK) return ps;
+  h->rs_gen = -1;  // the environment store is rewritten for this batch
   const int nt = std::max(h->tt.nterm, 1);
   const size_t need = (size_t)h->cfg.max_samples * nt * 2;
   if (need > h->bout_cap) {
@@ -861,7 +892,9 @@ extern "C" peps_status peps_sample(peps_handle* h, int move, uint8_t* S_dev, int
   cudaStream_t s = (cudaStream_t)stream;
   int* st = status_dev ? (int*)status_dev : h->status_tmp;
   CK(cudaMemsetAsync(st, 0, sizeof(int) * Ns, s), "memset status");
+  h->rs_gen = -1;
   if (Ns == 0 || nsweeps == 0) return PEPS_OK;
+  CK(cudaMemsetAsync(h->ustat, 0, sizeof(int) * Ns, s), "memset status");
   const KPlan& k = h->kp[3];
   const int grid = std::min(k.grid, Ns);
   const int ts = tstart(h, TC_SAMPLE, s);
@@ -869,9 +902,18 @@ extern "C" peps_status peps_sample(peps_handle* h, int move, uint8_t* S_dev, int
     using T = decltype(z);
     const KPlan& ke = h->kp[0];
     return launch_sample<T>(h->g, k.p, grid, k.smem, ke.p, std::min(ke.grid, Ns), ke.smem, (const T*)h->Tpad, S_dev, Ns,
-                            move, nsweeps, seed, sweep0, (T*)h->envs, h->logs, accepted_dev, st, s);
+                            move, nsweeps, seed, sweep0, (T*)h->envs, h->logs, accepted_dev, st, h->ustat, s);
   });
   if (e != cudaSuccess) return cuda_fail(h, e, "sampler kernel");
+  // the split FP32 sweep leaves E^u of the final configurations in the store (with their row
+  // steps' status bits in ustat); the single-launch sampler does not record the bits
+  if (h->elem == 1) {
+    h->rs_S = S_dev;
+    h->rs_Ns = Ns;
+    h->rs_gen = h->param_gen;
+  } else {
+    h->rs_gen = -1;
+  }
   tstop(h, ts, s);
   return PEPS_OK;
 }
@@ -1092,6 +1134,7 @@ extern "C" peps_status peps_autotune(peps_handle* h, const peps_hamiltonian* H, 
   }
   h->timing = was_timing;
   h->evn = 0;
+  h->rs_gen = -1;
   cleanup();
   if (st != PEPS_OK) {
     for (int i = 0; i < 4; ++i) h->budget[i] = default_budget(h, i);
@@ -1302,6 +1345,7 @@ static peps_status ensure_learned(peps_handle* h) {
 extern "C" peps_status peps_sample_learned(peps_handle* h, int C, int wprec, const void* w_dev, uint8_t* S_dev,
                                            double* logpsi_dev, int Ns, uint64_t seed, uint64_t step,
                                            long long* accepted_dev, int32_t* status_dev, void* stream) {
+  if (h) h->rs_gen = -1;  // S_dev is overwritten
   peps_status c = check_eval(h, S_dev, Ns);
   if (c != PEPS_OK) return c;
   if (!prop_shape_ok(h->g.Lx, h->g.Ly, C, wprec)) return fail(h, PEPS_E_SHAPE, "proposal network shape");

@@ -50,7 +50,7 @@ template <typename T>
 cudaError_t launch_sample(const Geo& g, const Plan& p, int grid, size_t smem, const Plan& pe, int grid_e,
                           size_t smem_e, const T* Tpad, uint8_t* S, int Ns, int move, int nsweeps,
                           unsigned long long seed, unsigned long long sweep0, T* envs, double* logs,
-                          long long* accepted, int* status, cudaStream_t s);
+                          long long* accepted, int* status, int* ustat, cudaStream_t s);
 template <typename T>
 cudaError_t launch_bound(const Geo& g, const Plan& p, int grid, size_t smem, const T* Tpad, const uint8_t* S, int Ns,
                          int cut, const T* envs, const double* logs, const TermTab& tt, double* bout, double* logabs,

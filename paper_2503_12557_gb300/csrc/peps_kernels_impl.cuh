@@ -877,11 +877,13 @@ __global__ void __launch_bounds__(NTHREADS, MinBlocks<T>::value) k_sweep_moves(G
 }
 
 // E^u[x] of every chain from its (updated) row x: the first row for x = 0, else one row step
-// from E^u[x-1]; compiled for the environment kernel's occupancy.
+// from E^u[x-1]; compiled for the environment kernel's occupancy.  ustat (may be null): also
+// collects the row steps' status bits (the last sweep's, for a later evaluation that reuses
+// these upper environments).
 template <typename T, typename G>
 __global__ void __launch_bounds__(NTHREADS, EnvBlocks<T>::value) k_env_row(G g, Plan plan, const T* __restrict__ Tpad,
                                                       const uint8_t* __restrict__ S, int Ns, int x, T* envs,
-                                                      double* logs, int* status) {
+                                                      double* logs, int* status, int* ustat) {
   extern __shared__ __align__(16) char smem[];
   char* gbase = plan.gbase;
   RowWork<T> w = carve_row<T>(plan, smem, gbase);
@@ -903,6 +905,7 @@ __global__ void __launch_bounds__(NTHREADS, EnvBlocks<T>::value) k_env_row(G g, 
     if (threadIdx.x == 0) {
       lg[slot_up(g, x)] = l;
       if (st) atomicOr(status + c, st);
+      if (st && ustat) atomicOr(ustat + c, st);
     }
     __syncthreads();
   }
@@ -1134,7 +1137,7 @@ template <typename T>
 cudaError_t launch_sample(const Geo& g, const Plan& p, int grid, size_t smem, const Plan& pe, int grid_e,
                           size_t smem_e, const T* Tpad, uint8_t* S, int Ns, int move, int nsweeps,
                           unsigned long long seed, unsigned long long sweep0, T* envs, double* logs,
-                          long long* accepted, int* status, cudaStream_t s) {
+                          long long* accepted, int* status, int* ustat, cudaStream_t s) {
   return with_geo_for<T>(g, [&](auto gg) {
     using GG = decltype(gg);
     if constexpr (sizeof(T) == 4) {
@@ -1143,7 +1146,9 @@ cudaError_t launch_sample(const Geo& g, const Plan& p, int grid, size_t smem, co
         for (int x = 0; x < g.Lx; ++x) {
           k_sweep_moves<T, GG><<<grid, NTHREADS, smem, s>>>(gg, p, Tpad, S, Ns, move, x, seed, sweep0 + t, envs, logs,
                                                             accepted, status);
-          if (x < g.Lx - 1) k_env_row<T, GG><<<grid_e, NTHREADS, smem_e, s>>>(gg, pe, Tpad, S, Ns, x, envs, logs, status);
+          if (x < g.Lx - 1)
+            k_env_row<T, GG><<<grid_e, NTHREADS, smem_e, s>>>(gg, pe, Tpad, S, Ns, x, envs, logs, status,
+                                                              t == nsweeps - 1 ? ustat : nullptr);
         }
       }
     } else {
@@ -1179,7 +1184,7 @@ cudaError_t kattr_sample(const Geo& g, size_t set_bytes, int* occ, size_t occ_sm
 #define PEPS_INST_SAMPLE(T)                                                                                       \
   template cudaError_t launch_sample<T>(const Geo&, const Plan&, int, size_t, const Plan&, int, size_t, const T*, \
                                         uint8_t*, int, int, int, unsigned long long, unsigned long long, T*,      \
-                                        double*, long long*, int*, cudaStream_t);                                 \
+                                        double*, long long*, int*, int*, cudaStream_t);                           \
   template cudaError_t kattr_sample<T>(const Geo&, size_t, int*, size_t);
 #endif
 

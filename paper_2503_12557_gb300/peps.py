@@ -70,6 +70,7 @@ def load():
         "peps_local_energy_bound": ([vp, C.POINTER(_Ham), vp, i32, i32, vp, vp, vp, vp, vp], i32),
         "peps_rotate_params": ([vp, vp, vp, i32, vp, vp], i32),
         "peps_direct_prepare": ([vp, i32, vp], i32),
+        "peps_set_env_reuse": ([vp, i32], i32),
         "peps_direct_sample": ([vp, vp, i32, C.c_uint64, C.c_uint64, vp, vp, vp], i32),
         "minsr_step": ([vp, vp, vp, vp, i32, dbl, dbl, dbl, vp, vp, vp], i32),
         "peps_sample": ([vp, i32, vp, i32, i32, C.c_uint64, C.c_uint64, vp, vp, vp], i32),
@@ -100,7 +101,8 @@ def exported_symbols():
             "peps_timing_enable", "peps_timing_read", "peps_apply_update", "peps_proposal_logits",
             "peps_proposal_train_step", "peps_sample_learned", "peps_amplitudes_noalloc", "peps_probe_fma",
             "peps_autotune", "peps_batch_create", "peps_batch_launch", "peps_batch_destroy",
-            "peps_local_energy_bound", "peps_rotate_params", "peps_direct_prepare", "peps_direct_sample"]
+            "peps_local_energy_bound", "peps_rotate_params", "peps_direct_prepare", "peps_direct_sample",
+            "peps_set_env_reuse"]
 
 
 def probe_fma(fp64=False):
@@ -325,6 +327,11 @@ class PEPS:
         self._check(self.L.peps_local_energy_bound(self.h, C.byref(hc.c), _ptr(S), ns, int(cut), _ptr(e), _ptr(la),
                                                    _ptr(ph), _ptr(st), _stream()), "peps_local_energy_bound")
         return dict(eloc=e, logabs=la, phase=ph, status=st)
+
+    def set_env_reuse(self, enable=True):
+        """Let an evaluation of the unmodified output of the last sample() reuse the sampler's
+        upper environments (see peps_set_env_reuse)."""
+        self._check(self.L.peps_set_env_reuse(self.h, 1 if enable else 0), "peps_set_env_reuse")
 
     def direct_prepare(self, chi_double):
         """Double-layer lower environments of the current parameters for direct sampling."""

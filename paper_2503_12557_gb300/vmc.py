@@ -37,6 +37,7 @@ class VMC:
         self.h = P.PEPS(Lx, Ly, d, D, chi, prec=prec, max_samples=len(S0), gram=gram, solve=solve)
         self.theta = torch.as_tensor(np.asarray(theta0, dtype=np.float64)).cuda().contiguous()
         self.h.set_params(self.theta)
+        self.h.set_env_reuse(True)  # evaluate() follows sample() on the same, unmodified chains
         self.S = torch.as_tensor(np.asarray(S0, dtype=np.uint8)).cuda().contiguous()
         self.acc = torch.zeros(len(S0), dtype=torch.int64, device="cuda")
         self.sweep = 0

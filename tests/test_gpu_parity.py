@@ -458,3 +458,35 @@ def test_fp32_sampler_chains_close_to_oracle(P):
     torch.cuda.synchronize()
     Sfr, accfr, _ = sampler.run_chains(th, S0, lat, 3, "flip", 23, 1)
     assert np.all(Sf.cpu().numpy() == Sfr, axis=1).sum() >= 22
+
+
+def test_env_reuse_after_sampling_equals_full_evaluation(P):
+    # the FP32 sampler leaves E^u of the final configurations in the store; an evaluation with
+    # reuse contracts only the lower side and must give the full evaluation's results
+    lat = I.Lattice(6, 5, 2, 3)
+    th = I.peps_random(lat, 47, scale=0.5, bias=1.0)
+    H = I.j1j2_chiral(lat, J1=1.0, J2=0.5, Jchi=0.0)
+    H["terms"] = [t for t in H["terms"] if len(t[0]) == 2]
+    h = _handle(P, lat, 9, 40, prec=1)
+    ref = _handle(P, lat, 9, 40, prec=1)
+    h.set_params(_dev(th))
+    ref.set_params(_dev(th))
+    h.set_env_reuse(True)
+    S = _dev(I.configs_neel(lat, 40))
+    h.sample(S, move=P.MOVE_EXCHANGE, nsweeps=2, seed=31)
+    r = h.evaluate(H, S)
+    e = ref.evaluate(H, S.clone())
+    torch.cuda.synchronize()
+    for k in ("logabs", "phase", "eloc", "O", "status"):
+        assert torch.equal(r[k], e[k]), k
+    a = h.amplitudes(S)
+    torch.cuda.synchronize()
+    assert torch.equal(a[0], e["logabs"])
+    # a parameter change invalidates the stored environments: the next evaluation recomputes
+    th2 = th * 1.01
+    h.set_params(_dev(th2))
+    ref.set_params(_dev(th2))
+    r2 = h.evaluate(H, S)
+    e2 = ref.evaluate(H, S.clone())
+    torch.cuda.synchronize()
+    assert torch.equal(r2["logabs"], e2["logabs"]) and torch.equal(r2["eloc"], e2["eloc"])
