@@ -200,13 +200,15 @@ static void place_overlay(Plan& p, size_t& smem, size_t budget, const std::vecto
 // Default shared-memory budget per CTA: FP64 one CTA per SM (the FP64 pipe is the limit), FP32
 // two CTAs per SM.
 // Default shared-memory budget per CTA and kernel class (0 env, 1 row, 2 pair, 3 sampler): FP64
-// one CTA per SM (the FP64 pipe is the limit); FP32 two CTAs per SM, except the environment and
-// one-row sandwich kernels, which run three (72 KB each, the larger buffers in the L2-resident
-// arena; measured 10 % and 13 % faster at 8x8, D = 4, chi = 16).
+// one CTA per SM (the FP64 pipe is the limit); FP32 three CTAs per SM (72 KB each, the larger
+// buffers in the L2-resident arena) for the environment, one-row and sampler kernels (the
+// sampler's moves and row steps run as separate launches in FP32), two for the two-row kernel.
 static size_t default_budget(const peps_handle* h, int cls) {
   if (h->esz >= 8) return 210 * 1024;
-  return (cls == 0 || cls == 1) ? 72 * 1024 : 110 * 1024;
+  return (cls == 2) ? 110 * 1024 : 72 * 1024;
 }
+// budget of the bound and direct-sampling plans (compiled for two CTAs per SM in FP32)
+static size_t wide_budget(const peps_handle* h) { return (h->esz >= 8) ? 210 * 1024 : 110 * 1024; }
 
 static void plan_all(peps_handle* h) {
   const Geo& g = h->g;
@@ -247,7 +249,7 @@ static void plan_all(peps_handle* h) {
         {B_RHIST, (size_t)std::max(1, Ly - 1) * n * n * E}, {B_S, (size_t)g.Lx * g.Ly},
         {B_LW, (size_t)2 * chi * chi * E}, {B_LW2, (size_t)g.se * E}, {B_LP, (size_t)2 * Ly * g.se * E},
         {B_RP, (size_t)2 * Ly * g.se * E}};
-    place(k.p, k.smem, h->budget[3], b);
+    place(k.p, k.smem, wide_budget(h), b);
   }
   // row plan
   budget = h->budget[1];
@@ -742,7 +744,7 @@ extern "C" peps_status peps_direct_prepare(peps_handle* h, int chi_double, void*
       {B_Z, env_z_elems(chi, D) * E}, {B_RHIST, (size_t)std::max(1, Ly - 1) * n * n * E}, {B_S, (size_t)Lx * Ly},
       {B_EU, (size_t)2 * Ly * g.se * E}, {B_LW2, (size_t)(g.d + 1) * rsz * E}, {B_RP, (size_t)(Ly + 1) * rsz * E},
       {B_LP, tsz * E}, {B_LW, tsz * E}, {B_T1, ksz * E}, {B_T2, ksz * E}};
-  place(k.p, k.smem, h->budget[3], b);
+  place(k.p, k.smem, wide_budget(h), b);
   cudaError_t e = cudaSuccess;
   {
     std::lock_guard<std::mutex> lk(g_direct_mu);

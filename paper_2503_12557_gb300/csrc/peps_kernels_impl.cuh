@@ -696,7 +696,7 @@ __global__ void __launch_bounds__(NTHREADS, MinBlocks<T>::value) k_sample(G g, P
 // as in k_sample) and k_env_row(x) (E^u[x] from the updated row).  The random slots continue
 // across rows as in k_sample: row x starts at x (moves per row + vertical moves per row).
 template <typename T, typename G>
-__global__ void __launch_bounds__(NTHREADS, MinBlocks<T>::value) k_sweep_moves(G g, Plan plan,
+__global__ void __launch_bounds__(NTHREADS, EnvBlocks<T>::value) k_sweep_moves(G g, Plan plan,
                                                         const T* __restrict__ Tpad, uint8_t* S, int Ns, int move,
                                                         int x, unsigned long long seed, unsigned long long sweep_id,
                                                         T* envs, double* logs, long long* accepted, int* status) {
