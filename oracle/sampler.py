@@ -6,7 +6,9 @@ Environment reuse inside a sweep follows Sec. "On reusing environments": a move 
 only needs E^u[x-1], the rows it touches and E^l below them.
 
 Readings (the paper prints no Markov-chain update scheme):
-  One sweep of one chain:
+  Sweeps alternate direction: an even sweep id runs down the rows, an odd one up, so that every
+  sweep starts from the environments the previous one left behind.
+  One downward sweep (even sweep id) of one chain:
     El[x] for the current S (all rows, bottom up);  Eu[-1] trivial;  slot = 0
     for x = 0 .. Lx-1:
       row moves, y in order:  exchange: (x,y)<->(x,y+1) for y = 0..Ly-2;  flip: (x,y) for y = 0..Ly-1
@@ -14,9 +16,16 @@ Readings (the paper prints no Markov-chain update scheme):
       vertical moves (exchange only, x < Lx-1): (x,y)<->(x+1,y) for y = 0..Ly-1
           ratio = psi_{x,x+1}(S')/psi_{x,x+1}(S) with Eu[x-1] and El[x+2]
       if x < Lx-1: Eu[x] = normalise(truncate(Eu[x-1] o T_proj[x]))  (with the updated S)
-    Every move slot draws u = uniform53(counter=(slot, sweep, chain, 0), key=seed) and then
-    slot += 1, whether or not a move is possible (an exchange of equal spins is skipped).
-    Accept iff u < |psi'/psi|^2, evaluated as u < exp(2 (ln|psi'| - ln|psi|)).
+  One upward sweep (odd sweep id), the mirror image:
+    Eu[x] for the current S (all rows, top down);  El[Lx] trivial;  slot = 0
+    for x = Lx-1 .. 0:
+      row moves as above, ratio psi_x with Eu[x-1] and El[x+1]
+      vertical moves (exchange only, x > 0): (x-1,y)<->(x,y) for y = 0..Ly-1,
+          ratio psi_{x-1,x} with Eu[x-2] and El[x+1]
+      if x > 0: El[x] = normalise(truncate(El[x+1] o T_proj[x]))  (with the updated S)
+  Every move slot draws u = uniform53(counter=(slot, sweep, chain, 0), key=seed) and then
+  slot += 1, whether or not a move is possible (an exchange of equal spins is skipped).
+  Accept iff u < |psi'/psi|^2, evaluated as u < exp(2 (ln|psi'| - ln|psi|)).
 """
 from __future__ import annotations
 
@@ -36,7 +45,10 @@ def _accept(u, l1, l0):
 
 
 def sweep(theta, S, lat: Lattice, chi: int, move: str, seed: int, chain: int, sweep_id: int):
-    """One sweep of one chain; returns (new S, accepted moves, attempted moves)."""
+    """One sweep of one chain (downward for an even sweep id, upward for an odd one); returns
+    (new S, accepted moves, attempted moves)."""
+    if sweep_id % 2 == 1:
+        return _sweep_up(theta, S, lat, chi, move, seed, chain, sweep_id)
     T = theta_to_tensors(lat, theta)
     S = np.array(S, dtype=np.uint8)
     Lx, Ly = lat.Lx, lat.Ly
@@ -99,6 +111,67 @@ def sweep(theta, S, lat: Lattice, chi: int, move: str, seed: int, chain: int, sw
     return S, acc, att
 
 
+def _sweep_up(theta, S, lat: Lattice, chi: int, move: str, seed: int, chain: int, sweep_id: int):
+    """The upward sweep: rows Lx-1 .. 0 with the upper environments of the sweep's start and the
+    lower ones built from the updated rows."""
+    T = theta_to_tensors(lat, theta)
+    S = np.array(S, dtype=np.uint8)
+    Lx, Ly = lat.Lx, lat.Ly
+    env, _ = tn.environments(T, S, lat, chi, sides=("u",))
+    key = key_of_seed(seed)
+    slot = 0
+    acc = att = 0
+    el_prev = env.El[Lx]
+    for x in range(Lx - 1, -1, -1):
+        moves = [(x * Ly + y, x * Ly + y + 1) for y in range(Ly - 1)] if move == "exchange" \
+            else [(x * Ly + y,) for y in range(Ly)]
+        for m in moves:
+            u = uniform53((slot, sweep_id, chain, 0), key)
+            slot += 1
+            if move == "exchange" and S[m[0]] == S[m[1]]:
+                continue
+            S2 = S.copy()
+            if move == "exchange":
+                S2[m[0]], S2[m[1]] = S[m[1]], S[m[0]]
+            else:
+                S2[m[0]] = lat.d - 1 - S[m[0]]
+            v0, g0 = tn.sandwich1(env.Eu[x - 1], tn.project(T, S, lat)[x], el_prev)
+            v1, g1 = tn.sandwich1(env.Eu[x - 1], tn.project(T, S2, lat)[x], el_prev)
+            l0 = math.log(abs(v0)) + g0 if v0 != 0 else -math.inf
+            l1 = math.log(abs(v1)) + g1 if v1 != 0 else -math.inf
+            att += 1
+            if _accept(u, l1, l0):
+                S = S2
+                acc += 1
+        if move == "exchange" and x > 0:
+            for y in range(Ly):
+                i, j = (x - 1) * Ly + y, x * Ly + y
+                u = uniform53((slot, sweep_id, chain, 0), key)
+                slot += 1
+                if S[i] == S[j]:
+                    continue
+                S2 = S.copy()
+                S2[i], S2[j] = S[j], S[i]
+                P0 = tn.project(T, S, lat)
+                P1 = tn.project(T, S2, lat)
+                v0, g0 = tn.sandwich2(env.Eu[x - 2], P0[x - 1], P0[x], el_prev)
+                v1, g1 = tn.sandwich2(env.Eu[x - 2], P1[x - 1], P1[x], el_prev)
+                l0 = math.log(abs(v0)) + g0 if v0 != 0 else -math.inf
+                l1 = math.log(abs(v1)) + g1 if v1 != 0 else -math.inf
+                att += 1
+                if _accept(u, l1, l0):
+                    S = S2
+                    acc += 1
+        if x > 0:
+            A = tn.project(T, S, lat)[x]
+            if x == Lx - 1:
+                prod = tn.bottom_row_mps(A)
+            else:
+                prod, _, _ = tn.truncate_svd(tn.apply_up(el_prev, A), chi)
+            el_prev, _, _ = tn.normalize(prod)
+    return S, acc, att
+
+
 def run_chains(theta, S0, lat: Lattice, chi: int, move: str, seed: int, nsweeps: int, sweep0: int = 0):
     """nsweeps sweeps for every chain (row of S0); sweep ids sweep0 .. sweep0+nsweeps-1."""
     S = np.array(S0, dtype=np.uint8)
@@ -112,10 +185,10 @@ def run_chains(theta, S0, lat: Lattice, chi: int, move: str, seed: int, nsweeps:
     return S, acc, att
 
 
-def transition_matrix_exact(psi, lat: Lattice, move: str):
-    """Full transition matrix of one sweep on a tiny lattice with exact amplitudes psi (basis
-    index sum s_i d^(N-1-i)), built as the product of the single-move kernels in sweep order.
-    Returns (P_sweep, list of single-move kernels)."""
+def transition_matrix_exact(psi, lat: Lattice, move: str, up: bool = False):
+    """Full transition matrix of one sweep (downward, or upward with up=True) on a tiny lattice
+    with exact amplitudes psi (basis index sum s_i d^(N-1-i)), built as the product of the
+    single-move kernels in sweep order.  Returns (P_sweep, list of single-move kernels)."""
     N, d, Ly, Lx = lat.nsites, lat.d, lat.Ly, lat.Lx
     dim = d ** N
     p = np.abs(psi) ** 2
@@ -124,10 +197,12 @@ def transition_matrix_exact(psi, lat: Lattice, move: str):
     pw = d ** np.arange(N - 1, -1, -1)
     kernels = []
     order = []
-    for x in range(Lx):
+    for x in (range(Lx - 1, -1, -1) if up else range(Lx)):
         if move == "exchange":
             order += [(x * Ly + y, x * Ly + y + 1) for y in range(Ly - 1)]
-            if x < Lx - 1:
+            if up and x > 0:
+                order += [((x - 1) * Ly + y, x * Ly + y) for y in range(Ly)]
+            if not up and x < Lx - 1:
                 order += [(x * Ly + y, (x + 1) * Ly + y) for y in range(Ly)]
         else:
             order += [(x * Ly + y,) for y in range(Ly)]

@@ -1,8 +1,8 @@
 """Pins of the oracle's Metropolis sweep.
 
-* On 3x3 lattices the full transition matrix built from exact amplitudes: every single-move
-  kernel satisfies detailed balance with respect to |psi|^2 and the sweep leaves |psi|^2
-  stationary (exchange moves also keep S^z).
+* On 3x3 lattices the full transition matrix built from exact amplitudes, for the downward and
+  the upward sweep: every single-move kernel satisfies detailed balance with respect to |psi|^2
+  and the sweep leaves |psi|^2 stationary (exchange moves also keep S^z).
 * At exact chi the oracle's sweep (environment reuse, running E^u updates) makes the same
   accept/reject decisions as a brute-force sweep that reads ratios off the exact state vector
   with the same Philox uniforms.
@@ -15,14 +15,14 @@ from oracle import sampler, exact
 from oracle.philox import uniform53, key_of_seed
 
 
-@pytest.mark.parametrize("move", ["exchange", "flip"])
-def test_detailed_balance_and_stationarity(move):
+@pytest.mark.parametrize("move,up", [("exchange", False), ("flip", False), ("exchange", True), ("flip", True)])
+def test_detailed_balance_and_stationarity(move, up):
     lat = Lattice(3, 3, 2, 2)
     th = peps_random(lat, 5, scale=0.5, bias=1.0)
     psi = exact.state_vector(th, lat)
     p = np.abs(psi) ** 2
     p = p / p.sum()
-    P, kernels = sampler.transition_matrix_exact(psi, lat, move)
+    P, kernels = sampler.transition_matrix_exact(psi, lat, move, up=up)
     for K in kernels:
         assert np.allclose(K.sum(1), 1.0, atol=1e-13)
         F = p[:, None] * K
@@ -44,11 +44,14 @@ def _bruteforce_sweep(psi, S, lat, move, seed, chain, sweep_id):
     def lnp(s):
         return np.log(abs(psi[exact.config_index(s, d)]))
 
-    for x in range(Lx):
+    up = sweep_id % 2 == 1      # odd sweeps run up the rows, vertical bonds to the row above
+    for x in (range(Lx - 1, -1, -1) if up else range(Lx)):
         moves = [(x * Ly + y, x * Ly + y + 1) for y in range(Ly - 1)] if move == "exchange" \
             else [(x * Ly + y,) for y in range(Ly)]
-        if move == "exchange" and x < Lx - 1:
+        if move == "exchange" and not up and x < Lx - 1:
             moves += [(x * Ly + y, (x + 1) * Ly + y) for y in range(Ly)]
+        if move == "exchange" and up and x > 0:
+            moves += [((x - 1) * Ly + y, x * Ly + y) for y in range(Ly)]
         for m in moves:
             u = uniform53((slot, sweep_id, chain, 0), key)
             slot += 1
