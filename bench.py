@@ -263,6 +263,11 @@ def run_gpu(a):
         if world > 1:
             dist.barrier()
     ms_total = e0.elapsed_time(e1)
+    # full one-side environment passes of the timed sampler calls: sweeps alternate direction
+    # (even ids down, odd up); a downward sweep, and an upward one that opens a call, need one
+    s0 = a.burnin + a.warmup * a.sweeps
+    sampler_passes = sum(1 for k in range(a.steps) for t in range(a.sweeps)
+                         if (s0 + k * a.sweeps + t) % 2 == 0 or t == 0)
     step_ms = [e0.elapsed_time(marks[0])] + [marks[k - 1].elapsed_time(marks[k]) for k in range(1, a.steps)]
     ms_cls, launches, ctr = h.timing_read()
     h.timing(False)
@@ -283,14 +288,17 @@ def run_gpu(a):
     alu_peak = fp32_peak if prec == P.PREC_FP32 else fp64_peak
     hwin, vwin = costmodel.heisenberg_windows(lat.Lx, lat.Ly, ns)
     # the Jacobi counters mix the sampler's and the environment kernel's SVDs; split them by SVD count
-    svd_env = a.steps * ns * 2 * (lat.Lx - 2) * (lat.Ly - 1)
+    # with environment reuse the evaluation contracts one side (the sampler left the other)
+    env_sides = 1
+    svd_env = a.steps * ns * env_sides * (lat.Lx - 2) * (lat.Ly - 1)
     svd_all = max(1, ctr["svds"])
     fe = min(1.0, svd_env / svd_all)
     flops = {
-        "env": costmodel.env_flops(lat.Lx, lat.Ly, w["chi"], w["D"], ns * a.steps, 2, ctr["jacobi_sweeps"] * fe,
+        "env": costmodel.env_flops(lat.Lx, lat.Ly, w["chi"], w["D"], ns * a.steps, env_sides, ctr["jacobi_sweeps"] * fe,
                                    ctr["jacobi_rotations"] * fe),
         "sample": costmodel.sample_flops(lat.Lx, lat.Ly, w["chi"], w["D"], ns, a.sweeps * a.steps,
-                                         ctr["jacobi_sweeps"] * (1 - fe), ctr["jacobi_rotations"] * (1 - fe)),
+                                         ctr["jacobi_sweeps"] * (1 - fe), ctr["jacobi_rotations"] * (1 - fe),
+                                         passes=sampler_passes),
         "row": costmodel.row_kernel_flops(lat.Lx, lat.Ly, w["chi"], w["D"], ns * a.steps, True, hwin * a.steps),
         "pair": costmodel.pair_kernel_flops(lat.Lx, lat.Ly, w["chi"], w["D"], ns * a.steps, vwin * a.steps),
         "minsr_gram": costmodel.gram_flops(ns, h.Np) * a.steps,

@@ -162,14 +162,15 @@ peps_status peps_evaluate(peps_handle* h, const peps_hamiltonian* H, const uint8
                           int32_t* status_dev, void* stream);
 
 /* Reuse of cached environments between sampling and evaluation (Sec. "On reusing environments";
- * opt-in, off by default).  After a Metropolis sweep of the FP32 real-PEPS sampler the stored
- * upper environments E^u[0..Lx-2] are those of the final configurations (every row is final
- * once its own moves are done).  With enable = 1, a peps_evaluate / peps_local_energy /
- * peps_amplitudes / peps_logderiv call whose S_dev and Ns are those of the last peps_sample on
- * this handle, with no parameter change (peps_set_params / peps_apply_update) and no other
- * call that rewrites the environments in between, takes them from the store and contracts
- * only the lower side (peps_amplitudes: nothing); the status bits of the upper row steps
- * come from the sampler's last sweep.  The caller promises that S_dev was not modified in
+ * opt-in, off by default).  Sweeps alternate direction (even sweep ids down the rows, odd ones
+ * up); after a sweep of the FP32 real-PEPS sampler the environments it rebuilt row by row
+ * (E^u[0..Lx-2] going down, E^l[1..Lx] going up) are those of the final configurations (every
+ * row is final once its own moves are done).  With enable = 1, a peps_evaluate /
+ * peps_local_energy / peps_amplitudes / peps_logderiv call whose S_dev and Ns are those of the
+ * last peps_sample on this handle, with no parameter change (peps_set_params /
+ * peps_apply_update) and no other call that rewrites the environments in between, takes that
+ * side from the store and contracts only the other one (peps_amplitudes after a downward
+ * sweep: nothing); the status bits of the reused row steps come from the sampler's last sweep.  The caller promises that S_dev was not modified in
  * between.  Results equal those of a full evaluation.  Other precisions and complex handles
  * always recompute.  PEPS_E_ARG for enable outside {0, 1}. */
 peps_status peps_set_env_reuse(peps_handle* h, int enable);
@@ -251,10 +252,14 @@ peps_status minsr_step(peps_handle* h, const void* O_dev, const double* eloc_dev
 peps_status peps_apply_update(peps_handle* h, double* theta_dev, const double* dtheta_dev, void* stream);
 
 /* nsweeps Metropolis sweeps of Ns independent chains (configurations updated in place).
- * One sweep: bottom environments of the current S; then for x = 0..Lx-1 the moves inside row
- * x in column order (exchange: bonds (x,y)-(x,y+1); flip: sites (x,y)) with psi_x ratios,
- * then (exchange only, x < Lx-1) the vertical bonds (x,y)-(x+1,y) with psi_{x,x+1} ratios,
- * then E^u[x] from the updated row.  Move slot k of sweep t of chain c draws
+ * Sweep t has id sweep0 + t; an even id runs down the rows, an odd one up.  Downward sweep:
+ * bottom environments of the current S; then for x = 0..Lx-1 the moves inside row x in column
+ * order (exchange: bonds (x,y)-(x,y+1); flip: sites (x,y)) with psi_x ratios, then (exchange
+ * only, x < Lx-1) the vertical bonds (x,y)-(x+1,y) with psi_{x,x+1} ratios, then E^u[x] from
+ * the updated row.  Upward sweep: the upper environments of the current S (those the previous
+ * sweep of the call left, else computed); then for x = Lx-1..0 the moves inside row x, then
+ * (exchange only, x > 0) the vertical bonds (x-1,y)-(x,y) with psi_{x-1,x} ratios, then E^l[x]
+ * from the updated row.  Slots are counted from 0 in this visiting order.  Move slot k of sweep t of chain c draws
  * u = Philox4x32-10(counter = (k, sweep0 + t, c, 0), key = seed) as a 53-bit double and
  * accepts iff u < |psi'/psi|^2.  accepted_dev: Ns int64, incremented by the accepted moves.
  * status_dev: Ns int32 (OR of the sweeps' status bits). */

@@ -71,17 +71,19 @@ def heisenberg_windows(Lx, Ly, ns, frac_antiparallel=0.5):
     return h, v
 
 
-def sample_flops(Lx, Ly, chi, D, nchains, nsweeps, sweeps, rotations, move="exchange", acc_frac=0.5):
-    """k_sample per sweep and chain: lower environments (Lx-2 steps), upper environments
-    (Lx-2 steps), per row the right partials and the running left partial, and the proposal
-    windows; the Jacobi work comes from the counters."""
-    steps = 2 * (Lx - 2) * row_step_flops(chi, D, Ly)
+def sample_flops(Lx, Ly, chi, D, nchains, nsweeps, sweeps, rotations, move="exchange", acc_frac=0.5, passes=None):
+    """The sampler per chain: every sweep rebuilds one environment side row by row (Lx-2
+    steps); `passes` full passes of the other side (Lx-2 steps each) open the downward sweeps
+    and an upward sweep that starts a call (default: one per sweep); per row the right partials,
+    the running left partial and the proposal windows; the Jacobi work comes from the counters."""
+    passes = nsweeps if passes is None else passes
+    steps = (nsweeps + passes) * (Lx - 2) * row_step_flops(chi, D, Ly)
     rows = Lx * (2 * Ly) * absorb1_flops(chi, D)
     props = Lx * (Ly - 1) * acc_frac * 2 * absorb1_flops(chi, D)
     if move == "exchange":
         rows += (Lx - 1) * 2 * Ly * absorb2_flops(chi, D)
         props += (Lx - 1) * Ly * acc_frac * absorb2_flops(chi, D)
-    return nchains * nsweeps * (steps + rows + props) + jacobi_flops(chi, D, sweeps, rotations)
+    return nchains * (steps + nsweeps * (rows + props)) + jacobi_flops(chi, D, sweeps, rotations)
 
 
 def gram_flops(ns, npar):

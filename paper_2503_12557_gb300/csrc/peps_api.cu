@@ -59,6 +59,7 @@ struct peps_handle {
   const uint8_t* rs_S = nullptr;
   int rs_Ns = 0;
   long long param_gen = 0, rs_gen = -1;
+  int rs_up = 0;  // the last sweep ran up the rows: the stored lower environments are current
   int* ustat = nullptr;
   // Hamiltonian cache
   std::vector<char> ham_key;
@@ -603,13 +604,15 @@ static peps_status run_eval(peps_handle* h, const peps_hamiltonian* H, const uin
   // parameters have not changed since
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   cudaStreamIsCapturing(s, &cap);
+  // (after an upward sweep the lower side is the stored one, which an amplitude-only call,
+  // needing just the upper side, cannot use)
   const bool reuse = h->env_reuse && cap == cudaStreamCaptureStatusNone && Ns > 0 && S == h->rs_S && Ns == h->rs_Ns &&
-                     h->rs_gen == h->param_gen;
+                     h->rs_gen == h->param_gen && !(h->rs_up && sides == 1);
   if (reuse) CK(cudaMemcpyAsync(st, h->ustat, sizeof(int) * Ns, cudaMemcpyDeviceToDevice, s), "copy status");
   else CK(cudaMemsetAsync(st, 0, sizeof(int) * Ns, s), "memset status");
   CK(cudaMemsetAsync(h->wdisc, 0, sizeof(float) * Ns, s), "memset wdisc");
   if (Ns == 0) return PEPS_OK;
-  if (reuse) sides = (sides == 3) ? 2 : 0;
+  if (reuse) sides = (sides == 3) ? (h->rs_up ? 1 : 2) : 0;
   else h->rs_gen = -1;  // the store's upper rows now belong to this batch
   TermTab none{};
   const bool want_e = (eloc != nullptr);
@@ -907,12 +910,14 @@ extern "C" peps_status peps_sample(peps_handle* h, int move, uint8_t* S_dev, int
                             move, nsweeps, seed, sweep0, (T*)h->envs, h->logs, accepted_dev, st, h->ustat, s);
   });
   if (e != cudaSuccess) return cuda_fail(h, e, "sampler kernel");
-  // the split FP32 sweep leaves E^u of the final configurations in the store (with their row
-  // steps' status bits in ustat); the single-launch sampler does not record the bits
+  // the split FP32 sweep leaves the environments of the final configurations on the side it
+  // rebuilt last (E^u after a downward sweep, E^l after an upward one), with their row steps'
+  // status bits in ustat; the single-launch sampler does not record the bits
   if (h->elem == 1) {
     h->rs_S = S_dev;
     h->rs_Ns = Ns;
     h->rs_gen = h->param_gen;
+    h->rs_up = (int)((sweep0 + (uint64_t)nsweeps - 1) & 1ull);
   } else {
     h->rs_gen = -1;
   }

@@ -486,387 +486,231 @@ __global__ void k_bound_combine(Geo g, int Ns, int nt, const uint8_t* __restrict
 #endif
 
 // ------------------------------------------------------------------------------------------
-// Metropolis sweeps: one CTA per chain (persistent over chains).
+// Buffers of the moves of one row, carved from the sampler's plan.
+template <typename T>
+struct MoveBufs {
+  T *RP, *t1, *t2, *eu, *el, *A1, *A2, *LW, *LW2, *LC;
+  double* red;
+};
+template <typename T>
+__device__ MoveBufs<T> carve_moves(const Plan& plan, char* smem, char* gbase) {
+  MoveBufs<T> b;
+  b.RP = (T*)buf_ptr(plan, B_RP, smem, gbase);
+  b.t1 = (T*)buf_ptr(plan, B_T1, smem, gbase);
+  b.t2 = (T*)buf_ptr(plan, B_T2, smem, gbase);
+  b.eu = (T*)buf_ptr(plan, B_EU, smem, gbase);
+  b.el = (T*)buf_ptr(plan, B_EL, smem, gbase);
+  b.A1 = (T*)buf_ptr(plan, B_A, smem, gbase);
+  b.A2 = (T*)buf_ptr(plan, B_A2, smem, gbase);
+  b.LW = (T*)buf_ptr(plan, B_LW, smem, gbase);
+  b.LW2 = (T*)buf_ptr(plan, B_LW2, smem, gbase);
+  b.LC = (T*)buf_ptr(plan, B_LP, smem, gbase);
+  b.red = (double*)buf_ptr(plan, B_RED, smem, gbase);
+  return b;
+}
+
+// Random slots before row x in a sweep: the rows already visited (x of them going down,
+// Lx-1-x going up) times the moves of a row (in-row moves plus, for exchanges, Ly vertical ones).
+template <typename G>
+__device__ inline unsigned sweep_slot0(const G& g, int x, int up, int move) {
+  const unsigned per = (unsigned)(((move == 0) ? g.Ly - 1 : g.Ly) + ((move == 0) ? g.Ly : 0));
+  return (unsigned)(up ? (g.Lx - 1 - x) : x) * per;
+}
+
+// The moves of row x of one chain in a sweep going down (up = 0) or up (up = 1): the in-row
+// moves (exchange (x,y)<->(x,y+1), flip (x,y), y in order) judged with
+// psi_x = E^u[x-1] . T[x] . E^l[x+1], then the vertical exchanges of the rows (xt, xt+1), with
+// xt = x going down (x < Lx-1) and xt = x-1 going up (x > 0), judged with
+// psi_{xt,xt+1} = E^u[xt-1] . T[xt] . T[xt+1] . E^l[xt+2].  Slots from slot0 on; Sl (shared) is
+// updated in place; *acc counts the accepted moves (the same value in every thread).
 template <typename T, typename G>
-__global__ void __launch_bounds__(NTHREADS, MinBlocks<T>::value) k_sample(G g, Plan plan, const T* __restrict__ Tpad, uint8_t* S,
-                                                     int Ns, int move, int nsweeps, unsigned long long seed,
-                                                     unsigned long long sweep0, T* envs, double* logs,
-                                                     long long* accepted, int* status) {
-  extern __shared__ __align__(16) char smem[];
-  char* gbase = plan.gbase;
-  RowWork<T> w = carve_row<T>(plan, smem, gbase);
-  T* RP = (T*)buf_ptr(plan, B_RP, smem, gbase);   // (Ly+1) x s2 (one- or two-row partials)
-  T* t1 = (T*)buf_ptr(plan, B_T1, smem, gbase);
-  T* t2 = (T*)buf_ptr(plan, B_T2, smem, gbase);
-  T* eu = (T*)buf_ptr(plan, B_EU, smem, gbase);
-  T* el = (T*)buf_ptr(plan, B_EL, smem, gbase);
-  T* A1 = (T*)buf_ptr(plan, B_A, smem, gbase);
-  T* A2 = (T*)buf_ptr(plan, B_A2, smem, gbase);
-  T* LW = (T*)buf_ptr(plan, B_LW, smem, gbase);
-  T* LW2 = (T*)buf_ptr(plan, B_LW2, smem, gbase);
-  T* LC = (T*)buf_ptr(plan, B_LP, smem, gbase);    // running left partial (s2)
-  uint8_t* Sl = (uint8_t*)buf_ptr(plan, B_S, smem, gbase);
-  double* red = w.red;
+__device__ void row_moves(const G& g, const Plan& plan, const MoveBufs<T>& b, const T* Tpad, uint8_t* Sl,
+                          const T* env, int x, int up, int move, unsigned slot0, unsigned long long sweep_id, int c,
+                          unsigned long long seed, long long* acc, int* st) {
   __shared__ double logR[MAX_LY + 1];
   __shared__ double logLc, lcur;
-  __shared__ int st, flag, accept_flag;
-  __shared__ float wd;
-  const int N = g.Lx * g.Ly, Ly = g.Ly, Lx = g.Lx, se = g.se, s2 = g.s2;
+  __shared__ int accept_flag;
+  const int Ly = g.Ly, Lx = g.Lx, se = g.se, s2 = g.s2;
   const size_t rowsz = (size_t)Ly * se;
-  for (int c = blockIdx.x; c < Ns; c += gridDim.x) {
-    uint8_t* Sg = S + (size_t)c * N;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) Sl[i] = Sg[i];
-    if (threadIdx.x == 0) { st = 0; wd = 0.f; }
-    long long acc = 0;
-    T* env = envs + (size_t)c * env_sample_elems(g);
-    double* lg = logs + (size_t)c * 2 * Lx;
+  const int nmv = (move == 0) ? Ly - 1 : Ly;
+  unsigned slot = slot0;
+  T *RP = b.RP, *t1 = b.t1, *t2 = b.t2, *eu = b.eu, *el = b.el, *A1 = b.A1, *A2 = b.A2, *LW = b.LW, *LW2 = b.LW2,
+    *LC = b.LC;
+  double* red = b.red;
+  // ---- moves inside row x with psi_x (E^u[x-1], E^l[x+1])
+  {
+    const T* EU = env + (size_t)slot_up(g, x - 1) * rowsz;
+    const T* EL = env + (size_t)slot_lo(g, x + 1) * rowsz;
+    blk_unit(RP + (size_t)Ly * se, se);
+    if (threadIdx.x == 0) logR[Ly] = 0.0;
     __syncthreads();
-    for (int t = 0; t < nsweeps; ++t) {
-      const unsigned long long sweep_id = sweep0 + (unsigned long long)t;
-      // lower environments E^l[1..Lx] of the current configuration
-      build_lower(g, Tpad, Sl, env, lg, w, &st, &wd, &flag, 1);
-      // E^u[-1]
-      {
-        T* trivial = env + (size_t)slot_up(g, -1) * rowsz;
-        for (int k = 0; k < Ly; ++k) blk_unit(trivial + (size_t)k * se, se);
-        if (threadIdx.x == 0) lg[slot_up(g, -1)] = 0.0;
-        __syncthreads();
-      }
-      unsigned slot = 0;
-      for (int x = 0; x < Lx; ++x) {
-        const T* EU = env + (size_t)slot_up(g, x - 1) * rowsz;
-        // ---- moves inside row x with psi_x (E^u[x-1], E^l[x+1])
-        {
-          const T* EL = env + (size_t)slot_lo(g, x + 1) * rowsz;
-          blk_unit(RP + (size_t)Ly * se, se);
-          if (threadIdx.x == 0) logR[Ly] = 0.0;
-          __syncthreads();
-          for (int y = Ly - 1; y >= 0; --y) {
-            blk_copy(eu, EU + (size_t)y * se, se);
-            blk_copy(el, EL + (size_t)y * se, se);
-            load_A(A1, Tpad, g, x * Ly + y, Sl[x * Ly + y], false);
-            __syncthreads();
-            absorb1_right(g, RP + (size_t)(y + 1) * se, eu, A1, el, t1, t2, RP + (size_t)y * se);
-            const double l = blk_normalize(RP + (size_t)y * se, se, red, &st);
-            if (threadIdx.x == 0) logR[y] = logR[y + 1] + l;
-          }
-          __syncthreads();
-          if (threadIdx.x == 0) {
-            const double v = dz_abs(to_dz(RP[0]));
-            lcur = (v != 0.0) ? log(v) + logR[0] : -INFINITY;
-            logLc = 0.0;
-          }
-          blk_unit(LC, se);
-          __syncthreads();
-          const int nmv = (move == 0) ? Ly - 1 : Ly;
-          for (int y = 0; y < nmv; ++y) {
-            const double u = uniform53(slot, (uint32_t)sweep_id, (uint32_t)c, 0u, seed);
-            ++slot;
-            const int i0 = x * Ly + y, i1 = i0 + 1;
-            const bool possible = (move == 0) ? (Sl[i0] != Sl[i1]) : true;
-            if (possible) {
-              const int w_ = (move == 0) ? 2 : 1;
-              blk_copy(LW, LC, se);
-              __syncthreads();
-              double lw = logLc;
-              for (int cc = 0; cc < w_; ++cc) {
-                const int site = i0 + cc;
-                int s_new;
-                if (move == 0) s_new = (cc == 0) ? Sl[i1] : Sl[i0];
-                else s_new = g.d - 1 - Sl[site];
-                blk_copy(eu, EU + (size_t)(y + cc) * se, se);
-                blk_copy(el, EL + (size_t)(y + cc) * se, se);
-                load_A(A1, Tpad, g, site, s_new, false);
-                __syncthreads();
-                absorb1(g, LW, eu, A1, el, t1, t2, LW2);
-                lw += blk_normalize(LW2, se, red, &st);
-                blk_copy(LW, LW2, se);
-                __syncthreads();
-              }
-              const T v = blk_dot(LW, RP + (size_t)(y + w_) * se, se, red);
-              if (threadIdx.x == 0) {
-                const double av = dz_abs(to_dz(v));
-                const double l1 = (av != 0.0) ? log(av) + lw + logR[y + w_] : -INFINITY;
-                accept_flag = (isfinite(l1) && u < exp(2.0 * (l1 - lcur))) ? 1 : 0;
-                if (accept_flag) {
-                  lcur = l1;
-                  if (move == 0) { const uint8_t tmp = Sl[i0]; Sl[i0] = Sl[i1]; Sl[i1] = tmp; }
-                  else Sl[i0] = (uint8_t)(g.d - 1 - Sl[i0]);
-                }
-              }
-              __syncthreads();
-              acc += accept_flag;
-            }
-            // advance the running left partial over column y (current state)
-            blk_copy(eu, EU + (size_t)y * se, se);
-            blk_copy(el, EL + (size_t)y * se, se);
-            load_A(A1, Tpad, g, x * Ly + y, Sl[x * Ly + y], false);
-            __syncthreads();
-            absorb1(g, LC, eu, A1, el, t1, t2, LW2);
-            const double l = blk_normalize(LW2, se, red, &st);
-            blk_copy(LC, LW2, se);
-            if (threadIdx.x == 0) logLc += l;
-            __syncthreads();
-          }
-        }
-        // ---- vertical moves (x, y) <-> (x+1, y) with psi_{x,x+1} (E^u[x-1], E^l[x+2])
-        if (move == 0 && x < Lx - 1) {
-          const T* EL2 = env + (size_t)slot_lo(g, x + 2) * rowsz;
-          blk_unit(RP + (size_t)Ly * s2, s2);
-          if (threadIdx.x == 0) logR[Ly] = 0.0;
-          __syncthreads();
-          for (int y = Ly - 1; y >= 0; --y) {
-            blk_copy(eu, EU + (size_t)y * se, se);
-            blk_copy(el, EL2 + (size_t)y * se, se);
-            load_A(A1, Tpad, g, x * Ly + y, Sl[x * Ly + y], false);
-            load_A(A2, Tpad, g, (x + 1) * Ly + y, Sl[(x + 1) * Ly + y], false);
-            __syncthreads();
-            absorb2_right(g, RP + (size_t)(y + 1) * s2, eu, A1, A2, el, t1, t2, RP + (size_t)y * s2, plan.cx);
-            const double l = blk_normalize(RP + (size_t)y * s2, s2, red, &st);
-            if (threadIdx.x == 0) logR[y] = logR[y + 1] + l;
-          }
-          __syncthreads();
-          if (threadIdx.x == 0) {
-            const double v = dz_abs(to_dz(RP[0]));
-            lcur = (v != 0.0) ? log(v) + logR[0] : -INFINITY;
-            logLc = 0.0;
-          }
-          blk_unit(LC, s2);
-          __syncthreads();
-          for (int y = 0; y < Ly; ++y) {
-            const double u = uniform53(slot, (uint32_t)sweep_id, (uint32_t)c, 0u, seed);
-            ++slot;
-            const int i0 = x * Ly + y, i1 = (x + 1) * Ly + y;
-            blk_copy(eu, EU + (size_t)y * se, se);
-            blk_copy(el, EL2 + (size_t)y * se, se);
-            if (Sl[i0] != Sl[i1]) {
-              load_A(A1, Tpad, g, i0, Sl[i1], false);
-              load_A(A2, Tpad, g, i1, Sl[i0], false);
-              __syncthreads();
-              absorb2(g, LC, eu, A1, A2, el, t1, t2, LW2, plan.cx);
-              const double lw = logLc + blk_normalize(LW2, s2, red, &st);
-              const T v = blk_dot(LW2, RP + (size_t)(y + 1) * s2, s2, red);
-              if (threadIdx.x == 0) {
-                const double av = dz_abs(to_dz(v));
-                const double l1 = (av != 0.0) ? log(av) + lw + logR[y + 1] : -INFINITY;
-                accept_flag = (isfinite(l1) && u < exp(2.0 * (l1 - lcur))) ? 1 : 0;
-                if (accept_flag) {
-                  lcur = l1;
-                  const uint8_t tmp = Sl[i0]; Sl[i0] = Sl[i1]; Sl[i1] = tmp;
-                }
-              }
-              __syncthreads();
-              acc += accept_flag;
-            }
-            load_A(A1, Tpad, g, i0, Sl[i0], false);
-            load_A(A2, Tpad, g, i1, Sl[i1], false);
-            __syncthreads();
-            absorb2(g, LC, eu, A1, A2, el, t1, t2, LW2, plan.cx);
-            const double l = blk_normalize(LW2, s2, red, &st);
-            blk_copy(LC, LW2, s2);
-            if (threadIdx.x == 0) logLc += l;
-            __syncthreads();
-          }
-        }
-        // ---- E^u[x] from the updated row
-        if (x < Lx - 1) {
-          const size_t sl = (size_t)slot_up(g, x) * rowsz;
-          double l;
-          if (x == 0) l = env_first_row(g, env + sl, Tpad, 0, Sl, false, w.A, w.Z, red, &st);
-          else l = lg[slot_up(g, x - 1)] + env_row_step(g, env + (size_t)slot_up(g, x - 1) * rowsz, env + sl, Tpad, x,
-                                                         Sl + (size_t)x * Ly, false, w, &st, &wd, &flag);
-          if (threadIdx.x == 0) lg[slot_up(g, x)] = l;
-          __syncthreads();
-        }
-      }
+    for (int y = Ly - 1; y >= 0; --y) {
+      blk_copy(eu, EU + (size_t)y * se, se);
+      blk_copy(el, EL + (size_t)y * se, se);
+      load_A(A1, Tpad, g, x * Ly + y, Sl[x * Ly + y], false);
+      __syncthreads();
+      absorb1_right(g, RP + (size_t)(y + 1) * se, eu, A1, el, t1, t2, RP + (size_t)y * se);
+      const double l = blk_normalize(RP + (size_t)y * se, se, red, st);
+      if (threadIdx.x == 0) logR[y] = logR[y + 1] + l;
     }
-    for (int i = threadIdx.x; i < N; i += blockDim.x) Sg[i] = Sl[i];
+    __syncthreads();
     if (threadIdx.x == 0) {
-      if (accepted) accepted[c] += acc;
-      if (st) atomicOr(status + c, st);
+      const double v = dz_abs(to_dz(RP[0]));
+      lcur = (v != 0.0) ? log(v) + logR[0] : -INFINITY;
+      logLc = 0.0;
+    }
+    blk_unit(LC, se);
+    __syncthreads();
+    for (int y = 0; y < nmv; ++y) {
+      const double u = uniform53(slot, (uint32_t)sweep_id, (uint32_t)c, 0u, seed);
+      ++slot;
+      const int i0 = x * Ly + y, i1 = i0 + 1;
+      const bool possible = (move == 0) ? (Sl[i0] != Sl[i1]) : true;
+      if (possible) {
+        const int w_ = (move == 0) ? 2 : 1;
+        blk_copy(LW, LC, se);
+        __syncthreads();
+        double lw = logLc;
+        for (int cc = 0; cc < w_; ++cc) {
+          const int site = i0 + cc;
+          int s_new;
+          if (move == 0) s_new = (cc == 0) ? Sl[i1] : Sl[i0];
+          else s_new = g.d - 1 - Sl[site];
+          blk_copy(eu, EU + (size_t)(y + cc) * se, se);
+          blk_copy(el, EL + (size_t)(y + cc) * se, se);
+          load_A(A1, Tpad, g, site, s_new, false);
+          __syncthreads();
+          absorb1(g, LW, eu, A1, el, t1, t2, LW2);
+          lw += blk_normalize(LW2, se, red, st);
+          blk_copy(LW, LW2, se);
+          __syncthreads();
+        }
+        const T v = blk_dot(LW, RP + (size_t)(y + w_) * se, se, red);
+        if (threadIdx.x == 0) {
+          const double av = dz_abs(to_dz(v));
+          const double l1 = (av != 0.0) ? log(av) + lw + logR[y + w_] : -INFINITY;
+          accept_flag = (isfinite(l1) && u < exp(2.0 * (l1 - lcur))) ? 1 : 0;
+          if (accept_flag) {
+            lcur = l1;
+            if (move == 0) { const uint8_t tmp = Sl[i0]; Sl[i0] = Sl[i1]; Sl[i1] = tmp; }
+            else Sl[i0] = (uint8_t)(g.d - 1 - Sl[i0]);
+          }
+        }
+        __syncthreads();
+        *acc += accept_flag;
+      }
+      blk_copy(eu, EU + (size_t)y * se, se);
+      blk_copy(el, EL + (size_t)y * se, se);
+      load_A(A1, Tpad, g, x * Ly + y, Sl[x * Ly + y], false);
+      __syncthreads();
+      absorb1(g, LC, eu, A1, el, t1, t2, LW2);
+      const double l = blk_normalize(LW2, se, red, st);
+      blk_copy(LC, LW2, se);
+      if (threadIdx.x == 0) logLc += l;
+      __syncthreads();
+    }
+  }
+  // ---- vertical moves (xt, y) <-> (xt+1, y) with psi_{xt,xt+1} (E^u[xt-1], E^l[xt+2])
+  const int xt = up ? x - 1 : x;
+  if (move == 0 && xt >= 0 && xt < Lx - 1) {
+    const T* EU = env + (size_t)slot_up(g, xt - 1) * rowsz;
+    const T* EL2 = env + (size_t)slot_lo(g, xt + 2) * rowsz;
+    blk_unit(RP + (size_t)Ly * s2, s2);
+    if (threadIdx.x == 0) logR[Ly] = 0.0;
+    __syncthreads();
+    for (int y = Ly - 1; y >= 0; --y) {
+      blk_copy(eu, EU + (size_t)y * se, se);
+      blk_copy(el, EL2 + (size_t)y * se, se);
+      load_A(A1, Tpad, g, xt * Ly + y, Sl[xt * Ly + y], false);
+      load_A(A2, Tpad, g, (xt + 1) * Ly + y, Sl[(xt + 1) * Ly + y], false);
+      __syncthreads();
+      absorb2_right(g, RP + (size_t)(y + 1) * s2, eu, A1, A2, el, t1, t2, RP + (size_t)y * s2, plan.cx);
+      const double l = blk_normalize(RP + (size_t)y * s2, s2, red, st);
+      if (threadIdx.x == 0) logR[y] = logR[y + 1] + l;
     }
     __syncthreads();
+    if (threadIdx.x == 0) {
+      const double v = dz_abs(to_dz(RP[0]));
+      lcur = (v != 0.0) ? log(v) + logR[0] : -INFINITY;
+      logLc = 0.0;
+    }
+    blk_unit(LC, s2);
+    __syncthreads();
+    for (int y = 0; y < Ly; ++y) {
+      const double u = uniform53(slot, (uint32_t)sweep_id, (uint32_t)c, 0u, seed);
+      ++slot;
+      const int i0 = xt * Ly + y, i1 = (xt + 1) * Ly + y;
+      blk_copy(eu, EU + (size_t)y * se, se);
+      blk_copy(el, EL2 + (size_t)y * se, se);
+      if (Sl[i0] != Sl[i1]) {
+        load_A(A1, Tpad, g, i0, Sl[i1], false);
+        load_A(A2, Tpad, g, i1, Sl[i0], false);
+        __syncthreads();
+        absorb2(g, LC, eu, A1, A2, el, t1, t2, LW2, plan.cx);
+        const double lw = logLc + blk_normalize(LW2, s2, red, st);
+        const T v = blk_dot(LW2, RP + (size_t)(y + 1) * s2, s2, red);
+        if (threadIdx.x == 0) {
+          const double av = dz_abs(to_dz(v));
+          const double l1 = (av != 0.0) ? log(av) + lw + logR[y + 1] : -INFINITY;
+          accept_flag = (isfinite(l1) && u < exp(2.0 * (l1 - lcur))) ? 1 : 0;
+          if (accept_flag) {
+            lcur = l1;
+            const uint8_t tmp = Sl[i0]; Sl[i0] = Sl[i1]; Sl[i1] = tmp;
+          }
+        }
+        __syncthreads();
+        *acc += accept_flag;
+      }
+      load_A(A1, Tpad, g, i0, Sl[i0], false);
+      load_A(A2, Tpad, g, i1, Sl[i1], false);
+      __syncthreads();
+      absorb2(g, LC, eu, A1, A2, el, t1, t2, LW2, plan.cx);
+      const double l = blk_normalize(LW2, s2, red, st);
+      blk_copy(LC, LW2, s2);
+      if (threadIdx.x == 0) logLc += l;
+      __syncthreads();
+    }
   }
+}
+
+// Trivial boundary rows of a sweep: E^u[-1] (going down) or E^l[Lx] (going up), log 0.
+template <typename T, typename G>
+__device__ void sweep_trivial_row(const G& g, T* env, double* lg, int up) {
+  const size_t rowsz = (size_t)g.Ly * g.se;
+  const int slot = up ? slot_lo(g, g.Lx) : slot_up(g, -1);
+  for (int k = 0; k < g.Ly; ++k) blk_unit(env + (size_t)slot * rowsz + (size_t)k * g.se, g.se);
+  if (threadIdx.x == 0) lg[slot] = 0.0;
 }
 
 // ------------------------------------------------------------------------------------------
 // The Metropolis sweep split by rows (FP32: the row steps then run at the environment kernel's
-// occupancy).  One sweep = k_env (lower environments of every chain), then for x = 0 .. Lx-1:
-// k_sweep_moves(x) (the in-row moves with psi_x and the vertical moves of rows x, x+1, exactly
-// as in k_sample) and k_env_row(x) (E^u[x] from the updated row).  The random slots continue
-// across rows as in k_sample: row x starts at x (moves per row + vertical moves per row).
+// occupancy).  A downward sweep = k_env (lower environments of every chain), then for
+// x = 0 .. Lx-1: k_sweep_moves(x) and k_env_row(x) (E^u[x] from the updated row); an upward
+// sweep starts from the upper environments (the previous sweep's, or k_env's at the start of a
+// call) and runs x = Lx-1 .. 0 with k_env_row building E^l[x].
 template <typename T, typename G>
 __global__ void __launch_bounds__(NTHREADS, EnvBlocks<T>::value) k_sweep_moves(G g, Plan plan,
                                                         const T* __restrict__ Tpad, uint8_t* S, int Ns, int move,
-                                                        int x, unsigned long long seed, unsigned long long sweep_id,
-                                                        T* envs, double* logs, long long* accepted, int* status) {
+                                                        int x, int up, unsigned long long seed,
+                                                        unsigned long long sweep_id, T* envs, double* logs,
+                                                        long long* accepted, int* status) {
   extern __shared__ __align__(16) char smem[];
   char* gbase = plan.gbase;
-  T* RP = (T*)buf_ptr(plan, B_RP, smem, gbase);
-  T* t1 = (T*)buf_ptr(plan, B_T1, smem, gbase);
-  T* t2 = (T*)buf_ptr(plan, B_T2, smem, gbase);
-  T* eu = (T*)buf_ptr(plan, B_EU, smem, gbase);
-  T* el = (T*)buf_ptr(plan, B_EL, smem, gbase);
-  T* A1 = (T*)buf_ptr(plan, B_A, smem, gbase);
-  T* A2 = (T*)buf_ptr(plan, B_A2, smem, gbase);
-  T* LW = (T*)buf_ptr(plan, B_LW, smem, gbase);
-  T* LW2 = (T*)buf_ptr(plan, B_LW2, smem, gbase);
-  T* LC = (T*)buf_ptr(plan, B_LP, smem, gbase);
+  const MoveBufs<T> b = carve_moves<T>(plan, smem, gbase);
   uint8_t* Sl = (uint8_t*)buf_ptr(plan, B_S, smem, gbase);
-  double* red = (double*)buf_ptr(plan, B_RED, smem, gbase);
-  __shared__ double logR[MAX_LY + 1];
-  __shared__ double logLc, lcur;
-  __shared__ int st, accept_flag;
-  const int N = g.Lx * g.Ly, Ly = g.Ly, Lx = g.Lx, se = g.se, s2 = g.s2;
-  const size_t rowsz = (size_t)Ly * se;
-  const int nmv = (move == 0) ? Ly - 1 : Ly;
-  unsigned slot0 = (unsigned)x * (unsigned)(nmv + ((move == 0) ? Ly : 0));
+  __shared__ int st;
+  const int N = g.Lx * g.Ly;
+  const unsigned slot0 = sweep_slot0(g, x, up, move);
   for (int c = blockIdx.x; c < Ns; c += gridDim.x) {
     uint8_t* Sg = S + (size_t)c * N;
     for (int i = threadIdx.x; i < N; i += blockDim.x) Sl[i] = Sg[i];
     if (threadIdx.x == 0) st = 0;
     long long acc = 0;
     T* env = envs + (size_t)c * env_sample_elems(g);
-    double* lg = logs + (size_t)c * 2 * Lx;
-    if (x == 0) {
-      T* trivial = env + (size_t)slot_up(g, -1) * rowsz;
-      for (int k = 0; k < Ly; ++k) blk_unit(trivial + (size_t)k * se, se);
-      if (threadIdx.x == 0) lg[slot_up(g, -1)] = 0.0;
-    }
+    double* lg = logs + (size_t)c * 2 * g.Lx;
+    if ((!up && x == 0) || (up && x == g.Lx - 1)) sweep_trivial_row(g, env, lg, up);
     __syncthreads();
-    unsigned slot = slot0;
-    const T* EU = env + (size_t)slot_up(g, x - 1) * rowsz;
-    // ---- moves inside row x with psi_x (E^u[x-1], E^l[x+1])
-    {
-      const T* EL = env + (size_t)slot_lo(g, x + 1) * rowsz;
-      blk_unit(RP + (size_t)Ly * se, se);
-      if (threadIdx.x == 0) logR[Ly] = 0.0;
-      __syncthreads();
-      for (int y = Ly - 1; y >= 0; --y) {
-        blk_copy(eu, EU + (size_t)y * se, se);
-        blk_copy(el, EL + (size_t)y * se, se);
-        load_A(A1, Tpad, g, x * Ly + y, Sl[x * Ly + y], false);
-        __syncthreads();
-        absorb1_right(g, RP + (size_t)(y + 1) * se, eu, A1, el, t1, t2, RP + (size_t)y * se);
-        const double l = blk_normalize(RP + (size_t)y * se, se, red, &st);
-        if (threadIdx.x == 0) logR[y] = logR[y + 1] + l;
-      }
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        const double v = dz_abs(to_dz(RP[0]));
-        lcur = (v != 0.0) ? log(v) + logR[0] : -INFINITY;
-        logLc = 0.0;
-      }
-      blk_unit(LC, se);
-      __syncthreads();
-      for (int y = 0; y < nmv; ++y) {
-        const double u = uniform53(slot, (uint32_t)sweep_id, (uint32_t)c, 0u, seed);
-        ++slot;
-        const int i0 = x * Ly + y, i1 = i0 + 1;
-        const bool possible = (move == 0) ? (Sl[i0] != Sl[i1]) : true;
-        if (possible) {
-          const int w_ = (move == 0) ? 2 : 1;
-          blk_copy(LW, LC, se);
-          __syncthreads();
-          double lw = logLc;
-          for (int cc = 0; cc < w_; ++cc) {
-            const int site = i0 + cc;
-            int s_new;
-            if (move == 0) s_new = (cc == 0) ? Sl[i1] : Sl[i0];
-            else s_new = g.d - 1 - Sl[site];
-            blk_copy(eu, EU + (size_t)(y + cc) * se, se);
-            blk_copy(el, EL + (size_t)(y + cc) * se, se);
-            load_A(A1, Tpad, g, site, s_new, false);
-            __syncthreads();
-            absorb1(g, LW, eu, A1, el, t1, t2, LW2);
-            lw += blk_normalize(LW2, se, red, &st);
-            blk_copy(LW, LW2, se);
-            __syncthreads();
-          }
-          const T v = blk_dot(LW, RP + (size_t)(y + w_) * se, se, red);
-          if (threadIdx.x == 0) {
-            const double av = dz_abs(to_dz(v));
-            const double l1 = (av != 0.0) ? log(av) + lw + logR[y + w_] : -INFINITY;
-            accept_flag = (isfinite(l1) && u < exp(2.0 * (l1 - lcur))) ? 1 : 0;
-            if (accept_flag) {
-              lcur = l1;
-              if (move == 0) { const uint8_t tmp = Sl[i0]; Sl[i0] = Sl[i1]; Sl[i1] = tmp; }
-              else Sl[i0] = (uint8_t)(g.d - 1 - Sl[i0]);
-            }
-          }
-          __syncthreads();
-          acc += accept_flag;
-        }
-        blk_copy(eu, EU + (size_t)y * se, se);
-        blk_copy(el, EL + (size_t)y * se, se);
-        load_A(A1, Tpad, g, x * Ly + y, Sl[x * Ly + y], false);
-        __syncthreads();
-        absorb1(g, LC, eu, A1, el, t1, t2, LW2);
-        const double l = blk_normalize(LW2, se, red, &st);
-        blk_copy(LC, LW2, se);
-        if (threadIdx.x == 0) logLc += l;
-        __syncthreads();
-      }
-    }
-    // ---- vertical moves (x, y) <-> (x+1, y) with psi_{x,x+1} (E^u[x-1], E^l[x+2])
-    if (move == 0 && x < Lx - 1) {
-      const T* EL2 = env + (size_t)slot_lo(g, x + 2) * rowsz;
-      blk_unit(RP + (size_t)Ly * s2, s2);
-      if (threadIdx.x == 0) logR[Ly] = 0.0;
-      __syncthreads();
-      for (int y = Ly - 1; y >= 0; --y) {
-        blk_copy(eu, EU + (size_t)y * se, se);
-        blk_copy(el, EL2 + (size_t)y * se, se);
-        load_A(A1, Tpad, g, x * Ly + y, Sl[x * Ly + y], false);
-        load_A(A2, Tpad, g, (x + 1) * Ly + y, Sl[(x + 1) * Ly + y], false);
-        __syncthreads();
-        absorb2_right(g, RP + (size_t)(y + 1) * s2, eu, A1, A2, el, t1, t2, RP + (size_t)y * s2, plan.cx);
-        const double l = blk_normalize(RP + (size_t)y * s2, s2, red, &st);
-        if (threadIdx.x == 0) logR[y] = logR[y + 1] + l;
-      }
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        const double v = dz_abs(to_dz(RP[0]));
-        lcur = (v != 0.0) ? log(v) + logR[0] : -INFINITY;
-        logLc = 0.0;
-      }
-      blk_unit(LC, s2);
-      __syncthreads();
-      for (int y = 0; y < Ly; ++y) {
-        const double u = uniform53(slot, (uint32_t)sweep_id, (uint32_t)c, 0u, seed);
-        ++slot;
-        const int i0 = x * Ly + y, i1 = (x + 1) * Ly + y;
-        blk_copy(eu, EU + (size_t)y * se, se);
-        blk_copy(el, EL2 + (size_t)y * se, se);
-        if (Sl[i0] != Sl[i1]) {
-          load_A(A1, Tpad, g, i0, Sl[i1], false);
-          load_A(A2, Tpad, g, i1, Sl[i0], false);
-          __syncthreads();
-          absorb2(g, LC, eu, A1, A2, el, t1, t2, LW2, plan.cx);
-          const double lw = logLc + blk_normalize(LW2, s2, red, &st);
-          const T v = blk_dot(LW2, RP + (size_t)(y + 1) * s2, s2, red);
-          if (threadIdx.x == 0) {
-            const double av = dz_abs(to_dz(v));
-            const double l1 = (av != 0.0) ? log(av) + lw + logR[y + 1] : -INFINITY;
-            accept_flag = (isfinite(l1) && u < exp(2.0 * (l1 - lcur))) ? 1 : 0;
-            if (accept_flag) {
-              lcur = l1;
-              const uint8_t tmp = Sl[i0]; Sl[i0] = Sl[i1]; Sl[i1] = tmp;
-            }
-          }
-          __syncthreads();
-          acc += accept_flag;
-        }
-        load_A(A1, Tpad, g, i0, Sl[i0], false);
-        load_A(A2, Tpad, g, i1, Sl[i1], false);
-        __syncthreads();
-        absorb2(g, LC, eu, A1, A2, el, t1, t2, LW2, plan.cx);
-        const double l = blk_normalize(LW2, s2, red, &st);
-        blk_copy(LC, LW2, s2);
-        if (threadIdx.x == 0) logLc += l;
-        __syncthreads();
-      }
-    }
+    row_moves(g, plan, b, Tpad, Sl, env, x, up, move, slot0, sweep_id, c, seed, &acc, &st);
     for (int i = threadIdx.x; i < N; i += blockDim.x) Sg[i] = Sl[i];
     if (threadIdx.x == 0) {
       if (accepted) accepted[c] += acc;
@@ -876,14 +720,15 @@ __global__ void __launch_bounds__(NTHREADS, EnvBlocks<T>::value) k_sweep_moves(G
   }
 }
 
-// E^u[x] of every chain from its (updated) row x: the first row for x = 0, else one row step
-// from E^u[x-1]; compiled for the environment kernel's occupancy.  ustat (may be null): also
-// collects the row steps' status bits (the last sweep's, for a later evaluation that reuses
-// these upper environments).
+// One environment row of every chain from its (updated) row x, for the sweep's direction:
+// going down E^u[x] (the first row for x = 0, else one row step from E^u[x-1]), going up E^l[x]
+// (the last row for x = Lx-1, else one row step from E^l[x+1]); compiled for the environment
+// kernel's occupancy.  ustat (may be null): also collects the row steps' status bits (the last
+// sweep's, for a later evaluation that reuses these environments).
 template <typename T, typename G>
 __global__ void __launch_bounds__(NTHREADS, EnvBlocks<T>::value) k_env_row(G g, Plan plan, const T* __restrict__ Tpad,
-                                                      const uint8_t* __restrict__ S, int Ns, int x, T* envs,
-                                                      double* logs, int* status, int* ustat) {
+                                                      const uint8_t* __restrict__ S, int Ns, int x, int lower,
+                                                      T* envs, double* logs, int* status, int* ustat) {
   extern __shared__ __align__(16) char smem[];
   char* gbase = plan.gbase;
   RowWork<T> w = carve_row<T>(plan, smem, gbase);
@@ -897,15 +742,99 @@ __global__ void __launch_bounds__(NTHREADS, EnvBlocks<T>::value) k_env_row(G g, 
     T* env = envs + (size_t)c * env_sample_elems(g);
     double* lg = logs + (size_t)c * 2 * g.Lx;
     const uint8_t* Ss = S + (size_t)c * N;
-    const size_t sl = (size_t)slot_up(g, x) * rowsz;
     double l;
-    if (x == 0) l = env_first_row(g, env + sl, Tpad, 0, Ss, false, w.A, w.Z, w.red, &st);
-    else l = lg[slot_up(g, x - 1)] + env_row_step(g, env + (size_t)slot_up(g, x - 1) * rowsz, env + sl, Tpad, x,
-                                                  Ss + (size_t)x * g.Ly, false, w, &st, &wd, &flag);
+    int slot;
+    if (!lower) {
+      slot = slot_up(g, x);
+      if (x == 0) l = env_first_row(g, env + (size_t)slot * rowsz, Tpad, 0, Ss, false, w.A, w.Z, w.red, &st);
+      else l = lg[slot_up(g, x - 1)] + env_row_step(g, env + (size_t)slot_up(g, x - 1) * rowsz, env + (size_t)slot * rowsz,
+                                                    Tpad, x, Ss + (size_t)x * g.Ly, false, w, &st, &wd, &flag);
+    } else {
+      slot = slot_lo(g, x);
+      if (x == g.Lx - 1)
+        l = env_first_row(g, env + (size_t)slot * rowsz, Tpad, x, Ss + (size_t)x * g.Ly, true, w.A, w.Z, w.red, &st);
+      else l = lg[slot_lo(g, x + 1)] + env_row_step(g, env + (size_t)slot_lo(g, x + 1) * rowsz, env + (size_t)slot * rowsz,
+                                                    Tpad, x, Ss + (size_t)x * g.Ly, true, w, &st, &wd, &flag);
+    }
     if (threadIdx.x == 0) {
-      lg[slot_up(g, x)] = l;
+      lg[slot] = l;
       if (st) atomicOr(status + c, st);
       if (st && ustat) atomicOr(ustat + c, st);
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Metropolis sweeps in one launch: one CTA per chain (persistent over chains); the FP64 and
+// complex path.  Sweeps alternate direction with the sweep id (even: down the rows, odd: up),
+// each starting from the environments the previous one left: going down, the lower
+// environments of the current configuration (built at the sweep's start) and E^u rebuilt row
+// by row; going up, the upper ones (the previous sweep's, or built at the start of the launch)
+// and E^l rebuilt row by row.  Same moves, slots and decisions as the split FP32 sweep.
+template <typename T, typename G>
+__global__ void __launch_bounds__(NTHREADS, MinBlocks<T>::value) k_sample(G g, Plan plan, const T* __restrict__ Tpad, uint8_t* S,
+                                                     int Ns, int move, int nsweeps, unsigned long long seed,
+                                                     unsigned long long sweep0, T* envs, double* logs,
+                                                     long long* accepted, int* status) {
+  extern __shared__ __align__(16) char smem[];
+  char* gbase = plan.gbase;
+  RowWork<T> w = carve_row<T>(plan, smem, gbase);
+  const MoveBufs<T> b = carve_moves<T>(plan, smem, gbase);
+  uint8_t* Sl = (uint8_t*)buf_ptr(plan, B_S, smem, gbase);
+  __shared__ int st, flag;
+  __shared__ float wd;
+  const int N = g.Lx * g.Ly, Ly = g.Ly, Lx = g.Lx;
+  const size_t rowsz = (size_t)Ly * g.se;
+  for (int c = blockIdx.x; c < Ns; c += gridDim.x) {
+    uint8_t* Sg = S + (size_t)c * N;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) Sl[i] = Sg[i];
+    if (threadIdx.x == 0) { st = 0; wd = 0.f; }
+    long long acc = 0;
+    T* env = envs + (size_t)c * env_sample_elems(g);
+    double* lg = logs + (size_t)c * 2 * Lx;
+    __syncthreads();
+    for (int t = 0; t < nsweeps; ++t) {
+      const unsigned long long sweep_id = sweep0 + (unsigned long long)t;
+      const int up = (int)(sweep_id & 1ull);
+      if (!up) {
+        build_lower(g, Tpad, Sl, env, lg, w, &st, &wd, &flag, 1);
+        sweep_trivial_row(g, env, lg, 0);
+        __syncthreads();
+        for (int x = 0; x < Lx; ++x) {
+          row_moves(g, plan, b, Tpad, Sl, env, x, 0, move, sweep_slot0(g, x, 0, move), sweep_id, c, seed, &acc, &st);
+          if (x < Lx - 1) {
+            const size_t sl = (size_t)slot_up(g, x) * rowsz;
+            double l;
+            if (x == 0) l = env_first_row(g, env + sl, Tpad, 0, Sl, false, w.A, w.Z, w.red, &st);
+            else l = lg[slot_up(g, x - 1)] + env_row_step(g, env + (size_t)slot_up(g, x - 1) * rowsz, env + sl, Tpad, x,
+                                                           Sl + (size_t)x * Ly, false, w, &st, &wd, &flag);
+            if (threadIdx.x == 0) lg[slot_up(g, x)] = l;
+            __syncthreads();
+          }
+        }
+      } else {
+        if (t == 0) build_upper(g, Tpad, Sl, env, lg, w, &st, &wd, &flag);
+        sweep_trivial_row(g, env, lg, 1);
+        __syncthreads();
+        for (int x = Lx - 1; x >= 0; --x) {
+          row_moves(g, plan, b, Tpad, Sl, env, x, 1, move, sweep_slot0(g, x, 1, move), sweep_id, c, seed, &acc, &st);
+          if (x > 0) {
+            const size_t sl = (size_t)slot_lo(g, x) * rowsz;
+            double l;
+            if (x == Lx - 1) l = env_first_row(g, env + sl, Tpad, x, Sl + (size_t)x * Ly, true, w.A, w.Z, w.red, &st);
+            else l = lg[slot_lo(g, x + 1)] + env_row_step(g, env + (size_t)slot_lo(g, x + 1) * rowsz, env + sl, Tpad, x,
+                                                           Sl + (size_t)x * Ly, true, w, &st, &wd, &flag);
+            if (threadIdx.x == 0) lg[slot_lo(g, x)] = l;
+            __syncthreads();
+          }
+        }
+      }
+    }
+    for (int i = threadIdx.x; i < N; i += blockDim.x) Sg[i] = Sl[i];
+    if (threadIdx.x == 0) {
+      if (accepted) accepted[c] += acc;
+      if (st) atomicOr(status + c, st);
     }
     __syncthreads();
   }
@@ -1142,13 +1071,26 @@ cudaError_t launch_sample(const Geo& g, const Plan& p, int grid, size_t smem, co
     using GG = decltype(gg);
     if constexpr (sizeof(T) == 4) {
       for (int t = 0; t < nsweeps; ++t) {
-        k_env<T, GG><<<grid_e, NTHREADS, smem_e, s>>>(gg, pe, Tpad, S, Ns, 2, envs, logs, status, nullptr);
-        for (int x = 0; x < g.Lx; ++x) {
-          k_sweep_moves<T, GG><<<grid, NTHREADS, smem, s>>>(gg, p, Tpad, S, Ns, move, x, seed, sweep0 + t, envs, logs,
-                                                            accepted, status);
-          if (x < g.Lx - 1)
-            k_env_row<T, GG><<<grid_e, NTHREADS, smem_e, s>>>(gg, pe, Tpad, S, Ns, x, envs, logs, status,
-                                                              t == nsweeps - 1 ? ustat : nullptr);
+        const unsigned long long sid = sweep0 + t;
+        const int up = (int)(sid & 1ull);
+        int* us = (t == nsweeps - 1) ? ustat : nullptr;
+        if (!up) {
+          k_env<T, GG><<<grid_e, NTHREADS, smem_e, s>>>(gg, pe, Tpad, S, Ns, 2, envs, logs, status, nullptr);
+          for (int x = 0; x < g.Lx; ++x) {
+            k_sweep_moves<T, GG><<<grid, NTHREADS, smem, s>>>(gg, p, Tpad, S, Ns, move, x, 0, seed, sid, envs, logs,
+                                                              accepted, status);
+            if (x < g.Lx - 1)
+              k_env_row<T, GG><<<grid_e, NTHREADS, smem_e, s>>>(gg, pe, Tpad, S, Ns, x, 0, envs, logs, status, us);
+          }
+        } else {
+          // the previous sweep of this call left the upper environments of these configurations
+          if (t == 0) k_env<T, GG><<<grid_e, NTHREADS, smem_e, s>>>(gg, pe, Tpad, S, Ns, 1, envs, logs, status, nullptr);
+          for (int x = g.Lx - 1; x >= 0; --x) {
+            k_sweep_moves<T, GG><<<grid, NTHREADS, smem, s>>>(gg, p, Tpad, S, Ns, move, x, 1, seed, sid, envs, logs,
+                                                              accepted, status);
+            if (x > 0)
+              k_env_row<T, GG><<<grid_e, NTHREADS, smem_e, s>>>(gg, pe, Tpad, S, Ns, x, 1, envs, logs, status, us);
+          }
         }
       }
     } else {

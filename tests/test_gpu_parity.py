@@ -460,9 +460,11 @@ def test_fp32_sampler_chains_close_to_oracle(P):
     assert np.all(Sf.cpu().numpy() == Sfr, axis=1).sum() >= 22
 
 
-def test_env_reuse_after_sampling_equals_full_evaluation(P):
-    # the FP32 sampler leaves E^u of the final configurations in the store; an evaluation with
-    # reuse contracts only the lower side and must give the full evaluation's results
+@pytest.mark.parametrize("nsweeps", [1, 2])
+def test_env_reuse_after_sampling_equals_full_evaluation(P, nsweeps):
+    # the FP32 sampler leaves the environments it rebuilt last (E^u after a downward sweep, E^l
+    # after an upward one) for the final configurations in the store; an evaluation with reuse
+    # contracts only the other side and must give the full evaluation's results
     lat = I.Lattice(6, 5, 2, 3)
     th = I.peps_random(lat, 47, scale=0.5, bias=1.0)
     H = I.j1j2_chiral(lat, J1=1.0, J2=0.5, Jchi=0.0)
@@ -473,7 +475,7 @@ def test_env_reuse_after_sampling_equals_full_evaluation(P):
     ref.set_params(_dev(th))
     h.set_env_reuse(True)
     S = _dev(I.configs_neel(lat, 40))
-    h.sample(S, move=P.MOVE_EXCHANGE, nsweeps=2, seed=31)
+    h.sample(S, move=P.MOVE_EXCHANGE, nsweeps=nsweeps, seed=31)
     r = h.evaluate(H, S)
     e = ref.evaluate(H, S.clone())
     torch.cuda.synchronize()
