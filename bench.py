@@ -174,9 +174,9 @@ def _peaks():
 # DRAM bytes (read + write) of one sampler call of 2 sweeps in FP32 (every kernel of the split
 # sweep), from an ncu capture of 304 chains, scaled by the chains processed (each chain's
 # environment rows and partials are its own traffic); None until such a capture of the current
-# kernels exists.  profiles/sampler_split_heis8x8_D4_chi16_ns304.md: 1.336 GB per call of 2 sweeps
-# over 304 chains (k_env lower 0.47 GB, k_sweep_moves 0.49 GB, k_env_row 0.38 GB).
-_SAMPLER_CAPTURE = {"bytes": 1.336e9, "chains": 304, "sweeps": 2}
+# kernels exists.  profiles/sampler_split_heis8x8_D4_chi16_ns304.md: 1.297 GB per call of 2 sweeps
+# over 304 chains (k_env one-side pass 0.24 GB, k_sweep_moves 0.66 GB, k_env_row 0.40 GB).
+_SAMPLER_CAPTURE = {"bytes": 1.297e9, "chains": 304, "sweeps": 2}
 
 
 def _measured_traffic(kernel, ns, sweeps, prec):
@@ -307,8 +307,8 @@ def run_gpu(a):
     dom_launch_ms = ms_cls[dom] / max(1, launches[dom])
     achieved = flops[dom] / max(1, launches[dom]) / (dom_launch_ms / 1e3) / 1e12
     peak = (fp64_peak if not mixed else peaks.get("bf16_tflops", 1900.0)) if dom == "minsr_gram" else alu_peak
-    sampler_name = ("sampler sweeps (per sweep: k_env lower, then k_sweep_moves and k_env_row per row)"
-                    if prec == P.PREC_FP32 else "k_sample")
+    sampler_name = ("sampler call of alternating sweeps (k_env one-side pass where a sweep needs one, then "
+                    "k_sweep_moves and k_env_row per row)" if prec == P.PREC_FP32 else "k_sample")
     roof = {"kernel": {"env": "k_env", "sample": sampler_name, "row": "k_row", "pair": "k_pair",
                        "minsr_gram": "k_gram"}[dom],
             "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
