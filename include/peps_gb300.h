@@ -82,7 +82,10 @@ typedef struct {
     int max_samples; /* largest Ns any later call may pass (sizes the environment store)     */
     int gram;     /* MinSR Gram matrix: 0 = FP64 on CUDA cores; 1 = split BF16 on the tcgen05
                      tensor cores (Obar = hi + lo, T ~ hi hi^T + hi lo^T + lo hi^T, FP32
-                     accumulation; about 1e-5 relative error per entry)                    */
+                     accumulation; about 1e-5 relative error per entry); 2 = float-float on
+                     the FP32 pipes (Obar = hi + lo in floats, exact hi products by FMA plus the
+                     cross terms, sums kept as float pairs; about 48 significant bits, for
+                     GPUs whose FP64 rate is a small fraction of their FP32 rate)          */
     int solve;    /* MinSR solve when rcond == 0: 0 = FP64 Cholesky; 1 = FP32 Cholesky of
                      T + lambda followed by 4 steps of iterative refinement with FP64 residuals
                      (info[1] reports the final relative residual)                           */
@@ -239,8 +242,9 @@ peps_status peps_local_energy_bound(peps_handle* h, const peps_hamiltonian* H, c
  * refined residual stayed above 1e-10 and the FP64 factorisation was used instead.  When T +
  * lambda is not positive definite in floating point even in FP64 (lambda far below the
  * rounding error of T, e.g. a split-BF16 Gram of badly scaled O), info[0] = -1, dtheta_dev is
- * set to zero and the call returns PEPS_W_NUMERIC.  Needs lambda > 0 or rcond > 0.  The Gram matrix is FP64 (cfg.gram == 0) or split
- * BF16 on the tensor cores (cfg.gram == 1); the eigendecomposition is FP64.  The call
+ * set to zero and the call returns PEPS_W_NUMERIC.  Needs lambda > 0 or rcond > 0.  The Gram matrix is FP64 (cfg.gram == 0), split
+ * BF16 on the tensor cores (cfg.gram == 1) or float-float on the FP32 pipes (cfg.gram == 2);
+ * the factorisation / eigendecomposition is FP64.  The call
  * synchronises the stream before it returns. */
 peps_status minsr_step(peps_handle* h, const void* O_dev, const double* eloc_dev, const double* w_dev,
                        int Ns, double lambda, double rcond, double tau, double* dtheta_dev,

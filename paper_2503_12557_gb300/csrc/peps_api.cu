@@ -368,11 +368,11 @@ extern "C" peps_status peps_create(peps_handle** out, const peps_config* cfg) {
       c.chi > 64 || c.max_samples < 1)
     return PEPS_E_SHAPE;
   if (c.prec != PEPS_PREC_FP64 && c.prec != PEPS_PREC_FP32) return PEPS_E_ARG;
-  if (c.gram != 0 && c.gram != 1) return PEPS_E_ARG;
+  if (c.gram != 0 && c.gram != 1 && c.gram != 2) return PEPS_E_ARG;
   if (c.solve != 0 && c.solve != 1) return PEPS_E_ARG;
   if (c.cplx != 0 && c.cplx != 1) return PEPS_E_ARG;
   if (!(c.trunc_weight >= 0.0 && c.trunc_weight < 1.0)) return PEPS_E_ARG;
-  if (c.cplx && c.gram != 0) return PEPS_E_UNSUPPORTED;  // the split-BF16 Gram is real only
+  if (c.cplx && c.gram == 1) return PEPS_E_UNSUPPORTED;  // the split-BF16 Gram is real only
   peps_handle* h = new peps_handle();
   h->cfg = c;
   h->elem = (c.cplx ? 2 : 0) + (c.prec == PEPS_PREC_FP64 ? 0 : 1);
@@ -935,19 +935,21 @@ static peps_status ensure_minsr(peps_handle* h, int Ns, long long Np) {
   for (double** b : bufs)
     if (*b) { cudaFree(*b); *b = nullptr; }
   const size_t nn = (size_t)n * n;
-  if (cudaMalloc(&h->Obar, sizeof(double) * (size_t)Ns * Np) != cudaSuccess ||
+  // Obar holds n rows (the capacity): a later call with an even Ns up to n reuses it
+  if (cudaMalloc(&h->Obar, sizeof(double) * (size_t)n * Np) != cudaSuccess ||
       cudaMalloc(&h->Tm, sizeof(double) * nn) != cudaSuccess || cudaMalloc(&h->Vm, sizeof(double) * nn) != cudaSuccess ||
       cudaMalloc(&h->Hm, sizeof(double) * nn) != cudaSuccess ||
       cudaMalloc(&h->mean, sizeof(double) * (size_t)Np) != cudaSuccess ||
       cudaMalloc(&h->ebar, sizeof(double) * n) != cudaSuccess || cudaMalloc(&h->yv, sizeof(double) * n) != cudaSuccess ||
       cudaMalloc(&h->xv, sizeof(double) * n) != cudaSuccess || cudaMalloc(&h->cnt, sizeof(double) * 8) != cudaSuccess)
     return fail(h, PEPS_E_WORKSPACE, "MinSR workspace allocation failed");
-  if (h->cfg.gram == 1) {
+  if (h->cfg.gram == 1 || h->cfg.gram == 2) {
     if (h->g_hi) { cudaFree(h->g_hi); h->g_hi = nullptr; }
     if (h->g_lo) { cudaFree(h->g_lo); h->g_lo = nullptr; }
-    const size_t e = (size_t)gram_tc_pad_rows(Ns) * (size_t)gram_tc_pad_k(h->Np) * 2;
+    const size_t e = (h->cfg.gram == 1) ? (size_t)gram_tc_pad_rows(Ns) * (size_t)gram_tc_pad_k(h->Np) * 2
+                                        : (size_t)n * (size_t)Np * sizeof(float);  // the capacity, n rows
     if (cudaMalloc(&h->g_hi, e) != cudaSuccess || cudaMalloc(&h->g_lo, e) != cudaSuccess)
-      return fail(h, PEPS_E_WORKSPACE, "tensor-core Gram workspace allocation failed");
+      return fail(h, PEPS_E_WORKSPACE, "Gram workspace allocation failed");
   }
   h->ms_cap = n;
   h->ms_np = Np;
@@ -993,6 +995,9 @@ extern "C" peps_status minsr_step(peps_handle* h, const void* O_dev, const doubl
     CK(launch_gram_tc(h->Obar, Ns, Np, h->g_hi, h->g_lo, h->Tm, n, rcond > 0.0, (int*)(h->cnt + 4), s),
        "tensor-core Gram");
     tstop(h, ts, s, rcond > 0.0 ? 3 : 2);
+  } else if (h->cfg.gram == 2) {
+    CK(launch_gram_ff(h->Obar, Ns, Np, (float*)h->g_hi, (float*)h->g_lo, h->Tm, n, s), "float-float Gram");
+    tstop(h, ts, s, 2);
   } else {
     CK(launch_gram(h->Obar, Ns, Np, h->Tm, n, s), "Gram");
     tstop(h, ts, s);

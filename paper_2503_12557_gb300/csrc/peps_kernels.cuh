@@ -171,6 +171,9 @@ cudaError_t launch_center_cplx(const TO* O, const double* w, int Ns, long long N
 cudaError_t launch_center_e_cplx(const double* eloc, const double* w, int Ns, double* ebar2, cudaStream_t s);
 cudaError_t launch_unembed(const double* d2, long long Np, double* dtheta, cudaStream_t s);
 cudaError_t launch_gram(const double* Obar, int Ns, long long Np, double* Tm, int ld, cudaStream_t s);
+// float-float Gram on the FP32 pipes (hi, lo: Ns x Np floats of scratch)
+cudaError_t launch_gram_ff(const double* Obar, int Ns, long long Np, float* hi, float* lo, double* Tm, int ld,
+                           cudaStream_t s);
 // cyclic Jacobi eigendecomposition of the symmetric Ns x Ns matrix A (overwritten by its
 // diagonal form), V accumulates the rotations; returns the sweeps used (host loop)
 int jacobi_eig(double* A, double* V, int n, double* rot, double* offn, double* hbuf, cudaStream_t s,

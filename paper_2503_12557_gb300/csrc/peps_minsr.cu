@@ -343,6 +343,104 @@ cudaError_t launch_center_e(const double* eloc, const double* w, int Ns, double*
   return cudaGetLastError();
 }
 
+// ---- float-float ("double-single") Gram on the FP32 pipes
+// Obar split once into hi = float(x), lo = float(x - hi) (x = hi + lo to about 48 bits).
+__global__ void k_split_ff(const double* __restrict__ x, size_t n, float* __restrict__ hi, float* __restrict__ lo) {
+  for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
+    const double v = x[o];
+    const float h = __double2float_rn(v);
+    hi[o] = h;
+    lo[o] = __double2float_rn(v - (double)h);
+  }
+}
+
+// T = Obar Obar^T from the float pairs: each product a b with a = ah + al, b = bh + bl is taken
+// as p + e + c, p = ah bh rounded, e = fma(ah, bh, -p) its exact error, c = ah bl + al bh (al bl,
+// about 2^-48 of the product, dropped); the running sum is a float pair (sh, sl): sh + p by
+// Knuth's two-sum, its error and e + c into sl, renormalised after every GK k-steps; the result
+// is sh + sl in double.  The error-free steps use the _rn intrinsics so that no multiply and add
+// are fused.  Same lower-triangle 64 x 64 tiling as k_gram.
+__global__ void __launch_bounds__(256) k_gram_ff(const float* __restrict__ Oh, const float* __restrict__ Ol, int Ns,
+                                                 long long Np, double* Tm, int ld) {
+  __shared__ float Ah[GK][GT + 1], Al[GK][GT + 1], Bh[GK][GT + 1], Bl[GK][GT + 1];
+  const int nt = (Ns + GT - 1) / GT;
+  int t = blockIdx.x, ti = 0;
+  while (t >= ti + 1) { t -= ti + 1; ++ti; }
+  const int tj = t;
+  if (ti >= nt) return;
+  const int r0 = ti * GT, c0 = tj * GT;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  float sh[4][4], sl[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) { sh[i][j] = 0.f; sl[i][j] = 0.f; }
+  for (long long k0 = 0; k0 < Np; k0 += GK) {
+    for (int o = threadIdx.x; o < GK * GT; o += blockDim.x) {
+      const int kk = o % GK, rr = o / GK;
+      const long long k = k0 + kk;
+      const bool ra = (r0 + rr < Ns && k < Np), rb = (c0 + rr < Ns && k < Np);
+      Ah[kk][rr] = ra ? Oh[(size_t)(r0 + rr) * Np + k] : 0.f;
+      Al[kk][rr] = ra ? Ol[(size_t)(r0 + rr) * Np + k] : 0.f;
+      Bh[kk][rr] = rb ? Oh[(size_t)(c0 + rr) * Np + k] : 0.f;
+      Bl[kk][rr] = rb ? Ol[(size_t)(c0 + rr) * Np + k] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < GK; ++kk) {
+      float ah[4], al[4], bh[4], bl[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        ah[i] = Ah[kk][ty * 4 + i]; al[i] = Al[kk][ty * 4 + i];
+        bh[i] = Bh[kk][tx * 4 + i]; bl[i] = Bl[kk][tx * 4 + i];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float p = __fmul_rn(ah[i], bh[j]);
+          const float e = __fmaf_rn(ah[i], bh[j], -p);
+          const float c = __fmaf_rn(ah[i], bl[j], __fmul_rn(al[i], bh[j]));
+          const float s0 = __fadd_rn(sh[i][j], p);
+          const float bb = __fsub_rn(s0, sh[i][j]);
+          const float er = __fadd_rn(__fsub_rn(sh[i][j], __fsub_rn(s0, bb)), __fsub_rn(p, bb));
+          sh[i][j] = s0;
+          sl[i][j] = __fadd_rn(sl[i][j], __fadd_rn(er, __fadd_rn(e, c)));
+        }
+    }
+    // renormalise the pairs (fast two-sum: |sh| >= |sl|)
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float s0 = __fadd_rn(sh[i][j], sl[i][j]);
+        sl[i][j] = __fsub_rn(sl[i][j], __fsub_rn(s0, sh[i][j]));
+        sh[i][j] = s0;
+      }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int r = r0 + ty * 4 + i, c = c0 + tx * 4 + j;
+      if (r < Ns && c < Ns) {
+        const double v = (double)sh[i][j] + (double)sl[i][j];
+        Tm[(size_t)r * ld + c] = v;
+        Tm[(size_t)c * ld + r] = v;
+      }
+    }
+}
+
+cudaError_t launch_gram_ff(const double* Obar, int Ns, long long Np, float* hi, float* lo, double* Tm, int ld,
+                           cudaStream_t s) {
+  const size_t n = (size_t)Ns * (size_t)Np;
+  k_split_ff<<<1216, 256, 0, s>>>(Obar, n, hi, lo);
+  const int nt = (Ns + GT - 1) / GT;
+  k_gram_ff<<<nt * (nt + 1) / 2, 256, 0, s>>>(hi, lo, Ns, Np, Tm, ld);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_gram(const double* Obar, int Ns, long long Np, double* Tm, int ld, cudaStream_t s) {
   const int nt = (Ns + GT - 1) / GT;
   const int ntiles = nt * (nt + 1) / 2;

@@ -492,3 +492,38 @@ def test_env_reuse_after_sampling_equals_full_evaluation(P, nsweeps):
     e2 = ref.evaluate(H, S.clone())
     torch.cuda.synchronize()
     assert torch.equal(r2["logabs"], e2["logabs"]) and torch.equal(r2["eloc"], e2["eloc"])
+
+
+@pytest.mark.parametrize("ns,npar,rc,lam,offset", [(700, 300, 0.0, 1e-3, 0.1), (333, 500, 1e-9, 1e-4, 0.1),
+                                                    (1030, 1200, 0.0, 1e-4, 50.0)])
+def test_minsr_float_float_gram_vs_oracle(P, ns, npar, rc, lam, offset):
+    # float-float Gram on the FP32 pipes (about 48 significant bits): dtheta within the FP64
+    # Gram's own agreement with the oracle times the conditioning of T + lambda; the last case
+    # has large column means (centring cancels most of each entry)
+    from oracle import minsr
+    rng = np.random.default_rng(ns + 7)
+    O = rng.standard_normal((ns, npar)) + offset * rng.standard_normal(npar)
+    e = rng.standard_normal(ns) - 3.0
+    d_ref, inf_ref = minsr.minsr(O, e, lam=lam, rcond=rc, tau=0.1)
+    dth, info = _minsr_raw(P, O, e, lam, rc, 0.1, gram=2)
+    d64, _ = _minsr_raw(P, O, e, lam, rc, 0.1, gram=0)
+    rel = np.linalg.norm(dth - d_ref) / np.linalg.norm(d_ref)
+    rel64 = np.linalg.norm(d64 - d_ref) / np.linalg.norm(d_ref)
+    print(f"float-float Gram: relative dtheta error {rel:.2e} (FP64 Gram {rel64:.2e})")
+    assert rel <= 1e-7
+    assert int(info[0]) == inf_ref["rank"]
+
+
+def test_minsr_float_float_gram_complex(P):
+    from oracle import energy, minsr
+    lat = I.Lattice(3, 3, 2, 2)
+    th = I.peps_random(lat, 4, scale=0.6, bias=1.0, complex_=True)
+    S = I.configs_uniform_sz0(lat, 48, 5)
+    H = I.j1j2_chiral(lat)
+    ref = energy.evaluate(th, S, lat, 4, H=H, want_O=True)
+    h = P.PEPS(3, 3, 2, 2, 4, max_samples=48, cplx=True, gram=2)
+    dth, info = h.minsr_step(_dev(ref["O"]), _dev(np.stack([ref["eloc"].real, ref["eloc"].imag], 1)),
+                             lam=1e-3, rcond=0.0, tau=0.07)
+    torch.cuda.synchronize()
+    d_ref, _ = minsr.minsr(ref["O"], ref["eloc"], lam=1e-3, rcond=0.0, tau=0.07)
+    assert np.linalg.norm(dth.cpu().numpy() - d_ref) <= 1e-7 * np.linalg.norm(d_ref)
