@@ -46,6 +46,9 @@ def _args():
     ap.add_argument("--cpu-samples", type=int, default=12)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--gram", default=None, choices=["ff", "fp64", "bf16"],
+                    help="MinSR Gram of the step: float-float on the FP32 pipes (default with --prec fp32), "
+                         "FP64 (default with --prec fp64), or split-BF16 tcgen05")
     return ap.parse_args()
 
 
@@ -211,8 +214,8 @@ def run_gpu(a):
     H = I.heisenberg(lat)
     theta0 = I.peps_random(lat, w["seed_theta"], **w["init"])
     S0 = I.configs_neel(lat, ns)
-    mixed = False  # MinSR Gram and solve in FP64 on either path
-    h = P.PEPS(lat.Lx, lat.Ly, lat.d, lat.D, w["chi"], prec=prec, max_samples=ns, gram=0, solve=0)
+    gram = {"fp64": 0, "bf16": 1, "ff": 2}[a.gram or ("ff" if a.prec == "fp32" else "fp64")]  # the solve stays FP64 Cholesky in every case
+    h = P.PEPS(lat.Lx, lat.Ly, lat.d, lat.D, w["chi"], prec=prec, max_samples=ns, gram=gram, solve=0)
     theta = torch.as_tensor(theta0).cuda()
     h.set_params(theta)
     h.set_env_reuse(True)  # the evaluation takes the sampler's upper environments (cached, unchanged S)
@@ -271,6 +274,14 @@ def run_gpu(a):
     step_ms = [e0.elapsed_time(marks[0])] + [marks[k - 1].elapsed_time(marks[k]) for k in range(1, a.steps)]
     ms_cls, launches, ctr = h.timing_read()
     h.timing(False)
+    # the last timed step's MinSR update against an FP64 Gram of the same O and E_loc
+    dtheta_check = None
+    if gram != 0:
+        dth_last = h.minsr_step(r["O"], r["eloc"], lam=w["lam"], rcond=w["rcond"], tau=w["tau"])[0].clone()
+        h64 = P.PEPS(lat.Lx, lat.Ly, lat.d, lat.D, w["chi"], prec=prec, max_samples=2, gram=0, solve=0)
+        dth64 = h64.minsr_step(r["O"], r["eloc"], lam=w["lam"], rcond=w["rcond"], tau=w["tau"])[0]
+        dtheta_check = float((dth_last - dth64).norm() / dth64.norm())
+        h64.close()
     ms_step = ms_total / a.steps
     if world > 1:
         t = torch.tensor([ms_step], device="cuda")
@@ -306,7 +317,9 @@ def run_gpu(a):
     dom = max(flops, key=lambda k: ms_cls.get(k, 0.0))
     dom_launch_ms = ms_cls[dom] / max(1, launches[dom])
     achieved = flops[dom] / max(1, launches[dom]) / (dom_launch_ms / 1e3) / 1e12
-    peak = (fp64_peak if not mixed else peaks.get("bf16_tflops", 1900.0)) if dom == "minsr_gram" else alu_peak
+    # a Gram-dominated step: FP64 FMA peak, FP32 pipe peak (float-float) or the BF16 tensor peak
+    gram_peak = {0: fp64_peak, 1: peaks.get("bf16_tflops", 1900.0), 2: fp32_peak}[gram]
+    peak = gram_peak if dom == "minsr_gram" else alu_peak
     sampler_name = ("sampler call of alternating sweeps (k_env one-side pass where a sweep needs one, then "
                     "k_sweep_moves and k_env_row per row)" if prec == P.PREC_FP32 else "k_sample")
     roof = {"kernel": {"env": "k_env", "sample": sampler_name, "row": "k_row", "pair": "k_pair",
@@ -323,11 +336,15 @@ def run_gpu(a):
             "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if prec == P.PREC_FP32 else "f64", "data": "synthetic",
             "config": _config(w, ns, a.prec, a.sweeps), "step_ms": step_ms, "minsr_step_s": minsr_s,
-            "minsr": {"gram": "split-BF16 tcgen05" if mixed else "FP64 CUDA cores",
+            "minsr": {"gram": {0: "FP64 CUDA cores", 1: "split-BF16 tcgen05",
+                               2: "float-float pairs on the FP32 pipes"}[gram],
                       "solve": "FP64 Cholesky",
                       "gram_ms": ms_cls["minsr_gram"] / a.steps, "solve_ms": ms_cls["minsr_eig"] / a.steps,
-                      "gram_tflops": (costmodel.gram_flops(ns, h.Np) * (3 if mixed else 1) /
-                                      max(1e-9, ms_cls["minsr_gram"] / a.steps / 1e3) / 1e12),
+                      "gram_tflops_algorithmic": (costmodel.gram_flops(ns, h.Np) /
+                                                  max(1e-9, ms_cls["minsr_gram"] / a.steps / 1e3) / 1e12),
+                      "gram_pipe_frac": (costmodel.gram_pipe_flops(ns, h.Np, gram) /
+                                         max(1e-9, ms_cls["minsr_gram"] / a.steps / 1e3) / 1e12 / gram_peak),
+                      "dtheta_rel_diff_vs_fp64_gram": dtheta_check,
                       "last_info": [float(x) for x in info_hist[-1].cpu()]},
             "kernel_ms_per_step": {k: v / a.steps for k, v in ms_cls.items()},
             "roofline": roof, "alu_peaks_measured_tflops": {"fp32": fp32_peak, "fp64": fp64_peak},
@@ -426,9 +443,10 @@ def run_learned(a):
 
 def run_gram(a):
     """MinSR step on a synthetic O (N_s x N_p, entries N(0,1) plus a 0.1 column offset so that
-    centring matters) with the FP64 CUDA-core Gram and with the split-BF16 tcgen05 Gram; reports
-    the Gram time, its tensor-pipe rate (3 BF16 products per algorithmic multiply-add) and the
-    relative difference of the two dtheta."""
+    centring matters) with the FP64 CUDA-core Gram, the split-BF16 tcgen05 Gram and the float-float
+    Gram on the FP32 pipes; reports each Gram's time, its pipe rate (3 BF16 products, 13 FP32
+    operations per algorithmic multiply-add) and the relative difference of each dtheta from the
+    FP64 one."""
     import torch
     from paper_2503_12557_gb300 import build, inputs as I, peps as P
     build.build()
@@ -438,7 +456,7 @@ def run_gram(a):
     out = {"mode": "gram", "ns": ns}
     res = {}
     g = torch.Generator(device="cuda").manual_seed(5005)
-    for gram, tag in ((1, "tcgen05_split_bf16"), (0, "fp64_cuda_cores")):
+    for gram, tag in ((1, "tcgen05_split_bf16"), (2, "float_float_fp32"), (0, "fp64_cuda_cores")):
         h = P.PEPS(lat.Lx, lat.Ly, 2, lat.D, lat.D, prec=P.PREC_FP64, max_samples=2, gram=gram)
         out["np"] = h.Np
         g.manual_seed(5005)
@@ -462,6 +480,9 @@ def run_gram(a):
             r["tensor_tflops_bf16"] = tflops
             r["roofline"] = {"bound": "tensor", "achieved": tflops, "peak": peaks.get("bf16_tflops", 1900.0),
                              "unit": "TFLOP/s", "frac": tflops / peaks.get("bf16_tflops", 1900.0)}
+        elif gram == 2:
+            r["fp32_pipe_tflops"] = 13 * 2 * mac / (gram_ms / 1e3) / 1e12
+            r["fp32_pipe_frac_of_measured_fma_peak"] = r["fp32_pipe_tflops"] / P.probe_fma(False)
         else:
             r["fp64_tflops"] = 2 * mac / (gram_ms / 1e3) / 1e12
         res[tag] = dth
@@ -469,8 +490,9 @@ def run_gram(a):
         del O
         h.close()
         torch.cuda.empty_cache()
-    d = res["tcgen05_split_bf16"] - res["fp64_cuda_cores"]
-    out["dtheta_rel_diff"] = float(d.norm() / res["fp64_cuda_cores"].norm())
+    for tag in ("tcgen05_split_bf16", "float_float_fp32"):
+        d = res[tag] - res["fp64_cuda_cores"]
+        out[tag]["dtheta_rel_diff"] = float(d.norm() / res["fp64_cuda_cores"].norm())
     print(json.dumps(out), flush=True)
 
 

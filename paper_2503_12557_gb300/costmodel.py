@@ -90,3 +90,14 @@ def gram_flops(ns, npar):
     """k_gram computes the lower-triangle 64x64 tiles in full: about (Ns^2/2 + 32 Ns) Np MACs."""
     nt = (ns + 63) // 64
     return 2.0 * (nt * (nt + 1) // 2) * 64 * 64 * npar
+
+
+# pipe operations per algorithmic multiply-add of each Gram kernel, counted as flops (2 per
+# issued FMA-pipe operation, so that the figure compares with the FMA peaks): FP64 one FMA;
+# split-BF16 three tensor products; float-float 13 FP32 operations (product and its FMA error,
+# the two cross terms, Knuth's two-sum, three adds into the low word)
+GRAM_PIPE_OPS = {0: 1, 1: 3, 2: 13}
+
+
+def gram_pipe_flops(ns, npar, gram):
+    return gram_flops(ns, npar) * GRAM_PIPE_OPS[gram]
