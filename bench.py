@@ -347,6 +347,8 @@ def run_gpu(a):
                       "dtheta_rel_diff_vs_fp64_gram": dtheta_check,
                       "last_info": [float(x) for x in info_hist[-1].cpu()]},
             "kernel_ms_per_step": {k: v / a.steps for k, v in ms_cls.items()},
+            "jacobi": {"svds": int(ctr["svds"]), "sweeps_per_svd": ctr["jacobi_sweeps"] / svd_all,
+                       "rotations_per_svd": ctr["jacobi_rotations"] / svd_all},
             "roofline": roof, "alu_peaks_measured_tflops": {"fp32": fp32_peak, "fp64": fp64_peak},
             "gpu_launches": gpu_launches, "clocks": clk.summary(),
             "acceptance": float(acc.sum().item()) / max(1.0, ns * (sweep_ctr[0]) * (2 * lat.Lx * lat.Ly - lat.Lx - lat.Ly) * 0.5),

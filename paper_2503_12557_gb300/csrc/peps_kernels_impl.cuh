@@ -566,11 +566,12 @@ __device__ void row_moves(const G& g, const Plan& plan, const MoveBufs<T>& b, co
       ++slot;
       const int i0 = x * Ly + y, i1 = i0 + 1;
       const bool possible = (move == 0) ? (Sl[i0] != Sl[i1]) : true;
+      int taken = 0;
       if (possible) {
+        // the window: LC with column y in its proposed state (LW2, kept: it is the next LC if
+        // the move is accepted), then for an exchange column y+1 as well (LW)
         const int w_ = (move == 0) ? 2 : 1;
-        blk_copy(LW, LC, se);
-        __syncthreads();
-        double lw = logLc;
+        double lw = logLc, l0 = 0.0;
         for (int cc = 0; cc < w_; ++cc) {
           const int site = i0 + cc;
           int s_new;
@@ -580,12 +581,17 @@ __device__ void row_moves(const G& g, const Plan& plan, const MoveBufs<T>& b, co
           blk_copy(el, EL + (size_t)(y + cc) * se, se);
           load_A(A1, Tpad, g, site, s_new, false);
           __syncthreads();
-          absorb1(g, LW, eu, A1, el, t1, t2, LW2);
-          lw += blk_normalize(LW2, se, red, st);
-          blk_copy(LW, LW2, se);
+          if (cc == 0) {
+            absorb1(g, LC, eu, A1, el, t1, t2, LW2);
+            l0 = blk_normalize(LW2, se, red, st);
+            lw += l0;
+          } else {
+            absorb1(g, LW2, eu, A1, el, t1, t2, LW);
+            lw += blk_normalize(LW, se, red, st);
+          }
           __syncthreads();
         }
-        const T v = blk_dot(LW, RP + (size_t)(y + w_) * se, se, red);
+        const T v = blk_dot(w_ == 2 ? LW : LW2, RP + (size_t)(y + w_) * se, se, red);
         if (threadIdx.x == 0) {
           const double av = dz_abs(to_dz(v));
           const double l1 = (av != 0.0) ? log(av) + lw + logR[y + w_] : -INFINITY;
@@ -598,16 +604,25 @@ __device__ void row_moves(const G& g, const Plan& plan, const MoveBufs<T>& b, co
         }
         __syncthreads();
         *acc += accept_flag;
+        taken = accept_flag;
+        if (taken) {
+          // column y now holds the proposed state: the new LC is the window's first column
+          blk_copy(LC, LW2, se);
+          if (threadIdx.x == 0) logLc += l0;
+          __syncthreads();
+        }
       }
-      blk_copy(eu, EU + (size_t)y * se, se);
-      blk_copy(el, EL + (size_t)y * se, se);
-      load_A(A1, Tpad, g, x * Ly + y, Sl[x * Ly + y], false);
-      __syncthreads();
-      absorb1(g, LC, eu, A1, el, t1, t2, LW2);
-      const double l = blk_normalize(LW2, se, red, st);
-      blk_copy(LC, LW2, se);
-      if (threadIdx.x == 0) logLc += l;
-      __syncthreads();
+      if (!taken) {
+        blk_copy(eu, EU + (size_t)y * se, se);
+        blk_copy(el, EL + (size_t)y * se, se);
+        load_A(A1, Tpad, g, x * Ly + y, Sl[x * Ly + y], false);
+        __syncthreads();
+        absorb1(g, LC, eu, A1, el, t1, t2, LW2);
+        const double l = blk_normalize(LW2, se, red, st);
+        blk_copy(LC, LW2, se);
+        if (threadIdx.x == 0) logLc += l;
+        __syncthreads();
+      }
     }
   }
   // ---- vertical moves (xt, y) <-> (xt+1, y) with psi_{xt,xt+1} (E^u[xt-1], E^l[xt+2])
@@ -642,12 +657,14 @@ __device__ void row_moves(const G& g, const Plan& plan, const MoveBufs<T>& b, co
       const int i0 = xt * Ly + y, i1 = (xt + 1) * Ly + y;
       blk_copy(eu, EU + (size_t)y * se, se);
       blk_copy(el, EL2 + (size_t)y * se, se);
+      int taken = 0;
       if (Sl[i0] != Sl[i1]) {
         load_A(A1, Tpad, g, i0, Sl[i1], false);
         load_A(A2, Tpad, g, i1, Sl[i0], false);
         __syncthreads();
         absorb2(g, LC, eu, A1, A2, el, t1, t2, LW2, plan.cx);
-        const double lw = logLc + blk_normalize(LW2, s2, red, st);
+        const double l0 = blk_normalize(LW2, s2, red, st);
+        const double lw = logLc + l0;
         const T v = blk_dot(LW2, RP + (size_t)(y + 1) * s2, s2, red);
         if (threadIdx.x == 0) {
           const double av = dz_abs(to_dz(v));
@@ -660,15 +677,24 @@ __device__ void row_moves(const G& g, const Plan& plan, const MoveBufs<T>& b, co
         }
         __syncthreads();
         *acc += accept_flag;
+        taken = accept_flag;
+        if (taken) {
+          // the proposal's window is the new LC
+          blk_copy(LC, LW2, s2);
+          if (threadIdx.x == 0) logLc += l0;
+          __syncthreads();
+        }
       }
-      load_A(A1, Tpad, g, i0, Sl[i0], false);
-      load_A(A2, Tpad, g, i1, Sl[i1], false);
-      __syncthreads();
-      absorb2(g, LC, eu, A1, A2, el, t1, t2, LW2, plan.cx);
-      const double l = blk_normalize(LW2, s2, red, st);
-      blk_copy(LC, LW2, s2);
-      if (threadIdx.x == 0) logLc += l;
-      __syncthreads();
+      if (!taken) {
+        load_A(A1, Tpad, g, i0, Sl[i0], false);
+        load_A(A2, Tpad, g, i1, Sl[i1], false);
+        __syncthreads();
+        absorb2(g, LC, eu, A1, A2, el, t1, t2, LW2, plan.cx);
+        const double l = blk_normalize(LW2, s2, red, st);
+        blk_copy(LC, LW2, s2);
+        if (threadIdx.x == 0) logLc += l;
+        __syncthreads();
+      }
     }
   }
 }

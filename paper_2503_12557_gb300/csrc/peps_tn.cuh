@@ -586,11 +586,13 @@ __device__ void zero_tiny_rows(T* X, int m, int L, int ldx, typename Scal<T>::R 
 }
 
 // One-sided (Hestenes) Jacobi on the rows of X (m rows, m even, row length L, leading dim
-// ldx): rotate pairs of rows until every pair is orthogonal to the relative tolerance L eps
-// (well above the sqrt(L) eps rounding noise of a converged pair's dot product, so a converged
-// sweep really makes no rotation), skipping pairs where one row is numerically zero (squared
-// norm below (L eps)^2 of the largest).  On return the rows are sigma_i v_i^T with v_i the right
-// singular vectors of the input.
+// ldx): rotate pairs of rows whose relative dot product exceeds the tolerance tol = L eps
+// (well above the sqrt(L) eps rounding noise of a converged pair's dot product), skipping pairs
+// where one row is numerically zero (squared norm below (L eps)^2 of the largest), and stop after
+// the first sweep in which no pair had a relative dot product of sqrt(tol) or more: by the
+// quadratic convergence of cyclic Jacobi, that sweep's rotations leave dot products of order tol,
+// so the next sweep would rotate nothing.  On return the rows are sigma_i v_i^T with v_i the
+// right singular vectors of the input.
 //   Each warp treats four pairs at once (eight lanes per pair).  The squared row norms live in
 //   nrm[] (m entries): exact at the start of every sweep, and within a sweep updated after a
 //   rotation by Rutishauser's formulas a' = a - t g, b' = b + t g (g the pair's dot product), so
@@ -605,6 +607,7 @@ __device__ int hestenes_rows_smem(T* X, int m, int L, int ldx, int* flag, unsign
   const unsigned gmask = 0xffu << (grp * 8);
   const R eps = JacobiTol<R>::eps;
   const R tol = R(L) * eps;
+  const R stop = sqrt(tol);
   R tiny = 0;
   unsigned long long nrot = 0;
   for (int sweep = 0; sweep < JacobiTol<R>::sweeps; ++sweep) {
@@ -622,7 +625,7 @@ __device__ int hestenes_rows_smem(T* X, int m, int L, int ldx, int* flag, unsign
       nmax = block_max(nmax, red);
       tiny = nmax * (R(L) * eps) * (R(L) * eps);
     }
-    int rotated = 0;
+    int rotated = 0, big = 0;
     for (int r = 0; r < m - 1; ++r) {
       for (int pi = warp * 4 + grp; pi < m / 2; pi += ngroups) {
         const int p = rr_player(pi, r, m), q = rr_player(m - 1 - pi, r, m);
@@ -636,6 +639,7 @@ __device__ int hestenes_rows_smem(T* X, int m, int L, int ldx, int* flag, unsign
         c += shfl_xor_(gmask, c, 1);
         const R ac = abs_(c);
         if (ac != R(0) && a > tiny && b > tiny && ac > tol * sqrt(a * b)) {
+          if (ac >= stop * sqrt(a * b)) big = 1;
           // with c = |c| e^{i phi}: rotate (x_p, e^{i phi} x_q), whose product is |c|;
           // zeta = (b - a) / (2|c|); t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)) is the smaller
           // root of t^2 + 2 zeta t - 1 = 0, which makes the rotated rows orthogonal
@@ -661,11 +665,13 @@ __device__ int hestenes_rows_smem(T* X, int m, int L, int ldx, int* flag, unsign
       }
       __syncthreads();
     }
-    if (rotated) *flag = 1;  // benign race: every writer stores 1
+    // bit 0: some pair rotated; bit 1: some pair had a relative dot product of at least `stop`
+    const unsigned bits = __ballot_sync(0xffffffffu, rotated) ? (__ballot_sync(0xffffffffu, big) ? 3u : 1u) : 0u;
+    if (lane == 0 && bits) atomicOr(flag, (int)bits);
     __syncthreads();
     const int any = *flag;
     __syncthreads();
-    if (!any) {
+    if (!(any & 2)) {
       zero_tiny_rows(X, m, L, ldx, tiny);
       if (ctr && nrot) atomicAdd(ctr + 1, nrot);
       if (ctr && threadIdx.x == 0) { atomicAdd(ctr + 0, (unsigned long long)(sweep + 1)); atomicAdd(ctr + 2, 1ull); }
@@ -682,10 +688,12 @@ __device__ int hestenes_rows_smem(T* X, int m, int L, int ldx, int* flag, unsign
 // to the relative tolerance and neither row is numerically zero: zeta = (b - a) / (2c),
 // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)) (the smaller root of t^2 + 2 zeta t - 1 = 0,
 // which makes the rotated rows orthogonal), cos = 1 / sqrt(1 + t^2), sin = cos t, and t c for
-// the norm updates.  FP32 takes the reciprocal square roots from the SFU (about 2 ulp).
-__device__ __forceinline__ void jac_params(double a, double b, double c, double tol, double tiny, double& cs,
-                                           double& sn, double& tc) {
+// the norm updates.  FP32 takes the reciprocal square roots from the SFU (about 2 ulp).  `big`
+// is set when the pair's relative dot product |c| / sqrt(a b) is at least `stop`.
+__device__ __forceinline__ void jac_params(double a, double b, double c, double tol, double tiny, double stop,
+                                           double& cs, double& sn, double& tc, int& big) {
   if (c != 0.0 && a > tiny && b > tiny && fabs(c) > tol * sqrt(a * b)) {
+    if (fabs(c) >= stop * sqrt(a * b)) big = 1;
     const double zeta = (b - a) / (2.0 * c);
     const double t = (fabs(zeta) > 1e15) ? 0.5 / zeta : copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
     cs = 1.0 / sqrt(1.0 + t * t);
@@ -693,9 +701,11 @@ __device__ __forceinline__ void jac_params(double a, double b, double c, double 
     tc = t * c;
   }
 }
-__device__ __forceinline__ void jac_params(float a, float b, float c, float tol, float tiny, float& cs, float& sn,
-                                           float& tc) {
-  if (c != 0.f && a > tiny && b > tiny && fabsf(c) * rsqrtf(a) * rsqrtf(b) > tol) {
+__device__ __forceinline__ void jac_params(float a, float b, float c, float tol, float tiny, float stop, float& cs,
+                                           float& sn, float& tc, int& big) {
+  const float d = fabsf(c) * rsqrtf(a) * rsqrtf(b);
+  if (c != 0.f && a > tiny && b > tiny && d > tol) {
+    if (d >= stop) big = 1;
     const float zeta = (b - a) / (2.f * c);
     const float az = fabsf(zeta);
     const float t = (az > 1e15f) ? 0.5f / zeta : copysignf(1.f, zeta) / (az + sqrtf(fmaf(zeta, zeta, 1.f)));
@@ -719,6 +729,10 @@ __device__ __forceinline__ void jac_params(float a, float b, float c, float tol,
 //   ordering, with one block barrier per super-round and the rows read and written once per
 //   super-round.  A group sums its dot product over its 8 lanes by an xor butterfly, which
 //   leaves the same bits in all 8 lanes.
+//   Stopping: the sweeps end after the first sweep in which no pair had a relative dot product
+//   |c| / sqrt(a b) of sqrt(tol) or more.  Cyclic Jacobi converges quadratically, so the
+//   rotations of such a sweep leave dot products of order (sqrt(tol))^2 = tol: the sweep that
+//   would follow finds no pair above tol and would only confirm convergence.
 template <typename T>
 __device__ __forceinline__ T grp_sum8(T v) {
   v += __shfl_xor_sync(0xffffffffu, v, 4);
@@ -744,11 +758,12 @@ __device__ __noinline__ int hestenes_rows_grp(T* X, int m, int L, int ldx, int* 
   }
   nmax = block_max(nmax, red);
   const T tiny = nmax * (T(L) * eps) * (T(L) * eps);
+  const T stop = sqrt(tol);
   unsigned long long nrot = 0;
   for (int sweep = 0; sweep < JacobiTol<T>::sweeps; ++sweep) {
     if (threadIdx.x == 0) *flag = 0;
     __syncthreads();
-    int rotated = 0;
+    int rotated = 0, big = 0;
     for (int s = 0; s < NB - 1; ++s) {
       for (int bp = warp; bp < NB / 2; bp += nw) {
         const int bP = rr_player(bp, s, NB), bQ = rr_player(NB - 1 - bp, s, NB);
@@ -785,8 +800,8 @@ __device__ __noinline__ int hestenes_rows_grp(T* X, int m, int L, int ldx, int* 
             cp = grp_sum8(cp);
             cq = grp_sum8(cq);
             T csp = 1, snp = 0, tcp = 0, csq = 1, snq = 0, tcq = 0;
-            jac_params(lo ? np : mp, lo ? mp : np, cp, tol, tiny, csp, snp, tcp);
-            jac_params(lo ? nq : mq, lo ? mq : nq, cq, tol, tiny, csq, snq, tcq);
+            jac_params(lo ? np : mp, lo ? mp : np, cp, tol, tiny, stop, csp, snp, tcp, big);
+            jac_params(lo ? nq : mq, lo ? mq : nq, cq, tol, tiny, stop, csq, snq, tcq, big);
 #pragma unroll
             for (int e = 0; e < E8; ++e) {
               xp[e] = lo ? (csp * xp[e] - snp * yp[e]) : (snp * yp[e] + csp * xp[e]);
@@ -809,7 +824,7 @@ __device__ __noinline__ int hestenes_rows_grp(T* X, int m, int L, int ldx, int* 
           for (int e = 0; e < E8; ++e) c += xp[e] * xq[e];
           c = grp_sum8(c);
           T cs = 1, sn = 0, tc = 0;
-          jac_params(np, nq, c, tol, tiny, cs, sn, tc);
+          jac_params(np, nq, c, tol, tiny, stop, cs, sn, tc, big);
           // late sweeps rotate few pairs: skip the update when no group of the warp rotates
           if (__any_sync(0xffffffffu, sn != T(0))) {
 #pragma unroll
@@ -848,11 +863,13 @@ __device__ __noinline__ int hestenes_rows_grp(T* X, int m, int L, int ldx, int* 
       }
       __syncthreads();
     }
-    if (rotated) *flag = 1;  // benign race: every writer stores 1
+    // bit 0: some pair rotated; bit 1: some pair had a relative dot product of at least `stop`
+    const unsigned bits = __ballot_sync(0xffffffffu, rotated) ? (__ballot_sync(0xffffffffu, big) ? 3u : 1u) : 0u;
+    if (lane == 0 && bits) atomicOr(flag, (int)bits);
     __syncthreads();
     const int any = *flag;
     __syncthreads();
-    if (!any) {
+    if (!(any & 2)) {
       zero_tiny_rows(X, m, L, ldx, tiny);
       if (ctr && nrot) atomicAdd(ctr + 1, nrot);
       if (ctr && threadIdx.x == 0) { atomicAdd(ctr + 0, (unsigned long long)(sweep + 1)); atomicAdd(ctr + 2, 1ull); }
