@@ -440,7 +440,9 @@ __device__ __forceinline__ void qr_panel_reg(T* Z, int m, int j0, int pb, T* tau
 //   i = lane + 32 r), applies the panel's reflectors to it in order and stores it once.
 template <typename T, int RPL>
 __device__ __noinline__ void qr_keep_r_reg(T* Z, int m, int nc, T* R, T* taus) {
-  constexpr int QB = 8;
+  // FP32 with 256 rows: panels of four columns, whose register panel (4 x 8 values a lane)
+  // fits the environment kernels' 80 registers; eight columns spilled there
+  constexpr int QB = (RPL == 8 && sizeof(T) == 4) ? 4 : 8;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   const int steps = (m < nc) ? m : nc;
   for (int j0 = 0; j0 < steps; j0 += QB) {
@@ -502,13 +504,19 @@ __device__ __noinline__ void qr_keep_r_reg(T* Z, int m, int nc, T* R, T* taus) {
       }
     }
     __syncthreads();
-    for (int c = j0 + pb + warp; c < nc; c += nw) {
-      T* zc = Z + (size_t)c * m;
-      T z[RPL];
+    // CW trailing columns per warp at a time (c, c + nw, ...; the later ones may be absent), so
+    // that their reductions overlap; one where the columns would not fit in registers
+    constexpr int CW = (RPL <= 12) ? 2 : 1;
+    for (int c = j0 + pb + warp; c < nc; c += CW * nw) {
+      T z[CW][RPL];
 #pragma unroll
-      for (int r = 0; r < RPL; ++r) {
-        const int i = lane + 32 * r;
-        z[r] = (i < m) ? zc[i] : T(0);
+      for (int w = 0; w < CW; ++w) {
+        const int cw = c + w * nw;
+#pragma unroll
+        for (int r = 0; r < RPL; ++r) {
+          const int i = lane + 32 * r;
+          z[w][r] = (cw < nc && i < m) ? Z[(size_t)cw * m + i] : T(0);
+        }
       }
       for (int jj = 0; jj < pb; ++jj) {
         const int j = j0 + jj;
@@ -516,21 +524,31 @@ __device__ __noinline__ void qr_keep_r_reg(T* Z, int m, int nc, T* R, T* taus) {
         if (tau == T(0)) continue;
         const T* v = Z + (size_t)j * m;  // reflector: 1 at row j, v[i] below, 0 above
         T vr[RPL];
-        T sdot = 0;
+        T sdot[CW];
+#pragma unroll
+        for (int w = 0; w < CW; ++w) sdot[w] = 0;
 #pragma unroll
         for (int r = 0; r < RPL; ++r) {
           const int i = lane + 32 * r;
           vr[r] = (i > j && i < m) ? v[i] : (i == j ? T(1) : T(0));
-          sdot += vr[r] * z[r];
-        }
-        const T wj = tau * warp_sum(sdot);
 #pragma unroll
-        for (int r = 0; r < RPL; ++r) z[r] -= vr[r] * wj;
+          for (int w = 0; w < CW; ++w) sdot[w] += vr[r] * z[w][r];
+        }
+#pragma unroll
+        for (int w = 0; w < CW; ++w) {
+          const T wj = tau * warp_sum(sdot[w]);
+#pragma unroll
+          for (int r = 0; r < RPL; ++r) z[w][r] -= vr[r] * wj;
+        }
       }
 #pragma unroll
-      for (int r = 0; r < RPL; ++r) {
-        const int i = lane + 32 * r;
-        if (i < m) zc[i] = z[r];
+      for (int w = 0; w < CW; ++w) {
+        const int cw = c + w * nw;
+#pragma unroll
+        for (int r = 0; r < RPL; ++r) {
+          const int i = lane + 32 * r;
+          if (cw < nc && i < m) Z[(size_t)cw * m + i] = z[w][r];
+        }
       }
     }
     __syncthreads();
