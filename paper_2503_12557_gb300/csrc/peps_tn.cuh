@@ -946,6 +946,68 @@ struct RowWork {
   unsigned long long* ctr;
 };
 
+// Strided contraction over the whole CTA, the form every sandwich step takes:
+//   C[cm(m) + cn(n)] = sum_{k1 < K1, k2 < K2} A[am(m) + k1 sa1 + k2 sa2] B[k1 sb1 + k2 sb2 + bn(n)]
+// for m < M, n < N, where fm(m) returns (am, cm) and fn(n) returns (bn, cn).  Each thread
+// accumulates an RM x RN register tile whose rows m = ti + i tm are interleaved across threads
+// (consecutive threads read consecutive rows of A) and whose columns n = tj + j tn are shared by
+// the threads of a warp when tm >= 32 (B is read as a broadcast).  Ends with a barrier.
+struct Off2 {
+  int a, c;
+};
+template <int RM, int RN, typename T, class FM, class FN>
+__device__ __forceinline__ void blk_gemm(const T* __restrict__ A, const T* __restrict__ B, T* __restrict__ C, int M,
+                                         int N, int K1, int K2, int sa1, int sa2, int sb1, int sb2, FM fm, FN fn) {
+  const int tm = (M + RM - 1) / RM, tn = (N + RN - 1) / RN;
+  for (int t = threadIdx.x; t < tm * tn; t += blockDim.x) {
+    const int ti = t % tm, tj = t / tm;
+    int ao[RM], co[RM], bo[RN], cn[RN];
+    bool mv[RM], nv[RN];
+#pragma unroll
+    for (int i = 0; i < RM; ++i) {
+      const int m = ti + i * tm;
+      mv[i] = m < M;
+      const Off2 o = fm(mv[i] ? m : 0);
+      ao[i] = o.a;
+      co[i] = o.c;
+    }
+#pragma unroll
+    for (int j = 0; j < RN; ++j) {
+      const int n = tj + j * tn;
+      nv[j] = n < N;
+      const Off2 o = fn(nv[j] ? n : 0);
+      bo[j] = o.a;
+      cn[j] = o.c;
+    }
+    T acc[RM][RN];
+#pragma unroll
+    for (int i = 0; i < RM; ++i)
+#pragma unroll
+      for (int j = 0; j < RN; ++j) acc[i][j] = T(0);
+    for (int k1 = 0; k1 < K1; ++k1) {
+      for (int k2 = 0; k2 < K2; ++k2) {
+        const int ka = k1 * sa1 + k2 * sa2, kb = k1 * sb1 + k2 * sb2;
+        T a[RM], b[RN];
+#pragma unroll
+        for (int i = 0; i < RM; ++i) a[i] = A[ao[i] + ka];
+#pragma unroll
+        for (int j = 0; j < RN; ++j) b[j] = B[kb + bo[j]];
+#pragma unroll
+        for (int i = 0; i < RM; ++i)
+#pragma unroll
+          for (int j = 0; j < RN; ++j) acc[i][j] = mad(acc[i][j], a[i], b[j]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < RM; ++i)
+#pragma unroll
+      for (int j = 0; j < RN; ++j)
+        if (mv[i] && nv[j]) C[co[i] + cn[j]] = acc[i][j];
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------------------------------------------------------
 // One row step of the boundary MPS: Eout = normalise(truncate_chi(Eprev o T_proj[row])).
 //   Eprev, Eout: Ly environment sites (chi x D x chi each), may be global memory.
 //   Srow: the Ly local states of the applied row; lower: lower-environment orientation.
@@ -970,28 +1032,18 @@ __device__ double env_row_step(const G& g, const T* Eprev, T* Eout, const T* Tpa
     const int WS = D * D * chi + 1;    // padded row stride of W (no bank conflicts across ii)
     for (int i0 = 0; i0 < n; i0 += w.ci) {
       const int ci = (n - i0 < w.ci) ? (n - i0) : w.ci;
-      // W[ii][l][u][b] = sum_a R[i0+ii][(a,l)] E[a][u][b]
-      const int nW = ci * D * D * chi;
-      for (int o = tid; o < nW; o += NT) {
-        const int b = o % chi, u = (o / chi) % D, l = (o / (chi * D)) % D, ii = o / (chi * D * D);
-        const T* Rr = w.R + (size_t)(i0 + ii) * n + l;
-        const T* Ec = w.E + u * chi + b;
-        T s = 0;
-        for (int a = 0; a < chi; ++a) s += Rr[a * D] * Ec[a * D * chi];
-        w.W[(size_t)ii * WS + (l * D + u) * chi + b] = s;
-      }
-      __syncthreads();
-      // Z[(i0+ii, d)][(b, r)] = sum_{l,u} W[ii][l][u][b] A[l][u][r][d]; consecutive threads walk
-      // down a column of the column-major Z
-      const int nZ = ci * D * n;
-      for (int o = tid; o < nZ; o += NT) {
-        const int dd = o % D, ii = (o / D) % ci, col = o / (D * ci), b = col / D, r = col % D;
-        const T* Wr = w.W + (size_t)ii * WS + b;
-        T s = 0;
-        for (int lu = 0; lu < D * D; ++lu) s += Wr[lu * chi] * w.A[(lu * D + r) * D + dd];
-        w.Z[(size_t)col * mZ + (i0 + ii) * D + dd] = s;
-      }
-      __syncthreads();
+      // W[ii][l][u][b] = sum_a R[i0+ii][(a,l)] E[a][u][b]   (m = (u, b), n = (ii, l), k = a)
+      blk_gemm<2, 8>(w.E, w.R + (size_t)i0 * n, w.W, D * chi, ci * D, chi, 1, D * chi, 0, D, 0,
+                     [=](int m) { return Off2{m, m}; },
+                     [=](int nn) { return Off2{(nn / D) * n + nn % D, (nn / D) * WS + (nn % D) * D * chi}; });
+      // Z[(i0+ii, d)][(b, r)] = sum_{l,u} W[ii][l][u][b] A[l][u][r][d]   (m = (ii, b) with ii
+      // fastest, n = (r, d), k = (l, u)); Z is column major with column (b, r)
+      blk_gemm<4, 4>(w.W, w.A, w.Z, ci * chi, D * D, D * D, 1, chi, 0, D * D, 0,
+                     [=](int m) {
+                       const int ii = m % ci, b = m / ci;
+                       return Off2{ii * WS + b, b * D * mZ + (i0 + ii) * D};
+                     },
+                     [=](int nn) { return Off2{nn, (nn / D) * mZ + nn % D}; });
     }
     qr_keep_r<T, GeoMz<G>::value>(w.Z, mZ, n, w.R, w.sig);
     blk_copy(w.Rhist + (size_t)k * n * n, w.R, n * n);
@@ -1017,17 +1069,10 @@ __device__ double env_row_step(const G& g, const T* Eprev, T* Eout, const T* Tpa
     blk_copy(w.E, Eprev + (size_t)k * g.se, g.se);
     load_A(w.A, Tpad, g, row * Ly + k, Srow[k], lower);
     __syncthreads();
-    // P[a][u][r][c] = sum_b E[a][u][b] C[(b,r)][c]
-    const int nP = chi * D * D * chi;
-    for (int o = tid; o < nP; o += NT) {
-      const int c = o % chi, r = (o / chi) % D, u = (o / (chi * D)) % D, a = o / (chi * D * D);
-      const T* Er = w.E + (a * D + u) * chi;
-      const T* Cc = w.C + r * chi + c;
-      T s = 0;
-      for (int b = 0; b < chi; ++b) s += Er[b] * Cc[b * D * chi];
-      P[o] = s;
-    }
-    __syncthreads();
+    // P[a][u][r][c] = sum_b E[a][u][b] C[(b,r)][c]   (m = (r, c), n = (a, u), k = b)
+    blk_gemm<2, 8>(w.C, w.E, P, D * chi, chi * D, chi, 1, D * chi, 0, 1, 0,
+                   [=](int m) { return Off2{m, m}; },
+                   [=](int nn) { return Off2{nn * chi, nn * D * chi}; });
     if (k == 0) {
       // first site: its left bond is trivial, keep only row (a,l) = (0,0) of Y = M_0 C_0
       for (int o = tid; o < g.se; o += NT) {
@@ -1045,16 +1090,10 @@ __device__ double env_row_step(const G& g, const T* Eprev, T* Eout, const T* Tpa
       __syncthreads();
       break;
     }
-    // Y[(a,l)][(d,c)] = sum_{u,r} P[a][u][r][c] A[l][u][r][d]
-    const int nY = n * Lr;
-    for (int o = tid; o < nY; o += NT) {
-      const int c = o % chi, dd = (o / chi) % D, l = (o / Lr) % D, a = o / (Lr * D);
-      const T* Pr = P + (size_t)a * D * D * chi + c;
-      const T* Ar = w.A + (size_t)l * D * D * D + dd;
-      T s = 0;
-      for (int ur = 0; ur < D * D; ++ur) s += Pr[ur * chi] * Ar[ur * D];
-      Y[(size_t)(o / Lr) * LY + o % Lr] = s;
-    }
+    // Y[(a,l)][(d,c)] = sum_{u,r} P[a][u][r][c] A[l][u][r][d]   (m = (a, c), n = (l, d), k = (u, r))
+    blk_gemm<4, 4>(P, w.A, Y, chi * chi, D * D, D * D, 1, chi, 0, D, 0,
+                   [=](int m) { return Off2{(m / chi) * D * D * chi + m % chi, (m / chi) * D * LY + m % chi}; },
+                   [=](int nn) { return Off2{(nn / D) * D * D * D + nn % D, (nn / D) * LY + (nn % D) * chi}; });
     // R_{k-1} from the left pass
     blk_copy(w.R, w.Rhist + (size_t)(k - 1) * n * n, n * n);
     __syncthreads();
@@ -1229,67 +1268,6 @@ __device__ double env_first_row(const G& g, T* Eout, const T* Tpad, int row, con
 }
 
 // ------------------------------------------------------------------------------------------
-// Strided contraction over the whole CTA, the form every sandwich step takes:
-//   C[cm(m) + cn(n)] = sum_{k1 < K1, k2 < K2} A[am(m) + k1 sa1 + k2 sa2] B[k1 sb1 + k2 sb2 + bn(n)]
-// for m < M, n < N, where fm(m) returns (am, cm) and fn(n) returns (bn, cn).  Each thread
-// accumulates an RM x RN register tile whose rows m = ti + i tm are interleaved across threads
-// (consecutive threads read consecutive rows of A) and whose columns n = tj + j tn are shared by
-// the threads of a warp when tm >= 32 (B is read as a broadcast).  Ends with a barrier.
-struct Off2 {
-  int a, c;
-};
-template <int RM, int RN, typename T, class FM, class FN>
-__device__ __forceinline__ void blk_gemm(const T* __restrict__ A, const T* __restrict__ B, T* __restrict__ C, int M,
-                                         int N, int K1, int K2, int sa1, int sa2, int sb1, int sb2, FM fm, FN fn) {
-  const int tm = (M + RM - 1) / RM, tn = (N + RN - 1) / RN;
-  for (int t = threadIdx.x; t < tm * tn; t += blockDim.x) {
-    const int ti = t % tm, tj = t / tm;
-    int ao[RM], co[RM], bo[RN], cn[RN];
-    bool mv[RM], nv[RN];
-#pragma unroll
-    for (int i = 0; i < RM; ++i) {
-      const int m = ti + i * tm;
-      mv[i] = m < M;
-      const Off2 o = fm(mv[i] ? m : 0);
-      ao[i] = o.a;
-      co[i] = o.c;
-    }
-#pragma unroll
-    for (int j = 0; j < RN; ++j) {
-      const int n = tj + j * tn;
-      nv[j] = n < N;
-      const Off2 o = fn(nv[j] ? n : 0);
-      bo[j] = o.a;
-      cn[j] = o.c;
-    }
-    T acc[RM][RN];
-#pragma unroll
-    for (int i = 0; i < RM; ++i)
-#pragma unroll
-      for (int j = 0; j < RN; ++j) acc[i][j] = T(0);
-    for (int k1 = 0; k1 < K1; ++k1) {
-      for (int k2 = 0; k2 < K2; ++k2) {
-        const int ka = k1 * sa1 + k2 * sa2, kb = k1 * sb1 + k2 * sb2;
-        T a[RM], b[RN];
-#pragma unroll
-        for (int i = 0; i < RM; ++i) a[i] = A[ao[i] + ka];
-#pragma unroll
-        for (int j = 0; j < RN; ++j) b[j] = B[kb + bo[j]];
-#pragma unroll
-        for (int i = 0; i < RM; ++i)
-#pragma unroll
-          for (int j = 0; j < RN; ++j) acc[i][j] = mad(acc[i][j], a[i], b[j]);
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < RM; ++i)
-#pragma unroll
-      for (int j = 0; j < RN; ++j)
-        if (mv[i] && nv[j]) C[co[i] + cn[j]] = acc[i][j];
-  }
-  __syncthreads();
-}
-
 // ------------------------------------------------------------------------------------------
 // One-row sandwich partials.  L[a][l][b] -> L'[x][r][z] over one column with eu[a][u][x],
 // A[l][u][r][d], el[b][d][z].  t1, t2: chi*chi*D*D each.  The intermediates are laid out so that
