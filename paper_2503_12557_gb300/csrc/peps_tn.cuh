@@ -1097,15 +1097,12 @@ __device__ double env_row_step(const G& g, const T* Eprev, T* Eout, const T* Tpa
     // R_{k-1} from the left pass
     blk_copy(w.R, w.Rhist + (size_t)(k - 1) * n * n, n * n);
     __syncthreads();
-    // X = R_{k-1} Y  (R upper triangular), padded to mX rows
-    for (int o = tid; o < mX * Lr; o += NT) {
-      const int q = o % Lr, i = o / Lr;
-      T s = 0;
-      if (i < n)
-        for (int j = i; j < n; ++j) s += w.R[(size_t)i * n + j] * Y[(size_t)j * LY + q];
-      X[(size_t)i * LX + q] = s;
-    }
-    __syncthreads();
+    // X = R_{k-1} Y (m = q, n = i, k = j), padded to mX rows.  R is stored with explicit zeros
+    // below the diagonal, so the full sum adds exact zeros before the j >= i terms.
+    if (mX > n)
+      for (int q = tid; q < Lr; q += NT) X[(size_t)n * LX + q] = T(0);
+    blk_gemm<2, 8>(Y, w.R, X, Lr, n, n, 1, LY, 0, 1, 0, [=](int m) { return Off2{m, m}; },
+                   [=](int i) { return Off2{i * n, i * LX}; });
     // norms, singular values and the selection in the real type (the QR's taus, in the same
     // buffer, are no longer needed)
     using RT = typename Scal<T>::R;
