@@ -1267,23 +1267,27 @@ __device__ double env_first_row(const G& g, T* Eout, const T* Tpad, int row, con
 // ------------------------------------------------------------------------------------------
 // ------------------------------------------------------------------------------------------
 // One-row sandwich partials.  L[a][l][b] -> L'[x][r][z] over one column with eu[a][u][x],
-// A[l][u][r][d], el[b][d][z].  t1, t2: chi*chi*D*D each.  The intermediates are laid out so that
-// the index that varies across threads is contiguous in the operand it is read from.
+// A[l][u][r][d], el[b][d][z].  t1: chi*chi*D*D, t2: D*D*chi*(chi+1) elements.  The
+// intermediates are laid out so that the index that varies across threads is contiguous in the
+// operand it is read from; t2's (x, r) rows are padded to D (chi + 1), so that the two column
+// groups a warp reads in the last product (16 rows per group at chi = 16) fall in different
+// shared-memory banks.
 template <typename T, typename G>
 __device__ void absorb1(const G& g, const T* L, const T* eu, const T* A, const T* el, T* t1, T* t2, T* out) {
   const int chi = g.chi, D = g.D;
+  const int PS = D * chi + D;  // padded (x, r) row stride of t2
   // t1[u][l][x][b] = sum_a L[a][l][b] eu[a][u][x]        (m = (l, b), n = (u, x), k = a)
   blk_gemm<2, 8>(L, eu, t1, D * chi, D * chi, chi, 1, D * chi, 0, D * chi, 0,
                  [=](int m) { return Off2{m, (m / chi) * chi * chi + m % chi}; },
                  [=](int n) { return Off2{n, (n / chi) * D * chi * chi + (n % chi) * chi}; });
   // t2[x][r][d][b] = sum_{l,u} t1[u][l][x][b] A[l][u][r][d]   (m = (x, b), n = (r, d), k = (l, u))
   blk_gemm<4, 4>(t1, A, t2, chi * chi, D * D, D, D, chi * chi, D * chi * chi, D * D * D, D * D,
-                 [=](int m) { return Off2{m, (m / chi) * D * D * chi + m % chi}; },
-                 [=](int n) { return Off2{n, n * chi}; });
+                 [=](int m) { return Off2{m, (m / chi) * D * PS + m % chi}; },
+                 [=](int n) { return Off2{n, (n / D) * PS + (n % D) * chi}; });
   // out[x][r][z] = sum_{b,d} el[b][d][z] t2[x][r][d][b]      (m = z, n = (x, r), k = (b, d))
   blk_gemm<1, 4>(el, t2, out, chi, chi * D, chi, D, D * chi, chi, 1, chi,
                  [=](int m) { return Off2{m, m}; },
-                 [=](int n) { return Off2{n * D * chi, n * chi}; });
+                 [=](int n) { return Off2{n * PS, n * chi}; });
 }
 
 // R[x][r][z] -> R'[a][l][b] = sum eu[a][u][x] A[l][u][r][d] el[b][d][z] R[x][r][z].
@@ -1308,22 +1312,24 @@ __device__ void absorb1_right(const G& g, const T* R, const T* eu, const T* A, c
 // Site environment of the one-row sandwich: env[l][u][r][d] = sum L[a][l][b] eu[a][u][x]
 // el[b][d][z] R[x][r][z]  (= d psi_x / d A[l][u][r][d]).  elT[z][b][d] = el[b][d][z] (the lower
 // environment site read transposed, so that the contraction over z has a contiguous operand).
-// t1: chi^2 D^2, t2: chi^2 D^2.
+// t1: D^2 chi (chi+1), its (u, l) rows padded to chi (chi + 1); t2: chi^2 D^2.
 template <typename T, typename G>
 __device__ void site_env1(const G& g, const T* L, const T* eu, const T* elT, const T* R, T* t1, T* t2, T* env) {
   const int chi = g.chi, D = g.D;
-  // t1[u][l][x][b] = sum_a L[a][l][b] eu[a][u][x]   (as in absorb1)
+  const int S1 = chi * chi + chi;  // padded (u, l) row stride of t1
+  // t1[u][l][x][b] = sum_a L[a][l][b] eu[a][u][x]   (as in absorb1, rows padded)
   blk_gemm<2, 8>(L, eu, t1, D * chi, D * chi, chi, 1, D * chi, 0, D * chi, 0,
-                 [=](int m) { return Off2{m, (m / chi) * chi * chi + m % chi}; },
-                 [=](int n) { return Off2{n, (n / chi) * D * chi * chi + (n % chi) * chi}; });
+                 [=](int m) { return Off2{m, (m / chi) * S1 + m % chi}; },
+                 [=](int n) { return Off2{n, (n / chi) * D * S1 + (n % chi) * chi}; });
   // t4[b][x][r][d] = sum_z elT[z][b][d] R[x][r][z]   (m = (b, d), n = (x, r), k = z)
   blk_gemm<2, 8>(elT, R, t2, chi * D, chi * D, chi, 1, chi * D, 0, 1, 0,
                  [=](int m) { return Off2{m, (m / D) * chi * D * D + m % D}; },
                  [=](int n) { return Off2{n * chi, n * D}; });
-  // env[l][u][r][d] = sum_{b,x} t4[b][x][r][d] t1[u][l][x][b]   (m = (r, d), n = (l, u), k = (b, x))
+  // env[l][u][r][d] = sum_{b,x} t4[b][x][r][d] t1[u][l][x][b]   (m = (r, d), n = (u, l) with l
+  // fastest, so that the two column groups of a warp read t1 rows one padded stride apart)
   blk_gemm<1, 1>(t2, t1, env, D * D, D * D, chi, chi, chi * D * D, D * D, 1, chi,
                  [=](int m) { return Off2{m, m}; },
-                 [=](int n) { return Off2{(n % D) * D * chi * chi + (n / D) * chi * chi, n * D * D}; });
+                 [=](int n) { return Off2{(n / D) * D * S1 + (n % D) * S1, ((n % D) * D + n / D) * D * D}; });
 }
 
 template <typename T>
@@ -1397,11 +1403,12 @@ __device__ void absorb2(const G& g, const T* L2, const T* eu, const T* A1, const
     blk_gemm<4, 4>(t2, A2, t1, cc * D, D * D, D, D, D * cc * D, cc * D, D * D * D, D * D,
                    [=](int m) { return Off2{m, m}; },
                    [=](int n) { return Off2{n, n * cc * D}; });
-    // out[x0+xx][r1][r2][z] = sum_{b,d} el[b][d][z] t3[r2][d][b][xx][r1]   (m = z, n = (xx, r1, r2))
+    // out[x0+xx][r1][r2][z] = sum_{b,d} el[b][d][z] t3[r2][d][b][xx][r1]   (m = z, n = (xx, r2, r1)
+    // with r1 fastest: the two column groups of a warp then read adjacent words of t3)
     blk_gemm<1, 4>(el, t1, out, chi, c * D * D, chi, D, D * chi, chi, c * D, cc * D,
                    [=](int m) { return Off2{m, m}; },
                    [=](int n) {
-                     const int xx = n / (D * D), r1 = (n / D) % D, r2 = n % D;
+                     const int xx = n / (D * D), r2 = (n / D) % D, r1 = n % D;
                      return Off2{r2 * D * cc * D + xx * D + r1, (((x0 + xx) * D + r1) * D + r2) * chi};
                    });
   }
