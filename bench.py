@@ -177,9 +177,9 @@ def _peaks():
 # DRAM bytes (read + write) of one sampler call of 2 sweeps in FP32 (every kernel of the split
 # sweep), from an ncu capture of 304 chains, scaled by the chains processed (each chain's
 # environment rows and partials are its own traffic); None until such a capture of the current
-# kernels exists.  profiles/sampler_split_heis8x8_D4_chi16_ns304.md: 1.227 GB per call of 2 sweeps
-# over 304 chains (k_env one-side pass 0.23 GB, k_sweep_moves 0.68 GB, k_env_row 0.32 GB).
-_SAMPLER_CAPTURE = {"bytes": 1.227e9, "chains": 304, "sweeps": 2}
+# kernels exists.  profiles/sampler_split_heis8x8_D4_chi16_ns304.md: 1.235 GB per call of 2 sweeps
+# over 304 chains (k_env one-side pass 0.23 GB, k_sweep_moves 0.69 GB, k_env_row 0.32 GB).
+_SAMPLER_CAPTURE = {"bytes": 1.235e9, "chains": 304, "sweeps": 2}
 
 
 def _measured_traffic(kernel, ns, sweeps, prec):
