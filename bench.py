@@ -52,10 +52,11 @@ def _args():
     return ap.parse_args()
 
 
-def _config(w, ns, prec, sweeps):
+def _config(w, ns, sweeps):
+    # the same for both arms; each line's "dtype" gives the arithmetic it ran in
     return {"workload": f"{w['Lx']}x{w['Ly']} open Heisenberg J=1, D={w['D']}, chi={w['chi']}, "
                         f"N_s={ns} Metropolis exchange chains ({WORKLOAD})",
-            "Lx": w["Lx"], "Ly": w["Ly"], "D": w["D"], "chi": w["chi"], "ns": ns, "precision": prec,
+            "Lx": w["Lx"], "Ly": w["Ly"], "D": w["D"], "chi": w["chi"], "ns": ns,
             "sweeps_per_step": sweeps, "minsr": {"lambda": w["lam"], "rcond": w["rcond"], "tau": w["tau"]},
             "l2": "inputs larger than L2 (environment store and O exceed 129 MB)"}
 
@@ -107,7 +108,7 @@ def run_reference(a):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "samples/s", "n_gpus": a.gpus,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": _config(w, ns, "fp64", a.sweeps),
+            "config": _config(w, ns, a.sweeps),
             "cpu_baseline": {"value": v, "unit": "samples/s", "cores": 1, "kind": "oracle",
                              "sample": f"each step: {nsamp} chains of the workload ({a.sweeps} sweeps + psi/E_loc/O "
                                        f"+ MinSR), one host core"},
@@ -335,7 +336,7 @@ def run_gpu(a):
     line = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if prec == P.PREC_FP32 else "f64", "data": "synthetic",
-            "config": _config(w, ns, a.prec, a.sweeps), "step_ms": step_ms, "minsr_step_s": minsr_s,
+            "config": _config(w, ns, a.sweeps), "step_ms": step_ms, "minsr_step_s": minsr_s,
             "minsr": {"gram": {0: "FP64 CUDA cores", 1: "split-BF16 tcgen05",
                                2: "float-float pairs on the FP32 pipes"}[gram],
                       "solve": "FP64 Cholesky",
