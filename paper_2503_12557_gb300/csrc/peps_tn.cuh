@@ -436,8 +436,8 @@ __device__ __forceinline__ void qr_panel_reg(T* Z, int m, int j0, int pb, T* tau
 //   Panel (warp 0): after column j's reflector is formed, its products with every remaining
 //   panel column are taken in one pass over the rows and summed over the warp together, so a
 //   panel column costs two warp reductions instead of one per remaining column.
-//   Trailing update (all warps): a warp loads one trailing column into registers (element
-//   i = lane + 32 r), applies the panel's reflectors to it in order and stores it once.
+//   Trailing update (all warps): a warp loads CW trailing columns into registers (element
+//   i = lane + 32 r), applies the panel's reflectors to each in order and stores them once.
 template <typename T, int RPL>
 __device__ __noinline__ void qr_keep_r_reg(T* Z, int m, int nc, T* R, T* taus) {
   // FP32 with 256 rows: panels of four columns, whose register panel (4 x 8 values a lane)
