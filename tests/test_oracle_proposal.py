@@ -1,7 +1,8 @@
-"""Pins of the learned-proposal oracle (no counterpart in the paper, so parity against the paper
-is unpinned): the convolution against a brute-force loop, the loss gradient against central
-finite differences, Adam's first step against its closed form, and the network move's exact
-transition matrix against detailed balance."""
+"""Pins of the learned-proposal oracle (no counterpart in the paper, so there is no printed
+value to pin it to; the pins are mathematical): the convolution against a brute-force loop, the
+loss gradient against central finite differences, Adam's first step against its closed form,
+the network move's exact transition matrix against detailed balance, and the chain step
+(learned_step) against that matrix's rows, with two planted mistakes that must fail."""
 import math
 
 import numpy as np
@@ -94,3 +95,102 @@ def test_log_q_is_a_normalised_distribution():
         s = [(b >> (3 - i)) & 1 for i in range(4)]
         tot += math.exp(Q.log_q(l, s))
     assert abs(tot - 1.0) < 1e-13
+
+
+# ---- the chain step itself (learned_step = propose + log q both ways + mh_accept), not only the
+# separately written transition matrix: many independent one-step moves from one state must
+# reproduce that state's row of the exact kernel, and two planted mistakes must not
+
+def _tiny_setup():
+    lat = Lattice(2, 2, 2, 2)
+    th = peps_random(lat, 9, scale=0.8, bias=0.3)
+    psi = exact.state_vector(th, lat)
+    w = proposal_init(11, C=4, scale=2.0)
+    return lat, th, psi, w
+
+
+def _empirical_row(lat, th, psi, w, a, nchain, step_fn):
+    Sall = exact.index_configs(lat.nsites, 2)
+    S = Sall[a]
+    lpsi = math.log(abs(psi[a]))
+    logamp = lambda t, s: math.log(abs(psi[exact.config_index(s, 2)]))  # noqa: E731
+    counts = np.zeros(len(Sall))
+    for c in range(nchain):
+        Sn, _, _ = step_fn(th, w, S.copy(), lpsi, lat, 2, 101, 3, c, logamp, C=4)
+        counts[exact.config_index(Sn, 2)] += 1
+    return counts
+
+
+def _chi2(counts, p):
+    # Pearson chi^2 over the bins whose expected count is at least 5 (the rest pooled)
+    n = counts.sum()
+    e = n * p
+    big = e >= 5
+    obs = np.append(counts[big], counts[~big].sum())
+    exp = np.append(e[big], e[~big].sum())
+    keep = exp > 0
+    obs, exp = obs[keep], exp[keep]
+    df = len(obs) - 1
+    return float(np.sum((obs - exp) ** 2 / exp)), df
+
+
+def _chi2_ok(counts, p):
+    x2, df = _chi2(counts, p)
+    return x2 <= df + 5.0 * math.sqrt(2.0 * df), x2, df
+
+
+def test_learned_step_reproduces_exact_kernel_rows():
+    lat, th, psi, w = _tiny_setup()
+    K = Q.network_kernel_exact(w, psi, lat, C=4)
+    for a in (3, 6, 12):
+        counts = _empirical_row(lat, th, psi, w, a, 3000, Q.learned_step)
+        ok, x2, df = _chi2_ok(counts, K[a])
+        assert ok, (a, x2, df)
+
+
+def test_learned_step_planted_mistakes_fail():
+    # (i) the forward and backward proposal log-probabilities swapped in the MH ratio;
+    # (ii) the proposal's Bernoulli draw inverted (s' = 1 with probability 1 - sigmoid(l)).
+    # Each gives a valid-looking chain with the wrong transition probabilities.
+    lat, th, psi, w = _tiny_setup()
+    K = Q.network_kernel_exact(w, psi, lat, C=4)
+    a = 6
+
+    def swapped(theta, w_, S, logpsi, lat_, chi, seed, step, chain, logamp, C=16):
+        Sp, lq_f = Q.propose(w_, S, lat_.Lx, lat_.Ly, seed, step, chain, C)
+        lq_b = Q.log_q(Q.forward(w_, Sp, lat_.Lx, lat_.Ly, C), S)
+        lnew = logamp(theta, Sp)
+        u = Q.uniform53((lat_.nsites, step, chain, 1), Q.key_of_seed(seed))
+        if Q.mh_accept(lnew, logpsi, lq_b, lq_f, u):  # planted: lq_fwd <-> lq_bwd
+            return Sp, lnew, True
+        return S, logpsi, False
+
+    def inverted(theta, w_, S, logpsi, lat_, chi, seed, step, chain, logamp, C=16):
+        l = Q.forward(w_, S, lat_.Lx, lat_.Ly, C).ravel()
+        key = Q.key_of_seed(seed)
+        p = Q.sigmoid(l)
+        Sp = np.array([1 if Q.uniform53((i, step, chain, 1), key) >= p[i] else 0 for i in range(lat_.nsites)],
+                      dtype=np.uint8)  # planted: Bernoulli(1 - p)
+        lq_f = Q.log_q(l.reshape(lat_.Lx, lat_.Ly), Sp)
+        lq_b = Q.log_q(Q.forward(w_, Sp, lat_.Lx, lat_.Ly, C), S)
+        lnew = logamp(theta, Sp)
+        u = Q.uniform53((lat_.nsites, step, chain, 1), key)
+        if Q.mh_accept(lnew, logpsi, lq_f, lq_b, u):
+            return Sp, lnew, True
+        return S, logpsi, False
+
+    for fn in (swapped, inverted):
+        counts = _empirical_row(lat, th, psi, w, a, 3000, fn)
+        ok, x2, df = _chi2_ok(counts, K[a])
+        assert not ok, (fn.__name__, x2, df)
+
+
+def test_mh_accept_boundaries():
+    # accept iff u < min(1, exp(2 (ln|psi'| - ln|psi|) + log q(S|S') - log q(S'|S)))
+    r = 2 * (0.1 - 0.4) + (-1.0) - (-1.5)  # ln of the ratio: -0.1
+    assert Q.mh_accept(0.1, 0.4, -1.5, -1.0, math.exp(r) - 1e-12)
+    assert not Q.mh_accept(0.1, 0.4, -1.5, -1.0, math.exp(r) + 1e-12)
+    assert not Q.mh_accept(0.1, 0.4, -1.0, -1.5, math.exp(r) - 1e-12)  # the swapped order rejects
+    assert Q.mh_accept(5.0, 0.0, 0.0, 0.0, 0.999999)  # ratio above 1: always accepted
+    assert not Q.mh_accept(float("-inf"), 0.0, 0.0, 0.0, 0.0)  # psi' = 0
+    assert not Q.mh_accept(float("nan"), 0.0, 0.0, 0.0, 0.0)
