@@ -324,12 +324,15 @@ peps_status peps_sample_learned(peps_handle* h, int C, int wprec, const void* w_
  *   process exits.  cfg gives the lattice, chi and precision (max_samples is ignored);
  *   theta_dev: N_p doubles; S_dev: Ns x (Lx*Ly) uint8; logabs_dev, phase_dev: Ns doubles;
  *   status_dev: Ns int32 or NULL.  All device memory owned by the caller.
- *   Returns PEPS_E_CAPACITY, before any launch, when the parameters, environments and work
- *   buffers of this lattice and Ns do not fit in the 32 MiB (about 8 KiB per sample at
- *   4x4, D=2, chi=4 in FP64; larger problems need a handle).
- *   The first call on a device looks up the array's device address with that device current;
- *   make that first call before any stream capture.  All calls share the array and leave their
- *   contents in it: calls that may overlap on the GPU race and must be serialised. */
+ *   Returns PEPS_E_CAPACITY, before any launch, when the parameters, environments and one CTA's
+ *   work buffers of this lattice and Ns do not fit in the 32 MiB (about 8 KiB per sample at
+ *   4x4, D=2, chi=4 in FP64; larger problems need a handle).  Where two CTAs per SM do not fit,
+ *   fewer CTAs share the samples: the same results, less concurrency.
+ *   Every call made outside a stream capture looks up the array's device address with the
+ *   current device (a cudaDeviceReset moves it); a call made during a capture uses the address
+ *   of the last lookup, so make a first call on each device before any stream capture.  All
+ *   calls share the array and leave their contents in it: calls that may overlap on the GPU
+ *   race and must be serialised. */
 peps_status peps_amplitudes_noalloc(const peps_config* cfg, const double* theta_dev, const uint8_t* S_dev, int Ns,
                                     double* logabs_dev, double* phase_dev, int32_t* status_dev, void* stream);
 

@@ -9,10 +9,13 @@
 // kNoAllocBytes (32 MiB) that the library reserves on every GPU it is loaded on, for the life
 // of the process.  The caller passes only its inputs and outputs.
 //
-// The first call on a device looks up that device's address of the array (with the device
-// current) and caches it; make that first call before any stream capture.  Every call shares
-// the one array and leaves its last contents there: calls that may overlap on the GPU (two
-// streams, two host threads) race on it and must be serialised by the caller.
+// Every call made outside a stream capture looks up that device's address of the array (with
+// the device current) and keeps it; a call made while the stream is being captured uses the
+// address of the last such lookup, so make a first call before any stream capture.  When the
+// problem does not fit with two CTAs per SM, fewer CTAs share the work (same results, less
+// concurrency).  Every call shares the one array and leaves its last contents there: calls
+// that may overlap on the GPU (two streams, two host threads) race on it and must be
+// serialised by the caller.
 #include <mutex>
 #include <utility>
 
@@ -27,7 +30,7 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 constexpr int kMaxDevices = 64;
 void* g_scratch_addr[kMaxDevices];
 cudaError_t g_scratch_err[kMaxDevices];
-std::once_flag g_scratch_once[kMaxDevices];
+std::mutex g_scratch_mu;
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
@@ -91,9 +94,7 @@ peps_status run(const peps_config& c, const double* theta, const uint8_t* S, int
   int dev = 0, nsm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return PEPS_E_CUDA;
-  const int grid = (2 * nsm < Ns) ? 2 * nsm : Ns;
-  const size_t arena = (size_t)grid * (pe.gstride > pr.gstride ? pe.gstride : pr.gstride);
-  // carve the scratch array
+  // carve the scratch array: the fixed buffers first, then one work-buffer slice per CTA
   size_t off = 0;
   auto take = [&](size_t bytes) { char* p = base + off; off += align256(bytes); return p; };
   long long* site_off = (long long*)take(sizeof(long long) * (N + 1));
@@ -103,7 +104,15 @@ peps_status run(const peps_config& c, const double* theta, const uint8_t* S, int
   double* rowout = (double*)take(sizeof(double) * 4 * (size_t)Ns * g.Lx);
   float* wdisc = (float*)take(sizeof(float) * (size_t)Ns);
   int* st_own = (int*)take(sizeof(int) * (size_t)Ns);
-  char* arena_base = take(arena);
+  if (off > kNoAllocBytes) return PEPS_E_CAPACITY;
+  // the kernels loop over samples with a grid stride, so fewer CTAs give the same results;
+  // take two per SM where the slices fit, else as many as fit, and give up below one
+  const size_t stride = pe.gstride > pr.gstride ? pe.gstride : pr.gstride;
+  const size_t fit = (kNoAllocBytes - off) / (stride > 0 ? stride : 1);
+  int grid = (2 * nsm < Ns) ? 2 * nsm : Ns;
+  if ((size_t)grid > fit) grid = (int)fit;
+  if (grid < 1) return PEPS_E_CAPACITY;
+  char* arena_base = take((size_t)grid * stride);
   if (off > kNoAllocBytes) return PEPS_E_CAPACITY;
   pe.gbase = pr.gbase = arena_base;
   int* st = status ? (int*)status : st_own;
@@ -138,12 +147,23 @@ extern "C" peps_status peps_amplitudes_noalloc(const peps_config* cfg, const dou
   if (Ns == 0) return PEPS_OK;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PEPS_E_CUDA;
-  std::call_once(g_scratch_once[dev], [dev]() {
-    g_scratch_err[dev] = cudaGetSymbolAddress(&g_scratch_addr[dev], g_noalloc_scratch);
-  });
-  if (g_scratch_err[dev] != cudaSuccess || !g_scratch_addr[dev]) return PEPS_E_CUDA;
   cudaStream_t s = (cudaStream_t)stream;
-  char* base = (char*)g_scratch_addr[dev];
+  // the array's device address: looked up with this device current on every call made outside
+  // a stream capture (a cudaDeviceReset reloads the module and moves the array), and taken from
+  // the last lookup while the stream is being captured (no runtime query may run then)
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return PEPS_E_CUDA;
+  void* addr = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (cap == cudaStreamCaptureStatusNone) {
+      g_scratch_err[dev] = cudaGetSymbolAddress(&g_scratch_addr[dev], g_noalloc_scratch);
+    }
+    if (g_scratch_err[dev] != cudaSuccess) g_scratch_addr[dev] = nullptr;
+    addr = g_scratch_addr[dev];
+  }
+  if (!addr) return PEPS_E_CUDA;
+  char* base = (char*)addr;
   return (c.prec == PEPS_PREC_FP64) ? run<double>(c, theta_dev, S_dev, Ns, logabs_dev, phase_dev, status_dev, s, base)
                                     : run<float>(c, theta_dev, S_dev, Ns, logabs_dev, phase_dev, status_dev, s, base);
 }

@@ -344,13 +344,15 @@ WORKLOADS = {
     # 4x4 open Heisenberg, D=2, chi=4 (exact), uniform Sz=0 configurations, one MinSR step
     "heis4x4_D2_chi4": dict(Lx=4, Ly=4, d=2, D=2, chi=4, ns=256, init=dict(kind="normal", scale=1.0),
                              seed_theta=1001, seed_S=2001, lam=1e-4, rcond=0.0, tau=0.05),
-    # 8x8 open Heisenberg, D=4, chi=16, biased Gaussian tensors, Metropolis exchange chains
+    # 8x8 open Heisenberg, D=4, chi=16, biased Gaussian tensors with the algebraically decaying
+    # virtual legs of Eq. (A_alpha) (alpha = 1.5, the paper's initialisation for optimisation
+    # runs), Metropolis exchange chains
     "heis8x8_D4_chi16": dict(Lx=8, Ly=8, d=2, D=4, chi=16, ns=4096,
-                              init=dict(kind="normal", scale=0.5, bias=1.0),
+                              init=dict(kind="normal", scale=0.5, bias=1.0, alpha=1.5),
                               seed_theta=1002, seed_S=2002, seed_chain=3002, lam=1e-4, rcond=0.0, tau=0.05),
-    # 12x12 Rydberg array, D=4, chi=24
+    # 12x12 Rydberg array, D=4, chi=24, tensors drawn as for the 8x8 Heisenberg workload
     "rydberg12x12_D4_chi24": dict(Lx=12, Ly=12, d=2, D=4, chi=24, ns=16384,
-                                   init=dict(kind="normal", scale=0.5, bias=1.0),
+                                   init=dict(kind="normal", scale=0.5, bias=1.0, alpha=1.5),
                                    seed_theta=1004, seed_S=2004, seed_chain=3004, lam=1e-4, rcond=0.0, tau=0.05),
 }
 

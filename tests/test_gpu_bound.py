@@ -107,7 +107,7 @@ def test_bound_fp32_close(P):
     ref = bound.evaluate_bound(th, S, lat, 9, H, 2)
     dl = np.abs(res["logabs"] - ref["logabs"])
     print(f"fp32 bound |d ln psi_i| max {dl.max():.2e}")
-    assert dl.max() < 1e-4
+    assert dl.max() <= 1e-5
     e = res["eloc"][:, 0]
     assert abs(np.mean(e) - np.mean(ref["eloc"].real)) / lat.nsites < 1e-4
 
@@ -183,7 +183,8 @@ def test_bound_complex64(P):
     H = I.j1j2_chiral(lat)
     res = _run(P, lat, 3, th, S, H, 2, prec=1, cplx=True)
     ref = bound.evaluate_bound(th, S, lat, 3, H, 2)
-    assert np.max(np.abs(res["logabs"] - ref["logabs"])) < 1e-4
+    print(f"complex64 bound |d ln psi_i| max {np.max(np.abs(res['logabs'] - ref['logabs'])):.2e}")
+    assert np.max(np.abs(res["logabs"] - ref["logabs"])) <= 1e-5
     e = res["eloc"][:, 0] + 1j * res["eloc"][:, 1]
     assert np.max(np.abs(e - ref["eloc"]) / np.maximum(1.0, np.abs(ref["eloc"]))) < 1e-3
 

@@ -97,7 +97,7 @@ def test_complex64_reduced_precision(P):
     ref = energy.evaluate(th, S, lat, 9, H=H, want_O=False)
     dl = np.abs(res["logabs"].cpu().numpy() - ref["logabs"])
     print(f"complex64 |d ln psi| max {dl.max():.2e} median {np.median(dl):.2e}")
-    assert dl.max() < 1e-4
+    assert dl.max() <= 1e-5
     el = res["eloc"].cpu().numpy()
     e = el[:, 0] + 1j * el[:, 1]
     assert abs(np.mean(e) - np.mean(ref["eloc"])) / lat.nsites < 1e-4

@@ -56,6 +56,28 @@ def test_noalloc_matches_handle_entry_point_twice(prec, tol):
     h.close()
 
 
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 1e-5)])
+def test_noalloc_many_samples_per_cta(prec, tol):
+    # more samples than two CTAs per SM: every CTA reuses its slice of the array for several
+    # samples in turn, the case where work buffers left over from an earlier sample would show
+    peps, f = _noalloc_fn()
+    lat = I.Lattice(4, 4, 2, 2)
+    chi = 3
+    theta = torch.as_tensor(I.peps_random(lat, 1003, scale=0.5, bias=1.0)).cuda()
+    h = peps.PEPS(lat.Lx, lat.Ly, lat.d, lat.D, chi, prec=prec, max_samples=1000)
+    h.set_params(theta)
+    for seed in (2003, 2004):
+        S = torch.as_tensor(I.configs_uniform_sz0(lat, 1000, seed)).cuda()
+        rc, la, ph, st = _call(peps, f, lat, chi, prec, theta, S)
+        assert rc == 0, f"status {rc}"
+        la_ref, ph_ref, st_ref = h.amplitudes(S)
+        torch.cuda.synchronize()
+        assert np.max(np.abs(la.cpu().numpy() - la_ref.cpu().numpy())) <= tol
+        assert np.array_equal(ph.cpu().numpy(), ph_ref.cpu().numpy())
+        assert np.array_equal(st.cpu().numpy(), st_ref.cpu().numpy())
+    h.close()
+
+
 def test_noalloc_rejects_problems_beyond_its_scratch():
     peps, f = _noalloc_fn()
     lat = I.Lattice(8, 8, 2, 4)
