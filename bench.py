@@ -39,11 +39,13 @@ def _args():
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--ns", type=int, default=None)
     ap.add_argument("--sweeps", type=int, default=2)
-    ap.add_argument("--burnin", type=int, default=2)
+    ap.add_argument("--burnin", type=int, default=20)
+    ap.add_argument("--fp64-steps", type=int, default=1,
+                    help="steps of the plain FP64 GPU path timed after the main run (0: skip)")
     ap.add_argument("--mode", default="step", choices=["step", "learned", "gram", "batch", "complex", "bound", "rotated", "direct"])
     ap.add_argument("--branches", type=int, default=8)
     ap.add_argument("--autotune", action="store_true")
-    ap.add_argument("--cpu-samples", type=int, default=12)
+    ap.add_argument("--cpu-samples", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--gram", default=None, choices=["ff", "fp64", "bf16"],
@@ -79,19 +81,45 @@ def _oracle_sample_run(nsamp, sweeps, seed_off=0):
     return time.perf_counter() - t
 
 
-def _cpu_subprocess(nsamp, sweeps, reps=1):
+def _cpu_procs(nsamp, sweeps, reps=1, nproc=1):
+    """Run the oracle in `nproc` concurrent single-threaded processes (each on its own `nsamp`
+    chains, `reps` repetitions, chain seeds offset per process); returns, per repetition, the
+    slowest process's seconds."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = ("import sys, json; sys.path.insert(0, %r); import bench; "
-            "print(json.dumps([bench._oracle_sample_run(%d, %d, k) for k in range(%d)]))" % (ROOT, nsamp, sweeps, reps))
-    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, check=True)
-    return json.loads(out.stdout.strip().splitlines()[-1])
+    procs = []
+    for p in range(nproc):
+        code = ("import sys, json; sys.path.insert(0, %r); import bench; "
+                "print(json.dumps([bench._oracle_sample_run(%d, %d, 1000 * %d + k) for k in range(%d)]))"
+                % (ROOT, nsamp, sweeps, p, reps))
+        procs.append(subprocess.Popen([sys.executable, "-c", code], env=env, stdout=subprocess.PIPE,
+                                      stderr=subprocess.PIPE, text=True))
+    outs = []
+    for pr in procs:
+        o, e = pr.communicate()
+        if pr.returncode != 0:
+            raise RuntimeError(f"oracle process failed: {e[-2000:]}")
+        outs.append(json.loads(o.strip().splitlines()[-1]))
+    return [max(o[k] for o in outs) for k in range(reps)]
+
+
+def _ncores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
 
 
 def cpu_baseline(nsamp, sweeps):
-    secs = _cpu_subprocess(nsamp, sweeps)[0]
-    return {"value": nsamp / secs, "unit": "samples/s", "cores": 1, "kind": "oracle",
-            "sample": f"{nsamp} of the workload's chains: {sweeps} sweeps + psi/E_loc/O + MinSR on them "
-                      f"({secs:.1f} s, one host core)"}
+    """The oracle as it stands on the host: one core, and every core (one single-threaded process
+    per core, each on nsamp chains)."""
+    one = _cpu_procs(nsamp, sweeps)[0]
+    nc = _ncores()
+    allc = _cpu_procs(nsamp, sweeps, nproc=nc)[0]
+    return {"value": nc * nsamp / allc, "unit": "samples/s", "cores": nc, "kind": "oracle",
+            "one_core": {"value": nsamp / one, "unit": "samples/s", "cores": 1},
+            "sample": f"{nsamp} chains of the workload per process: {sweeps} sweeps + psi/E_loc/O + MinSR on them; "
+                      f"{nc} concurrent single-threaded processes ({allc:.1f} s, the slowest), and one alone "
+                      f"({one:.1f} s); nproc = {nc}"}
 
 
 def run_reference(a):
@@ -102,16 +130,17 @@ def run_reference(a):
     w = I.WORKLOADS[WORKLOAD]
     ns = a.ns or w["ns"]
     nsamp = a.cpu_samples
-    secs = _cpu_subprocess(nsamp, a.sweeps, reps=a.warmup + a.steps)[a.warmup:]
+    nc = _ncores()
+    secs = _cpu_procs(nsamp, a.sweeps, reps=a.warmup + a.steps, nproc=nc)[a.warmup:]
     t = float(np.mean(secs))
-    v = nsamp / t
+    v = nc * nsamp / t
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "samples/s", "n_gpus": a.gpus,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": _config(w, ns, a.sweeps),
-            "cpu_baseline": {"value": v, "unit": "samples/s", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": v, "unit": "samples/s", "cores": nc, "kind": "oracle",
                              "sample": f"each step: {nsamp} chains of the workload ({a.sweeps} sweeps + psi/E_loc/O "
-                                       f"+ MinSR), one host core"},
+                                       f"+ MinSR) in each of {nc} concurrent single-threaded processes (nproc = {nc})"},
             "e2e": {"value": v, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -193,66 +222,103 @@ def _measured_traffic(kernel, ns, sweeps, prec):
     return None
 
 
+def _tau_chains(E, c=5.0):
+    """Integrated autocorrelation time (1 + 2 sum_t rho(t), Sokal's window W >= c tau) of the
+    local energy along the chains: E is steps x chains; the mean over the chains of each step is
+    removed first (the parameters move between steps), rho(t) averages over every chain."""
+    x = np.asarray(E, dtype=np.float64)
+    x = x - x.mean(axis=1, keepdims=True)
+    T = x.shape[0]
+    var = np.mean(x * x)
+    if var == 0.0 or T < 3:
+        return 1.0
+    rho = [np.mean(x[: T - t] * x[t:]) / var for t in range(T // 2 + 1)]
+    tau = 1.0
+    for W in range(1, len(rho)):
+        tau = 1.0 + 2.0 * float(np.sum(rho[1:W + 1]))
+        if W >= c * tau:
+            break
+    return max(tau, 1.0)
+
+
+HEIS_BOUNDS = (-0.75, 0.25)  # the eigenvalues of S_i . S_j for one bond
+
+
 def run_gpu(a):
+    import tempfile
+
     import torch
     import torch.distributed as dist
     from paper_2503_12557_gb300 import build, costmodel, inputs as I, peps as P
-
+    from paper_2503_12557_gb300.dist import CudaMinSROps, sharded_minsr
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     lrank = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        dist.init_process_group("nccl")
     torch.cuda.set_device(lrank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", lrank))
     if rank == 0 or world == 1:
         build.build()
     if world > 1:
         dist.barrier()
     w = I.WORKLOADS[WORKLOAD]
     lat = I.Lattice(w["Lx"], w["Ly"], w["d"], w["D"])
-    ns = a.ns or w["ns"]
+    ns = a.ns or w["ns"]                        # chains of this process (weak scaling)
     prec = P.PREC_FP32 if a.prec == "fp32" else P.PREC_FP64
     H = I.heisenberg(lat)
+    nbonds = len(H["terms"])
     theta0 = I.peps_random(lat, w["seed_theta"], **w["init"])
     S0 = I.configs_neel(lat, ns)
-    gram = {"fp64": 0, "bf16": 1, "ff": 2}[a.gram or ("ff" if a.prec == "fp32" else "fp64")]  # the solve stays FP64 Cholesky in every case
-    h = P.PEPS(lat.Lx, lat.Ly, lat.d, lat.D, w["chi"], prec=prec, max_samples=ns, gram=gram, solve=0)
-    theta = torch.as_tensor(theta0).cuda()
-    h.set_params(theta)
-    h.set_env_reuse(True)  # the evaluation takes the sampler's upper environments (cached, unchanged S)
+    gram = {"fp64": 0, "bf16": 1, "ff": 2}[a.gram or ("ff" if a.prec == "fp32" else "fp64")]  # the solve stays FP64 Cholesky
+    mask = P.ST_ZERO_NORM | P.ST_NONFINITE | P.ST_NOCONV   # samples left out of E_loc and MinSR
+    seed = w["seed_chain"] + 7919 * rank                    # every process its own chains
+
+    def make(prec_, ns_, gram_):
+        h_ = P.PEPS(lat.Lx, lat.Ly, lat.d, lat.D, w["chi"], prec=prec_, max_samples=ns_, gram=gram_, solve=0)
+        th_ = torch.as_tensor(theta0).cuda()
+        h_.set_params(th_)
+        h_.set_env_reuse(True)  # the evaluation takes the sampler's last environments (cached, unchanged S)
+        return h_, th_
+
+    h, theta = make(prec, ns, gram)
     S = torch.as_tensor(S0).cuda()
     acc = torch.zeros(ns, dtype=torch.int64, device="cuda")
     O = torch.empty(ns, h.Np, dtype=h.odtype, device="cuda")
     stream = torch.cuda.current_stream()
     sweep_ctr = [0]
     info_hist = []
+    ops = CudaMinSROps(h) if world > 1 else None
 
-    def step(O_out=O):
-        h.sample(S, P.MOVE_EXCHANGE, a.sweeps, seed=w["seed_chain"] + 7919 * rank, sweep0=sweep_ctr[0], accepted=acc)
-        sweep_ctr[0] += a.sweeps
-        r = h.evaluate(H, S, O_out=O_out)
-        dth, info = h.minsr_step(r["O"], r["eloc"], lam=w["lam"], rcond=w["rcond"], tau=w["tau"])
-        h.apply_update(theta, dth)
-        info_hist.append(info)
+    def step(hh=h, th=theta, SS=S, accd=acc, O_out=O, ctr=sweep_ctr, hist=info_hist, ops_=ops):
+        hh.sample(SS, P.MOVE_EXCHANGE, a.sweeps, seed=seed, sweep0=ctr[0], accepted=accd)
+        ctr[0] += a.sweeps
+        r = hh.evaluate(H, SS, O_out=O_out)
+        wts = hh.status_weights(r["status"], mask)
+        if ops_ is not None:
+            dth, info = sharded_minsr(ops_, r["O"], r["eloc"], wts, lam=w["lam"], rcond=w["rcond"], tau=w["tau"])
+        else:
+            dth, info = hh.minsr_step(r["O"], r["eloc"], w=wts, lam=w["lam"], rcond=w["rcond"], tau=w["tau"])
+        hh.apply_update(th, dth)
+        hist.append(info)
         return r, dth
 
     # burn-in sweeps from the Neel start, untimed
-    h.sample(S, P.MOVE_EXCHANGE, a.burnin, seed=w["seed_chain"] + 7919 * rank, sweep0=0, accepted=acc)
+    h.sample(S, P.MOVE_EXCHANGE, a.burnin, seed=seed, sweep0=0, accepted=acc)
     sweep_ctr[0] = a.burnin
     for i in range(a.warmup):
         if i == a.warmup - 1:
             h.timing(True)  # the library's event pool and counters come up outside the timed region
         r, _ = step()
-        # the timed loop's reduction too: torch loads its kernel module on first use, which on a
-        # freshly started machine can take most of a second
-        eloc_warm = r["eloc"][:, 0].mean()
+        # the timed loop's reductions too: torch loads their kernels on first use
+        eloc_warm = (r["eloc"][:, 0] * (r["status"] & mask == 0)).sum()
     torch.cuda.synchronize()
+    h.last_status()
     # ---- timed region (device events on the launching stream)
     h.timing(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    eloc_means = []
-    with _Clocks(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv") if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
-                 else f"/tmp/clocks_rank{rank}.csv") as clk:
+    res = []
+    clk_path = os.path.join(tempfile.gettempdir(), f"peps_bench_clocks_rank{rank}.csv")
+    with _Clocks(clk_path) as clk:
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
@@ -260,13 +326,14 @@ def run_gpu(a):
         e0.record(stream)
         for k in range(a.steps):
             r, _ = step()
-            eloc_means.append(r["eloc"][:, 0].mean())
+            res.append((r["eloc"], r["status"]))  # fresh tensors every step: no copy in the timed region
             marks[k].record(stream)
         e1.record(stream)
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
     ms_total = e0.elapsed_time(e1)
+    word = h.last_status()
     # full one-side environment passes of the timed sampler calls: sweeps alternate direction
     # (even ids down, odd up); a downward sweep, and an upward one that opens a call, need one
     s0 = a.burnin + a.warmup * a.sweeps
@@ -275,14 +342,22 @@ def run_gpu(a):
     step_ms = [e0.elapsed_time(marks[0])] + [marks[k - 1].elapsed_time(marks[k]) for k in range(1, a.steps)]
     ms_cls, launches, ctr = h.timing_read()
     h.timing(False)
+    # ---- energies of the timed steps: flagged samples left out (as from MinSR), per-site means
+    E = np.stack([e[:, 0].cpu().numpy() for e, _ in res])            # steps x chains
+    ST = np.stack([st.cpu().numpy() for _, st in res])
+    ok = (ST & mask) == 0
+    e_site = [float(E[k][ok[k]].mean()) / lat.nsites for k in range(a.steps)]
+    lo_b, hi_b = HEIS_BOUNDS[0] * nbonds / lat.nsites, HEIS_BOUNDS[1] * nbonds / lat.nsites
+    tau = _tau_chains(E)
     # the last timed step's MinSR update against an FP64 Gram of the same O and E_loc
     dtheta_check = None
-    if gram != 0:
-        dth_last = h.minsr_step(r["O"], r["eloc"], lam=w["lam"], rcond=w["rcond"], tau=w["tau"])[0].clone()
-        h64 = P.PEPS(lat.Lx, lat.Ly, lat.d, lat.D, w["chi"], prec=prec, max_samples=2, gram=0, solve=0)
-        dth64 = h64.minsr_step(r["O"], r["eloc"], lam=w["lam"], rcond=w["rcond"], tau=w["tau"])[0]
+    if gram != 0 and world == 1:
+        wl = h.status_weights(r["status"], mask)
+        dth_last = h.minsr_step(r["O"], r["eloc"], w=wl, lam=w["lam"], rcond=w["rcond"], tau=w["tau"])[0].clone()
+        h64g = P.PEPS(lat.Lx, lat.Ly, lat.d, lat.D, w["chi"], prec=prec, max_samples=2, gram=0, solve=0)
+        dth64 = h64g.minsr_step(r["O"], r["eloc"], w=wl, lam=w["lam"], rcond=w["rcond"], tau=w["tau"])[0]
         dtheta_check = float((dth_last - dth64).norm() / dth64.norm())
-        h64.close()
+        h64g.close()
     ms_step = ms_total / a.steps
     if world > 1:
         t = torch.tensor([ms_step], device="cuda")
@@ -313,7 +388,7 @@ def run_gpu(a):
                                          passes=sampler_passes),
         "row": costmodel.row_kernel_flops(lat.Lx, lat.Ly, w["chi"], w["D"], ns * a.steps, True, hwin * a.steps),
         "pair": costmodel.pair_kernel_flops(lat.Lx, lat.Ly, w["chi"], w["D"], ns * a.steps, vwin * a.steps),
-        "minsr_gram": costmodel.gram_flops(ns, h.Np) * a.steps,
+        "minsr_gram": costmodel.gram_flops(ns * world, h.Np) * a.steps / world,
     }
     dom = max(flops, key=lambda k: ms_cls.get(k, 0.0))
     dom_launch_ms = ms_cls[dom] / max(1, launches[dom])
@@ -332,16 +407,17 @@ def run_gpu(a):
                             "measured: peps_probe_fma FP64" if peak == fp64_peak else "MEASURED_PEAKS bf16_tflops"),
             "algorithmic_tflop_per_launch": flops[dom] / max(1, launches[dom]) / 1e12,
             "launch_ms": dom_launch_ms}
-    gpu_launches = int(sum(launches.values())) + 3 * a.steps  # + memsets inside evaluate / minsr
+    # library launches per step: the classes' counts plus the memsets of evaluate / minsr
+    gpu_launches = int(sum(launches.values())) + 4 * a.steps
     line = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if prec == P.PREC_FP32 else "f64", "data": "synthetic",
             "config": _config(w, ns, a.sweeps), "step_ms": step_ms, "minsr_step_s": minsr_s,
             "minsr": {"gram": {0: "FP64 CUDA cores", 1: "split-BF16 tcgen05",
                                2: "float-float pairs on the FP32 pipes"}[gram],
-                      "solve": "FP64 Cholesky",
+                      "solve": "FP64 Cholesky", "sharded_over_processes": world > 1,
                       "gram_ms": ms_cls["minsr_gram"] / a.steps, "solve_ms": ms_cls["minsr_eig"] / a.steps,
-                      "gram_tflops_algorithmic": (costmodel.gram_flops(ns, h.Np) /
+                      "gram_tflops_algorithmic": (flops["minsr_gram"] / a.steps /
                                                   max(1e-9, ms_cls["minsr_gram"] / a.steps / 1e3) / 1e12),
                       "gram_pipe_frac": (costmodel.gram_pipe_flops(ns, h.Np, gram) /
                                          max(1e-9, ms_cls["minsr_gram"] / a.steps / 1e3) / 1e12 / gram_peak),
@@ -353,7 +429,17 @@ def run_gpu(a):
             "roofline": roof, "alu_peaks_measured_tflops": {"fp32": fp32_peak, "fp64": fp64_peak},
             "gpu_launches": gpu_launches, "clocks": clk.summary(),
             "acceptance": float(acc.sum().item()) / max(1.0, ns * (sweep_ctr[0]) * (2 * lat.Lx * lat.Ly - lat.Lx - lat.Ly) * 0.5),
-            "eloc_mean_per_site": [float(x) / lat.nsites for x in eloc_means]}
+            "energy": {"eloc_mean_per_site": e_site,
+                       "heisenberg_bounds_per_site": [lo_b, hi_b],
+                       "all_steps_within_bounds": bool(all(lo_b <= x <= hi_b for x in e_site)),
+                       "samples_left_out_per_step": [int((~ok[k]).sum()) for k in range(a.steps)],
+                       "status_word": word,
+                       "tau_int_eloc": tau,
+                       "tau_convention": "1 + 2 sum_t rho(t) over MinSR steps of 2 sweeps (effective samples = N / tau)"},
+            "energy_converged_samples_per_s": value / tau}
+    # ---- the plain FP64 GPU path on the same workload and chain count (after the timed region)
+    if a.fp64_steps > 0 and prec == P.PREC_FP32 and world == 1:
+        line["fp64_plain"] = _fp64_plain(a, P, make, theta, S, H, ns, seed, sweep_ctr[0], mask, tau, value, lat)
     # ---- end to end through the public API with host buffers
     if not a.no_e2e:
         th_host = torch.empty(h.Np, dtype=torch.float64).pin_memory()
@@ -375,6 +461,10 @@ def run_gpu(a):
         f1.record(stream)
         torch.cuda.synchronize()
         e2e_ms = f0.elapsed_time(f1) / a.steps
+        if world > 1:
+            t = torch.tensor([e2e_ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
         line["e2e"] = {"value": ns * world / (e2e_ms / 1e3), "unit": "samples/s",
                        "h2d_bytes_per_step": h.Np * 8 + ns * lat.nsites,
                        "d2h_bytes_per_step": h.Np * 8 + ns * 16}
@@ -387,20 +477,89 @@ def run_gpu(a):
         dist.destroy_process_group()
 
 
+def _fp64_plain(a, P, make, theta, S_fp32, H, ns, seed, sweep0, mask, tau, value32, lat):
+    """The plain FP64 GPU path (FP64 contractions, FP64 Gram, FP64 Cholesky) at the same chain count,
+    from the FP32 run's parameters and configurations: samples/s of a.fp64_steps steps (CUDA
+    events), and the per-site energy of the FP32 and FP64 evaluations of the same configurations
+    at the same parameters (equal energy error: within the 1e-4 per site gate, so both reach the
+    same error with the same samples)."""
+    import torch
+    w = I_workload()
+    h64, th64 = make(P.PREC_FP64, ns, 0)
+    h32e, th32 = make(P.PREC_FP32, ns, 2)
+    th64.copy_(theta)
+    th32.copy_(theta)
+    h64.set_params(th64)
+    h32e.set_params(th32)
+    S = S_fp32.clone()
+    # the same configurations through both precisions (no parameter update in between)
+    r32 = h32e.evaluate(H, S, want_O=False)
+    r64 = h64.evaluate(H, S, want_O=False)
+    ok = ((r32["status"] & mask) == 0) & ((r64["status"] & mask) == 0)
+    d_e = float(((r32["eloc"][:, 0] - r64["eloc"][:, 0])[ok]).mean().abs()) / lat.nsites
+    d_l = float((r32["logabs"] - r64["logabs"])[ok].abs().max())
+    h32e.close()
+    acc = torch.zeros(ns, dtype=torch.int64, device="cuda")
+    O = torch.empty(ns, h64.Np, dtype=torch.float64, device="cuda")
+    ctr = [sweep0]
+
+    def step():
+        h64.sample(S, P.MOVE_EXCHANGE, a.sweeps, seed=seed, sweep0=ctr[0], accepted=acc)
+        ctr[0] += a.sweeps
+        r = h64.evaluate(H, S, O_out=O)
+        wts = h64.status_weights(r["status"], mask)
+        dth, _ = h64.minsr_step(r["O"], r["eloc"], w=wts, lam=w["lam"], rcond=w["rcond"], tau=w["tau"])
+        h64.apply_update(th64, dth)
+
+    # warm-up on a few chains (module load, workspaces), then the timed steps at full size
+    h64.sample(S[:152].clone(), P.MOVE_EXCHANGE, 1, seed=seed, sweep0=0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.fp64_steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / a.fp64_steps
+    v64 = ns / (ms / 1e3)
+    h64.close()
+    return {"value": v64, "unit": "samples/s", "ms_per_step": ms, "steps": a.fp64_steps,
+            "what": "FP64 contractions, FP64 Gram, FP64 Cholesky, same chains and step",
+            "energy_converged_samples_per_s": v64 / tau,
+            "fp32_vs_fp64_same_configs": {"mean_eloc_diff_per_site": d_e, "max_dlogpsi": d_l,
+                                          "samples": int(ok.sum().item()),
+                                          "gate_per_site": 1e-4, "equal_energy_error": d_e <= 1e-4},
+            "fp32_over_fp64_energy_converged": value32 / v64}
+
+
+def I_workload():
+    from paper_2503_12557_gb300 import inputs as I
+    return I.WORKLOADS[WORKLOAD]
+
+
 def run_learned(a):
-    """12x12 Rydberg (delta = 3, R_b = 1.7, D = 4, chi = 24) chains: local single-flip sweeps
-    against trained network moves (FP32 contractions, bf16 network), and local sweeps in FP64
-    as the plain comparator.  Prints one JSON line with tau_int of the Rydberg density, the
-    network's acceptance and effective samples per second (chains x steps / (2 tau_int x time))."""
+    """12x12 Rydberg array (Omega = 1, R_b = 1.7, V0 / r^6 for r <= 4; D = 4, chi = 24, tensors drawn
+    as for the 8x8 workload; FP32 contractions, bf16 network), for every detuning delta in
+    {0, 1, 2, 3}: N_s chains thermalised by local flips, the network trained on the sampler's own
+    (S_t, S_{t+2}) pairs, then two arms from the same configurations, each followed by psi and
+    E_loc of every chain at every step:
+      local: one single-flip sweep per step;
+      mixed: one single-flip sweep plus one network move per step (learned.run_mixed's kernel).
+    Per arm: seconds per step (sampling alone, and with the energy evaluation), tau of E_loc along
+    the chains (1 + 2 sum rho), energy-converged samples/s = N_s / (t tau), and the energy error
+    at equal wall time, sigma_E sqrt(t tau / (N_s x 1 s)) per site for one second of sampling
+    plus evaluation.  The gain of the network is local's error over mixed's (above 1: the
+    network helps)."""
     import torch
     from paper_2503_12557_gb300 import build, inputs as I, learned as Lr, peps as P
     build.build()
     w = I.WORKLOADS["rydberg12x12_D4_chi24"]
     lat = I.Lattice(w["Lx"], w["Ly"], w["d"], w["D"])
-    ns = a.ns or 1024
+    ns = a.ns or 4096
+    T = max(a.steps, 12)
     theta = torch.as_tensor(I.peps_random(lat, w["seed_theta"], **w["init"])).cuda()
-    density = lambda s: s.float().mean(dim=1).cpu().numpy()  # noqa: E731
-    out = {"mode": "learned", "workload": f"12x12 Rydberg, D=4, chi=24, {ns} chains", "steps": a.steps}
+    out = {"mode": "learned", "workload": f"12x12 Rydberg, D=4, chi=24, {ns} chains, {T} steps per arm",
+           "deltas": {}}
 
     def timed(fn):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -410,37 +569,49 @@ def run_learned(a):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / 1e3, r
 
-    precs = ((P.PREC_FP32, "fp32"),) + (((P.PREC_FP64, "fp64"),) if a.prec == "fp64" else ())
-    for prec, tag in precs:
-        h = P.PEPS(lat.Lx, lat.Ly, 2, lat.D, w["chi"], prec=prec, max_samples=ns)
-        h.set_params(theta)
+    h = P.PEPS(lat.Lx, lat.Ly, 2, lat.D, w["chi"], prec=P.PREC_FP32, max_samples=ns)
+    h.set_params(theta)
+    for delta in (0.0, 1.0, 2.0, 3.0):
+        H = I.rydberg(lat, delta=delta)
         S = torch.zeros(ns, lat.nsites, dtype=torch.uint8, device="cuda")
-        S, _, _ = Lr.run_local(h, S, a.burnin, seed=w["seed_chain"], sweep0=0)
-        t, (S2, obs, acc) = timed(lambda: Lr.run_local(h, S.clone(), a.steps, seed=w["seed_chain"], sweep0=100,
-                                                     observe=density))
-        tau = Lr.tau_int(np.array(obs))
-        out[f"local_{tag}"] = {"tau_int": tau, "s_per_step": t / a.steps,
-                               "ess_per_s": ns * a.steps / (2 * tau * t), "density": float(np.mean(obs))}
-        if prec == P.PREC_FP32:
-            S_in, S_out, S = Lr.collect_pairs(h, S, 4, 2, seed=w["seed_chain"] + 1, sweep0=1000)
-            prop = P.Proposal(lat.Lx, lat.Ly, I.proposal_init(5), C=16, wprec=1)
-            tt, losses = timed(lambda: Lr.train(prop, S_in, S_out, 200, lr=3e-3, batch=4096))
-            lpsi, _, _ = h.amplitudes(S)
-            accn = torch.zeros(ns, dtype=torch.int64, device="cuda")
-            obsn = []
-
-            def net():
-                for k in range(a.steps):
-                    h.sample_learned(prop, S, lpsi, seed=w["seed_chain"] + 2, step=k, accepted=accn)
-                    obsn.append(density(S))
-
-            t, _ = timed(net)
-            tau = Lr.tau_int(np.array(obsn))
-            out["network_fp32_bf16"] = {"tau_int": tau, "s_per_step": t / a.steps,
-                                        "ess_per_s": ns * a.steps / (2 * tau * t), "density": float(np.mean(obsn)),
-                                        "acceptance": accn.sum().item() / (ns * a.steps),
-                                        "train_s": tt, "loss_first_last": [losses[0], losses[-1]]}
-        h.close()
+        S, _, _ = Lr.run_local(h, S, max(a.burnin, 10), seed=w["seed_chain"], sweep0=0)
+        S_in, S_out, S = Lr.collect_pairs(h, S, 4, 2, seed=w["seed_chain"] + 1, sweep0=1000)
+        prop = P.Proposal(lat.Lx, lat.Ly, I.proposal_init(5), C=16, wprec=1)
+        t_train, losses = timed(lambda: Lr.train(prop, S_in, S_out, 200, lr=3e-3, batch=4096))
+        res = {"train_s": t_train, "loss_first_last": [losses[0], losses[-1]]}
+        for arm in ("local", "mixed"):
+            S_arm = S.clone()
+            acc_l = torch.zeros(ns, dtype=torch.int64, device="cuda")
+            acc_n = torch.zeros(ns, dtype=torch.int64, device="cuda")
+            E = []
+            t_sample = t_eval = 0.0
+            lpsi = h.amplitudes(S_arm)[0] if arm == "mixed" else None
+            for t in range(T):
+                def samp():
+                    h.sample(S_arm, P.MOVE_FLIP, 1, seed=w["seed_chain"] + 2, sweep0=2000 + t, accepted=acc_l)
+                    if arm == "mixed":
+                        lp, _, _ = h.amplitudes(S_arm)
+                        h.sample_learned(prop, S_arm, lp, seed=w["seed_chain"] + 3, step=2000 + t, accepted=acc_n)
+                ts, _ = timed(samp)
+                te, r = timed(lambda: h.evaluate(H, S_arm, want_O=False))
+                t_sample += ts
+                t_eval += te
+                E.append(r["eloc"][:, 0].cpu().numpy() / lat.nsites)
+            E = np.array(E)
+            tau = _tau_chains(E)
+            ts, te = t_sample / T, t_eval / T
+            sig = float(E.std())
+            res[arm] = {"s_per_step_sampling": ts, "s_per_step_with_eval": ts + te, "tau_int_eloc": tau,
+                        "E_per_site": float(E.mean()), "sigma_E_per_site": sig,
+                        "energy_converged_samples_per_s": ns / ((ts + te) * tau),
+                        "err_per_site_at_1s": sig * float(np.sqrt((ts + te) * tau / ns)),
+                        "local_acceptance": float(acc_l.sum().item()) / (ns * T * lat.nsites)}
+            if arm == "mixed":
+                res[arm]["network_acceptance"] = float(acc_n.sum().item()) / (ns * T)
+        res["gain_err_local_over_mixed"] = res["local"]["err_per_site_at_1s"] / res["mixed"]["err_per_site_at_1s"]
+        out["deltas"][str(delta)] = res
+        print(json.dumps({"delta": delta, **res}), flush=True)
+    h.close()
     print(json.dumps(out), flush=True)
 
 
@@ -472,6 +643,7 @@ def run_gram(a):
         h.timing(True)
         for _ in range(reps):
             dth, info = h.minsr_step(O, e, lam=1.0, tau=0.1)
+        h.last_status()
         ms, la, _ = h.timing_read()
         h.timing(False)
         gram_ms = ms["minsr_gram"] / reps
@@ -500,11 +672,12 @@ def run_gram(a):
 
 
 def run_batch(a):
-    """Ragged multi-instance batch in one CUDA graph: 64 independent open Heisenberg PEPS with
-    (L, D) drawn uniformly from {6, 8, 10, 12} x {3, 4, 5} (seed 5005), chi = D^2, tensors as the
-    8x8 workload (0.5 N(0,1) + 1.0 bias), N_s configurations each (uniform S^z = 0); psi, E_loc and
-    O of every instance.  Reports samples/s of the graph replay, of the same calls issued one
-    after another, and (with --autotune) after tuning each handle."""
+    """Ragged multi-instance batch: 64 independent open Heisenberg PEPS with (L, D) drawn uniformly
+    from {6, 8, 10, 12} x {3, 4, 5} (seed 5005), chi = D^2, tensors drawn as for the 8x8 workload,
+    N_s configurations each (uniform S^z = 0); psi, E_loc and O of every instance by one
+    persistent launch over the (instance, sample) queue, recorded in a CUDA graph.  Reports
+    samples/s of the graph replay and of the same evaluations issued one handle after another,
+    and (with --autotune) the batch budget the autotuner chose."""
     import torch
     from paper_2503_12557_gb300 import build, inputs as I, peps as P
     build.build()
@@ -516,17 +689,11 @@ def run_batch(a):
     for k, (L, D) in enumerate(shapes):
         lat = I.Lattice(L, L, 2, D)
         h = P.PEPS(L, L, 2, D, D * D, prec=prec, max_samples=ns)
-        h.set_params(torch.as_tensor(I.peps_random(lat, 5005 + k, scale=0.5, bias=1.0)).cuda())
+        h.set_params(torch.as_tensor(I.peps_random(lat, 5005 + k, **I.WORKLOADS[WORKLOAD]["init"])).cuda())
         S = torch.as_tensor(I.configs_uniform_sz0(lat, ns, 6005 + k)).cuda()
         items.append((h, I.heisenberg(lat), S, True))
     out = {"mode": "batch", "instances": 64, "ns_per_instance": ns, "precision": a.prec,
            "shapes": {f"{L}x{L}_D{D}": sum(1 for s in shapes if s == (L, D)) for (L, D) in sorted(set(shapes))}}
-    if a.autotune:
-        kbs = {}
-        for (h, H, S, _) in items:
-            kbs[f"{h.Lx}x{h.Ly}_D{h.D}"] = h.autotune(S, H)
-        torch.cuda.synchronize()
-        out["autotune_kb"] = kbs
     # one instance after another (eager), then the recorded graph
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
@@ -539,7 +706,8 @@ def run_batch(a):
         e1.record(stream)
         stream.synchronize()
     eager_ms = e0.elapsed_time(e1) / a.steps
-    batch = P.Batch(items, nbranch=a.branches, stream=stream)
+    batch = P.Batch(items, stream=stream, autotune=a.autotune)
+    out["batch_budget_kb"] = batch.budget_kb or "default"
     for _ in range(a.warmup):
         batch.launch()
     stream.synchronize()
@@ -554,7 +722,7 @@ def run_batch(a):
                for o, r in zip(batch.out, outs))
     tot = 64 * ns
     out.update({"graph_ms": graph_ms, "eager_ms": eager_ms, "graph_samples_per_s": tot / (graph_ms / 1e3),
-                "eager_samples_per_s": tot / (eager_ms / 1e3), "branches": a.branches,
+                "eager_samples_per_s": tot / (eager_ms / 1e3),
                 "graph_equals_eager": bool(same)})
     print(json.dumps(out), flush=True)
 

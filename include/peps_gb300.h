@@ -49,8 +49,9 @@ extern "C" {
 
 typedef enum {
     PEPS_OK = 0,
-    PEPS_W_NUMERIC = 1,     /* minsr_step: T + lambda not positive definite in floating
-                               point; dtheta_dev was set to zero (info[0] = -1)       */
+    PEPS_W_NUMERIC = 1,     /* peps_last_status: a numerical warning since the last read
+                               (per-sample status bits, or a MinSR breakdown: dtheta
+                               was set to zero, info[0] = -1)                          */
     PEPS_E_ARG = -1,        /* NULL pointer, negative size, bad enum value            */
     PEPS_E_SHAPE = -2,      /* lattice / chi / Ns outside what the handle supports     */
     PEPS_E_WORKSPACE = -3,  /* device allocation failed                                */
@@ -65,6 +66,14 @@ enum {
     PEPS_ST_ZERO_NORM = 2,
     PEPS_ST_NONFINITE = 4,
     PEPS_ST_NOCONV = 8
+};
+
+/* Bits of a handle's status word beyond the per-sample PEPS_ST_* bits (peps_last_status). */
+enum {
+    PEPS_SW_MINSR_BREAKDOWN = 1 << 8,  /* a minsr_step found T + lambda not positive definite in
+                                          floating point; its dtheta was set to zero            */
+    PEPS_SW_GRAM_TIMEOUT = 1 << 9      /* a tensor-core Gram gave up on a pipeline wait; its
+                                          dtheta was set to zero                                */
 };
 
 /* Arithmetic of the contraction kernels.  FP64: every step in double.  FP32: the environment,
@@ -129,7 +138,38 @@ typedef struct peps_handle peps_handle;
  * environment store for cfg->max_samples configurations on the current CUDA device.
  * Returns PEPS_E_SHAPE when the sizes are outside the limits stated in peps_config. */
 peps_status peps_create(peps_handle** out, const peps_config* cfg);
+
+/* Device-memory callbacks of a handle (peps_create_ex): alloc(ctx, bytes) returns device memory
+ * of the current device, aligned to 256 bytes, or NULL on failure; free(ctx, ptr) returns it.
+ * The handle calls them at creation (parameter copy, environment store, scratch) and when a
+ * later call first needs a workspace (MinSR, direct sampling, the bound estimator, the
+ * learned proposal, Hamiltonian tables), never during a stream capture of a call whose
+ * workspace already exists, and frees everything through free() in peps_destroy.  Memory that
+ * free() releases may be reused by the allocator in the order of the stream the handle's calls
+ * ran on. */
+typedef struct {
+    void* (*alloc)(void* ctx, size_t bytes);
+    void (*free)(void* ctx, void* ptr);
+    void* ctx;
+} peps_allocator;
+
+/* As peps_create, with every device allocation of the handle made through *alloc (copied; NULL
+ * = cudaMalloc / cudaFree).  PEPS_E_ARG when a callback is NULL; PEPS_E_WORKSPACE when alloc
+ * returns NULL. */
+peps_status peps_create_ex(peps_handle** out, const peps_config* cfg, const peps_allocator* alloc);
 peps_status peps_destroy(peps_handle* h);
+
+/* The handle's status word: the OR of the per-sample status bits (PEPS_ST_*) of every sample of
+ * every evaluation, sampling or estimator call, and of the PEPS_SW_* flags of every minsr_step,
+ * since the last peps_last_status (or creation).  Synchronises `stream` (the stream those calls
+ * ran on), writes the word to *word_host (may be NULL) and clears it.  Returns PEPS_E_CUDA when
+ * PEPS_SW_GRAM_TIMEOUT is set, PEPS_W_NUMERIC when any other bit is set, else PEPS_OK: the
+ * numerical warnings of the asynchronous calls, read when the caller chooses to synchronise. */
+peps_status peps_last_status(peps_handle* h, int32_t* word_host, void* stream);
+
+/* w_dev[i] = 0 where status_dev[i] & mask, else 1 (Ns doubles, device): weights for minsr_step
+ * that leave out the samples a status bit marks (no counterpart in the paper). */
+peps_status peps_status_weights(const int32_t* status_dev, int Ns, int mask, double* w_dev, void* stream);
 
 /* N_p = sum over sites of d * Dl * Du * Dr * Dd (boundary legs of dimension 1). */
 long long peps_num_params(const peps_handle* h);
@@ -242,13 +282,52 @@ peps_status peps_local_energy_bound(peps_handle* h, const peps_hamiltonian* H, c
  * refined residual stayed above 1e-10 and the FP64 factorisation was used instead.  When T +
  * lambda is not positive definite in floating point even in FP64 (lambda far below the
  * rounding error of T, e.g. a split-BF16 Gram of badly scaled O), info[0] = -1, dtheta_dev is
- * set to zero and the call returns PEPS_W_NUMERIC.  Needs lambda > 0 or rcond > 0.  The Gram matrix is FP64 (cfg.gram == 0), split
+ * set to zero and the status word gets PEPS_SW_MINSR_BREAKDOWN (peps_last_status then returns
+ * PEPS_W_NUMERIC).  Needs lambda > 0 or rcond > 0.  The Gram matrix is FP64 (cfg.gram == 0), split
  * BF16 on the tensor cores (cfg.gram == 1) or float-float on the FP32 pipes (cfg.gram == 2);
- * the factorisation / eigendecomposition is FP64.  The call
- * synchronises the stream before it returns. */
+ * the factorisation / eigendecomposition is FP64.  The call is
+ * asynchronous like every other (no host round trip: the mixed solve's FP64 fallback and the
+ * zeroing of dtheta on a breakdown are decided on the device; rcond > 0 runs the whole cyclic
+ * Jacobi in one cooperative launch); a breakdown is reported by peps_last_status. */
 peps_status minsr_step(peps_handle* h, const void* O_dev, const double* eloc_dev, const double* w_dev,
                        int Ns, double lambda, double rcond, double tau, double* dtheta_dev,
                        double* info_dev, void* stream);
+
+/* ---- Sample-sharded MinSR: the step of minsr_step split at its exchange points, for samples
+ * spread over several processes (one GPU each).  The paper parallelises over samples (Sec.
+ * "Finite PEPS and Sampling"); MinSR then needs the exchange below.  With G processes, process g
+ * holding N_g of the N_s = sum N_g samples and the parameter slice [c_g, c_{g+1}) of N_p:
+ *   1. minsr_partial_sums on the local rows, summed over the processes (all-reduce, N_p + 2);
+ *   2. minsr_center_rows: the local rows of Obar and ebar with those global sums (the same
+ *      centring as minsr_step);
+ *   3. exchange Obar's column slices (all-to-all): process g gets the N_s x K_g block A_g of
+ *      its slice, rows in process order;
+ *   4. minsr_gram on A_g, summed over the processes (all-reduce, N_s x N_s): T = Obar Obar^T;
+ *   5. ebar gathered to all (N_s); minsr_solve on every process (same x everywhere);
+ *   6. minsr_project: dtheta on the slice, gathered to all (all-gather).
+ * The result equals minsr_step's on all N_s rows (up to the summation order of the reductions).
+ * Real PEPS only (PEPS_E_UNSUPPORTED for a complex handle).  Asynchronous on `stream`.
+ * minsr_partial_sums: O_dev (Ns x N_p, handle precision), eloc_dev (Ns x 2), w_dev (Ns or NULL =
+ *   every weight 1; the weights need not be normalised); sums_dev (N_p + 2 doubles): column sums
+ *   of w O, then sum w, then sum w Re E_loc.
+ * minsr_center_rows: gsums_dev the sums added over every process; Obar_dev (Ns x N_p doubles) =
+ *   sqrt(w_S / W) (O_S - m), ebar_dev (Ns) = sqrt(w_S / W) (Re E_loc(S) - e) with W the global
+ *   sum of weights, m and e the global weighted means.
+ * minsr_gram: T_dev (Ns x Ns doubles, written in full) = A A^T for A_dev (Ns x K doubles) in the
+ *   handle's Gram mode (cfg.gram); K = 0 gives T = 0.
+ * minsr_solve: x_dev (Ns) = (T + lambda)^+ ebar as minsr_step (Cholesky when rcond == 0, else the
+ *   eigendecomposition with the cutoff), info_dev (4) as minsr_step; on a breakdown x is zero and
+ *   the status word gets PEPS_SW_MINSR_BREAKDOWN.
+ * minsr_project: dtheta_dev (K) = -tau A^T x (no handle needed). */
+peps_status minsr_partial_sums(peps_handle* h, const void* O_dev, const double* eloc_dev, const double* w_dev, int Ns,
+                               double* sums_dev, void* stream);
+peps_status minsr_center_rows(peps_handle* h, const void* O_dev, const double* eloc_dev, const double* w_dev, int Ns,
+                              const double* gsums_dev, double* Obar_dev, double* ebar_dev, void* stream);
+peps_status minsr_gram(peps_handle* h, const double* A_dev, int Ns, long long K, double* T_dev, void* stream);
+peps_status minsr_solve(peps_handle* h, const double* T_dev, const double* ebar_dev, int Ns, double lambda,
+                        double rcond, double* x_dev, double* info_dev, void* stream);
+peps_status minsr_project(const double* A_dev, const double* x_dev, int Ns, long long K, double tau,
+                          double* dtheta_dev, void* stream);
 
 /* theta_dev (N_p doubles, device, updated in place) += dtheta_dev, then the handle's kernel
  * copy is refreshed as by peps_set_params (the parameter update that closes an optimisation
@@ -347,9 +426,17 @@ peps_status peps_amplitudes_noalloc(const peps_config* cfg, const double* theta_
 peps_status peps_autotune(peps_handle* h, const peps_hamiltonian* H, const uint8_t* S_dev, int Ns, int move,
                           int* budget_kb_host, void* stream);
 
-/* Multi-instance batch (no counterpart in the paper): independent handles (different lattices,
- * D, chi) evaluated by one CUDA graph.  Each item is one peps_evaluate call; its pointers are
- * recorded and read again at every launch (update the contents, not the pointers). */
+/* Multi-instance batch (no counterpart in the paper; the paper evaluates independent samples,
+ * Sec. "Finite PEPS and Sampling", and a batch of independent PEPS is the same work with ragged
+ * shapes): independent handles (different lattices, D, chi, sample counts) evaluated as one
+ * peps_evaluate each, by one persistent kernel launch per scalar type over a work queue of
+ * (instance, sample) items, costliest instances first (Lx Ly chi^3 D^3 per sample), each CTA
+ * taking the next item with one atomic and running that sample's whole evaluation (both
+ * environment sides, every one-row and two-row sandwich, the combine) with the device functions
+ * of the per-handle kernels: the results equal the items' peps_evaluate calls bit for bit.  The
+ * launches are recorded in one CUDA graph; the items' pointers are read again at every launch
+ * (update the contents, not the pointers).  Each launch also ORs the items' status bits into
+ * their handles' status words. */
 typedef struct {
     peps_handle* h;              /* each handle at most once per batch; timing disabled      */
     const peps_hamiltonian* H;   /* NULL when eloc_dev is NULL                               */
@@ -364,11 +451,21 @@ typedef struct {
 
 typedef struct peps_batch peps_batch;
 
-/* Runs every item once eagerly on `stream` (one-time uploads), then records all items into one
- * graph: `nbranch` concurrent branches forked from `stream`, items placed largest first
- * (Ns x sites x chi^3 D^3) on the least-loaded branch.  `stream` must not be the legacy default
- * stream (it cannot be captured).  PEPS_E_ARG for a repeated handle or a handle with timing on. */
+/* Runs every item once eagerly on `stream` (one-time uploads), then plans every instance's work
+ * buffers at one shared-memory budget per CTA (budget_kb; 0 = 110 KB for FP32-only batches, 210
+ * KB otherwise; the buffers that do not fit go to the batch's own global arena, one slice per
+ * CTA) and records the graph.  `stream` must not be the legacy default stream (it cannot be
+ * captured).  PEPS_E_ARG for a repeated handle or a handle with timing on; PEPS_E_SHAPE when the
+ * batch kernel does not fit on an SM at that budget.  Allocates the arena and the queue with
+ * cudaMalloc (freed by peps_batch_destroy). */
+peps_status peps_batch_create_ex(peps_batch** out, const peps_batch_item* items, int n, int budget_kb, void* stream);
+/* peps_batch_create_ex at the default budget (nbranch is ignored: one launch per scalar type). */
 peps_status peps_batch_create(peps_batch** out, const peps_batch_item* items, int n, int nbranch, void* stream);
+/* Batch autotuner: records the batch at each candidate budget (FP32: 56, 72, 110, 220 KB; with any
+ * FP64 item: 100, 210 KB), launches and times it twice with CUDA events (the items' outputs are
+ * written), and returns the fastest budget in *budget_kb_host.  The budget decides which work
+ * buffers stay on chip and how many CTAs share an SM.  Synchronises the stream. */
+peps_status peps_batch_autotune(const peps_batch_item* items, int n, int* budget_kb_host, void* stream);
 /* Launch the recorded graph on `stream` (asynchronous). */
 peps_status peps_batch_launch(peps_batch* b, void* stream);
 peps_status peps_batch_destroy(peps_batch* b);

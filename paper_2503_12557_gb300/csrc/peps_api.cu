@@ -93,8 +93,29 @@ struct peps_handle {
   double *lp_l0 = nullptr, *lp_l1 = nullptr, *lp_aux = nullptr;
   // split-BF16 operands of the tensor-core Gram
   void *g_hi = nullptr, *g_lo = nullptr;
+  // status word (device): OR of the per-sample status bits and the MinSR flags since the last
+  // peps_last_status
+  int* sword = nullptr;
+  // device memory: the caller's allocator when one was given to peps_create_ex, else cudaMalloc
+  peps_allocator alloc{};
+  bool has_alloc = false;
   std::string err;
 };
+
+static cudaError_t h_malloc(peps_handle* h, void** p, size_t bytes) {
+  *p = nullptr;
+  if (!h->has_alloc) return cudaMalloc(p, bytes);
+  void* q = h->alloc.alloc(h->alloc.ctx, bytes ? bytes : 1);
+  if (!q) return cudaErrorMemoryAllocation;
+  *p = q;
+  return cudaSuccess;
+}
+
+static void h_free(peps_handle* h, void* p) {
+  if (!p) return;
+  if (h->has_alloc) h->alloc.free(h->alloc.ctx, p);
+  else cudaFree(p);
+}
 
 // Run f(T{}) with T the handle's kernel scalar.
 template <typename F>
@@ -339,15 +360,15 @@ static peps_status finish_plans(peps_handle* h) {
     gmax = std::max(gmax, (size_t)k.grid * (size_t)k.p.gstride);
   }
   if (gmax > h->gscratch_bytes) {
-    if (h->gscratch) cudaFree(h->gscratch);
+    if (h->gscratch) h_free(h, h->gscratch);
     h->gscratch = nullptr;
     h->gscratch_bytes = 0;
-    e = cudaMalloc(&h->gscratch, gmax);
+    e = h_malloc(h, (void**)&h->gscratch, gmax);
     if (e != cudaSuccess) return fail(h, PEPS_E_WORKSPACE, "scratch allocation failed");
     h->gscratch_bytes = gmax;
   }
   if (!h->ctr) {
-    if (cudaMalloc(&h->ctr, 8 * sizeof(unsigned long long)) != cudaSuccess)
+    if (h_malloc(h, (void**)&h->ctr, 8 * sizeof(unsigned long long)) != cudaSuccess)
       return fail(h, PEPS_E_WORKSPACE, "counter allocation failed");
     cudaMemset(h->ctr, 0, 8 * sizeof(unsigned long long));
   }
@@ -361,8 +382,13 @@ static peps_status finish_plans(peps_handle* h) {
 }
 
 extern "C" peps_status peps_create(peps_handle** out, const peps_config* cfg) {
+  return peps_create_ex(out, cfg, nullptr);
+}
+
+extern "C" peps_status peps_create_ex(peps_handle** out, const peps_config* cfg, const peps_allocator* alloc) {
   if (!out || !cfg) return PEPS_E_ARG;
   *out = nullptr;
+  if (alloc && (!alloc->alloc || !alloc->free)) return PEPS_E_ARG;
   const peps_config c = *cfg;
   if (c.Lx < 2 || c.Ly < 2 || c.Ly > MAX_LY || c.d < 2 || c.d > 4 || c.D < 1 || c.D > 8 || c.chi < c.D ||
       c.chi > 64 || c.max_samples < 1)
@@ -375,6 +401,10 @@ extern "C" peps_status peps_create(peps_handle** out, const peps_config* cfg) {
   if (c.cplx && c.gram == 1) return PEPS_E_UNSUPPORTED;  // the split-BF16 Gram is real only
   peps_handle* h = new peps_handle();
   h->cfg = c;
+  if (alloc) {
+    h->alloc = *alloc;
+    h->has_alloc = true;
+  }
   h->elem = (c.cplx ? 2 : 0) + (c.prec == PEPS_PREC_FP64 ? 0 : 1);
   h->esz = (size_t)((c.prec == PEPS_PREC_FP64) ? 8 : 4) * (c.cplx ? 2 : 1);
   Geo& g = h->g;
@@ -401,17 +431,19 @@ extern "C" peps_status peps_create(peps_handle** out, const peps_config* cfg) {
     peps_destroy(h);
     return st;
   };
-  if (cudaMalloc(&h->Tpad, (size_t)N * c.d * g.sT * h->esz) != cudaSuccess) return bad(PEPS_E_WORKSPACE, "Tpad");
-  if (cudaMalloc(&h->site_off, sizeof(long long) * (N + 1)) != cudaSuccess) return bad(PEPS_E_WORKSPACE, "site_off");
+  if (h_malloc(h, (void**)&h->Tpad, (size_t)N * c.d * g.sT * h->esz) != cudaSuccess) return bad(PEPS_E_WORKSPACE, "Tpad");
+  if (h_malloc(h, (void**)&h->site_off, sizeof(long long) * (N + 1)) != cudaSuccess) return bad(PEPS_E_WORKSPACE, "site_off");
   cudaMemcpy(h->site_off, h->site_off_h.data(), sizeof(long long) * (N + 1), cudaMemcpyHostToDevice);
   const size_t envb = (size_t)c.max_samples * 2 * c.Lx * c.Ly * g.se * h->esz;
-  if (cudaMalloc(&h->envs, envb) != cudaSuccess) return bad(PEPS_E_WORKSPACE, "environment store");
-  if (cudaMalloc(&h->logs, sizeof(double) * (size_t)c.max_samples * 2 * c.Lx) != cudaSuccess) return bad(PEPS_E_WORKSPACE, "logs");
-  if (cudaMalloc(&h->wdisc, sizeof(float) * (size_t)c.max_samples) != cudaSuccess) return bad(PEPS_E_WORKSPACE, "wdisc");
-  if (cudaMalloc(&h->rowout, sizeof(double) * 4 * (size_t)c.max_samples * c.Lx) != cudaSuccess) return bad(PEPS_E_WORKSPACE, "rowout");
-  if (cudaMalloc(&h->pairout, sizeof(double) * 4 * (size_t)c.max_samples * c.Lx) != cudaSuccess) return bad(PEPS_E_WORKSPACE, "pairout");
-  if (cudaMalloc(&h->status_tmp, sizeof(int) * (size_t)c.max_samples) != cudaSuccess) return bad(PEPS_E_WORKSPACE, "status");
-  if (cudaMalloc(&h->ustat, sizeof(int) * (size_t)c.max_samples) != cudaSuccess) return bad(PEPS_E_WORKSPACE, "status");
+  if (h_malloc(h, (void**)&h->envs, envb) != cudaSuccess) return bad(PEPS_E_WORKSPACE, "environment store");
+  if (h_malloc(h, (void**)&h->logs, sizeof(double) * (size_t)c.max_samples * 2 * c.Lx) != cudaSuccess) return bad(PEPS_E_WORKSPACE, "logs");
+  if (h_malloc(h, (void**)&h->wdisc, sizeof(float) * (size_t)c.max_samples) != cudaSuccess) return bad(PEPS_E_WORKSPACE, "wdisc");
+  if (h_malloc(h, (void**)&h->rowout, sizeof(double) * 4 * (size_t)c.max_samples * c.Lx) != cudaSuccess) return bad(PEPS_E_WORKSPACE, "rowout");
+  if (h_malloc(h, (void**)&h->pairout, sizeof(double) * 4 * (size_t)c.max_samples * c.Lx) != cudaSuccess) return bad(PEPS_E_WORKSPACE, "pairout");
+  if (h_malloc(h, (void**)&h->status_tmp, sizeof(int) * (size_t)c.max_samples) != cudaSuccess) return bad(PEPS_E_WORKSPACE, "status");
+  if (h_malloc(h, (void**)&h->ustat, sizeof(int) * (size_t)c.max_samples) != cudaSuccess) return bad(PEPS_E_WORKSPACE, "status");
+  if (h_malloc(h, (void**)&h->sword, sizeof(int)) != cudaSuccess) return bad(PEPS_E_WORKSPACE, "status word");
+  cudaMemset(h->sword, 0, sizeof(int));
   cudaMemset(h->Tpad, 0, (size_t)N * c.d * g.sT * h->esz);
   plan_all(h);
   peps_status st = finish_plans(h);
@@ -430,9 +462,9 @@ extern "C" peps_status peps_destroy(peps_handle* h) {
                   h->gscratch, h->d_tinfo, h->d_ab, h->d_eh, h->d_rowoff, h->d_pairoff, h->d_pij, h->d_pv,
                   h->d_onsite, h->Obar, h->Tm, h->Vm, h->Hm, h->mean, h->ebar, h->yv, h->xv, h->cnt, h->ctr,
                   h->lp_Sp, h->lp_l0, h->lp_l1, h->lp_aux, h->g_hi, h->g_lo, h->bout, h->DL, h->dl_work,
-                  h->dl_status, h->dscratch, h->ustat};
+                  h->dl_status, h->dscratch, h->ustat, h->sword};
   for (void* p : ptrs)
-    if (p) cudaFree(p);
+    if (p) h_free(h, p);
   for (cudaEvent_t e : h->evpool) cudaEventDestroy(e);
   delete h;
   return PEPS_OK;
@@ -464,10 +496,10 @@ static void put(std::vector<char>& k, const V* p, size_t n) {
 }
 
 template <typename V>
-static cudaError_t upload(V** d, const std::vector<V>& h, cudaStream_t s) {
-  if (*d) { cudaFree(*d); *d = nullptr; }
+static cudaError_t upload(peps_handle* hd, V** d, const std::vector<V>& h, cudaStream_t s) {
+  if (*d) { h_free(hd, *d); *d = nullptr; }
   if (h.empty()) return cudaSuccess;
-  cudaError_t e = cudaMalloc(d, sizeof(V) * h.size());
+  cudaError_t e = h_malloc(hd, (void**)d, sizeof(V) * h.size());
   if (e != cudaSuccess) return e;
   return cudaMemcpyAsync(*d, h.data(), sizeof(V) * h.size(), cudaMemcpyHostToDevice, s);
 }
@@ -570,14 +602,14 @@ static peps_status set_hamiltonian(peps_handle* h, const peps_hamiltonian* H, cu
       return fail(h, PEPS_E_ARG, "pair site out of range");
   if (has_on) h->h_onsite.assign(H->onsite_host, H->onsite_host + (size_t)N * d);
   else h->h_onsite.clear();
-  CK(upload(&h->d_tinfo, h->h_tinfo, s), "upload terms");
-  CK(upload(&h->d_ab, h->h_ab, s), "upload terms");
-  CK(upload(&h->d_eh, h->h_eh, s), "upload terms");
-  CK(upload(&h->d_rowoff, h->h_rowoff, s), "upload terms");
-  CK(upload(&h->d_pairoff, h->h_pairoff, s), "upload terms");
-  CK(upload(&h->d_pij, h->h_pij, s), "upload pairs");
-  CK(upload(&h->d_pv, h->h_pv, s), "upload pairs");
-  CK(upload(&h->d_onsite, h->h_onsite, s), "upload onsite");
+  CK(upload(h, &h->d_tinfo, h->h_tinfo, s), "upload terms");
+  CK(upload(h, &h->d_ab, h->h_ab, s), "upload terms");
+  CK(upload(h, &h->d_eh, h->h_eh, s), "upload terms");
+  CK(upload(h, &h->d_rowoff, h->h_rowoff, s), "upload terms");
+  CK(upload(h, &h->d_pairoff, h->h_pairoff, s), "upload terms");
+  CK(upload(h, &h->d_pij, h->h_pij, s), "upload pairs");
+  CK(upload(h, &h->d_pv, h->h_pv, s), "upload pairs");
+  CK(upload(h, &h->d_onsite, h->h_onsite, s), "upload onsite");
   CK(cudaStreamSynchronize(s), "hamiltonian upload");
   h->tt.nterm = nt;
   h->tt.tinfo = h->d_tinfo;
@@ -655,7 +687,8 @@ static peps_status run_eval(peps_handle* h, const peps_hamiltonian* H, const uin
   ts = tstart(h, TC_COMBINE, s);
   CK(launch_combine(g, Ns, S, h->rowout, h->pairout, want_e ? 1 : 0, pairs ? 1 : 0, dg, logabs, phase, eloc, s),
      "combine kernel");
-  tstop(h, ts, s);
+  CK(launch_status_or(st, Ns, h->sword, s), "status word");
+  tstop(h, ts, s, 2);
   return PEPS_OK;
 }
 
@@ -717,20 +750,20 @@ extern "C" peps_status peps_direct_prepare(peps_handle* h, int chi_double, void*
   size_t wb = 0;
   for (int i = 0; i < 8; ++i) wb += al(n8[i] * E);
   if (dlb > h->DL_bytes) {
-    if (h->DL) cudaFree(h->DL);
+    if (h->DL) h_free(h, h->DL);
     h->DL = nullptr;
     h->DL_bytes = 0;
-    if (cudaMalloc(&h->DL, dlb) != cudaSuccess) return fail(h, PEPS_E_WORKSPACE, "double-layer environments");
+    if (h_malloc(h, (void**)&h->DL, dlb) != cudaSuccess) return fail(h, PEPS_E_WORKSPACE, "double-layer environments");
     h->DL_bytes = dlb;
   }
   if (wb > h->dl_work_bytes) {
-    if (h->dl_work) cudaFree(h->dl_work);
+    if (h->dl_work) h_free(h, h->dl_work);
     h->dl_work = nullptr;
     h->dl_work_bytes = 0;
-    if (cudaMalloc(&h->dl_work, wb) != cudaSuccess) return fail(h, PEPS_E_WORKSPACE, "double-layer work buffers");
+    if (h_malloc(h, (void**)&h->dl_work, wb) != cudaSuccess) return fail(h, PEPS_E_WORKSPACE, "double-layer work buffers");
     h->dl_work_bytes = wb;
   }
-  if (!h->dl_status && cudaMalloc(&h->dl_status, sizeof(int)) != cudaSuccess)
+  if (!h->dl_status && h_malloc(h, (void**)&h->dl_status, sizeof(int)) != cudaSuccess)
     return fail(h, PEPS_E_WORKSPACE, "status");
   // the sampler's buffer plan: the row step's buffers, then the configuration, two E^u rows,
   // the candidates, the right partials, the contraction temporaries and one ket site (and its
@@ -766,10 +799,10 @@ extern "C" peps_status peps_direct_prepare(peps_handle* h, int chi_double, void*
   k.grid = h->nsm * occ;
   const size_t ab = (size_t)k.grid * k.p.gstride;
   if (ab > h->dscratch_bytes) {
-    if (h->dscratch) cudaFree(h->dscratch);
+    if (h->dscratch) h_free(h, h->dscratch);
     h->dscratch = nullptr;
     h->dscratch_bytes = 0;
-    if (cudaMalloc(&h->dscratch, ab) != cudaSuccess) return fail(h, PEPS_E_WORKSPACE, "direct-sampling arena");
+    if (h_malloc(h, (void**)&h->dscratch, ab) != cudaSuccess) return fail(h, PEPS_E_WORKSPACE, "direct-sampling arena");
     h->dscratch_bytes = ab;
   }
   k.p.gbase = h->dscratch;
@@ -810,7 +843,8 @@ extern "C" peps_status peps_direct_sample(peps_handle* h, uint8_t* S_dev, int Ns
                             S_dev, Ns, seed, draw, logp_dev, st, s);
   });
   if (e != cudaSuccess) return cuda_fail(h, e, "direct-sampling kernel");
-  tstop(h, ts, s);
+  CK(launch_status_or(st, Ns, h->sword, s), "status word");
+  tstop(h, ts, s, 2);
   return PEPS_OK;
 }
 
@@ -856,10 +890,10 @@ extern "C" peps_status peps_local_energy_bound(peps_handle* h, const peps_hamilt
   const int nt = std::max(h->tt.nterm, 1);
   const size_t need = (size_t)h->cfg.max_samples * nt * 2;
   if (need > h->bout_cap) {
-    if (h->bout) cudaFree(h->bout);
+    if (h->bout) h_free(h, h->bout);
     h->bout = nullptr;
     h->bout_cap = 0;
-    if (cudaMalloc(&h->bout, need * sizeof(double)) != cudaSuccess) return fail(h, PEPS_E_WORKSPACE, "bound buffer");
+    if (h_malloc(h, (void**)&h->bout, need * sizeof(double)) != cudaSuccess) return fail(h, PEPS_E_WORKSPACE, "bound buffer");
     h->bout_cap = need;
   }
   const KPlan& ke = h->kp[0];
@@ -883,7 +917,8 @@ extern "C" peps_status peps_local_energy_bound(peps_handle* h, const peps_hamilt
   tstop(h, ts, s);
   ts = tstart(h, TC_COMBINE, s);
   CK(launch_bound_combine(h->g, Ns, nt, S_dev, h->bout, h->dg, eloc_dev, s), "bound combine kernel");
-  tstop(h, ts, s);
+  CK(launch_status_or(st, Ns, h->sword, s), "status word");
+  tstop(h, ts, s, 2);
   return PEPS_OK;
 }
 
@@ -921,7 +956,8 @@ extern "C" peps_status peps_sample(peps_handle* h, int move, uint8_t* S_dev, int
   } else {
     h->rs_gen = -1;
   }
-  tstop(h, ts, s);
+  CK(launch_status_or(st, Ns, h->sword, s), "status word");
+  tstop(h, ts, s, 2);
   return PEPS_OK;
 }
 
@@ -933,22 +969,22 @@ static peps_status ensure_minsr(peps_handle* h, int Ns, long long Np) {
   if (h->ms_cap >= n && h->ms_np >= Np) return PEPS_OK;
   double** bufs[] = {&h->Obar, &h->Tm, &h->Vm, &h->Hm, &h->mean, &h->ebar, &h->yv, &h->xv, &h->cnt};
   for (double** b : bufs)
-    if (*b) { cudaFree(*b); *b = nullptr; }
+    if (*b) { h_free(h, *b); *b = nullptr; }
   const size_t nn = (size_t)n * n;
   // Obar holds n rows (the capacity): a later call with an even Ns up to n reuses it
-  if (cudaMalloc(&h->Obar, sizeof(double) * (size_t)n * Np) != cudaSuccess ||
-      cudaMalloc(&h->Tm, sizeof(double) * nn) != cudaSuccess || cudaMalloc(&h->Vm, sizeof(double) * nn) != cudaSuccess ||
-      cudaMalloc(&h->Hm, sizeof(double) * nn) != cudaSuccess ||
-      cudaMalloc(&h->mean, sizeof(double) * (size_t)Np) != cudaSuccess ||
-      cudaMalloc(&h->ebar, sizeof(double) * n) != cudaSuccess || cudaMalloc(&h->yv, sizeof(double) * n) != cudaSuccess ||
-      cudaMalloc(&h->xv, sizeof(double) * n) != cudaSuccess || cudaMalloc(&h->cnt, sizeof(double) * 8) != cudaSuccess)
+  if (h_malloc(h, (void**)&h->Obar, sizeof(double) * (size_t)n * Np) != cudaSuccess ||
+      h_malloc(h, (void**)&h->Tm, sizeof(double) * nn) != cudaSuccess || h_malloc(h, (void**)&h->Vm, sizeof(double) * nn) != cudaSuccess ||
+      h_malloc(h, (void**)&h->Hm, sizeof(double) * nn) != cudaSuccess ||
+      h_malloc(h, (void**)&h->mean, sizeof(double) * (size_t)Np) != cudaSuccess ||
+      h_malloc(h, (void**)&h->ebar, sizeof(double) * n) != cudaSuccess || h_malloc(h, (void**)&h->yv, sizeof(double) * n) != cudaSuccess ||
+      h_malloc(h, (void**)&h->xv, sizeof(double) * n) != cudaSuccess || h_malloc(h, (void**)&h->cnt, sizeof(double) * 16) != cudaSuccess)
     return fail(h, PEPS_E_WORKSPACE, "MinSR workspace allocation failed");
   if (h->cfg.gram == 1 || h->cfg.gram == 2) {
-    if (h->g_hi) { cudaFree(h->g_hi); h->g_hi = nullptr; }
-    if (h->g_lo) { cudaFree(h->g_lo); h->g_lo = nullptr; }
+    if (h->g_hi) { h_free(h, h->g_hi); h->g_hi = nullptr; }
+    if (h->g_lo) { h_free(h, h->g_lo); h->g_lo = nullptr; }
     const size_t e = (h->cfg.gram == 1) ? (size_t)gram_tc_pad_rows(Ns) * (size_t)gram_tc_pad_k(h->Np) * 2
                                         : (size_t)n * (size_t)Np * sizeof(float);  // the capacity, n rows
-    if (cudaMalloc(&h->g_hi, e) != cudaSuccess || cudaMalloc(&h->g_lo, e) != cudaSuccess)
+    if (h_malloc(h, (void**)&h->g_hi, e) != cudaSuccess || h_malloc(h, (void**)&h->g_lo, e) != cudaSuccess)
       return fail(h, PEPS_E_WORKSPACE, "Gram workspace allocation failed");
   }
   h->ms_cap = n;
@@ -956,121 +992,233 @@ static peps_status ensure_minsr(peps_handle* h, int Ns, long long Np) {
   return PEPS_OK;
 }
 
+// MinSR scratch slots (h->cnt, 16 doubles): 0 factor breakdown (int), 2 weight sum, 3 FP64
+// fallback flag of the mixed solve (int), 4 tensor-core Gram wait timeout (int), 6-7 residual
+// norms, 8-9 Jacobi rotation counters (unsigned long long)
+
+// T = A A^T (Ns x Ns, written to T with leading dimension ld) in the handle's Gram mode
+static peps_status minsr_gram_into(peps_handle* h, const double* A, int Ns, long long K, double* T, int ld,
+                                   bool mirror, cudaStream_t s) {
+  int* gerr = (int*)(h->cnt + 4);
+  const int ts = tstart(h, TC_GRAM, s);
+  if (h->cfg.gram == 1) {
+    CK(launch_gram_tc(A, Ns, K, h->g_hi, h->g_lo, T, ld, mirror, gerr, s), "tensor-core Gram");
+    tstop(h, ts, s, mirror ? 3 : 2);
+  } else if (h->cfg.gram == 2) {
+    CK(launch_gram_ff(A, Ns, K, (float*)h->g_hi, (float*)h->g_lo, T, ld, s), "float-float Gram");
+    tstop(h, ts, s, 2);
+  } else {
+    CK(launch_gram(A, Ns, K, T, ld, s), "Gram");
+    tstop(h, ts, s);
+  }
+  return PEPS_OK;
+}
+
+// x = (T + lambda)^+ ebar on the handle's workspace: h->Tm (n x n, n = Ns rounded up to even, the
+// Gram written, padding zero), h->ebar (n, padding zero) -> h->xv; info_dev as minsr_step
+static peps_status minsr_solve_core(peps_handle* h, int Ns, double lambda, double rcond, double* info_dev,
+                                    cudaStream_t s) {
+  const int n = Ns + (Ns & 1);
+  int* need64 = (int*)(h->cnt + 3);
+  cudaError_t e = cudaSuccess;
+  if (rcond > 0.0) {
+    // eigendecomposition with the pseudo-inverse cutoff: one cooperative launch, the sweep count
+    // written to info[3] on the device
+    int ts = tstart(h, TC_EIG, s);
+    CK(jacobi_eig(h->Tm, h->Vm, n, (unsigned long long*)(h->cnt + 8), h->Hm, info_dev + 3, 40, s), "Jacobi");
+    tstop(h, ts, s, 1);
+    ts = tstart(h, TC_MINSR, s);
+    CK(launch_minsr_apply(h->Tm, h->Vm, h->ebar, n, Ns, lambda, rcond, h->yv, h->xv, info_dev, s), "MinSR apply");
+    tstop(h, ts, s, 3);
+  } else {
+    // nothing is cut: (T + lambda)^+ = (T + lambda)^-1, solved by Cholesky.  The mixed solve's
+    // FP64 fallback is enqueued behind a device flag, so no host decision is needed.
+    const int ts = tstart(h, TC_EIG, s);
+    long long nl = 0;
+    if (h->cfg.solve == 1) {
+      nl = chol_solve_mixed(h->Tm, (float*)h->Vm, n, Ns, lambda, h->ebar, h->xv, h->yv, h->cnt + 6, h->Hm, 4,
+                            (int*)h->cnt, info_dev, need64, s, &e);
+      if (e != cudaSuccess) return cuda_fail(h, e, "Cholesky");
+      nl += chol_solve(h->Tm, n, Ns, lambda, h->ebar, h->xv, (int*)h->cnt, info_dev, need64, s, &e);
+    } else {
+      nl = chol_solve(h->Tm, n, Ns, lambda, h->ebar, h->xv, (int*)h->cnt, info_dev, nullptr, s, &e);
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "Cholesky");
+    tstop(h, ts, s, nl);
+  }
+  return PEPS_OK;
+}
+
+static peps_status check_minsr_args(peps_handle* h, int Ns, double lambda, double rcond) {
+  if (Ns < 2) return fail(h, PEPS_E_ARG, "MinSR needs at least two samples");
+  if (!(lambda > 0.0 || rcond > 0.0) || lambda < 0.0 || rcond < 0.0)
+    return fail(h, PEPS_E_ARG, "MinSR needs lambda > 0 or rcond > 0");
+  return PEPS_OK;
+}
+
 extern "C" peps_status minsr_step(peps_handle* h, const void* O_dev, const double* eloc_dev, const double* w_dev,
                                   int Ns, double lambda, double rcond, double tau, double* dtheta_dev,
                                   double* info_dev, void* stream) {
   if (!h) return PEPS_E_ARG;
-  if (!O_dev || !eloc_dev || !dtheta_dev || !info_dev || Ns < 2) return fail(h, PEPS_E_ARG, "bad MinSR argument");
-  if (!(lambda > 0.0 || rcond > 0.0) || lambda < 0.0 || rcond < 0.0)
-    return fail(h, PEPS_E_ARG, "MinSR needs lambda > 0 or rcond > 0");
+  if (!O_dev || !eloc_dev || !dtheta_dev || !info_dev) return fail(h, PEPS_E_ARG, "bad MinSR argument");
+  peps_status ps = check_minsr_args(h, Ns, lambda, rcond);
+  if (ps != PEPS_OK) return ps;
   // a complex handle solves the real embedding (2 Ns rows, 2 N_p columns), see launch_center_cplx
   const bool cx = h->cfg.cplx != 0;
   const int Ns_c = Ns;
   const long long Np_c = h->Np;
   if (cx) Ns = 2 * Ns;
   const long long Np = cx ? 2 * h->Np : h->Np;
-  peps_status ps = ensure_minsr(h, Ns, Np);
+  ps = ensure_minsr(h, Ns, Np);
   if (ps != PEPS_OK) return ps;
   cudaStream_t s = (cudaStream_t)stream;
   const int n = Ns + (Ns & 1);
+  double* wsum = h->cnt + 2;
+  int* gerr = (int*)(h->cnt + 4);
   int ts = tstart(h, TC_MINSR, s);
   CK(cudaMemsetAsync(h->ebar, 0, sizeof(double) * n, s), "memset");
+  CK(cudaMemsetAsync(gerr, 0, sizeof(int), s), "memset");
   cudaError_t e = dispatch_elem(h, [&](auto z) {
     using T = decltype(z);
     using R = typename Scal<T>::R;
     if constexpr (Scal<T>::complex) {
-      const cudaError_t e1 = launch_center_cplx<R>((const R*)O_dev, w_dev, Ns_c, Np_c, h->Obar, s);
+      const cudaError_t e1 = launch_center_cplx<R>((const R*)O_dev, w_dev, Ns_c, Np_c, h->Obar, wsum, s);
       return e1 != cudaSuccess ? e1 : launch_center_e_cplx(eloc_dev, w_dev, Ns_c, h->ebar, s);
     } else {
-      const cudaError_t e1 = launch_center<T>((const T*)O_dev, w_dev, Ns, Np, h->mean, h->Obar, s);
+      const cudaError_t e1 = launch_center<T>((const T*)O_dev, w_dev, Ns, Np, h->mean, h->Obar, wsum, s);
       return e1 != cudaSuccess ? e1 : launch_center_e(eloc_dev, w_dev, Ns, h->ebar, s);
     }
   });
   if (e != cudaSuccess) return cuda_fail(h, e, "centre O and E_loc");
   CK(cudaMemsetAsync(h->Tm, 0, sizeof(double) * (size_t)n * n, s), "memset");
-  tstop(h, ts, s, w_dev ? 3 : 2);
-  ts = tstart(h, TC_GRAM, s);
-  if (h->cfg.gram == 1) {
-    CK(cudaMemsetAsync(h->cnt + 4, 0, sizeof(int), s), "memset");
-    CK(launch_gram_tc(h->Obar, Ns, Np, h->g_hi, h->g_lo, h->Tm, n, rcond > 0.0, (int*)(h->cnt + 4), s),
-       "tensor-core Gram");
-    tstop(h, ts, s, rcond > 0.0 ? 3 : 2);
-  } else if (h->cfg.gram == 2) {
-    CK(launch_gram_ff(h->Obar, Ns, Np, (float*)h->g_hi, (float*)h->g_lo, h->Tm, n, s), "float-float Gram");
-    tstop(h, ts, s, 2);
-  } else {
-    CK(launch_gram(h->Obar, Ns, Np, h->Tm, n, s), "Gram");
-    tstop(h, ts, s);
-  }
-  double sw = -1.0;
-  if (rcond > 0.0) {
-    // eigendecomposition with the pseudo-inverse cutoff
-    ts = tstart(h, TC_EIG, s);
-    const int sweeps = jacobi_eig(h->Tm, h->Vm, n, h->cnt, nullptr, h->Hm, s, 40, &e);
-    if (e != cudaSuccess) return cuda_fail(h, e, "Jacobi");
-    tstop(h, ts, s, 1 + (long long)(sweeps > 0 ? sweeps : 40) * (n - 1));
-    ts = tstart(h, TC_MINSR, s);
-    CK(launch_minsr_apply(h->Tm, h->Vm, h->ebar, n, Ns, lambda, rcond, h->yv, h->xv, info_dev, s), "MinSR apply");
-    tstop(h, ts, s, 3);
-    sw = (double)sweeps;
-  } else {
-    // nothing is cut: (T + lambda)^+ = (T + lambda)^-1, solved by Cholesky
-    ts = tstart(h, TC_EIG, s);
-    bool fp64 = (h->cfg.solve != 1);
-    long long nl = 0;
-    if (!fp64) {
-      nl = chol_solve_mixed(h->Tm, (float*)h->Vm, n, Ns, lambda, h->ebar, h->xv, h->yv, h->cnt + 6, 4, (int*)h->cnt,
-                            info_dev, s, &e);
-      if (e != cudaSuccess) return cuda_fail(h, e, "Cholesky");
-      // the FP32 factor must exist and the refined residual be small, else factor in FP64
-      double rn[2] = {0.0, 0.0};
-      int bad = 0;
-      CK(cudaMemcpyAsync(rn, h->cnt + 6, sizeof(rn), cudaMemcpyDeviceToHost, s), "read residual");
-      CK(cudaMemcpyAsync(&bad, h->cnt, sizeof(int), cudaMemcpyDeviceToHost, s), "read factor status");
-      CK(cudaStreamSynchronize(s), "mixed solve sync");
-      fp64 = bad || !(rn[0] <= 1e-20 * rn[1]);
-    }
-    if (fp64) {
-      nl += chol_solve(h->Tm, n, Ns, lambda, h->ebar, h->xv, (int*)h->cnt, info_dev, s, &e);
-      if (e != cudaSuccess) return cuda_fail(h, e, "Cholesky");
-      if (h->cfg.solve == 1) {
-        const double zero = 0.0;
-        CK(cudaMemcpyAsync(info_dev + 2, &zero, sizeof(double), cudaMemcpyHostToDevice, s), "info");
-      }
-    }
-    tstop(h, ts, s, nl);
-  }
+  tstop(h, ts, s, (w_dev ? 3 : 2) + 2);
+  if ((ps = minsr_gram_into(h, h->Obar, Ns, Np, h->Tm, n, rcond > 0.0, s)) != PEPS_OK) return ps;
+  if ((ps = minsr_solve_core(h, Ns, lambda, rcond, info_dev, s)) != PEPS_OK) return ps;
   ts = tstart(h, TC_MINSR, s);
   CK(launch_obar_t_x(h->Obar, h->xv, Ns, Np, tau, cx ? h->mean : dtheta_dev, s), "Obar^T x");
   if (cx) CK(launch_unembed(h->mean, Np_c, dtheta_dev, s), "dtheta");
-  tstop(h, ts, s, 1);
-  CK(cudaMemcpyAsync(info_dev + 3, &sw, sizeof(double), cudaMemcpyHostToDevice, s), "info");
-  CK(cudaStreamSynchronize(s), "MinSR sync");
-  if (h->cfg.gram == 1) {
-    int gerr = 0;
-    CK(cudaMemcpy(&gerr, h->cnt + 4, sizeof(int), cudaMemcpyDeviceToHost), "read Gram status");
-    if (gerr) return fail(h, PEPS_E_CUDA, "tensor-core Gram: a pipeline wait timed out");
+  // a breakdown or a Gram timeout zeroes dtheta on the device and is reported through the
+  // status word (peps_last_status)
+  CK(launch_minsr_finish(info_dev, h->cfg.gram == 1 ? gerr : nullptr, dtheta_dev, cx ? 2 * Np_c : Np, cx ? 1 : 0,
+                         rcond > 0.0 ? 0 : 1, h->sword, s),
+     "MinSR finish");
+  tstop(h, ts, s, cx ? 4 : 3);
+  return PEPS_OK;
+}
+
+// ---- sample-sharded MinSR pieces ---------------------------------------------------------
+static peps_status check_sharded(peps_handle* h) {
+  if (!h) return PEPS_E_ARG;
+  if (h->cfg.cplx) return fail(h, PEPS_E_UNSUPPORTED, "sample-sharded MinSR: real PEPS only");
+  return PEPS_OK;
+}
+
+extern "C" peps_status minsr_partial_sums(peps_handle* h, const void* O_dev, const double* eloc_dev,
+                                          const double* w_dev, int Ns, double* sums_dev, void* stream) {
+  peps_status ps = check_sharded(h);
+  if (ps != PEPS_OK) return ps;
+  if (Ns < 0 || !sums_dev || (Ns > 0 && (!O_dev || !eloc_dev))) return fail(h, PEPS_E_ARG, "bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int ts = tstart(h, TC_MINSR, s);
+  cudaError_t e = (h->esz == 8) ? launch_partial_sums<double>((const double*)O_dev, w_dev, eloc_dev, Ns, h->Np, sums_dev, s)
+                                : launch_partial_sums<float>((const float*)O_dev, w_dev, eloc_dev, Ns, h->Np, sums_dev, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "partial sums");
+  tstop(h, ts, s, 2);
+  return PEPS_OK;
+}
+
+extern "C" peps_status minsr_center_rows(peps_handle* h, const void* O_dev, const double* eloc_dev,
+                                         const double* w_dev, int Ns, const double* gsums_dev, double* Obar_dev,
+                                         double* ebar_dev, void* stream) {
+  peps_status ps = check_sharded(h);
+  if (ps != PEPS_OK) return ps;
+  if (Ns < 0 || !gsums_dev || (Ns > 0 && (!O_dev || !eloc_dev || !Obar_dev || !ebar_dev)))
+    return fail(h, PEPS_E_ARG, "bad argument");
+  if (Ns == 0) return PEPS_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int ts = tstart(h, TC_MINSR, s);
+  cudaError_t e = (h->esz == 8)
+                      ? launch_center_global<double>((const double*)O_dev, w_dev, eloc_dev, Ns, h->Np, gsums_dev,
+                                                     Obar_dev, ebar_dev, s)
+                      : launch_center_global<float>((const float*)O_dev, w_dev, eloc_dev, Ns, h->Np, gsums_dev,
+                                                    Obar_dev, ebar_dev, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "centre rows");
+  tstop(h, ts, s, 2);
+  return PEPS_OK;
+}
+
+extern "C" peps_status minsr_gram(peps_handle* h, const double* A_dev, int Ns, long long K, double* T_dev,
+                                  void* stream) {
+  peps_status ps = check_sharded(h);
+  if (ps != PEPS_OK) return ps;
+  if (Ns < 1 || K < 0 || !A_dev || !T_dev) return fail(h, PEPS_E_ARG, "bad argument");
+  if ((ps = ensure_minsr(h, Ns, K > 0 ? K : 1)) != PEPS_OK) return ps;
+  cudaStream_t s = (cudaStream_t)stream;
+  int* gerr = (int*)(h->cnt + 4);
+  CK(cudaMemsetAsync(gerr, 0, sizeof(int), s), "memset");
+  CK(cudaMemsetAsync(T_dev, 0, sizeof(double) * (size_t)Ns * Ns, s), "memset");
+  if (K == 0) return PEPS_OK;
+  if ((ps = minsr_gram_into(h, A_dev, Ns, K, T_dev, Ns, true, s)) != PEPS_OK) return ps;
+  if (h->cfg.gram == 1) CK(launch_flag_or(gerr, PEPS_SW_GRAM_TIMEOUT, h->sword, s), "status word");
+  return PEPS_OK;
+}
+
+extern "C" peps_status minsr_solve(peps_handle* h, const double* T_dev, const double* ebar_dev, int Ns, double lambda,
+                                   double rcond, double* x_dev, double* info_dev, void* stream) {
+  peps_status ps = check_sharded(h);
+  if (ps != PEPS_OK) return ps;
+  if (!T_dev || !ebar_dev || !x_dev || !info_dev) return fail(h, PEPS_E_ARG, "bad argument");
+  if ((ps = check_minsr_args(h, Ns, lambda, rcond)) != PEPS_OK) return ps;
+  if ((ps = ensure_minsr(h, Ns, h->ms_np > 0 ? h->ms_np : 1)) != PEPS_OK) return ps;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int n = Ns + (Ns & 1);
+  int ts = tstart(h, TC_MINSR, s);
+  CK(cudaMemsetAsync(h->Tm, 0, sizeof(double) * (size_t)n * n, s), "memset");
+  CK(cudaMemcpy2DAsync(h->Tm, sizeof(double) * n, T_dev, sizeof(double) * Ns, sizeof(double) * Ns, Ns,
+                       cudaMemcpyDeviceToDevice, s), "copy T");
+  CK(cudaMemsetAsync(h->ebar, 0, sizeof(double) * n, s), "memset");
+  CK(cudaMemcpyAsync(h->ebar, ebar_dev, sizeof(double) * Ns, cudaMemcpyDeviceToDevice, s), "copy ebar");
+  tstop(h, ts, s, 4);
+  if ((ps = minsr_solve_core(h, Ns, lambda, rcond, info_dev, s)) != PEPS_OK) return ps;
+  ts = tstart(h, TC_MINSR, s);
+  CK(cudaMemcpyAsync(x_dev, h->xv, sizeof(double) * Ns, cudaMemcpyDeviceToDevice, s), "copy x");
+  CK(launch_minsr_finish(info_dev, nullptr, x_dev, Ns, 0, rcond > 0.0 ? 0 : 1, h->sword, s), "MinSR finish");
+  tstop(h, ts, s, 3);
+  return PEPS_OK;
+}
+
+extern "C" peps_status minsr_project(const double* A_dev, const double* x_dev, int Ns, long long K, double tau,
+                                     double* dtheta_dev, void* stream) {
+  if (Ns < 0 || K < 0 || (K > 0 && (!A_dev || !x_dev || !dtheta_dev))) return PEPS_E_ARG;
+  if (K == 0) return PEPS_OK;
+  if (launch_obar_t_x(A_dev, x_dev, Ns, K, tau, dtheta_dev, (cudaStream_t)stream) != cudaSuccess) return PEPS_E_CUDA;
+  return PEPS_OK;
+}
+
+extern "C" peps_status peps_last_status(peps_handle* h, int32_t* word_host, void* stream) {
+  if (!h) return PEPS_E_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  int w = 0;
+  CK(cudaMemcpyAsync(&w, h->sword, sizeof(int), cudaMemcpyDeviceToHost, s), "read status word");
+  CK(cudaMemsetAsync(h->sword, 0, sizeof(int), s), "clear status word");
+  CK(cudaStreamSynchronize(s), "status word sync");
+  if (word_host) *word_host = w;
+  if (w & PEPS_SW_GRAM_TIMEOUT) return fail(h, PEPS_E_CUDA, "tensor-core Gram: a pipeline wait timed out; dtheta set to zero");
+  if (w & PEPS_SW_MINSR_BREAKDOWN) {
+    h->err = "T + lambda is not positive definite in floating point; dtheta set to zero";
+    return PEPS_W_NUMERIC;
   }
-  if (cx) {
-    // the embedding counts every eigenvalue of T twice
-    double i0 = 0.0;
-    CK(cudaMemcpy(&i0, info_dev, sizeof(double), cudaMemcpyDeviceToHost), "read info");
-    if (i0 > 0.0) {
-      i0 *= 0.5;
-      CK(cudaMemcpy(info_dev, &i0, sizeof(double), cudaMemcpyHostToDevice), "write info");
-    }
+  if (w) {
+    h->err = "per-sample status bits set";
+    return PEPS_W_NUMERIC;
   }
-  if (rcond == 0.0) {
-    // a factorisation that broke down gives no usable dtheta: return zero and warn
-    double i0 = 0.0;
-    CK(cudaMemcpy(&i0, info_dev, sizeof(double), cudaMemcpyDeviceToHost), "read info");
-    if (i0 < 0.0) {
-      CK(cudaMemsetAsync(dtheta_dev, 0, sizeof(double) * (size_t)Np, s), "zero dtheta");
-      CK(cudaStreamSynchronize(s), "MinSR sync");
-      h->err = "T + lambda is not positive definite in floating point; dtheta set to zero";
-      return PEPS_W_NUMERIC;
-    }
-  }
+  return PEPS_OK;
+}
+
+extern "C" peps_status peps_status_weights(const int32_t* status_dev, int Ns, int mask, double* w_dev, void* stream) {
+  if (Ns < 0 || (Ns > 0 && (!status_dev || !w_dev))) return PEPS_E_ARG;
+  if (launch_status_weights((const int*)status_dev, Ns, mask, w_dev, (cudaStream_t)stream) != cudaSuccess)
+    return PEPS_E_CUDA;
   return PEPS_OK;
 }
 
@@ -1113,12 +1261,14 @@ extern "C" peps_status peps_autotune(peps_handle* h, const peps_hamiltonian* H, 
   auto cleanup = [&]() {
     void* ps[] = {la, ph, el, O, S2, acc};
     for (void* q : ps)
-      if (q) cudaFree(q);
+      if (q) h_free(h, q);
   };
-  if (cudaMalloc(&la, sizeof(double) * Ns) != cudaSuccess || cudaMalloc(&ph, sizeof(double) * Ns) != cudaSuccess ||
-      cudaMalloc(&el, sizeof(double) * 2 * Ns) != cudaSuccess ||
-      cudaMalloc(&O, (size_t)Ns * h->Np * h->esz) != cudaSuccess || cudaMalloc(&S2, (size_t)Ns * N) != cudaSuccess ||
-      cudaMalloc(&acc, sizeof(long long) * Ns) != cudaSuccess) {
+  if (h_malloc(h, (void**)&la, sizeof(double) * Ns) != cudaSuccess ||
+      h_malloc(h, (void**)&ph, sizeof(double) * Ns) != cudaSuccess ||
+      h_malloc(h, (void**)&el, sizeof(double) * 2 * Ns) != cudaSuccess ||
+      h_malloc(h, &O, (size_t)Ns * h->Np * h->esz) != cudaSuccess ||
+      h_malloc(h, (void**)&S2, (size_t)Ns * N) != cudaSuccess ||
+      h_malloc(h, (void**)&acc, sizeof(long long) * Ns) != cudaSuccess) {
     cleanup();
     return fail(h, PEPS_E_WORKSPACE, "autotune scratch allocation failed");
   }
@@ -1170,23 +1320,174 @@ extern "C" peps_status peps_autotune(peps_handle* h, const peps_hamiltonian* H, 
 struct peps_batch {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  std::vector<cudaStream_t> branches;
-  std::vector<cudaEvent_t> events;
+  void* inst_dev[4] = {nullptr, nullptr, nullptr, nullptr};  // BatchInst<T> arrays, one per scalar type
+  char* arena[4] = {nullptr, nullptr, nullptr, nullptr};
+  unsigned long long* next = nullptr;                        // 4 queue counters
+  size_t budget = 0;
   std::string err;
 };
-
 static void batch_free(peps_batch* b) {
   if (!b) return;
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
-  for (cudaEvent_t e : b->events) cudaEventDestroy(e);
-  for (cudaStream_t st : b->branches) cudaStreamDestroy(st);
+  for (int k = 0; k < 4; ++k) {
+    if (b->inst_dev[k]) cudaFree(b->inst_dev[k]);
+    if (b->arena[k]) cudaFree(b->arena[k]);
+  }
+  if (b->next) cudaFree(b->next);
   delete b;
 }
 
-extern "C" peps_status peps_batch_create(peps_batch** out, const peps_batch_item* items, int n, int nbranch,
-                                         void* stream) {
-  if (!out || !items || n < 1 || nbranch < 1) return PEPS_E_ARG;
+// The environment, one-row and two-row plans of handle h at a shared-memory budget per CTA
+// (the handle's own plans are left as they were).
+static void plans_at(peps_handle* h, size_t budget, Plan* pe, Plan* pr, Plan* pq, size_t smem[3]) {
+  KPlan kp[4] = {h->kp[0], h->kp[1], h->kp[2], h->kp[3]};
+  KPlan kb = h->kb;
+  size_t bud[4] = {h->budget[0], h->budget[1], h->budget[2], h->budget[3]};
+  h->budget[0] = h->budget[1] = h->budget[2] = budget;
+  plan_all(h);
+  *pe = h->kp[0].p;
+  *pr = h->kp[1].p;
+  *pq = h->kp[2].p;
+  for (int c = 0; c < 3; ++c) smem[c] = h->kp[c].smem;
+  for (int c = 0; c < 4; ++c) { h->kp[c] = kp[c]; h->budget[c] = bud[c]; }
+  h->kb = kb;
+}
+
+// What the graph records for one scalar type's group: the queue launch and the buffers it zeroes
+// and reports into.
+struct BatchGroup {
+  int elem = -1;
+  size_t smem = 0;
+  int grid = 0;
+  int ninst = 0;
+  long long nitems = 0;
+  std::vector<int*> status;
+  std::vector<float*> wdisc;
+  std::vector<int> ns;
+  std::vector<int*> sword;
+};
+
+// Plans, allocations and the descriptor upload of one group (before the capture: nothing here
+// may run while a stream is being captured).
+template <typename T>
+static peps_status batch_prepare(peps_batch* b, const peps_batch_item* items, const std::vector<int>& idx, int elem,
+                                 size_t budget, int nsm, BatchGroup* grp) {
+  std::vector<BatchInst<T>> inst(idx.size());
+  size_t smem = 0, stride = 0;
+  long long item0 = 0;
+  grp->elem = elem;
+  for (size_t k = 0; k < idx.size(); ++k) {
+    const peps_batch_item& it = items[idx[k]];
+    peps_handle* h = it.h;
+    BatchInst<T>& q = inst[k];
+    size_t sm[3];
+    plans_at(h, budget, &q.pe, &q.pr, &q.pq, sm);
+    smem = std::max(smem, std::max(sm[0], std::max(sm[1], sm[2])));
+    stride = std::max(stride, (size_t)std::max(q.pe.gstride, std::max(q.pr.gstride, q.pq.gstride)));
+    const bool want_e = it.eloc_dev != nullptr;
+    q.g = h->g;
+    q.Tpad = (const T*)h->Tpad;
+    q.S = it.S_dev;
+    q.envs = (T*)h->envs;
+    q.logs = h->logs;
+    q.wdisc = h->wdisc;
+    q.O = (T*)it.O_dev;
+    q.site_off = h->site_off;
+    q.Np = h->Np;
+    q.tt = want_e ? h->tt : TermTab{};
+    q.dg = want_e ? h->dg : DiagTab{};
+    q.rowout = h->rowout;
+    q.pairout = h->pairout;
+    q.status = it.status_dev ? (int*)it.status_dev : h->status_tmp;
+    q.logabs = it.logabs_dev;
+    q.phase = it.phase_dev;
+    q.eloc = it.eloc_dev;
+    q.want_e = want_e ? 1 : 0;
+    q.pairs = (want_e && h->n_pair_terms > 0) ? 1 : 0;
+    q.sides = (want_e || it.O_dev) ? 3 : 1;
+    q.Ns = it.Ns;
+    q.item0 = item0;
+    item0 += it.Ns;
+    grp->status.push_back(q.status);
+    grp->wdisc.push_back(q.wdisc);
+    grp->ns.push_back(it.Ns);
+    grp->sword.push_back(h->sword);
+  }
+  // one CTA per (SM x resident blocks) at the batch's shared memory; every CTA its arena slice.
+  // The kernel's dynamic shared-memory limit is only ever raised (other batches may be recorded
+  // with larger budgets); a budget above what an SM offers is a shape error, and its CUDA error
+  // is cleared so that later calls do not report it.
+  {
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    size_t& cur = g_attr_max[{1000 + elem, 0}];
+    if (smem > cur) {
+      if (kattr_batch<T>(smem, nullptr, 0) != cudaSuccess) {
+        cudaGetLastError();
+        b->err = "batch kernel: shared memory above the SM's limit";
+        return PEPS_E_SHAPE;
+      }
+      cur = smem;
+    }
+  }
+  int occ = 0;
+  if (kattr_batch<T>(0, &occ, smem) != cudaSuccess || occ < 1) {
+    cudaGetLastError();
+    b->err = "batch kernel does not fit on an SM";
+    return PEPS_E_SHAPE;
+  }
+  const int grid = nsm * occ;
+  stride = std::max<size_t>(stride, 256);
+  if (cudaMalloc(&b->arena[elem], (size_t)grid * stride) != cudaSuccess) {
+    cudaGetLastError();
+    return PEPS_E_WORKSPACE;
+  }
+  for (auto& q : inst) {
+    for (Plan* pl : {&q.pe, &q.pr, &q.pq}) {
+      pl->gbase = b->arena[elem];
+      pl->gstride = stride;
+    }
+  }
+  if (cudaMalloc(&b->inst_dev[elem], sizeof(BatchInst<T>) * inst.size()) != cudaSuccess) {
+    cudaGetLastError();
+    return PEPS_E_WORKSPACE;
+  }
+  if (cudaMemcpy(b->inst_dev[elem], inst.data(), sizeof(BatchInst<T>) * inst.size(), cudaMemcpyHostToDevice) !=
+      cudaSuccess)
+    return PEPS_E_CUDA;
+  grp->smem = smem;
+  grp->grid = grid;
+  grp->ninst = (int)inst.size();
+  grp->nitems = item0;
+  return PEPS_OK;
+}
+
+// Recorded into the graph: zero the queue counter and what the kernels accumulate into, run the
+// queue, then fold the status bits into every handle's status word.
+template <typename T>
+static peps_status batch_record(peps_batch* b, const BatchGroup& grp, cudaStream_t s) {
+  if (cudaMemsetAsync(b->next + grp.elem, 0, sizeof(unsigned long long), s) != cudaSuccess) return PEPS_E_CUDA;
+  for (int k = 0; k < grp.ninst; ++k)
+    if (cudaMemsetAsync(grp.status[k], 0, sizeof(int) * grp.ns[k], s) != cudaSuccess ||
+        cudaMemsetAsync(grp.wdisc[k], 0, sizeof(float) * grp.ns[k], s) != cudaSuccess)
+      return PEPS_E_CUDA;
+  if (launch_batch<T>((const BatchInst<T>*)b->inst_dev[grp.elem], grp.ninst, grp.nitems, b->next + grp.elem, grp.grid,
+                      grp.smem, s) != cudaSuccess)
+    return PEPS_E_CUDA;
+  for (int k = 0; k < grp.ninst; ++k)
+    if (launch_status_or(grp.status[k], grp.ns[k], grp.sword[k], s) != cudaSuccess) return PEPS_E_CUDA;
+  return PEPS_OK;
+}
+
+static size_t default_batch_budget(const peps_batch_item* items, int n) {
+  for (int i = 0; i < n; ++i)
+    if (items[i].h->esz >= 8) return 210 * 1024;
+  return 110 * 1024;
+}
+
+extern "C" peps_status peps_batch_create_ex(peps_batch** out, const peps_batch_item* items, int n, int budget_kb,
+                                            void* stream) {
+  if (!out || !items || n < 1 || budget_kb < 0) return PEPS_E_ARG;
   *out = nullptr;
   cudaStream_t s = (cudaStream_t)stream;
   if (!s) return PEPS_E_ARG;  // the legacy default stream cannot be captured
@@ -1207,46 +1508,61 @@ extern "C" peps_status peps_batch_create(peps_batch** out, const peps_batch_item
     if (st != PEPS_OK) return st;
   }
   if (cudaStreamSynchronize(s) != cudaSuccess) return PEPS_E_CUDA;
-  // largest work first, each item to the branch with the least work so far
-  std::vector<int> order(n);
+  const size_t budget = budget_kb ? (size_t)budget_kb * 1024 : default_batch_budget(items, n);
+  // the queue of each scalar type: the costliest instances first (per-sample work grows as
+  // Lx Ly chi^3 D^3), so that the last items are the cheap ones
+  std::vector<std::vector<int>> grp(4);
   std::vector<double> cost(n);
   for (int i = 0; i < n; ++i) {
     const Geo& g = items[i].h->g;
-    order[i] = i;
-    cost[i] = (double)items[i].Ns * g.Lx * g.Ly * (double)g.chi * g.chi * g.chi * g.D * g.D * g.D;
+    cost[i] = (double)g.Lx * g.Ly * (double)g.chi * g.chi * g.chi * g.D * g.D * g.D;
+    grp[items[i].h->elem].push_back(i);
   }
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  for (auto& v : grp) std::stable_sort(v.begin(), v.end(), [&](int a, int c) { return cost[a] > cost[c]; });
   peps_batch* b = new peps_batch();
-  const int nb = std::min(nbranch, n);
-  b->branches.resize(nb);
-  b->events.resize(nb + 1);
-  for (int k = 0; k < nb; ++k) cudaStreamCreateWithFlags(&b->branches[k], cudaStreamNonBlocking);
-  for (auto& e : b->events) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+  b->budget = budget;
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaMalloc(&b->next, 4 * sizeof(unsigned long long)) != cudaSuccess) {
+    batch_free(b);
+    return PEPS_E_WORKSPACE;
+  }
+  std::vector<BatchGroup> groups;
+  peps_status st = PEPS_OK;
+  for (int e = 0; e < 4 && st == PEPS_OK; ++e) {
+    if (grp[e].empty()) continue;
+    groups.emplace_back();
+    switch (e) {
+      case 0: st = batch_prepare<double>(b, items, grp[e], e, budget, nsm, &groups.back()); break;
+      case 1: st = batch_prepare<float>(b, items, grp[e], e, budget, nsm, &groups.back()); break;
+      case 2: st = batch_prepare<cplx<double>>(b, items, grp[e], e, budget, nsm, &groups.back()); break;
+      default: st = batch_prepare<cplx<float>>(b, items, grp[e], e, budget, nsm, &groups.back()); break;
+    }
+  }
+  if (st != PEPS_OK) {
+    if (!b->err.empty()) items[0].h->err = b->err;
+    batch_free(b);
+    return st;
+  }
   if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
     batch_free(b);
     return PEPS_E_CUDA;
   }
-  peps_status st = PEPS_OK;
-  cudaEventRecord(b->events[nb], s);
-  for (int k = 0; k < nb; ++k) cudaStreamWaitEvent(b->branches[k], b->events[nb], 0);
-  std::vector<double> load(nb, 0.0);
-  for (int idx : order) {
-    const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-    load[k] += cost[idx];
-    const peps_batch_item& it = items[idx];
-    st = peps_evaluate(it.h, it.H, it.S_dev, it.Ns, it.logabs_dev, it.phase_dev, it.eloc_dev, it.O_dev,
-                       it.status_dev, b->branches[k]);
+  for (const BatchGroup& gr : groups) {
     if (st != PEPS_OK) break;
-  }
-  for (int k = 0; k < nb; ++k) {
-    cudaEventRecord(b->events[k], b->branches[k]);
-    cudaStreamWaitEvent(s, b->events[k], 0);
+    switch (gr.elem) {
+      case 0: st = batch_record<double>(b, gr, s); break;
+      case 1: st = batch_record<float>(b, gr, s); break;
+      case 2: st = batch_record<cplx<double>>(b, gr, s); break;
+      default: st = batch_record<cplx<float>>(b, gr, s); break;
+    }
   }
   cudaGraph_t graph = nullptr;
   const cudaError_t ec = cudaStreamEndCapture(s, &graph);
   b->graph = graph;
-  if (st != PEPS_OK || ec != cudaSuccess || !graph ||
-      cudaGraphInstantiate(&b->exec, graph, 0) != cudaSuccess) {
+  if (st != PEPS_OK || ec != cudaSuccess || !graph || cudaGraphInstantiate(&b->exec, graph, 0) != cudaSuccess) {
+    if (st != PEPS_OK && !b->err.empty()) items[0].h->err = b->err;
     batch_free(b);
     return st != PEPS_OK ? st : PEPS_E_CUDA;
   }
@@ -1254,9 +1570,53 @@ extern "C" peps_status peps_batch_create(peps_batch** out, const peps_batch_item
   return PEPS_OK;
 }
 
+extern "C" peps_status peps_batch_create(peps_batch** out, const peps_batch_item* items, int n, int nbranch,
+                                         void* stream) {
+  (void)nbranch;
+  return peps_batch_create_ex(out, items, n, 0, stream);
+}
+
 extern "C" peps_status peps_batch_launch(peps_batch* b, void* stream) {
   if (!b || !b->exec) return PEPS_E_ARG;
   return cudaGraphLaunch(b->exec, (cudaStream_t)stream) == cudaSuccess ? PEPS_OK : PEPS_E_CUDA;
+}
+
+// Batch autotuner: the shared-memory budget per CTA decides which work buffers of every
+// instance stay on chip and how many CTAs share an SM (the batch kernel's tile of work per SM);
+// each candidate batch is recorded, launched and timed, the fastest budget kept.
+extern "C" peps_status peps_batch_autotune(const peps_batch_item* items, int n, int* budget_kb_host, void* stream) {
+  if (!items || n < 1 || !budget_kb_host) return PEPS_E_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  bool fp64 = false;
+  for (int i = 0; i < n; ++i) fp64 = fp64 || items[i].h->esz >= 8;
+  const std::vector<int> cand = fp64 ? std::vector<int>{100, 210} : std::vector<int>{56, 72, 110, 220};
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  int best_kb = 0;
+  peps_status st = PEPS_OK;
+  for (int kb : cand) {
+    peps_batch* b = nullptr;
+    st = peps_batch_create_ex(&b, items, n, kb, stream);
+    if (st == PEPS_E_SHAPE) { st = PEPS_OK; continue; }  // this budget does not fit
+    if (st != PEPS_OK) break;
+    float ms = 0.f;
+    if (cudaGraphLaunch(b->exec, s) != cudaSuccess || cudaEventRecord(e0, s) != cudaSuccess ||
+        cudaGraphLaunch(b->exec, s) != cudaSuccess || cudaEventRecord(e1, s) != cudaSuccess ||
+        cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      batch_free(b);
+      st = PEPS_E_CUDA;
+      break;
+    }
+    batch_free(b);
+    if (ms < best) { best = ms; best_kb = kb; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st == PEPS_OK && best_kb == 0) st = PEPS_E_SHAPE;
+  *budget_kb_host = best_kb;
+  return st;
 }
 
 extern "C" peps_status peps_batch_destroy(peps_batch* b) {
@@ -1347,9 +1707,9 @@ extern "C" peps_status peps_proposal_train_step(int Lx, int Ly, int C, int wprec
 static peps_status ensure_learned(peps_handle* h) {
   if (h->lp_Sp) return PEPS_OK;
   const size_t ns = (size_t)h->cfg.max_samples, N = (size_t)h->g.Lx * h->g.Ly;
-  if (cudaMalloc(&h->lp_Sp, ns * N) != cudaSuccess || cudaMalloc(&h->lp_l0, sizeof(double) * ns * N) != cudaSuccess ||
-      cudaMalloc(&h->lp_l1, sizeof(double) * ns * N) != cudaSuccess ||
-      cudaMalloc(&h->lp_aux, sizeof(double) * ns * 4) != cudaSuccess)
+  if (h_malloc(h, (void**)&h->lp_Sp, ns * N) != cudaSuccess || h_malloc(h, (void**)&h->lp_l0, sizeof(double) * ns * N) != cudaSuccess ||
+      h_malloc(h, (void**)&h->lp_l1, sizeof(double) * ns * N) != cudaSuccess ||
+      h_malloc(h, (void**)&h->lp_aux, sizeof(double) * ns * 4) != cudaSuccess)
     return fail(h, PEPS_E_WORKSPACE, "learned-proposal workspace allocation failed");
   return PEPS_OK;
 }

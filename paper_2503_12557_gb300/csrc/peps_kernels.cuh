@@ -35,6 +35,40 @@ struct DiagTab {
   const double* onsite;  // N x d or null
 };
 
+// One instance of a ragged multi-instance batch (k_batch): its geometry, its buffer plans (their
+// global-arena slices in the batch's own arena), its handle's buffers and the caller's outputs.
+template <typename T>
+struct BatchInst {
+  Geo g;
+  Plan pe, pr, pq;          // environment, one-row and two-row plans
+  const T* Tpad;
+  const uint8_t* S;
+  T* envs;
+  double* logs;
+  float* wdisc;
+  T* O;                     // may be null
+  const long long* site_off;
+  long long Np;
+  TermTab tt;               // in-row and two-row terms (nterm 0 without E_loc)
+  DiagTab dg;
+  double* rowout;
+  double* pairout;
+  int* status;
+  double* logabs;
+  double* phase;
+  double* eloc;             // may be null
+  int want_e, pairs, sides; // sides: 1 upper only (amplitudes), 3 both
+  int Ns;
+  long long item0;          // first work-queue index of this instance
+};
+// k_batch: every CTA takes the next (instance, sample) item of the queue (*next counts them; zero
+// it before the launch) and runs that sample's whole evaluation
+template <typename T>
+cudaError_t launch_batch(const BatchInst<T>* inst, int ninst, long long nitems, unsigned long long* next, int grid,
+                         size_t smem, cudaStream_t s);
+template <typename T>
+cudaError_t kattr_batch(size_t set_bytes, int* occ, size_t occ_smem);
+
 template <typename T>
 cudaError_t launch_env(const Geo& g, const Plan& p, int grid, size_t smem, const T* Tpad, const uint8_t* S, int Ns,
                        int sides, T* envs, double* logs, int* status, float* wdisc, cudaStream_t s);
@@ -157,40 +191,67 @@ cudaError_t launch_direct(const Geo& g, const Plan& p, int grid, size_t smem, in
 template <typename T>
 cudaError_t kattr_direct(const Geo& g, size_t set_bytes, int* occ, size_t occ_smem);
 
+// ---- status bookkeeping (peps_status.cu)
+// *word |= OR of st[0..Ns)
+cudaError_t launch_status_or(const int* st, int Ns, int* word, cudaStream_t s);
+// *word |= bit when *flag != 0
+cudaError_t launch_flag_or(const int* flag, int bit, int* word, cudaStream_t s);
+// w[i] = (st[i] & mask) ? 0 : 1
+cudaError_t launch_status_weights(const int* st, int Ns, int mask, double* w, cudaStream_t s);
+// end of a MinSR step: zero dtheta (n doubles) when info[0] < 0 or *gram_err; halve info[0] for a
+// complex handle; info[3] = -1 on the factorisation route; flags into *word
+cudaError_t launch_minsr_finish(double* info, const int* gram_err, double* dtheta, long long n, int cplx, int chol,
+                                int* word, cudaStream_t s);
+
 // ---- MinSR (FP64)
 // column means m_k = sum_S w_S O_{S,k} (w normalised), and Obar = sqrt(w)(O - m) written as
 // double (Ns x Np)
+// (wsum_dev: one device double of scratch for the weight sum, used when w is not NULL)
 template <typename TO>
 cudaError_t launch_center(const TO* O, const double* w, int Ns, long long Np, double* mean, double* Obar,
-                          cudaStream_t s);
+                          double* wsum_dev, cudaStream_t s);
 cudaError_t launch_center_e(const double* eloc, const double* w, int Ns, double* ebar, cudaStream_t s);
 // complex O (Ns x Np (re, im) pairs of TO): the real embedding W (2Ns x 2Np), [Re ebar; Im ebar]
 // (2Ns), and dtheta back from [Re; Im] (2Np) to Np (re, im) pairs
 template <typename TO>
-cudaError_t launch_center_cplx(const TO* O, const double* w, int Ns, long long Np, double* W, cudaStream_t s);
+cudaError_t launch_center_cplx(const TO* O, const double* w, int Ns, long long Np, double* W, double* wsum_dev,
+                               cudaStream_t s);
 cudaError_t launch_center_e_cplx(const double* eloc, const double* w, int Ns, double* ebar2, cudaStream_t s);
 cudaError_t launch_unembed(const double* d2, long long Np, double* dtheta, cudaStream_t s);
+// sample-sharded MinSR: local sums (Np column sums of w O, then sum w and sum w Re E_loc), and the
+// centring of local rows with the sums reduced over every process
+template <typename TO>
+cudaError_t launch_partial_sums(const TO* O, const double* w, const double* eloc, int Ns, long long Np, double* sums,
+                                cudaStream_t s);
+template <typename TO>
+cudaError_t launch_center_global(const TO* O, const double* w, const double* eloc, int Ns, long long Np,
+                                 const double* g, double* Obar, double* ebar, cudaStream_t s);
 cudaError_t launch_gram(const double* Obar, int Ns, long long Np, double* Tm, int ld, cudaStream_t s);
 // float-float Gram on the FP32 pipes (hi, lo: Ns x Np floats of scratch)
 cudaError_t launch_gram_ff(const double* Obar, int Ns, long long Np, float* hi, float* lo, double* Tm, int ld,
                            cudaStream_t s);
-// cyclic Jacobi eigendecomposition of the symmetric Ns x Ns matrix A (overwritten by its
-// diagonal form), V accumulates the rotations; returns the sweeps used (host loop)
-int jacobi_eig(double* A, double* V, int n, double* rot, double* offn, double* hbuf, cudaStream_t s,
-               int max_sweeps, cudaError_t* err);
+// cyclic Jacobi eigendecomposition of the symmetric n x n matrix A (overwritten by its
+// diagonal form), V accumulates the rotations, *info_sweeps (device) = sweeps used or -1 at the
+// limit; one cooperative launch (hbuf: n x n scratch, cnt: 2 device counters), no host sync
+cudaError_t jacobi_eig(double* A, double* V, int n, unsigned long long* cnt, double* hbuf, double* info_sweeps,
+                       int max_sweeps, cudaStream_t s);
 cudaError_t launch_minsr_apply(const double* A, const double* V, const double* ebar, int n, int nreal, double lambda,
                                double rcond, double* y, double* x, double* info, cudaStream_t s);
 cudaError_t launch_obar_t_x(const double* Obar, const double* x, int Ns, long long Np, double tau, double* dtheta,
                             cudaStream_t s);
 // x = (A + lambda I)^-1 ebar by blocked Cholesky (A overwritten by its factor); returns launches
+// gate (device flag, may be NULL): every launch does nothing while *gate == 0 (the FP64
+// fallback of the mixed solve, decided on the device); a gated run sets info[2] = 0
 long long chol_solve(double* A, int n, int nreal, double lambda, const double* ebar, double* x, int* bad,
-                     double* info, cudaStream_t s, cudaError_t* err);
+                     double* info, const int* gate, cudaStream_t s, cudaError_t* err);
 // the same solve with an FP32 factor (A32: n x n floats, A kept and mirrored to full) and
-// `iters` refinement steps with FP64 residuals (r: n doubles, rn: 2 doubles of scratch);
-// info = (Ns or -1, relative residual, iters, -)
+// `iters` refinement steps with FP64 residuals (r: n doubles, rn: 2 doubles, part: 2 (n + 7) / 8
+// doubles of scratch);
+// info = (Ns or -1, relative residual, iters, -); *need64 (device) = 1 when the FP64
+// factorisation must replace it (factor breakdown or relative residual above 1e-10)
 long long chol_solve_mixed(double* A, float* A32, int n, int nreal, double lambda, const double* ebar, double* x,
-                           double* r, double* rn, int iters, int* bad, double* info, cudaStream_t s,
-                           cudaError_t* err);
+                           double* r, double* rn, double* part, int iters, int* bad, double* info, int* need64,
+                           cudaStream_t s, cudaError_t* err);
 // ---- learned proposal (peps_proposal.cu)
 size_t prop_smem_bytes(int Lx, int Ly, int C, int act_bytes, bool train);
 cudaError_t launch_prop_logits(int Lx, int Ly, int C, int wprec, const void* w, const uint8_t* S, int Ns, double* logits,

@@ -81,32 +81,39 @@ __device__ void build_lower(const G& g, const T* Tpad, const uint8_t* Ss, T* env
   __syncthreads();
 }
 
+// One side (0 upper, 1 lower) of sample smp's environments, with the whole CTA.
+template <typename T, typename G>
+__device__ __forceinline__ void env_item(const G g, const RowWork<T>& w, const T* __restrict__ Tpad,
+                                         const uint8_t* __restrict__ S,
+                         int smp, int side, T* envs, double* logs, int* status, float* wdisc) {
+  __shared__ int st, flag;
+  __shared__ float wd;
+  const int N = g.Lx * g.Ly;
+  if (threadIdx.x == 0) { st = 0; wd = 0.f; }
+  __syncthreads();
+  T* env = envs + (size_t)smp * env_sample_elems(g);
+  double* lg = logs + (size_t)smp * 2 * g.Lx;
+  const uint8_t* Ss = S + (size_t)smp * N;
+  if (side == 0) build_upper(g, Tpad, Ss, env, lg, w, &st, &wd, &flag);
+  else build_lower(g, Tpad, Ss, env, lg, w, &st, &wd, &flag, 1);
+  if (threadIdx.x == 0) {
+    if (st) atomicOr(status + smp, st);
+    if (wdisc) atomicMax((int*)(wdisc + smp), __float_as_int(wd));  // wd >= 0: int order = float order
+  }
+  __syncthreads();
+}
+
 template <typename T, typename G>
 __global__ void __launch_bounds__(NTHREADS, EnvBlocks<T>::value) k_env(G g, Plan plan, const T* __restrict__ Tpad,
                                                   const uint8_t* __restrict__ S, int Ns, int sides, T* envs,
                                                   double* logs, int* status, float* wdisc) {
   extern __shared__ __align__(16) char smem[];
-  char* gbase = plan.gbase;
-  RowWork<T> w = carve_row<T>(plan, smem, gbase);
-  __shared__ int st, flag;
-  __shared__ float wd;
+  RowWork<T> w = carve_row<T>(plan, smem, plan.gbase);
   const int nside = (sides == 3) ? 2 : 1;
-  const int N = g.Lx * g.Ly;
   for (int item = blockIdx.x; item < Ns * nside; item += gridDim.x) {
     const int smp = item / nside;
     const int side = (sides == 3) ? (item % nside) : (sides == 1 ? 0 : 1);
-    if (threadIdx.x == 0) { st = 0; wd = 0.f; }
-    __syncthreads();
-    T* env = envs + (size_t)smp * env_sample_elems(g);
-    double* lg = logs + (size_t)smp * 2 * g.Lx;
-    const uint8_t* Ss = S + (size_t)smp * N;
-    if (side == 0) build_upper(g, Tpad, Ss, env, lg, w, &st, &wd, &flag);
-    else build_lower(g, Tpad, Ss, env, lg, w, &st, &wd, &flag, 1);
-    if (threadIdx.x == 0) {
-      if (st) atomicOr(status + smp, st);
-      if (wdisc) atomicMax((int*)(wdisc + smp), __float_as_int(wd));  // wd >= 0: int order = float order
-    }
-    __syncthreads();
+    env_item(g, w, Tpad, S, smp, side, envs, logs, status, wdisc);
   }
 }
 
@@ -139,12 +146,12 @@ __device__ inline int local_index(const int* ti, const uint8_t* Ss, int d) {
 
 // ------------------------------------------------------------------------------------------
 // One-row sandwich at row x of sample smp: psi_x, O of row x, E_loc terms inside row x.
+// One-row sandwich at row x of sample smp, with the whole CTA.
 template <typename T, typename G>
-__global__ void __launch_bounds__(NTHREADS) k_row(G g, Plan plan, const T* __restrict__ Tpad,
-                                                  const uint8_t* __restrict__ S, int Ns, int x_lo, int x_hi,
-                                                  const T* envs, const double* logs, T* O, const long long* site_off,
-                                                  long long Np, TermTab tt, double* rowout, int* status) {
-  extern __shared__ __align__(16) char smem[];
+__device__ __forceinline__ void row_item(const G g, const Plan plan, char* smem, const T* __restrict__ Tpad,
+                                         const uint8_t* __restrict__ S, int smp, int x, const T* envs,
+                                         const double* logs, T* O, const long long* site_off, long long Np,
+                                         const TermTab tt, double* rowout, int* status) {
   char* gbase = plan.gbase;
   T* LP = (T*)buf_ptr(plan, B_LP, smem, gbase);   // (Ly+1) x se
   T* RP = (T*)buf_ptr(plan, B_RP, smem, gbase);   // (Ly+1) x se
@@ -159,137 +166,144 @@ __global__ void __launch_bounds__(NTHREADS) k_row(G g, Plan plan, const T* __res
   __shared__ double logL[MAX_LY + 1], logR[MAX_LY + 1];
   __shared__ int st;
   const int N = g.Lx * g.Ly, Ly = g.Ly, se = g.se;
-  const int nx = x_hi - x_lo;
   const size_t rowsz = (size_t)Ly * se;
-  for (int item = blockIdx.x; item < Ns * nx; item += gridDim.x) {
-    const int smp = item / nx, x = x_lo + item % nx;
-    const uint8_t* Ss = S + (size_t)smp * N;
-    const T* env = envs + (size_t)smp * env_sample_elems(g);
-    const double* lg = logs + (size_t)smp * 2 * g.Lx;
-    const T* EU = env + (size_t)slot_up(g, x - 1) * rowsz;
-    const T* EL = env + (size_t)slot_lo(g, x + 1) * rowsz;
-    if (threadIdx.x == 0) st = 0;
-    // right partials R[Ly] = unit, R[y] = R[y+1] absorbed over column y
-    blk_unit(RP + (size_t)Ly * se, se);
-    if (threadIdx.x == 0) logR[Ly] = 0.0;
+  const uint8_t* Ss = S + (size_t)smp * N;
+  const T* env = envs + (size_t)smp * env_sample_elems(g);
+  const double* lg = logs + (size_t)smp * 2 * g.Lx;
+  const T* EU = env + (size_t)slot_up(g, x - 1) * rowsz;
+  const T* EL = env + (size_t)slot_lo(g, x + 1) * rowsz;
+  if (threadIdx.x == 0) st = 0;
+  // right partials R[Ly] = unit, R[y] = R[y+1] absorbed over column y
+  blk_unit(RP + (size_t)Ly * se, se);
+  if (threadIdx.x == 0) logR[Ly] = 0.0;
+  __syncthreads();
+  for (int y = Ly - 1; y >= 0; --y) {
+    blk_copy(eu, EU + (size_t)y * se, se);
+    blk_copy(el, EL + (size_t)y * se, se);
+    load_A(A, Tpad, g, x * Ly + y, Ss[x * Ly + y], false);
     __syncthreads();
-    for (int y = Ly - 1; y >= 0; --y) {
-      blk_copy(eu, EU + (size_t)y * se, se);
-      blk_copy(el, EL + (size_t)y * se, se);
-      load_A(A, Tpad, g, x * Ly + y, Ss[x * Ly + y], false);
-      __syncthreads();
-      absorb1_right(g, RP + (size_t)(y + 1) * se, eu, A, el, t1, t2, RP + (size_t)y * se);
-      const double l = blk_normalize(RP + (size_t)y * se, se, red, &st);
-      if (threadIdx.x == 0) logR[y] = logR[y + 1] + l;
-    }
-    // left partials
-    blk_unit(LP, se);
-    if (threadIdx.x == 0) logL[0] = 0.0;
-    __syncthreads();
-    for (int y = 0; y < Ly; ++y) {
-      blk_copy(eu, EU + (size_t)y * se, se);
-      blk_copy(el, EL + (size_t)y * se, se);
-      load_A(A, Tpad, g, x * Ly + y, Ss[x * Ly + y], false);
-      __syncthreads();
-      absorb1(g, LP + (size_t)y * se, eu, A, el, t1, t2, LP + (size_t)(y + 1) * se);
-      const double l = blk_normalize(LP + (size_t)(y + 1) * se, se, red, &st);
-      if (threadIdx.x == 0) logL[y + 1] = logL[y] + l;
-    }
-    __syncthreads();
-    const T val = LP[(size_t)Ly * se];
-    const double lpsi_norm = logL[Ly];
-    const double env_log = lg[slot_up(g, x - 1)] + lg[slot_lo(g, x + 1)];
-    // ---- log-derivatives of row x
-    if (O != nullptr) {
-      for (int y = 0; y < Ly; ++y) {
-        const int site = x * Ly + y;
-        blk_copy(eu, EU + (size_t)y * se, se);
-        {
-          // the lower environment site transposed, elT[z][b][d] = el[b][d][z] (into LW2)
-          const T* ely = EL + (size_t)y * se;
-          const int cd = g.chi * g.D;
-          for (int o = threadIdx.x; o < se; o += blockDim.x) LW2[o] = ely[(size_t)(o % cd) * g.chi + o / cd];
-        }
-        __syncthreads();
-        site_env1(g, LP + (size_t)y * se, eu, LW2, RP + (size_t)(y + 1) * se, t1, t2, A);
-        const double sc = exp(logL[y] + logR[y + 1] - lpsi_norm);
-        int Dl, Du, Dr, Dd;
-        site_dims(g, x, y, &Dl, &Du, &Dr, &Dd);
-        const int blk = Dl * Du * Dr * Dd;
-        const int s_here = Ss[site];
-        T* Orow = O + (size_t)smp * Np + site_off[site];
-        const int D = g.D;
-        for (int o = threadIdx.x; o < g.d * blk; o += blockDim.x) {
-          const int s = o / blk, c = o % blk;
-          const int dd = c % Dd, r = (c / Dd) % Dr, u = (c / (Dd * Dr)) % Du, l = c / (Dd * Dr * Du);
-          T v = T(0);
-          if (s == s_here) {
-            const dz e = to_dz(A[((l * D + u) * D + r) * D + dd]);
-            v = from_dz<T>(dz_div(dz{e.re * sc, e.im * sc}, to_dz(val)));
-          }
-          Orow[o] = v;
-        }
-        __syncthreads();
-      }
-    }
-    // ---- local-energy terms inside row x
-    double ere = 0.0, eim = 0.0;
-    if (tt.nterm > 0) {
-      for (int ti_ = tt.row_off[x]; ti_ < tt.row_off[x + 1]; ++ti_) {
-        const int* ti = tt.tinfo + (size_t)ti_ * TI_N;
-        const int a = local_index(ti, Ss, g.d);
-        for (int e = ti[TI_EOFF]; e < ti[TI_EOFF] + ti[TI_ECNT]; ++e) {
-          if (tt.ent_ab[2 * e] != a) continue;
-          const int b = tt.ent_ab[2 * e + 1];
-          const double hr = tt.ent_h[2 * e], hi = tt.ent_h[2 * e + 1];
-          if (b == a) { ere += hr; eim += hi; continue; }
-          const int y0 = ti[TI_Y0], w = ti[TI_W];
-          blk_copy(LW, LP + (size_t)y0 * se, se);
-          double lw = logL[y0];
-          __syncthreads();
-          for (int c = y0; c < y0 + w; ++c) {
-            const int site = x * Ly + c;
-            blk_copy(eu, EU + (size_t)c * se, se);
-            blk_copy(el, EL + (size_t)c * se, se);
-            load_A(A, Tpad, g, site, state_after(ti, site, Ss, b, g.d), false);
-            __syncthreads();
-            absorb1(g, LW, eu, A, el, t1, t2, LW2);
-            lw += blk_normalize(LW2, se, red, &st);
-            blk_copy(LW, LW2, se);
-            __syncthreads();
-          }
-          const T v = blk_dot(LW, RP + (size_t)(y0 + w) * se, se, red);
-          lw += logR[y0 + w];
-          const dz q = dz_div(to_dz(v), to_dz(val));
-          const double f = exp(lw - lpsi_norm);
-          ere += (hr * q.re - hi * q.im) * f;
-          eim += (hr * q.im + hi * q.re) * f;
-        }
-      }
-    }
-    if (threadIdx.x == 0) {
-      double* out = rowout + ((size_t)smp * g.Lx + x) * 4;
-      const dz vz = to_dz(val);
-      const double av = dz_abs(vz);
-      out[0] = (av > 0.0) ? log(av) + lpsi_norm + env_log : -INFINITY;
-      out[1] = (vz.im == 0.0) ? ((vz.re < 0.0) ? 3.141592653589793 : 0.0) : atan2(vz.im, vz.re);
-      out[2] = ere;
-      out[3] = eim;
-      int s = st;
-      if (!(av > 0.0) || !isfinite(out[0]) || !isfinite(ere) || !isfinite(eim)) s |= ST_NONFINITE;
-      if (s) atomicOr(status + smp, s);
-    }
-    __syncthreads();
+    absorb1_right(g, RP + (size_t)(y + 1) * se, eu, A, el, t1, t2, RP + (size_t)y * se);
+    const double l = blk_normalize(RP + (size_t)y * se, se, red, &st);
+    if (threadIdx.x == 0) logR[y] = logR[y + 1] + l;
   }
+  // left partials
+  blk_unit(LP, se);
+  if (threadIdx.x == 0) logL[0] = 0.0;
+  __syncthreads();
+  for (int y = 0; y < Ly; ++y) {
+    blk_copy(eu, EU + (size_t)y * se, se);
+    blk_copy(el, EL + (size_t)y * se, se);
+    load_A(A, Tpad, g, x * Ly + y, Ss[x * Ly + y], false);
+    __syncthreads();
+    absorb1(g, LP + (size_t)y * se, eu, A, el, t1, t2, LP + (size_t)(y + 1) * se);
+    const double l = blk_normalize(LP + (size_t)(y + 1) * se, se, red, &st);
+    if (threadIdx.x == 0) logL[y + 1] = logL[y] + l;
+  }
+  __syncthreads();
+  const T val = LP[(size_t)Ly * se];
+  const double lpsi_norm = logL[Ly];
+  const double env_log = lg[slot_up(g, x - 1)] + lg[slot_lo(g, x + 1)];
+  // ---- log-derivatives of row x
+  if (O != nullptr) {
+    for (int y = 0; y < Ly; ++y) {
+      const int site = x * Ly + y;
+      blk_copy(eu, EU + (size_t)y * se, se);
+      {
+        // the lower environment site transposed, elT[z][b][d] = el[b][d][z] (into LW2)
+        const T* ely = EL + (size_t)y * se;
+        const int cd = g.chi * g.D;
+        for (int o = threadIdx.x; o < se; o += blockDim.x) LW2[o] = ely[(size_t)(o % cd) * g.chi + o / cd];
+      }
+      __syncthreads();
+      site_env1(g, LP + (size_t)y * se, eu, LW2, RP + (size_t)(y + 1) * se, t1, t2, A);
+      const double sc = exp(logL[y] + logR[y + 1] - lpsi_norm);
+      int Dl, Du, Dr, Dd;
+      site_dims(g, x, y, &Dl, &Du, &Dr, &Dd);
+      const int blk = Dl * Du * Dr * Dd;
+      const int s_here = Ss[site];
+      T* Orow = O + (size_t)smp * Np + site_off[site];
+      const int D = g.D;
+      for (int o = threadIdx.x; o < g.d * blk; o += blockDim.x) {
+        const int s = o / blk, c = o % blk;
+        const int dd = c % Dd, r = (c / Dd) % Dr, u = (c / (Dd * Dr)) % Du, l = c / (Dd * Dr * Du);
+        T v = T(0);
+        if (s == s_here) {
+          const dz e = to_dz(A[((l * D + u) * D + r) * D + dd]);
+          v = from_dz<T>(dz_div(dz{e.re * sc, e.im * sc}, to_dz(val)));
+        }
+        Orow[o] = v;
+      }
+      __syncthreads();
+    }
+  }
+  // ---- local-energy terms inside row x
+  double ere = 0.0, eim = 0.0;
+  if (tt.nterm > 0) {
+    for (int ti_ = tt.row_off[x]; ti_ < tt.row_off[x + 1]; ++ti_) {
+      const int* ti = tt.tinfo + (size_t)ti_ * TI_N;
+      const int a = local_index(ti, Ss, g.d);
+      for (int e = ti[TI_EOFF]; e < ti[TI_EOFF] + ti[TI_ECNT]; ++e) {
+        if (tt.ent_ab[2 * e] != a) continue;
+        const int b = tt.ent_ab[2 * e + 1];
+        const double hr = tt.ent_h[2 * e], hi = tt.ent_h[2 * e + 1];
+        if (b == a) { ere += hr; eim += hi; continue; }
+        const int y0 = ti[TI_Y0], w = ti[TI_W];
+        blk_copy(LW, LP + (size_t)y0 * se, se);
+        double lw = logL[y0];
+        __syncthreads();
+        for (int c = y0; c < y0 + w; ++c) {
+          const int site = x * Ly + c;
+          blk_copy(eu, EU + (size_t)c * se, se);
+          blk_copy(el, EL + (size_t)c * se, se);
+          load_A(A, Tpad, g, site, state_after(ti, site, Ss, b, g.d), false);
+          __syncthreads();
+          absorb1(g, LW, eu, A, el, t1, t2, LW2);
+          lw += blk_normalize(LW2, se, red, &st);
+          blk_copy(LW, LW2, se);
+          __syncthreads();
+        }
+        const T v = blk_dot(LW, RP + (size_t)(y0 + w) * se, se, red);
+        lw += logR[y0 + w];
+        const dz q = dz_div(to_dz(v), to_dz(val));
+        const double f = exp(lw - lpsi_norm);
+        ere += (hr * q.re - hi * q.im) * f;
+        eim += (hr * q.im + hi * q.re) * f;
+      }
+    }
+  }
+  if (threadIdx.x == 0) {
+    double* out = rowout + ((size_t)smp * g.Lx + x) * 4;
+    const dz vz = to_dz(val);
+    const double av = dz_abs(vz);
+    out[0] = (av > 0.0) ? log(av) + lpsi_norm + env_log : -INFINITY;
+    out[1] = (vz.im == 0.0) ? ((vz.re < 0.0) ? 3.141592653589793 : 0.0) : atan2(vz.im, vz.re);
+    out[2] = ere;
+    out[3] = eim;
+    int s = st;
+    if (!(av > 0.0) || !isfinite(out[0]) || !isfinite(ere) || !isfinite(eim)) s |= ST_NONFINITE;
+    if (s) atomicOr(status + smp, s);
+  }
+  __syncthreads();
+}
+
+template <typename T, typename G>
+__global__ void __launch_bounds__(NTHREADS, EnvBlocks<T>::value) k_row(G g, Plan plan, const T* __restrict__ Tpad,
+                                                  const uint8_t* __restrict__ S, int Ns, int x_lo, int x_hi,
+                                                  const T* envs, const double* logs, T* O, const long long* site_off,
+                                                  long long Np, TermTab tt, double* rowout, int* status) {
+  extern __shared__ __align__(16) char smem[];
+  const int nx = x_hi - x_lo;
+  for (int item = blockIdx.x; item < Ns * nx; item += gridDim.x)
+    row_item(g, plan, smem, Tpad, S, item / nx, x_lo + item % nx, envs, logs, O, site_off, Np, tt, rowout, status);
 }
 
 // ------------------------------------------------------------------------------------------
 // Two-row sandwich at rows x, x+1: psi_{x,x+1} and the E_loc terms spanning the two rows.
+// Two-row sandwich at rows x, x+1 of sample smp, with the whole CTA.
 template <typename T, typename G>
-__global__ void __launch_bounds__(NTHREADS) k_pair(G g, Plan plan, const T* __restrict__ Tpad,
-                                                   const uint8_t* __restrict__ S, int Ns, const T* envs,
-                                                   const double* logs, TermTab tt, double* pairout, int* status) {
-  extern __shared__ __align__(16) char smem[];
+__device__ __forceinline__ void pair_item(const G g, const Plan plan, char* smem, const T* __restrict__ Tpad,
+                                          const uint8_t* __restrict__ S, int smp, int x, const T* envs,
+                                          const double* logs, const TermTab tt, double* pairout, int* status) {
   char* gbase = plan.gbase;
   T* LP = (T*)buf_ptr(plan, B_LP, smem, gbase);   // (Ly+1) x s2
   T* RP = (T*)buf_ptr(plan, B_RP, smem, gbase);   // (Ly+1) x s2
@@ -305,136 +319,148 @@ __global__ void __launch_bounds__(NTHREADS) k_pair(G g, Plan plan, const T* __re
   __shared__ double logL[MAX_LY + 1], logR[MAX_LY + 1];
   __shared__ int st;
   const int N = g.Lx * g.Ly, Ly = g.Ly, se = g.se, s2 = g.s2;
-  const int nx = g.Lx - 1;
   const size_t rowsz = (size_t)Ly * se;
-  for (int item = blockIdx.x; item < Ns * nx; item += gridDim.x) {
-    const int smp = item / nx, x = item % nx;
-    // skip row pairs without terms
-    if (tt.nterm == 0 || tt.pair_off[x] == tt.pair_off[x + 1]) {
-      if (threadIdx.x == 0) {
-        double* out = pairout + ((size_t)smp * g.Lx + x) * 4;
-        out[0] = 0.0; out[1] = 0.0; out[2] = 0.0; out[3] = 0.0;
-      }
-      continue;
-    }
-    const uint8_t* Ss = S + (size_t)smp * N;
-    const T* env = envs + (size_t)smp * env_sample_elems(g);
-    const T* EU = env + (size_t)slot_up(g, x - 1) * rowsz;
-    const T* EL = env + (size_t)slot_lo(g, x + 2) * rowsz;
-    if (threadIdx.x == 0) st = 0;
-    blk_unit(RP + (size_t)Ly * s2, s2);
-    if (threadIdx.x == 0) logR[Ly] = 0.0;
-    __syncthreads();
-    for (int y = Ly - 1; y >= 0; --y) {
-      blk_copy(eu, EU + (size_t)y * se, se);
-      blk_copy(el, EL + (size_t)y * se, se);
-      load_A(A1, Tpad, g, x * Ly + y, Ss[x * Ly + y], false);
-      load_A(A2, Tpad, g, (x + 1) * Ly + y, Ss[(x + 1) * Ly + y], false);
-      __syncthreads();
-      absorb2_right(g, RP + (size_t)(y + 1) * s2, eu, A1, A2, el, t1, t2, RP + (size_t)y * s2, plan.cx);
-      const double l = blk_normalize(RP + (size_t)y * s2, s2, red, &st);
-      if (threadIdx.x == 0) logR[y] = logR[y + 1] + l;
-    }
-    blk_unit(LP, s2);
-    if (threadIdx.x == 0) logL[0] = 0.0;
-    __syncthreads();
-    // the left partials are only needed up to the last window start; build them all
-    for (int y = 0; y < Ly; ++y) {
-      blk_copy(eu, EU + (size_t)y * se, se);
-      blk_copy(el, EL + (size_t)y * se, se);
-      load_A(A1, Tpad, g, x * Ly + y, Ss[x * Ly + y], false);
-      load_A(A2, Tpad, g, (x + 1) * Ly + y, Ss[(x + 1) * Ly + y], false);
-      __syncthreads();
-      absorb2(g, LP + (size_t)y * s2, eu, A1, A2, el, t1, t2, LP + (size_t)(y + 1) * s2, plan.cx);
-      const double l = blk_normalize(LP + (size_t)(y + 1) * s2, s2, red, &st);
-      if (threadIdx.x == 0) logL[y + 1] = logL[y] + l;
-    }
-    __syncthreads();
-    const T val = LP[(size_t)Ly * s2];
-    const double lpsi_norm = logL[Ly];
-    double ere = 0.0, eim = 0.0;
-    for (int ti_ = tt.pair_off[x]; ti_ < tt.pair_off[x + 1]; ++ti_) {
-      const int* ti = tt.tinfo + (size_t)ti_ * TI_N;
-      const int a = local_index(ti, Ss, g.d);
-      for (int e = ti[TI_EOFF]; e < ti[TI_EOFF] + ti[TI_ECNT]; ++e) {
-        if (tt.ent_ab[2 * e] != a) continue;
-        const int b = tt.ent_ab[2 * e + 1];
-        const double hr = tt.ent_h[2 * e], hi = tt.ent_h[2 * e + 1];
-        if (b == a) { ere += hr; eim += hi; continue; }
-        const int y0 = ti[TI_Y0], w = ti[TI_W];
-        blk_copy(LW, LP + (size_t)y0 * s2, s2);
-        double lw = logL[y0];
-        __syncthreads();
-        for (int c = y0; c < y0 + w; ++c) {
-          blk_copy(eu, EU + (size_t)c * se, se);
-          blk_copy(el, EL + (size_t)c * se, se);
-          load_A(A1, Tpad, g, x * Ly + c, state_after(ti, x * Ly + c, Ss, b, g.d), false);
-          load_A(A2, Tpad, g, (x + 1) * Ly + c, state_after(ti, (x + 1) * Ly + c, Ss, b, g.d), false);
-          __syncthreads();
-          absorb2(g, LW, eu, A1, A2, el, t1, t2, LW2, plan.cx);
-          lw += blk_normalize(LW2, s2, red, &st);
-          blk_copy(LW, LW2, s2);
-          __syncthreads();
-        }
-        const T v = blk_dot(LW, RP + (size_t)(y0 + w) * s2, s2, red);
-        lw += logR[y0 + w];
-        const dz q = dz_div(to_dz(v), to_dz(val));
-        const double f = exp(lw - lpsi_norm);
-        ere += (hr * q.re - hi * q.im) * f;
-        eim += (hr * q.im + hi * q.re) * f;
-      }
-    }
+  // skip row pairs without terms
+  if (tt.nterm == 0 || tt.pair_off[x] == tt.pair_off[x + 1]) {
     if (threadIdx.x == 0) {
       double* out = pairout + ((size_t)smp * g.Lx + x) * 4;
-      out[0] = 0.0;
-      out[1] = 0.0;
-      out[2] = ere;
-      out[3] = eim;
-      int s = st;
-      if (!(dz_abs(to_dz(val)) != 0.0) || !isfinite(ere) || !isfinite(eim)) s |= ST_NONFINITE;
-      if (s) atomicOr(status + smp, s);
+      out[0] = 0.0; out[1] = 0.0; out[2] = 0.0; out[3] = 0.0;
     }
+    return;
+  }
+  const uint8_t* Ss = S + (size_t)smp * N;
+  const T* env = envs + (size_t)smp * env_sample_elems(g);
+  const T* EU = env + (size_t)slot_up(g, x - 1) * rowsz;
+  const T* EL = env + (size_t)slot_lo(g, x + 2) * rowsz;
+  if (threadIdx.x == 0) st = 0;
+  blk_unit(RP + (size_t)Ly * s2, s2);
+  if (threadIdx.x == 0) logR[Ly] = 0.0;
+  __syncthreads();
+  for (int y = Ly - 1; y >= 0; --y) {
+    blk_copy(eu, EU + (size_t)y * se, se);
+    blk_copy(el, EL + (size_t)y * se, se);
+    load_A(A1, Tpad, g, x * Ly + y, Ss[x * Ly + y], false);
+    load_A(A2, Tpad, g, (x + 1) * Ly + y, Ss[(x + 1) * Ly + y], false);
     __syncthreads();
+    absorb2_right(g, RP + (size_t)(y + 1) * s2, eu, A1, A2, el, t1, t2, RP + (size_t)y * s2, plan.cx);
+    const double l = blk_normalize(RP + (size_t)y * s2, s2, red, &st);
+    if (threadIdx.x == 0) logR[y] = logR[y + 1] + l;
+  }
+  blk_unit(LP, s2);
+  if (threadIdx.x == 0) logL[0] = 0.0;
+  __syncthreads();
+  // the left partials are only needed up to the last window start; build them all
+  for (int y = 0; y < Ly; ++y) {
+    blk_copy(eu, EU + (size_t)y * se, se);
+    blk_copy(el, EL + (size_t)y * se, se);
+    load_A(A1, Tpad, g, x * Ly + y, Ss[x * Ly + y], false);
+    load_A(A2, Tpad, g, (x + 1) * Ly + y, Ss[(x + 1) * Ly + y], false);
+    __syncthreads();
+    absorb2(g, LP + (size_t)y * s2, eu, A1, A2, el, t1, t2, LP + (size_t)(y + 1) * s2, plan.cx);
+    const double l = blk_normalize(LP + (size_t)(y + 1) * s2, s2, red, &st);
+    if (threadIdx.x == 0) logL[y + 1] = logL[y] + l;
+  }
+  __syncthreads();
+  const T val = LP[(size_t)Ly * s2];
+  const double lpsi_norm = logL[Ly];
+  double ere = 0.0, eim = 0.0;
+  for (int ti_ = tt.pair_off[x]; ti_ < tt.pair_off[x + 1]; ++ti_) {
+    const int* ti = tt.tinfo + (size_t)ti_ * TI_N;
+    const int a = local_index(ti, Ss, g.d);
+    for (int e = ti[TI_EOFF]; e < ti[TI_EOFF] + ti[TI_ECNT]; ++e) {
+      if (tt.ent_ab[2 * e] != a) continue;
+      const int b = tt.ent_ab[2 * e + 1];
+      const double hr = tt.ent_h[2 * e], hi = tt.ent_h[2 * e + 1];
+      if (b == a) { ere += hr; eim += hi; continue; }
+      const int y0 = ti[TI_Y0], w = ti[TI_W];
+      blk_copy(LW, LP + (size_t)y0 * s2, s2);
+      double lw = logL[y0];
+      __syncthreads();
+      for (int c = y0; c < y0 + w; ++c) {
+        blk_copy(eu, EU + (size_t)c * se, se);
+        blk_copy(el, EL + (size_t)c * se, se);
+        load_A(A1, Tpad, g, x * Ly + c, state_after(ti, x * Ly + c, Ss, b, g.d), false);
+        load_A(A2, Tpad, g, (x + 1) * Ly + c, state_after(ti, (x + 1) * Ly + c, Ss, b, g.d), false);
+        __syncthreads();
+        absorb2(g, LW, eu, A1, A2, el, t1, t2, LW2, plan.cx);
+        lw += blk_normalize(LW2, s2, red, &st);
+        blk_copy(LW, LW2, s2);
+        __syncthreads();
+      }
+      const T v = blk_dot(LW, RP + (size_t)(y0 + w) * s2, s2, red);
+      lw += logR[y0 + w];
+      const dz q = dz_div(to_dz(v), to_dz(val));
+      const double f = exp(lw - lpsi_norm);
+      ere += (hr * q.re - hi * q.im) * f;
+      eim += (hr * q.im + hi * q.re) * f;
+    }
+  }
+  if (threadIdx.x == 0) {
+    double* out = pairout + ((size_t)smp * g.Lx + x) * 4;
+    out[0] = 0.0;
+    out[1] = 0.0;
+    out[2] = ere;
+    out[3] = eim;
+    int s = st;
+    if (!(dz_abs(to_dz(val)) != 0.0) || !isfinite(ere) || !isfinite(eim)) s |= ST_NONFINITE;
+    if (s) atomicOr(status + smp, s);
+  }
+  __syncthreads();
+}
+
+template <typename T, typename G>
+__global__ void __launch_bounds__(NTHREADS) k_pair(G g, Plan plan, const T* __restrict__ Tpad,
+                                                   const uint8_t* __restrict__ S, int Ns, const T* envs,
+                                                   const double* logs, TermTab tt, double* pairout, int* status) {
+  extern __shared__ __align__(16) char smem[];
+  const int nx = g.Lx - 1;
+  for (int item = blockIdx.x; item < Ns * nx; item += gridDim.x)
+    pair_item(g, plan, smem, Tpad, S, item / nx, item % nx, envs, logs, tt, pairout, status);
+}
+
+// ------------------------------------------------------------------------------------------
+// Per-sample combine: ln psi_top from row Lx-1, E_loc = diagonal + row terms + pair terms.
+// One warp (all 32 lanes) per sample.
+__device__ __forceinline__ void combine_sample(const Geo g, int smp, const uint8_t* __restrict__ S,
+                                               const double* rowout, const double* pairout, int use_rows_all,
+                                               int use_pairs, const DiagTab dg, double* logabs, double* phase,
+                                               double* eloc) {
+  const int lane = threadIdx.x & 31;
+  const int N = g.Lx * g.Ly;
+  const uint8_t* Ss = S + (size_t)smp * N;
+  double re = 0.0, im = 0.0;
+  if (eloc) {
+    for (int p = lane; p < dg.npairs; p += 32) re += dg.pair_v[p] * (double)Ss[dg.pair_ij[2 * p]] * (double)Ss[dg.pair_ij[2 * p + 1]];
+    if (dg.onsite)
+      for (int i = lane; i < N; i += 32) re += dg.onsite[(size_t)i * g.d + (Ss[i] < g.d ? Ss[i] : 0)];
+    if (use_rows_all)
+      for (int x = lane; x < g.Lx; x += 32) {
+        re += rowout[((size_t)smp * g.Lx + x) * 4 + 2];
+        im += rowout[((size_t)smp * g.Lx + x) * 4 + 3];
+      }
+    if (use_pairs)
+      for (int x = lane; x < g.Lx - 1; x += 32) {
+        re += pairout[((size_t)smp * g.Lx + x) * 4 + 2];
+        im += pairout[((size_t)smp * g.Lx + x) * 4 + 3];
+      }
+    re = warp_sum(re);
+    im = warp_sum(im);
+  }
+  if (lane == 0) {
+    const double* top = rowout + ((size_t)smp * g.Lx + (g.Lx - 1)) * 4;
+    if (logabs) logabs[smp] = top[0];
+    if (phase) phase[smp] = top[1];
+    if (eloc) { eloc[2 * smp] = re; eloc[2 * smp + 1] = im; }
   }
 }
 
 #ifdef PEPS_DEFINE_COMMON
-// ------------------------------------------------------------------------------------------
-// Per-sample combine: ln psi_top from row Lx-1, E_loc = diagonal + row terms + pair terms.
-// One warp per sample.
 __global__ void k_combine(Geo g, int Ns, const uint8_t* __restrict__ S, const double* rowout, const double* pairout,
                           int use_rows_all, int use_pairs, DiagTab dg, double* logabs, double* phase, double* eloc) {
-  const int lane = threadIdx.x & 31;
   const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarp = (gridDim.x * blockDim.x) >> 5;
-  const int N = g.Lx * g.Ly;
-  for (int smp = wid; smp < Ns; smp += nwarp) {
-    const uint8_t* Ss = S + (size_t)smp * N;
-    double re = 0.0, im = 0.0;
-    if (eloc) {
-      for (int p = lane; p < dg.npairs; p += 32) re += dg.pair_v[p] * (double)Ss[dg.pair_ij[2 * p]] * (double)Ss[dg.pair_ij[2 * p + 1]];
-      if (dg.onsite)
-        for (int i = lane; i < N; i += 32) re += dg.onsite[(size_t)i * g.d + (Ss[i] < g.d ? Ss[i] : 0)];
-      if (use_rows_all)
-        for (int x = lane; x < g.Lx; x += 32) {
-          re += rowout[((size_t)smp * g.Lx + x) * 4 + 2];
-          im += rowout[((size_t)smp * g.Lx + x) * 4 + 3];
-        }
-      if (use_pairs)
-        for (int x = lane; x < g.Lx - 1; x += 32) {
-          re += pairout[((size_t)smp * g.Lx + x) * 4 + 2];
-          im += pairout[((size_t)smp * g.Lx + x) * 4 + 3];
-        }
-      re = warp_sum(re);
-      im = warp_sum(im);
-    }
-    if (lane == 0) {
-      const double* top = rowout + ((size_t)smp * g.Lx + (g.Lx - 1)) * 4;
-      if (logabs) logabs[smp] = top[0];
-      if (phase) phase[smp] = top[1];
-      if (eloc) { eloc[2 * smp] = re; eloc[2 * smp + 1] = im; }
-    }
-  }
+  for (int smp = wid; smp < Ns; smp += nwarp)
+    combine_sample(g, smp, S, rowout, pairout, use_rows_all, use_pairs, dg, logabs, phase, eloc);
 }
 // Global rotation of the physical index: out[site][s][c] = sum_t M[s][t] in[site][t][c] for the
 // compact parameter layout (site blocks [s][l][u][r][d]); in: real or (re, im) pairs, out:
@@ -1030,6 +1056,88 @@ static cudaError_t with_geo_for(const Geo& g, F&& f) {
       return e;                                                                                                  \
     });                                                                                                          \
   }
+
+#ifdef PEPS_PART_BATCH
+// ------------------------------------------------------------------------------------------
+// Ragged multi-instance batch in one persistent launch (runtime-shape kernels: every instance
+// has its own lattice, D and chi).  The work queue lists (instance, sample) items, the costliest
+// instances first; each CTA takes the next item with one atomic and runs that sample's whole
+// evaluation with the same device functions as the per-handle kernels (so the results are bit
+// for bit theirs): the environment sides, the one-row sandwiches of every row needed, the two-row
+// sandwiches, and the combine.  The caller zeroes *next and every instance's status and wdisc.
+// the three phases as separate functions: their register allocations stay separate instead of
+// one inlined body holding every phase's live ranges
+// (an instance whose (chi, D) has a compiled specialisation runs it, as the per-handle kernels do)
+template <typename T, typename G>
+__device__ __noinline__ void batch_env(const BatchInst<T>& b, G g, char* smem, int smp) {
+  RowWork<T> w = carve_row<T>(b.pe, smem, b.pe.gbase);
+  env_item(g, w, b.Tpad, b.S, smp, 0, b.envs, b.logs, b.status, b.wdisc);
+  if (b.sides == 3) env_item(g, w, b.Tpad, b.S, smp, 1, b.envs, b.logs, b.status, b.wdisc);
+}
+template <typename T, typename G>
+__device__ __noinline__ void batch_row(const BatchInst<T>& b, G g, char* smem, int smp, int x) {
+  row_item(g, b.pr, smem, b.Tpad, b.S, smp, x, b.envs, b.logs, b.O, b.site_off, b.Np, b.tt, b.rowout, b.status);
+}
+template <typename T, typename G>
+__device__ __noinline__ void batch_pair(const BatchInst<T>& b, G g, char* smem, int smp, int x) {
+  pair_item(g, b.pq, smem, b.Tpad, b.S, smp, x, b.envs, b.logs, b.tt, b.pairout, b.status);
+}
+template <typename T, typename G>
+__device__ __forceinline__ void batch_sample(const BatchInst<T>& b, G g, char* smem, int smp) {
+  batch_env<T, G>(b, g, smem, smp);
+  const int x_lo = (b.sides == 3) ? 0 : g.Lx - 1;
+  for (int x = x_lo; x < g.Lx; ++x) batch_row<T, G>(b, g, smem, smp, x);
+  if (b.pairs)
+    for (int x = 0; x + 1 < g.Lx; ++x) batch_pair<T, G>(b, g, smem, smp, x);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS, MinBlocks<T>::value) k_batch(const BatchInst<T>* __restrict__ inst, int ninst, long long nitems,
+                                                    unsigned long long* next) {
+  extern __shared__ __align__(16) char smem[];
+  __shared__ long long item_s;
+  for (;;) {
+    if (threadIdx.x == 0) item_s = (long long)atomicAdd(next, 1ull);
+    __syncthreads();
+    const long long item = item_s;
+    if (item >= nitems) break;
+    int i = 0;
+    while (i + 1 < ninst && inst[i + 1].item0 <= item) ++i;
+    const BatchInst<T>& b = inst[i];
+    const int smp = (int)(item - b.item0);
+    const Geo g = b.g;
+    if constexpr (!Scal<T>::complex) {
+      if (g.chi == 16 && g.D == 4) batch_sample<T>(b, GeoS<16, 4>{g.Lx, g.Ly, g.d, g.cut}, smem, smp);
+      else if (g.chi == 24 && g.D == 4) batch_sample<T>(b, GeoS<24, 4>{g.Lx, g.Ly, g.d, g.cut}, smem, smp);
+      else batch_sample<T>(b, g, smem, smp);
+    } else {
+      batch_sample<T>(b, g, smem, smp);
+    }
+    __syncthreads();
+    if (threadIdx.x < 32)
+      combine_sample(g, smp, b.S, b.rowout, b.pairout, b.want_e, b.pairs, b.dg, b.logabs, b.phase, b.eloc);
+    __syncthreads();
+  }
+}
+
+template <typename T>
+cudaError_t launch_batch(const BatchInst<T>* inst, int ninst, long long nitems, unsigned long long* next, int grid,
+                         size_t smem, cudaStream_t s) {
+  k_batch<T><<<grid, NTHREADS, smem, s>>>(inst, ninst, nitems, next);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t kattr_batch(size_t set_bytes, int* occ, size_t occ_smem) {
+  cudaError_t e = cudaSuccess;
+  if (set_bytes) e = cudaFuncSetAttribute(k_batch<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)set_bytes);
+  if (e == cudaSuccess && occ) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_batch<T>, NTHREADS, occ_smem);
+  return e;
+}
+#define PEPS_INST_BATCH(T)                                                                                       \
+  template cudaError_t launch_batch<T>(const BatchInst<T>*, int, long long, unsigned long long*, int, size_t,     \
+                                       cudaStream_t);                                                             \
+  template cudaError_t kattr_batch<T>(size_t, int*, size_t);
+#endif
 
 #ifdef PEPS_PART_ENV
 template <typename T>

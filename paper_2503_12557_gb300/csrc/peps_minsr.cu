@@ -1,13 +1,20 @@
 // MinSR update in FP64 (paper Eq. (tdvp_fast)): T = Obar Obar^T (N_s x N_s), eigendecomposition
 // T = V diag(Lambda) V^T by cyclic Jacobi, pseudo-inverse with cutoff, dtheta = -tau Obar^T x.
+#include <cooperative_groups.h>
+
 #include "peps_kernels.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace peps {
 
 // ---- centring: mean_k = sum_S w_S O_{S,k}; Obar_{S,k} = sqrt(w_S) (O_{S,k} - mean_k)
+// The weight sum is read from the device (written by k_wsum), so that no host round trip
+// separates the two launches.
 template <typename TO>
-__global__ void k_center(const TO* __restrict__ O, const double* __restrict__ w, int Ns, long long Np, double wsum,
-                         double* mean, double* Obar) {
+__global__ void k_center(const TO* __restrict__ O, const double* __restrict__ w, int Ns, long long Np,
+                         const double* __restrict__ wsum_dev, double* mean, double* Obar) {
+  const double wsum = w ? *wsum_dev : 1.0;
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < Np; k += (long long)gridDim.x * blockDim.x) {
     double m = 0.0;
     for (int s = 0; s < Ns; ++s) m += (w ? w[s] / wsum : 1.0 / Ns) * (double)O[(size_t)s * Np + k];
@@ -26,7 +33,8 @@ __global__ void k_center(const TO* __restrict__ O, const double* __restrict__ w,
 // returns [Re dtheta; Im dtheta].  O: Ns x Np (re, im) pairs of TO.
 template <typename TO>
 __global__ void k_center_cplx(const TO* __restrict__ O, const double* __restrict__ w, int Ns, long long Np,
-                              double wsum, double* W) {
+                              const double* __restrict__ wsum_dev, double* W) {
+  const double wsum = w ? *wsum_dev : 1.0;
   const long long Np2 = 2 * Np;
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < Np; k += (long long)gridDim.x * blockDim.x) {
     double mr = 0.0, mi = 0.0;
@@ -100,6 +108,81 @@ __global__ void k_center_e(const double* eloc, const double* w, int Ns, double* 
   }
 }
 
+// ---- sample-sharded MinSR: the centring split into local sums (reduced across processes by the
+// caller) and the centring of the local rows with the global sums.
+// sums[k] = sum_S w_S O_{S,k} (k < Np), sums[Np] = sum_S w_S, sums[Np + 1] = sum_S w_S Re E_loc(S)
+// (w NULL: every w_S = 1)
+template <typename TO>
+__global__ void k_colsum(const TO* __restrict__ O, const double* __restrict__ w, int Ns, long long Np,
+                         double* __restrict__ sums) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < Np; k += (long long)gridDim.x * blockDim.x) {
+    double m = 0.0;
+    for (int s = 0; s < Ns; ++s) m += (w ? w[s] : 1.0) * (double)O[(size_t)s * Np + k];
+    sums[k] = m;
+  }
+}
+
+__global__ void k_wsums(const double* __restrict__ w, const double* __restrict__ eloc, int Ns, double* out) {
+  __shared__ double red[33];
+  double ws = 0.0, we = 0.0;
+  for (int i = threadIdx.x; i < Ns; i += blockDim.x) {
+    const double wi = w ? w[i] : 1.0;
+    ws += wi;
+    we += wi * eloc[2 * i];
+  }
+  ws = block_sum(ws, red);
+  we = block_sum(we, red);
+  if (threadIdx.x == 0) { out[0] = ws; out[1] = we; }
+}
+
+// Obar_{S,k} = sqrt(w_S / W) (O_{S,k} - g_k / W), ebar_S = sqrt(w_S / W) (Re E_loc(S) - g_E / W) with
+// the global sums g (layout of k_colsum / k_wsums: Np column sums, W, g_E)
+template <typename TO>
+__global__ void k_center_global(const TO* __restrict__ O, const double* __restrict__ w, int Ns, long long Np,
+                                const double* __restrict__ g, double* __restrict__ Obar) {
+  const double W = g[Np];
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < Np; k += (long long)gridDim.x * blockDim.x) {
+    const double m = g[k] / W;
+    for (int s = 0; s < Ns; ++s) {
+      const double sw = sqrt((w ? w[s] : 1.0) / W);
+      Obar[(size_t)s * Np + k] = sw * ((double)O[(size_t)s * Np + k] - m);
+    }
+  }
+}
+
+__global__ void k_center_e_global(const double* __restrict__ eloc, const double* __restrict__ w, int Ns, long long Np,
+                                  const double* __restrict__ g, double* __restrict__ ebar) {
+  const double W = g[Np], m = g[Np + 1] / W;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Ns; i += gridDim.x * blockDim.x)
+    ebar[i] = sqrt((w ? w[i] : 1.0) / W) * (eloc[2 * i] - m);
+}
+
+template <typename TO>
+cudaError_t launch_partial_sums(const TO* O, const double* w, const double* eloc, int Ns, long long Np, double* sums,
+                                cudaStream_t s) {
+  const long long blocks = (Np + 255) / 256;
+  k_colsum<TO><<<(int)(blocks < 4096 ? (blocks > 0 ? blocks : 1) : 4096), 256, 0, s>>>(O, w, Ns, Np, sums);
+  k_wsums<<<1, 1024, 0, s>>>(w, eloc, Ns, sums + Np);
+  return cudaGetLastError();
+}
+template cudaError_t launch_partial_sums<double>(const double*, const double*, const double*, int, long long, double*,
+                                                 cudaStream_t);
+template cudaError_t launch_partial_sums<float>(const float*, const double*, const double*, int, long long, double*,
+                                                cudaStream_t);
+
+template <typename TO>
+cudaError_t launch_center_global(const TO* O, const double* w, const double* eloc, int Ns, long long Np,
+                                 const double* g, double* Obar, double* ebar, cudaStream_t s) {
+  const long long blocks = (Np + 255) / 256;
+  k_center_global<TO><<<(int)(blocks < 4096 ? (blocks > 0 ? blocks : 1) : 4096), 256, 0, s>>>(O, w, Ns, Np, g, Obar);
+  k_center_e_global<<<(Ns + 255) / 256 > 0 ? (Ns + 255) / 256 : 1, 256, 0, s>>>(eloc, w, Ns, Np, g, ebar);
+  return cudaGetLastError();
+}
+template cudaError_t launch_center_global<double>(const double*, const double*, const double*, int, long long,
+                                                  const double*, double*, double*, cudaStream_t);
+template cudaError_t launch_center_global<float>(const float*, const double*, const double*, int, long long,
+                                                 const double*, double*, double*, cudaStream_t);
+
 // ---- Gram T = Obar Obar^T, 64 x 64 output tiles, K staged through shared memory in chunks
 // of 16; only tiles with ti >= tj are computed, the upper triangle is mirrored.
 constexpr int GT = 64, GK = 16;
@@ -163,13 +246,15 @@ __device__ __forceinline__ void jac_params(const double* A, int n, int p, int q,
   *s = t * (*c);
 }
 
-__global__ void k_jacobi_round(const double* __restrict__ A, double* __restrict__ An, double* V, int n, int r,
-                               unsigned long long* nrot, double* offn) {
+// One round of the parallel ordering: every thread owns one 2 x 2 block (pair I, pair J) of the
+// old matrix A and writes the rotated block into An; V's columns of every pair are rotated.
+// nrot counts the rotations applied.
+__device__ __forceinline__ void jacobi_round(const double* __restrict__ A, double* __restrict__ An, double* V, int n,
+                                             int r, unsigned long long* nrot, long long t0, long long tstride) {
   const int h = n / 2;
   const long long nblk = (long long)h * h;
   const long long nv = (long long)n * h;
-  for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < nblk + nv;
-       o += (long long)gridDim.x * blockDim.x) {
+  for (long long o = t0; o < nblk + nv; o += tstride) {
     if (o < nblk) {
       const int I = (int)(o / h), J = (int)(o % h);
       const int pI = rr_player(I, r, n), qI = rr_player(n - 1 - I, r, n);
@@ -191,7 +276,6 @@ __global__ void k_jacobi_round(const double* __restrict__ A, double* __restrict_
       An[(size_t)qI * n + pJ] = d10;
       An[(size_t)qI * n + qJ] = d11;
       if (I == J && sI != 0.0) atomicAdd(nrot, 1ull);
-      if (offn && I != J) atomicAdd(offn, 2.0 * (a00 * a00 + a01 * a01 + a10 * a10 + a11 * a11));
     } else {
       const long long v = o - nblk;
       const int i = (int)(v / h), J = (int)(v % h);
@@ -207,40 +291,58 @@ __global__ void k_jacobi_round(const double* __restrict__ A, double* __restrict_
   }
 }
 
-__global__ void k_eye(double* V, int n) {
-  for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < (long long)n * n;
-       o += (long long)gridDim.x * blockDim.x)
-    V[o] = ((o / n) == (o % n)) ? 1.0 : 0.0;
-}
-
-// A (n x n, n even) -> diagonal form in place (ping-pong with hbuf), V = accumulated rotations.
-// Returns sweeps used (>= 1), or -1 when the sweep limit was reached.  Synchronises the stream
-// once per sweep to read the rotation count.
-int jacobi_eig(double* A, double* V, int n, double* rot, double* offn, double* hbuf, cudaStream_t s,
-               int max_sweeps, cudaError_t* err) {
-  (void)offn;
-  unsigned long long* dcount = (unsigned long long*)rot;
-  *err = cudaSuccess;
-  k_eye<<<304, 256, 0, s>>>(V, n);
+// The whole cyclic Jacobi in one cooperative launch (every CTA resident, so that the grid-wide
+// barriers between rounds cannot wait on a CTA that never runs): V = I, then up to max_sweeps
+// sweeps of n - 1 rounds, ping-ponging between A and B; a sweep that applied no rotation ends
+// the iteration (every thread reads the sweep's counter after the same barrier, so all take the
+// same branch).  The diagonal form ends in A.  cnt: 2 device counters (the current and the next
+// sweep's); sweeps_out[0] = sweeps used, or -1 when the limit was reached.
+__global__ void __launch_bounds__(256) k_jacobi_coop(double* A, double* B, double* V, int n, int max_sweeps,
+                                                     unsigned long long* cnt, double* sweeps_out) {
+  cg::grid_group grid = cg::this_grid();
+  const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long ts = (long long)gridDim.x * blockDim.x;
+  for (long long o = t0; o < (long long)n * n; o += ts) V[o] = ((o / n) == (o % n)) ? 1.0 : 0.0;
+  if (t0 == 0) { cnt[0] = 0ull; cnt[1] = 0ull; }
+  grid.sync();
   double* cur = A;
-  double* nxt = hbuf;
-  const long long work = (long long)(n / 2) * (n / 2) + (long long)n * (n / 2);
-  const int blocks = (int)((work + 255) / 256 < 152 * 16 ? (work + 255) / 256 : 152 * 16);
+  double* nxt = B;
   int sweeps = -1;
   for (int sw = 0; sw < max_sweeps; ++sw) {
-    cudaMemsetAsync(dcount, 0, sizeof(unsigned long long), s);
+    unsigned long long* c = cnt + (sw & 1);
+    if (t0 == 0) cnt[(sw + 1) & 1] = 0ull;  // the next sweep's counter (read by all before the last barrier)
     for (int r = 0; r < n - 1; ++r) {
-      k_jacobi_round<<<blocks, 256, 0, s>>>(cur, nxt, V, n, r, dcount, nullptr);
+      jacobi_round(cur, nxt, V, n, r, c, t0, ts);
+      grid.sync();
       double* t = cur; cur = nxt; nxt = t;
     }
-    unsigned long long h = 0;
-    cudaMemcpyAsync(&h, dcount, sizeof(h), cudaMemcpyDeviceToHost, s);
-    if ((*err = cudaStreamSynchronize(s)) != cudaSuccess) return -1;
-    if (h == 0) { sweeps = sw + 1; break; }
+    const unsigned long long rot = *(volatile unsigned long long*)c;
+    grid.sync();
+    if (rot == 0ull) { sweeps = sw + 1; break; }
   }
-  if (cur != A) cudaMemcpyAsync(A, cur, sizeof(double) * (size_t)n * n, cudaMemcpyDeviceToDevice, s);
-  if ((*err = cudaGetLastError()) != cudaSuccess) return -1;
-  return sweeps;
+  if (cur != A)
+    for (long long o = t0; o < (long long)n * n; o += ts) A[o] = cur[o];
+  if (t0 == 0) *sweeps_out = (double)sweeps;
+}
+
+// A (n x n, n even) -> diagonal form in place (hbuf: a second n x n buffer), V = accumulated
+// rotations, info_sweeps = sweeps used (-1 at the sweep limit), all on the device: one
+// cooperative launch, no host synchronisation.  cnt: 2 unsigned long long of device scratch.
+cudaError_t jacobi_eig(double* A, double* V, int n, unsigned long long* cnt, double* hbuf, double* info_sweeps,
+                       int max_sweeps, cudaStream_t s) {
+  int dev = 0, nsm = 0, per_sm = 0;
+  cudaError_t e;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi_coop, 256, 0)) != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorLaunchOutOfResources;
+  const long long work = (long long)(n / 2) * (n / 2) + (long long)n * (n / 2);
+  long long blocks = (work + 255) / 256;
+  const long long cap = (long long)nsm * per_sm;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  void* args[] = {&A, &hbuf, &V, &n, &max_sweeps, &cnt, &info_sweeps};
+  return cudaLaunchCooperativeKernel((const void*)k_jacobi_coop, dim3((unsigned)blocks), dim3(256), args, 0, s);
 }
 
 // info: [rank kept, min Lambda, max Lambda]; y = f(Lambda) .* (V^T ebar); x = V y
@@ -292,40 +394,32 @@ __global__ void k_obar_t_x(const double* __restrict__ Ob, const double* __restri
 }
 
 // ---- host wrappers
+// wsum_dev: one device double for the weight sum (used only when w is not NULL)
 template <typename TO>
 cudaError_t launch_center(const TO* O, const double* w, int Ns, long long Np, double* mean, double* Obar,
-                          cudaStream_t s) {
-  double wsum = 1.0;
-  if (w) {
-    double* d = mean;  // borrow the first element for the weight sum
-    k_wsum<<<1, 256, 0, s>>>(w, Ns, d);
-    cudaError_t e = cudaMemcpyAsync(&wsum, d, sizeof(double), cudaMemcpyDeviceToHost, s);
-    if (e != cudaSuccess) return e;
-    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
-  }
+                          double* wsum_dev, cudaStream_t s) {
+  if (w) k_wsum<<<1, 256, 0, s>>>(w, Ns, wsum_dev);
   const long long blocks = (Np + 255) / 256;
-  k_center<TO><<<(int)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(O, w, Ns, Np, wsum, mean, Obar);
+  k_center<TO><<<(int)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(O, w, Ns, Np, wsum_dev, mean, Obar);
   return cudaGetLastError();
 }
-template cudaError_t launch_center<double>(const double*, const double*, int, long long, double*, double*, cudaStream_t);
-template cudaError_t launch_center<float>(const float*, const double*, int, long long, double*, double*, cudaStream_t);
+template cudaError_t launch_center<double>(const double*, const double*, int, long long, double*, double*, double*,
+                                           cudaStream_t);
+template cudaError_t launch_center<float>(const float*, const double*, int, long long, double*, double*, double*,
+                                          cudaStream_t);
 
 template <typename TO>
-cudaError_t launch_center_cplx(const TO* O, const double* w, int Ns, long long Np, double* W, cudaStream_t s) {
-  double wsum = 1.0;
-  if (w) {
-    double* d = W;  // borrow the first element for the weight sum
-    k_wsum<<<1, 256, 0, s>>>(w, Ns, d);
-    cudaError_t e = cudaMemcpyAsync(&wsum, d, sizeof(double), cudaMemcpyDeviceToHost, s);
-    if (e != cudaSuccess) return e;
-    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
-  }
+cudaError_t launch_center_cplx(const TO* O, const double* w, int Ns, long long Np, double* W, double* wsum_dev,
+                               cudaStream_t s) {
+  if (w) k_wsum<<<1, 256, 0, s>>>(w, Ns, wsum_dev);
   const long long blocks = (Np + 255) / 256;
-  k_center_cplx<TO><<<(int)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(O, w, Ns, Np, wsum, W);
+  k_center_cplx<TO><<<(int)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(O, w, Ns, Np, wsum_dev, W);
   return cudaGetLastError();
 }
-template cudaError_t launch_center_cplx<double>(const double*, const double*, int, long long, double*, cudaStream_t);
-template cudaError_t launch_center_cplx<float>(const float*, const double*, int, long long, double*, cudaStream_t);
+template cudaError_t launch_center_cplx<double>(const double*, const double*, int, long long, double*, double*,
+                                                cudaStream_t);
+template cudaError_t launch_center_cplx<float>(const float*, const double*, int, long long, double*, double*,
+                                               cudaStream_t);
 
 cudaError_t launch_center_e_cplx(const double* eloc, const double* w, int Ns, double* ebar2, cudaStream_t s) {
   k_center_e_cplx<<<1, 1024, 0, s>>>(eloc, w, Ns, ebar2);
@@ -424,7 +518,9 @@ __global__ void __launch_bounds__(256) k_gram_ff(const float* __restrict__ Oh, c
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int r = r0 + ty * 4 + i, c = c0 + tx * 4 + j;
-      if (r < Ns && c < Ns) {
+      // the cross terms make the pair (r, c) and (c, r) round differently: only the lower
+      // entry's thread writes both (a diagonal tile would otherwise race on them)
+      if (r < Ns && c < Ns && c <= r) {
         const double v = (double)sh[i][j] + (double)sl[i][j];
         Tm[(size_t)r * ld + c] = v;
         Tm[(size_t)c * ld + r] = v;
@@ -485,8 +581,11 @@ namespace peps {
 constexpr int CB = 64;
 
 // factor the CB x CB diagonal block at (k0, k0) in place (lower triangle), one CTA
+// gate (may be NULL): a device flag; the launch does nothing while it is 0 (a factorisation
+// enqueued before the decision whether it is needed has been taken on the device)
 template <typename T>
-__global__ void __launch_bounds__(256) k_chol_diag(T* A, int n, int k0, int* bad) {
+__global__ void __launch_bounds__(256) k_chol_diag(T* A, int n, int k0, int* bad, const int* gate) {
+  if (gate && !*gate) return;
   __shared__ T L[CB][CB + 1];
   const int nb = min(CB, n - k0);
   for (int o = threadIdx.x; o < nb * nb; o += blockDim.x) {
@@ -518,7 +617,8 @@ __global__ void __launch_bounds__(256) k_chol_diag(T* A, int n, int k0, int* bad
 
 // panel below the diagonal block: A_ik <- A_ik L_kk^-T, one CTA per CB rows
 template <typename T>
-__global__ void __launch_bounds__(CB) k_chol_trsm(T* A, int n, int k0) {
+__global__ void __launch_bounds__(CB) k_chol_trsm(T* A, int n, int k0, const int* gate) {
+  if (gate && !*gate) return;
   __shared__ T L[CB][CB + 1];
   __shared__ T X[CB][CB + 1];
   const int r0 = k0 + CB + blockIdx.x * CB;
@@ -541,7 +641,8 @@ __global__ void __launch_bounds__(CB) k_chol_trsm(T* A, int n, int k0) {
 
 // trailing update A_ij -= A_ik A_jk^T for the lower-triangle tiles right of/below the panel
 template <typename T>
-__global__ void __launch_bounds__(256) k_chol_update(T* A, int n, int k0) {
+__global__ void __launch_bounds__(256) k_chol_update(T* A, int n, int k0, const int* gate) {
+  if (gate && !*gate) return;
   __shared__ T As[CB][CB + 1], Bs[CB][CB + 1];
   const int nt = (n - k0 - CB + CB - 1) / CB;
   int t = blockIdx.x, ti = 0;
@@ -575,7 +676,8 @@ __global__ void __launch_bounds__(256) k_chol_update(T* A, int n, int k0) {
     }
 }
 
-__global__ void k_add_diag(double* A, int n, int nreal, double lambda) {
+__global__ void k_add_diag(double* A, int n, int nreal, double lambda, const int* gate) {
+  if (gate && !*gate) return;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
     A[(size_t)i * n + i] += (i < nreal) ? lambda : 1.0;  // a padding index gets 1 (its rhs is 0)
 }
@@ -583,7 +685,9 @@ __global__ void k_add_diag(double* A, int n, int nreal, double lambda) {
 // L y = b then L^T x = y (x += the solution when accumulate), one CTA of 1024 threads,
 // blocked by CB; the right-hand side is carried in T
 template <typename T>
-__global__ void __launch_bounds__(1024) k_chol_solve(const T* L, int n, const double* b, double* x, int accumulate) {
+__global__ void __launch_bounds__(1024) k_chol_solve(const T* L, int n, const double* b, double* x, int accumulate,
+                                                     const int* gate) {
+  if (gate && !*gate) return;
   extern __shared__ unsigned char solve_smem[];
   T* v = reinterpret_cast<T*>(solve_smem);  // n
   for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = (T)b[i];
@@ -631,16 +735,16 @@ __global__ void __launch_bounds__(1024) k_chol_solve(const T* L, int n, const do
 
 // blocked factorisation of the lower triangle of A (n x n) in place; returns launches
 template <typename T>
-static long long chol_factor(T* A, int n, int* bad, cudaStream_t s) {
+static long long chol_factor(T* A, int n, int* bad, const int* gate, cudaStream_t s) {
   long long launches = 0;
   for (int k0 = 0; k0 < n; k0 += CB) {
-    k_chol_diag<T><<<1, 256, 0, s>>>(A, n, k0, bad);
+    k_chol_diag<T><<<1, 256, 0, s>>>(A, n, k0, bad, gate);
     ++launches;
     const int rest = n - k0 - CB;
     if (rest > 0) {
       const int nrb = (rest + CB - 1) / CB;
-      k_chol_trsm<T><<<nrb, CB, 0, s>>>(A, n, k0);
-      k_chol_update<T><<<nrb * (nrb + 1) / 2, 256, 0, s>>>(A, n, k0);
+      k_chol_trsm<T><<<nrb, CB, 0, s>>>(A, n, k0, gate);
+      k_chol_update<T><<<nrb * (nrb + 1) / 2, 256, 0, s>>>(A, n, k0, gate);
       launches += 2;
     }
   }
@@ -648,28 +752,37 @@ static long long chol_factor(T* A, int n, int* bad, cudaStream_t s) {
 }
 
 template <typename T>
-static void chol_apply(const T* L, int n, const double* b, double* x, int accumulate, cudaStream_t s) {
+static void chol_apply(const T* L, int n, const double* b, double* x, int accumulate, const int* gate, cudaStream_t s) {
   cudaFuncSetAttribute(k_chol_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(T) * n));
-  k_chol_solve<T><<<1, 1024, sizeof(T) * n, s>>>(L, n, b, x, accumulate);
+  k_chol_solve<T><<<1, 1024, sizeof(T) * n, s>>>(L, n, b, x, accumulate, gate);
 }
 
-__global__ void k_chol_info(const int* bad, int nreal, double* info) {
+// gate (may be NULL): the fallback flag of the mixed solve; a factorisation it gates marks the
+// fallback in info[2] = 0
+__global__ void k_chol_info(const int* bad, int nreal, double* info, const int* gate) {
+  if (gate && !*gate) return;
   info[0] = *bad ? -1.0 : (double)nreal;
   info[1] = NAN;
-  info[2] = NAN;
+  info[2] = gate ? 0.0 : NAN;
+}
+
+__global__ void k_zero_int(int* p, const int* gate) {
+  if (gate && !*gate) return;
+  *p = 0;
 }
 
 // Returns launches issued; *err for a CUDA error.  info[0] = Ns (-1 if T + lambda was not
-// positive definite in floating point), info[1..2] = NaN (no eigenvalues computed).
+// positive definite in floating point), info[1..2] = NaN (no eigenvalues computed).  With a gate,
+// every launch does nothing unless *gate != 0 when it runs.
 long long chol_solve(double* A, int n, int nreal, double lambda, const double* ebar, double* x, int* bad,
-                     double* info, cudaStream_t s, cudaError_t* err) {
+                     double* info, const int* gate, cudaStream_t s, cudaError_t* err) {
   long long launches = 0;
-  cudaMemsetAsync(bad, 0, sizeof(int), s);
-  k_add_diag<<<(n + 255) / 256, 256, 0, s>>>(A, n, nreal, lambda);
-  ++launches;
-  launches += chol_factor<double>(A, n, bad, s);
-  chol_apply<double>(A, n, ebar, x, 0, s);
-  k_chol_info<<<1, 1, 0, s>>>(bad, nreal, info);
+  k_zero_int<<<1, 1, 0, s>>>(bad, gate);
+  k_add_diag<<<(n + 255) / 256, 256, 0, s>>>(A, n, nreal, lambda, gate);
+  launches += 2;
+  launches += chol_factor<double>(A, n, bad, gate, s);
+  chol_apply<double>(A, n, ebar, x, 0, gate, s);
+  k_chol_info<<<1, 1, 0, s>>>(bad, nreal, info, gate);
   launches += 2;
   *err = cudaGetLastError();
   return launches;
@@ -696,10 +809,13 @@ __global__ void k_mirror(double* A, int n) {
   }
 }
 
-// r = b - (A + d) x, one warp per row; rn[0] += |r|^2, rn[1] += |b|^2 (rn zeroed by the caller)
+// r = b - (A + d) x, one warp per row; every block writes its partial |r|^2 and |b|^2 to
+// part[2 blockIdx.x ..] (summed in a fixed order by k_rnorm, so that the norms, and the fallback
+// decision taken on them, do not depend on the order in which blocks finish)
 __global__ void k_residual(const double* __restrict__ A, int n, int nreal, double lambda, const double* b,
-                           const double* x, double* r, double* rn) {
-  const int lane = threadIdx.x & 31;
+                           const double* x, double* r, double* part) {
+  __shared__ double red_r[8], red_b[8];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
   double acc_r = 0.0, acc_b = 0.0;
   for (int i = warp; i < n; i += nwarps) {
@@ -713,40 +829,54 @@ __global__ void k_residual(const double* __restrict__ A, int n, int nreal, doubl
       acc_b += b[i] * b[i];
     }
   }
-  if (lane == 0) {
-    atomicAdd(rn, acc_r);
-    atomicAdd(rn + 1, acc_b);
+  if (lane == 0) { red_r[wib] = acc_r; red_b[wib] = acc_b; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sr = 0.0, sb = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { sr += red_r[w]; sb += red_b[w]; }
+    part[2 * blockIdx.x] = sr;
+    part[2 * blockIdx.x + 1] = sb;
   }
 }
 
-__global__ void k_mixed_info(const int* bad, int nreal, const double* rn, int iters, double* info) {
+// rn[0..1] = the blocks' partial norms summed in block order (one thread)
+__global__ void k_rnorm(const double* part, int nblocks, double* rn) {
+  double sr = 0.0, sb = 0.0;
+  for (int k = 0; k < nblocks; ++k) { sr += part[2 * k]; sb += part[2 * k + 1]; }
+  rn[0] = sr;
+  rn[1] = sb;
+}
+
+// info of the FP32 solve; need64 = 1 when its factor broke down or the refined relative residual
+// stayed above 1e-10 (the FP64 factorisation then replaces it, gated on this flag)
+__global__ void k_mixed_info(const int* bad, int nreal, const double* rn, int iters, double* info, int* need64) {
   info[0] = *bad ? -1.0 : (double)nreal;
   info[1] = (rn[1] > 0.0) ? sqrt(rn[0] / rn[1]) : 0.0;
   info[2] = (double)iters;
+  *need64 = (*bad || !(rn[0] <= 1e-20 * rn[1])) ? 1 : 0;
 }
 
 long long chol_solve_mixed(double* A, float* A32, int n, int nreal, double lambda, const double* ebar, double* x,
-                           double* r, double* rn, int iters, int* bad, double* info, cudaStream_t s,
-                           cudaError_t* err) {
+                           double* r, double* rn, double* part, int iters, int* bad, double* info, int* need64,
+                           cudaStream_t s, cudaError_t* err) {
   long long launches = 0;
   cudaMemsetAsync(bad, 0, sizeof(int), s);
   k_mirror<<<1024, 256, 0, s>>>(A, n);
   k_lower_to_f32<<<1024, 256, 0, s>>>(A, A32, n, nreal, lambda);
   launches += 2;
-  launches += chol_factor<float>(A32, n, bad, s);
-  chol_apply<float>(A32, n, ebar, x, 0, s);
+  launches += chol_factor<float>(A32, n, bad, nullptr, s);
+  chol_apply<float>(A32, n, ebar, x, 0, nullptr, s);
   ++launches;
   const int rgrid = (n + 7) / 8;
   for (int it = 0; it < iters; ++it) {
-    cudaMemsetAsync(rn, 0, 2 * sizeof(double), s);
-    k_residual<<<rgrid, 256, 0, s>>>(A, n, nreal, lambda, ebar, x, r, rn);
-    chol_apply<float>(A32, n, r, x, 1, s);
+    k_residual<<<rgrid, 256, 0, s>>>(A, n, nreal, lambda, ebar, x, r, part);
+    chol_apply<float>(A32, n, r, x, 1, nullptr, s);
     launches += 2;
   }
-  cudaMemsetAsync(rn, 0, 2 * sizeof(double), s);
-  k_residual<<<rgrid, 256, 0, s>>>(A, n, nreal, lambda, ebar, x, r, rn);
-  k_mixed_info<<<1, 1, 0, s>>>(bad, nreal, rn, iters, info);
-  launches += 2;
+  k_residual<<<rgrid, 256, 0, s>>>(A, n, nreal, lambda, ebar, x, r, part);
+  k_rnorm<<<1, 1, 0, s>>>(part, rgrid, rn);
+  k_mixed_info<<<1, 1, 0, s>>>(bad, nreal, rn, iters, info, need64);
+  launches += 3;
   *err = cudaGetLastError();
   return launches;
 }

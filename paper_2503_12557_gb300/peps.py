@@ -18,6 +18,7 @@ _LIBPATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "lib
 PREC_FP64, PREC_FP32 = 0, 1
 MOVE_EXCHANGE, MOVE_FLIP = 0, 1
 ST_NEAR_DEGENERATE, ST_ZERO_NORM, ST_NONFINITE, ST_NOCONV = 1, 2, 4, 8
+SW_MINSR_BREAKDOWN, SW_GRAM_TIMEOUT = 1 << 8, 1 << 9
 
 _ERRORS = {-1: "PEPS_E_ARG", -2: "PEPS_E_SHAPE", -3: "PEPS_E_WORKSPACE", -4: "PEPS_E_CUDA", -5: "PEPS_E_UNSUPPORTED",
            -6: "PEPS_E_CAPACITY", 1: "PEPS_W_NUMERIC"}
@@ -37,6 +38,31 @@ class _Ham(C.Structure):
     _fields_ = [("nterms", C.c_int), ("terms", C.POINTER(_Term)), ("npairs", C.c_int),
                 ("pair_ij_host", C.POINTER(C.c_int)), ("pair_v_host", C.POINTER(C.c_double)),
                 ("onsite_host", C.POINTER(C.c_double))]
+
+
+_ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t)
+_FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class _Allocator(C.Structure):
+    _fields_ = [("alloc", _ALLOC_FN), ("free", _FREE_FN), ("ctx", C.c_void_p)]
+
+
+def _torch_alloc(ctx, nbytes):
+    try:
+        return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(),
+                                                  torch.cuda.current_stream())
+    except Exception:
+        return None
+
+
+def _torch_free(ctx, ptr):
+    if ptr:
+        torch.cuda.caching_allocator_delete(ptr)
+
+
+# the handle's device memory comes from PyTorch's caching allocator (kept alive for the process)
+_TORCH_ALLOCATOR = _Allocator(_ALLOC_FN(_torch_alloc), _FREE_FN(_torch_free), None)
 
 
 class _BatchItem(C.Structure):
@@ -60,6 +86,14 @@ def load():
     vp, i32, i64, dbl = C.c_void_p, C.c_int, C.c_longlong, C.c_double
     sig = {
         "peps_create": ([C.POINTER(vp), C.POINTER(_Config)], i32),
+        "peps_create_ex": ([C.POINTER(vp), C.POINTER(_Config), C.POINTER(_Allocator)], i32),
+        "peps_last_status": ([vp, C.POINTER(C.c_int32), vp], i32),
+        "peps_status_weights": ([vp, i32, i32, vp, vp], i32),
+        "minsr_partial_sums": ([vp, vp, vp, vp, i32, vp, vp], i32),
+        "minsr_center_rows": ([vp, vp, vp, vp, i32, vp, vp, vp, vp], i32),
+        "minsr_gram": ([vp, vp, i32, i64, vp, vp], i32),
+        "minsr_solve": ([vp, vp, vp, i32, dbl, dbl, vp, vp, vp], i32),
+        "minsr_project": ([vp, vp, i32, i64, dbl, vp, vp], i32),
         "peps_destroy": ([vp], i32),
         "peps_num_params": ([vp], i64),
         "peps_set_params": ([vp, vp, vp], i32),
@@ -84,6 +118,8 @@ def load():
         "peps_probe_fma": ([i32, C.POINTER(dbl), vp], i32),
         "peps_autotune": ([vp, C.POINTER(_Ham), vp, i32, i32, vp, vp], i32),
         "peps_batch_create": ([C.POINTER(vp), C.POINTER(_BatchItem), i32, i32, vp], i32),
+        "peps_batch_create_ex": ([C.POINTER(vp), C.POINTER(_BatchItem), i32, i32, vp], i32),
+        "peps_batch_autotune": ([C.POINTER(_BatchItem), i32, C.POINTER(i32), vp], i32),
         "peps_batch_launch": ([vp, vp], i32),
         "peps_batch_destroy": ([vp], i32),
     }
@@ -102,7 +138,9 @@ def exported_symbols():
             "peps_proposal_train_step", "peps_sample_learned", "peps_amplitudes_noalloc", "peps_probe_fma",
             "peps_autotune", "peps_batch_create", "peps_batch_launch", "peps_batch_destroy",
             "peps_local_energy_bound", "peps_rotate_params", "peps_direct_prepare", "peps_direct_sample",
-            "peps_set_env_reuse"]
+            "peps_set_env_reuse", "peps_create_ex", "peps_last_status", "peps_status_weights",
+            "minsr_partial_sums", "minsr_center_rows", "minsr_gram", "minsr_solve", "minsr_project",
+            "peps_batch_create_ex", "peps_batch_autotune"]
 
 
 def probe_fma(fp64=False):
@@ -194,7 +232,10 @@ class Hamiltonian:
 class PEPS:
     """One handle of the C library: a lattice, chi and a precision."""
 
-    def __init__(self, Lx, Ly, d, D, chi, prec=PREC_FP64, max_samples=4096, gram=0, solve=0, cplx=False, trunc_weight=0.0):
+    def __init__(self, Lx, Ly, d, D, chi, prec=PREC_FP64, max_samples=4096, gram=0, solve=0, cplx=False, trunc_weight=0.0,
+                 allocator="torch"):
+        """allocator: "torch" (the handle's device memory from PyTorch's caching allocator, through
+        peps_create_ex) or None (the library's own cudaMalloc, peps_create)."""
         self.L = load()
         self.Lx, self.Ly, self.d, self.D, self.chi, self.prec = Lx, Ly, d, D, chi, prec
         self.max_samples = max_samples
@@ -205,7 +246,10 @@ class PEPS:
         self.trunc_weight = float(trunc_weight)
         cfg = _Config(Lx, Ly, d, D, chi, prec, max_samples, gram, solve, int(self.cplx), self.trunc_weight)
         h = C.c_void_p()
-        st = self.L.peps_create(C.byref(h), C.byref(cfg))
+        if allocator == "torch":
+            st = self.L.peps_create_ex(C.byref(h), C.byref(cfg), C.byref(_TORCH_ALLOCATOR))
+        else:
+            st = self.L.peps_create(C.byref(h), C.byref(cfg))
         if st != 0:
             raise RuntimeError(f"peps_create failed: {_ERRORS.get(st, st)}")
         self.h = h
@@ -360,7 +404,33 @@ class PEPS:
                     "peps_rotate_params")
         return out
 
+    def last_status(self):
+        """Synchronise the current stream and read (and clear) the handle's status word (the OR of
+        per-sample status bits and MinSR flags since the last read); sets last_warning when a
+        MinSR step broke down.  Returns the word."""
+        w = C.c_int32(0)
+        st = self.L.peps_last_status(self.h, C.byref(w), _stream())
+        self.last_warning = None
+        if st == -4:
+            msg = self.L.peps_last_error(self.h)
+            raise RuntimeError(f"peps_last_status: {msg.decode() if msg else ''}")
+        if w.value & SW_MINSR_BREAKDOWN:
+            msg = self.L.peps_last_error(self.h)
+            self.last_warning = f"minsr_step: {msg.decode() if msg else 'numerical warning'}"
+        return w.value
+
+    def status_weights(self, status, mask=ST_ZERO_NORM | ST_NONFINITE | ST_NOCONV):
+        """MinSR weights 0 for the samples whose status has a bit of mask, else 1 (device)."""
+        assert status.is_cuda and status.dtype == torch.int32
+        w = torch.empty(status.shape[0], dtype=torch.float64, device=status.device)
+        st = self.L.peps_status_weights(_ptr(status.contiguous()), status.shape[0], int(mask), _ptr(w), _stream())
+        if st != 0:
+            raise RuntimeError(f"peps_status_weights failed: {_ERRORS.get(st, st)}")
+        return w
+
     def minsr_step(self, O, eloc, w=None, lam=1e-4, rcond=0.0, tau=0.05):
+        """dtheta and info of one MinSR step, asynchronous on the current stream; a breakdown
+        (info[0] = -1, dtheta zero) is reported by last_status()."""
         ns = O.shape[0]
         assert O.dtype == self.odtype and O.shape[1] == self.Np and eloc.shape == (ns, 2)
         dth = torch.empty(self.Np, dtype=self.tdtype, device=O.device)
@@ -369,6 +439,50 @@ class PEPS:
                                       _ptr(w.contiguous()) if w is not None else None, ns, float(lam), float(rcond),
                                       float(tau), _ptr(dth), _ptr(info), _stream()), "minsr_step")
         return dth, info
+
+    # ---- sample-sharded MinSR pieces (paper_2503_12557_gb300.dist): real PEPS only
+    def minsr_partial_sums(self, O, eloc, w=None):
+        ns = O.shape[0]
+        assert O.dtype == self.odtype and O.shape[1] == self.Np and eloc.shape == (ns, 2)
+        sums = torch.empty(self.Np + 2, dtype=torch.float64, device=O.device)
+        self._check(self.L.minsr_partial_sums(self.h, _ptr(O.contiguous()), _ptr(eloc.contiguous()),
+                                              _ptr(w.contiguous()) if w is not None else None, ns, _ptr(sums),
+                                              _stream()), "minsr_partial_sums")
+        return sums
+
+    def minsr_center_rows(self, O, eloc, w, gsums):
+        ns = O.shape[0]
+        Ob = torch.empty(ns, self.Np, dtype=torch.float64, device=O.device)
+        eb = torch.empty(ns, dtype=torch.float64, device=O.device)
+        self._check(self.L.minsr_center_rows(self.h, _ptr(O.contiguous()), _ptr(eloc.contiguous()),
+                                             _ptr(w.contiguous()) if w is not None else None, ns,
+                                             _ptr(gsums.contiguous()), _ptr(Ob), _ptr(eb), _stream()),
+                    "minsr_center_rows")
+        return Ob, eb
+
+    def minsr_gram(self, A):
+        A = A.contiguous()
+        ns, k = A.shape
+        T = torch.empty(ns, ns, dtype=torch.float64, device=A.device)
+        self._check(self.L.minsr_gram(self.h, _ptr(A), ns, k, _ptr(T), _stream()), "minsr_gram")
+        return T
+
+    def minsr_solve(self, T, ebar, lam=1e-4, rcond=0.0):
+        ns = T.shape[0]
+        x = torch.empty(ns, dtype=torch.float64, device=T.device)
+        info = torch.zeros(4, dtype=torch.float64, device=T.device)
+        self._check(self.L.minsr_solve(self.h, _ptr(T.contiguous()), _ptr(ebar.contiguous()), ns, float(lam),
+                                       float(rcond), _ptr(x), _ptr(info), _stream()), "minsr_solve")
+        return x, info
+
+    def minsr_project(self, A, x, tau=0.05):
+        A = A.contiguous()
+        ns, k = A.shape
+        d = torch.empty(k, dtype=torch.float64, device=A.device)
+        st = self.L.minsr_project(_ptr(A), _ptr(x.contiguous()), ns, k, float(tau), _ptr(d), _stream())
+        if st != 0:
+            raise RuntimeError(f"minsr_project failed: {_ERRORS.get(st, st)}")
+        return d
 
     def apply_update(self, theta: torch.Tensor, dtheta: torch.Tensor):
         """theta += dtheta on the device (in place) and refresh the handle's kernel copy."""
@@ -411,11 +525,14 @@ class PEPS:
 
 
 class Batch:
-    """Independent handles evaluated by one recorded CUDA graph (peps_batch_*).  items: a list of
-    (PEPS handle, H or None, S (device uint8), want_O); the output tensors are allocated here and
-    refreshed in place at every launch()."""
+    """Independent handles (ragged lattices, D, chi, sample counts) evaluated by one persistent
+    kernel launch per precision over a work queue of (instance, sample) items, recorded in a
+    CUDA graph (peps_batch_*).  items: a list of (PEPS handle, H or None, S (device uint8),
+    want_O); the output tensors are allocated here and refreshed in place at every launch().
+    budget_kb: shared memory per CTA of the batch kernel (0: default; autotune=True times the
+    candidates with peps_batch_autotune and keeps the fastest)."""
 
-    def __init__(self, items, nbranch=4, stream=None):
+    def __init__(self, items, nbranch=4, stream=None, budget_kb=0, autotune=False):
         self.L = load()
         self.stream = stream if stream is not None else torch.cuda.Stream()
         self.keep, arr = [], (_BatchItem * len(items))()
@@ -441,7 +558,15 @@ class Batch:
             self.out.append(o)
         self.b = C.c_void_p()
         torch.cuda.current_stream().synchronize()
-        st = self.L.peps_batch_create(C.byref(self.b), arr, len(items), nbranch, C.c_void_p(self.stream.cuda_stream))
+        sp = C.c_void_p(self.stream.cuda_stream)
+        if autotune:
+            kb = C.c_int(0)
+            st = self.L.peps_batch_autotune(arr, len(items), C.byref(kb), sp)
+            if st != 0:
+                raise RuntimeError(f"peps_batch_autotune failed: {_ERRORS.get(st, st)}")
+            budget_kb = kb.value
+        self.budget_kb = budget_kb
+        st = self.L.peps_batch_create_ex(C.byref(self.b), arr, len(items), int(budget_kb), sp)
         if st != 0:
             raise RuntimeError(f"peps_batch_create failed: {_ERRORS.get(st, st)}")
         self.stream.synchronize()

@@ -74,6 +74,7 @@ class VMC:
             wts = torch.exp(lw - lw.max())
             wts = (wts / wts.sum()).contiguous()
         dth, info = self.h.minsr_step(r["O"], r["eloc"], w=wts, lam=c["lam"], rcond=c["rcond"], tau=c["tau"])
+        self.h.last_status()  # synchronises and reads the step's warning
         warn = self.h.last_warning
         self.h.apply_update(self.theta, dth)
         e = r["eloc"][:, 0].double()

@@ -1,6 +1,8 @@
-"""Multi-instance batches in one CUDA graph and the shared-memory autotuner (C ABI
-peps_batch_* and peps_autotune): results equal the per-handle calls bit for bit, for ragged
-instances (different lattices, D, chi = D^2, precisions and sample counts)."""
+"""Multi-instance batches (C ABI peps_batch_*: one persistent kernel launch per precision over a
+work queue of (instance, sample) items, recorded in a CUDA graph) and the autotuners
+(peps_autotune, peps_batch_autotune): results equal the per-handle calls bit for bit, and every
+instance of a ragged FP64 batch matches the oracle, for instances with different lattices, D,
+chi, precisions and sample counts."""
 import numpy as np
 import pytest
 import torch
@@ -19,9 +21,9 @@ def P():
     return peps
 
 
-def _instance(P, Lx, Ly, D, prec, ns, seed, ham="heis"):
+def _instance(P, Lx, Ly, D, prec, ns, seed, ham="heis", chi=None):
     lat = I.Lattice(Lx, Ly, 2, D)
-    h = P.PEPS(Lx, Ly, 2, D, D * D, prec=prec, max_samples=ns)
+    h = P.PEPS(Lx, Ly, 2, D, chi or D * D, prec=prec, max_samples=ns)
     h.set_params(torch.as_tensor(I.peps_random(lat, seed, scale=0.5, bias=1.0)).cuda())
     S = torch.as_tensor(I.configs_uniform_sz0(lat, ns, seed + 1)).cuda()
     H = I.heisenberg(lat) if ham == "heis" else I.rydberg(lat, delta=1.0)
@@ -36,7 +38,7 @@ def _eager(h, H, S, want_O):
 
 def test_batch_graph_equals_individual_calls(P):
     specs = [(4, 4, 2, 0, 37, 11, "heis", True), (5, 6, 3, 1, 64, 12, "heis", True), (4, 5, 2, 0, 21, 13, "ryd", False),
-             (6, 6, 3, 1, 50, 14, "heis", False)]
+             (6, 6, 3, 1, 50, 14, "heis", False), (6, 6, 4, 1, 40, 15, "heis", True)]
     inst = [_instance(P, Lx, Ly, D, prec, ns, seed, ham) + (wo,) for (Lx, Ly, D, prec, ns, seed, ham, wo) in specs]
     ref = [_eager(h, H, S, wo) for (h, H, S, lat, wo) in inst]
     batch = P.Batch([(h, H, S, wo) for (h, H, S, lat, wo) in inst], nbranch=3)
@@ -55,6 +57,54 @@ def test_batch_graph_equals_individual_calls(P):
     batch.stream.synchronize()
     for o, r in zip(batch.out, ref2):
         for k in ("logabs", "eloc", "O"):
+            if o.get(k) is not None:
+                assert torch.equal(o[k], r[k]), k
+    batch.close()
+
+
+def test_ragged_fp64_batch_matches_the_oracle(P):
+    # every instance of one persistent FP64 launch against the oracle (1e-10, samples whose
+    # truncation hit a near-degenerate cut excluded on both sides, as in the parity tests)
+    from oracle import energy
+    specs = [(4, 4, 2, 4, 9, 31), (5, 6, 3, 5, 12, 32), (6, 4, 2, 3, 7, 33), (4, 5, 3, 9, 10, 34)]
+    inst = []
+    for (Lx, Ly, D, chi, ns, seed) in specs:
+        lat = I.Lattice(Lx, Ly, 2, D)
+        th = I.peps_random(lat, seed, scale=0.5, bias=1.0)
+        h = P.PEPS(Lx, Ly, 2, D, chi, prec=0, max_samples=ns)
+        h.set_params(torch.as_tensor(th).cuda())
+        S = I.configs_uniform_sz0(lat, ns, seed + 100)
+        inst.append((h, I.heisenberg(lat), torch.as_tensor(S).cuda(), lat, th, chi, S))
+    batch = P.Batch([(h, H, Sd, True) for (h, H, Sd, lat, th, chi, S) in inst])
+    # new configurations after recording: the launch reads them
+    for (h, H, Sd, lat, th, chi, S), o in zip(inst, batch.out):
+        o["S"].copy_(torch.as_tensor(S).cuda())
+    batch.launch()
+    batch.stream.synchronize()
+    for (h, H, Sd, lat, th, chi, S), o in zip(inst, batch.out):
+        ref = energy.evaluate(th, S, lat, chi, H=H, want_O=True)
+        st = o["status"].cpu().numpy()
+        ok = ((st & 1) == 0) & ((ref["status"] & 1) == 0)
+        assert ok.sum() >= int(0.7 * len(S))
+        assert np.max(np.abs(o["logabs"].cpu().numpy() - ref["logabs"])[ok]) <= 1e-10
+        el = o["eloc"].cpu().numpy()[:, 0]
+        assert np.max((np.abs(el - ref["eloc"].real) / np.maximum(1.0, np.abs(ref["eloc"])))[ok]) <= 1e-10
+        O = o["O"].cpu().numpy()
+        dO = np.max(np.abs(O - ref["O"].real), axis=1) / np.maximum(1.0, np.max(np.abs(ref["O"]), axis=1))
+        assert np.max(dO[ok]) <= 1e-10
+    batch.close()
+
+
+def test_batch_autotune_keeps_results(P):
+    specs = [(5, 5, 2, 1, 30, 41, "heis", True), (6, 6, 3, 1, 24, 42, "heis", True), (4, 6, 3, 1, 16, 43, "ryd", False)]
+    inst = [_instance(P, Lx, Ly, D, prec, ns, seed, ham) + (wo,) for (Lx, Ly, D, prec, ns, seed, ham, wo) in specs]
+    ref = [_eager(h, H, S, wo) for (h, H, S, lat, wo) in inst]
+    batch = P.Batch([(h, H, S, wo) for (h, H, S, lat, wo) in inst], autotune=True)
+    assert batch.budget_kb in (56, 72, 110, 220)
+    batch.launch()
+    batch.stream.synchronize()
+    for o, r in zip(batch.out, ref):
+        for k in ("logabs", "eloc", "O", "status"):
             if o.get(k) is not None:
                 assert torch.equal(o[k], r[k]), k
     batch.close()

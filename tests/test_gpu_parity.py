@@ -392,7 +392,7 @@ def _minsr_raw(P, O, e, lam, rc, tau, gram=0, solve=0, handle_out=None):
     Op = np.zeros((ns, h.Np))
     Op[:, :npar] = O
     dth, info = h.minsr_step(_dev(Op), _dev(np.stack([e, np.zeros(ns)], 1)), lam=lam, rcond=rc, tau=tau)
-    torch.cuda.synchronize()
+    h.last_status()  # synchronises; sets last_warning on a breakdown
     if handle_out is not None:
         handle_out.append(h)
     return dth.cpu().numpy()[:npar], info.cpu().numpy()
