@@ -205,11 +205,12 @@ def _peaks():
 
 
 # DRAM bytes (read + write) of one sampler call of 2 sweeps in FP32 (every kernel of the split
-# sweep), from an ncu capture of 304 chains, scaled by the chains processed (each chain's
-# environment rows and partials are its own traffic); None until such a capture of the current
-# kernels exists.  profiles/sampler_split_heis8x8_D4_chi16_ns304.md: 1.235 GB per call of 2 sweeps
-# over 304 chains (k_env one-side pass 0.23 GB, k_sweep_moves 0.69 GB, k_env_row 0.32 GB).
-_SAMPLER_CAPTURE = {"bytes": 1.235e9, "chains": 304, "sweeps": 2}
+# sweep), from ncu captures of 304 chains (one kernel per capture), scaled by the chains processed
+# (each chain's environment rows and partials are its own traffic); None until such a capture of
+# the current kernels exists.  profiles/sampler_split_heis8x8_D4_chi16_ns304.md: 1.277 GB per call
+# of 2 sweeps over 304 chains (k_env one-side pass 0.223 GB, 16 k_sweep_moves 0.739 GB, 12
+# k_env_row 0.315 GB).
+_SAMPLER_CAPTURE = {"bytes": 1.277e9, "chains": 304, "sweeps": 2}
 
 
 def _measured_traffic(kernel, ns, sweeps, prec):
@@ -706,8 +707,16 @@ def run_batch(a):
         e1.record(stream)
         stream.synchronize()
     eager_ms = e0.elapsed_time(e1) / a.steps
-    batch = P.Batch(items, stream=stream, autotune=a.autotune)
-    out["batch_budget_kb"] = batch.budget_kb or "default"
+    kb = 0
+    if a.autotune:
+        # the budget is chosen on the first 32 samples of every instance (the full batch at
+        # 2048 samples takes minutes per launch), then used for the full one
+        sub = [(h, H, S[:min(32, S.shape[0])].contiguous(), wo) for (h, H, S, wo) in items]
+        tb = P.Batch(sub, stream=stream, autotune=True)
+        kb = tb.budget_kb
+        tb.close()
+    batch = P.Batch(items, stream=stream, budget_kb=kb)
+    out["batch_budget_kb"] = kb or "default"
     for _ in range(a.warmup):
         batch.launch()
     stream.synchronize()

@@ -452,8 +452,8 @@ typedef struct {
 typedef struct peps_batch peps_batch;
 
 /* Runs every item once eagerly on `stream` (one-time uploads), then plans every instance's work
- * buffers at one shared-memory budget per CTA (budget_kb; 0 = 110 KB for FP32-only batches, 210
- * KB otherwise; the buffers that do not fit go to the batch's own global arena, one slice per
+ * buffers at one shared-memory budget per CTA (budget_kb; 0 = 72 KB for FP32-only batches, three
+ * CTAs per SM, 210 KB otherwise; the buffers that do not fit go to the batch's own global arena, one slice per
  * CTA) and records the graph.  `stream` must not be the legacy default stream (it cannot be
  * captured).  PEPS_E_ARG for a repeated handle or a handle with timing on; PEPS_E_SHAPE when the
  * batch kernel does not fit on an SM at that budget.  Allocates the arena and the queue with

@@ -1479,10 +1479,11 @@ static peps_status batch_record(peps_batch* b, const BatchGroup& grp, cudaStream
   return PEPS_OK;
 }
 
+// FP32: three CTAs per SM, the environment kernels' occupancy; FP64: one
 static size_t default_batch_budget(const peps_batch_item* items, int n) {
   for (int i = 0; i < n; ++i)
     if (items[i].h->esz >= 8) return 210 * 1024;
-  return 110 * 1024;
+  return 72 * 1024;
 }
 
 extern "C" peps_status peps_batch_create_ex(peps_batch** out, const peps_batch_item* items, int n, int budget_kb,

@@ -154,7 +154,10 @@ __global__ void __launch_bounds__(128, 1) k_gram_tc(const __grid_constant__ CUte
   if (!ok) atomicExch(&failed, 1);
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (ok && !failed) {
-    const int row = r0 + warp * 32 + lane;
+    // every MMA has completed (done_bar), so the operand ring is free: each warp stages its
+    // 32 x 32 block there (row = lane on the way in, padded to 33 against bank conflicts) and
+    // writes it out row by row, a warp's 32 lanes storing 32 consecutive columns
+    float* stage = reinterpret_cast<float*>(ring) + (size_t)warp * 32 * 33;
 #pragma unroll 1
     for (int cc = 0; cc < TN; cc += 32) {
       uint32_t v[32];
@@ -168,11 +171,15 @@ __global__ void __launch_bounds__(128, 1) k_gram_tc(const __grid_constant__ CUte
             "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
           : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (row < Ns)
-        for (int j = 0; j < 32; ++j) {
-          const int col = c0 + cc + j;
-          if (col < Ns && col <= row) Tm[(size_t)row * ld + col] = (double)__uint_as_float(v[j]);
-        }
+#pragma unroll
+      for (int j = 0; j < 32; ++j) stage[lane * 33 + j] = __uint_as_float(v[j]);
+      __syncwarp();
+      const int col = c0 + cc + lane;
+      for (int r = 0; r < 32; ++r) {
+        const int row = r0 + warp * 32 + r;
+        if (row < Ns && col < Ns && col <= row) Tm[(size_t)row * ld + col] = (double)stage[r * 33 + lane];
+      }
+      __syncwarp();
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");

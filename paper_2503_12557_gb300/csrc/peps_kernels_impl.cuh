@@ -1092,7 +1092,7 @@ __device__ __forceinline__ void batch_sample(const BatchInst<T>& b, G g, char* s
 }
 
 template <typename T>
-__global__ void __launch_bounds__(NTHREADS, MinBlocks<T>::value) k_batch(const BatchInst<T>* __restrict__ inst, int ninst, long long nitems,
+__global__ void __launch_bounds__(NTHREADS, EnvBlocks<T>::value) k_batch(const BatchInst<T>* __restrict__ inst, int ninst, long long nitems,
                                                     unsigned long long* next) {
   extern __shared__ __align__(16) char smem[];
   __shared__ long long item_s;

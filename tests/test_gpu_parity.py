@@ -232,6 +232,31 @@ def test_fp32_bench_workload_vs_oracle(P):
     assert res["O"].dtype == torch.float32
 
 
+def test_fp32_compiled_24_4_rydberg_vs_oracle(P):
+    # the other compiled FP32 shape, (chi, D) = (24, 4) of the Rydberg workload, on a 6x6 array
+    # with the workload's tensors and |psi|^2-distributed configurations (FP64 flip chains):
+    # |d ln|psi|| <= 1e-5 and E_loc per site within 1e-4 on every sample
+    w = I.WORKLOADS["rydberg12x12_D4_chi24"]
+    lat = I.Lattice(6, 6, 2, 4)
+    th = I.peps_random(lat, w["seed_theta"], **w["init"])
+    H = I.rydberg(lat, delta=2.0)
+    ns = 12
+    h64 = _handle(P, lat, 24, ns)
+    h64.set_params(_dev(th))
+    Sd, _, _ = h64.sample(_dev(I.configs_constant(lat, ns, 0)), move=P.MOVE_FLIP, nsweeps=10, seed=w["seed_chain"])
+    S = Sd.cpu().numpy()
+    h = _handle(P, lat, 24, ns, prec=1)
+    h.set_params(_dev(th))
+    res = h.evaluate(H, _dev(S))
+    torch.cuda.synchronize()
+    ref = _oracle_eval(th, S, lat, 24, H)
+    dl = np.abs(res["logabs"].cpu().numpy() - ref["logabs"])
+    de = np.abs(res["eloc"].cpu().numpy()[:, 0] - ref["eloc"].real) / lat.nsites
+    print(f"fp32 (24, 4): |d ln psi| max {dl.max():.2e}; |dE|/N max {de.max():.2e}")
+    assert dl.max() <= 1e-5
+    assert de.max() <= 1e-4
+
+
 def test_fp32_bench_workload_chains_vs_oracle(P):
     # the FP32 split sweep (lower environments, per-row moves, per-row E^u steps) compiled for
     # (16, 4) against the oracle's FP64 chains on the benchmark's lattice and tensors: FP32
