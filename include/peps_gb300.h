@@ -77,8 +77,13 @@ enum {
 };
 
 /* Arithmetic of the contraction kernels.  FP64: every step in double.  FP32: the environment,
- * truncation and sandwich arithmetic in float, logarithms and E_loc accumulated in double. */
-typedef enum { PEPS_PREC_FP64 = 0, PEPS_PREC_FP32 = 1 } peps_prec;
+ * truncation and sandwich arithmetic in float, logarithms and E_loc accumulated in double.
+ * MIXED: the reduced-precision preset of the whole step: the FP32 contraction kernels (CUDA
+ * cores; logarithms, E_loc and O's scale in double), the MinSR Gram as float-float pairs on the
+ * FP32 pipes (cfg.gram == 0 becomes 2; 1 keeps the split-BF16 tensor-core Gram) and the solve as
+ * an FP32 Cholesky with FP64 refinement and an FP64 fallback (cfg.solve becomes 1); the handle
+ * then reports FP32 (its O is float). */
+typedef enum { PEPS_PREC_FP64 = 0, PEPS_PREC_FP32 = 1, PEPS_PREC_MIXED = 2 } peps_prec;
 
 typedef enum { PEPS_MOVE_EXCHANGE = 0, PEPS_MOVE_FLIP = 1 } peps_move;
 

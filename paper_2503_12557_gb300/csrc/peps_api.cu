@@ -389,11 +389,18 @@ extern "C" peps_status peps_create_ex(peps_handle** out, const peps_config* cfg,
   if (!out || !cfg) return PEPS_E_ARG;
   *out = nullptr;
   if (alloc && (!alloc->alloc || !alloc->free)) return PEPS_E_ARG;
-  const peps_config c = *cfg;
+  peps_config c = *cfg;
   if (c.Lx < 2 || c.Ly < 2 || c.Ly > MAX_LY || c.d < 2 || c.d > 4 || c.D < 1 || c.D > 8 || c.chi < c.D ||
       c.chi > 64 || c.max_samples < 1)
     return PEPS_E_SHAPE;
-  if (c.prec != PEPS_PREC_FP64 && c.prec != PEPS_PREC_FP32) return PEPS_E_ARG;
+  if (c.prec != PEPS_PREC_FP64 && c.prec != PEPS_PREC_FP32 && c.prec != PEPS_PREC_MIXED) return PEPS_E_ARG;
+  if (c.prec == PEPS_PREC_MIXED) {
+    // the mixed-precision preset: the FP32 contraction kernels, a float-float Gram unless the
+    // caller asked for the tensor-core one, and the FP32 Cholesky with FP64 refinement
+    c.prec = PEPS_PREC_FP32;
+    if (c.gram == 0) c.gram = 2;
+    c.solve = 1;
+  }
   if (c.gram != 0 && c.gram != 1 && c.gram != 2) return PEPS_E_ARG;
   if (c.solve != 0 && c.solve != 1) return PEPS_E_ARG;
   if (c.cplx != 0 && c.cplx != 1) return PEPS_E_ARG;
@@ -1025,7 +1032,7 @@ static peps_status minsr_solve_core(peps_handle* h, int Ns, double lambda, doubl
     // eigendecomposition with the pseudo-inverse cutoff: one cooperative launch, the sweep count
     // written to info[3] on the device
     int ts = tstart(h, TC_EIG, s);
-    CK(jacobi_eig(h->Tm, h->Vm, n, (unsigned long long*)(h->cnt + 8), h->Hm, info_dev + 3, 40, s), "Jacobi");
+    CK(jacobi_eig(h->Tm, h->Vm, n, (unsigned long long*)(h->cnt + 8), h->Hm, h->yv, info_dev + 3, 40, s), "Jacobi");
     tstop(h, ts, s, 1);
     ts = tstart(h, TC_MINSR, s);
     CK(launch_minsr_apply(h->Tm, h->Vm, h->ebar, n, Ns, lambda, rcond, h->yv, h->xv, info_dev, s), "MinSR apply");

@@ -232,9 +232,10 @@ cudaError_t launch_gram_ff(const double* Obar, int Ns, long long Np, float* hi, 
                            cudaStream_t s);
 // cyclic Jacobi eigendecomposition of the symmetric n x n matrix A (overwritten by its
 // diagonal form), V accumulates the rotations, *info_sweeps (device) = sweeps used or -1 at the
-// limit; one cooperative launch (hbuf: n x n scratch, cnt: 2 device counters), no host sync
-cudaError_t jacobi_eig(double* A, double* V, int n, unsigned long long* cnt, double* hbuf, double* info_sweeps,
-                       int max_sweeps, cudaStream_t s);
+// limit; one cooperative launch (hbuf: n x n scratch, cs: n doubles of scratch, cnt: 2 device
+// counters), no host sync
+cudaError_t jacobi_eig(double* A, double* V, int n, unsigned long long* cnt, double* hbuf, double* cs,
+                       double* info_sweeps, int max_sweeps, cudaStream_t s);
 cudaError_t launch_minsr_apply(const double* A, const double* V, const double* ebar, int n, int nreal, double lambda,
                                double rcond, double* y, double* x, double* info, cudaStream_t s);
 cudaError_t launch_obar_t_x(const double* Obar, const double* x, int Ns, long long Np, double tau, double* dtheta,

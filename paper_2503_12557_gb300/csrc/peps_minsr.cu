@@ -246,11 +246,27 @@ __device__ __forceinline__ void jac_params(const double* A, int n, int p, int q,
   *s = t * (*c);
 }
 
-// One round of the parallel ordering: every thread owns one 2 x 2 block (pair I, pair J) of the
-// old matrix A and writes the rotated block into An; V's columns of every pair are rotated.
-// nrot counts the rotations applied.
-__device__ __forceinline__ void jacobi_round(const double* __restrict__ A, double* __restrict__ An, double* V, int n,
-                                             int r, unsigned long long* nrot, long long t0, long long tstride) {
+// One round of the parallel ordering, in two phases separated by a grid barrier: (1) the
+// rotation of every pair of the round from the old matrix A (cs: c, s of pair J at 2J, 2J + 1;
+// nrot counts the rotations), (2) every thread owns 2 x 2 blocks (pair I, pair J) of A and writes
+// the rotated block into An, and V's columns of every pair are rotated.  The parameters are
+// computed once per pair, not once per block.
+__device__ __forceinline__ void jacobi_round_params(const double* __restrict__ A, double* cs, int n, int r,
+                                                    unsigned long long* nrot, long long t0, long long tstride) {
+  const int h = n / 2;
+  for (long long J = t0; J < h; J += tstride) {
+    const int p = rr_player((int)J, r, n), q = rr_player(n - 1 - (int)J, r, n);
+    double c, s;
+    jac_params(A, n, p, q, &c, &s);
+    cs[2 * J] = c;
+    cs[2 * J + 1] = s;
+    if (s != 0.0) atomicAdd(nrot, 1ull);
+  }
+}
+
+__device__ __forceinline__ void jacobi_round_apply(const double* __restrict__ A, double* __restrict__ An, double* V,
+                                                   const double* __restrict__ cs, int n, int r, long long t0,
+                                                   long long tstride) {
   const int h = n / 2;
   const long long nblk = (long long)h * h;
   const long long nv = (long long)n * h;
@@ -259,9 +275,7 @@ __device__ __forceinline__ void jacobi_round(const double* __restrict__ A, doubl
       const int I = (int)(o / h), J = (int)(o % h);
       const int pI = rr_player(I, r, n), qI = rr_player(n - 1 - I, r, n);
       const int pJ = rr_player(J, r, n), qJ = rr_player(n - 1 - J, r, n);
-      double cI, sI, cJ, sJ;
-      jac_params(A, n, pI, qI, &cI, &sI);
-      jac_params(A, n, pJ, qJ, &cJ, &sJ);
+      const double cI = cs[2 * I], sI = cs[2 * I + 1], cJ = cs[2 * J], sJ = cs[2 * J + 1];
       const double a00 = A[(size_t)pI * n + pJ], a01 = A[(size_t)pI * n + qJ];
       const double a10 = A[(size_t)qI * n + pJ], a11 = A[(size_t)qI * n + qJ];
       // columns: (x, y) -> (c x - s y, s x + c y)
@@ -275,14 +289,12 @@ __device__ __forceinline__ void jacobi_round(const double* __restrict__ A, doubl
       An[(size_t)pI * n + qJ] = d01;
       An[(size_t)qI * n + pJ] = d10;
       An[(size_t)qI * n + qJ] = d11;
-      if (I == J && sI != 0.0) atomicAdd(nrot, 1ull);
     } else {
       const long long v = o - nblk;
       const int i = (int)(v / h), J = (int)(v % h);
-      const int pJ = rr_player(J, r, n), qJ = rr_player(n - 1 - J, r, n);
-      double c, s;
-      jac_params(A, n, pJ, qJ, &c, &s);
+      const double c = cs[2 * J], s = cs[2 * J + 1];
       if (s != 0.0) {
+        const int pJ = rr_player(J, r, n), qJ = rr_player(n - 1 - J, r, n);
         const double x = V[(size_t)i * n + pJ], y = V[(size_t)i * n + qJ];
         V[(size_t)i * n + pJ] = c * x - s * y;
         V[(size_t)i * n + qJ] = s * x + c * y;
@@ -292,13 +304,14 @@ __device__ __forceinline__ void jacobi_round(const double* __restrict__ A, doubl
 }
 
 // The whole cyclic Jacobi in one cooperative launch (every CTA resident, so that the grid-wide
-// barriers between rounds cannot wait on a CTA that never runs): V = I, then up to max_sweeps
-// sweeps of n - 1 rounds, ping-ponging between A and B; a sweep that applied no rotation ends
-// the iteration (every thread reads the sweep's counter after the same barrier, so all take the
-// same branch).  The diagonal form ends in A.  cnt: 2 device counters (the current and the next
-// sweep's); sweeps_out[0] = sweeps used, or -1 when the limit was reached.
-__global__ void __launch_bounds__(256) k_jacobi_coop(double* A, double* B, double* V, int n, int max_sweeps,
-                                                     unsigned long long* cnt, double* sweeps_out) {
+// barriers between the phases cannot wait on a CTA that never runs): V = I, then up to
+// max_sweeps sweeps of n - 1 rounds, ping-ponging between A and B; a sweep that applied no
+// rotation ends the iteration (every thread reads the sweep's counter after the same barrier,
+// so all take the same branch).  The diagonal form ends in A.  cnt: 2 device counters (the
+// current and the next sweep's); cs: n doubles of scratch; sweeps_out[0] = sweeps used, or -1
+// when the limit was reached.
+__global__ void __launch_bounds__(256) k_jacobi_coop(double* A, double* B, double* V, double* cs, int n,
+                                                     int max_sweeps, unsigned long long* cnt, double* sweeps_out) {
   cg::grid_group grid = cg::this_grid();
   const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long ts = (long long)gridDim.x * blockDim.x;
@@ -312,7 +325,9 @@ __global__ void __launch_bounds__(256) k_jacobi_coop(double* A, double* B, doubl
     unsigned long long* c = cnt + (sw & 1);
     if (t0 == 0) cnt[(sw + 1) & 1] = 0ull;  // the next sweep's counter (read by all before the last barrier)
     for (int r = 0; r < n - 1; ++r) {
-      jacobi_round(cur, nxt, V, n, r, c, t0, ts);
+      jacobi_round_params(cur, cs, n, r, c, t0, ts);
+      grid.sync();
+      jacobi_round_apply(cur, nxt, V, cs, n, r, t0, ts);
       grid.sync();
       double* t = cur; cur = nxt; nxt = t;
     }
@@ -327,9 +342,10 @@ __global__ void __launch_bounds__(256) k_jacobi_coop(double* A, double* B, doubl
 
 // A (n x n, n even) -> diagonal form in place (hbuf: a second n x n buffer), V = accumulated
 // rotations, info_sweeps = sweeps used (-1 at the sweep limit), all on the device: one
-// cooperative launch, no host synchronisation.  cnt: 2 unsigned long long of device scratch.
-cudaError_t jacobi_eig(double* A, double* V, int n, unsigned long long* cnt, double* hbuf, double* info_sweeps,
-                       int max_sweeps, cudaStream_t s) {
+// cooperative launch, no host synchronisation.  cnt: 2 unsigned long long, cs: n doubles of
+// device scratch.
+cudaError_t jacobi_eig(double* A, double* V, int n, unsigned long long* cnt, double* hbuf, double* cs,
+                       double* info_sweeps, int max_sweeps, cudaStream_t s) {
   int dev = 0, nsm = 0, per_sm = 0;
   cudaError_t e;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
@@ -341,7 +357,7 @@ cudaError_t jacobi_eig(double* A, double* V, int n, unsigned long long* cnt, dou
   const long long cap = (long long)nsm * per_sm;
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
-  void* args[] = {&A, &hbuf, &V, &n, &max_sweeps, &cnt, &info_sweeps};
+  void* args[] = {&A, &hbuf, &V, &cs, &n, &max_sweeps, &cnt, &info_sweeps};
   return cudaLaunchCooperativeKernel((const void*)k_jacobi_coop, dim3((unsigned)blocks), dim3(256), args, 0, s);
 }
 

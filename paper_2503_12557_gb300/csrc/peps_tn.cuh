@@ -560,14 +560,15 @@ __device__ __noinline__ void qr_keep_r_reg(T* Z, int m, int nc, T* R, T* taus) {
   __syncthreads();
 }
 
-// Dispatch on the row count; MC > 0: m is the compile-time MC.
+// Dispatch on the row count; MC > 0: a compile-time bound on m (m <= MC).
 template <typename T, int MC = 0>
 __device__ void qr_keep_r(T* Z, int m, int nc, T* R, T* taus) {
   if constexpr (Scal<T>::complex) {
     qr_keep_r_smem(Z, m, nc, R, taus);
   } else if constexpr (MC > 0) {
+    // the register form is compiled for up to MC rows and runs on the m <= MC rows given
     constexpr int RPL = (MC + 31) / 32;
-    if constexpr (RPL <= 24) qr_keep_r_reg<T, RPL>(Z, MC, nc, R, taus);
+    if constexpr (RPL <= 24) qr_keep_r_reg<T, RPL>(Z, m, nc, R, taus);
     else qr_keep_r_smem(Z, m, nc, R, taus);
   } else {
     if (m <= 256) qr_keep_r_reg<T, 8>(Z, m, nc, R, taus);
@@ -1021,17 +1022,23 @@ __device__ double env_row_step(const G& g, const T* Eprev, T* Eout, const T* Tpa
   const int tid = threadIdx.x, NT = blockDim.x;
   const int Lr = D * chi;           // row length of X, Y (open leg x truncated bond)
   const int mX = n + (n & 1);       // Jacobi needs an even row count
-  // ---- left pass: R_{-1} = e00, R_k from QR(R_{k-1} M_k), k = 0..Ly-2
+  // ---- left pass: R_{-1} = e00, R_k from QR(R_{k-1} M_k), k = 0..Ly-2.  Near the open edge
+  // the exact product's bond is small: only the first rk rows of R_{k-1} are nonzero (rk = 1 for
+  // R_{-1}, then at most D times the previous count, capped at n), so Z has only rk D nonzero
+  // rows, all of them first in its (i, d) row order.  The products and the QR run on those rows
+  // alone (Z stored compactly with ld rk D); the dropped rows are exact zeros that would leave
+  // every reflector, and so R, unchanged.
   blk_unit(w.R, n * n);
   __syncthreads();
+  int rk = 1;
   for (int k = 0; k + 1 < Ly; ++k) {
     blk_copy(w.E, Eprev + (size_t)k * g.se, g.se);
     load_A(w.A, Tpad, g, row * Ly + k, Srow[k], lower);
     __syncthreads();
-    const int mZ = n * D;              // rows of Z; Z is stored column major (ld mZ)
+    const int mZ = rk * D;             // nonzero rows of Z; Z is stored column major (ld mZ)
     const int WS = D * D * chi + 1;    // padded row stride of W (no bank conflicts across ii)
-    for (int i0 = 0; i0 < n; i0 += w.ci) {
-      const int ci = (n - i0 < w.ci) ? (n - i0) : w.ci;
+    for (int i0 = 0; i0 < rk; i0 += w.ci) {
+      const int ci = (rk - i0 < w.ci) ? (rk - i0) : w.ci;
       // W[ii][l][u][b] = sum_a R[i0+ii][(a,l)] E[a][u][b]   (m = (u, b), n = (ii, l), k = a)
       blk_gemm<2, 8>(w.E, w.R + (size_t)i0 * n, w.W, D * chi, ci * D, chi, 1, D * chi, 0, D, 0,
                      [=](int m) { return Off2{m, m}; },
@@ -1048,6 +1055,7 @@ __device__ double env_row_step(const G& g, const T* Eprev, T* Eout, const T* Tpa
     qr_keep_r<T, GeoMz<G>::value>(w.Z, mZ, n, w.R, w.sig);
     blk_copy(w.Rhist + (size_t)k * n * n, w.R, n * n);
     __syncthreads();
+    rk = (mZ < n) ? mZ : n;
   }
   // ---- right pass
   // Y and Vt rows are padded to LY = Lr + 1 so that rows read side by side hit different

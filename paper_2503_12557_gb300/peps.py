@@ -15,7 +15,7 @@ import torch
 _LIB = None
 _LIBPATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libpeps_gb300.so")
 
-PREC_FP64, PREC_FP32 = 0, 1
+PREC_FP64, PREC_FP32, PREC_MIXED = 0, 1, 2
 MOVE_EXCHANGE, MOVE_FLIP = 0, 1
 ST_NEAR_DEGENERATE, ST_ZERO_NORM, ST_NONFINITE, ST_NOCONV = 1, 2, 4, 8
 SW_MINSR_BREAKDOWN, SW_GRAM_TIMEOUT = 1 << 8, 1 << 9

@@ -305,6 +305,31 @@ def test_fp32_handle_close_to_oracle(P):
     assert res["O"].dtype == torch.float32
 
 
+def test_mixed_precision_preset(P):
+    # PEPS_PREC_MIXED: the FP32 contraction kernels (results equal an FP32 handle's bit for bit),
+    # a float-float Gram and the FP32 Cholesky with FP64 refinement (info[2] = refinement steps)
+    from oracle import minsr
+    lat = I.Lattice(5, 5, 2, 3)
+    th = I.peps_random(lat, 81, scale=0.5, bias=1.0, alpha=1.5)
+    S = I.configs_uniform_sz0(lat, 40, 82)
+    H = I.heisenberg(lat)
+    hm = P.PEPS(5, 5, 2, 3, 9, prec=P.PREC_MIXED, max_samples=40)
+    hf = P.PEPS(5, 5, 2, 3, 9, prec=P.PREC_FP32, max_samples=40)
+    for h in (hm, hf):
+        h.set_params(_dev(th))
+    rm = hm.evaluate(H, _dev(S))
+    rf = hf.evaluate(H, _dev(S))
+    torch.cuda.synchronize()
+    for k in ("logabs", "eloc", "O", "status"):
+        assert torch.equal(rm[k], rf[k]), k
+    assert rm["O"].dtype == torch.float32
+    dth, info = hm.minsr_step(rm["O"], rm["eloc"], lam=1e-3, tau=0.05)
+    hm.last_status()
+    d_ref, _ = minsr.minsr(rm["O"].double().cpu().numpy(), rm["eloc"][:, 0].cpu().numpy(), lam=1e-3, tau=0.05)
+    assert np.linalg.norm(dth.cpu().numpy() - d_ref) <= 1e-7 * np.linalg.norm(d_ref)
+    assert float(info[2]) in (0.0, 4.0)  # refinement steps, or 0 where the FP64 factor took over
+
+
 def test_amplitudes_and_logderiv_entry_points(P):
     lat = I.Lattice(4, 4, 2, 2)
     th = I.peps_random(lat, 1001)
