@@ -1115,7 +1115,13 @@ __device__ double env_row_step(const G& g, const T* Eprev, T* Eout, const T* Tpa
     // buffer, are no longer needed)
     using RT = typename Scal<T>::R;
     RT* sig = reinterpret_cast<RT*>(w.sig);
-    const int sweeps = hestenes_rows<T, GeoLr<G>::value>(X, mX, Lr, LX, flag, w.ctr, w.red, sig);
+    // only the first min(D^k, n) rows of R_{k-1}, hence of X, are nonzero (the left pass's
+    // bound): the Jacobi runs on those rows (an even count; the rest are exact zeros that no
+    // rotation would touch)
+    int mJ = 1;
+    for (int t = 0; t < k && mJ < n; ++t) mJ = (mJ * D < n) ? mJ * D : n;
+    mJ += (mJ & 1);
+    const int sweeps = hestenes_rows<T, GeoLr<G>::value>(X, mJ < mX ? mJ : mX, Lr, LX, flag, w.ctr, w.red, sig);
     if (sweeps < 0 && tid == 0) *st |= ST_NOCONV;
     // singular values = row norms
     {
