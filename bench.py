@@ -407,7 +407,10 @@ def run_gpu(a):
                             % fp32_derived if peak == fp32_peak else
                             "measured: peps_probe_fma FP64" if peak == fp64_peak else "MEASURED_PEAKS bf16_tflops"),
             "algorithmic_tflop_per_launch": flops[dom] / max(1, launches[dom]) / 1e12,
-            "launch_ms": dom_launch_ms}
+            "launch_ms": dom_launch_ms,
+            "counting": ("the loop nests' flops at the full bond chi (products, QR, sandwiches) plus the Jacobi "
+                         "rotations and sweeps the library counted; the kernels skip the exact-zero rows and "
+                         "columns near the open edge, so the executed flops are fewer")}
     # library launches per step: the classes' counts plus the memsets of evaluate / minsr
     gpu_launches = int(sum(launches.values())) + 4 * a.steps
     line = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": a.steps,

@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(NTHREADS) k_dl_env(G g, int chid, const T* __r
         w.Z[o] = acc;
       }
       __syncthreads();
-      qr_keep_r_smem(w.Z, mZ, nb, w.Rh + (size_t)k * nb * nb, taus);
+      qr_keep_r_smem(w.Z, mZ, nb, w.Rh + (size_t)k * nb * nb, taus, nb);
     }
     // ---- right pass
     blk_unit(w.C, nb * chid);

@@ -11,7 +11,6 @@ template <typename T> struct MinBlocks { static constexpr int value = sizeof(T) 
 // the environment kernel in FP32: three blocks per SM (80 registers; measured 10 % faster than
 // two at 8x8, D = 4, chi = 16, where the sampler, which also runs the sandwiches, is 9 % slower)
 template <typename T> struct EnvBlocks { static constexpr int value = sizeof(T) == 4 ? 3 : 1; };
-constexpr int MAX_LY = 32;
 
 // term record (ints): number of sites, the sites, window (first row, first column, width,
 // two-row flag) and the entry range

@@ -119,6 +119,8 @@ enum : int {
   ST_NOCONV = 8
 };
 
+constexpr int MAX_LY = 32;  // the longest row (columns) the kernels take
+
 struct Geo {
   int Lx, Ly, d, D, chi;
   int n;   // chi*D, exact product bond
@@ -305,7 +307,7 @@ __device__ __forceinline__ void qr_apply_reflector(const T* zj, int j, T tau, T*
 // the rest of the panel), then every warp applies the panel's reflectors, in order, to the
 // trailing columns it owns.  Two block barriers per panel.  taus: at least nc entries.
 template <typename T>
-__device__ void qr_keep_r_smem(T* Z, int m, int nc, T* R, T* taus) {
+__device__ void qr_keep_r_smem(T* Z, int m, int nc, T* R, T* taus, int ldr) {
   constexpr int QB = 8;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   const int steps = (m < nc) ? m : nc;
@@ -350,9 +352,9 @@ __device__ void qr_keep_r_smem(T* Z, int m, int nc, T* R, T* taus) {
     }
     __syncthreads();
   }
-  for (int o = tid; o < nc * nc; o += blockDim.x) {
-    const int i = o / nc, c = o % nc;
-    R[o] = (i <= c && i < m) ? Z[(size_t)c * m + i] : T(0);
+  for (int o = tid; o < ldr * ldr; o += blockDim.x) {
+    const int i = o / ldr, c = o % ldr;
+    R[o] = (c < nc && i <= c && i < m) ? Z[(size_t)c * m + i] : T(0);
   }
   __syncthreads();
 }
@@ -439,7 +441,7 @@ __device__ __forceinline__ void qr_panel_reg(T* Z, int m, int j0, int pb, T* tau
 //   Trailing update (all warps): a warp loads CW trailing columns into registers (element
 //   i = lane + 32 r), applies the panel's reflectors to each in order and stores them once.
 template <typename T, int RPL>
-__device__ __noinline__ void qr_keep_r_reg(T* Z, int m, int nc, T* R, T* taus) {
+__device__ __noinline__ void qr_keep_r_reg(T* Z, int m, int nc, T* R, T* taus, int ldr) {
   // FP32 with 256 rows: panels of four columns, whose register panel (4 x 8 values a lane)
   // fits the environment kernels' 80 registers; eight columns spilled there
   constexpr int QB = (RPL == 8 && sizeof(T) == 4) ? 4 : 8;
@@ -553,27 +555,28 @@ __device__ __noinline__ void qr_keep_r_reg(T* Z, int m, int nc, T* R, T* taus) {
     }
     __syncthreads();
   }
-  for (int o = tid; o < nc * nc; o += blockDim.x) {
-    const int i = o / nc, c = o % nc;
-    R[o] = (i <= c && i < m) ? Z[(size_t)c * m + i] : T(0);
+  for (int o = tid; o < ldr * ldr; o += blockDim.x) {
+    const int i = o / ldr, c = o % ldr;
+    R[o] = (c < nc && i <= c && i < m) ? Z[(size_t)c * m + i] : T(0);
   }
   __syncthreads();
 }
 
-// Dispatch on the row count; MC > 0: a compile-time bound on m (m <= MC).
+// Dispatch on the row count; MC > 0: a compile-time bound on m (m <= MC).  R is written as an
+// ldr x ldr row-major upper-triangular matrix (ldr >= nc; the columns from nc on are zero).
 template <typename T, int MC = 0>
-__device__ void qr_keep_r(T* Z, int m, int nc, T* R, T* taus) {
+__device__ void qr_keep_r(T* Z, int m, int nc, T* R, T* taus, int ldr) {
   if constexpr (Scal<T>::complex) {
-    qr_keep_r_smem(Z, m, nc, R, taus);
+    qr_keep_r_smem(Z, m, nc, R, taus, ldr);
   } else if constexpr (MC > 0) {
     // the register form is compiled for up to MC rows and runs on the m <= MC rows given
     constexpr int RPL = (MC + 31) / 32;
-    if constexpr (RPL <= 24) qr_keep_r_reg<T, RPL>(Z, m, nc, R, taus);
-    else qr_keep_r_smem(Z, m, nc, R, taus);
+    if constexpr (RPL <= 24) qr_keep_r_reg<T, RPL>(Z, m, nc, R, taus, ldr);
+    else qr_keep_r_smem(Z, m, nc, R, taus, ldr);
   } else {
-    if (m <= 256) qr_keep_r_reg<T, 8>(Z, m, nc, R, taus);
-    else if (m <= 768) qr_keep_r_reg<T, 24>(Z, m, nc, R, taus);
-    else qr_keep_r_smem(Z, m, nc, R, taus);
+    if (m <= 256) qr_keep_r_reg<T, 8>(Z, m, nc, R, taus, ldr);
+    else if (m <= 768) qr_keep_r_reg<T, 24>(Z, m, nc, R, taus, ldr);
+    else qr_keep_r_smem(Z, m, nc, R, taus, ldr);
   }
 }
 
@@ -1029,6 +1032,7 @@ __device__ double env_row_step(const G& g, const T* Eprev, T* Eout, const T* Tpa
   // alone (Z stored compactly with ld rk D); the dropped rows are exact zeros that would leave
   // every reflector, and so R, unchanged.
   blk_unit(w.R, n * n);
+  __shared__ int rks_s[MAX_LY];  // rks_s[k]: nonzero rows of R_{k-1}
   __syncthreads();
   int rk = 1;
   for (int k = 0; k + 1 < Ly; ++k) {
@@ -1052,11 +1056,32 @@ __device__ double env_row_step(const G& g, const T* Eprev, T* Eout, const T* Tpa
                      },
                      [=](int nn) { return Off2{nn, (nn / D) * mZ + nn % D}; });
     }
-    qr_keep_r<T, GeoMz<G>::value>(w.Z, mZ, n, w.R, w.sig);
-    blk_copy(w.Rhist + (size_t)k * n * n, w.R, n * n);
+    // the columns (b, r) of Z with b at or beyond the bond of E's site k are exact zeros (E's
+    // bonds are padded to chi with zeros; the first row has bond D, a truncation keeps at most
+    // chi): find the nonzero prefix and factor only it (a zero column leaves every reflector
+    // unchanged and is a zero column of R); R's rank, hence the next rk, is at most that width
+    __shared__ int ncz_s;
+    if (tid == 0) ncz_s = 0;
     __syncthreads();
-    rk = (mZ < n) ? mZ : n;
+    {
+      int last = 0;
+      for (int o = tid; o < mZ * n; o += NT)
+        if (w.Z[o] != T(0)) last = max(last, o / mZ + 1);  // NaN compares unequal: kept
+      last = __reduce_max_sync(0xffffffffu, (unsigned)last);
+      if ((tid & 31) == 0 && last) atomicMax(&ncz_s, last);
+    }
+    __syncthreads();
+    const int ncz = ncz_s;
+    qr_keep_r<T, GeoMz<G>::value>(w.Z, mZ, ncz, w.R, w.sig, n);
+    blk_copy(w.Rhist + (size_t)k * n * n, w.R, n * n);
+    if (tid == 0) rks_s[k] = rk;
+    __syncthreads();
+    rk = (mZ < ncz) ? mZ : ncz;
+    if (rk > n) rk = n;
+    if (rk < 1) rk = 1;
   }
+  if (tid == 0) rks_s[Ly - 1] = rk;  // the rows of R_{Ly-2}, the right pass's first cut
+  __syncthreads();
   // ---- right pass
   // Y and Vt rows are padded to LY = Lr + 1 so that rows read side by side hit different
   // shared-memory banks; X rows to LX = 8 mod 32, the stride at which the Jacobi's four lane
@@ -1115,11 +1140,10 @@ __device__ double env_row_step(const G& g, const T* Eprev, T* Eout, const T* Tpa
     // buffer, are no longer needed)
     using RT = typename Scal<T>::R;
     RT* sig = reinterpret_cast<RT*>(w.sig);
-    // only the first min(D^k, n) rows of R_{k-1}, hence of X, are nonzero (the left pass's
-    // bound): the Jacobi runs on those rows (an even count; the rest are exact zeros that no
+    // only the first rks_s[k] rows of R_{k-1}, hence of X, are nonzero (found by the left
+    // pass): the Jacobi runs on those rows (an even count; the rest are exact zeros that no
     // rotation would touch)
-    int mJ = 1;
-    for (int t = 0; t < k && mJ < n; ++t) mJ = (mJ * D < n) ? mJ * D : n;
+    int mJ = rks_s[k] < n ? rks_s[k] : n;  // nonzero rows of R_{k-1} (k >= 1 here)
     mJ += (mJ & 1);
     const int sweeps = hestenes_rows<T, GeoLr<G>::value>(X, mJ < mX ? mJ : mX, Lr, LX, flag, w.ctr, w.red, sig);
     if (sweeps < 0 && tid == 0) *st |= ST_NOCONV;
