@@ -1303,48 +1303,136 @@ __device__ double env_first_row(const G& g, T* Eout, const T* Tpad, int row, con
 }
 
 // ------------------------------------------------------------------------------------------
+// Quotient m / k for 0 <= m < 2^22 and k >= 1 from a float reciprocal: (m + 1/2) / k lies at
+// least 1 / (2k) from every integer, and the two roundings (of 1 / k and of the product) move it
+// by at most (m + 1/2) 2^-23 / k < 1 / (2k), so truncation gives the exact quotient.  Cheaper
+// than an integer division when k is only known at run time.
+struct FDiv {
+  int k;
+  float r;
+};
+__device__ __forceinline__ FDiv fdiv_of(int k) { return FDiv{k, __frcp_rn((float)k)}; }
+__device__ __forceinline__ int fdiv_q(int m, FDiv d) { return __float2int_rz(((float)m + 0.5f) * d.r); }
+
+// Nonzero prefixes of the bond legs of an upper environment site eu[a][u][x] and a lower one
+// el[b][d][z] (chi x D x chi each): a = 1 + the largest left-bond index with a nonzero entry of
+// eu, x the same for its right bond, b and z for el (each at least 1).  Near the open edges
+// and in the first rows the boundary MPS's bonds are smaller than chi and the row step stores
+// them zero-padded (its kept singular values come in descending order, the zero ones last), so
+// a contraction over such a bond can stop at the prefix: the skipped terms are exact zeros and
+// the kept ones are summed in the same order, which leaves every result unchanged.  NaN and Inf
+// entries count as nonzero.  Ends with a barrier; every thread gets the same extents.
+struct BondExt {
+  int a, x, b, z;
+};
+template <typename T, typename G>
+__device__ BondExt bond_ext(const G& g, const T* eu, const T* el) {
+  __shared__ int ext_w[32][4];
+  const int chi = g.chi, Dc = g.D * g.chi;
+  int ea = 0, ex = 0, eb = 0, ez = 0;
+  for (int o = threadIdx.x; o < g.se; o += blockDim.x) {
+    const int a = o / Dc + 1, x = o % chi + 1;
+    if (eu[o] != T(0)) { ea = max(ea, a); ex = max(ex, x); }
+    if (el[o] != T(0)) { eb = max(eb, a); ez = max(ez, x); }
+  }
+  const unsigned full = 0xffffffffu;
+  ea = (int)__reduce_max_sync(full, (unsigned)ea);
+  ex = (int)__reduce_max_sync(full, (unsigned)ex);
+  eb = (int)__reduce_max_sync(full, (unsigned)eb);
+  ez = (int)__reduce_max_sync(full, (unsigned)ez);
+  if ((threadIdx.x & 31) == 0) {
+    int* w = ext_w[threadIdx.x >> 5];
+    w[0] = ea; w[1] = ex; w[2] = eb; w[3] = ez;
+  }
+  __syncthreads();
+  BondExt e{1, 1, 1, 1};
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+    e.a = max(e.a, ext_w[i][0]);
+    e.x = max(e.x, ext_w[i][1]);
+    e.b = max(e.b, ext_w[i][2]);
+    e.z = max(e.z, ext_w[i][3]);
+  }
+  return e;
+}
+
+// Zero v[p][q][r] (P x Q x R, row major) outside p < kp, r < kr.  Ends with a barrier.
+template <typename T>
+__device__ void zero_outside(T* v, int P, int Q, int R, int kp, int kr) {
+  if (kp >= P && kr >= R) return;
+  const int QR = Q * R;
+  for (int o = threadIdx.x; o < P * QR; o += blockDim.x)
+    if (o / QR >= kp || o % R >= kr) v[o] = T(0);
+  __syncthreads();
+}
+
 // ------------------------------------------------------------------------------------------
 // One-row sandwich partials.  L[a][l][b] -> L'[x][r][z] over one column with eu[a][u][x],
 // A[l][u][r][d], el[b][d][z].  t1: chi*chi*D*D, t2: D*D*chi*(chi+1) elements.  The
 // intermediates are laid out so that the index that varies across threads is contiguous in the
 // operand it is read from; t2's (x, r) rows are padded to D (chi + 1), so that the two column
 // groups a warp reads in the last product (16 rows per group at chi = 16) fall in different
-// shared-memory banks.
+// shared-memory banks.  The bond indices run over the nonzero prefixes of bond_ext (a < ka,
+// b < kb, x < kx, z < kz): the intermediates keep their full layouts, entries outside the
+// prefixes are neither computed nor read, and L' is zero outside x < kx, z < kz.
 template <typename T, typename G>
 __device__ void absorb1(const G& g, const T* L, const T* eu, const T* A, const T* el, T* t1, T* t2, T* out) {
   const int chi = g.chi, D = g.D;
   const int PS = D * chi + D;  // padded (x, r) row stride of t2
+  const BondExt e = bond_ext(g, eu, el);
+  const int kb = e.b, kx = e.x;
+  const FDiv fb = fdiv_of(kb), fx = fdiv_of(kx);
   // t1[u][l][x][b] = sum_a L[a][l][b] eu[a][u][x]        (m = (l, b), n = (u, x), k = a)
-  blk_gemm<2, 8>(L, eu, t1, D * chi, D * chi, chi, 1, D * chi, 0, D * chi, 0,
-                 [=](int m) { return Off2{m, (m / chi) * chi * chi + m % chi}; },
-                 [=](int n) { return Off2{n, (n / chi) * D * chi * chi + (n % chi) * chi}; });
+  blk_gemm<2, 8>(L, eu, t1, D * kb, D * kx, e.a, 1, D * chi, 0, D * chi, 0,
+                 [=](int m) {
+                   const int l = fdiv_q(m, fb), b = m - l * kb;
+                   return Off2{l * chi + b, l * chi * chi + b};
+                 },
+                 [=](int n) {
+                   const int u = fdiv_q(n, fx), x = n - u * kx;
+                   return Off2{u * chi + x, u * D * chi * chi + x * chi};
+                 });
   // t2[x][r][d][b] = sum_{l,u} t1[u][l][x][b] A[l][u][r][d]   (m = (x, b), n = (r, d), k = (l, u))
-  blk_gemm<4, 4>(t1, A, t2, chi * chi, D * D, D, D, chi * chi, D * chi * chi, D * D * D, D * D,
-                 [=](int m) { return Off2{m, (m / chi) * D * PS + m % chi}; },
+  blk_gemm<4, 4>(t1, A, t2, kx * kb, D * D, D, D, chi * chi, D * chi * chi, D * D * D, D * D,
+                 [=](int m) {
+                   const int x = fdiv_q(m, fb), b = m - x * kb;
+                   return Off2{x * chi + b, x * D * PS + b};
+                 },
                  [=](int n) { return Off2{n, (n / D) * PS + (n % D) * chi}; });
   // out[x][r][z] = sum_{b,d} el[b][d][z] t2[x][r][d][b]      (m = z, n = (x, r), k = (b, d))
-  blk_gemm<1, 4>(el, t2, out, chi, chi * D, chi, D, D * chi, chi, 1, chi,
+  blk_gemm<1, 4>(el, t2, out, e.z, kx * D, kb, D, D * chi, chi, 1, chi,
                  [=](int m) { return Off2{m, m}; },
                  [=](int n) { return Off2{n * PS, n * chi}; });
+  zero_outside(out, chi, D, chi, kx, e.z);
 }
 
 // R[x][r][z] -> R'[a][l][b] = sum eu[a][u][x] A[l][u][r][d] el[b][d][z] R[x][r][z].
-// t1: D^2 chi (chi+1) elements (its rows padded to chi+1), t2: chi^2 D^2.
+// t1: D^2 chi (chi+1) elements (its rows padded to chi+1), t2: chi^2 D^2.  Bond indices over
+// the nonzero prefixes of bond_ext, as in absorb1; R' is zero outside a < ka, b < kb.
 template <typename T, typename G>
 __device__ void absorb1_right(const G& g, const T* R, const T* eu, const T* A, const T* el, T* t1, T* t2, T* out) {
   const int chi = g.chi, D = g.D, P = chi + 1;
+  const BondExt e = bond_ext(g, eu, el);
+  const int ka = e.a, kz = e.z;
+  const FDiv fz = fdiv_of(kz), fa = fdiv_of(ka);
   // t1[u][r][z][a] (rows of a padded to P) = sum_x R[x][r][z] eu[a][u][x]   (m = (r, z), n = (a, u))
-  blk_gemm<2, 8>(R, eu, t1, D * chi, chi * D, chi, 1, D * chi, 0, 1, 0,
-                 [=](int m) { return Off2{m, m * P}; },
+  blk_gemm<2, 8>(R, eu, t1, D * kz, ka * D, e.x, 1, D * chi, 0, 1, 0,
+                 [=](int m) {
+                   const int r = fdiv_q(m, fz), z = m - r * kz;
+                   return Off2{r * chi + z, (r * chi + z) * P};
+                 },
                  [=](int n) { return Off2{n * chi, (n % D) * D * chi * P + n / D}; });
   // t2[z][d][a][l] = sum_{u,r} t1[u][r][z][a] A[l][u][r][d]   (m = (z, a), n = (l, d), k = (u, r))
-  blk_gemm<4, 4>(t1, A, t2, chi * chi, D * D, D, D, D * chi * P, chi * P, D * D, D,
-                 [=](int m) { return Off2{(m / chi) * P + m % chi, (m / chi) * D * chi * D + (m % chi) * D}; },
+  blk_gemm<4, 4>(t1, A, t2, kz * ka, D * D, D, D, D * chi * P, chi * P, D * D, D,
+                 [=](int m) {
+                   const int z = fdiv_q(m, fa), a = m - z * ka;
+                   return Off2{z * P + a, z * D * chi * D + a * D};
+                 },
                  [=](int n) { return Off2{(n / D) * D * D * D + n % D, (n % D) * chi * D + n / D}; });
   // out[a][l][b] = sum_{z,d} t2[z][d][a][l] el[b][d][z]   (m = (a, l), n = b, k = (z, d))
-  blk_gemm<2, 2>(t2, el, out, chi * D, chi, chi, D, D * chi * D, chi * D, 1, chi,
+  blk_gemm<2, 2>(t2, el, out, ka * D, e.b, kz, D, D * chi * D, chi * D, 1, chi,
                  [=](int m) { return Off2{m, m * chi}; },
                  [=](int n) { return Off2{n * D * chi, n}; });
+  zero_outside(out, chi, D, chi, ka, e.b);
 }
 
 // Site environment of the one-row sandwich: env[l][u][r][d] = sum L[a][l][b] eu[a][u][x]
@@ -1421,69 +1509,91 @@ __device__ T mps_overlap(const G& g, const T* EU, const T* EL, T* Lb, T* Lb2, T*
 // (absorb2_right) so that the temporaries hold D^3 chi c elements (c <= cx; absorb2_right's
 // first temporary holds chi more).  Intermediates are laid out so that the index that varies
 // across threads is contiguous in the operand it is read from.
-// L2[a][i][j][b] -> out[x][r1][r2][z] with eu[a][u][x], A1[i][u][r1][v], A2[j][v][r2][d], el[b][d][z]
+// L2[a][i][j][b] -> out[x][r1][r2][z] with eu[a][u][x], A1[i][u][r1][v], A2[j][v][r2][d], el[b][d][z].
+// Bond indices over the nonzero prefixes of bond_ext, as in absorb1 (the chunks cover x < kx);
+// out is zero outside x < kx, z < kz.
 template <typename T, typename G>
 __device__ void absorb2(const G& g, const T* L2, const T* eu, const T* A1, const T* A2, const T* el,
                         T* t1, T* t2, T* out, int cx) {
   const int chi = g.chi, D = g.D;
-  for (int x0 = 0; x0 < chi; x0 += cx) {
-    const int c = (chi - x0 < cx) ? chi - x0 : cx;
+  const BondExt e = bond_ext(g, eu, el);
+  const int kb = e.b, kx = e.x;
+  const FDiv fb = fdiv_of(kb);
+  for (int x0 = 0; x0 < kx; x0 += cx) {
+    const int c = (kx - x0 < cx) ? kx - x0 : cx;
     const int cc = chi * c;
+    const FDiv fbc = fdiv_of(kb * c);
     // t1[i][u][j][b][xx] = sum_a L2[a][i][j][b] eu[a][u][x0+xx]      (m = (i, j, b), n = (u, xx))
-    blk_gemm<4, 4>(L2, eu + x0, t1, D * D * chi, D * c, chi, 1, D * D * chi, 0, D * chi, 0,
-                   [=](int m) { return Off2{m, (m / (D * chi)) * D * D * cc + (m % (D * chi)) * c}; },
+    blk_gemm<4, 4>(L2, eu + x0, t1, D * D * kb, D * c, e.a, 1, D * D * chi, 0, D * chi, 0,
+                   [=](int m) {
+                     const int ij = fdiv_q(m, fb), b = m - ij * kb;
+                     return Off2{ij * chi + b, (ij / D) * D * D * cc + ((ij % D) * chi + b) * c};
+                   },
                    [=](int n) { return Off2{(n / c) * chi + n % c, (n / c) * D * cc + n % c}; });
     // t2[j][v][b][xx][r1] = sum_{i,u} t1[i][u][j][b][xx] A1[i][u][r1][v]   (m = (j, b, xx), n = (r1, v))
-    blk_gemm<4, 4>(t1, A1, t2, D * cc, D * D, D, D, D * D * cc, D * cc, D * D * D, D * D,
-                   [=](int m) { return Off2{m, (m / cc) * D * D * cc + (m % cc) * D}; },
+    blk_gemm<4, 4>(t1, A1, t2, D * kb * c, D * D, D, D, D * D * cc, D * cc, D * D * D, D * D,
+                   [=](int m) {
+                     const int j = fdiv_q(m, fbc), rem = m - j * kb * c;
+                     return Off2{j * cc + rem, j * D * D * cc + rem * D};
+                   },
                    [=](int n) { return Off2{n, (n % D) * cc * D + n / D}; });
     // t3[r2][d][b][xx][r1] = sum_{j,v} t2[j][v][b][xx][r1] A2[j][v][r2][d]   (into t1; m = (b, xx, r1), n = (r2, d))
-    blk_gemm<4, 4>(t2, A2, t1, cc * D, D * D, D, D, D * cc * D, cc * D, D * D * D, D * D,
+    blk_gemm<4, 4>(t2, A2, t1, kb * c * D, D * D, D, D, D * cc * D, cc * D, D * D * D, D * D,
                    [=](int m) { return Off2{m, m}; },
                    [=](int n) { return Off2{n, n * cc * D}; });
     // out[x0+xx][r1][r2][z] = sum_{b,d} el[b][d][z] t3[r2][d][b][xx][r1]   (m = z, n = (xx, r2, r1)
     // with r1 fastest: the two column groups of a warp then read adjacent words of t3)
-    blk_gemm<1, 4>(el, t1, out, chi, c * D * D, chi, D, D * chi, chi, c * D, cc * D,
+    blk_gemm<1, 4>(el, t1, out, e.z, c * D * D, kb, D, D * chi, chi, c * D, cc * D,
                    [=](int m) { return Off2{m, m}; },
                    [=](int n) {
                      const int xx = n / (D * D), r2 = (n / D) % D, r1 = n % D;
                      return Off2{r2 * D * cc * D + xx * D + r1, (((x0 + xx) * D + r1) * D + r2) * chi};
                    });
   }
+  zero_outside(out, chi, D * D, chi, kx, e.z);
 }
 
-// R2[x][r1][r2][z] -> out[a][i][j][b] = sum eu[a][u][x] A1[i][u][r1][v] A2[j][v][r2][d] el[b][d][z] R2[x][r1][r2][z]
+// R2[x][r1][r2][z] -> out[a][i][j][b] = sum eu[a][u][x] A1[i][u][r1][v] A2[j][v][r2][d] el[b][d][z] R2[x][r1][r2][z].
+// Bond indices over the nonzero prefixes of bond_ext (the chunks cover a < ka); out is zero
+// outside a < ka, b < kb.
 template <typename T, typename G>
 __device__ void absorb2_right(const G& g, const T* R2, const T* eu, const T* A1, const T* A2, const T* el,
                               T* t1, T* t2, T* out, int ca) {
   const int chi = g.chi, D = g.D;
-  for (int a0 = 0; a0 < chi; a0 += ca) {
-    const int c = (chi - a0 < ca) ? chi - a0 : ca;
+  const BondExt e = bond_ext(g, eu, el);
+  const int ka = e.a, kz = e.z;
+  const FDiv fz = fdiv_of(kz);
+  for (int a0 = 0; a0 < ka; a0 += ca) {
+    const int c = (ka - a0 < ca) ? ka - a0 : ca;
     const int cdx = c * D * chi;             // one (u, r1) block of t1, one (v, r2) block of t2
     const int Sz = D * c * D * D + 1;        // z stride of t3 (odd: consecutive z in different banks)
     // t1[u][r1][aa][r2][z] = sum_x R2[x][r1][r2][z] eu[a0+aa][u][x]   (m = (r1, r2, z), n = (aa, u))
-    blk_gemm<4, 4>(R2, eu + (size_t)a0 * D * chi, t1, D * D * chi, c * D, chi, 1, D * D * chi, 0, 1, 0,
-                   [=](int m) { return Off2{m, (m / (D * chi)) * cdx + m % (D * chi)}; },
+    blk_gemm<4, 4>(R2, eu + (size_t)a0 * D * chi, t1, D * D * kz, c * D, e.x, 1, D * D * chi, 0, 1, 0,
+                   [=](int m) {
+                     const int q = fdiv_q(m, fz), z = m - q * kz;  // q = (r1, r2)
+                     return Off2{q * chi + z, (q / D) * cdx + (q % D) * chi + z};
+                   },
                    [=](int n) { return Off2{n * chi, (n % D) * D * cdx + (n / D) * D * chi}; });
     // t2[v][r2][aa][i][z] = sum_{u,r1} t1[u][r1][aa][r2][z] A1[i][u][r1][v]   (m = (aa, r2, z), n = (i, v))
-    blk_gemm<4, 4>(t1, A1, t2, cdx, D * D, D, D, D * cdx, cdx, D * D, D,
+    blk_gemm<4, 4>(t1, A1, t2, c * D * kz, D * D, D, D, D * cdx, cdx, D * D, D,
                    [=](int m) {
-                     const int aa = m / (D * chi), r2 = (m / chi) % D, z = m % chi;
-                     return Off2{m, r2 * cdx + aa * D * chi + z};
+                     const int q = fdiv_q(m, fz), z = m - q * kz;  // q = (aa, r2)
+                     return Off2{q * chi + z, (q % D) * cdx + (q / D) * D * chi + z};
                    },
                    [=](int n) { return Off2{(n / D) * D * D * D + n % D, (n % D) * D * cdx + (n / D) * chi}; });
     // t3[z][d][aa][i][j] (z stride Sz) = sum_{v,r2} t2[v][r2][aa][i][z] A2[j][v][r2][d]   (into t1)
-    blk_gemm<4, 4>(t2, A2, t1, cdx, D * D, D, D, D * cdx, cdx, D * D, D,
+    blk_gemm<4, 4>(t2, A2, t1, c * D * kz, D * D, D, D, D * cdx, cdx, D * D, D,
                    [=](int m) {
-                     const int aa = m / (D * chi), i = (m / chi) % D, z = m % chi;
-                     return Off2{m, z * Sz + aa * D * D + i * D};
+                     const int q = fdiv_q(m, fz), z = m - q * kz;  // q = (aa, i)
+                     return Off2{q * chi + z, z * Sz + q * D};
                    },
                    [=](int n) { return Off2{(n / D) * D * D * D + n % D, (n % D) * c * D * D + n / D}; });
     // out[a0+aa][i][j][b] = sum_{z,d} t3[z][d][aa][i][j] el[b][d][z]   (m = (aa, i, j), n = b)
-    blk_gemm<2, 4>(t1, el, out, c * D * D, chi, chi, D, Sz, c * D * D, 1, chi,
+    blk_gemm<2, 4>(t1, el, out, c * D * D, e.b, kz, D, Sz, c * D * D, 1, chi,
                    [=](int m) { return Off2{m, (a0 * D * D + m) * chi}; },
                    [=](int n) { return Off2{n * D * chi, n}; });
   }
+  zero_outside(out, chi, D * D, chi, ka, e.b);
 }
 
 // ------------------------------------------------------------------------------------------
