@@ -210,7 +210,7 @@ def _peaks():
 # the current kernels exists.  profiles/sampler_split_heis8x8_D4_chi16_ns304.md: 1.277 GB per call
 # of 2 sweeps over 304 chains (k_env one-side pass 0.223 GB, 16 k_sweep_moves 0.739 GB, 12
 # k_env_row 0.315 GB).
-_SAMPLER_CAPTURE = {"bytes": 1.277e9, "chains": 304, "sweeps": 2}
+_SAMPLER_CAPTURE = {"bytes": 1.250e9, "chains": 304, "sweeps": 2}
 
 
 def _measured_traffic(kernel, ns, sweeps, prec):
@@ -501,7 +501,9 @@ def _fp64_plain(a, P, make, theta, S_fp32, H, ns, seed, sweep0, mask, tau, value
     r64 = h64.evaluate(H, S, want_O=False)
     ok = ((r32["status"] & mask) == 0) & ((r64["status"] & mask) == 0)
     d_e = float(((r32["eloc"][:, 0] - r64["eloc"][:, 0])[ok]).mean().abs()) / lat.nsites
-    d_l = float((r32["logabs"] - r64["logabs"])[ok].abs().max())
+    dl_all = (r32["logabs"] - r64["logabs"])[ok].abs().double().cpu().numpy()
+    de_all = ((r32["eloc"][:, 0] - r64["eloc"][:, 0])[ok].abs() / lat.nsites).double().cpu().numpy()
+    d_l = float(dl_all.max())
     h32e.close()
     acc = torch.zeros(ns, dtype=torch.int64, device="cuda")
     O = torch.empty(ns, h64.Np, dtype=torch.float64, device="cuda")
@@ -531,6 +533,13 @@ def _fp64_plain(a, P, make, theta, S_fp32, H, ns, seed, sweep0, mask, tau, value
             "what": "FP64 contractions, FP64 Gram, FP64 Cholesky, same chains and step",
             "energy_converged_samples_per_s": v64 / tau,
             "fp32_vs_fp64_same_configs": {"mean_eloc_diff_per_site": d_e, "max_dlogpsi": d_l,
+                                          "median_dlogpsi": float(np.median(dl_all)),
+                                          "p99_dlogpsi": float(np.quantile(dl_all, 0.99)),
+                                          "samples_dlogpsi_over_1e-5": int((dl_all > 1e-5).sum()),
+                                          "samples_dlogpsi_over_1e-3": int((dl_all > 1e-3).sum()),
+                                          "max_deloc_per_site": float(de_all.max()),
+                                          "median_deloc_per_site": float(np.median(de_all)),
+                                          "samples_deloc_per_site_over_1e-4": int((de_all > 1e-4).sum()),
                                           "samples": int(ok.sum().item()),
                                           "gate_per_site": 1e-4, "equal_energy_error": d_e <= 1e-4},
             "fp32_over_fp64_energy_converged": value32 / v64}
