@@ -48,6 +48,9 @@ def _args():
     ap.add_argument("--cpu-samples", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--solve", default=None, choices=["ff", "fp64", "fp32"],
+                    help="MinSR Cholesky: float-float factor + FP64 refinement (FP32 default), FP64 "
+                         "(FP64 default), or FP32 factor + FP64 refinement")
     ap.add_argument("--gram", default=None, choices=["ff", "fp64", "bf16"],
                     help="MinSR Gram of the step: float-float on the FP32 pipes (default with --prec fp32), "
                          "FP64 (default with --prec fp64), or split-BF16 tcgen05")
@@ -270,18 +273,19 @@ def run_gpu(a):
     nbonds = len(H["terms"])
     theta0 = I.peps_random(lat, w["seed_theta"], **w["init"])
     S0 = I.configs_neel(lat, ns)
-    gram = {"fp64": 0, "bf16": 1, "ff": 2}[a.gram or ("ff" if a.prec == "fp32" else "fp64")]  # the solve stays FP64 Cholesky
+    gram = {"fp64": 0, "bf16": 1, "ff": 2}[a.gram or ("ff" if a.prec == "fp32" else "fp64")]
+    solve = {"fp64": 0, "fp32": 1, "ff": 2}[a.solve or ("ff" if a.prec == "fp32" else "fp64")]
     mask = P.ST_ZERO_NORM | P.ST_NONFINITE | P.ST_NOCONV   # samples left out of E_loc and MinSR
     seed = w["seed_chain"] + 7919 * rank                    # every process its own chains
 
-    def make(prec_, ns_, gram_):
-        h_ = P.PEPS(lat.Lx, lat.Ly, lat.d, lat.D, w["chi"], prec=prec_, max_samples=ns_, gram=gram_, solve=0)
+    def make(prec_, ns_, gram_, solve_=0):
+        h_ = P.PEPS(lat.Lx, lat.Ly, lat.d, lat.D, w["chi"], prec=prec_, max_samples=ns_, gram=gram_, solve=solve_)
         th_ = torch.as_tensor(theta0).cuda()
         h_.set_params(th_)
         h_.set_env_reuse(True)  # the evaluation takes the sampler's last environments (cached, unchanged S)
         return h_, th_
 
-    h, theta = make(prec, ns, gram)
+    h, theta = make(prec, ns, gram, solve)
     S = torch.as_tensor(S0).cuda()
     acc = torch.zeros(ns, dtype=torch.int64, device="cuda")
     O = torch.empty(ns, h.Np, dtype=h.odtype, device="cuda")
@@ -419,13 +423,15 @@ def run_gpu(a):
             "config": _config(w, ns, a.sweeps), "step_ms": step_ms, "minsr_step_s": minsr_s,
             "minsr": {"gram": {0: "FP64 CUDA cores", 1: "split-BF16 tcgen05",
                                2: "float-float pairs on the FP32 pipes"}[gram],
-                      "solve": "FP64 Cholesky", "sharded_over_processes": world > 1,
+                      "solve": {0: "FP64 Cholesky", 1: "FP32 Cholesky + FP64 refinement",
+                                2: "float-float Cholesky + FP64 refinement"}[solve],
+                      "sharded_over_processes": world > 1,
                       "gram_ms": ms_cls["minsr_gram"] / a.steps, "solve_ms": ms_cls["minsr_eig"] / a.steps,
                       "gram_tflops_algorithmic": (flops["minsr_gram"] / a.steps /
                                                   max(1e-9, ms_cls["minsr_gram"] / a.steps / 1e3) / 1e12),
                       "gram_pipe_frac": (costmodel.gram_pipe_flops(ns, h.Np, gram) /
                                          max(1e-9, ms_cls["minsr_gram"] / a.steps / 1e3) / 1e12 / gram_peak),
-                      "dtheta_rel_diff_vs_fp64_gram": dtheta_check,
+                      "dtheta_rel_diff_vs_fp64_gram_and_solve": dtheta_check,
                       "last_info": [float(x) for x in info_hist[-1].cpu()]},
             "kernel_ms_per_step": {k: v / a.steps for k, v in ms_cls.items()},
             "jacobi": {"svds": int(ctr["svds"]), "sweeps_per_svd": ctr["jacobi_sweeps"] / svd_all,
@@ -497,9 +503,13 @@ def _fp64_plain(a, P, make, theta, S_fp32, H, ns, seed, sweep0, mask, tau, value
     h32e.set_params(th32)
     S = S_fp32.clone()
     # the same configurations through both precisions (no parameter update in between)
-    r32 = h32e.evaluate(H, S, want_O=False)
-    r64 = h64.evaluate(H, S, want_O=False)
+    r32 = h32e.evaluate(H, S)
+    r64 = h64.evaluate(H, S)
     ok = ((r32["status"] & mask) == 0) & ((r64["status"] & mask) == 0)
+    # O rows: largest |O32 - O64| over each row's largest |O64|
+    dO_all = ((r32["O"].double() - r64["O"]).abs().amax(dim=1) /
+              r64["O"].abs().amax(dim=1).clamp_min(1e-300))[ok].cpu().numpy()
+    del r32["O"], r64["O"]
     d_e = float(((r32["eloc"][:, 0] - r64["eloc"][:, 0])[ok]).mean().abs()) / lat.nsites
     dl_all = (r32["logabs"] - r64["logabs"])[ok].abs().double().cpu().numpy()
     de_all = ((r32["eloc"][:, 0] - r64["eloc"][:, 0])[ok].abs() / lat.nsites).double().cpu().numpy()
@@ -540,6 +550,9 @@ def _fp64_plain(a, P, make, theta, S_fp32, H, ns, seed, sweep0, mask, tau, value
                                           "max_deloc_per_site": float(de_all.max()),
                                           "median_deloc_per_site": float(np.median(de_all)),
                                           "samples_deloc_per_site_over_1e-4": int((de_all > 1e-4).sum()),
+                                          "median_dO_row_rel": float(np.median(dO_all)),
+                                          "p99_dO_row_rel": float(np.quantile(dO_all, 0.99)),
+                                          "max_dO_row_rel": float(dO_all.max()),
                                           "samples": int(ok.sum().item()),
                                           "gate_per_site": 1e-4, "equal_energy_error": d_e <= 1e-4},
             "fp32_over_fp64_energy_converged": value32 / v64}

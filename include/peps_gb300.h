@@ -81,8 +81,8 @@ enum {
  * MIXED: the reduced-precision preset of the whole step: the FP32 contraction kernels (CUDA
  * cores; logarithms, E_loc and O's scale in double), the MinSR Gram as float-float pairs on the
  * FP32 pipes (cfg.gram == 0 becomes 2; 1 keeps the split-BF16 tensor-core Gram) and the solve as
- * an FP32 Cholesky with FP64 refinement and an FP64 fallback (cfg.solve becomes 1); the handle
- * then reports FP32 (its O is float). */
+ * a float-float Cholesky with FP64 refinement and an FP64 fallback (cfg.solve becomes 2); the
+ * handle then reports FP32 (its O is float). */
 typedef enum { PEPS_PREC_FP64 = 0, PEPS_PREC_FP32 = 1, PEPS_PREC_MIXED = 2 } peps_prec;
 
 typedef enum { PEPS_MOVE_EXCHANGE = 0, PEPS_MOVE_FLIP = 1 } peps_move;
@@ -102,7 +102,11 @@ typedef struct {
                      GPUs whose FP64 rate is a small fraction of their FP32 rate)          */
     int solve;    /* MinSR solve when rcond == 0: 0 = FP64 Cholesky; 1 = FP32 Cholesky of
                      T + lambda followed by 4 steps of iterative refinement with FP64 residuals
-                     (info[1] reports the final relative residual)                           */
+                     (info[1] reports the final relative residual); 2 = float-float Cholesky
+                     (T + lambda as float pairs of about 48 bits, the trailing updates on the
+                     FP32 pipes, diagonal blocks and panels in FP64) followed by 2 steps of
+                     refinement with FP64 residuals: the FP64 factor's work at a fraction of
+                     its time on GPUs whose FP64 rate is a small fraction of their FP32 rate */
     int cplx;     /* 0 = real PEPS; 1 = complex PEPS: theta is N_p (re, im) pairs of doubles,
                      O is N_s x N_p complex numbers in the handle's precision ((re, im) pairs
                      of doubles or floats), phases and E_loc are complex.  Not with gram = 1,
@@ -284,13 +288,16 @@ peps_status peps_local_energy_bound(peps_handle* h, const peps_hamiltonian* H, c
  * operator (T + lambda)^-1 applied through a Cholesky factorisation, info = (Ns, NaN, NaN, -1)
  * with cfg.solve == 0, info = (Ns, |ebar - (T + lambda) x| / |ebar|, refinement steps, -1)
  * with cfg.solve == 1, where refinement steps = 0 means that the FP32 factor failed or the
- * refined residual stayed above 1e-10 and the FP64 factorisation was used instead.  When T +
+ * refined residual stayed above 1e-10 and the FP64 factorisation was used instead; the same
+ * with cfg.solve == 2, where the FP64 factorisation replaces the float-float one only when the
+ * latter breaks down (a pivot that is not positive).  When T +
  * lambda is not positive definite in floating point even in FP64 (lambda far below the
  * rounding error of T, e.g. a split-BF16 Gram of badly scaled O), info[0] = -1, dtheta_dev is
  * set to zero and the status word gets PEPS_SW_MINSR_BREAKDOWN (peps_last_status then returns
  * PEPS_W_NUMERIC).  Needs lambda > 0 or rcond > 0.  The Gram matrix is FP64 (cfg.gram == 0), split
  * BF16 on the tensor cores (cfg.gram == 1) or float-float on the FP32 pipes (cfg.gram == 2);
- * the factorisation / eigendecomposition is FP64.  The call is
+ * the factorisation is FP64, FP32 or float-float (cfg.solve), the eigendecomposition FP64, the
+ * residuals of the refinement FP64.  The call is
  * asynchronous like every other (no host round trip: the mixed solve's FP64 fallback and the
  * zeroing of dtheta on a breakdown are decided on the device; rcond > 0 runs the whole cyclic
  * Jacobi in one cooperative launch); a breakdown is reported by peps_last_status. */

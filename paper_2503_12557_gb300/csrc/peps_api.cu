@@ -396,13 +396,13 @@ extern "C" peps_status peps_create_ex(peps_handle** out, const peps_config* cfg,
   if (c.prec != PEPS_PREC_FP64 && c.prec != PEPS_PREC_FP32 && c.prec != PEPS_PREC_MIXED) return PEPS_E_ARG;
   if (c.prec == PEPS_PREC_MIXED) {
     // the mixed-precision preset: the FP32 contraction kernels, a float-float Gram unless the
-    // caller asked for the tensor-core one, and the FP32 Cholesky with FP64 refinement
+    // caller asked for the tensor-core one, and the float-float Cholesky with FP64 refinement
     c.prec = PEPS_PREC_FP32;
     if (c.gram == 0) c.gram = 2;
-    c.solve = 1;
+    c.solve = 2;
   }
   if (c.gram != 0 && c.gram != 1 && c.gram != 2) return PEPS_E_ARG;
-  if (c.solve != 0 && c.solve != 1) return PEPS_E_ARG;
+  if (c.solve != 0 && c.solve != 1 && c.solve != 2) return PEPS_E_ARG;
   if (c.cplx != 0 && c.cplx != 1) return PEPS_E_ARG;
   if (!(c.trunc_weight >= 0.0 && c.trunc_weight < 1.0)) return PEPS_E_ARG;
   if (c.cplx && c.gram == 1) return PEPS_E_UNSUPPORTED;  // the split-BF16 Gram is real only
@@ -1042,13 +1042,19 @@ static peps_status minsr_solve_core(peps_handle* h, int Ns, double lambda, doubl
     // FP64 fallback is enqueued behind a device flag, so no host decision is needed.
     const int ts = tstart(h, TC_EIG, s);
     long long nl = 0;
-    if (h->cfg.solve == 1) {
-      nl = chol_solve_mixed(h->Tm, (float*)h->Vm, n, Ns, lambda, h->ebar, h->xv, h->yv, h->cnt + 6, h->Hm, 4,
-                            (int*)h->cnt, info_dev, need64, s, &e);
+    if (h->cfg.solve == 1 || h->cfg.solve == 2) {
+      // h->Hm: the residual norms' block partials at its start, the solves' vector from n on;
+      // h->Vm (n x n doubles) holds the FP32 factor, or the float-float factor's two n x n halves
+      if (h->cfg.solve == 1)
+        nl = chol_solve_mixed(h->Tm, (float*)h->Vm, n, Ns, lambda, h->ebar, h->xv, h->yv, h->cnt + 6, h->Hm, 4,
+                              (int*)h->cnt, info_dev, need64, h->Hm + n, s, &e);
+      else
+        nl = chol_solve_ff(h->Tm, (float*)h->Vm, (float*)h->Vm + (size_t)n * n, n, Ns, lambda, h->ebar, h->xv, h->yv,
+                           h->cnt + 6, h->Hm, 2, (int*)h->cnt, info_dev, need64, h->Hm + n, s, &e);
       if (e != cudaSuccess) return cuda_fail(h, e, "Cholesky");
-      nl += chol_solve(h->Tm, n, Ns, lambda, h->ebar, h->xv, (int*)h->cnt, info_dev, need64, s, &e);
+      nl += chol_solve(h->Tm, n, Ns, lambda, h->ebar, h->xv, (int*)h->cnt, info_dev, need64, h->yv, s, &e);
     } else {
-      nl = chol_solve(h->Tm, n, Ns, lambda, h->ebar, h->xv, (int*)h->cnt, info_dev, nullptr, s, &e);
+      nl = chol_solve(h->Tm, n, Ns, lambda, h->ebar, h->xv, (int*)h->cnt, info_dev, nullptr, h->yv, s, &e);
     }
     if (e != cudaSuccess) return cuda_fail(h, e, "Cholesky");
     tstop(h, ts, s, nl);

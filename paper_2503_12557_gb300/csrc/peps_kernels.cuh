@@ -241,17 +241,23 @@ cudaError_t launch_obar_t_x(const double* Obar, const double* x, int Ns, long lo
                             cudaStream_t s);
 // x = (A + lambda I)^-1 ebar by blocked Cholesky (A overwritten by its factor); returns launches
 // gate (device flag, may be NULL): every launch does nothing while *gate == 0 (the FP64
-// fallback of the mixed solve, decided on the device); a gated run sets info[2] = 0
+// fallback of the mixed solve, decided on the device); a gated run sets info[2] = 0;
+// scratch: n doubles (the triangular solves' intermediate vector)
 long long chol_solve(double* A, int n, int nreal, double lambda, const double* ebar, double* x, int* bad,
-                     double* info, const int* gate, cudaStream_t s, cudaError_t* err);
+                     double* info, const int* gate, double* scratch, cudaStream_t s, cudaError_t* err);
 // the same solve with an FP32 factor (A32: n x n floats, A kept and mirrored to full) and
 // `iters` refinement steps with FP64 residuals (r: n doubles, rn: 2 doubles, part: 2 (n + 7) / 8
-// doubles of scratch);
+// doubles of scratch, scratch: n doubles);
 // info = (Ns or -1, relative residual, iters, -); *need64 (device) = 1 when the FP64
 // factorisation must replace it (factor breakdown or relative residual above 1e-10)
 long long chol_solve_mixed(double* A, float* A32, int n, int nreal, double lambda, const double* ebar, double* x,
                            double* r, double* rn, double* part, int iters, int* bad, double* info, int* need64,
-                           cudaStream_t s, cudaError_t* err);
+                           double* scratch, cudaStream_t s, cudaError_t* err);
+// the same with the float-float factor (Fh, Fl: n x n floats each); *need64 = 1 only when the
+// pair factorisation broke down; info = (Ns or -1, relative residual after refinement, iters, -)
+long long chol_solve_ff(double* A, float* Fh, float* Fl, int n, int nreal, double lambda, const double* ebar, double* x,
+                        double* r, double* rn, double* part, int iters, int* bad, double* info, int* need64,
+                        double* scratch, cudaStream_t s, cudaError_t* err);
 // ---- learned proposal (peps_proposal.cu)
 size_t prop_smem_bytes(int Lx, int Ly, int C, int act_bytes, bool train);
 cudaError_t launch_prop_logits(int Lx, int Ly, int C, int wprec, const void* w, const uint8_t* S, int Ns, double* logits,

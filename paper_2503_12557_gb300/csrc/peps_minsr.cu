@@ -596,63 +596,98 @@ cudaError_t launch_axpy(double* y, const double* x, long long n, cudaStream_t s)
 namespace peps {
 constexpr int CB = 64;
 
-// factor the CB x CB diagonal block at (k0, k0) in place (lower triangle), one CTA
+// Storage of the factor: a plain matrix (double or float), or a float pair hi + lo (about 48
+// bits, the float-float factor), read and written through double.
+template <typename T>
+struct FacPlain {
+  T* a;
+  __device__ __forceinline__ double get(size_t o) const { return (double)a[o]; }
+  __device__ __forceinline__ void set(size_t o, double v) const { a[o] = (T)v; }
+};
+struct FacFF {
+  float *h, *l;
+  __device__ __forceinline__ double get(size_t o) const { return (double)h[o] + (double)l[o]; }
+  __device__ __forceinline__ void set(size_t o, double v) const {
+    const float hi = __double2float_rn(v);
+    h[o] = hi;
+    l[o] = __double2float_rn(v - (double)hi);
+  }
+};
+
+// factor the CB x CB diagonal block at (k0, k0) in place (lower triangle), one CTA.  Per column
+// j: thread 0 takes the pivot's square root and its reciprocal; then every thread updates its
+// share of the trailing triangle with column j still unscaled (a_il -= a_ij a_lj / a_jj; four
+// threads per row, the columns of a row interleaved) and scales column j - 1 by its reciprocal
+// (no column is read and written in the same phase): two barriers per column.
 // gate (may be NULL): a device flag; the launch does nothing while it is 0 (a factorisation
 // enqueued before the decision whether it is needed has been taken on the device)
-template <typename T>
-__global__ void __launch_bounds__(256) k_chol_diag(T* A, int n, int k0, int* bad, const int* gate) {
+template <typename T, typename F>
+__global__ void __launch_bounds__(256) k_chol_diag(F A, int n, int k0, int* bad, const int* gate) {
   if (gate && !*gate) return;
   __shared__ T L[CB][CB + 1];
+  __shared__ T rd[CB];
   const int nb = min(CB, n - k0);
-  for (int o = threadIdx.x; o < nb * nb; o += blockDim.x) {
+  const int tid = threadIdx.x, row = tid >> 2, part = tid & 3;
+  for (int o = tid; o < nb * nb; o += blockDim.x) {
     const int i = o / nb, j = o % nb;
-    L[i][j] = A[(size_t)(k0 + i) * n + k0 + j];
+    L[i][j] = (T)A.get((size_t)(k0 + i) * n + k0 + j);
   }
   __syncthreads();
   for (int j = 0; j < nb; ++j) {
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
       const T d = L[j][j];
-      if (!(d > T(0))) { *bad = 1; L[j][j] = T(1); }
-      else L[j][j] = sqrt(d);
+      const bool ok = d > T(0);  // false for NaN too
+      const T dj = ok ? sqrt(d) : T(1);
+      if (!ok) *bad = 1;
+      L[j][j] = dj;
+      rd[j] = T(1) / dj;
     }
     __syncthreads();
-    const T djj = L[j][j];
-    for (int i = j + 1 + threadIdx.x; i < nb; i += blockDim.x) L[i][j] /= djj;
-    __syncthreads();
-    for (int o = threadIdx.x; o < (nb - j - 1) * (nb - j - 1); o += blockDim.x) {
-      const int i = j + 1 + o / (nb - j - 1), l = j + 1 + o % (nb - j - 1);
-      if (l <= i) L[i][l] -= L[i][j] * L[l][j];
+    const T r2 = rd[j] * rd[j];
+    const int i = j + 1 + row;
+    if (i < nb) {
+      const T lij = L[i][j] * r2;
+      for (int l = j + 1 + part; l <= i; l += 4) L[i][l] -= lij * L[l][j];
     }
+    if (j > 0 && tid > j - 1 && tid < nb) L[tid][j - 1] *= rd[j - 1];
     __syncthreads();
   }
-  for (int o = threadIdx.x; o < nb * nb; o += blockDim.x) {
+  if (nb > 0 && tid > nb - 1 && tid < nb) L[tid][nb - 1] *= rd[nb - 1];  // (no row below the last pivot)
+  __syncthreads();
+  for (int o = tid; o < nb * nb; o += blockDim.x) {
     const int i = o / nb, j = o % nb;
-    A[(size_t)(k0 + i) * n + k0 + j] = (j <= i) ? L[i][j] : T(0);
+    A.set((size_t)(k0 + i) * n + k0 + j, (j <= i) ? (double)L[i][j] : 0.0);
   }
 }
 
-// panel below the diagonal block: A_ik <- A_ik L_kk^-T, one CTA per CB rows
-template <typename T>
-__global__ void __launch_bounds__(CB) k_chol_trsm(T* A, int n, int k0, const int* gate) {
+// panel below the diagonal block: A_ik <- A_ik L_kk^-T (the block is full, CB columns: the panel
+// exists only when CB rows follow the diagonal block).  TRSM_RB rows per CTA, one thread per
+// row, the row in registers and solved column by column: each solved entry (times the diagonal
+// reciprocal) updates the later entries, independent multiply-adds.
+constexpr int TRSM_RB = 32;
+template <typename T, typename F>
+__global__ void __launch_bounds__(TRSM_RB) k_chol_trsm(F A, int n, int k0, const int* gate) {
   if (gate && !*gate) return;
   __shared__ T L[CB][CB + 1];
-  __shared__ T X[CB][CB + 1];
-  const int r0 = k0 + CB + blockIdx.x * CB;
-  const int nb = min(CB, n - k0);
-  const int nr = min(CB, n - r0);
-  for (int o = threadIdx.x; o < nb * nb; o += blockDim.x) L[o / nb][o % nb] = A[(size_t)(k0 + o / nb) * n + k0 + o % nb];
-  for (int o = threadIdx.x; o < nr * nb; o += blockDim.x) X[o / nb][o % nb] = A[(size_t)(r0 + o / nb) * n + k0 + o % nb];
+  __shared__ T rd[CB];
+  for (int o = threadIdx.x; o < CB * CB; o += blockDim.x) L[o / CB][o % CB] = (T)A.get((size_t)(k0 + o / CB) * n + k0 + o % CB);
   __syncthreads();
-  const int r = threadIdx.x;
-  if (r < nr) {
-    for (int j = 0; j < nb; ++j) {
-      T s = X[r][j];
-      for (int l = 0; l < j; ++l) s -= X[r][l] * L[j][l];
-      X[r][j] = s / L[j][j];
-    }
+  for (int j = threadIdx.x; j < CB; j += blockDim.x) rd[j] = T(1) / L[j][j];
+  __syncthreads();
+  const int r = k0 + CB + blockIdx.x * TRSM_RB + threadIdx.x;
+  if (r >= n) return;
+  const size_t ar = (size_t)r * n + k0;
+  T x[CB];
+#pragma unroll
+  for (int j = 0; j < CB; ++j) x[j] = (T)A.get(ar + j);
+#pragma unroll
+  for (int j = 0; j < CB; ++j) {
+    x[j] *= rd[j];
+#pragma unroll
+    for (int jj = j + 1; jj < CB; ++jj) x[jj] -= x[j] * L[jj][j];
   }
-  __syncthreads();
-  for (int o = threadIdx.x; o < nr * nb; o += blockDim.x) A[(size_t)(r0 + o / nb) * n + k0 + o % nb] = X[o / nb][o % nb];
+#pragma unroll
+  for (int j = 0; j < CB; ++j) A.set(ar + j, (double)x[j]);
 }
 
 // trailing update A_ij -= A_ik A_jk^T for the lower-triangle tiles right of/below the panel
@@ -692,61 +727,208 @@ __global__ void __launch_bounds__(256) k_chol_update(T* A, int n, int k0, const 
     }
 }
 
+// The same trailing update on the float-float factor: the panel's columns as float pairs, each
+// product a b = (ah + al)(bh + bl) taken as p + e + c (p = ah bh rounded, e its exact error by
+// fma, c = ah bl + al bh; al bl, about 2^-48 of the product, dropped) and summed into a float
+// pair by Knuth's two-sum, as the float-float Gram does; the pair is then subtracted from A_ij
+// with one more two-sum and stored renormalised.
+constexpr int UK = 32;  // panel columns staged per pass (four UK x CB float tiles: 33 KB)
+__global__ void __launch_bounds__(256) k_chol_update_ff(float* Ah, float* Al, int n, int k0, const int* gate) {
+  if (gate && !*gate) return;
+  __shared__ float Ph[UK][CB + 1], Pl[UK][CB + 1], Qh[UK][CB + 1], Ql[UK][CB + 1];
+  const int nt = (n - k0 - CB + CB - 1) / CB;
+  int t = blockIdx.x, ti = 0;
+  while (t >= ti + 1) { t -= ti + 1; ++ti; }
+  const int tj = t;
+  if (ti >= nt) return;
+  const int r0 = k0 + CB + ti * CB, c0 = k0 + CB + tj * CB;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  float sh[4][4], sl[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) { sh[i][j] = 0.f; sl[i][j] = 0.f; }
+  for (int kc = 0; kc < CB; kc += UK) {
+  __syncthreads();
+  for (int o = threadIdx.x; o < UK * CB; o += blockDim.x) {
+    const int rr = o / UK, kk = o % UK;
+    const bool ra = r0 + rr < n, rb = c0 + rr < n;
+    const size_t oa = (size_t)(r0 + rr) * n + k0 + kc + kk, ob = (size_t)(c0 + rr) * n + k0 + kc + kk;
+    Ph[kk][rr] = ra ? Ah[oa] : 0.f;
+    Pl[kk][rr] = ra ? Al[oa] : 0.f;
+    Qh[kk][rr] = rb ? Ah[ob] : 0.f;
+    Ql[kk][rr] = rb ? Al[ob] : 0.f;
+  }
+  __syncthreads();
+#pragma unroll 4
+  for (int kk = 0; kk < UK; ++kk) {
+    float ah[4], al[4], bh[4], bl[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      ah[i] = Ph[kk][ty * 4 + i]; al[i] = Pl[kk][ty * 4 + i];
+      bh[i] = Qh[kk][tx * 4 + i]; bl[i] = Ql[kk][tx * 4 + i];
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float p = __fmul_rn(ah[i], bh[j]);
+        const float e = __fmaf_rn(ah[i], bh[j], -p);
+        const float c = __fmaf_rn(ah[i], bl[j], __fmul_rn(al[i], bh[j]));
+        const float s0 = __fadd_rn(sh[i][j], p);
+        const float bb = __fsub_rn(s0, sh[i][j]);
+        const float er = __fadd_rn(__fsub_rn(sh[i][j], __fsub_rn(s0, bb)), __fsub_rn(p, bb));
+        sh[i][j] = s0;
+        sl[i][j] = __fadd_rn(sl[i][j], __fadd_rn(er, __fadd_rn(e, c)));
+      }
+  }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int r = r0 + ty * 4 + i, c = c0 + tx * 4 + j;
+      if (r < n && c < n && c <= r) {
+        const size_t o = (size_t)r * n + c;
+        // (xh + xl) - (sh + sl): two-sum of the high parts, the rest into the low part
+        const float xh = Ah[o], xl = Al[o];
+        const float d0 = __fsub_rn(xh, sh[i][j]);
+        const float bb = __fsub_rn(d0, xh);
+        const float er = __fadd_rn(__fsub_rn(xh, __fsub_rn(d0, bb)), __fsub_rn(-sh[i][j], bb));
+        const float lo = __fadd_rn(er, __fsub_rn(xl, sl[i][j]));
+        const float hi = __fadd_rn(d0, lo);
+        Ah[o] = hi;
+        Al[o] = __fsub_rn(lo, __fsub_rn(hi, d0));
+      }
+    }
+}
+
 __global__ void k_add_diag(double* A, int n, int nreal, double lambda, const int* gate) {
   if (gate && !*gate) return;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
     A[(size_t)i * n + i] += (i < nreal) ? lambda : 1.0;  // a padding index gets 1 (its rhs is 0)
 }
 
-// L y = b then L^T x = y (x += the solution when accumulate), one CTA of 1024 threads,
-// blocked by CB; the right-hand side is carried in T
-template <typename T>
-__global__ void __launch_bounds__(1024) k_chol_solve(const T* L, int n, const double* b, double* x, int accumulate,
-                                                     const int* gate) {
+// L y = v then L^T z = y by blocks of CB rows, one launch per block and direction, spread over
+// the whole GPU (the single-CTA form held every row update on one SM).  In a forward launch
+// every CTA stages the diagonal block in shared memory and solves its CB rows from v (read only
+// in that launch) with one warp, column by column in registers (lane l holds rows l and l + 32:
+// each solved entry is broadcast by a shuffle and subtracted from the rows below it), CTA 0
+// stores them in y, and the warps of all CTAs subtract the block's contribution from the rows
+// below it (one warp per row, disjoint rows); the backward launch mirrors it on L^T with one
+// thread per row above the block.  The right-hand sides are carried in FP64 whatever the
+// factor's storage.
+template <typename F>
+__global__ void __launch_bounds__(256) k_trsv_fwd(F L, int n, int k0, double* v, double* y, const int* gate) {
   if (gate && !*gate) return;
-  extern __shared__ unsigned char solve_smem[];
-  T* v = reinterpret_cast<T*>(solve_smem);  // n
-  for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = (T)b[i];
+  __shared__ double Ld[CB][CB + 1];
+  __shared__ double ys[CB];
+  __shared__ double rdg[CB];
+  const int nb = min(CB, n - k0);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int o = threadIdx.x; o < nb * nb; o += blockDim.x) {
+    const int i = o / nb, j = o - i * nb;
+    if (j <= i) Ld[i][j] = L.get((size_t)(k0 + i) * n + k0 + j);
+  }
   __syncthreads();
+  if (threadIdx.x < nb) rdg[threadIdx.x] = 1.0 / Ld[threadIdx.x][threadIdx.x];
+  __syncthreads();
+  if (warp == 0) {
+    double v0 = (lane < nb) ? v[k0 + lane] : 0.0, v1 = (lane + 32 < nb) ? v[k0 + lane + 32] : 0.0;
+    for (int j = 0; j < nb; ++j) {
+      const double vj = (j < 32) ? __shfl_sync(0xffffffffu, v0, j) : __shfl_sync(0xffffffffu, v1, j - 32);
+      const double yj = vj * rdg[j];
+      if (lane == 0) ys[j] = yj;
+      if (lane > j && lane < nb) v0 -= Ld[lane][j] * yj;
+      if (lane + 32 > j && lane + 32 < nb) v1 -= Ld[lane + 32][j] * yj;
+    }
+  }
+  __syncthreads();
+  if (blockIdx.x == 0)
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) y[k0 + j] = ys[j];
+  const int nw = blockDim.x >> 5;
+  for (int i = k0 + nb + blockIdx.x * nw + warp; i < n; i += gridDim.x * nw) {
+    const size_t li = (size_t)i * n + k0;
+    double s = 0.0;
+    for (int l = lane; l < nb; l += 32) s += L.get(li + l) * ys[l];
+    s = warp_sum(s);
+    if (lane == 0) v[i] -= s;
+  }
+}
+
+template <typename F>
+__global__ void __launch_bounds__(256) k_trsv_bwd(F L, int n, int k0, double* y, double* z, const int* gate) {
+  if (gate && !*gate) return;
+  __shared__ double Ld[CB][CB + 1];
+  __shared__ double zs[CB];
+  __shared__ double rdg[CB];
+  const int nb = min(CB, n - k0);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int o = threadIdx.x; o < nb * nb; o += blockDim.x) {
+    const int i = o / nb, j = o - i * nb;
+    if (j <= i) Ld[i][j] = L.get((size_t)(k0 + i) * n + k0 + j);
+  }
+  __syncthreads();
+  if (threadIdx.x < nb) rdg[threadIdx.x] = 1.0 / Ld[threadIdx.x][threadIdx.x];
+  __syncthreads();
+  if (warp == 0) {
+    double y0 = (lane < nb) ? y[k0 + lane] : 0.0, y1 = (lane + 32 < nb) ? y[k0 + lane + 32] : 0.0;
+    for (int j = nb - 1; j >= 0; --j) {
+      const double yj = (j < 32) ? __shfl_sync(0xffffffffu, y0, j) : __shfl_sync(0xffffffffu, y1, j - 32);
+      const double zj = yj * rdg[j];
+      if (lane == 0) zs[j] = zj;
+      if (lane < j) y0 -= Ld[j][lane] * zj;
+      if (lane + 32 < j) y1 -= Ld[j][lane + 32] * zj;
+    }
+  }
+  __syncthreads();
+  if (blockIdx.x == 0)
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) z[k0 + j] = zs[j];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k0; i += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int l = 0; l < nb; ++l) s += L.get((size_t)(k0 + l) * n + i) * zs[l];
+    y[i] -= s;
+  }
+}
+
+__global__ void k_vcopy(const double* src, double* dst, int n, const int* gate) {
+  if (gate && !*gate) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = src[i];
+}
+__global__ void k_vadd(const double* src, double* dst, int n, const int* gate) {
+  if (gate && !*gate) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] += src[i];
+}
+
+// (L L^T)^-1 b into x (x += it when accumulate).  accumulate == 0: b is read only (copied to x
+// first).  accumulate != 0: b is overwritten (it carries the solve).  scratch: n doubles.
+// Returns the launches issued.
+template <typename F>
+static long long chol_apply(F L, int n, double* b, double* x, int accumulate, double* scratch, const int* gate,
+                            cudaStream_t s) {
+  long long launches = 0;
+  double* v = accumulate ? b : x;
+  if (!accumulate) {
+    k_vcopy<<<(n + 255) / 256, 256, 0, s>>>(b, x, n, gate);
+    ++launches;
+  }
   for (int k0 = 0; k0 < n; k0 += CB) {
-    const int nb = min(CB, n - k0);
-    if (threadIdx.x < 32) {
-      for (int j = 0; j < nb; ++j) {
-        T s = 0;
-        for (int l = threadIdx.x; l < j; l += 32) s += L[(size_t)(k0 + j) * n + k0 + l] * v[k0 + l];
-        s = warp_sum(s);
-        if (threadIdx.x == 0) v[k0 + j] = (v[k0 + j] - s) / L[(size_t)(k0 + j) * n + k0 + j];
-        __syncwarp();
-      }
-    }
-    __syncthreads();
-    for (int i = k0 + nb + threadIdx.x; i < n; i += blockDim.x) {
-      T s = 0;
-      for (int l = 0; l < nb; ++l) s += L[(size_t)i * n + k0 + l] * v[k0 + l];
-      v[i] -= s;
-    }
-    __syncthreads();
+    const int rows = n - k0 - CB;  // rows below the block
+    const int grid = rows > 0 ? min(2 * 152, (rows + 7) / 8) : 1;
+    k_trsv_fwd<F><<<grid, 256, 0, s>>>(L, n, k0, v, scratch, gate);
+    ++launches;
   }
+  // the forward pass is done with v: the backward one writes the solution there
   for (int k0 = ((n - 1) / CB) * CB; k0 >= 0; k0 -= CB) {
-    const int nb = min(CB, n - k0);
-    if (threadIdx.x < 32) {
-      for (int j = nb - 1; j >= 0; --j) {
-        T s = 0;
-        for (int l = j + 1 + threadIdx.x; l < nb; l += 32) s += L[(size_t)(k0 + l) * n + k0 + j] * v[k0 + l];
-        s = warp_sum(s);
-        if (threadIdx.x == 0) v[k0 + j] = (v[k0 + j] - s) / L[(size_t)(k0 + j) * n + k0 + j];
-        __syncwarp();
-      }
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < k0; i += blockDim.x) {
-      T s = 0;
-      for (int l = 0; l < nb; ++l) s += L[(size_t)(k0 + l) * n + i] * v[k0 + l];
-      v[i] -= s;
-    }
-    __syncthreads();
+    const int grid = k0 > 0 ? min(2 * 152, (k0 + 255) / 256) : 1;
+    k_trsv_bwd<F><<<grid, 256, 0, s>>>(L, n, k0, scratch, v, gate);
+    ++launches;
   }
-  for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = (accumulate ? x[i] : 0.0) + (double)v[i];
+  if (accumulate) {
+    k_vadd<<<(n + 255) / 256, 256, 0, s>>>(v, x, n, gate);
+    ++launches;
+  }
+  return launches;
 }
 
 // blocked factorisation of the lower triangle of A (n x n) in place; returns launches
@@ -754,23 +936,17 @@ template <typename T>
 static long long chol_factor(T* A, int n, int* bad, const int* gate, cudaStream_t s) {
   long long launches = 0;
   for (int k0 = 0; k0 < n; k0 += CB) {
-    k_chol_diag<T><<<1, 256, 0, s>>>(A, n, k0, bad, gate);
+    k_chol_diag<T, FacPlain<T>><<<1, 256, 0, s>>>(FacPlain<T>{A}, n, k0, bad, gate);
     ++launches;
     const int rest = n - k0 - CB;
     if (rest > 0) {
       const int nrb = (rest + CB - 1) / CB;
-      k_chol_trsm<T><<<nrb, CB, 0, s>>>(A, n, k0, gate);
+      k_chol_trsm<T, FacPlain<T>><<<(rest + TRSM_RB - 1) / TRSM_RB, TRSM_RB, 0, s>>>(FacPlain<T>{A}, n, k0, gate);
       k_chol_update<T><<<nrb * (nrb + 1) / 2, 256, 0, s>>>(A, n, k0, gate);
       launches += 2;
     }
   }
   return launches;
-}
-
-template <typename T>
-static void chol_apply(const T* L, int n, const double* b, double* x, int accumulate, const int* gate, cudaStream_t s) {
-  cudaFuncSetAttribute(k_chol_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(T) * n));
-  k_chol_solve<T><<<1, 1024, sizeof(T) * n, s>>>(L, n, b, x, accumulate, gate);
 }
 
 // gate (may be NULL): the fallback flag of the mixed solve; a factorisation it gates marks the
@@ -791,15 +967,15 @@ __global__ void k_zero_int(int* p, const int* gate) {
 // positive definite in floating point), info[1..2] = NaN (no eigenvalues computed).  With a gate,
 // every launch does nothing unless *gate != 0 when it runs.
 long long chol_solve(double* A, int n, int nreal, double lambda, const double* ebar, double* x, int* bad,
-                     double* info, const int* gate, cudaStream_t s, cudaError_t* err) {
+                     double* info, const int* gate, double* scratch, cudaStream_t s, cudaError_t* err) {
   long long launches = 0;
   k_zero_int<<<1, 1, 0, s>>>(bad, gate);
   k_add_diag<<<(n + 255) / 256, 256, 0, s>>>(A, n, nreal, lambda, gate);
   launches += 2;
   launches += chol_factor<double>(A, n, bad, gate, s);
-  chol_apply<double>(A, n, ebar, x, 0, gate, s);
+  launches += chol_apply(FacPlain<double>{A}, n, const_cast<double*>(ebar), x, 0, scratch, gate, s);
   k_chol_info<<<1, 1, 0, s>>>(bad, nreal, info, gate);
-  launches += 2;
+  launches += 1;
   *err = cudaGetLastError();
   return launches;
 }
@@ -874,24 +1050,83 @@ __global__ void k_mixed_info(const int* bad, int nreal, const double* rn, int it
 
 long long chol_solve_mixed(double* A, float* A32, int n, int nreal, double lambda, const double* ebar, double* x,
                            double* r, double* rn, double* part, int iters, int* bad, double* info, int* need64,
-                           cudaStream_t s, cudaError_t* err) {
+                           double* scratch, cudaStream_t s, cudaError_t* err) {
   long long launches = 0;
   cudaMemsetAsync(bad, 0, sizeof(int), s);
   k_mirror<<<1024, 256, 0, s>>>(A, n);
   k_lower_to_f32<<<1024, 256, 0, s>>>(A, A32, n, nreal, lambda);
   launches += 2;
   launches += chol_factor<float>(A32, n, bad, nullptr, s);
-  chol_apply<float>(A32, n, ebar, x, 0, nullptr, s);
-  ++launches;
+  launches += chol_apply(FacPlain<float>{A32}, n, const_cast<double*>(ebar), x, 0, scratch, nullptr, s);
   const int rgrid = (n + 7) / 8;
   for (int it = 0; it < iters; ++it) {
     k_residual<<<rgrid, 256, 0, s>>>(A, n, nreal, lambda, ebar, x, r, part);
-    chol_apply<float>(A32, n, r, x, 1, nullptr, s);
-    launches += 2;
+    launches += 1 + chol_apply(FacPlain<float>{A32}, n, r, x, 1, scratch, nullptr, s);
   }
   k_residual<<<rgrid, 256, 0, s>>>(A, n, nreal, lambda, ebar, x, r, part);
   k_rnorm<<<1, 1, 0, s>>>(part, rgrid, rn);
   k_mixed_info<<<1, 1, 0, s>>>(bad, nreal, rn, iters, info, need64);
+  launches += 3;
+  *err = cudaGetLastError();
+  return launches;
+}
+
+// ---- float-float factor (solve = 2): T + lambda split into float pairs (about 48 bits, the
+// precision of the float-float Gram that usually produced T), the trailing updates on the FP32
+// pipes (k_chol_update_ff), the diagonal blocks and panels in FP64 through the pair accessor,
+// then `iters` steps of refinement with FP64 residuals as in the FP32 mixed solve.  On this part
+// FP64 runs at 1/64 of the FP32 rate, so the factor's n^3/6 multiply-adds cost several times
+// less as float pairs (about 13 FP32 operations each) than in FP64.  The FP64 factorisation
+// replaces it only when the pair factorisation breaks down (need64 = 1); info[1] is the relative
+// residual after refinement.
+__global__ void k_lower_to_ff(const double* A, float* Fh, float* Fl, int n, int nreal, double lambda) {
+  const size_t nn = (size_t)n * n;
+  for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < nn; o += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(o / n), j = (int)(o % n);
+    double v = (j <= i) ? A[o] : 0.0;
+    if (i == j) v += (i < nreal) ? lambda : 1.0;
+    const float h = __double2float_rn(v);
+    Fh[o] = h;
+    Fl[o] = __double2float_rn(v - (double)h);
+  }
+}
+
+__global__ void k_ff_info(const int* bad, int nreal, const double* rn, int iters, double* info, int* need64) {
+  info[0] = *bad ? -1.0 : (double)nreal;
+  info[1] = (rn[1] > 0.0) ? sqrt(rn[0] / rn[1]) : 0.0;
+  info[2] = (double)iters;
+  *need64 = *bad ? 1 : 0;
+}
+
+long long chol_solve_ff(double* A, float* Fh, float* Fl, int n, int nreal, double lambda, const double* ebar, double* x,
+                        double* r, double* rn, double* part, int iters, int* bad, double* info, int* need64,
+                        double* scratch, cudaStream_t s, cudaError_t* err) {
+  long long launches = 0;
+  cudaMemsetAsync(bad, 0, sizeof(int), s);
+  k_mirror<<<1024, 256, 0, s>>>(A, n);
+  k_lower_to_ff<<<1024, 256, 0, s>>>(A, Fh, Fl, n, nreal, lambda);
+  launches += 2;
+  const FacFF F{Fh, Fl};
+  for (int k0 = 0; k0 < n; k0 += CB) {
+    k_chol_diag<double, FacFF><<<1, 256, 0, s>>>(F, n, k0, bad, nullptr);
+    ++launches;
+    const int rest = n - k0 - CB;
+    if (rest > 0) {
+      const int nrb = (rest + CB - 1) / CB;
+      k_chol_trsm<double, FacFF><<<(rest + TRSM_RB - 1) / TRSM_RB, TRSM_RB, 0, s>>>(F, n, k0, nullptr);
+      k_chol_update_ff<<<nrb * (nrb + 1) / 2, 256, 0, s>>>(Fh, Fl, n, k0, nullptr);
+      launches += 2;
+    }
+  }
+  launches += chol_apply(F, n, const_cast<double*>(ebar), x, 0, scratch, nullptr, s);
+  const int rgrid = (n + 7) / 8;
+  for (int it = 0; it < iters; ++it) {
+    k_residual<<<rgrid, 256, 0, s>>>(A, n, nreal, lambda, ebar, x, r, part);
+    launches += 1 + chol_apply(F, n, r, x, 1, scratch, nullptr, s);
+  }
+  k_residual<<<rgrid, 256, 0, s>>>(A, n, nreal, lambda, ebar, x, r, part);
+  k_rnorm<<<1, 1, 0, s>>>(part, rgrid, rn);
+  k_ff_info<<<1, 1, 0, s>>>(bad, nreal, rn, iters, info, need64);
   launches += 3;
   *err = cudaGetLastError();
   return launches;

@@ -591,6 +591,18 @@ template <typename T> struct JacobiTol;
 template <> struct JacobiTol<double> { static constexpr double eps = 1.1102230246251565e-16; static constexpr int sweeps = 30; };
 template <> struct JacobiTol<float> { static constexpr float eps = 5.9604645e-8f; static constexpr int sweeps = 30; };
 
+// Relative dot product above which a pair of rows of length L is rotated.  FP64: L eps.  FP32:
+// 2 sqrt(L) eps, a few times the typical rounding of a converged pair's dot product (sqrt(L)
+// eps): L eps (3.8e-6 at L = 64) leaves the kept rows non-orthogonal at a level that shows in
+// ln|psi| (on the 8x8, D = 4, chi = 16 workload after ten MinSR steps, against FP64: median
+// 3.5e-6 and 12 % of the samples above 1e-5, against 1.9e-6 and 3 % at 2 sqrt(L) eps, for 2 %
+// more rotations).
+__device__ __forceinline__ double jacobi_tol(int L) { return double(L) * JacobiTol<double>::eps; }
+__device__ __forceinline__ float jacobi_tol_f(int L) { return 2.f * sqrtf(float(L)) * JacobiTol<float>::eps; }
+template <typename R> __device__ __forceinline__ R jacobi_tol_r(int L);
+template <> __device__ __forceinline__ double jacobi_tol_r<double>(int L) { return jacobi_tol(L); }
+template <> __device__ __forceinline__ float jacobi_tol_r<float>(int L) { return jacobi_tol_f(L); }
+
 // Rows whose squared norm is at most `tiny` are numerically zero singular values: the Jacobi
 // sweeps never rotate them against the others, so they are not orthogonal to the kept
 // directions and must not enter the kept basis.  Set them to exactly zero.  Ends with a barrier.
@@ -608,7 +620,7 @@ __device__ void zero_tiny_rows(T* X, int m, int L, int ldx, typename Scal<T>::R 
 }
 
 // One-sided (Hestenes) Jacobi on the rows of X (m rows, m even, row length L, leading dim
-// ldx): rotate pairs of rows whose relative dot product exceeds the tolerance tol = L eps
+// ldx): rotate pairs of rows whose relative dot product exceeds the tolerance tol (jacobi_tol_r)
 // (well above the sqrt(L) eps rounding noise of a converged pair's dot product), skipping pairs
 // where one row is numerically zero (squared norm below (L eps)^2 of the largest), and stop after
 // the first sweep in which no pair had a relative dot product of sqrt(tol) or more: by the
@@ -628,7 +640,7 @@ __device__ int hestenes_rows_smem(T* X, int m, int L, int ldx, int* flag, unsign
   const int grp = lane >> 3, sub = lane & 7, ngroups = nw * 4;
   const unsigned gmask = 0xffu << (grp * 8);
   const R eps = JacobiTol<R>::eps;
-  const R tol = R(L) * eps;
+  const R tol = jacobi_tol_r<R>(L);
   const R stop = sqrt(tol);
   R tiny = 0;
   unsigned long long nrot = 0;
@@ -769,7 +781,7 @@ __device__ __noinline__ int hestenes_rows_grp(T* X, int m, int L, int ldx, int* 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int g = lane >> 3, u = lane & 7;
   const T eps = JacobiTol<T>::eps;
-  const T tol = T(L) * eps;
+  const T tol = jacobi_tol_r<T>(L);
   const int NB = ((m + 7) / 8) * 2;  // blocks of four rows, an even number of them
   // tiny = (L eps)^2 times the largest squared row norm
   T nmax = 0;

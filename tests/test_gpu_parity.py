@@ -307,7 +307,8 @@ def test_fp32_handle_close_to_oracle(P):
 
 def test_mixed_precision_preset(P):
     # PEPS_PREC_MIXED: the FP32 contraction kernels (results equal an FP32 handle's bit for bit),
-    # a float-float Gram and the FP32 Cholesky with FP64 refinement (info[2] = refinement steps)
+    # a float-float Gram and the float-float Cholesky with FP64 refinement (info[2] = refinement
+    # steps)
     from oracle import minsr
     lat = I.Lattice(5, 5, 2, 3)
     th = I.peps_random(lat, 81, scale=0.5, bias=1.0, alpha=1.5)
@@ -327,7 +328,7 @@ def test_mixed_precision_preset(P):
     hm.last_status()
     d_ref, _ = minsr.minsr(rm["O"].double().cpu().numpy(), rm["eloc"][:, 0].cpu().numpy(), lam=1e-3, tau=0.05)
     assert np.linalg.norm(dth.cpu().numpy() - d_ref) <= 1e-7 * np.linalg.norm(d_ref)
-    assert float(info[2]) in (0.0, 4.0)  # refinement steps, or 0 where the FP64 factor took over
+    assert float(info[2]) in (0.0, 2.0)  # refinement steps, or 0 where the FP64 factor took over
 
 
 def test_amplitudes_and_logderiv_entry_points(P):
@@ -509,6 +510,41 @@ def test_minsr_mixed_solve_falls_back_to_fp64(P):
     # the two FP64 routes differ by about cond * eps ~ 1e-4 here (the CPU's Cholesky and eigh
     # disagree by 1.1e-4 on this input), hence the gate
     assert rel <= 1e-3
+
+
+@pytest.mark.parametrize("ns,npar,lam", [(700, 300, 1e-3), (1030, 1200, 1e-4), (333, 2000, 1e-4)])
+def test_minsr_float_float_solve_vs_oracle(P, ns, npar, lam):
+    # float-float Cholesky (about 48 bits) of T + lambda, then 2 refinement steps with FP64
+    # residuals: as accurate as the FP64 solve; with the float-float Gram too (the MIXED preset)
+    from oracle import minsr
+    rng = np.random.default_rng(ns + 5)
+    O = rng.standard_normal((ns, npar)) + 0.1 * rng.standard_normal(npar)
+    e = rng.standard_normal(ns) - 3.0
+    d_ref, inf_ref = minsr.minsr(O, e, lam=lam, rcond=0.0, tau=0.1)
+    for gram in (0, 2):
+        dth, info = _minsr_raw(P, O, e, lam, 0.0, 0.1, gram=gram, solve=2)
+        rel = np.linalg.norm(dth - d_ref) / np.linalg.norm(d_ref)
+        print(f"float-float solve (gram {gram}): relative dtheta error {rel:.2e}, final residual {info[1]:.2e}")
+        assert int(info[0]) == inf_ref["rank"]
+        assert info[2] == 2 and info[1] <= 1e-12
+        assert rel <= 1e-9
+
+
+def test_minsr_float_float_solve_badly_conditioned(P):
+    # cond(T + lambda) ~ 1.5e11, where the FP32 factor breaks down: cond * 2^-48 ~ 5e-4, so the
+    # float-float factor holds (no FP64 fallback, info[2] = 2) and the refinement with FP64
+    # residuals brings dtheta as close to the oracle's as the FP64 factorisation's
+    from oracle import minsr
+    O, e = _badly_scaled(11)
+    d_ref, inf_ref = minsr.minsr(O, e, lam=1e-4, rcond=0.0, tau=0.1)
+    dff, info = _minsr_raw(P, O, e, 1e-4, 0.0, 0.1, solve=2)
+    d64, _ = _minsr_raw(P, O, e, 1e-4, 0.0, 0.1, solve=0)
+    rel = np.linalg.norm(dff - d_ref) / np.linalg.norm(d_ref)
+    rel64 = np.linalg.norm(d64 - d_ref) / np.linalg.norm(d_ref)
+    print(f"float-float solve at cond ~1.5e11: {rel:.2e} from the oracle (FP64 Cholesky: {rel64:.2e}), "
+          f"residual {info[1]:.2e}")
+    assert info[0] == inf_ref["rank"] and info[2] == 2
+    assert rel <= 1e-3 and rel <= 2.0 * rel64 + 1e-9
 
 
 def test_minsr_breakdown_warns_and_zeroes_dtheta(P):
