@@ -614,6 +614,27 @@ struct FacFF {
   }
 };
 
+// sqrt(d) and 1 / sqrt(d) of a pivot d > 0.  Double: the single-precision reciprocal square root
+// refined by two Newton steps y <- y (3 - d y^2) / 2 (each doubles the correct bits: 23 -> 46 ->
+// beyond double), a short chain of FP64 operations where sqrt and a division would each take a
+// long one on a GPU with few FP64 units; outside the float range the plain sqrt and division.
+__device__ __forceinline__ void pivot_sqrt(double d, double& s, double& r) {
+  if (d > 1e-30 && d < 1e30) {
+    double y = (double)rsqrtf((float)d);
+    y = y * fma(-0.5 * d, y * y, 1.5);
+    y = y * fma(-0.5 * d, y * y, 1.5);
+    r = y;
+    s = d * y;
+  } else {
+    s = sqrt(d);
+    r = 1.0 / s;
+  }
+}
+__device__ __forceinline__ void pivot_sqrt(float d, float& s, float& r) {
+  s = sqrtf(d);
+  r = 1.f / s;
+}
+
 // factor the CB x CB diagonal block at (k0, k0) in place (lower triangle), one CTA.  Per column
 // j: thread 0 takes the pivot's square root and its reciprocal; then every thread updates its
 // share of the trailing triangle with column j still unscaled (a_il -= a_ij a_lj / a_jj; four
@@ -637,10 +658,11 @@ __global__ void __launch_bounds__(256) k_chol_diag(F A, int n, int k0, int* bad,
     if (tid == 0) {
       const T d = L[j][j];
       const bool ok = d > T(0);  // false for NaN too
-      const T dj = ok ? sqrt(d) : T(1);
+      T dj, rj;
+      pivot_sqrt(ok ? d : T(1), dj, rj);
       if (!ok) *bad = 1;
       L[j][j] = dj;
-      rd[j] = T(1) / dj;
+      rd[j] = rj;
     }
     __syncthreads();
     const T r2 = rd[j] * rd[j];
@@ -815,8 +837,8 @@ __global__ void k_add_diag(double* A, int n, int nreal, double lambda, const int
 // in that launch) with one warp, column by column in registers (lane l holds rows l and l + 32:
 // each solved entry is broadcast by a shuffle and subtracted from the rows below it), CTA 0
 // stores them in y, and the warps of all CTAs subtract the block's contribution from the rows
-// below it (one warp per row, disjoint rows); the backward launch mirrors it on L^T with one
-// thread per row above the block.  The right-hand sides are carried in FP64 whatever the
+// below it (one warp per row, disjoint rows); the backward launch mirrors it on L^T with four
+// threads per row above the block.  The right-hand sides are carried in FP64 whatever the
 // factor's storage.
 template <typename F>
 __global__ void __launch_bounds__(256) k_trsv_fwd(F L, int n, int k0, double* v, double* y, const int* gate) {
@@ -884,10 +906,17 @@ __global__ void __launch_bounds__(256) k_trsv_bwd(F L, int n, int k0, double* y,
   __syncthreads();
   if (blockIdx.x == 0)
     for (int j = threadIdx.x; j < nb; j += blockDim.x) z[k0 + j] = zs[j];
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k0; i += gridDim.x * blockDim.x) {
+  // rows above the block: four threads per row, each summing a quarter of the block's columns,
+  // combined by two shuffles (warp-uniform trips)
+  const int tot = 4 * k0;
+  for (int t0 = blockIdx.x * blockDim.x; t0 < tot; t0 += gridDim.x * blockDim.x) {
+    const int t = t0 + threadIdx.x, i = t >> 2, part = t & 3;
     double s = 0.0;
-    for (int l = 0; l < nb; ++l) s += L.get((size_t)(k0 + l) * n + i) * zs[l];
-    y[i] -= s;
+    if (t < tot)
+      for (int l = part; l < nb; l += 4) s += L.get((size_t)(k0 + l) * n + i) * zs[l];
+    s += __shfl_xor_sync(0xffffffffu, s, 1);
+    s += __shfl_xor_sync(0xffffffffu, s, 2);
+    if (t < tot && part == 0) y[i] -= s;
   }
 }
 
@@ -920,7 +949,7 @@ static long long chol_apply(F L, int n, double* b, double* x, int accumulate, do
   }
   // the forward pass is done with v: the backward one writes the solution there
   for (int k0 = ((n - 1) / CB) * CB; k0 >= 0; k0 -= CB) {
-    const int grid = k0 > 0 ? min(2 * 152, (k0 + 255) / 256) : 1;
+    const int grid = k0 > 0 ? min(4 * 152, (4 * k0 + 255) / 256) : 1;
     k_trsv_bwd<F><<<grid, 256, 0, s>>>(L, n, k0, scratch, v, gate);
     ++launches;
   }

@@ -1139,15 +1139,46 @@ __device__ double env_row_step(const G& g, const T* Eprev, T* Eout, const T* Tpa
     blk_gemm<4, 4>(P, w.A, Y, chi * chi, D * D, D * D, 1, chi, 0, D, 0,
                    [=](int m) { return Off2{(m / chi) * D * D * chi + m % chi, (m / chi) * D * LY + m % chi}; },
                    [=](int nn) { return Off2{(nn / D) * D * D * D + nn % D, (nn / D) * LY + (nn % D) * chi}; });
-    // R_{k-1} from the left pass
-    blk_copy(w.R, w.Rhist + (size_t)(k - 1) * n * n, n * n);
+    // R_{k-1} from the left pass: only its first rks_s[k] rows are nonzero
+    const int rkx = rks_s[k] < n ? rks_s[k] : n;
+    blk_copy(w.R, w.Rhist + (size_t)(k - 1) * n * n, rkx * n);
     __syncthreads();
-    // X = R_{k-1} Y (m = q, n = i, k = j), padded to mX rows.  R is stored with explicit zeros
-    // below the diagonal, so the full sum adds exact zeros before the j >= i terms.
-    if (mX > n)
-      for (int q = tid; q < Lr; q += NT) X[(size_t)n * LX + q] = T(0);
-    blk_gemm<2, 8>(Y, w.R, X, Lr, n, n, 1, LY, 0, 1, 0, [=](int m) { return Off2{m, m}; },
-                   [=](int i) { return Off2{i * n, i * LX}; });
+    // X = R_{k-1} Y (m = q, n = i, k = j), padded to mX rows, on the nonzero rows of R_{k-1}:
+    // a thread takes two columns q and a block of 8 rows i in [8b, 8b + 8), and since R is upper
+    // triangular (explicit zeros below the diagonal) its sums start at j = 8b: the terms skipped
+    // are exact zeros and the others are added in the same order as the full product.  Rows from
+    // rkx on are zero.
+    {
+      const int nbk = (rkx + 7) / 8, tmq = (Lr + 1) / 2;
+      for (int t = tid; t < tmq * nbk; t += NT) {
+        const int ti = t % tmq, b = t / tmq;
+        const int q0 = ti, q1 = ti + tmq;
+        const bool v1 = q1 < Lr;
+        T acc0[8], acc1[8];
+#pragma unroll
+        for (int ii = 0; ii < 8; ++ii) { acc0[ii] = T(0); acc1[ii] = T(0); }
+        for (int j = 8 * b; j < n; ++j) {
+          const T a0 = Y[(size_t)j * LY + q0], a1 = v1 ? Y[(size_t)j * LY + q1] : T(0);
+#pragma unroll
+          for (int ii = 0; ii < 8; ++ii) {
+            const int i = 8 * b + ii;
+            const T r = (i < rkx) ? w.R[(size_t)i * n + j] : T(0);
+            acc0[ii] = mad(acc0[ii], a0, r);
+            acc1[ii] = mad(acc1[ii], a1, r);
+          }
+        }
+#pragma unroll
+        for (int ii = 0; ii < 8; ++ii) {
+          const int i = 8 * b + ii;
+          if (i < rkx) {
+            X[(size_t)i * LX + q0] = acc0[ii];
+            if (v1) X[(size_t)i * LX + q1] = acc1[ii];
+          }
+        }
+      }
+      for (int o = tid; o < (mX - rkx) * Lr; o += NT) X[(size_t)(rkx + o / Lr) * LX + o % Lr] = T(0);
+      __syncthreads();
+    }
     // norms, singular values and the selection in the real type (the QR's taus, in the same
     // buffer, are no longer needed)
     using RT = typename Scal<T>::R;
