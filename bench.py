@@ -207,17 +207,17 @@ def _peaks():
         return {}
 
 
-# DRAM bytes (read + write) of one sampler call of 2 sweeps in FP32 (every kernel of the split
-# sweep), from ncu captures of 304 chains (one kernel per capture), scaled by the chains processed
+# DRAM bytes (read + write) of one sampler call of 2 sweeps in FP32 (the 31 kernel launches of the
+# split sweep), from one ncu capture of such a call at 304 chains, scaled by the chains processed
 # (each chain's environment rows and partials are its own traffic); None until such a capture of
-# the current kernels exists.  profiles/sampler_split_heis8x8_D4_chi16_ns304.md: 1.277 GB per call
-# of 2 sweeps over 304 chains (k_env one-side pass 0.223 GB, 16 k_sweep_moves 0.739 GB, 12
-# k_env_row 0.315 GB).
-_SAMPLER_CAPTURE = {"bytes": 1.250e9, "chains": 304, "sweeps": 2}
+# the current kernels exists.  profiles/sampler_split_heis8x8_D4_chi16_ns304.md: 1.192 GB per call
+# of 2 sweeps over 304 chains (k_env one-side pass 0.223 GB, 16 k_sweep_moves 0.700 GB, 14
+# k_env_row 0.269 GB).
+_SAMPLER_CAPTURE = {"bytes": 1.1915e9, "chains": 304, "sweeps": 2}
 
 
 def _measured_traffic(kernel, ns, sweeps, prec):
-    """Per-call DRAM traffic of the dominant kernel (set) from its ncu capture, or None where no
+    """DRAM traffic of one call of the dominant kernel (set) from its ncu capture, or None where no
     capture of the current kernels at this precision and sweep count exists."""
     from paper_2503_12557_gb300 import peps as P
     c = _SAMPLER_CAPTURE
@@ -406,7 +406,9 @@ def run_gpu(a):
     roof = {"kernel": {"env": "k_env", "sample": sampler_name, "row": "k_row", "pair": "k_pair",
                        "minsr_gram": "k_gram"}[dom],
             "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": _measured_traffic(dom, ns, a.sweeps, prec),
+            # per launch, as achieved: the call's bytes spread over the launches the call made
+            "traffic": (None if _measured_traffic(dom, ns, a.sweeps, prec) is None else
+                        _measured_traffic(dom, ns, a.sweeps, prec) * a.steps / max(1, launches[dom])),
             "peak_source": ("measured: peps_probe_fma FP32 (derived 152 SMs x 128 lanes x 2 x max clock = %.1f)"
                             % fp32_derived if peak == fp32_peak else
                             "measured: peps_probe_fma FP64" if peak == fp64_peak else "MEASURED_PEAKS bf16_tflops"),

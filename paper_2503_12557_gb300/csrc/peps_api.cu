@@ -964,7 +964,19 @@ extern "C" peps_status peps_sample(peps_handle* h, int move, uint8_t* S_dev, int
     h->rs_gen = -1;
   }
   CK(launch_status_or(st, Ns, h->sword, s), "status word");
-  tstop(h, ts, s, 2);
+  // kernel launches of the call: the FP32 split sweep launches a one-side k_env pass (every
+  // downward sweep, and an upward sweep that opens the call), then per row k_sweep_moves and,
+  // except after the last row, k_env_row; the other precisions one k_sample; then the status OR
+  long long nl = 1;
+  if (h->elem == 1) {
+    for (int t = 0; t < nsweeps; ++t) {
+      const bool up = ((sweep0 + (uint64_t)t) & 1ull) != 0;
+      nl += (up && t > 0 ? 0 : 1) + 2 * (long long)h->cfg.Lx - 1;
+    }
+  } else {
+    nl += 1;
+  }
+  tstop(h, ts, s, nl);
   return PEPS_OK;
 }
 
