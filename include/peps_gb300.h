@@ -106,7 +106,9 @@ typedef struct {
                      (T + lambda as float pairs of about 48 bits, the trailing updates on the
                      FP32 pipes, diagonal blocks and panels in FP64) followed by 2 steps of
                      refinement with FP64 residuals: the FP64 factor's work at a fraction of
-                     its time on GPUs whose FP64 rate is a small fraction of their FP32 rate */
+                     its time on GPUs whose FP64 rate is a small fraction of their FP32 rate;
+                     3 = FP64 Cholesky when rcond == 0, and the tridiagonal eigen route (see
+                     minsr_step) instead of the cyclic Jacobi when rcond > 0 */
     int cplx;     /* 0 = real PEPS; 1 = complex PEPS: theta is N_p (re, im) pairs of doubles,
                      O is N_s x N_p complex numbers in the handle's precision ((re, im) pairs
                      of doubles or floats), phases and E_loc are complex.  Not with gram = 1,
@@ -283,8 +285,21 @@ peps_status peps_local_energy_bound(peps_handle* h, const peps_hamiltonian* H, c
  * doubles, or N_p (re, im) pairs for a complex PEPS (written).  A complex PEPS runs the same
  * steps on the real embedding W = [[Re Obar, -Im Obar], [Im Obar, Re Obar]] (W W^T is the real
  * form of the Hermitian T = Obar Obar^H), with the rank in info[0] counted once per eigenvalue;
- * info_dev: 4 doubles.  rcond > 0: eigendecomposition by cyclic Jacobi, info = (rank kept,
- * min Lambda, max Lambda, Jacobi sweeps).  rcond == 0 (nothing cut, lambda > 0): the same
+ * info_dev: 4 doubles.  rcond > 0: the eigendecomposition with the cutoff, info = (rank kept,
+ * min Lambda, max Lambda, iterations): with cfg.solve 0, 1 or 2 by cyclic Jacobi (iterations =
+ * sweeps, -1 at the sweep limit); with cfg.solve == 3 without forming V: Householder reduction of
+ * T to tridiagonal form, implicit QR steps with a Wilkinson shift on the tridiagonal form
+ * applied to the transformed ebar (the rotations recorded, one double each, in the handle's
+ * workspace, then replayed in reverse), and the reflectors applied back (iterations = QR steps;
+ * info[0] = -1 and a breakdown as below when an eigenvalue needs more than 60 steps or the
+ * record outgrows its 2 max(n^2, 4096) doubles, n = Ns rounded up to even).  The two routes keep
+ * the same eigenvalues; their results differ by rounding, the tridiagonal route's error growing
+ * as eps max(Lambda) / (smallest kept Lambda + lambda) (both are backward stable; Jacobi has the
+ * higher relative accuracy on small eigenvalues).  The tridiagonal route needs about 2 Ns^3
+ * FP64 flops in parallel launches against tens of Ns^3 for the Jacobi sweeps, but its QR chain
+ * is one thread of sequential FP64 arithmetic, about 0.9 Ns^2 rotations: on a GPU whose FP64
+ * rate is a small fraction of its FP32 rate that chain dominates (GB300: 3.2 s at 1024 rows,
+ * 47 s at 4096, 184 s at 8192, against 0.37 s and 20 s for the Jacobi).  rcond == 0 (nothing cut, lambda > 0): the same
  * operator (T + lambda)^-1 applied through a Cholesky factorisation, info = (Ns, NaN, NaN, -1)
  * with cfg.solve == 0, info = (Ns, |ebar - (T + lambda) x| / |ebar|, refinement steps, -1)
  * with cfg.solve == 1, where refinement steps = 0 means that the FP32 factor failed or the
@@ -300,7 +315,8 @@ peps_status peps_local_energy_bound(peps_handle* h, const peps_hamiltonian* H, c
  * residuals of the refinement FP64.  The call is
  * asynchronous like every other (no host round trip: the mixed solve's FP64 fallback and the
  * zeroing of dtheta on a breakdown are decided on the device; rcond > 0 runs the whole cyclic
- * Jacobi in one cooperative launch); a breakdown is reported by peps_last_status. */
+ * Jacobi in one cooperative launch, or the tridiagonal route's launches, about 6 Ns of them); a
+ * breakdown is reported by peps_last_status. */
 peps_status minsr_step(peps_handle* h, const void* O_dev, const double* eloc_dev, const double* w_dev,
                        int Ns, double lambda, double rcond, double tau, double* dtheta_dev,
                        double* info_dev, void* stream);

@@ -81,6 +81,7 @@ struct peps_handle {
   long long ms_np = 0;
   double *Obar = nullptr, *Tm = nullptr, *Vm = nullptr, *Hm = nullptr, *mean = nullptr, *ebar = nullptr,
          *yv = nullptr, *xv = nullptr, *cnt = nullptr;
+  double* td = nullptr;  // tridiagonal eigen route: vectors and partial sums (td_workspace_doubles)
   // timing: event pairs per kernel class, recorded on the call's stream when enabled
   bool timing = false;
   std::vector<cudaEvent_t> evpool;
@@ -402,7 +403,7 @@ extern "C" peps_status peps_create_ex(peps_handle** out, const peps_config* cfg,
     c.solve = 2;
   }
   if (c.gram != 0 && c.gram != 1 && c.gram != 2) return PEPS_E_ARG;
-  if (c.solve != 0 && c.solve != 1 && c.solve != 2) return PEPS_E_ARG;
+  if (c.solve < 0 || c.solve > 3) return PEPS_E_ARG;
   if (c.cplx != 0 && c.cplx != 1) return PEPS_E_ARG;
   if (!(c.trunc_weight >= 0.0 && c.trunc_weight < 1.0)) return PEPS_E_ARG;
   if (c.cplx && c.gram == 1) return PEPS_E_UNSUPPORTED;  // the split-BF16 Gram is real only
@@ -467,7 +468,7 @@ extern "C" peps_status peps_destroy(peps_handle* h) {
   if (!h) return PEPS_E_ARG;
   void* ptrs[] = {h->Tpad, h->site_off, h->envs, h->logs, h->wdisc, h->rowout, h->pairout, h->status_tmp,
                   h->gscratch, h->d_tinfo, h->d_ab, h->d_eh, h->d_rowoff, h->d_pairoff, h->d_pij, h->d_pv,
-                  h->d_onsite, h->Obar, h->Tm, h->Vm, h->Hm, h->mean, h->ebar, h->yv, h->xv, h->cnt, h->ctr,
+                  h->d_onsite, h->Obar, h->Tm, h->Vm, h->Hm, h->mean, h->ebar, h->yv, h->xv, h->cnt, h->td, h->ctr,
                   h->lp_Sp, h->lp_l0, h->lp_l1, h->lp_aux, h->g_hi, h->g_lo, h->bout, h->DL, h->dl_work,
                   h->dl_status, h->dscratch, h->ustat, h->sword};
   for (void* p : ptrs)
@@ -981,19 +982,25 @@ extern "C" peps_status peps_sample(peps_handle* h, int move, uint8_t* S_dev, int
 }
 
 // ---- MinSR -------------------------------------------------------------------------------
+// doubles in each of the MinSR V and H buffers: n x n, and at least 4096 so that the rotation
+// record of the tridiagonal eigen route (about n^2 doubles, relatively more for tiny n) fits
+static size_t rec_doubles(int n) { return std::max((size_t)n * n, (size_t)4096); }
+
 // MinSR workspace for Ns rows of Np real columns (a complex handle passes its real embedding:
 // 2 Ns x 2 Np)
 static peps_status ensure_minsr(peps_handle* h, int Ns, long long Np) {
   const int n = Ns + (Ns & 1);
   if (h->ms_cap >= n && h->ms_np >= Np) return PEPS_OK;
-  double** bufs[] = {&h->Obar, &h->Tm, &h->Vm, &h->Hm, &h->mean, &h->ebar, &h->yv, &h->xv, &h->cnt};
+  double** bufs[] = {&h->Obar, &h->Tm, &h->Vm, &h->Hm, &h->mean, &h->ebar, &h->yv, &h->xv, &h->cnt, &h->td};
   for (double** b : bufs)
     if (*b) { h_free(h, *b); *b = nullptr; }
   const size_t nn = (size_t)n * n;
+  const size_t nr = rec_doubles(n);  // V and H: also the tridiagonal route's rotation record
   // Obar holds n rows (the capacity): a later call with an even Ns up to n reuses it
   if (h_malloc(h, (void**)&h->Obar, sizeof(double) * (size_t)n * Np) != cudaSuccess ||
-      h_malloc(h, (void**)&h->Tm, sizeof(double) * nn) != cudaSuccess || h_malloc(h, (void**)&h->Vm, sizeof(double) * nn) != cudaSuccess ||
-      h_malloc(h, (void**)&h->Hm, sizeof(double) * nn) != cudaSuccess ||
+      h_malloc(h, (void**)&h->Tm, sizeof(double) * nn) != cudaSuccess || h_malloc(h, (void**)&h->Vm, sizeof(double) * nr) != cudaSuccess ||
+      h_malloc(h, (void**)&h->Hm, sizeof(double) * nr) != cudaSuccess ||
+      h_malloc(h, (void**)&h->td, sizeof(double) * td_workspace_doubles(n)) != cudaSuccess ||
       h_malloc(h, (void**)&h->mean, sizeof(double) * (size_t)Np) != cudaSuccess ||
       h_malloc(h, (void**)&h->ebar, sizeof(double) * n) != cudaSuccess || h_malloc(h, (void**)&h->yv, sizeof(double) * n) != cudaSuccess ||
       h_malloc(h, (void**)&h->xv, sizeof(double) * n) != cudaSuccess || h_malloc(h, (void**)&h->cnt, sizeof(double) * 16) != cudaSuccess)
@@ -1040,7 +1047,17 @@ static peps_status minsr_solve_core(peps_handle* h, int Ns, double lambda, doubl
   const int n = Ns + (Ns & 1);
   int* need64 = (int*)(h->cnt + 3);
   cudaError_t e = cudaSuccess;
-  if (rcond > 0.0) {
+  if (rcond > 0.0 && h->cfg.solve == 3) {
+    // eigendecomposition with the pseudo-inverse cutoff through the tridiagonal form, applied to
+    // ebar without forming V (opt-in: its QR chain is one thread of FP64 arithmetic, slower on
+    // this GPU than the parallel Jacobi up to 8192 rows); the QR step count written to info[3]
+    const int ts = tstart(h, TC_EIG, s);
+    long long nl = 0;
+    const size_t nr = rec_doubles(n);
+    CK(td_pinv_apply(h->Tm, n, Ns, h->ebar, lambda, rcond, h->xv, h->Vm, nr, h->Hm, nr, h->td, info_dev, s, &nl),
+       "tridiagonal eigen route");
+    tstop(h, ts, s, nl);
+  } else if (rcond > 0.0) {
     // eigendecomposition with the pseudo-inverse cutoff: one cooperative launch, the sweep count
     // written to info[3] on the device
     int ts = tstart(h, TC_EIG, s);

@@ -237,6 +237,16 @@ cudaError_t jacobi_eig(double* A, double* V, int n, unsigned long long* cnt, dou
                        double* info_sweeps, int max_sweeps, cudaStream_t s);
 cudaError_t launch_minsr_apply(const double* A, const double* V, const double* ebar, int n, int nreal, double lambda,
                                double rcond, double* y, double* x, double* info, cudaStream_t s);
+// x = V diag(kept / (Lambda + lambda)) V^T ebar for the symmetric N x N matrix A (full storage,
+// leading dimension ld >= N, overwritten by the Householder reflectors) through its tridiagonal
+// form, without forming V (peps_eig.cu); x: ld doubles (zero beyond N); r0 / r1: the rotation
+// record's two segments (cap0 / cap1 doubles); ws: td_workspace_doubles(ld) doubles; info as
+// launch_minsr_apply plus info[3] = QR steps (-1 and info[0] = -1 when the QR iteration fails).
+// *launches = kernels launched.
+size_t td_workspace_doubles(int n);
+cudaError_t td_pinv_apply(double* A, int ld, int N, const double* ebar, double lambda, double rcond, double* x,
+                          double* r0, size_t cap0, double* r1, size_t cap1, double* ws, double* info,
+                          cudaStream_t s, long long* launches);
 cudaError_t launch_obar_t_x(const double* Obar, const double* x, int Ns, long long Np, double tau, double* dtheta,
                             cudaStream_t s);
 // x = (A + lambda I)^-1 ebar by blocked Cholesky (A overwritten by its factor); returns launches
